@@ -1,0 +1,262 @@
+"""CPU oracle for the Kadir-Brady saliency hot path -- TEST INFRASTRUCTURE.
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg (and its
+`--impl reference` arm) may import this package.  The product path (the
+C-ABI library and its Python binding) never imports it, and the two share no
+code: this package is plain C (ks_oracle.c, built with gcc -O2
+-ffp-contract=off) behind ctypes, plus numpy marshalling.
+
+Every function follows a passage of arXiv 1310.6736 (cited in ks_oracle.c)
+and is pinned by tests/test_oracle_*.py against brute force, closed forms
+(Eq. 2-3) and invariants.  Parity unpinned: none of the functions here; the
+paper's accuracy experiments (Table 1, Jaccard indices) need datasets that
+are not available and are out of scope.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ks_oracle.c")
+_LIB = os.path.join(_HERE, "libks_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+BIN_CLAMP_SHIFT, BIN_AFFINE_F32, BIN_WINDOW = 0, 1, 2
+
+
+def build(force=False):
+    """Compile ks_oracle.c into libks_oracle.so (gcc, OpenMP, no FMA)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared",
+           "-fPIC", "-o", tmp, _SRC, "-lquadmath", "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB)
+            P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int, C.c_double
+            sig = {
+                "ko_tables": (None, [I64, P, P]),
+                "ko_bin_int": (None, [P, I64, I32, I32, I32, I32, I32, P]),
+                "ko_bin_f32": (None, [P, I64, I32, P, P, P]),
+                "ko_window_counts": (None, [P, I32, I32, I32, I32, I32, I32, I32, I32, P]),
+                "ko_entropy": (D, [P, I32, P, P]),
+                "ko_weight": (D, [P, P, I32, I32, I32]),
+                "ko_dense": (None, [P, I32, I32, I32, I32, I32, I32, I32, P, P, P, I64, I32,
+                                    I32, P, P, P, P]),
+                "ko_seed_grid": (I64, [I32, I32, I32, I32, P]),
+                "ko_octant_climb": (None, [P, I32, I32, I32, I32, I32, I32, I32, I32, P, P,
+                                           P, I64, I32, P, P, P, P, P, P, P, P]),
+                "ko_meanshift": (None, [P, I32, I32, I32, I32, I32, I32, I32, P, P, P, I64,
+                                        I32, P, P, P, P, P]),
+                "ko_octant_counts": (None, [P, I32, I32, I32, I32, I32, I32, I32, I32, I32, P]),
+                "ko_octant_one_step": (None, [P, I32, I32, I32, I32, I32, I32, P, P, I32, I32,
+                                              I32, P]),
+                "ko_ms_window": (None, [P, I32, I32, I32, I32, I32, I32, I32, I32, P, P]),
+                "ko_max_threads": (I32, []),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+_tables = {"n": -1, "T": None, "L": None}
+
+
+def tables(nmax):
+    """(T, L) with T[c] = c ln c and L[n] = ln n, correctly rounded, c,n <= nmax."""
+    with _lock:
+        if _tables["n"] < nmax:
+            n = max(nmax, 1)
+            T = np.empty(n + 1, np.float64)
+            Lt = np.empty(n + 1, np.float64)
+            _tables.update(n=n, T=T, L=Lt)
+            build_needed = True
+        else:
+            build_needed = False
+    if build_needed:
+        lib().ko_tables(_tables["n"], _p(_tables["T"]), _p(_tables["L"]))
+    return _tables["T"], _tables["L"]
+
+
+def ball_size(r):
+    """|Ball(r)| = number of integer offsets with |o|^2 <= r^2."""
+    r = int(r)
+    if r < 0:
+        return 0
+    d = np.arange(-r, r + 1)
+    return int(((d[:, None, None] ** 2 + d[None, :, None] ** 2 + d[None, None, :] ** 2)
+                <= r * r).sum())
+
+
+def bin_volume(vol, binning):
+    """Stored-bin volume (uint8, b+1; 0 = not counted) for a raw volume."""
+    vol = np.ascontiguousarray(vol)
+    out = np.empty(vol.shape, np.uint8)
+    kind = binning["kind"]
+    if kind == BIN_AFFINE_F32:
+        v = np.ascontiguousarray(vol, dtype=np.float32)
+        lo = np.zeros(1, np.float32)
+        hi = np.zeros(1, np.float32)
+        lib().ko_bin_f32(_p(v), v.size, binning["bins"], _p(out), _p(lo), _p(hi))
+        return out
+    v = np.ascontiguousarray(vol, dtype=np.int32)
+    lib().ko_bin_int(_p(v), v.size, kind, binning["bins"], binning["shift"],
+                     binning["lo"], binning["hi"], _p(out))
+    return out
+
+
+def _dims(bins):
+    nz, ny, nx = bins.shape
+    return nx, ny, nz
+
+
+def window_counts(bins, B, p, r):
+    nx, ny, nz = _dims(bins)
+    c = np.zeros(B, np.int64)
+    lib().ko_window_counts(_p(np.ascontiguousarray(bins)), nx, ny, nz, B, int(p[0]), int(p[1]),
+                           int(p[2]), int(r), _p(c))
+    return c
+
+
+def octant_counts(bins, B, p, r, j):
+    nx, ny, nz = _dims(bins)
+    c = np.zeros(B, np.int64)
+    lib().ko_octant_counts(_p(np.ascontiguousarray(bins)), nx, ny, nz, B, int(p[0]), int(p[1]),
+                           int(p[2]), int(r), int(j), _p(c))
+    return c
+
+
+def entropy(counts, nmax=None):
+    c = np.ascontiguousarray(counts, dtype=np.int64)
+    T, L = tables(max(int(c.sum()), int(c.max(initial=0)), 1) if nmax is None else nmax)
+    return lib().ko_entropy(_p(c), c.size, _p(T), _p(L))
+
+
+def weight(counts, prev_counts, r, w_norm=0):
+    c = np.ascontiguousarray(counts, dtype=np.int64)
+    cp = np.ascontiguousarray(prev_counts, dtype=np.int64)
+    return lib().ko_weight(_p(c), _p(cp), c.size, int(r), int(w_norm))
+
+
+def dense(bins, B, r_min, r_max, w_norm=0, centres=None, brute=False, nthreads=0,
+          want_hw=False):
+    """Dense Kadir-Brady: (Y_best, s_best[, H, W]) per centre.
+
+    centres=None evaluates every voxel and returns arrays shaped like `bins`;
+    otherwise `centres` is an (n, 3) int array of xyz and outputs are flat."""
+    bins = np.ascontiguousarray(bins, dtype=np.uint8)
+    nx, ny, nz = _dims(bins)
+    S = r_max - r_min + 1
+    T, L = tables(ball_size(r_max))
+    if centres is None:
+        n = bins.size
+        cp = None
+    else:
+        cen = np.ascontiguousarray(centres, dtype=np.int32).reshape(-1, 3)
+        n = cen.shape[0]
+        cp = _p(cen)
+    Y = np.zeros(n, np.float64)
+    s = np.zeros(n, np.uint8)
+    H = np.zeros((n, S), np.float64) if want_hw else None
+    W = np.zeros((n, S), np.float64) if want_hw else None
+    lib().ko_dense(_p(bins), nx, ny, nz, B, r_min, r_max, w_norm, _p(T), _p(L), cp, n,
+                   int(brute), int(nthreads), _p(Y), _p(s),
+                   _p(H) if want_hw else None, _p(W) if want_hw else None)
+    if centres is None:
+        Y = Y.reshape(bins.shape)
+        s = s.reshape(bins.shape)
+    return (Y, s, H, W) if want_hw else (Y, s)
+
+
+def seed_grid(dims, stride):
+    nx, ny, nz = dims
+    n = lib().ko_seed_grid(nx, ny, nz, stride, None)
+    out = np.zeros((n, 3), np.int32)
+    lib().ko_seed_grid(nx, ny, nz, stride, _p(out))
+    return out
+
+
+def octant_climb(bins, B, r_min, r_max, seeds, max_iter=20, w_norm=0, nthreads=0,
+                 want_traj=False):
+    bins = np.ascontiguousarray(bins, dtype=np.uint8)
+    nx, ny, nz = _dims(bins)
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32).reshape(-1, 3)
+    n = seeds.shape[0]
+    T, L = tables(ball_size(r_max))
+    out = {
+        "xyz": np.zeros((n, 3), np.int32), "iters": np.zeros(n, np.int32),
+        "converged": np.zeros(n, np.int32), "Y": np.zeros(n), "s": np.zeros(n, np.int32),
+        "H": np.zeros(n), "W": np.zeros(n),
+    }
+    traj = np.zeros((n, max_iter + 1, 3), np.int32) if want_traj else None
+    lib().ko_octant_climb(_p(bins), nx, ny, nz, B, r_min, r_max, max_iter, w_norm, _p(T), _p(L),
+                          _p(seeds), n, int(nthreads), _p(out["xyz"]), _p(out["iters"]),
+                          _p(out["converged"]), _p(traj) if want_traj else None, _p(out["Y"]),
+                          _p(out["s"]), _p(out["H"]), _p(out["W"]))
+    if want_traj:
+        out["traj"] = traj
+    return out
+
+
+def octant_one_step(bins, B, r_min, r_max, p):
+    bins = np.ascontiguousarray(bins, dtype=np.uint8)
+    nx, ny, nz = _dims(bins)
+    T, L = tables(ball_size(r_max))
+    st = np.zeros(3, np.int32)
+    lib().ko_octant_one_step(_p(bins), nx, ny, nz, B, r_min, r_max, _p(T), _p(L), int(p[0]),
+                             int(p[1]), int(p[2]), _p(st))
+    return st
+
+
+def meanshift(bins, B, r_min, r_max, seeds, max_iter=20, nthreads=0):
+    """Items are (seed, r) seed-major: item = seed*S + (r - r_min)."""
+    bins = np.ascontiguousarray(bins, dtype=np.uint8)
+    nx, ny, nz = _dims(bins)
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32).reshape(-1, 3)
+    S = r_max - r_min + 1
+    n = seeds.shape[0] * S
+    T, L = tables(ball_size(r_max))
+    out = {
+        "xyz": np.zeros((n, 3), np.int32), "iters": np.zeros(n, np.int32),
+        "converged": np.zeros(n, np.int32), "rho": np.zeros(n), "H": np.zeros(n),
+    }
+    lib().ko_meanshift(_p(bins), nx, ny, nz, B, r_min, r_max, max_iter, _p(T), _p(L), _p(seeds),
+                       seeds.shape[0], int(nthreads), _p(out["xyz"]), _p(out["iters"]),
+                       _p(out["converged"]), _p(out["rho"]), _p(out["H"]))
+    return out
+
+
+def ms_window(bins, B, p, r):
+    bins = np.ascontiguousarray(bins, dtype=np.uint8)
+    nx, ny, nz = _dims(bins)
+    c = np.zeros(B, np.int64)
+    m = np.zeros((B, 3), np.int64)
+    lib().ko_ms_window(_p(bins), nx, ny, nz, B, int(p[0]), int(p[1]), int(p[2]), int(r), _p(c),
+                       _p(m))
+    return c, m
+
+
+def max_threads():
+    return lib().ko_max_threads()

@@ -1,0 +1,594 @@
+/*
+ * ks_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, obviously-correct CPU statement of what the Kadir-Brady
+ * saliency hot path computes.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file's library; the product
+ * path never calls it and shares no code with it.
+ *
+ * Built with: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (x86-64 SSE2
+ * doubles, so every + - * / and sqrt below is one IEEE binary64 operation
+ * rounded to nearest, with no fused multiply-add).
+ *
+ * Conventions
+ *   - Volumes are x-fastest: voxel (x,y,z) is element (z*ny + y)*nx + x.
+ *   - Bin volumes hold the STORED value b+1 for bin b in [0,B), and 0 for a
+ *     voxel that is not counted (outside the tissue window).  Voxels outside
+ *     the volume are never counted either.
+ *   - Ball(r) = { o in Z^3 : |o|^2 <= r^2 }.
+ *
+ * Paper passages followed (arXiv 1310.6736):
+ *   Sec. 1 / Sec. 2.1   Kadir-Brady saliency: entropy over multi-scale
+ *                       neighbourhoods times the rate of change of the pdf
+ *                       with scale, maximised over scale.
+ *   Eq. 1-3             entropy of a window; used by the tests as closed forms.
+ *   Sec. 2.2, Alg. 1    quadrant (here: octant) hill-climbing.
+ *   Sec. 2.3, Eq. 4-6   mean shift towards a uniform target pmf with
+ *                       Bhattacharyya weights.
+ *
+ * Parity pins for every function live in tests/test_oracle_*.py.
+ */
+#include <math.h>
+#include <quadmath.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Tables.  T[c] = c*ln(c) and L[n] = ln(n), each correctly rounded to      */
+/* binary64.  They are evaluated in binary128 (113-bit) arithmetic with     */
+/* libquadmath's logq and rounded once, so the double is the nearest one to */
+/* the exact value except for inputs within ~2^-60 ulp of a rounding        */
+/* midpoint.  T[0] = T[1] = 0 and L[0] = L[1] = 0.                          */
+/* ------------------------------------------------------------------------ */
+void ko_tables(int64_t nmax, double *T, double *L)
+{
+    for (int64_t c = 0; c <= nmax; ++c) {
+        if (c <= 1) {
+            T[c] = 0.0;
+            L[c] = 0.0;
+            continue;
+        }
+        __float128 q = (__float128)c;
+        __float128 lq = logq(q);
+        T[c] = (double)(q * lq);
+        L[c] = (double)lq;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Binning: the bin index beta(s) of Eq. 4-5, stored as b+1.                 */
+/* ------------------------------------------------------------------------ */
+enum { KO_BIN_CLAMP_SHIFT = 0, KO_BIN_AFFINE_F32 = 1, KO_BIN_WINDOW = 2 };
+
+/* Integer inputs (uint8 / int16 widened to int32).
+ *   CLAMP_SHIFT: b = (clamp(v, lo, hi) - lo) >> shift
+ *   WINDOW:      voxels outside [lo, hi] are not counted (Sec. 3.2's
+ *                window-level restriction); inside, b = (v - lo) >> shift. */
+void ko_bin_int(const int32_t *v, int64_t n, int kind, int bins, int shift,
+                int lo, int hi, uint8_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t x = v[i];
+        if (kind == KO_BIN_WINDOW && (x < lo || x > hi)) {
+            out[i] = 0;
+            continue;
+        }
+        if (x < lo) x = lo;
+        if (x > hi) x = hi;
+        int32_t b = (x - lo) >> shift;
+        if (b > bins - 1) b = bins - 1;
+        out[i] = (uint8_t)(b + 1);
+    }
+}
+
+/* float32 input: b = clamp(floor(bins*(v - vmin) / ((vmax - vmin) + 1e-6)),
+ * 0, bins-1), every operation in binary32 rounded to nearest, in this order:
+ * a = v - vmin; t = bins*a; d = (vmax - vmin) + 1e-6f; q = t / d.
+ * vmin / vmax are the exact minimum and maximum over the whole volume. */
+void ko_bin_f32(const float *v, int64_t n, int bins, uint8_t *out,
+                float *vmin_out, float *vmax_out)
+{
+    float vmin = v[0], vmax = v[0];
+    for (int64_t i = 1; i < n; ++i) {
+        if (v[i] < vmin) vmin = v[i];
+        if (v[i] > vmax) vmax = v[i];
+    }
+    float d = vmax - vmin;
+    d = d + 1e-6f;
+    float fb = (float)bins;
+    for (int64_t i = 0; i < n; ++i) {
+        float a = v[i] - vmin;
+        float t = fb * a;
+        float q = t / d;
+        int b = (int)floorf(q);
+        if (b < 0) b = 0;
+        if (b > bins - 1) b = bins - 1;
+        out[i] = (uint8_t)(b + 1);
+    }
+    if (vmin_out) *vmin_out = vmin;
+    if (vmax_out) *vmax_out = vmax;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Window histograms and the scalar quantities built from them.             */
+/* ------------------------------------------------------------------------ */
+
+/* Stored bin value at (x,y,z), or 0 when the voxel lies outside the volume. */
+static inline int ko_at(const uint8_t *bins, int nx, int ny, int nz, int x, int y, int z)
+{
+    if (x < 0 || y < 0 || z < 0 || x >= nx || y >= ny || z >= nz) return 0;
+    return bins[((int64_t)z * ny + y) * nx + x];
+}
+
+/* Brute force: counts c[b] of bin b over Ball(r) centred at (px,py,pz),
+ * enumerating the cube [-r, r]^3 and keeping |o|^2 <= r^2. */
+void ko_window_counts(const uint8_t *bins, int nx, int ny, int nz, int B,
+                      int px, int py, int pz, int r, int64_t *c)
+{
+    for (int b = 0; b < B; ++b) c[b] = 0;
+    for (int dz = -r; dz <= r; ++dz)
+        for (int dy = -r; dy <= r; ++dy)
+            for (int dx = -r; dx <= r; ++dx) {
+                if (dx * dx + dy * dy + dz * dz > r * r) continue;
+                int s = ko_at(bins, nx, ny, nz, px + dx, py + dy, pz + dz);
+                if (s) c[s - 1] += 1;
+            }
+}
+
+/* Shannon entropy of a window's counts:
+ *   H = ln N - (1/N) * sum_b c_b ln c_b
+ * which equals -sum_b p_b ln p_b with p_b = c_b / N (Eq. 1).  The sum runs
+ * over b = 0..B-1 in order starting from +0.0, then one division and one
+ * subtraction.  A window with at most one occupied bin (alpha = 0 in
+ * Sec. 2.1, or N <= 1) has H = 0 exactly; the formula would leave rounding
+ * noise of order 1e-15 there. */
+double ko_entropy(const int64_t *c, int B, const double *T, const double *L)
+{
+    int64_t N = 0;
+    int occupied = 0;
+    for (int b = 0; b < B; ++b) { N += c[b]; occupied += c[b] > 0; }
+    if (occupied <= 1) return 0.0;
+    double s = 0.0;
+    for (int b = 0; b < B; ++b) s = s + T[c[b]];
+    return L[N] - s / (double)N;
+}
+
+/* Kadir-Brady inter-scale weight at radius r from the counts at r (c) and
+ * r-1 (cp): W = f(r) * sum_b | c_b/N - cp_b/Np |, evaluated exactly as the
+ * integer D = sum_b | c_b*Np - cp_b*N | over the integer N*Np, with the
+ * discrete scale normalisation f(r) = r^2 / (2r - 1) (w_norm = 0) or
+ * f = 1 (w_norm = 1).  An empty window at either scale gives W = 0. */
+double ko_weight(const int64_t *c, const int64_t *cp, int B, int r, int w_norm)
+{
+    int64_t N = 0, Np = 0;
+    for (int b = 0; b < B; ++b) { N += c[b]; Np += cp[b]; }
+    if (N == 0 || Np == 0) return 0.0;
+    int64_t D = 0;
+    for (int b = 0; b < B; ++b) {
+        int64_t d = c[b] * Np - cp[b] * N;
+        D += d < 0 ? -d : d;
+    }
+    double f = w_norm == 1 ? 1.0 : (double)(r * r) / (double)(2 * r - 1);
+    return f * ((double)D / (double)(N * Np));
+}
+
+/* Kadir-Brady saliency at one centre over scales r_min..r_max.
+ * H[k], W[k] for r = r_min + k (W[0] = 0: no r_min - 1 histogram).
+ * Peaks in scale: interior r (r_min < r < r_max) with H(r-1) < H(r) and
+ * H(r) >= H(r+1).  Y(r) = H(r) * W(r).  The best peak is the first peak in
+ * ascending r, replaced only by a later peak with strictly larger Y.
+ * No peak: Y_best = 0, s_best = 0.
+ * brute = 1 enumerates Ball(r) afresh for every r; brute = 0 enumerates
+ * Ball(r_max) once, sorted by the shell each offset first enters
+ * (the smallest r >= r_min with |o|^2 <= r^2), and adds shell r to the
+ * counts of r-1.  Both give the same integer counts. */
+typedef struct { int dx, dy, dz, shell; } ko_off;
+
+static int ko_shell_of(int d2, int r_min)
+{
+    int r = r_min;
+    while (r * r < d2) ++r;
+    return r;
+}
+
+/* Ball(r_max) offsets ordered by shell (stable within a shell: dz, dy, dx). */
+static ko_off *ko_ball_by_shell(int r_min, int r_max, int64_t *count)
+{
+    int64_t n = 0;
+    for (int dz = -r_max; dz <= r_max; ++dz)
+        for (int dy = -r_max; dy <= r_max; ++dy)
+            for (int dx = -r_max; dx <= r_max; ++dx)
+                if (dx * dx + dy * dy + dz * dz <= r_max * r_max) ++n;
+    ko_off *o = (ko_off *)malloc(sizeof(ko_off) * (size_t)(n > 0 ? n : 1));
+    int64_t k = 0;
+    for (int r = r_min; r <= r_max; ++r)
+        for (int dz = -r_max; dz <= r_max; ++dz)
+            for (int dy = -r_max; dy <= r_max; ++dy)
+                for (int dx = -r_max; dx <= r_max; ++dx) {
+                    int d2 = dx * dx + dy * dy + dz * dz;
+                    if (d2 <= r_max * r_max && ko_shell_of(d2, r_min) == r) {
+                        o[k].dx = dx; o[k].dy = dy; o[k].dz = dz; o[k].shell = r;
+                        ++k;
+                    }
+                }
+    *count = n;
+    return o;
+}
+
+static void ko_kb_core(const uint8_t *bins, int nx, int ny, int nz, int B,
+                       int px, int py, int pz, int r_min, int r_max, int w_norm,
+                       const double *T, const double *L, int brute,
+                       const ko_off *ball, int64_t nball,
+                       double *H, double *W, double *Y_best, int *s_best,
+                       int64_t *cur, int64_t *prev)
+{
+    int S = r_max - r_min + 1;
+    int64_t k = 0;
+    for (int b = 0; b < B; ++b) cur[b] = 0;
+    for (int i = 0; i < S; ++i) {
+        int r = r_min + i;
+        for (int b = 0; b < B; ++b) prev[b] = cur[b];
+        if (brute) {
+            ko_window_counts(bins, nx, ny, nz, B, px, py, pz, r, cur);
+        } else {
+            while (k < nball && ball[k].shell == r) {
+                int s = ko_at(bins, nx, ny, nz, px + ball[k].dx, py + ball[k].dy, pz + ball[k].dz);
+                if (s) cur[s - 1] += 1;
+                ++k;
+            }
+        }
+        H[i] = ko_entropy(cur, B, T, L);
+        W[i] = i == 0 ? 0.0 : ko_weight(cur, prev, B, r, w_norm);
+    }
+    double yb = 0.0;
+    int sb = 0;
+    for (int i = 1; i + 1 < S; ++i) {
+        if (H[i - 1] < H[i] && H[i] >= H[i + 1]) {
+            double y = H[i] * W[i];
+            if (sb == 0 || y > yb) { yb = y; sb = r_min + i; }
+        }
+    }
+    *Y_best = yb;
+    *s_best = sb;
+}
+
+/* Dense Kadir-Brady sweep over a list of centres (xyz triples), or over
+ * every voxel when centres == NULL (then ncentres = nx*ny*nz and centre i
+ * is voxel i).  Outputs Y_best (double) and s_best (uint8) per centre, and
+ * optionally H / W per centre and scale (ncentres x S, may be NULL). */
+void ko_dense(const uint8_t *bins, int nx, int ny, int nz, int B,
+              int r_min, int r_max, int w_norm, const double *T, const double *L,
+              const int32_t *centres, int64_t ncentres, int brute, int nthreads,
+              double *Y, uint8_t *s_out, double *H_out, double *W_out)
+{
+    int S = r_max - r_min + 1;
+    int64_t nball = 0;
+    ko_off *ball = ko_ball_by_shell(r_min, r_max, &nball);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        int64_t *cur = (int64_t *)malloc(sizeof(int64_t) * B);
+        int64_t *prev = (int64_t *)malloc(sizeof(int64_t) * B);
+        double *H = (double *)malloc(sizeof(double) * S);
+        double *W = (double *)malloc(sizeof(double) * S);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+        for (int64_t i = 0; i < ncentres; ++i) {
+            int px, py, pz;
+            if (centres) {
+                px = centres[3 * i]; py = centres[3 * i + 1]; pz = centres[3 * i + 2];
+            } else {
+                px = (int)(i % nx); py = (int)((i / nx) % ny); pz = (int)(i / ((int64_t)nx * ny));
+            }
+            double yb;
+            int sb;
+            ko_kb_core(bins, nx, ny, nz, B, px, py, pz, r_min, r_max, w_norm, T, L,
+                       brute, ball, nball, H, W, &yb, &sb, cur, prev);
+            Y[i] = yb;
+            s_out[i] = (uint8_t)sb;
+            if (H_out) memcpy(H_out + i * S, H, sizeof(double) * S);
+            if (W_out) memcpy(W_out + i * S, W, sizeof(double) * S);
+        }
+        free(cur); free(prev); free(H); free(W);
+    }
+    free(ball);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Seed grid (Sec. 2.2: "a uniformly sampled grid of points").               */
+/* Positions stride/2 + i*stride < dim per axis; seed index is x-fastest.   */
+/* Returns the seed count; writes xyz triples when out != NULL.             */
+/* ------------------------------------------------------------------------ */
+int64_t ko_seed_grid(int nx, int ny, int nz, int stride, int32_t *out)
+{
+    int64_t n = 0;
+    for (int z = stride / 2; z < nz; z += stride)
+        for (int y = stride / 2; y < ny; y += stride)
+            for (int x = stride / 2; x < nx; x += stride) {
+                if (out) { out[3 * n] = x; out[3 * n + 1] = y; out[3 * n + 2] = z; }
+                ++n;
+            }
+    return n;
+}
+
+static inline int ko_clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* Round half away from zero; exact for every binary64 (C99 round). */
+static inline int ko_round(double d) { return (int)round(d); }
+
+/* ------------------------------------------------------------------------ */
+/* Octant hill-climbing: the 3D form of Alg. 1 (Sec. 2.2).                   */
+/*                                                                          */
+/* Octant j (bit0: x<0, bit1: y<0, bit2: z<0) has sign vector sigma_j.  Its */
+/* window at scale k is the CLOSED octant of Ball(k) at P: offsets whose    */
+/* every nonzero component has the octant's sign (an offset on a coordinate */
+/* plane belongs to every octant it touches).  Per iteration:               */
+/*   eps_jk  = entropy of window (j, k)                                      */
+/*   eps_j   = max_k eps_jk, k_j = argmax (first, i.e. smallest, k on ties)  */
+/*   d_j     = k_j * sigma_j  (3D counterpart of the diagonal step sqrt2*k)  */
+/*   delta   = sum_j eps_j d_j / sum_j eps_j  (normalised-entropy weights;   */
+/*             numerator and denominator summed over j = 0..7 in order, one  */
+/*             division per axis; sum_j eps_j = 0 gives delta = 0)           */
+/*   P'      = clamp(P + round_half_away(delta), 0, dim-1)                    */
+/* The climb stops when P' == P (converged) or after max_iter iterations.    */
+/* Afterwards the Kadir-Brady quantities are evaluated on the full ball at  */
+/* the final P (Sec. 2.2: the change in pdf about the optimal scale).        */
+/* ------------------------------------------------------------------------ */
+static int ko_in_octant(int j, int dx, int dy, int dz)
+{
+    if ((j & 1) ? dx > 0 : dx < 0) return 0;
+    if ((j & 2) ? dy > 0 : dy < 0) return 0;
+    if ((j & 4) ? dz > 0 : dz < 0) return 0;
+    return 1;
+}
+
+static void ko_octant_step(const uint8_t *bins, int nx, int ny, int nz, int B,
+                           int r_min, int r_max, const double *T, const double *L,
+                           const ko_off *ball, int64_t nball,
+                           const int P[3], int step[3], int64_t *cnt /* 8*B */)
+{
+    int S = r_max - r_min + 1;
+    double eps[8];
+    int kopt[8];
+    for (int j = 0; j < 8; ++j) {
+        for (int b = 0; b < B; ++b) cnt[j * B + b] = 0;
+        eps[j] = 0.0;
+        kopt[j] = r_min;
+    }
+    int64_t k = 0;
+    for (int i = 0; i < S; ++i) {
+        int r = r_min + i;
+        while (k < nball && ball[k].shell == r) {
+            int dx = ball[k].dx, dy = ball[k].dy, dz = ball[k].dz;
+            int s = ko_at(bins, nx, ny, nz, P[0] + dx, P[1] + dy, P[2] + dz);
+            if (s)
+                for (int j = 0; j < 8; ++j)
+                    if (ko_in_octant(j, dx, dy, dz)) cnt[j * B + s - 1] += 1;
+            ++k;
+        }
+        for (int j = 0; j < 8; ++j) {
+            double e = ko_entropy(cnt + j * B, B, T, L);
+            if (i == 0 || e > eps[j]) { eps[j] = e; kopt[j] = r; }
+        }
+    }
+    double num[3] = {0.0, 0.0, 0.0}, den = 0.0;
+    for (int j = 0; j < 8; ++j) {
+        int sg[3] = {(j & 1) ? -1 : 1, (j & 2) ? -1 : 1, (j & 4) ? -1 : 1};
+        for (int a = 0; a < 3; ++a) num[a] = num[a] + eps[j] * (double)(kopt[j] * sg[a]);
+        den = den + eps[j];
+    }
+    for (int a = 0; a < 3; ++a) step[a] = den == 0.0 ? 0 : ko_round(num[a] / den);
+}
+
+void ko_octant_climb(const uint8_t *bins, int nx, int ny, int nz, int B,
+                     int r_min, int r_max, int max_iter, int w_norm,
+                     const double *T, const double *L,
+                     const int32_t *seeds, int64_t nseeds, int nthreads,
+                     int32_t *final_xyz, int32_t *iters, int32_t *converged,
+                     int32_t *traj /* nseeds x (max_iter+1) x 3, or NULL */,
+                     double *Y_best, int32_t *s_best, double *H_best, double *W_best)
+{
+    int S = r_max - r_min + 1;
+    int64_t nball = 0;
+    ko_off *ball = ko_ball_by_shell(r_min, r_max, &nball);
+    int dim[3] = {nx, ny, nz};
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * 8 * B);
+        int64_t *cur = (int64_t *)malloc(sizeof(int64_t) * B);
+        int64_t *prev = (int64_t *)malloc(sizeof(int64_t) * B);
+        double *H = (double *)malloc(sizeof(double) * S);
+        double *W = (double *)malloc(sizeof(double) * S);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t i = 0; i < nseeds; ++i) {
+            int P[3] = {seeds[3 * i], seeds[3 * i + 1], seeds[3 * i + 2]};
+            int it = 0, conv = 0;
+            if (traj) for (int a = 0; a < 3; ++a) traj[(i * (max_iter + 1)) * 3 + a] = P[a];
+            while (it < max_iter) {
+                int step[3], Pn[3];
+                ko_octant_step(bins, nx, ny, nz, B, r_min, r_max, T, L, ball, nball, P, step, cnt);
+                ++it;
+                for (int a = 0; a < 3; ++a) Pn[a] = ko_clampi(P[a] + step[a], 0, dim[a] - 1);
+                if (Pn[0] == P[0] && Pn[1] == P[1] && Pn[2] == P[2]) { conv = 1; break; }
+                for (int a = 0; a < 3; ++a) P[a] = Pn[a];
+                if (traj) for (int a = 0; a < 3; ++a) traj[(i * (max_iter + 1) + it) * 3 + a] = P[a];
+            }
+            if (traj)   /* positions after the last move are repeated to the end */
+                for (int t = it + (conv ? 0 : 1); t <= max_iter; ++t)
+                    for (int a = 0; a < 3; ++a) traj[(i * (max_iter + 1) + t) * 3 + a] = P[a];
+            for (int a = 0; a < 3; ++a) final_xyz[3 * i + a] = P[a];
+            iters[i] = it;
+            converged[i] = conv;
+            double yb; int sb;
+            ko_kb_core(bins, nx, ny, nz, B, P[0], P[1], P[2], r_min, r_max, w_norm, T, L,
+                       0, ball, nball, H, W, &yb, &sb, cur, prev);
+            Y_best[i] = yb;
+            s_best[i] = sb;
+            H_best[i] = sb ? H[sb - r_min] : 0.0;
+            W_best[i] = sb ? W[sb - r_min] : 0.0;
+        }
+        free(cnt); free(cur); free(prev); free(H); free(W);
+    }
+    free(ball);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mean shift towards a uniform target pmf (Sec. 2.3, Eq. 4-6).              */
+/*                                                                          */
+/* Item = (seed, r).  The window is Ball(r) at P with a flat profile, so    */
+/* p_b = c_b / N (Eq. 4) and -K' is constant in Eq. 6.  With q_b = 1/B the  */
+/* voxel weight of Eq. 5 is w(s) = sqrt(q_b / p_b) = sqrt(N / (B c_b)) for  */
+/* s in bin b.  Eq. 6 then moves P to the w-weighted centroid:              */
+/*   P + delta,  delta = sum_s w(s) o_s / sum_s w(s)                          */
+/*              = sum_b w_b m_b / sum_b w_b c_b                               */
+/* with m_b = sum of offsets o_s over the voxels of bin b (integers).  The   */
+/* two FP64 sums run over b = 0..B-1 in order, skipping empty bins.          */
+/*   P' = clamp(P + round_half_away(delta), 0, dim-1); stop when P' == P or   */
+/* after max_iter iterations.  At the final P the item reports the           */
+/* Bhattacharyya coefficient rho = sum_b sqrt(p_b q_b) = sum_b sqrt(c_b/(N B))*/
+/* (bin order) and the window entropy H.                                    */
+/* ------------------------------------------------------------------------ */
+static void ko_ms_moments(const uint8_t *bins, int nx, int ny, int nz, int B,
+                          int r, const int P[3], int64_t *c, int64_t *m /* 3*B */)
+{
+    for (int b = 0; b < B; ++b) { c[b] = 0; m[3 * b] = m[3 * b + 1] = m[3 * b + 2] = 0; }
+    for (int dz = -r; dz <= r; ++dz)
+        for (int dy = -r; dy <= r; ++dy)
+            for (int dx = -r; dx <= r; ++dx) {
+                if (dx * dx + dy * dy + dz * dz > r * r) continue;
+                int s = ko_at(bins, nx, ny, nz, P[0] + dx, P[1] + dy, P[2] + dz);
+                if (!s) continue;
+                c[s - 1] += 1;
+                m[3 * (s - 1)] += dx;
+                m[3 * (s - 1) + 1] += dy;
+                m[3 * (s - 1) + 2] += dz;
+            }
+}
+
+void ko_meanshift(const uint8_t *bins, int nx, int ny, int nz, int B,
+                  int r_min, int r_max, int max_iter, const double *T, const double *L,
+                  const int32_t *seeds, int64_t nseeds, int nthreads,
+                  int32_t *final_xyz, int32_t *iters, int32_t *converged,
+                  double *rho, double *H)
+{
+    int S = r_max - r_min + 1;
+    int dim[3] = {nx, ny, nz};
+    int64_t nitems = nseeds * S;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        int64_t *c = (int64_t *)malloc(sizeof(int64_t) * B);
+        int64_t *m = (int64_t *)malloc(sizeof(int64_t) * 3 * B);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t item = 0; item < nitems; ++item) {
+            int64_t sd = item / S;
+            int r = r_min + (int)(item % S);
+            int P[3] = {seeds[3 * sd], seeds[3 * sd + 1], seeds[3 * sd + 2]};
+            int it = 0, conv = 0, fresh = 0;
+            while (it < max_iter) {
+                ko_ms_moments(bins, nx, ny, nz, B, r, P, c, m);
+                fresh = 1;
+                ++it;
+                int64_t N = 0;
+                for (int b = 0; b < B; ++b) N += c[b];
+                int step[3] = {0, 0, 0};
+                if (N > 0) {
+                    double num[3] = {0.0, 0.0, 0.0}, den = 0.0;
+                    for (int b = 0; b < B; ++b) {
+                        if (c[b] == 0) continue;
+                        double w = sqrt((double)N / (double)(B * c[b]));
+                        for (int a = 0; a < 3; ++a) num[a] = num[a] + w * (double)m[3 * b + a];
+                        den = den + w * (double)c[b];
+                    }
+                    for (int a = 0; a < 3; ++a) step[a] = ko_round(num[a] / den);
+                }
+                int Pn[3];
+                for (int a = 0; a < 3; ++a) Pn[a] = ko_clampi(P[a] + step[a], 0, dim[a] - 1);
+                if (Pn[0] == P[0] && Pn[1] == P[1] && Pn[2] == P[2]) { conv = 1; break; }
+                for (int a = 0; a < 3; ++a) P[a] = Pn[a];
+                fresh = 0;
+            }
+            if (!fresh) ko_ms_moments(bins, nx, ny, nz, B, r, P, c, m);
+            int64_t N = 0;
+            for (int b = 0; b < B; ++b) N += c[b];
+            double rh = 0.0;
+            if (N > 0)
+                for (int b = 0; b < B; ++b)
+                    if (c[b] > 0) rh = rh + sqrt((double)c[b] / (double)(N * B));
+            for (int a = 0; a < 3; ++a) final_xyz[3 * item + a] = P[a];
+            iters[item] = it;
+            converged[item] = conv;
+            rho[item] = rh;
+            H[item] = ko_entropy(c, B, T, L);
+        }
+        free(c); free(m);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-window debug views used by the pins.                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Counts of the closed octant j of Ball(r) at P, by brute force. */
+void ko_octant_counts(const uint8_t *bins, int nx, int ny, int nz, int B,
+                      int px, int py, int pz, int r, int j, int64_t *c)
+{
+    for (int b = 0; b < B; ++b) c[b] = 0;
+    for (int dz = -r; dz <= r; ++dz)
+        for (int dy = -r; dy <= r; ++dy)
+            for (int dx = -r; dx <= r; ++dx) {
+                if (dx * dx + dy * dy + dz * dz > r * r) continue;
+                if (!ko_in_octant(j, dx, dy, dz)) continue;
+                int s = ko_at(bins, nx, ny, nz, px + dx, py + dy, pz + dz);
+                if (s) c[s - 1] += 1;
+            }
+}
+
+/* One octant step at P (the rounded move, before clamping). */
+void ko_octant_one_step(const uint8_t *bins, int nx, int ny, int nz, int B,
+                        int r_min, int r_max, const double *T, const double *L,
+                        int px, int py, int pz, int32_t *step_out)
+{
+    int64_t nball = 0;
+    ko_off *ball = ko_ball_by_shell(r_min, r_max, &nball);
+    int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * 8 * B);
+    int P[3] = {px, py, pz}, step[3];
+    ko_octant_step(bins, nx, ny, nz, B, r_min, r_max, T, L, ball, nball, P, step, cnt);
+    for (int a = 0; a < 3; ++a) step_out[a] = step[a];
+    free(cnt);
+    free(ball);
+}
+
+/* Mean-shift counts and moments of Ball(r) at P. */
+void ko_ms_window(const uint8_t *bins, int nx, int ny, int nz, int B,
+                  int px, int py, int pz, int r, int64_t *c, int64_t *m)
+{
+    int P[3] = {px, py, pz};
+    ko_ms_moments(bins, nx, ny, nz, B, r, P, c, m);
+}
+
+int ko_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
