@@ -1,0 +1,291 @@
+/*
+ * ks.h -- C ABI of the B300 Kadir-Brady saliency library (libks.so).
+ *
+ * The library evaluates intensity histograms and their Shannon entropy over
+ * spherical windows Ball(r) = { o in Z^3 : |o|^2 <= r^2 } around many
+ * centres and scales of a 3D volume (arXiv 1310.6736, "Fast 3D Salient
+ * Region Detection in Medical Images using GPUs").  Three uses share that
+ * primitive:
+ *   - the dense Kadir-Brady sweep (Sec. 1 and the opening of Sec. 2.1):
+ *     entropy H(r) at every voxel and scale, inter-scale pdf change W(r),
+ *     saliency Y = H*W at entropy peaks in scale;
+ *   - octant hill-climbing from a sparse seed grid (Sec. 2.2, Alg. 1, in 3D);
+ *   - mean shift towards a uniform target pmf (Sec. 2.3, Eq. 4-6).
+ *
+ * Conventions (all entry points)
+ *   - Return value is a ks_status; no call aborts or throws across the ABI.
+ *     ks_last_error() gives a one-line message for the last failure.
+ *   - Volumes are x-fastest: voxel (x,y,z) is element (z*ny + y)*nx + x.
+ *     Coordinates are int32 voxel indices, 0 <= x < nx etc.
+ *   - Output buffers are owned by the caller.  `out_on_device` = 1 means the
+ *     pointer is device memory on the context's device, 0 means host memory.
+ *   - Every call is synchronous on the context's stream: it returns after the
+ *     work is complete (ks_submit/ks_poll are the asynchronous interface).
+ *   - FP64 results follow one fixed operation order (below), so they are
+ *     reproducible bit for bit from run to run and batch to batch.
+ *
+ * Arithmetic (fixed by this library; see the oracle for the plain statement)
+ *   bins      stored value b+1 for bin b in [0,B); 0 = voxel not counted
+ *             (outside the window level, Sec. 3.2).  Voxels outside the
+ *             volume are not counted.
+ *   entropy   H = ln N - (sum_{b=0..B-1} T[c_b]) / N, with T[c] = c ln c and
+ *             ln N taken from correctly rounded binary64 tables, the sum in
+ *             bin order; H = 0 when at most one bin is occupied.
+ *   weight    W(r) = f(r) * (D / (N_r N_{r-1})), D = sum_b |c_r(b) N_{r-1} -
+ *             c_{r-1}(b) N_r| in exact integers, f(r) = r^2/(2r-1)
+ *             (KS_WNORM_KB) or 1 (KS_WNORM_ONE).
+ */
+#ifndef KS_H
+#define KS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ks_ctx ks_ctx;   /* opaque context: one device, one stream */
+typedef int64_t ks_vol;         /* handle of a resident (binned) volume   */
+typedef int64_t ks_req;         /* handle of a submitted serving request  */
+
+typedef enum ks_status {
+    KS_OK = 0,
+    KS_PENDING = 1,       /* ks_poll: request not finished yet              */
+    KS_EINVAL = -1,       /* bad argument (sizes, ranges, null pointers)    */
+    KS_ENOMEM = -2,       /* HBM budget exceeded or cudaMalloc failed       */
+    KS_ECUDA = -3,        /* CUDA runtime/driver error                      */
+    KS_ETIMEDOUT = -4,    /* a bounded device wait or a poll timed out      */
+    KS_ECANCELED = -5,    /* request was cancelled                          */
+    KS_ENOTFOUND = -6,    /* unknown volume or request handle               */
+    KS_ENODEV = -7        /* no usable CUDA device                          */
+} ks_status;
+
+typedef enum ks_dtype { KS_U8 = 0, KS_I16 = 1, KS_F32 = 2 } ks_dtype;
+
+/* Intensity -> bin map beta(s) (Eq. 4-5: "the bin number in which pixel s
+ * lies"; Sec. 3.2: the constrained window-level range).
+ *   KS_BIN_CLAMP_SHIFT  integer input: b = (clamp(v, lo, hi) - lo) >> shift
+ *   KS_BIN_AFFINE_F32   float input:   b = clamp(floor(bins*(v - vmin) /
+ *                       ((vmax - vmin) + 1e-6f)), 0, bins-1) in binary32,
+ *                       vmin/vmax = exact volume minimum/maximum
+ *   KS_BIN_WINDOW       integer input: v outside [lo, hi] is not counted,
+ *                       otherwise b = (v - lo) >> shift
+ * Requirements: 2 <= bins <= 64; for the integer kinds lo <= hi and
+ * ((hi - lo) >> shift) <= bins - 1. */
+typedef enum ks_bin_kind {
+    KS_BIN_CLAMP_SHIFT = 0, KS_BIN_AFFINE_F32 = 1, KS_BIN_WINDOW = 2
+} ks_bin_kind;
+
+typedef struct ks_binning {
+    int32_t kind, bins, shift, lo, hi;
+} ks_binning;
+
+typedef enum ks_wnorm { KS_WNORM_KB = 0, KS_WNORM_ONE = 1 } ks_wnorm;
+
+/* Scales r_min..r_max (1 <= r_min < r_max <= 32); seed grid stride (>= 1,
+ * seeds at stride/2 + i*stride per axis); max_iter iterations per climb
+ * (0..64); w_norm a ks_wnorm. */
+typedef struct ks_params {
+    int32_t r_min, r_max, stride, max_iter, w_norm;
+} ks_params;
+
+/* One octant-climb seed (Sec. 2.2).  (x,y,z) is the final centre, iters the
+ * number of window evaluations, converged = 1 when the last evaluation gave
+ * no move.  s_best / Y_best / H_best / W_best: the Kadir-Brady evaluation of
+ * the full ball at the final centre (s_best = 0: no entropy peak in scale). */
+typedef struct ks_seed_result {
+    int32_t x, y, z;
+    int32_t seed_x, seed_y, seed_z;
+    int32_t iters, converged;
+    int32_t s_best, reserved;
+    double Y_best, H_best, W_best;
+} ks_seed_result;
+
+/* One mean-shift item (Sec. 2.3): seed index `seed`, window radius r.
+ * rho = Bhattacharyya coefficient with the uniform pmf and H = window
+ * entropy, both at the final centre. */
+typedef struct ks_ms_result {
+    int32_t x, y, z, r;
+    int32_t seed, iters, converged, reserved;
+    double rho, H;
+} ks_ms_result;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` using stream `cuda_stream`
+ * (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL = the
+ * library creates its own non-blocking stream).  hbm_budget_bytes caps the
+ * device memory the context allocates (0 = no cap).  Builds the FP64 tables
+ * T[c] = c ln c and L[n] = ln n for c, n <= |Ball(32)| on the device.
+ * Errors: KS_ENODEV, KS_ENOMEM, KS_ECUDA. */
+int ks_init(ks_ctx **out, size_t hbm_budget_bytes, void *cuda_stream, int device);
+
+/* Release every volume, request and buffer of the context.  NULL is a no-op. */
+int ks_destroy(ks_ctx *ctx);
+
+const char *ks_strerror(int status);
+const char *ks_last_error(ks_ctx *ctx);
+
+/* Block until all work issued by the context is complete and report any
+ * device-side error recorded by its kernels (KS_ETIMEDOUT for a bounded
+ * wait that gave up). */
+int ks_sync(ks_ctx *ctx);
+
+/* ---------------------------------------------------------------- volumes */
+
+/* Copy a raw volume (dtype, nx*ny*nz elements, x-fastest; host memory, or
+ * device memory when is_device_ptr = 1) to the device and bin it (Eq. 4's
+ * beta).  The library keeps only the uint8 bin volume (padded with a
+ * 32-voxel "not counted" halo); the caller keeps ownership of `data`.
+ * Errors: KS_EINVAL (dims < 1 or > 4096, bad binning, dtype mismatch with
+ * kind), KS_ENOMEM, KS_ECUDA. */
+int ks_create_volume(ks_ctx *ctx, const void *data, int is_device_ptr, int dtype,
+                     int nx, int ny, int nz, const ks_binning *binning, ks_vol *out);
+
+int ks_release_volume(ks_ctx *ctx, ks_vol vol);
+
+/* Copy the stored bin values (b+1, 0 = not counted; nx*ny*nz bytes,
+ * x-fastest, no halo) to `out`. */
+int ks_volume_bins(ks_ctx *ctx, ks_vol vol, uint8_t *out, int out_on_device);
+
+/* ------------------------------------------------------------- hot path */
+
+/* Dense Kadir-Brady sweep (Sec. 1; Sec. 2.1 opening): at every voxel,
+ * histograms of Ball(r) for r = r_min..r_max built shell by shell, H(r),
+ * W(r) (r > r_min), entropy peaks at interior scales (H(r-1) < H(r) >=
+ * H(r+1)), Y(r) = H(r) W(r).  Writes Y_best (double, nx*ny*nz) and s_best
+ * (uint8, 0 = no peak; the first peak in r, replaced only by a strictly
+ * larger Y).  Errors: KS_EINVAL, KS_ENOTFOUND, KS_ENOMEM, KS_ECUDA,
+ * KS_ETIMEDOUT. */
+int ks_dense_saliency(ks_ctx *ctx, ks_vol vol, const ks_params *params,
+                      double *Y_best, uint8_t *s_best, int out_on_device);
+
+/* As ks_dense_saliency, optionally also writing H(r) and W(r) for every
+ * voxel and scale: H, W are nx*ny*nz*S doubles (S = r_max - r_min + 1),
+ * voxel-major; either may be NULL. */
+int ks_dense_saliency_ex(ks_ctx *ctx, ks_vol vol, const ks_params *params,
+                         double *Y_best, uint8_t *s_best, double *H, double *W,
+                         int out_on_device);
+
+/* Number of seeds of the uniform grid for `params->stride` (Sec. 2.2). */
+int ks_seed_count(ks_ctx *ctx, ks_vol vol, const ks_params *params, int64_t *n_seeds);
+
+/* Octant hill-climbing (Sec. 2.2, Alg. 1 extended to the 8 closed octants
+ * of Ball(k) in 3D).  seeds_xyz: n_seeds int32 triples on the host, or NULL
+ * for the uniform grid (n_seeds ignored).  Writes one ks_seed_result per
+ * seed into `out` (capacity entries) and the seed count into *n_out.
+ * traj: optional (NULL) host/device int32 buffer of n * (max_iter+1) * 3
+ * positions: entry 0 is the seed, entry t the centre after move t, repeated
+ * after the last move.  Errors: KS_EINVAL (capacity too small, seeds
+ * outside the volume), KS_ENOTFOUND, KS_ENOMEM, KS_ECUDA. */
+int ks_seed_climb(ks_ctx *ctx, ks_vol vol, const ks_params *params,
+                  const int32_t *seeds_xyz, int64_t n_seeds,
+                  ks_seed_result *out, int64_t capacity, int64_t *n_out,
+                  int32_t *traj, int out_on_device);
+
+/* Mean shift to the uniform pmf (Sec. 2.3, Eq. 4-6) for every (seed, r)
+ * item, r = r_min..r_max, item = seed * S + (r - r_min).  Seeds as in
+ * ks_seed_climb.  Writes one ks_ms_result per item. */
+int ks_meanshift(ks_ctx *ctx, ks_vol vol, const ks_params *params,
+                 const int32_t *seeds_xyz, int64_t n_seeds,
+                 ks_ms_result *out, int64_t capacity, int64_t *n_out,
+                 int out_on_device);
+
+/* ---------------------------------------------------------- batched form */
+
+/* Run the octant climb and/or mean shift (kinds: bit 0 octant, bit 1 mean
+ * shift) of n_vols resident volumes, each with its own params and grid
+ * seeds, as ONE persistent launch over a device work queue of
+ * (volume, seed, scale) items; use_graph = 1 replays a captured CUDA graph
+ * of that launch.  oct_out[i] / ms_out[i]: host arrays sized by
+ * ks_seed_count (x S for mean shift); entries may be NULL to skip.  The
+ * per-item arithmetic is identical to ks_seed_climb / ks_meanshift. */
+int ks_batch_seeds(ks_ctx *ctx, const ks_vol *vols, const ks_params *params, int n_vols,
+                   int kinds, ks_seed_result *const *oct_out, ks_ms_result *const *ms_out,
+                   int use_graph);
+
+/* -------------------------------------------------------------- serving */
+
+typedef enum ks_req_kind { KS_REQ_SEEDS = 0, KS_REQ_DENSE = 1 } ks_req_kind;
+
+/* A serving request: a raw host volume plus what to compute.  The library
+ * copies `data` during ks_submit, so the caller may reuse it on return. */
+typedef struct ks_request {
+    const void *data;
+    int32_t dtype, nx, ny, nz;
+    ks_binning binning;
+    ks_params params;
+    int32_t kind;          /* ks_req_kind                                   */
+    int32_t seed_kinds;    /* KS_REQ_SEEDS: bit 0 octant, bit 1 mean shift  */
+} ks_request;
+
+/* Result of a finished request.  Arrays are owned by the library and stay
+ * valid until ks_release_result (or ks_destroy). */
+typedef struct ks_result {
+    int32_t status;                       /* KS_OK, KS_ECANCELED, ...     */
+    int32_t kind;
+    int64_t n_seeds, n_items, n_voxels;
+    const ks_seed_result *oct;            /* n_seeds (or NULL)            */
+    const ks_ms_result *ms;               /* n_items (or NULL)            */
+    const double *Y_best;                 /* dense: n_voxels (or NULL)    */
+    const uint8_t *s_best;
+    double t_submit_us, t_admit_us, t_done_us;   /* context clock         */
+} ks_result;
+
+/* Enqueue a request.  It is admitted to the device when its HBM footprint
+ * fits the budget, and its work is interleaved with the other admitted
+ * requests' in iteration-level waves (continuous batching).  Errors:
+ * KS_EINVAL, KS_ENOMEM (footprint larger than the whole budget). */
+int ks_submit(ks_ctx *ctx, const ks_request *req, ks_req *out);
+
+/* Wait up to timeout_us (0 = just look, < 0 = forever) for a request.
+ * KS_OK: done and *out filled; KS_PENDING: still running after a 0 timeout;
+ * KS_ETIMEDOUT: still running after a positive timeout; KS_ENOTFOUND. */
+int ks_poll(ks_ctx *ctx, ks_req req, int64_t timeout_us, ks_result *out);
+
+/* Cancel a request that has not finished; its later poll reports
+ * KS_ECANCELED. */
+int ks_cancel(ks_ctx *ctx, ks_req req);
+
+/* Free a finished request's result arrays. */
+int ks_release_result(ks_ctx *ctx, ks_req req);
+
+/* ---------------------------------------------------------- diagnostics */
+
+/* Copy the device tables T[0..nmax] and L[0..nmax] (nmax <= |Ball(32)|) to
+ * host arrays. */
+int ks_tables(ks_ctx *ctx, int64_t nmax, double *T, double *L);
+
+/* Number of kernels the context has launched so far. */
+int64_t ks_launch_count(ks_ctx *ctx);
+
+/* Per-kernel CUDA-event timing on the context's stream: when enabled, every
+ * launch is bracketed by events; ks_kernel_time returns the summed device
+ * time (ms) and launch count of kernels whose name starts with `prefix`. */
+int ks_set_profiling(ks_ctx *ctx, int on);
+int ks_kernel_time(ks_ctx *ctx, const char *prefix, double *ms_total, int64_t *launches);
+
+/* Shared-memory histogram-increment rate of this device (increments per
+ * second) for the kernel's counter layout, measured by a dedicated
+ * micro-kernel: the denominator of the histogram kernels' roofline. */
+int ks_measure_smem_peak(ks_ctx *ctx, double *increments_per_s);
+
+/* Dense-sweep launch configuration chosen for (bins, r_max) by the
+ * autotuner: path 0 = TMA brick in shared memory, 1 = direct L2 reads;
+ * warps per block; tile rows in y and z. */
+int ks_dense_config(ks_ctx *ctx, int bins, int r_max, int *path, int *warps,
+                    int *tile_y, int *tile_z);
+
+/* Force the dense launch configuration for every context of the process
+ * (tests use it to cover both paths); path < 0 returns to the autotuner.
+ * KS_EINVAL: path > 1, warps outside [1, 16] or tile_y * tile_z != warps.
+ * A forced shape that does not fit a given (bins, r_max) is ignored for
+ * that call. */
+int ks_force_dense_config(int path, int warps, int tile_y, int tile_z);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KS_H */

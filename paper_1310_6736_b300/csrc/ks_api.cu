@@ -1,0 +1,1106 @@
+// C ABI of the library: context, budgeted device memory, offset tables,
+// volumes, the dense sweep (with its autotuner), the seed searches, the
+// batched persistent launch and diagnostics.  Serving lives in ks_serve.cu.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <unordered_map>
+
+#include "ks_ctx.h"
+
+namespace ks {
+
+// ------------------------------------------------------------------ errors
+int set_err(Ctx *c, int status, const std::string &msg) {
+    if (c) {
+        std::lock_guard<std::mutex> g(c->mu);
+        c->err = msg;
+    }
+    return status;
+}
+
+int cuda_err(Ctx *c, cudaError_t e, const char *where) {
+    if (e == cudaSuccess) return KS_OK;
+    const int st = (e == cudaErrorMemoryAllocation) ? KS_ENOMEM : KS_ECUDA;
+    return set_err(c, st, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define KS_TRY_CUDA(c, expr)                                    \
+    do {                                                        \
+        cudaError_t _e = (expr);                                \
+        if (_e != cudaSuccess) return cuda_err((c), _e, #expr); \
+    } while (0)
+
+// ---------------------------------------------------------------- memory
+cudaError_t dev_alloc(Ctx *c, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    size_t cur = c->used.load();
+    do {
+        if (c->budget && cur + bytes > c->budget) return cudaErrorMemoryAllocation;
+    } while (!c->used.compare_exchange_weak(cur, cur + bytes));
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        c->used -= bytes;
+        *p = nullptr;
+    }
+    return e;
+}
+
+void dev_free(Ctx *c, void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    c->used -= bytes;
+}
+
+// Growable per-context scratch buffers (device), one per purpose.
+struct Scratch {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+enum ScratchSlot {
+    kScRaw, kScSeeds, kScOct, kScMs, kScTraj, kScY, kScS, kScH, kScW, kScTune, kScCount
+};
+static std::mutex g_scratch_mu;
+static std::unordered_map<Ctx *, std::vector<Scratch>> g_scratch;
+
+static void *scratch(Ctx *c, int slot, size_t bytes, cudaError_t *err) {
+    std::lock_guard<std::mutex> g(g_scratch_mu);
+    auto &v = g_scratch[c];
+    if (v.empty()) v.resize(kScCount);
+    Scratch &s = v[slot];
+    *err = cudaSuccess;
+    if (s.bytes >= bytes && s.p) return s.p;
+    if (s.p) {
+        cudaStreamSynchronize(c->stream);
+        dev_free(c, s.p, s.bytes);
+        s.p = nullptr;
+        s.bytes = 0;
+    }
+    const size_t want = std::max<size_t>(bytes, 256);
+    *err = dev_alloc(c, &s.p, want);
+    if (*err != cudaSuccess) return nullptr;
+    s.bytes = want;
+    return s.p;
+}
+
+static void scratch_release_all(Ctx *c) {
+    std::lock_guard<std::mutex> g(g_scratch_mu);
+    auto it = g_scratch.find(c);
+    if (it == g_scratch.end()) return;
+    for (auto &s : it->second) dev_free(c, s.p, s.bytes);
+    g_scratch.erase(it);
+}
+
+// -------------------------------------------------------------- profiling
+void prof_begin(Ctx *c, const char *name, cudaStream_t s, ProfRec *rec) {
+    c->launches++;
+    rec->name = name;
+    rec->a = rec->b = nullptr;
+    if (!c->profiling) return;
+    cudaEventCreate(&rec->a);
+    cudaEventCreate(&rec->b);
+    cudaEventRecord(rec->a, s);
+}
+
+void prof_end(Ctx *c, ProfRec *rec, cudaStream_t s) {
+    if (!rec->a) return;
+    cudaEventRecord(rec->b, s);
+    std::lock_guard<std::mutex> g(c->mu);
+    c->prof.push_back(*rec);
+}
+
+// ------------------------------------------------------------- validation
+int validate_binning(int dtype, const ks_binning *b, std::string *why) {
+    if (!b) return *why = "binning is NULL", KS_EINVAL;
+    if (b->bins < 2 || b->bins > kMaxBins) return *why = "bins must be in [2, 64]", KS_EINVAL;
+    if (dtype != KS_U8 && dtype != KS_I16 && dtype != KS_F32)
+        return *why = "unknown dtype", KS_EINVAL;
+    if (b->kind == KS_BIN_AFFINE_F32) {
+        if (dtype != KS_F32) return *why = "AFFINE_F32 binning needs float32 data", KS_EINVAL;
+        return KS_OK;
+    }
+    if (b->kind != KS_BIN_CLAMP_SHIFT && b->kind != KS_BIN_WINDOW)
+        return *why = "unknown binning kind", KS_EINVAL;
+    if (dtype == KS_F32) return *why = "integer binning needs uint8 or int16 data", KS_EINVAL;
+    if (b->shift < 0 || b->shift > 16 || b->lo > b->hi)
+        return *why = "binning needs 0 <= shift <= 16 and lo <= hi", KS_EINVAL;
+    if (((int64_t)b->hi - b->lo) >> b->shift > b->bins - 1)
+        return *why = "(hi - lo) >> shift exceeds bins - 1", KS_EINVAL;
+    return KS_OK;
+}
+
+int validate_params(const ks_params *p, std::string *why) {
+    if (!p) return *why = "params is NULL", KS_EINVAL;
+    if (p->r_min < 1 || p->r_max > kRmax || p->r_min >= p->r_max)
+        return *why = "scales need 1 <= r_min < r_max <= 32", KS_EINVAL;
+    if (p->stride < 1) return *why = "stride must be >= 1", KS_EINVAL;
+    if (p->max_iter < 0 || p->max_iter > 64) return *why = "max_iter must be in [0, 64]", KS_EINVAL;
+    if (p->w_norm != KS_WNORM_KB && p->w_norm != KS_WNORM_ONE)
+        return *why = "unknown w_norm", KS_EINVAL;
+    return KS_OK;
+}
+
+// ------------------------------------------------------------ ball tables
+static int rho_of(int d2) {
+    int r = 0;
+    while (r * r < d2) ++r;
+    return r;
+}
+
+static int build_ball_tables(Ctx *c) {
+    struct O {
+        int dx, dy, dz, rho;
+    };
+    std::vector<O> ball;
+    for (int dz = -kRmax; dz <= kRmax; ++dz)
+        for (int dy = -kRmax; dy <= kRmax; ++dy)
+            for (int dx = -kRmax; dx <= kRmax; ++dx) {
+                const int d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 <= kRmax * kRmax) ball.push_back({dx, dy, dz, rho_of(d2)});
+            }
+    std::stable_sort(ball.begin(), ball.end(), [](const O &a, const O &b) {
+        if (a.rho != b.rho) return a.rho < b.rho;
+        if (a.dz != b.dz) return a.dz < b.dz;
+        if (a.dy != b.dy) return a.dy < b.dy;
+        return a.dx < b.dx;
+    });
+    std::vector<uint32_t> hb(ball.size());
+    for (size_t i = 0; i < ball.size(); ++i)
+        hb[i] = (uint32_t)(ball[i].dx + 64) | ((uint32_t)(ball[i].dy + 64) << 8) |
+                ((uint32_t)(ball[i].dz + 64) << 16) | ((uint32_t)ball[i].rho << 24);
+    for (int r = 0; r <= kRmax; ++r) {
+        int n = 0;
+        for (auto &o : ball) n += o.rho <= r;
+        c->h_ball_size[r] = n;
+    }
+    struct Cn {
+        int dx, dy, dz, rho;
+        uint32_t mask;
+    };
+    std::vector<Cn> canon;
+    for (int dz = 0; dz <= kRmax; ++dz)
+        for (int dy = 0; dy <= kRmax; ++dy)
+            for (int dx = 0; dx <= kRmax; ++dx) {
+                const int d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 > kRmax * kRmax) continue;
+                uint32_t mask = 0;
+                for (int s = 0; s < 8; ++s) {
+                    if ((s & 1) && dx == 0) continue;
+                    if ((s & 2) && dy == 0) continue;
+                    if ((s & 4) && dz == 0) continue;
+                    mask |= 1u << s;
+                }
+                canon.push_back({dx, dy, dz, rho_of(d2), mask});
+            }
+    std::stable_sort(canon.begin(), canon.end(), [](const Cn &a, const Cn &b) {
+        if (a.rho != b.rho) return a.rho < b.rho;
+        const bool fa = a.mask == 0xFFu, fb = b.mask == 0xFFu;
+        if (fa != fb) return fa;
+        if (a.dz != b.dz) return a.dz < b.dz;
+        if (a.dy != b.dy) return a.dy < b.dy;
+        return a.dx < b.dx;
+    });
+    std::vector<uint32_t> hc(canon.size());
+    int start[kRmax + 2], split[kRmax + 1];
+    size_t k = 0, expanded = 0;
+    for (int rho = 0; rho <= kRmax; ++rho) {
+        start[rho] = (int)k;
+        split[rho] = -1;
+        while (k < canon.size() && canon[k].rho == rho) {
+            if (split[rho] < 0 && canon[k].mask != 0xFFu) split[rho] = (int)k;
+            expanded += __builtin_popcount(canon[k].mask);
+            ++k;
+        }
+        if (split[rho] < 0) split[rho] = (int)k;
+    }
+    start[kRmax + 1] = (int)k;
+    if (expanded != ball.size() || (int)ball.size() != kTableN)
+        return set_err(c, KS_ECUDA, "internal: offset tables inconsistent");
+    for (size_t i = 0; i < canon.size(); ++i)
+        hc[i] = (uint32_t)canon[i].dx | ((uint32_t)canon[i].dy << 8) |
+                ((uint32_t)canon[i].dz << 16) | (canon[i].mask << 24);
+
+    void *p;
+    c->canon_n = hc.size();
+    KS_TRY_CUDA(c, dev_alloc(c, &p, hb.size() * 4));
+    c->d_ball = (uint32_t *)p;
+    KS_TRY_CUDA(c, dev_alloc(c, &p, hc.size() * 4));
+    c->d_canon = (uint32_t *)p;
+    KS_TRY_CUDA(c, dev_alloc(c, &p, sizeof(start)));
+    c->d_canon_start = (int *)p;
+    KS_TRY_CUDA(c, dev_alloc(c, &p, sizeof(split)));
+    c->d_canon_split = (int *)p;
+    KS_TRY_CUDA(c, dev_alloc(c, &p, sizeof(c->h_ball_size)));
+    c->d_ball_size = (int *)p;
+    KS_TRY_CUDA(c, cudaMemcpy(c->d_ball, hb.data(), hb.size() * 4, cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(c->d_canon, hc.data(), hc.size() * 4, cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(c->d_canon_start, start, sizeof(start), cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(c->d_canon_split, split, sizeof(split), cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(c->d_ball_size, c->h_ball_size, sizeof(c->h_ball_size),
+                              cudaMemcpyHostToDevice));
+    c->bt = BallTables{c->d_ball, c->d_canon, c->d_canon_start, c->d_canon_split, c->d_ball_size};
+    return KS_OK;
+}
+
+// ----------------------------------------------------------------- volumes
+size_t volume_bytes(int nx, int ny, int nz) {
+    const int64_t pitch = ((int64_t)nx + 2 * kHalo + 15) / 16 * 16;
+    return (size_t)(pitch * (ny + 2 * kHalo) * (nz + 2 * kHalo));
+}
+
+static size_t dtype_size(int dtype) { return dtype == KS_U8 ? 1 : dtype == KS_I16 ? 2 : 4; }
+
+Volume *find_volume(Ctx *c, int64_t id) {
+    std::lock_guard<std::mutex> g(c->mu);
+    auto it = c->vols.find(id);
+    return it == c->vols.end() ? nullptr : it->second.get();
+}
+
+int create_volume_on(Ctx *c, cudaStream_t s, const void *data, int is_device, int dtype, int nx,
+                     int ny, int nz, const ks_binning *b, int64_t *out_id) {
+    std::string why;
+    if (!data || !out_id) return set_err(c, KS_EINVAL, "data / out is NULL");
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096)
+        return set_err(c, KS_EINVAL, "dims must be in [1, 4096]");
+    int st = validate_binning(dtype, b, &why);
+    if (st) return set_err(c, st, why);
+    auto v = std::make_unique<Volume>();
+    v->nx = nx;
+    v->ny = ny;
+    v->nz = nz;
+    v->binning = *b;
+    v->pitch = ((int64_t)nx + 2 * kHalo + 15) / 16 * 16;
+    v->plane = v->pitch * (ny + 2 * kHalo);
+    v->bytes = volume_bytes(nx, ny, nz);
+    void *p;
+    KS_TRY_CUDA(c, dev_alloc(c, &p, v->bytes));
+    v->alloc = (uint8_t *)p;
+    cudaError_t e = cudaMemsetAsync(v->alloc, 0, v->bytes, s);
+    uint8_t *base = v->alloc + kHalo * v->plane + kHalo * v->pitch + kHalo;
+    const void *raw = data;
+    const size_t raw_bytes = (size_t)nx * ny * nz * dtype_size(dtype);
+    void *staging = nullptr;
+    if (e == cudaSuccess && !is_device) {
+        e = dev_alloc(c, &staging, raw_bytes);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(staging, data, raw_bytes, cudaMemcpyHostToDevice, s);
+        raw = staging;
+    }
+    if (e == cudaSuccess) {
+        ProfRec rec;
+        prof_begin(c, "ks_bin", s, &rec);
+        if (b->kind == KS_BIN_AFFINE_F32) {
+            c->launches++;   // two kernels: partials, then binning
+            e = launch_bin_f32(c->lc(s), (const float *)raw, nx, ny, nz, b->bins, base, v->pitch,
+                               v->plane, c->d_minmax, c->minmax_blocks);
+        } else {
+            e = launch_bin_int(c->lc(s), raw, dtype, nx, ny, nz, *b, base, v->pitch, v->plane);
+        }
+        prof_end(c, &rec, s);
+    }
+    if (staging) {
+        cudaStreamSynchronize(s);
+        dev_free(c, staging, raw_bytes);
+    }
+    if (e != cudaSuccess) {
+        dev_free(c, v->alloc, v->bytes);
+        return cuda_err(c, e, "ks_create_volume");
+    }
+    v->desc = VolDesc{base, nx, ny, nz, b->bins, v->pitch, v->plane};
+    std::lock_guard<std::mutex> g(c->mu);
+    const int64_t id = c->next_vol++;
+    c->vols[id] = std::move(v);
+    *out_id = id;
+    return KS_OK;
+}
+
+// ------------------------------------------------------------- seed grid
+std::vector<int32_t> seed_grid(int nx, int ny, int nz, int stride) {
+    std::vector<int32_t> s;
+    for (int z = stride / 2; z < nz; z += stride)
+        for (int y = stride / 2; y < ny; y += stride)
+            for (int x = stride / 2; x < nx; x += stride) {
+                s.push_back(x);
+                s.push_back(y);
+                s.push_back(z);
+            }
+    return s;
+}
+
+// ------------------------------------------------------------ TMA tensor map
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+static bool make_tmap(Volume *v, int bx, int by, int bz, CUtensorMap *out) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)v->pitch, (cuuint64_t)(v->ny + 2 * kHalo),
+                                (cuuint64_t)(v->nz + 2 * kHalo)};
+    const cuuint64_t strides[2] = {(cuuint64_t)v->pitch, (cuuint64_t)v->plane};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, v->alloc, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// ------------------------------------------------------------- dense sweep
+static std::vector<DenseConfig> dense_candidates(int B, int r_max) {
+    std::vector<DenseConfig> out;
+    const int shapes[][3] = {{4, 4, 1}, {4, 2, 2}, {8, 8, 1}, {8, 4, 2}, {8, 2, 4},
+                             {16, 16, 1}, {16, 4, 4}, {16, 8, 2}, {16, 2, 8}};
+    for (int path = 0; path < 2; ++path)
+        for (auto &s : shapes) {
+            DenseConfig c{path, s[0], s[1], s[2]};
+            if (dense_config_fits(c, B, r_max)) out.push_back(c);
+        }
+    return out;
+}
+
+static int g_forced_path = -1, g_forced_warps = 0, g_forced_ty = 0, g_forced_tz = 0;
+
+static int launch_dense_cfg(Ctx *c, cudaStream_t s, Volume *v, int r_min, int r_max, int w_norm,
+                            const DenseConfig &cfg, const DenseOut &out, int z0, int z1) {
+    CUtensorMap tm{};
+    if (cfg.path == 0) {
+        const int padx = (r_max + 15) / 16 * 16;
+        const int bx = (padx + 32 + r_max + 15) / 16 * 16;
+        if (!make_tmap(v, bx, cfg.ty + 2 * r_max, cfg.tz + 2 * r_max, &tm))
+            return set_err(c, KS_ECUDA, "cuTensorMapEncodeTiled failed");
+    }
+    ProfRec rec;
+    prof_begin(c, "ks_dense", s, &rec);
+    cudaError_t e = launch_dense(c->lc(s), v->desc, cfg.path == 0 ? &tm : nullptr, c->bt, c->T,
+                                 c->L, r_min, r_max, w_norm, cfg, out, z0, z1);
+    prof_end(c, &rec, s);
+    return cuda_err(c, e, "dense launch");
+}
+
+DenseConfig pick_dense_config(Ctx *c, cudaStream_t s, Volume *v, int r_min, int r_max,
+                              int w_norm) {
+    if (g_forced_path >= 0) {
+        DenseConfig f{g_forced_path, g_forced_warps, g_forced_ty, g_forced_tz};
+        if (dense_config_fits(f, v->binning.bins, r_max)) return f;
+    }
+    const int64_t nvox = (int64_t)v->nx * v->ny * v->nz;
+    const DenseTuneKey key{v->binning.bins, r_max, nvox < (1 << 18) ? 0 : 1};
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        auto it = c->tune.find(key);
+        if (it != c->tune.end()) return it->second;
+    }
+    auto cands = dense_candidates(v->binning.bins, r_max);
+    DenseConfig best = cands.empty() ? DenseConfig{1, 8, 8, 1} : cands[0];
+    if (cands.size() > 1) {
+        // Time every candidate on the same slab of the volume (outputs to a
+        // temporary buffer) and keep the fastest.
+        const int z1 = std::min(v->nz, 16);
+        const size_t n = (size_t)v->nx * v->ny * z1;
+        void *buf = nullptr;
+        if (dev_alloc(c, &buf, n * 9 + 256) == cudaSuccess) {
+            DenseOut o{(double *)buf, (uint8_t *)buf + n * 8, nullptr, nullptr};
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            float best_ms = 1e30f;
+            for (auto &cfg : cands) {
+                bool ok = true;
+                for (int rep = 0; rep < 2 && ok; ++rep) {
+                    cudaEventRecord(e0, s);
+                    ok = launch_dense_cfg(c, s, v, r_min, r_max, w_norm, cfg, o, 0, z1) == KS_OK;
+                    cudaEventRecord(e1, s);
+                }
+                if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = cfg;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cudaStreamSynchronize(s);
+            dev_free(c, buf, n * 9 + 256);
+        }
+    }
+    std::lock_guard<std::mutex> g(c->mu);
+    c->tune[key] = best;
+    return best;
+}
+
+int run_dense(Ctx *c, cudaStream_t s, Volume *v, const ks_params *p, const DenseOut &dev_out,
+              int z0, int z1) {
+    const DenseConfig cfg = pick_dense_config(c, s, v, p->r_min, p->r_max, p->w_norm);
+    return launch_dense_cfg(c, s, v, p->r_min, p->r_max, p->w_norm, cfg, dev_out, z0, z1);
+}
+
+static int check_status(Ctx *c) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "sync");
+    if (h) {
+        cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+        cudaStreamSynchronize(c->stream);
+        return set_err(c, KS_ETIMEDOUT, "a bounded device wait gave up (status " +
+                                            std::to_string(h) + ")");
+    }
+    return KS_OK;
+}
+
+}  // namespace ks
+
+using namespace ks;
+
+namespace ks {
+struct BatchGraph {
+    std::vector<int64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    void *mem = nullptr;
+    size_t bytes = 0;
+    size_t oct_off = 0, ms_off = 0;
+    std::vector<int64_t> n_oct, n_ms;
+    std::vector<size_t> oct_at, ms_at;
+    int max_B = 0, max_S = 0;
+    SeedQueue q{};
+    int grid = 0;
+};
+}  // namespace ks
+static std::mutex g_graph_mu;
+static std::unordered_map<Ctx *, std::vector<std::unique_ptr<ks::BatchGraph>>> g_graphs;
+
+// ====================================================================== ABI
+extern "C" {
+
+const char *ks_strerror(int s) {
+    switch (s) {
+        case KS_OK: return "ok";
+        case KS_PENDING: return "pending";
+        case KS_EINVAL: return "invalid argument";
+        case KS_ENOMEM: return "out of device memory or over the HBM budget";
+        case KS_ECUDA: return "CUDA error";
+        case KS_ETIMEDOUT: return "timed out";
+        case KS_ECANCELED: return "cancelled";
+        case KS_ENOTFOUND: return "unknown handle";
+        case KS_ENODEV: return "no CUDA device";
+        default: return "unknown status";
+    }
+}
+
+const char *ks_last_error(ks_ctx *ctx) {
+    if (!ctx) return "no context";
+    return ctx->impl.err.c_str();
+}
+
+int ks_init(ks_ctx **out, size_t budget, void *stream, int device) {
+    if (!out) return KS_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n <= device || device < 0) return KS_ENODEV;
+    auto *h = new ks_ctx();
+    Ctx *c = &h->impl;
+    c->device = device;
+    c->budget = budget;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) {
+        if (stream) {
+            c->stream = (cudaStream_t)stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            c->own_stream = true;
+        }
+    }
+    void *p = nullptr;
+    if (e == cudaSuccess) e = dev_alloc(c, &p, 256);
+    c->d_status = (int *)p;
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 256);
+    if (e == cudaSuccess) e = dev_alloc(c, &p, (kTableN + 1) * sizeof(double));
+    c->T = (double *)p;
+    if (e == cudaSuccess) e = dev_alloc(c, &p, (kTableN + 1) * sizeof(double));
+    c->L = (double *)p;
+    if (e == cudaSuccess) {
+        c->minmax_blocks = bin_f32_scratch_blocks(c->num_sms);
+        e = dev_alloc(c, &p, c->minmax_blocks * sizeof(float2));
+        c->d_minmax = (float2 *)p;
+    }
+    if (e == cudaSuccess) {
+        ProfRec rec;
+        prof_begin(c, "ks_tables", c->stream, &rec);
+        e = launch_tables(c->lc(), c->T, c->L, kTableN);
+        prof_end(c, &rec, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    int st = e == cudaSuccess ? KS_OK : (e == cudaErrorMemoryAllocation ? KS_ENOMEM : KS_ECUDA);
+    if (st == KS_OK) st = build_ball_tables(c);
+    if (st != KS_OK) {
+        ks_destroy(h);
+        return st;
+    }
+    *out = h;
+    return KS_OK;
+}
+
+int ks_destroy(ks_ctx *ctx) {
+    if (!ctx) return KS_OK;
+    Ctx *c = &ctx->impl;
+    serve_shutdown(c);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto &kv : c->vols) dev_free(c, kv.second->alloc, kv.second->bytes);
+    c->vols.clear();
+    scratch_release_all(c);
+    for (auto &r : c->prof) {
+        if (r.a) cudaEventDestroy(r.a);
+        if (r.b) cudaEventDestroy(r.b);
+    }
+    dev_free(c, c->d_status, 256);
+    dev_free(c, c->T, (kTableN + 1) * sizeof(double));
+    dev_free(c, c->L, (kTableN + 1) * sizeof(double));
+    dev_free(c, c->d_minmax, c->minmax_blocks * sizeof(float2));
+    dev_free(c, c->d_ball, kTableN * 4);
+    dev_free(c, c->d_canon, c->canon_n * 4);
+    dev_free(c, c->d_canon_start, (kRmax + 2) * sizeof(int));
+    dev_free(c, c->d_canon_split, (kRmax + 1) * sizeof(int));
+    dev_free(c, c->d_ball_size, (kRmax + 1) * sizeof(int));
+    {
+        std::lock_guard<std::mutex> g(g_graph_mu);
+        auto it = g_graphs.find(c);
+        if (it != g_graphs.end()) {
+            for (auto &bg : it->second) {
+                if (bg->exec) cudaGraphExecDestroy(bg->exec);
+                dev_free(c, bg->mem, bg->bytes);
+            }
+            g_graphs.erase(it);
+        }
+    }
+    dev_free(c, c->batch_mem, c->batch_mem_bytes);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete ctx;
+    return KS_OK;
+}
+
+int ks_sync(ks_ctx *ctx) {
+    if (!ctx) return KS_EINVAL;
+    return check_status(&ctx->impl);
+}
+
+int ks_create_volume(ks_ctx *ctx, const void *data, int is_device_ptr, int dtype, int nx, int ny,
+                     int nz, const ks_binning *binning, ks_vol *out) {
+    if (!ctx) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    int st = create_volume_on(c, c->stream, data, is_device_ptr, dtype, nx, ny, nz, binning, out);
+    if (st) return st;
+    KS_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+    return KS_OK;
+}
+
+int ks_release_volume(ks_ctx *ctx, ks_vol vol) {
+    if (!ctx) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    std::unique_ptr<Volume> v;
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        auto it = c->vols.find(vol);
+        if (it == c->vols.end()) return KS_ENOTFOUND;
+        v = std::move(it->second);
+        c->vols.erase(it);
+    }
+    cudaStreamSynchronize(c->stream);
+    dev_free(c, v->alloc, v->bytes);
+    return KS_OK;
+}
+
+int ks_volume_bins(ks_ctx *ctx, ks_vol vol, uint8_t *out, int out_on_device) {
+    if (!ctx || !out) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    Volume *v = find_volume(c, vol);
+    if (!v) return set_err(c, KS_ENOTFOUND, "unknown volume");
+    cudaMemcpy3DParms prm{};
+    prm.srcPtr = make_cudaPitchedPtr(v->alloc, v->pitch, v->pitch, v->ny + 2 * kHalo);
+    prm.srcPos = make_cudaPos(kHalo, kHalo, kHalo);
+    prm.dstPtr = make_cudaPitchedPtr(out, v->nx, v->nx, v->ny);
+    prm.dstPos = make_cudaPos(0, 0, 0);
+    prm.extent = make_cudaExtent(v->nx, v->ny, v->nz);
+    prm.kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    KS_TRY_CUDA(c, cudaMemcpy3DAsync(&prm, c->stream));
+    KS_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+    return KS_OK;
+}
+
+int ks_dense_saliency_ex(ks_ctx *ctx, ks_vol vol, const ks_params *params, double *Y,
+                         uint8_t *s_best, double *H, double *W, int out_on_device) {
+    if (!ctx) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    std::string why;
+    int st = validate_params(params, &why);
+    if (st) return set_err(c, st, why);
+    if (!Y || !s_best) return set_err(c, KS_EINVAL, "Y_best / s_best is NULL");
+    Volume *v = find_volume(c, vol);
+    if (!v) return set_err(c, KS_ENOTFOUND, "unknown volume");
+    const size_t n = (size_t)v->nx * v->ny * v->nz;
+    const int S = params->r_max - params->r_min + 1;
+    DenseOut o{Y, s_best, H, W};
+    cudaError_t e = cudaSuccess;
+    if (!out_on_device) {
+        o.Y = (double *)scratch(c, kScY, n * 8, &e);
+        if (o.Y) o.s = (uint8_t *)scratch(c, kScS, n, &e);
+        if (o.s && H) o.H = (double *)scratch(c, kScH, n * S * 8, &e);
+        if (e == cudaSuccess && W) o.W = (double *)scratch(c, kScW, n * S * 8, &e);
+        if (e != cudaSuccess) return cuda_err(c, e, "dense outputs");
+    }
+    st = run_dense(c, c->stream, v, params, o, 0, v->nz);
+    if (st) return st;
+    if (!out_on_device) {
+        KS_TRY_CUDA(c, cudaMemcpyAsync(Y, o.Y, n * 8, cudaMemcpyDeviceToHost, c->stream));
+        KS_TRY_CUDA(c, cudaMemcpyAsync(s_best, o.s, n, cudaMemcpyDeviceToHost, c->stream));
+        if (H) KS_TRY_CUDA(c, cudaMemcpyAsync(H, o.H, n * S * 8, cudaMemcpyDeviceToHost, c->stream));
+        if (W) KS_TRY_CUDA(c, cudaMemcpyAsync(W, o.W, n * S * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    return check_status(c);
+}
+
+int ks_dense_saliency(ks_ctx *ctx, ks_vol vol, const ks_params *params, double *Y,
+                      uint8_t *s_best, int out_on_device) {
+    return ks_dense_saliency_ex(ctx, vol, params, Y, s_best, nullptr, nullptr, out_on_device);
+}
+
+int ks_seed_count(ks_ctx *ctx, ks_vol vol, const ks_params *params, int64_t *n) {
+    if (!ctx || !params || !n) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    Volume *v = find_volume(c, vol);
+    if (!v) return set_err(c, KS_ENOTFOUND, "unknown volume");
+    if (params->stride < 1) return set_err(c, KS_EINVAL, "stride must be >= 1");
+    auto cnt = [&](int d) { return d > params->stride / 2 ? (d - params->stride / 2 - 1) / params->stride + 1 : 0; };
+    *n = (int64_t)cnt(v->nx) * cnt(v->ny) * cnt(v->nz);
+    return KS_OK;
+}
+
+}  // extern "C"
+
+namespace ks {
+
+// Shared by ks_seed_climb, ks_meanshift and the batched launch: seeds to the
+// device, one SeedJob, one queue segment.
+static int seeds_to_device(Ctx *c, Volume *v, const ks_params *p, const int32_t *seeds_xyz,
+                           int64_t n_in, std::vector<int32_t> *host, int32_t **dev) {
+    if (seeds_xyz) {
+        host->assign(seeds_xyz, seeds_xyz + 3 * n_in);
+        for (int64_t i = 0; i < n_in; ++i) {
+            const int32_t x = seeds_xyz[3 * i], y = seeds_xyz[3 * i + 1], z = seeds_xyz[3 * i + 2];
+            if (x < 0 || y < 0 || z < 0 || x >= v->nx || y >= v->ny || z >= v->nz)
+                return set_err(c, KS_EINVAL, "seed outside the volume");
+        }
+    } else {
+        *host = seed_grid(v->nx, v->ny, v->nz, p->stride);
+    }
+    cudaError_t e;
+    *dev = (int32_t *)scratch(c, kScSeeds, std::max<size_t>(host->size() * 4, 16), &e);
+    if (!*dev) return cuda_err(c, e, "seed buffer");
+    if (!host->empty())
+        KS_TRY_CUDA(c, cudaMemcpyAsync(*dev, host->data(), host->size() * 4,
+                                       cudaMemcpyHostToDevice, c->stream));
+    return KS_OK;
+}
+
+struct QueueBuf {
+    SeedJob *jobs;
+    int64_t *seg_start;
+    int *seg_kind, *seg_job;
+};
+
+// Lay jobs + segments out in one device buffer (c->batch_mem, grown on
+// demand), copy them, and fill a SeedQueue.
+static int upload_queue(Ctx *c, const std::vector<SeedJob> &jobs, const std::vector<int64_t> &ss,
+                        const std::vector<int> &sk, const std::vector<int> &sj, SeedQueue *q) {
+    const size_t bj = jobs.size() * sizeof(SeedJob);
+    const size_t bs = ss.size() * 8, bk = sk.size() * 4, bjj = sj.size() * 4;
+    const size_t need = 256 + bj + bs + bk + bjj + 64;
+    if (c->batch_mem_bytes < need) {
+        cudaStreamSynchronize(c->stream);
+        dev_free(c, c->batch_mem, c->batch_mem_bytes);
+        c->batch_mem = nullptr;
+        c->batch_mem_bytes = 0;
+        void *p;
+        KS_TRY_CUDA(c, dev_alloc(c, &p, need * 2));
+        c->batch_mem = p;
+        c->batch_mem_bytes = need * 2;
+    }
+    std::vector<uint8_t> h(need, 0);
+    size_t off = 256;   // first 256 bytes: the persistent-queue head counter
+    auto put = [&](const void *src, size_t n) {
+        const size_t at = off;
+        if (n) std::memcpy(h.data() + at, src, n);
+        off += (n + 15) / 16 * 16;
+        return (uint8_t *)c->batch_mem + at;
+    };
+    q->jobs = (const SeedJob *)put(jobs.data(), bj);
+    q->seg_start = (const int64_t *)put(ss.data(), bs);
+    q->seg_kind = (const int *)put(sk.data(), bk);
+    q->seg_job = (const int *)put(sj.data(), bjj);
+    q->n_segs = (int)sk.size();
+    q->n_items = ss.back();
+    q->head = (unsigned long long *)c->batch_mem;
+    KS_TRY_CUDA(c, cudaMemcpyAsync(c->batch_mem, h.data(), off, cudaMemcpyHostToDevice, c->stream));
+    return KS_OK;
+}
+
+static int run_queue(Ctx *c, const SeedQueue &q, int max_B, int max_S, bool persistent) {
+    if (q.n_items == 0) return KS_OK;
+    const int grid = persistent ? c->num_sms * seed_blocks_per_sm(max_B, max_S) : (int)q.n_items;
+    ProfRec rec;
+    prof_begin(c, persistent ? "ks_seeds_persistent" : "ks_seeds", c->stream, &rec);
+    cudaError_t e = launch_seeds(c->lc(), q, c->bt, c->T, c->L, max_B, max_S, persistent, grid);
+    prof_end(c, &rec, c->stream);
+    return cuda_err(c, e, "seed launch");
+}
+
+static int seed_common(Ctx *c, ks_vol vol, const ks_params *p, const int32_t *seeds_xyz,
+                       int64_t n_seeds, int kind, void *out, int64_t capacity, int64_t *n_out,
+                       int32_t *traj, int out_on_device) {
+    std::string why;
+    int st = validate_params(p, &why);
+    if (st) return set_err(c, st, why);
+    if (!out || !n_out) return set_err(c, KS_EINVAL, "out / n_out is NULL");
+    if (seeds_xyz && n_seeds < 0) return set_err(c, KS_EINVAL, "n_seeds < 0");
+    Volume *v = find_volume(c, vol);
+    if (!v) return set_err(c, KS_ENOTFOUND, "unknown volume");
+    std::vector<int32_t> hs;
+    int32_t *ds;
+    st = seeds_to_device(c, v, p, seeds_xyz, n_seeds, &hs, &ds);
+    if (st) return st;
+    const int64_t ns = (int64_t)hs.size() / 3;
+    const int S = p->r_max - p->r_min + 1;
+    const int64_t n_items = kind == kOctant ? ns : ns * S;
+    *n_out = n_items;
+    if (capacity < n_items) return set_err(c, KS_EINVAL, "output capacity too small");
+    const size_t rec = kind == kOctant ? sizeof(ks_seed_result) : sizeof(ks_ms_result);
+    cudaError_t e = cudaSuccess;
+    void *dout = out;
+    if (!out_on_device) dout = scratch(c, kind == kOctant ? kScOct : kScMs, n_items * rec + 16, &e);
+    int32_t *dtraj = traj;
+    const size_t traj_bytes = (size_t)ns * (p->max_iter + 1) * 3 * 4;
+    if (traj && !out_on_device && e == cudaSuccess)
+        dtraj = (int32_t *)scratch(c, kScTraj, traj_bytes + 16, &e);
+    if (e != cudaSuccess) return cuda_err(c, e, "seed outputs");
+    SeedJob J{};
+    J.vol = v->desc;
+    J.r_min = p->r_min;
+    J.r_max = p->r_max;
+    J.S = S;
+    J.max_iter = p->max_iter;
+    J.w_norm = p->w_norm;
+    J.seeds = ds;
+    J.n_seeds = ns;
+    J.oct_out = kind == kOctant ? (ks_seed_result *)dout : nullptr;
+    J.ms_out = kind == kMeanShift ? (ks_ms_result *)dout : nullptr;
+    J.traj = kind == kOctant ? dtraj : nullptr;
+    SeedQueue q{};
+    st = upload_queue(c, {J}, {0, n_items}, {kind}, {0}, &q);
+    if (st) return st;
+    st = run_queue(c, q, v->binning.bins, S, false);
+    if (st) return st;
+    if (!out_on_device && n_items) {
+        KS_TRY_CUDA(c, cudaMemcpyAsync(out, dout, n_items * rec, cudaMemcpyDeviceToHost, c->stream));
+        if (traj && kind == kOctant)
+            KS_TRY_CUDA(c, cudaMemcpyAsync(traj, dtraj, traj_bytes, cudaMemcpyDeviceToHost, c->stream));
+    }
+    return check_status(c);
+}
+
+}  // namespace ks
+
+extern "C" {
+
+int ks_seed_climb(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_t *seeds_xyz,
+                  int64_t n_seeds, ks_seed_result *out, int64_t capacity, int64_t *n_out,
+                  int32_t *traj, int out_on_device) {
+    if (!ctx) return KS_EINVAL;
+    return seed_common(&ctx->impl, vol, params, seeds_xyz, n_seeds, kOctant, out, capacity, n_out,
+                       traj, out_on_device);
+}
+
+int ks_meanshift(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_t *seeds_xyz,
+                 int64_t n_seeds, ks_ms_result *out, int64_t capacity, int64_t *n_out,
+                 int out_on_device) {
+    if (!ctx) return KS_EINVAL;
+    return seed_common(&ctx->impl, vol, params, seeds_xyz, n_seeds, kMeanShift, out, capacity,
+                       n_out, nullptr, out_on_device);
+}
+
+}  // extern "C"
+
+
+extern "C" {
+
+int ks_batch_seeds(ks_ctx *ctx, const ks_vol *vols, const ks_params *params, int n_vols,
+                   int kinds, ks_seed_result *const *oct_out, ks_ms_result *const *ms_out,
+                   int use_graph) {
+    if (!ctx || !vols || !params || n_vols < 1 || !(kinds & 3)) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    std::string why;
+    std::vector<Volume *> vs(n_vols);
+    for (int i = 0; i < n_vols; ++i) {
+        int st = validate_params(&params[i], &why);
+        if (st) return set_err(c, st, why);
+        vs[i] = find_volume(c, vols[i]);
+        if (!vs[i]) return set_err(c, KS_ENOTFOUND, "unknown volume");
+    }
+    // signature of this batch (volume handles, params, kinds)
+    std::vector<int64_t> key{kinds, n_vols};
+    for (int i = 0; i < n_vols; ++i) {
+        key.push_back(vols[i]);
+        const ks_params &p = params[i];
+        key.insert(key.end(), {p.r_min, p.r_max, p.stride, p.max_iter, p.w_norm});
+    }
+    BatchGraph *bg = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_graph_mu);
+        for (auto &x : g_graphs[c])
+            if (x->key == key) bg = x.get();
+    }
+    if (!bg) {
+        auto nb = std::make_unique<BatchGraph>();
+        nb->key = key;
+        // seeds + outputs of every volume in one allocation
+        std::vector<std::vector<int32_t>> seeds(n_vols);
+        size_t seed_bytes = 0, oct_bytes = 0, ms_bytes = 0;
+        for (int i = 0; i < n_vols; ++i) {
+            seeds[i] = seed_grid(vs[i]->nx, vs[i]->ny, vs[i]->nz, params[i].stride);
+            const int64_t ns = (int64_t)seeds[i].size() / 3;
+            const int S = params[i].r_max - params[i].r_min + 1;
+            nb->n_oct.push_back((kinds & 1) ? ns : 0);
+            nb->n_ms.push_back((kinds & 2) ? ns * S : 0);
+            seed_bytes += (seeds[i].size() * 4 + 15) / 16 * 16;
+            nb->oct_at.push_back(oct_bytes);
+            nb->ms_at.push_back(ms_bytes);
+            oct_bytes += nb->n_oct.back() * sizeof(ks_seed_result);
+            ms_bytes += nb->n_ms.back() * sizeof(ks_ms_result);
+            nb->max_B = std::max(nb->max_B, vs[i]->binning.bins);
+            nb->max_S = std::max(nb->max_S, S);
+        }
+        std::vector<SeedJob> jobs(n_vols);
+        std::vector<int64_t> ss{0};
+        std::vector<int> sk, sj;
+        const size_t jobs_at = 0, seg_at = (n_vols * sizeof(SeedJob) + 255) / 256 * 256;
+        const size_t segs_bytes = (2 * n_vols + 1) * 8 + 2 * (2 * n_vols) * 4 + 64;
+        const size_t seeds_at = seg_at + (segs_bytes + 255) / 256 * 256;
+        nb->oct_off = seeds_at + (seed_bytes + 255) / 256 * 256;
+        nb->ms_off = nb->oct_off + (oct_bytes + 255) / 256 * 256;
+        nb->bytes = nb->ms_off + ms_bytes + 256 + 256;   // + head counter
+        void *p;
+        cudaError_t e = dev_alloc(c, &p, nb->bytes);
+        if (e != cudaSuccess) return cuda_err(c, e, "batch buffers");
+        nb->mem = p;
+        uint8_t *m = (uint8_t *)p;
+        std::vector<uint8_t> host(nb->ms_off, 0);
+        size_t so = seeds_at;
+        for (int i = 0; i < n_vols; ++i) {
+            std::memcpy(host.data() + so, seeds[i].data(), seeds[i].size() * 4);
+            SeedJob &J = jobs[i];
+            J.vol = vs[i]->desc;
+            J.r_min = params[i].r_min;
+            J.r_max = params[i].r_max;
+            J.S = params[i].r_max - params[i].r_min + 1;
+            J.max_iter = params[i].max_iter;
+            J.w_norm = params[i].w_norm;
+            J.seeds = (const int32_t *)(m + so);
+            J.n_seeds = (int64_t)seeds[i].size() / 3;
+            J.oct_out = (ks_seed_result *)(m + nb->oct_off + nb->oct_at[i]);
+            J.ms_out = (ks_ms_result *)(m + nb->ms_off + nb->ms_at[i]);
+            J.traj = nullptr;
+            so += (seeds[i].size() * 4 + 15) / 16 * 16;
+        }
+        // octant segments first (the longest items), then mean shift
+        for (int kind = 0; kind < 2; ++kind)
+            for (int i = 0; i < n_vols; ++i) {
+                const int64_t n = kind == 0 ? nb->n_oct[i] : nb->n_ms[i];
+                if (!n) continue;
+                ss.push_back(ss.back() + n);
+                sk.push_back(kind == 0 ? kOctant : kMeanShift);
+                sj.push_back(i);
+            }
+        std::memcpy(host.data() + jobs_at, jobs.data(), n_vols * sizeof(SeedJob));
+        size_t o = seg_at;
+        std::memcpy(host.data() + o, ss.data(), ss.size() * 8);
+        SeedQueue q{};
+        q.jobs = (const SeedJob *)(m + jobs_at);
+        q.seg_start = (const int64_t *)(m + o);
+        o += (ss.size() * 8 + 15) / 16 * 16;
+        std::memcpy(host.data() + o, sk.data(), sk.size() * 4);
+        q.seg_kind = (const int *)(m + o);
+        o += (sk.size() * 4 + 15) / 16 * 16;
+        std::memcpy(host.data() + o, sj.data(), sj.size() * 4);
+        q.seg_job = (const int *)(m + o);
+        q.n_segs = (int)sk.size();
+        q.n_items = ss.back();
+        q.head = (unsigned long long *)(m + nb->bytes - 256);
+        KS_TRY_CUDA(c, cudaMemcpyAsync(m, host.data(), host.size(), cudaMemcpyHostToDevice,
+                                       c->stream));
+        KS_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+        // capture [reset head; persistent launch] as a graph
+        const int grid = c->num_sms * seed_blocks_per_sm(nb->max_B, nb->max_S);
+        cudaGraph_t graph;
+        KS_TRY_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        cudaMemsetAsync(q.head, 0, 8, c->stream);
+        cudaError_t le = launch_seeds(c->lc(), q, c->bt, c->T, c->L, nb->max_B, nb->max_S, true, grid);
+        e = cudaStreamEndCapture(c->stream, &graph);
+        if (le != cudaSuccess) e = le;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&nb->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            dev_free(c, nb->mem, nb->bytes);
+            return cuda_err(c, e, "batch graph");
+        }
+        nb->q = q;                      // kept for the direct (non-graph) launch
+        nb->grid = grid;
+        bg = nb.get();
+        std::lock_guard<std::mutex> g(g_graph_mu);
+        g_graphs[c].push_back(std::move(nb));
+    }
+    ProfRec rec;
+    prof_begin(c, "ks_seeds_persistent", c->stream, &rec);
+    if (use_graph) {
+        KS_TRY_CUDA(c, cudaGraphLaunch(bg->exec, c->stream));
+    } else {
+        KS_TRY_CUDA(c, cudaMemsetAsync(bg->q.head, 0, 8, c->stream));
+        KS_TRY_CUDA(c, launch_seeds(c->lc(), bg->q, c->bt, c->T, c->L, bg->max_B, bg->max_S, true,
+                                    bg->grid));
+    }
+    prof_end(c, &rec, c->stream);
+    for (int i = 0; i < n_vols; ++i) {
+        if (oct_out && oct_out[i] && bg->n_oct[i])
+            KS_TRY_CUDA(c, cudaMemcpyAsync(oct_out[i], (uint8_t *)bg->mem + bg->oct_off + bg->oct_at[i],
+                                           bg->n_oct[i] * sizeof(ks_seed_result),
+                                           cudaMemcpyDeviceToHost, c->stream));
+        if (ms_out && ms_out[i] && bg->n_ms[i])
+            KS_TRY_CUDA(c, cudaMemcpyAsync(ms_out[i], (uint8_t *)bg->mem + bg->ms_off + bg->ms_at[i],
+                                           bg->n_ms[i] * sizeof(ks_ms_result),
+                                           cudaMemcpyDeviceToHost, c->stream));
+    }
+    return check_status(c);
+}
+
+// ------------------------------------------------------------- diagnostics
+int ks_tables(ks_ctx *ctx, int64_t nmax, double *T, double *L) {
+    if (!ctx || nmax < 0 || nmax > kTableN || !T || !L) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    KS_TRY_CUDA(c, cudaMemcpy(T, c->T, (nmax + 1) * 8, cudaMemcpyDeviceToHost));
+    KS_TRY_CUDA(c, cudaMemcpy(L, c->L, (nmax + 1) * 8, cudaMemcpyDeviceToHost));
+    return KS_OK;
+}
+
+int64_t ks_launch_count(ks_ctx *ctx) { return ctx ? ctx->impl.launches.load() : -1; }
+
+int ks_set_profiling(ks_ctx *ctx, int on) {
+    if (!ctx) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    cudaStreamSynchronize(c->stream);
+    std::lock_guard<std::mutex> g(c->mu);
+    for (auto &r : c->prof) {
+        if (r.a) cudaEventDestroy(r.a);
+        if (r.b) cudaEventDestroy(r.b);
+    }
+    c->prof.clear();
+    c->profiling = on != 0;
+    return KS_OK;
+}
+
+int ks_kernel_time(ks_ctx *ctx, const char *prefix, double *ms_total, int64_t *launches) {
+    if (!ctx || !prefix || !ms_total || !launches) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    cudaStreamSynchronize(c->stream);
+    std::lock_guard<std::mutex> g(c->mu);
+    double t = 0;
+    int64_t n = 0;
+    const size_t lp = std::strlen(prefix);
+    for (auto &r : c->prof) {
+        if (r.name.compare(0, lp, prefix) != 0 || !r.a) continue;
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            t += ms;
+            ++n;
+        }
+    }
+    *ms_total = t;
+    *launches = n;
+    return KS_OK;
+}
+
+int ks_measure_smem_peak(ks_ctx *ctx, double *per_s) {
+    if (!ctx || !per_s) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    cudaError_t e;
+    uint32_t *sink = (uint32_t *)scratch(c, kScTune, 4096 * 4, &e);
+    if (!sink) return cuda_err(c, e, "smem peak");
+    const int blocks = c->num_sms * 4, iters = 4096;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(a, c->stream);
+        c->launches++;
+        e = launch_smem_peak(c->lc(), sink, blocks, iters);
+        cudaEventRecord(b, c->stream);
+        if (e != cudaSuccess) break;
+        cudaEventSynchronize(b);
+        float ms;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_err(c, e, "smem peak");
+    *per_s = (double)blocks * 512.0 * iters * 16.0 / (best * 1e-3);
+    return KS_OK;
+}
+
+int ks_dense_config(ks_ctx *ctx, int bins, int r_max, int *path, int *warps, int *ty, int *tz) {
+    if (!ctx || !path || !warps || !ty || !tz) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    std::lock_guard<std::mutex> g(c->mu);
+    for (auto &kv : c->tune)
+        if (kv.first.B == bins && kv.first.r_max == r_max) {
+            *path = kv.second.path;
+            *warps = kv.second.warps;
+            *ty = kv.second.ty;
+            *tz = kv.second.tz;
+            return KS_OK;
+        }
+    return KS_ENOTFOUND;
+}
+
+// Force the dense launch configuration for every context (path < 0: back
+// to the autotuner).  Returns KS_EINVAL for a shape that can never fit.
+int ks_force_dense_config(int path, int warps, int ty, int tz) {
+    if (path < 0) {
+        g_forced_path = -1;
+        return KS_OK;
+    }
+    if (path > 1 || warps < 1 || warps > 16 || ty * tz != warps) return KS_EINVAL;
+    g_forced_path = path;
+    g_forced_warps = warps;
+    g_forced_ty = ty;
+    g_forced_tz = tz;
+    return KS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,242 @@
+// Intensity -> bin map beta(s) (Eq. 4-5; Sec. 3.2's window level), written
+// as the stored value b+1 (0 = not counted) into the halo-padded bin volume.
+//
+// HBM-bound: each thread handles a 16-voxel run of one row, read with
+// 16-byte vector loads when the row layout allows it and written with one
+// 16-byte store (the padded volume keeps every run 16-byte aligned).
+#include "ks_internal.cuh"
+
+namespace ks {
+namespace {
+
+struct IntBin {
+    int kind, bins, shift, lo, hi;
+    __device__ __forceinline__ uint8_t operator()(int v) const {
+        if (kind == KS_BIN_WINDOW && (v < lo || v > hi)) return 0;
+        v = v < lo ? lo : (v > hi ? hi : v);
+        int b = (v - lo) >> shift;
+        b = b > bins - 1 ? bins - 1 : b;
+        return (uint8_t)(b + 1);
+    }
+};
+
+struct F32Bin {
+    float vmin, d, fb;
+    int bins;
+    // a = v - vmin; t = bins * a; q = t / d, d = (vmax - vmin) + 1e-6f;
+    // every step one binary32 operation rounded to nearest.
+    __device__ __forceinline__ uint8_t operator()(float v) const {
+        const float a = __fsub_rn(v, vmin);
+        const float t = __fmul_rn(fb, a);
+        const float q = __fdiv_rn(t, d);
+        int b = (int)floorf(q);
+        b = b < 0 ? 0 : (b > bins - 1 ? bins - 1 : b);
+        return (uint8_t)(b + 1);
+    }
+};
+
+template <typename T>
+struct Vec16;  // 16 consecutive elements as whole 16-byte words
+template <>
+struct Vec16<uint8_t> {
+    static constexpr int kWords = 1;
+};
+template <>
+struct Vec16<int16_t> {
+    static constexpr int kWords = 2;
+};
+template <>
+struct Vec16<float> {
+    static constexpr int kWords = 4;
+};
+
+// One thread per (row, 16-voxel run).  `vec` = rows start 16-byte aligned
+// and nx is a multiple of 16 (then every run is full and aligned).
+template <typename T, typename Op>
+__global__ void k_bin_rows(const T *__restrict__ in, int nx, int ny, int nz, int64_t pitch,
+                           int64_t plane, uint8_t *__restrict__ base, Op op, bool vec) {
+    const int runs = (nx + 15) >> 4;
+    const int64_t total = (int64_t)runs * ny * nz;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int run = (int)(t % runs);
+        const int64_t row = t / runs;          // z * ny + y
+        const int y = (int)(row % ny);
+        const int z = (int)(row / ny);
+        const int x0 = run << 4;
+        const T *src = in + row * nx + x0;
+        uint8_t *dst = base + z * plane + y * pitch + x0;
+        if (vec) {
+            union {
+                uint4 w[Vec16<T>::kWords];
+                T e[16];
+            } u;
+#pragma unroll
+            for (int k = 0; k < Vec16<T>::kWords; ++k)
+                u.w[k] = __ldg(reinterpret_cast<const uint4 *>(src) + k);
+            union {
+                uint4 w;
+                uint8_t b[16];
+            } o;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) o.b[k] = op(u.e[k]);
+            *reinterpret_cast<uint4 *>(dst) = o.w;
+        } else {
+            const int n = nx - x0 < 16 ? nx - x0 : 16;
+            for (int k = 0; k < n; ++k) dst[k] = op(src[k]);
+        }
+    }
+}
+
+// Per-block (min, max) partials of a float volume.
+__global__ void k_minmax_partials(const float *__restrict__ in, int64_t n, float2 *partial,
+                                  bool vec4) {
+    float lo = INFINITY, hi = -INFINITY;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (vec4) {
+        const int64_t n4 = n >> 2;
+        for (int64_t i = t0; i < n4; i += stride) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(in) + i);
+            lo = fminf(lo, fminf(fminf(v.x, v.y), fminf(v.z, v.w)));
+            hi = fmaxf(hi, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+        }
+        for (int64_t i = (n4 << 2) + t0; i < n; i += stride) {
+            lo = fminf(lo, in[i]);
+            hi = fmaxf(hi, in[i]);
+        }
+    } else {
+        for (int64_t i = t0; i < n; i += stride) {
+            lo = fminf(lo, in[i]);
+            hi = fmaxf(hi, in[i]);
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    __shared__ float2 w[32];
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = make_float2(lo, hi);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int nw = blockDim.x >> 5;
+        float2 v = threadIdx.x < nw ? w[threadIdx.x] : make_float2(INFINITY, -INFINITY);
+        for (int o = 16; o; o >>= 1) {
+            v.x = fminf(v.x, __shfl_xor_sync(0xffffffffu, v.x, o));
+            v.y = fmaxf(v.y, __shfl_xor_sync(0xffffffffu, v.y, o));
+        }
+        if (threadIdx.x == 0) partial[blockIdx.x] = v;
+    }
+}
+
+// Every block first folds the partials into the exact volume min/max, then
+// bins its runs.  min/max are exact and order-free, so each block obtains
+// the same pair.
+__global__ void k_bin_f32(const float *__restrict__ in, int nx, int ny, int nz, int64_t pitch,
+                          int64_t plane, uint8_t *__restrict__ base, int bins,
+                          const float2 *__restrict__ partial, int nparts, bool vec) {
+    float lo = INFINITY, hi = -INFINITY;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        const float2 p = partial[i];
+        lo = fminf(lo, p.x);
+        hi = fmaxf(hi, p.y);
+    }
+    for (int o = 16; o; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    __shared__ float2 w[32];
+    __shared__ float2 mm;
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = make_float2(lo, hi);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float2 v = w[0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            v.x = fminf(v.x, w[k].x);
+            v.y = fmaxf(v.y, w[k].y);
+        }
+        mm = v;
+    }
+    __syncthreads();
+    F32Bin op;
+    op.vmin = mm.x;
+    op.d = __fadd_rn(__fsub_rn(mm.y, mm.x), 1e-6f);
+    op.fb = (float)bins;
+    op.bins = bins;
+    // same loop as k_bin_rows<float>
+    const int runs = (nx + 15) >> 4;
+    const int64_t total = (int64_t)runs * ny * nz;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int run = (int)(t % runs);
+        const int64_t row = t / runs;
+        const int y = (int)(row % ny);
+        const int z = (int)(row / ny);
+        const int x0 = run << 4;
+        const float *src = in + row * nx + x0;
+        uint8_t *dst = base + z * plane + y * pitch + x0;
+        if (vec) {
+            union {
+                uint4 w[4];
+                float e[16];
+            } u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) u.w[k] = __ldg(reinterpret_cast<const uint4 *>(src) + k);
+            union {
+                uint4 w;
+                uint8_t b[16];
+            } o;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) o.b[k] = op(u.e[k]);
+            *reinterpret_cast<uint4 *>(dst) = o.w;
+        } else {
+            const int n = nx - x0 < 16 ? nx - x0 : 16;
+            for (int k = 0; k < n; ++k) dst[k] = op(src[k]);
+        }
+    }
+}
+
+int grid_for(int64_t work, int num_sms) {
+    const int64_t per = 256;
+    int64_t g = (work + per - 1) / per;
+    const int64_t cap = (int64_t)num_sms * 16;
+    return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+}  // namespace
+
+cudaError_t launch_bin_int(const LaunchCtx &lc, const void *raw, int dtype, int nx, int ny,
+                           int nz, const ks_binning &b, uint8_t *base, int64_t pitch,
+                           int64_t plane) {
+    IntBin op{b.kind, b.bins, b.shift, b.lo, b.hi};
+    const int64_t work = (int64_t)((nx + 15) / 16) * ny * nz;
+    const int grid = grid_for(work, lc.num_sms);
+    const bool aligned = (reinterpret_cast<uintptr_t>(raw) & 15) == 0 && nx % 16 == 0;
+    if (dtype == KS_U8)
+        k_bin_rows<uint8_t, IntBin><<<grid, 256, 0, lc.stream>>>(
+            static_cast<const uint8_t *>(raw), nx, ny, nz, pitch, plane, base, op, aligned);
+    else
+        k_bin_rows<int16_t, IntBin><<<grid, 256, 0, lc.stream>>>(
+            static_cast<const int16_t *>(raw), nx, ny, nz, pitch, plane, base, op, aligned);
+    return cudaGetLastError();
+}
+
+int bin_f32_scratch_blocks(int num_sms) { return num_sms * 4; }
+
+cudaError_t launch_bin_f32(const LaunchCtx &lc, const float *raw, int nx, int ny, int nz,
+                           int bins, uint8_t *base, int64_t pitch, int64_t plane,
+                           float2 *scratch, int scratch_blocks) {
+    const int64_t n = (int64_t)nx * ny * nz;
+    const bool vec4 = (reinterpret_cast<uintptr_t>(raw) & 15) == 0;
+    k_minmax_partials<<<scratch_blocks, 256, 0, lc.stream>>>(raw, n, scratch, vec4);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t work = (int64_t)((nx + 15) / 16) * ny * nz;
+    const int grid = grid_for(work, lc.num_sms);
+    const bool aligned = vec4 && nx % 16 == 0;
+    k_bin_f32<<<grid, 256, 0, lc.stream>>>(raw, nx, ny, nz, pitch, plane, base, bins, scratch,
+                                           scratch_blocks, aligned);
+    return cudaGetLastError();
+}
+
+}  // namespace ks

@@ -1,0 +1,207 @@
+// Internal declarations shared by the library's CUDA translation units.
+// Device-side descriptors, PTX helpers (mbarrier, TMA, shared-memory
+// reductions) and the host-side launch functions each kernel file exports.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ks.h"
+
+namespace ks {
+
+// Every bin volume is stored with this many "not counted" (zero) voxels on
+// each side, so a window of radius <= KS_HALO around any in-volume centre
+// reads only allocated, zero-initialised memory and needs no bounds checks.
+constexpr int kHalo = 32;
+constexpr int kRmax = 32;            // largest supported window radius
+constexpr int kTableN = 137065;      // |Ball(32)|: largest possible count
+constexpr int kMaxBins = 64;
+constexpr int kMaxScales = kRmax;    // r_max - r_min + 1 <= 32
+constexpr int kSeedThreads = 256;    // block size of the seed kernels
+
+// Device status word bits (ctx->d_status); read back by ks_sync.
+constexpr int kStatusTmaTimeout = 1;
+constexpr int kStatusQueueTimeout = 2;
+
+// A resident bin volume as the kernels see it.  base points at voxel
+// (0,0,0); voxel (x,y,z) is base[z*plane + y*pitch + x] for
+// -kHalo <= x < nx + kHalo (same for y, z).  pitch is a multiple of 16.
+struct VolDesc {
+    const uint8_t *base;
+    int nx, ny, nz, B;
+    int64_t pitch, plane;
+};
+
+// Offsets of Ball(32) used by the kernels (built once per context).
+//  ball:   every offset o with |o| <= 32, sorted by its radius class
+//          rho(o) = ceil(|o|) (the smallest r with |o|^2 <= r^2), then by
+//          dz, dy, dx; packed (dx+64) | (dy+64) << 8 | (dz+64) << 16 |
+//          rho << 24.  Ball(r) is the prefix of length ball_size[r].
+//  canon:  offsets with dx, dy, dz >= 0 (one per set of sign mirrors),
+//          sorted by rho, then "all three nonzero" entries first; packed
+//          dx | dy << 8 | dz << 16 | mirror_mask << 24 where bit s of the
+//          mask marks the distinct sign pattern s (bit0: -x, bit1: -y,
+//          bit2: -z).  canon_start[rho] .. canon_start[rho+1] is class rho,
+//          and canon_split[rho] the first entry whose mask is not 0xFF.
+struct BallTables {
+    const uint32_t *ball;
+    const uint32_t *canon;
+    const int *canon_start;   // [kRmax + 2]
+    const int *canon_split;   // [kRmax + 1]
+    const int *ball_size;     // [kRmax + 1]
+};
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void red_add_shared(uint32_t addr, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+__device__ __forceinline__ uint32_t ld_shared_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void st_shared_u32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after `limit` polls (each poll may suspend the
+// thread for a hardware-chosen time); returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase, int limit) {
+    for (int i = 0; i < limit; ++i)
+        if (mbar_try_wait(mbar, phase)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            int z, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+        : "memory");
+}
+
+// ------------------------------------------------------- exact FP64 steps
+// The entropy of a window's counts.  One fixed operation order shared by
+// every kernel: occupied-bin count, sum of T[c_b] in bin order (terms with
+// c_b <= 1 are exactly +0 and are skipped, which leaves the sum unchanged),
+// one IEEE division and one subtraction.  At most one occupied bin -> 0.
+__device__ __forceinline__ double entropy_from_sum(double s, uint32_t N, int occupied,
+                                                   const double *__restrict__ L) {
+    if (occupied <= 1) return 0.0;
+    return __dsub_rn(__ldg(L + N), __ddiv_rn(s, (double)N));
+}
+
+// W(r) = f(r) * (D / (N * Np)), f = r^2/(2r-1) or 1.
+__device__ __forceinline__ double kb_weight(uint64_t D, uint32_t N, uint32_t Np, int r,
+                                            int w_norm) {
+    if (N == 0 || Np == 0) return 0.0;
+    const double f = w_norm == KS_WNORM_ONE
+                         ? 1.0
+                         : __ddiv_rn((double)(r * r), (double)(2 * r - 1));
+    const double q = __ddiv_rn((double)D, (double)((uint64_t)N * (uint64_t)Np));
+    return __dmul_rn(f, q);
+}
+
+// --------------------------------------------------------------- launches
+struct LaunchCtx {
+    cudaStream_t stream;
+    int *d_status;
+    int num_sms;
+};
+
+// |Ball(r)| by enumeration (host).
+int ball_size_host(int r);
+
+// ks_tables.cu
+cudaError_t launch_tables(const LaunchCtx &lc, double *T, double *L, int64_t n);
+
+// ks_bin.cu
+cudaError_t launch_bin_int(const LaunchCtx &lc, const void *raw, int dtype, int nx, int ny,
+                           int nz, const ks_binning &b, uint8_t *base, int64_t pitch,
+                           int64_t plane);
+// float32 affine binning: a min/max pass writing per-block partials into
+// `scratch` (scratch_blocks float2 entries), then the binning pass.
+int bin_f32_scratch_blocks(int num_sms);
+cudaError_t launch_bin_f32(const LaunchCtx &lc, const float *raw, int nx, int ny, int nz,
+                           int bins, uint8_t *base, int64_t pitch, int64_t plane,
+                           float2 *scratch, int scratch_blocks);
+
+// ks_dense.cu
+struct DenseConfig {
+    int path;      // 0 = TMA brick in shared memory, 1 = direct loads (L1/L2)
+    int warps;     // warps per block (each warp owns one row of 32 centres)
+    int ty, tz;    // tile rows in y and z (ty * tz = warps)
+};
+struct DenseOut {
+    double *Y;
+    uint8_t *s;
+    double *H;     // optional, voxel-major x S
+    double *W;     // optional
+};
+bool dense_config_fits(const DenseConfig &c, int B, int r_max);
+size_t dense_smem_bytes(const DenseConfig &c, int B, int r_max);
+cudaError_t launch_dense(const LaunchCtx &lc, const VolDesc &v, const CUtensorMap *tmap,
+                         const BallTables &bt, const double *T, const double *L, int r_min,
+                         int r_max, int w_norm, const DenseConfig &cfg, const DenseOut &out,
+                         int z0, int z1);
+
+// ks_seeds.cu
+enum ItemKind { kOctant = 0, kMeanShift = 1 };
+struct SeedJob {
+    VolDesc vol;
+    int r_min, r_max, S, max_iter, w_norm;
+    const int32_t *seeds;        // device xyz triples
+    int64_t n_seeds;
+    ks_seed_result *oct_out;     // device, n_seeds (kind octant)
+    ks_ms_result *ms_out;        // device, n_seeds * S (kind mean shift)
+    int32_t *traj;               // device, n_seeds * (max_iter+1) * 3, or null
+};
+// A work queue: segments of items, segment k covers items
+// [seg_start[k], seg_start[k+1]) of kind seg_kind[k] on job seg_job[k].
+struct SeedQueue {
+    const SeedJob *jobs;
+    const int64_t *seg_start;
+    const int *seg_kind;
+    const int *seg_job;
+    int n_segs;
+    int64_t n_items;
+    unsigned long long *head;    // persistent mode: next item counter
+};
+size_t seed_smem_bytes(int B, int S);
+cudaError_t launch_seeds(const LaunchCtx &lc, const SeedQueue &q, const BallTables &bt,
+                         const double *T, const double *L, int max_B, int max_S,
+                         bool persistent, int grid);
+int seed_blocks_per_sm(int max_B, int max_S);
+
+// Micro-kernel: shared-memory increment rate (see ks_measure_smem_peak).
+cudaError_t launch_smem_peak(const LaunchCtx &lc, uint32_t *sink, int blocks, int iters);
+
+}  // namespace ks

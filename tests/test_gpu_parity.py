@@ -1,0 +1,337 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on
+the same seeded inputs.
+
+Bar: integer results bit-exact (bins, scale indices, seed positions,
+iteration counts, trajectories); FP64 results (H, W, Y, rho) within
+|gpu - oracle| <= 1e-12 * max(1, |oracle|), the entropy tolerance of the
+method's statement.  Both sides evaluate one fixed operation order on
+correctly rounded tables, so the observed difference is expected to be 0;
+the tests also report how many values are bit-identical.
+"""
+import numpy as np
+import pytest
+
+from paper_1310_6736_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+def close(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    assert a.shape == b.shape
+    bad = np.abs(a - b) > RTOL * np.maximum(1.0, np.abs(b))
+    assert not bad.any(), f"{bad.sum()} of {bad.size} differ; first at {np.argwhere(bad)[:3]}"
+    return int((a == b).sum())
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1310_6736_b300 import build, ks
+    build.build()
+    c = ks.Context()
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ks_mod():
+    from paper_1310_6736_b300 import ks
+    return ks
+
+
+def _params(ks, w):
+    return ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter)
+
+
+# ------------------------------------------------------------------ tables
+def test_tables_bit_exact(ctx, ko):
+    T, L = ctx.tables(137065)
+    To, Lo = ko.tables(137065)
+    assert np.array_equal(T.view(np.uint64), To[:137066].view(np.uint64))
+    assert np.array_equal(L.view(np.uint64), Lo[:137066].view(np.uint64))
+
+
+# ----------------------------------------------------------------- binning
+@pytest.mark.parametrize("name", ["spheres48", "pet128", "mr256"])
+def test_binning_bit_exact(ctx, ko, name):
+    w = synth.workload(name)
+    v = ctx.create_volume(w.volume, w.binning)
+    got = ctx.volume_bins(v, w.volume.shape)
+    ctx.release_volume(v)
+    assert np.array_equal(got, ko.bin_volume(w.volume, w.binning))
+
+
+@pytest.mark.parametrize("dims,dtype", [((37, 23, 19), np.uint8), ((33, 5, 7), np.int16),
+                                        ((17, 16, 3), np.float32), ((1, 1, 1), np.uint8),
+                                        ((64, 2, 2), np.int16)])
+def test_binning_ragged_and_kinds(ctx, ko, dims, dtype):
+    rng = np.random.default_rng(sum(dims))
+    nx, ny, nz = dims
+    if dtype == np.float32:
+        vol = rng.normal(3.0, 2.0, size=(nz, ny, nx)).astype(np.float32)
+        bins = [{"kind": 1, "bins": 32}]
+    elif dtype == np.int16:
+        vol = rng.integers(-200, 2300, size=(nz, ny, nx)).astype(np.int16)
+        bins = [{"kind": 0, "bins": 64, "shift": 5, "lo": 0, "hi": 2047},
+                {"kind": 2, "bins": 40, "shift": 5, "lo": 100, "hi": 1300}]
+    else:
+        vol = rng.integers(0, 256, size=(nz, ny, nx)).astype(np.uint8)
+        bins = [{"kind": 0, "bins": 16, "shift": 4, "lo": 0, "hi": 255},
+                {"kind": 2, "bins": 7, "shift": 4, "lo": 30, "hi": 140}]
+    for b in bins:
+        v = ctx.create_volume(vol, b)
+        got = ctx.volume_bins(v, vol.shape)
+        ctx.release_volume(v)
+        assert np.array_equal(got, ko.bin_volume(vol, b)), b
+
+
+# ------------------------------------------------------------------- dense
+def _dense_vs_oracle(ctx, ko, ks, bins_vol_raw, binning, r_min, r_max, w_norm=0, hw=True):
+    v = ctx.create_volume(bins_vol_raw, binning)
+    p = ks.make_params(r_min, r_max, 8, 20, w_norm)
+    if hw:
+        Y, s, H, W = ctx.dense_saliency(v, p, bins_vol_raw.shape, want_hw=True)
+    else:
+        Y, s = ctx.dense_saliency(v, p, bins_vol_raw.shape)
+    ctx.release_volume(v)
+    b = ko.bin_volume(bins_vol_raw, binning)
+    B = binning["bins"]
+    if hw:
+        Yo, so, Ho, Wo = ko.dense(b, B, r_min, r_max, w_norm=w_norm, want_hw=True)
+        close(H, Ho)
+        close(W, Wo)
+    else:
+        Yo, so = ko.dense(b, B, r_min, r_max, w_norm=w_norm)
+    assert np.array_equal(s, so)
+    return close(Y, Yo)
+
+
+@pytest.mark.parametrize("cfg", [None, (0, 16, 4, 4), (0, 8, 2, 4), (0, 4, 4, 1), (1, 16, 4, 4),
+                                 (1, 8, 8, 1)])
+def test_dense_spheres48_full_volume(ctx, ko, ks_mod, cfg):
+    ks = ks_mod
+    try:
+        if cfg is not None:
+            ks.force_dense_config(*cfg)
+        w = synth.workload("spheres48")
+        _dense_vs_oracle(ctx, ko, ks, w.volume, w.binning, w.r_min, w.r_max)
+    finally:
+        ks.force_dense_config(-1)
+
+
+@pytest.mark.parametrize("case", [
+    ((37, 23, 19), 5, 1, 6, 0),      # ragged tiles, odd bin count, r_min = 1
+    ((45, 9, 30), 33, 3, 9, 1),      # bins between template sizes, w_norm ONE
+    ((20, 20, 20), 64, 2, 7, 0),
+    ((1, 1, 1), 16, 1, 3, 0),        # one voxel
+    ((70, 3, 2), 16, 2, 12, 0),      # thin slab, radius larger than the volume
+])
+@pytest.mark.parametrize("path", [0, 1])
+def test_dense_random_volumes(ctx, ko, ks_mod, case, path):
+    ks = ks_mod
+    dims, B, r_min, r_max, wn = case
+    nx, ny, nz = dims
+    rng = np.random.default_rng(nx * 7 + B)
+    # blobs of high entropy over a two-level background, plus excluded voxels
+    vol = rng.choice([40, 41, 90], size=(nz, ny, nx), p=[0.6, 0.3, 0.1]).astype(np.int16)
+    blob = rng.random((nz, ny, nx)) < 0.25
+    vol[blob] = rng.integers(0, 2048, size=int(blob.sum()))
+    shift = max(0, int(np.ceil(np.log2(2048 / B))))
+    binning = {"kind": 2, "bins": B, "shift": shift, "lo": 30, "hi": min(2047, (B << shift) - 1)}
+    try:
+        ks.force_dense_config(path, 8, 4, 2)
+        _dense_vs_oracle(ctx, ko, ks, vol, binning, r_min, r_max, wn)
+    finally:
+        ks.force_dense_config(-1)
+
+
+def test_dense_pet128_full_size_sampled(ctx, ko, ks_mod):
+    """The bench workload (128x128x64 float32, 32 bins, r=4..20) at full size,
+    in the autotuned launch configuration; checked on sampled centres."""
+    ks = ks_mod
+    w = synth.workload("pet128")
+    v = ctx.create_volume(w.volume, w.binning)
+    p = _params(ks, w)
+    Y, s = ctx.dense_saliency(v, p, w.volume.shape)
+    ctx.release_volume(v)
+    b = ko.bin_volume(w.volume, w.binning)
+    rng = np.random.default_rng(0)
+    nz, ny, nx = w.volume.shape
+    cen = np.stack([rng.integers(0, nx, 3000), rng.integers(0, ny, 3000),
+                    rng.integers(0, nz, 3000)], axis=1)
+    edges = np.array([[0, 0, 0], [nx - 1, ny - 1, nz - 1], [nx - 1, 0, nz // 2],
+                      [0, ny - 1, 0], [nx // 2, ny // 2, nz - 1]])
+    cen = np.concatenate([cen, edges]).astype(np.int32)
+    Yo, so = ko.dense(b, 32, w.r_min, w.r_max, centres=cen)
+    got_Y = Y[cen[:, 2], cen[:, 1], cen[:, 0]]
+    got_s = s[cen[:, 2], cen[:, 1], cen[:, 0]]
+    assert np.array_equal(got_s, so)
+    close(got_Y, Yo)
+    # properties that hold at every voxel: s in {0} u (r_min, r_max), Y >= 0, Y = 0 iff no peak
+    assert set(np.unique(s)) <= {0} | set(range(w.r_min + 1, w.r_max))
+    assert (Y >= 0).all() and ((Y > 0) <= (s > 0)).all()
+
+
+# ------------------------------------------------------------------- seeds
+def _oct_vs_oracle(ctx, ko, ks, w, seeds=None, traj=True):
+    v = ctx.create_volume(w.volume, w.binning)
+    p = _params(ks, w)
+    if traj:
+        got, gtraj = ctx.seed_climb(v, p, seeds=seeds, want_traj=True)
+    else:
+        got = ctx.seed_climb(v, p, seeds=seeds)
+    ctx.release_volume(v)
+    b = ko.bin_volume(w.volume, w.binning)
+    sd = ko.seed_grid(w.dims, w.stride) if seeds is None else np.asarray(seeds, np.int32)
+    ref = ko.octant_climb(b, w.binning["bins"], w.r_min, w.r_max, sd, w.max_iter,
+                          want_traj=traj)
+    assert np.array_equal(np.stack([got["seed_x"], got["seed_y"], got["seed_z"]], 1), sd)
+    assert np.array_equal(np.stack([got["x"], got["y"], got["z"]], 1), ref["xyz"])
+    assert np.array_equal(got["iters"], ref["iters"])
+    assert np.array_equal(got["converged"], ref["converged"])
+    assert np.array_equal(got["s_best"], ref["s"])
+    if traj:
+        assert np.array_equal(gtraj, ref["traj"])
+    close(got["Y_best"], ref["Y"])
+    close(got["H_best"], ref["H"])
+    close(got["W_best"], ref["W"])
+    return got
+
+
+def _ms_vs_oracle(ctx, ko, ks, w, seeds=None):
+    v = ctx.create_volume(w.volume, w.binning)
+    p = _params(ks, w)
+    got = ctx.meanshift(v, p, seeds=seeds)
+    ctx.release_volume(v)
+    b = ko.bin_volume(w.volume, w.binning)
+    sd = ko.seed_grid(w.dims, w.stride) if seeds is None else np.asarray(seeds, np.int32)
+    ref = ko.meanshift(b, w.binning["bins"], w.r_min, w.r_max, sd, w.max_iter)
+    S = w.r_max - w.r_min + 1
+    assert np.array_equal(got["seed"], np.repeat(np.arange(len(sd)), S))
+    assert np.array_equal(got["r"], np.tile(np.arange(w.r_min, w.r_max + 1), len(sd)))
+    assert np.array_equal(np.stack([got["x"], got["y"], got["z"]], 1), ref["xyz"])
+    assert np.array_equal(got["iters"], ref["iters"])
+    assert np.array_equal(got["converged"], ref["converged"])
+    close(got["rho"], ref["rho"])
+    close(got["H"], ref["H"])
+    return got
+
+
+def test_octant_spheres48_all_seeds(ctx, ko, ks_mod):
+    _oct_vs_oracle(ctx, ko, ks_mod, synth.workload("spheres48"))
+
+
+def test_meanshift_spheres48_all_items(ctx, ko, ks_mod):
+    _ms_vs_oracle(ctx, ko, ks_mod, synth.workload("spheres48"))
+
+
+def test_octant_pet128_all_seeds(ctx, ko, ks_mod):
+    _oct_vs_oracle(ctx, ko, ks_mod, synth.workload("pet128"), traj=True)
+
+
+def test_meanshift_pet128_all_items(ctx, ko, ks_mod):
+    _ms_vs_oracle(ctx, ko, ks_mod, synth.workload("pet128"))
+
+
+def test_seeds_mr256_sampled(ctx, ko, ks_mod):
+    w = synth.workload("mr256")
+    grid = ko.seed_grid(w.dims, w.stride)
+    rng = np.random.default_rng(3)
+    pick = grid[rng.choice(len(grid), 48, replace=False)]
+    edge = np.array([[0, 0, 0], [255, 255, 159], [128, 0, 80]], np.int32)
+    seeds = np.concatenate([pick, edge]).astype(np.int32)
+    _oct_vs_oracle(ctx, ko, ks_mod, w, seeds=seeds, traj=True)
+    _ms_vs_oracle(ctx, ko, ks_mod, w, seeds=seeds[:20])
+
+
+def test_seed_edge_cases(ctx, ko, ks_mod):
+    ks = ks_mod
+    # constant volume: every seed converges at once; excluded voxels only: N = 0
+    vol = np.full((20, 21, 22), 77, np.uint8)
+    w = synth.Workload("const", vol, {"kind": 0, "bins": 16, "shift": 4, "lo": 0, "hi": 255},
+                       2, 6, 5, 20)
+    g = _oct_vs_oracle(ctx, ko, ks, w)
+    assert (g["iters"] == 1).all() and (g["s_best"] == 0).all()
+    _ms_vs_oracle(ctx, ko, ks, w)
+    w2 = synth.Workload("empty", vol, {"kind": 2, "bins": 8, "shift": 4, "lo": 200, "hi": 255},
+                        1, 4, 7, 3)
+    _oct_vs_oracle(ctx, ko, ks, w2)
+    _ms_vs_oracle(ctx, ko, ks, w2)
+    # max_iter = 0: no move, evaluation at the seed
+    w3 = synth.workload("spheres48")
+    w3.max_iter = 0
+    _oct_vs_oracle(ctx, ko, ks, w3)
+    _ms_vs_oracle(ctx, ko, ks, w3)
+
+
+# ---------------------------------------------------- batched and serving
+def test_batch_equals_plain_calls(ctx, ks_mod):
+    ks = ks_mod
+    ws = synth.batch_volumes(seed=5, count=6, hi=96)
+    vols = [ctx.create_volume(w.volume, w.binning) for w in ws]
+    ps = [_params(ks, w) for w in ws]
+    for use_graph in (1, 0, 1):
+        octs, mss = ctx.batch_seeds(vols, ps, kinds=3, use_graph=use_graph)
+        for v, p, o, m in zip(vols, ps, octs, mss):
+            assert np.array_equal(o, ctx.seed_climb(v, p))
+            assert np.array_equal(m, ctx.meanshift(v, p))
+    for v in vols:
+        ctx.release_volume(v)
+
+
+def test_serving_results_alone_equal_mixed(ks_mod):
+    ks = ks_mod
+    ws = synth.batch_volumes(seed=9, count=5, hi=80)
+    c1 = ks.Context()
+    alone = []
+    for i, w in enumerate(ws):
+        kind = ks.KS_REQ_DENSE if i % 3 == 2 else ks.KS_REQ_SEEDS
+        rid = c1.submit(w.volume, w.binning, _params(ks, w), kind=kind)
+        st, res = c1.poll(rid, -1)
+        assert st == ks.KS_OK
+        alone.append(res)
+    mixed_ids = []
+    for i, w in enumerate(ws):
+        kind = ks.KS_REQ_DENSE if i % 3 == 2 else ks.KS_REQ_SEEDS
+        mixed_ids.append(c1.submit(w.volume, w.binning, _params(ks, w), kind=kind))
+    for rid, a in zip(mixed_ids, alone):
+        st, res = c1.poll(rid, -1)
+        assert st == ks.KS_OK
+        for k in ("oct", "ms", "Y", "s"):
+            assert (k in a) == (k in res)
+            if k in a:
+                assert np.array_equal(a[k], res[k]), k
+    # the plain path gives the same numbers
+    v = c1.create_volume(ws[0].volume, ws[0].binning)
+    assert np.array_equal(alone[0]["oct"], c1.seed_climb(v, _params(ks, ws[0])))
+    c1.close()
+
+
+def test_errors_are_reported_not_raised_across_abi(ctx, ks_mod):
+    ks = ks_mod
+    w = synth.workload("spheres48")
+    with pytest.raises(ks.KsError) as e:
+        ctx.create_volume(w.volume, {"kind": 0, "bins": 16, "shift": 2, "lo": 0, "hi": 255})
+    assert e.value.status == ks.KS_EINVAL
+    v = ctx.create_volume(w.volume, w.binning)
+    with pytest.raises(ks.KsError) as e:
+        ctx.seed_climb(v, ks.make_params(5, 40, 6))
+    assert e.value.status == ks.KS_EINVAL
+    with pytest.raises(ks.KsError) as e:
+        ctx.seed_climb(v, ks.make_params(2, 10, 6), seeds=[[48, 0, 0]])
+    assert e.value.status == ks.KS_EINVAL
+    ctx.release_volume(v)
+    with pytest.raises(ks.KsError) as e:
+        ctx.seed_climb(v, ks.make_params(2, 10, 6))
+    assert e.value.status == ks.KS_ENOTFOUND
+    small = ks.Context(hbm_budget_bytes=64 << 20)
+    big = np.zeros((300, 300, 300), np.uint8)
+    with pytest.raises(ks.KsError) as e:
+        small.create_volume(big, w.binning)
+    assert e.value.status == ks.KS_ENOMEM
+    small.close()
