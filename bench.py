@@ -158,9 +158,11 @@ def run_reference(args):
     for _ in range(args.warmup if args.warmup < 1 else 1):
         oracle_sample(w, budget_s=2.0)
     vals = []
+    # keep the whole run to about two minutes of oracle work
+    budget = max(0.5, min(args.ref_budget, 120.0 / max(1, args.steps)))
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        v, threads, desc, dt = oracle_sample(w, budget_s=args.ref_budget)
+        v, threads, desc, dt = oracle_sample(w, budget_s=budget)
         vals.append(v)
     total = time.perf_counter() - t0
     value = statistics.median(vals)
@@ -284,7 +286,10 @@ def run_ks(args):
                        "volumes_per_s": ws / (ms_step * 1e-3),
                        "step_ms_p50": statistics.median(step_ms),
                        "step_ms_p99": float(np.percentile(step_ms, 99)),
-                       "parallelism": f"{ws} independent volume(s), one per GPU"},
+                       "parallelism": f"{ws} independent volume(s), one per GPU",
+                       "dense_launch": dict(zip(("path", "warps", "tile_y", "tile_z"),
+                                                ctx.dense_config(w.binning["bins"], w.r_max)
+                                                or (None,) * 4))},
             "roofline": {"bound": "smem", "achieved": achieved / 1e9,
                          "peak": smem_peak / 1e9, "unit": "Gupdates/s",
                          "frac": achieved / smem_peak, "traffic": None,
@@ -314,6 +319,43 @@ def run_ks(args):
     return 0
 
 
+def run_case(args):
+    """Run one part of the step (for profilers): --case dense|octant|meanshift|bin."""
+    import torch
+    from paper_1310_6736_b300 import build, ks, synth
+    build.build()
+    if args.dense_config:
+        ks.force_dense_config(*[int(x) for x in args.dense_config.split(",")])
+    w = synth.workload(WORKLOAD)
+    nz, ny, nx = w.volume.shape
+    params = ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter)
+    ctx = ks.Context()
+    raw_dev = torch.from_numpy(w.volume).cuda()
+    Y = torch.empty((nz, ny, nx), dtype=torch.float64, device="cuda")
+    sb = torch.empty((nz, ny, nx), dtype=torch.uint8, device="cuda")
+    v = ctx.create_volume(raw_dev, w.binning)
+    t = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if args.case == "dense":
+            ctx.dense_saliency(v, params, (nz, ny, nx), out=(Y, sb))
+        elif args.case == "octant":
+            ctx.seed_climb(v, params)
+        elif args.case == "meanshift":
+            ctx.meanshift(v, params)
+        elif args.case == "bin":
+            ctx.release_volume(v)
+            v = ctx.create_volume(raw_dev, w.binning)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            t.append(time.perf_counter() - t0)
+    print(json.dumps({"case": args.case, "workload": WORKLOAD, "ms": [1e3 * x for x in t],
+                      "dense_config": ctx.dense_config(w.binning["bins"], w.r_max)}), flush=True)
+    ctx.close()
+    return 0
+
+
 def ks_ball_size(r):
     d = np.arange(-r, r + 1)
     return int(((d[:, None, None] ** 2 + d[None, :, None] ** 2 + d[None, None, :] ** 2)
@@ -323,15 +365,21 @@ def ks_ball_size(r):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ks", choices=["ks", "reference"])
     ap.add_argument("--ref-budget", type=float, default=12.0,
                     help="seconds of oracle work per reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=["dense", "octant", "meanshift", "bin"],
+                    help="run one part of the step only (profiling)")
+    ap.add_argument("--dense-config", default="",
+                    help="force the dense launch shape: path,warps,tile_y,tile_z")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args)
     return run_ks(args)
 
 
