@@ -284,6 +284,32 @@ int ks_dense_config(ks_ctx *ctx, int bins, int r_max, int *path, int *warps,
  * that call. */
 int ks_force_dense_config(int path, int warps, int tile_y, int tile_z);
 
+/* ------------------------------------------------ allocation-free binning */
+
+/* The float32 binning of ks_create_volume (KS_BIN_AFFINE_F32) for callers
+ * that may not allocate device memory: code running under an allocator that
+ * owns all device memory, a loop that must not take the synchronisation a
+ * cudaMalloc/cudaFree can impose, or an application whose memory budget is
+ * already spent.  The paper has no counterpart; this is a library-interface
+ * convenience.
+ *   in     device pointer, nx*ny*nz float32 values, x-fastest
+ *   out    device pointer, nx*ny*nz bytes: the stored bin value b+1 of each
+ *          voxel, x-fastest, no halo (the layout of ks_volume_bins)
+ *   cuda_stream  cudaStream_t the two kernels are enqueued on (NULL = the
+ *          legacy default stream); the call returns without waiting.
+ * No cudaMalloc, cudaFree or other allocating call is made.  The reduction
+ * scratch is a 32 KB array compiled into the library (held on every device
+ * that loads it, until exit) and shared by all calls: calls whose kernels
+ * overlap on the GPU race on it, so serialise them (one stream, or events).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.
+ * Errors: KS_EINVAL for null pointers, dims < 1, bins outside [2, 64], or
+ * more than 2^30 voxels (the scratch holds 4096 partials of 2^18 voxels);
+ * KS_ECUDA for a launch failure. */
+int ks_bin_f32_noalloc(const float *in, int nx, int ny, int nz, int bins, uint8_t *out,
+                       void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -233,7 +233,7 @@ cudaError_t launch_bin_f32(const LaunchCtx &lc, const float *raw, int nx, int ny
     if (e != cudaSuccess) return e;
     const int64_t work = (int64_t)((nx + 15) / 16) * ny * nz;
     const int grid = grid_for(work, lc.num_sms);
-    const bool aligned = vec4 && nx % 16 == 0;
+    const bool aligned = vec4 && nx % 16 == 0 && (reinterpret_cast<uintptr_t>(base) & 15) == 0;
     k_bin_f32<<<grid, 256, 0, lc.stream>>>(raw, nx, ny, nz, pitch, plane, base, bins, scratch,
                                            scratch_blocks, aligned);
     return cudaGetLastError();

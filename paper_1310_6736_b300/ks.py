@@ -95,6 +95,7 @@ SIGNATURES = {
     "ks_dense_config": (_I, [_P, _I, _I, C.POINTER(C.c_int), C.POINTER(C.c_int),
                              C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ks_force_dense_config": (_I, [_I, _I, _I, _I]),
+    "ks_bin_f32_noalloc": (_I, [_P, _I, _I, _I, _I, _P, _P]),
 }
 
 _lib = None
