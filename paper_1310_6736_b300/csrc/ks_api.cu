@@ -179,72 +179,56 @@ static int build_ball_tables(Ctx *c) {
         for (auto &o : ball) n += o.rho <= r;
         c->h_ball_size[r] = n;
     }
-    struct Cn {
-        int dx, dy, dz, rho;
-        uint32_t mask;
-    };
-    std::vector<Cn> canon;
-    for (int dz = 0; dz <= kRmax; ++dz)
-        for (int dy = 0; dy <= kRmax; ++dy)
-            for (int dx = 0; dx <= kRmax; ++dx) {
-                const int d2 = dx * dx + dy * dy + dz * dz;
-                if (d2 > kRmax * kRmax) continue;
-                uint32_t mask = 0;
-                for (int s = 0; s < 8; ++s) {
-                    if ((s & 1) && dx == 0) continue;
-                    if ((s & 2) && dy == 0) continue;
-                    if ((s & 4) && dz == 0) continue;
-                    mask |= 1u << s;
-                }
-                canon.push_back({dx, dy, dz, rho_of(d2), mask});
-            }
-    std::stable_sort(canon.begin(), canon.end(), [](const Cn &a, const Cn &b) {
-        if (a.rho != b.rho) return a.rho < b.rho;
-        const bool fa = a.mask == 0xFFu, fb = b.mask == 0xFFu;
-        if (fa != fb) return fa;
-        if (a.dz != b.dz) return a.dz < b.dz;
-        if (a.dy != b.dy) return a.dy < b.dy;
-        return a.dx < b.dx;
-    });
-    std::vector<uint32_t> hc(canon.size());
-    int start[kRmax + 2], split[kRmax + 1];
-    size_t k = 0, expanded = 0;
+    // Dense-kernel table: per radius class, the three-nonzero offsets once
+    // per 8 sign mirrors (as |dx|, |dy|, |dz|), then every plane/axis offset.
+    std::vector<uint32_t> hd;
+    int start[kRmax + 2], rest[kRmax + 1];
+    size_t expanded = 0;
     for (int rho = 0; rho <= kRmax; ++rho) {
-        start[rho] = (int)k;
-        split[rho] = -1;
-        while (k < canon.size() && canon[k].rho == rho) {
-            if (split[rho] < 0 && canon[k].mask != 0xFFu) split[rho] = (int)k;
-            expanded += __builtin_popcount(canon[k].mask);
-            ++k;
-        }
-        if (split[rho] < 0) split[rho] = (int)k;
+        start[rho] = (int)hd.size();
+        for (int dz = 1; dz <= kRmax; ++dz)
+            for (int dy = 1; dy <= kRmax; ++dy)
+                for (int dx = 1; dx <= kRmax; ++dx) {
+                    const int d2 = dx * dx + dy * dy + dz * dz;
+                    if (d2 > kRmax * kRmax || rho_of(d2) != rho) continue;
+                    hd.push_back((uint32_t)dx | ((uint32_t)dy << 8) | ((uint32_t)dz << 16));
+                    expanded += 8;
+                }
+        rest[rho] = (int)hd.size();
+        for (auto &o : ball)
+            if (o.rho == rho && (o.dx == 0 || o.dy == 0 || o.dz == 0)) {
+                hd.push_back((uint32_t)(o.dx + 64) | ((uint32_t)(o.dy + 64) << 8) |
+                             ((uint32_t)(o.dz + 64) << 16));
+                expanded += 1;
+            }
     }
-    start[kRmax + 1] = (int)k;
+    start[kRmax + 1] = (int)hd.size();
     if (expanded != ball.size() || (int)ball.size() != kTableN)
         return set_err(c, KS_ECUDA, "internal: offset tables inconsistent");
-    for (size_t i = 0; i < canon.size(); ++i)
-        hc[i] = (uint32_t)canon[i].dx | ((uint32_t)canon[i].dy << 8) |
-                ((uint32_t)canon[i].dz << 16) | (canon[i].mask << 24);
 
     void *p;
-    c->canon_n = hc.size();
+    c->dtab_n = hd.size();
     KS_TRY_CUDA(c, dev_alloc(c, &p, hb.size() * 4));
     c->d_ball = (uint32_t *)p;
-    KS_TRY_CUDA(c, dev_alloc(c, &p, hc.size() * 4));
-    c->d_canon = (uint32_t *)p;
+    KS_TRY_CUDA(c, dev_alloc(c, &p, hd.size() * 4));
+    c->d_dtab = (uint32_t *)p;
     KS_TRY_CUDA(c, dev_alloc(c, &p, sizeof(start)));
-    c->d_canon_start = (int *)p;
-    KS_TRY_CUDA(c, dev_alloc(c, &p, sizeof(split)));
-    c->d_canon_split = (int *)p;
+    c->d_dtab_start = (int *)p;
+    KS_TRY_CUDA(c, dev_alloc(c, &p, sizeof(rest)));
+    c->d_dtab_rest = (int *)p;
     KS_TRY_CUDA(c, dev_alloc(c, &p, sizeof(c->h_ball_size)));
     c->d_ball_size = (int *)p;
     KS_TRY_CUDA(c, cudaMemcpy(c->d_ball, hb.data(), hb.size() * 4, cudaMemcpyHostToDevice));
-    KS_TRY_CUDA(c, cudaMemcpy(c->d_canon, hc.data(), hc.size() * 4, cudaMemcpyHostToDevice));
-    KS_TRY_CUDA(c, cudaMemcpy(c->d_canon_start, start, sizeof(start), cudaMemcpyHostToDevice));
-    KS_TRY_CUDA(c, cudaMemcpy(c->d_canon_split, split, sizeof(split), cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(c->d_dtab, hd.data(), hd.size() * 4, cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(c->d_dtab_start, start, sizeof(start), cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(c->d_dtab_rest, rest, sizeof(rest), cudaMemcpyHostToDevice));
     KS_TRY_CUDA(c, cudaMemcpy(c->d_ball_size, c->h_ball_size, sizeof(c->h_ball_size),
                               cudaMemcpyHostToDevice));
-    c->bt = BallTables{c->d_ball, c->d_canon, c->d_canon_start, c->d_canon_split, c->d_ball_size};
+    // the classes up to dense_const_rmax() also go to constant memory
+    KS_TRY_CUDA(c, dense_upload_constant_table(hd.data(), start[dense_const_rmax() + 1], start,
+                                               rest));
+    c->bt = BallTables{c->d_ball, c->d_ball_size};
+    c->dt = DenseTables{c->d_dtab, c->d_dtab_start, c->d_dtab_rest, c->d_ball_size};
     return KS_OK;
 }
 
@@ -387,7 +371,7 @@ static int launch_dense_cfg(Ctx *c, cudaStream_t s, Volume *v, int r_min, int r_
     }
     ProfRec rec;
     prof_begin(c, "ks_dense", s, &rec);
-    cudaError_t e = launch_dense(c->lc(s), v->desc, cfg.path == 0 ? &tm : nullptr, c->bt, c->T,
+    cudaError_t e = launch_dense(c->lc(s), v->desc, cfg.path == 0 ? &tm : nullptr, c->dt, c->T,
                                  c->L, r_min, r_max, w_norm, cfg, out, z0, z1);
     prof_end(c, &rec, s);
     return cuda_err(c, e, "dense launch");
@@ -576,9 +560,9 @@ int ks_destroy(ks_ctx *ctx) {
     dev_free(c, c->L, (kTableN + 1) * sizeof(double));
     dev_free(c, c->d_minmax, c->minmax_blocks * sizeof(float2));
     dev_free(c, c->d_ball, kTableN * 4);
-    dev_free(c, c->d_canon, c->canon_n * 4);
-    dev_free(c, c->d_canon_start, (kRmax + 2) * sizeof(int));
-    dev_free(c, c->d_canon_split, (kRmax + 1) * sizeof(int));
+    dev_free(c, c->d_dtab, c->dtab_n * 4);
+    dev_free(c, c->d_dtab_start, (kRmax + 2) * sizeof(int));
+    dev_free(c, c->d_dtab_rest, (kRmax + 1) * sizeof(int));
     dev_free(c, c->d_ball_size, (kRmax + 1) * sizeof(int));
     {
         std::lock_guard<std::mutex> g(g_graph_mu);

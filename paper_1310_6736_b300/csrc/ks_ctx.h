@@ -51,10 +51,11 @@ struct Ctx {
     int *d_status = nullptr;               // device status word
     double *T = nullptr, *L = nullptr;     // entropy tables
     // Ball(32) offset tables
-    uint32_t *d_ball = nullptr, *d_canon = nullptr;
-    int *d_canon_start = nullptr, *d_canon_split = nullptr, *d_ball_size = nullptr;
-    size_t canon_n = 0;
+    uint32_t *d_ball = nullptr, *d_dtab = nullptr;
+    int *d_dtab_start = nullptr, *d_dtab_rest = nullptr, *d_ball_size = nullptr;
+    size_t dtab_n = 0;
     BallTables bt{};
+    DenseTables dt{};
     int h_ball_size[kRmax + 1] = {};
     // f32-binning scratch: per-block min/max partials
     float2 *d_minmax = nullptr;

@@ -5,80 +5,111 @@
 // Work decomposition
 //   block  = a tile of 32 (x) * ty * tz centres; warp = one x-row of 32
 //            centres; lane = one centre with its own histogram.
-//   path 0 = the tile's brick (tile + r_max halo) is copied into shared
-//            memory by one TMA 3D tile load; path 1 = bins are read through
-//            L1/L2 straight from the halo-padded volume (large radii whose
-//            brick does not fit in shared memory).
-//   scale  = built incrementally: shell r (offsets with ceil|o| == r, and
+//   PATH 0 = the tile's brick (tile + r_max halo) is copied into shared
+//            memory by one TMA 3D tile load (out-of-range voxels arrive as
+//            0 = not counted); PATH 1 = bins are read through L1/L2 straight
+//            from the halo-padded volume.  The autotuner picks per shape.
+//   scale  = built incrementally: shell r (offsets o with ceil|o| == r, and
 //            everything up to r_min for the first scale) is added to the
-//            counts of r-1.  Offsets come from the "canonical" table: one
-//            entry per set of sign mirrors, expanded to up to 8 voxels with
-//            warp-uniform address arithmetic.
-//   counts = each lane owns a column of 32-bit words in shared memory,
-//            stride 32 words so that the 32 lanes always hit 32 different
-//            banks; words hold two 16-bit counters (stored values 2w and
-//            2w+1) while |Ball(r_max)| <= 65535, else one 32-bit counter.
-//            Stored value 0 (not counted) goes to a dummy counter, so the
-//            update has no branch.  Updates are shared-memory reductions
-//            (red.shared.add), which carry no register dependence.
-//   FP64   = after each shell, one pass over the lane's counters computes
-//            the bin-order entropy sum, the exact integer D of W, and
-//            copies the counts to the previous-scale column.  W and Y are
-//            only evaluated at entropy peaks.
+//            counts of r-1.
+//   offsets= one table per radius class rho: first the offsets with three
+//            nonzero components, stored once per set of 8 sign mirrors as
+//            (|dx|, |dy|, |dz|) and expanded with warp-uniform arithmetic,
+//            then every offset on a coordinate plane or axis, stored with
+//            its signs.  For r_max <= 25 the table sits in constant memory
+//            (warp-uniform reads through the constant cache), beyond that
+//            in global memory.
+//   counts = each lane owns a column of 32-bit words in shared memory
+//            (word v at +128 v bytes, so the 32 lanes of a warp always hit
+//            32 different banks), one word per stored value v = 0..B;
+//            v = 0 (not counted) is a dummy word, so the update has no
+//            branch: it is one shared-memory reduction (red.shared.add).
+//   FP64   = after each shell one pass over the lane's counters computes the
+//            bin-order entropy sum and the exact integer D of W against the
+//            previous scale's counts (a second column of the same layout,
+//            refreshed in the same pass).  W and Y are evaluated only at
+//            entropy peaks.
+#include <type_traits>
+
 #include "ks_internal.cuh"
 
 namespace ks {
 namespace {
 
 constexpr int kTmaPollLimit = 1 << 20;
+constexpr int kConstRmax = 25;            // largest r_max whose table fits
+constexpr int kConstEntries = 16000;
+
+// Offset table of radius classes 0..kConstRmax (see header comment).
+__constant__ uint32_t c_tab[kConstEntries];
+__constant__ int c_tab_start[kConstRmax + 2];    // first entry of class rho
+__constant__ int c_tab_rest[kConstRmax + 1];     // first plane/axis entry of rho
 
 struct DenseArgs {
     VolDesc vol;
-    BallTables bt;
+    const uint32_t *g_tab;       // global copy of the table (all classes <= 32)
+    const int *g_tab_start;      // [kRmax + 2]
+    const int *g_tab_rest;       // [kRmax + 1]
+    const int *ball_size;        // [kRmax + 1]
     const double *T;
     const double *L;
     int r_min, r_max, S, w_norm;
     int ty, tz;
-    int z0, z1;                // centres with z0 <= z < z1 (a slab of the volume)
-    int bx, by, padx;          // brick row length and rows per plane (path 0)
+    int z0, z1;                  // centres with z0 <= z < z1 (a slab of the volume)
+    int bx, by, padx;            // brick row length and rows per plane (path 0)
     uint32_t brick_bytes;
     uint32_t cnt_off, mbar_off;
     DenseOut out;
     int *status;
 };
 
-template <int B, bool WIDE>
-struct Counters {
-    static constexpr int kWords = WIDE ? B + 1 : B / 2 + 1;
-    __device__ static __forceinline__ uint32_t word_of(uint32_t v) { return WIDE ? v : v >> 1; }
-    __device__ static __forceinline__ uint32_t inc_of(uint32_t v) {
-        return WIDE ? 1u : 1u << ((v & 1u) << 4);
+template <bool CTAB>
+struct Tab {
+    const uint32_t *g;
+    const int *gs, *gr;
+    __device__ __forceinline__ uint32_t entry(int k) const {
+        if constexpr (CTAB) return c_tab[k]; else return __ldg(g + k);
+    }
+    __device__ __forceinline__ int start(int rho) const {
+        if constexpr (CTAB) return c_tab_start[rho]; else return __ldg(gs + rho);
+    }
+    __device__ __forceinline__ int rest(int rho) const {
+        if constexpr (CTAB) return c_tab_rest[rho]; else return __ldg(gr + rho);
     }
 };
 
-template <int B, bool WIDE>
-__device__ __forceinline__ void add_voxel(uint32_t cnt_lane, const uint8_t *p) {
-    const uint32_t v = *p;
-    red_add_shared(cnt_lane + (Counters<B, WIDE>::word_of(v) << 7), Counters<B, WIDE>::inc_of(v));
-}
+template <int PATH>
+struct Src;
+template <>
+struct Src<0> {              // brick in shared memory, byte offsets from smem
+    const uint8_t *smem;
+    __device__ __forceinline__ uint32_t at(int base, int off) const { return smem[base + off]; }
+};
+template <>
+struct Src<1> {              // halo-padded volume in global memory
+    const uint8_t *vol;
+    __device__ __forceinline__ uint32_t at(int64_t base, int off) const {
+        return __ldg(vol + (base + off));
+    }
+};
 
-template <int B, bool WIDE>
+template <int B, bool WIDE, int PATH>
 __global__ void __launch_bounds__(512) k_dense(const DenseArgs a,
-                                               const __grid_constant__ CUtensorMap tmap,
-                                               int path) {
+                                               const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ int s_ok;
-    using C = Counters<B, WIDE>;
-    constexpr int NW = C::kWords;
+    constexpr bool CTAB = !WIDE;                 // r_max <= 25: table in constant memory
+    constexpr int NW = B + 1;                    // counter words per lane
+    constexpr int NPREV = NW;                    // previous-scale words
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int tx0 = blockIdx.x * 32, ty0 = blockIdx.y * a.ty, tz0 = a.z0 + blockIdx.z * a.tz;
     const int R = a.r_max;
 
-    const uint8_t *src;
+    Src<PATH> src;
     int pz, py;
-    if (path == 0) {
+    if constexpr (PATH == 0) {
         const uint32_t mbar = smem_u32(smem + a.mbar_off);
         if (threadIdx.x == 0) {
             mbar_init(mbar, 1);
@@ -97,36 +128,36 @@ __global__ void __launch_bounds__(512) k_dense(const DenseArgs a,
         }
         __syncthreads();
         if (!s_ok) return;
-        src = smem;
+        src.smem = smem;
         pz = a.bx * a.by;
         py = a.bx;
     } else {
-        src = a.vol.base;
+        src.vol = a.vol.base;
         pz = (int)a.vol.plane;
         py = (int)a.vol.pitch;
     }
+    const Tab<CTAB> tab{a.g_tab, a.g_tab_start, a.g_tab_rest};
 
-    // Lane's counter column: cur words at +w*128, prev words at +(NW+w)*128.
-    const uint32_t cnt_lane = smem_u32(smem + a.cnt_off) + (warp * 2 * NW * 32 + lane) * 4;
+    // Lane's counter column: word v at +128 v; previous-scale words (WIDE)
+    // at +128 (NW + v).
+    const uint32_t cnt_lane = smem_u32(smem + a.cnt_off) + (warp * (NW + NPREV) * 32 + lane) * 4;
     const int nrows = a.ty * a.tz;
-    const int *__restrict__ cstart = a.bt.canon_start;
-    const int *__restrict__ csplit = a.bt.canon_split;
-    const uint32_t *__restrict__ canon = a.bt.canon;
 
     for (int row = warp; row < nrows; row += nwarps) {
         const int cy = ty0 + row % a.ty, cz = tz0 + row / a.ty;
         if (cy >= a.vol.ny || cz >= a.z1) continue;              // warp-uniform
         const int cx = tx0 + lane;
         const bool live = cx < a.vol.nx;
-        const uint8_t *c0;
-        if (path == 0)
-            c0 = src + (cz - tz0 + R) * pz + (cy - ty0 + R) * py + (a.padx + lane);
+        // lane's centre as an offset into the source
+        using Base = typename std::conditional<PATH == 0, int, int64_t>::type;
+        Base c0;
+        if constexpr (PATH == 0)
+            c0 = (cz - tz0 + R) * pz + (cy - ty0 + R) * py + (a.padx + lane);
         else
-            c0 = src + (int64_t)cz * a.vol.plane + (int64_t)cy * a.vol.pitch +
-                 (live ? cx : a.vol.nx - 1);
+            c0 = (int64_t)cz * a.vol.plane + (int64_t)cy * a.vol.pitch + (live ? cx : a.vol.nx - 1);
 
 #pragma unroll 4
-        for (int w = 0; w < 2 * NW; ++w) st_shared_u32(cnt_lane + (w << 7), 0u);
+        for (int w = 0; w < NW + NPREV; ++w) st_shared_u32(cnt_lane + (w << 7), 0u);
 
         double hm1 = 0.0, hm2 = 0.0;      // H at scale index i-1, i-2
         uint32_t nm1 = 0, nm2 = 0;        // N at i-1, i-2
@@ -138,63 +169,53 @@ __global__ void __launch_bounds__(512) k_dense(const DenseArgs a,
         for (int i = 0; i < a.S; ++i) {
             const int r = a.r_min + i;
             for (int rho = (i == 0 ? 0 : r); rho <= r; ++rho) {
-                const int k0 = __ldg(cstart + rho), k1 = __ldg(csplit + rho),
-                          k2 = __ldg(cstart + rho + 1);
-                // entries whose 8 sign mirrors are all distinct
+                const int k0 = tab.start(rho), k1 = tab.rest(rho), k2 = tab.start(rho + 1);
+                // three nonzero components: 8 sign mirrors
+                uint32_t e = k0 < k1 ? tab.entry(k0) : 0u;
                 for (int k = k0; k < k1; ++k) {
-                    const uint32_t e = __ldg(canon + k);
+                    const uint32_t en = k + 1 < k1 ? tab.entry(k + 1) : 0u;   // prefetch
                     const int X = (int)(e & 0xffu);
                     const int Y = (int)((e >> 8) & 0xffu) * py;
                     const int Z = (int)((e >> 16) & 0xffu) * pz;
-                    const int zy0 = Z + Y, zy1 = Z - Y, zy2 = Y - Z, zy3 = -Z - Y;
-                    add_voxel<B, WIDE>(cnt_lane, c0 + zy0 + X);
-                    add_voxel<B, WIDE>(cnt_lane, c0 + zy0 - X);
-                    add_voxel<B, WIDE>(cnt_lane, c0 + zy1 + X);
-                    add_voxel<B, WIDE>(cnt_lane, c0 + zy1 - X);
-                    add_voxel<B, WIDE>(cnt_lane, c0 + zy2 + X);
-                    add_voxel<B, WIDE>(cnt_lane, c0 + zy2 - X);
-                    add_voxel<B, WIDE>(cnt_lane, c0 + zy3 + X);
-                    add_voxel<B, WIDE>(cnt_lane, c0 + zy3 - X);
+                    const int o0 = Z + Y, o1 = Z - Y, o2 = Y - Z, o3 = -Z - Y;
+                    const uint32_t v0 = src.at(c0, o0 + X), v1 = src.at(c0, o0 - X);
+                    const uint32_t v2 = src.at(c0, o1 + X), v3 = src.at(c0, o1 - X);
+                    const uint32_t v4 = src.at(c0, o2 + X), v5 = src.at(c0, o2 - X);
+                    const uint32_t v6 = src.at(c0, o3 + X), v7 = src.at(c0, o3 - X);
+                    red_add_shared(cnt_lane + (v0 << 7), 1u);
+                    red_add_shared(cnt_lane + (v1 << 7), 1u);
+                    red_add_shared(cnt_lane + (v2 << 7), 1u);
+                    red_add_shared(cnt_lane + (v3 << 7), 1u);
+                    red_add_shared(cnt_lane + (v4 << 7), 1u);
+                    red_add_shared(cnt_lane + (v5 << 7), 1u);
+                    red_add_shared(cnt_lane + (v6 << 7), 1u);
+                    red_add_shared(cnt_lane + (v7 << 7), 1u);
+                    e = en;
                 }
-                // entries on a coordinate plane or axis: distinct mirrors only
+                // offsets on a coordinate plane or axis, one entry each
                 for (int k = k1; k < k2; ++k) {
-                    const uint32_t e = __ldg(canon + k);
-                    const int X = (int)(e & 0xffu);
-                    const int Y = (int)((e >> 8) & 0xffu) * py;
-                    const int Z = (int)((e >> 16) & 0xffu) * pz;
-                    const uint32_t mask = e >> 24;
-#pragma unroll
-                    for (int s = 0; s < 8; ++s)
-                        if (mask & (1u << s))
-                            add_voxel<B, WIDE>(cnt_lane, c0 + ((s & 4) ? -Z : Z) +
-                                                             ((s & 2) ? -Y : Y) +
-                                                             ((s & 1) ? -X : X));
+                    const uint32_t f = tab.entry(k);
+                    const int off = ((int)((f >> 16) & 0xffu) - 64) * pz +
+                                    ((int)((f >> 8) & 0xffu) - 64) * py + ((int)(f & 0xffu) - 64);
+                    red_add_shared(cnt_lane + (src.at(c0, off) << 7), 1u);
                 }
             }
 
             // ---- exact per-scale quantities from the lane's counters
-            const uint32_t w0 = ld_shared_u32(cnt_lane);
-            const uint32_t zero_cnt = WIDE ? w0 : (w0 & 0xffffu);
-            const uint32_t N = (uint32_t)__ldg(a.bt.ball_size + r) - zero_cnt;
+            const uint32_t zero_cnt = ld_shared_u32(cnt_lane);
+            const uint32_t N = (uint32_t)__ldg(a.ball_size + r) - zero_cnt;
             double ssum = 0.0;
             int occ = 0;
             uint64_t D = 0;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                const uint32_t cw = ld_shared_u32(cnt_lane + (w << 7));
-                const uint32_t pw = ld_shared_u32(cnt_lane + ((NW + w) << 7));
-                st_shared_u32(cnt_lane + ((NW + w) << 7), cw);
-#pragma unroll
-                for (int h = 0; h < (WIDE ? 1 : 2); ++h) {
-                    const int v = WIDE ? w : 2 * w + h;
-                    if (v < 1 || v > B) continue;                 // compile-time
-                    const uint32_t c = WIDE ? cw : ((cw >> (16 * h)) & 0xffffu);
-                    const uint32_t p = WIDE ? pw : ((pw >> (16 * h)) & 0xffffu);
-                    occ += c > 0u;
-                    if (c > 1u) ssum = __dadd_rn(ssum, __ldg(a.T + c));
-                    const int64_t d = (int64_t)c * nm1 - (int64_t)p * N;
-                    D += (uint64_t)(d < 0 ? -d : d);
-                }
+            for (int v = 1; v <= B; ++v) {
+                const uint32_t c = ld_shared_u32(cnt_lane + (v << 7));
+                const uint32_t p = ld_shared_u32(cnt_lane + ((NW + v) << 7));
+                st_shared_u32(cnt_lane + ((NW + v) << 7), c);
+                occ += c > 0u;
+                if (c > 1u) ssum = __dadd_rn(ssum, __ldg(a.T + c));
+                const int64_t d = (int64_t)c * nm1 - (int64_t)p * N;
+                D += (uint64_t)(d < 0 ? -d : d);
             }
             const double H = entropy_from_sum(ssum, N, occ, a.L);
 
@@ -222,43 +243,55 @@ __global__ void __launch_bounds__(512) k_dense(const DenseArgs a,
     }
 }
 
+int template_bins(int B) {
+    return B <= 2 ? 2 : B <= 4 ? 4 : B <= 8 ? 8 : B <= 16 ? 16 : B <= 32 ? 32 : 64;
+}
+
+bool is_wide(int r_max) { return r_max > kConstRmax; }
+
 struct Geometry {
     int padx, bx, by, bz;
     size_t brick, cnt_off, cnt_bytes, mbar_off, total;
 };
 
-int template_bins(int B) {
-    return B <= 2 ? 2 : B <= 4 ? 4 : B <= 8 ? 8 : B <= 16 ? 16 : B <= 32 ? 32 : 64;
-}
-
 Geometry geometry(const DenseConfig &c, int B_, int r_max) {
     Geometry g{};
     const int B = template_bins(B_);
-    const bool wide = ball_size_host(r_max) > 65535;
-    const int words = wide ? B + 1 : B / 2 + 1;
+    const int words = (B + 1) * 2;          // counts + previous-scale counts
     g.padx = (r_max + 15) / 16 * 16;
     g.bx = (g.padx + 32 + r_max + 15) / 16 * 16;
     g.by = c.ty + 2 * r_max;
     g.bz = c.tz + 2 * r_max;
     g.brick = c.path == 0 ? (size_t)g.bx * g.by * g.bz : 0;
     g.cnt_off = (g.brick + 127) / 128 * 128;
-    g.cnt_bytes = (size_t)c.warps * 2 * words * 32 * 4;
+    g.cnt_bytes = (size_t)c.warps * words * 32 * 4;
     g.mbar_off = g.cnt_off + g.cnt_bytes;
     g.total = g.mbar_off + 16;
     return g;
 }
 
-template <int B, bool WIDE>
+template <int B, bool WIDE, int PATH>
 cudaError_t launch_t(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap *tmap,
                      const DenseConfig &cfg, size_t smem) {
-    auto kern = k_dense<B, WIDE>;
+    auto kern = k_dense<B, WIDE, PATH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.vol.nx + 31) / 32, (a.vol.ny + a.ty - 1) / a.ty, (a.z1 - a.z0 + a.tz - 1) / a.tz);
     CUtensorMap dummy{};
-    kern<<<grid, cfg.warps * 32, smem, lc.stream>>>(a, tmap ? *tmap : dummy, cfg.path);
+    kern<<<grid, cfg.warps * 32, smem, lc.stream>>>(a, tmap ? *tmap : dummy);
     return cudaGetLastError();
+}
+
+template <int B>
+cudaError_t launch_b(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap *tmap,
+                     const DenseConfig &cfg, size_t smem) {
+    const bool wide = is_wide(a.r_max);
+    if (cfg.path == 0)
+        return wide ? launch_t<B, true, 0>(lc, a, tmap, cfg, smem)
+                    : launch_t<B, false, 0>(lc, a, tmap, cfg, smem);
+    return wide ? launch_t<B, true, 1>(lc, a, tmap, cfg, smem)
+                : launch_t<B, false, 1>(lc, a, tmap, cfg, smem);
 }
 
 }  // namespace
@@ -272,6 +305,17 @@ int ball_size_host(int r) {
     return n;
 }
 
+cudaError_t dense_upload_constant_table(const uint32_t *tab, int n_const, const int *start,
+                                        const int *rest) {
+    if (n_const > kConstEntries) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyToSymbol(c_tab, tab, n_const * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tab_start, start, (kConstRmax + 2) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tab_rest, rest, (kConstRmax + 1) * sizeof(int));
+    return e;
+}
+
+int dense_const_rmax() { return kConstRmax; }
+
 size_t dense_smem_bytes(const DenseConfig &c, int B, int r_max) {
     return geometry(c, B, r_max).total;
 }
@@ -284,13 +328,16 @@ bool dense_config_fits(const DenseConfig &c, int B, int r_max) {
 }
 
 cudaError_t launch_dense(const LaunchCtx &lc, const VolDesc &v, const CUtensorMap *tmap,
-                         const BallTables &bt, const double *T, const double *L, int r_min,
+                         const DenseTables &dt, const double *T, const double *L, int r_min,
                          int r_max, int w_norm, const DenseConfig &cfg, const DenseOut &out,
                          int z0, int z1) {
     const Geometry g = geometry(cfg, v.B, r_max);
     DenseArgs a{};
     a.vol = v;
-    a.bt = bt;
+    a.g_tab = dt.tab;
+    a.g_tab_start = dt.start;
+    a.g_tab_rest = dt.rest;
+    a.ball_size = dt.ball_size;
     a.T = T;
     a.L = L;
     a.r_min = r_min;
@@ -309,25 +356,18 @@ cudaError_t launch_dense(const LaunchCtx &lc, const VolDesc &v, const CUtensorMa
     a.mbar_off = (uint32_t)g.mbar_off;
     a.out = out;
     a.status = lc.d_status;
-    const bool wide = ball_size_host(r_max) > 65535;
     const CUtensorMap *tm = cfg.path == 0 ? tmap : nullptr;
     // Counter columns are sized for the next supported bin count; the extra
     // stored values never occur, so their counters stay 0 and add nothing
     // to the entropy sum or to D.
     switch (template_bins(v.B)) {
-#define KS_CASE(BB)                                                                 \
-    case BB:                                                                        \
-        return wide ? launch_t<BB, true>(lc, a, tm, cfg, g.total)                   \
-                    : launch_t<BB, false>(lc, a, tm, cfg, g.total);
-        KS_CASE(2)
-        KS_CASE(4)
-        KS_CASE(8)
-        KS_CASE(16)
-        KS_CASE(32)
-        KS_CASE(64)
-#undef KS_CASE
-        default:
-            return cudaErrorInvalidValue;
+        case 2: return launch_b<2>(lc, a, tm, cfg, g.total);
+        case 4: return launch_b<4>(lc, a, tm, cfg, g.total);
+        case 8: return launch_b<8>(lc, a, tm, cfg, g.total);
+        case 16: return launch_b<16>(lc, a, tm, cfg, g.total);
+        case 32: return launch_b<32>(lc, a, tm, cfg, g.total);
+        case 64: return launch_b<64>(lc, a, tm, cfg, g.total);
+        default: return cudaErrorInvalidValue;
     }
 }
 

@@ -34,22 +34,13 @@ struct VolDesc {
     int64_t pitch, plane;
 };
 
-// Offsets of Ball(32) used by the kernels (built once per context).
-//  ball:   every offset o with |o| <= 32, sorted by its radius class
-//          rho(o) = ceil(|o|) (the smallest r with |o|^2 <= r^2), then by
-//          dz, dy, dx; packed (dx+64) | (dy+64) << 8 | (dz+64) << 16 |
-//          rho << 24.  Ball(r) is the prefix of length ball_size[r].
-//  canon:  offsets with dx, dy, dz >= 0 (one per set of sign mirrors),
-//          sorted by rho, then "all three nonzero" entries first; packed
-//          dx | dy << 8 | dz << 16 | mirror_mask << 24 where bit s of the
-//          mask marks the distinct sign pattern s (bit0: -x, bit1: -y,
-//          bit2: -z).  canon_start[rho] .. canon_start[rho+1] is class rho,
-//          and canon_split[rho] the first entry whose mask is not 0xFF.
+// Offsets of Ball(32) used by the seed kernels (built once per context):
+// every offset o with |o| <= 32, sorted by its radius class rho(o) =
+// ceil(|o|) (the smallest r with |o|^2 <= r^2), then by dz, dy, dx; packed
+// (dx+64) | (dy+64) << 8 | (dz+64) << 16 | rho << 24.  Ball(r) is the
+// prefix of length ball_size[r].
 struct BallTables {
     const uint32_t *ball;
-    const uint32_t *canon;
-    const int *canon_start;   // [kRmax + 2]
-    const int *canon_split;   // [kRmax + 1]
     const int *ball_size;     // [kRmax + 1]
 };
 
@@ -166,10 +157,25 @@ struct DenseOut {
     double *H;     // optional, voxel-major x S
     double *W;     // optional
 };
+// Offset table of the dense kernel: for each radius class rho, entries
+// [start[rho], rest[rho]) are offsets with three nonzero components stored
+// once per set of 8 sign mirrors, packed |dx| | |dy| << 8 | |dz| << 16, and
+// [rest[rho], start[rho+1]) are the offsets on a coordinate plane or axis,
+// packed (dx+64) | (dy+64) << 8 | (dz+64) << 16.
+struct DenseTables {
+    const uint32_t *tab;
+    const int *start;       // [kRmax + 2]
+    const int *rest;        // [kRmax + 1]
+    const int *ball_size;   // [kRmax + 1]
+};
+// The classes rho <= dense_const_rmax() also live in constant memory.
+cudaError_t dense_upload_constant_table(const uint32_t *tab, int n_const, const int *start,
+                                        const int *rest);
+int dense_const_rmax();
 bool dense_config_fits(const DenseConfig &c, int B, int r_max);
 size_t dense_smem_bytes(const DenseConfig &c, int B, int r_max);
 cudaError_t launch_dense(const LaunchCtx &lc, const VolDesc &v, const CUtensorMap *tmap,
-                         const BallTables &bt, const double *T, const double *L, int r_min,
+                         const DenseTables &dt, const double *T, const double *L, int r_min,
                          int r_max, int w_norm, const DenseConfig &cfg, const DenseOut &out,
                          int z0, int z1);
 
