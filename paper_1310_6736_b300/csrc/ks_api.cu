@@ -170,67 +170,57 @@ static int build_ball_tables(Ctx *c) {
         if (a.dy != b.dy) return a.dy < b.dy;
         return a.dx < b.dx;
     });
-    std::vector<uint32_t> hb(ball.size());
-    for (size_t i = 0; i < ball.size(); ++i)
-        hb[i] = (uint32_t)(ball[i].dx + 64) | ((uint32_t)(ball[i].dy + 64) << 8) |
-                ((uint32_t)(ball[i].dz + 64) << 16) | ((uint32_t)ball[i].rho << 24);
     for (int r = 0; r <= kRmax; ++r) {
         int n = 0;
         for (auto &o : ball) n += o.rho <= r;
         c->h_ball_size[r] = n;
     }
-    // Dense-kernel table: per radius class, the three-nonzero offsets once
-    // per 8 sign mirrors (as |dx|, |dy|, |dz|), then every plane/axis offset.
-    std::vector<uint32_t> hd;
-    int start[kRmax + 2], rest[kRmax + 1];
-    size_t expanded = 0;
+    // Offset tables (see OffsetTables): three-nonzero offsets once per 8 sign
+    // mirrors, then the plane/axis offsets, each part sorted by rho.
+    std::vector<uint32_t> h8, hr;
+    int s8[kRmax + 2], sr[kRmax + 2];
     for (int rho = 0; rho <= kRmax; ++rho) {
-        start[rho] = (int)hd.size();
-        for (int dz = 1; dz <= kRmax; ++dz)
-            for (int dy = 1; dy <= kRmax; ++dy)
-                for (int dx = 1; dx <= kRmax; ++dx) {
-                    const int d2 = dx * dx + dy * dy + dz * dz;
-                    if (d2 > kRmax * kRmax || rho_of(d2) != rho) continue;
-                    hd.push_back((uint32_t)dx | ((uint32_t)dy << 8) | ((uint32_t)dz << 16));
-                    expanded += 8;
-                }
-        rest[rho] = (int)hd.size();
-        for (auto &o : ball)
-            if (o.rho == rho && (o.dx == 0 || o.dy == 0 || o.dz == 0)) {
-                hd.push_back((uint32_t)(o.dx + 64) | ((uint32_t)(o.dy + 64) << 8) |
-                             ((uint32_t)(o.dz + 64) << 16));
-                expanded += 1;
-            }
+        s8[rho] = (int)h8.size();
+        sr[rho] = (int)hr.size();
+        for (auto &o : ball) {
+            if (o.rho != rho) continue;
+            if (o.dx > 0 && o.dy > 0 && o.dz > 0)
+                h8.push_back((uint32_t)o.dx | ((uint32_t)o.dy << 8) | ((uint32_t)o.dz << 16) |
+                             ((uint32_t)rho << 24));
+            else if (o.dx == 0 || o.dy == 0 || o.dz == 0)
+                hr.push_back((uint32_t)(o.dx + 64) | ((uint32_t)(o.dy + 64) << 8) |
+                             ((uint32_t)(o.dz + 64) << 16) | ((uint32_t)rho << 24));
+        }
     }
-    start[kRmax + 1] = (int)hd.size();
-    if (expanded != ball.size() || (int)ball.size() != kTableN)
-        return set_err(c, KS_ECUDA, "internal: offset tables inconsistent");
-
+    s8[kRmax + 1] = (int)h8.size();
+    sr[kRmax + 1] = (int)hr.size();
+    for (int r = 0; r <= kRmax; ++r)
+        if (8 * s8[r + 1] + sr[r + 1] != c->h_ball_size[r])
+            return set_err(c, KS_ECUDA, "internal: offset tables inconsistent");
+    if ((int)ball.size() != kTableN) return set_err(c, KS_ECUDA, "internal: ball size");
+    // one allocation: c8 | rest | c8_start | rest_start | ball_size
+    const size_t b8 = h8.size() * 4, br = hr.size() * 4, bs = sizeof(s8);
+    const size_t at_r = (b8 + 255) / 256 * 256, at_s8 = at_r + (br + 255) / 256 * 256;
+    const size_t at_sr = at_s8 + 256, at_bs = at_sr + 256;
+    c->offsets_bytes = at_bs + 256;
     void *p;
-    c->dtab_n = hd.size();
-    KS_TRY_CUDA(c, dev_alloc(c, &p, hb.size() * 4));
-    c->d_ball = (uint32_t *)p;
-    KS_TRY_CUDA(c, dev_alloc(c, &p, hd.size() * 4));
-    c->d_dtab = (uint32_t *)p;
-    KS_TRY_CUDA(c, dev_alloc(c, &p, sizeof(start)));
-    c->d_dtab_start = (int *)p;
-    KS_TRY_CUDA(c, dev_alloc(c, &p, sizeof(rest)));
-    c->d_dtab_rest = (int *)p;
-    KS_TRY_CUDA(c, dev_alloc(c, &p, sizeof(c->h_ball_size)));
-    c->d_ball_size = (int *)p;
-    KS_TRY_CUDA(c, cudaMemcpy(c->d_ball, hb.data(), hb.size() * 4, cudaMemcpyHostToDevice));
-    KS_TRY_CUDA(c, cudaMemcpy(c->d_dtab, hd.data(), hd.size() * 4, cudaMemcpyHostToDevice));
-    KS_TRY_CUDA(c, cudaMemcpy(c->d_dtab_start, start, sizeof(start), cudaMemcpyHostToDevice));
-    KS_TRY_CUDA(c, cudaMemcpy(c->d_dtab_rest, rest, sizeof(rest), cudaMemcpyHostToDevice));
-    KS_TRY_CUDA(c, cudaMemcpy(c->d_ball_size, c->h_ball_size, sizeof(c->h_ball_size),
+    KS_TRY_CUDA(c, dev_alloc(c, &p, c->offsets_bytes));
+    c->d_offsets = p;
+    uint8_t *m = (uint8_t *)p;
+    KS_TRY_CUDA(c, cudaMemcpy(m, h8.data(), b8, cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(m + at_r, hr.data(), br, cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(m + at_s8, s8, bs, cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(m + at_sr, sr, bs, cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(m + at_bs, c->h_ball_size, sizeof(c->h_ball_size),
                               cudaMemcpyHostToDevice));
+    c->ot = OffsetTables{(const uint32_t *)m, (const int *)(m + at_s8),
+                         (const uint32_t *)(m + at_r), (const int *)(m + at_sr),
+                         (const int *)(m + at_bs)};
     // the classes up to dense_const_rmax() also go to constant memory
-    KS_TRY_CUDA(c, dense_upload_constant_table(hd.data(), start[dense_const_rmax() + 1], start,
-                                               rest));
-    c->bt = BallTables{c->d_ball, c->d_ball_size};
-    c->dt = DenseTables{c->d_dtab, c->d_dtab_start, c->d_dtab_rest, c->d_ball_size};
+    KS_TRY_CUDA(c, dense_upload_constant_table(h8.data(), s8, hr.data(), sr));
     return KS_OK;
 }
+
 
 // ----------------------------------------------------------------- volumes
 size_t volume_bytes(int nx, int ny, int nz) {
@@ -371,7 +361,7 @@ static int launch_dense_cfg(Ctx *c, cudaStream_t s, Volume *v, int r_min, int r_
     }
     ProfRec rec;
     prof_begin(c, "ks_dense", s, &rec);
-    cudaError_t e = launch_dense(c->lc(s), v->desc, cfg.path == 0 ? &tm : nullptr, c->dt, c->T,
+    cudaError_t e = launch_dense(c->lc(s), v->desc, cfg.path == 0 ? &tm : nullptr, c->ot, c->T,
                                  c->L, r_min, r_max, w_norm, cfg, out, z0, z1);
     prof_end(c, &rec, s);
     return cuda_err(c, e, "dense launch");
@@ -559,11 +549,7 @@ int ks_destroy(ks_ctx *ctx) {
     dev_free(c, c->T, (kTableN + 1) * sizeof(double));
     dev_free(c, c->L, (kTableN + 1) * sizeof(double));
     dev_free(c, c->d_minmax, c->minmax_blocks * sizeof(float2));
-    dev_free(c, c->d_ball, kTableN * 4);
-    dev_free(c, c->d_dtab, c->dtab_n * 4);
-    dev_free(c, c->d_dtab_start, (kRmax + 2) * sizeof(int));
-    dev_free(c, c->d_dtab_rest, (kRmax + 1) * sizeof(int));
-    dev_free(c, c->d_ball_size, (kRmax + 1) * sizeof(int));
+    dev_free(c, c->d_offsets, c->offsets_bytes);
     {
         std::lock_guard<std::mutex> g(g_graph_mu);
         auto it = g_graphs.find(c);
@@ -740,18 +726,18 @@ static int upload_queue(Ctx *c, const std::vector<SeedJob> &jobs, const std::vec
     q->seg_kind = (const int *)put(sk.data(), bk);
     q->seg_job = (const int *)put(sj.data(), bjj);
     q->n_segs = (int)sk.size();
-    q->n_items = ss.back();
+    q->n_tickets = ss.back();
     q->head = (unsigned long long *)c->batch_mem;
     KS_TRY_CUDA(c, cudaMemcpyAsync(c->batch_mem, h.data(), off, cudaMemcpyHostToDevice, c->stream));
     return KS_OK;
 }
 
 static int run_queue(Ctx *c, const SeedQueue &q, int max_B, int max_S, bool persistent) {
-    if (q.n_items == 0) return KS_OK;
-    const int grid = persistent ? c->num_sms * seed_blocks_per_sm(max_B, max_S) : (int)q.n_items;
+    if (q.n_tickets == 0) return KS_OK;
+    const int grid = persistent ? c->num_sms * seed_blocks_per_sm(max_B, max_S) : (int)q.n_tickets;
     ProfRec rec;
     prof_begin(c, persistent ? "ks_seeds_persistent" : "ks_seeds", c->stream, &rec);
-    cudaError_t e = launch_seeds(c->lc(), q, c->bt, c->T, c->L, max_B, max_S, persistent, grid);
+    cudaError_t e = launch_seeds(c->lc(), q, c->ot, c->T, c->L, max_B, max_S, persistent, grid);
     prof_end(c, &rec, c->stream);
     return cuda_err(c, e, "seed launch");
 }
@@ -797,7 +783,7 @@ static int seed_common(Ctx *c, ks_vol vol, const ks_params *p, const int32_t *se
     J.ms_out = kind == kMeanShift ? (ks_ms_result *)dout : nullptr;
     J.traj = kind == kOctant ? dtraj : nullptr;
     SeedQueue q{};
-    st = upload_queue(c, {J}, {0, n_items}, {kind}, {0}, &q);
+    st = upload_queue(c, {J}, {0, seed_tickets(kind, ns, S)}, {kind}, {0}, &q);
     if (st) return st;
     st = run_queue(c, q, v->binning.bins, S, false);
     if (st) return st;
@@ -917,7 +903,8 @@ int ks_batch_seeds(ks_ctx *ctx, const ks_vol *vols, const ks_params *params, int
             for (int i = 0; i < n_vols; ++i) {
                 const int64_t n = kind == 0 ? nb->n_oct[i] : nb->n_ms[i];
                 if (!n) continue;
-                ss.push_back(ss.back() + n);
+                ss.push_back(ss.back() + seed_tickets(kind == 0 ? kOctant : kMeanShift,
+                                                      jobs[i].n_seeds, jobs[i].S));
                 sk.push_back(kind == 0 ? kOctant : kMeanShift);
                 sj.push_back(i);
             }
@@ -934,7 +921,7 @@ int ks_batch_seeds(ks_ctx *ctx, const ks_vol *vols, const ks_params *params, int
         std::memcpy(host.data() + o, sj.data(), sj.size() * 4);
         q.seg_job = (const int *)(m + o);
         q.n_segs = (int)sk.size();
-        q.n_items = ss.back();
+        q.n_tickets = ss.back();
         q.head = (unsigned long long *)(m + nb->bytes - 256);
         KS_TRY_CUDA(c, cudaMemcpyAsync(m, host.data(), host.size(), cudaMemcpyHostToDevice,
                                        c->stream));
@@ -944,7 +931,7 @@ int ks_batch_seeds(ks_ctx *ctx, const ks_vol *vols, const ks_params *params, int
         cudaGraph_t graph;
         KS_TRY_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         cudaMemsetAsync(q.head, 0, 8, c->stream);
-        cudaError_t le = launch_seeds(c->lc(), q, c->bt, c->T, c->L, nb->max_B, nb->max_S, true, grid);
+        cudaError_t le = launch_seeds(c->lc(), q, c->ot, c->T, c->L, nb->max_B, nb->max_S, true, grid);
         e = cudaStreamEndCapture(c->stream, &graph);
         if (le != cudaSuccess) e = le;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&nb->exec, graph, 0);
@@ -965,7 +952,7 @@ int ks_batch_seeds(ks_ctx *ctx, const ks_vol *vols, const ks_params *params, int
         KS_TRY_CUDA(c, cudaGraphLaunch(bg->exec, c->stream));
     } else {
         KS_TRY_CUDA(c, cudaMemsetAsync(bg->q.head, 0, 8, c->stream));
-        KS_TRY_CUDA(c, launch_seeds(c->lc(), bg->q, c->bt, c->T, c->L, bg->max_B, bg->max_S, true,
+        KS_TRY_CUDA(c, launch_seeds(c->lc(), bg->q, c->ot, c->T, c->L, bg->max_B, bg->max_S, true,
                                     bg->grid));
     }
     prof_end(c, &rec, c->stream);
@@ -1034,7 +1021,7 @@ int ks_measure_smem_peak(ks_ctx *ctx, double *per_s) {
     cudaError_t e;
     uint32_t *sink = (uint32_t *)scratch(c, kScTune, 4096 * 4, &e);
     if (!sink) return cuda_err(c, e, "smem peak");
-    const int blocks = c->num_sms * 4, iters = 4096;
+    const int blocks = c->num_sms * 6, iters = 4096;    // 6 blocks of 8 warps per SM
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
@@ -1053,7 +1040,7 @@ int ks_measure_smem_peak(ks_ctx *ctx, double *per_s) {
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (e != cudaSuccess) return cuda_err(c, e, "smem peak");
-    *per_s = (double)blocks * 512.0 * iters * 16.0 / (best * 1e-3);
+    *per_s = (double)blocks * 256.0 * iters * 16.0 / (best * 1e-3);
     return KS_OK;
 }
 

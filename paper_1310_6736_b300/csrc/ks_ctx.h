@@ -50,12 +50,11 @@ struct Ctx {
     std::atomic<size_t> used{0};
     int *d_status = nullptr;               // device status word
     double *T = nullptr, *L = nullptr;     // entropy tables
-    // Ball(32) offset tables
-    uint32_t *d_ball = nullptr, *d_dtab = nullptr;
-    int *d_dtab_start = nullptr, *d_dtab_rest = nullptr, *d_ball_size = nullptr;
-    size_t dtab_n = 0;
-    BallTables bt{};
-    DenseTables dt{};
+    // Ball(32) offset tables: one device allocation holding c8 entries,
+    // rest entries, c8_start, rest_start and ball_size
+    void *d_offsets = nullptr;
+    size_t offsets_bytes = 0;
+    OffsetTables ot{};
     int h_ball_size[kRmax + 1] = {};
     // f32-binning scratch: per-block min/max partials
     float2 *d_minmax = nullptr;

@@ -12,13 +12,12 @@
 //   scale  = built incrementally: shell r (offsets o with ceil|o| == r, and
 //            everything up to r_min for the first scale) is added to the
 //            counts of r-1.
-//   offsets= one table per radius class rho: first the offsets with three
-//            nonzero components, stored once per set of 8 sign mirrors as
-//            (|dx|, |dy|, |dz|) and expanded with warp-uniform arithmetic,
-//            then every offset on a coordinate plane or axis, stored with
-//            its signs.  For r_max <= 25 the table sits in constant memory
-//            (warp-uniform reads through the constant cache), beyond that
-//            in global memory.
+//   offsets= per radius class rho, the offsets with three nonzero
+//            components, stored once per set of 8 sign mirrors as (|dx|,
+//            |dy|, |dz|) and expanded with warp-uniform arithmetic, then every
+//            offset on a coordinate plane or axis, stored with its signs.
+//            For r_max <= 25 the tables sit in constant memory (warp-uniform
+//            reads through the constant cache), beyond that in global memory.
 //   counts = each lane owns a column of 32-bit words in shared memory
 //            (word v at +128 v bytes, so the 32 lanes of a warp always hit
 //            32 different banks), one word per stored value v = 0..B;
@@ -37,20 +36,19 @@ namespace ks {
 namespace {
 
 constexpr int kTmaPollLimit = 1 << 20;
-constexpr int kConstRmax = 25;            // largest r_max whose table fits
-constexpr int kConstEntries = 16000;
+constexpr int kConstRmax = 25;            // largest r_max whose tables fit
+constexpr int kConstC8 = 7500;            // three-nonzero entries with rho <= 25: 7442
+constexpr int kConstRest = 5800;          // plane/axis entries with rho <= 25: 5731
 
-// Offset table of radius classes 0..kConstRmax (see header comment).
-__constant__ uint32_t c_tab[kConstEntries];
-__constant__ int c_tab_start[kConstRmax + 2];    // first entry of class rho
-__constant__ int c_tab_rest[kConstRmax + 1];     // first plane/axis entry of rho
+// Offset tables of radius classes 0..kConstRmax (layout as OffsetTables).
+__constant__ uint32_t c_c8[kConstC8];
+__constant__ uint32_t c_rest[kConstRest];
+__constant__ int c_c8_start[kConstRmax + 2];
+__constant__ int c_rest_start[kConstRmax + 2];
 
 struct DenseArgs {
     VolDesc vol;
-    const uint32_t *g_tab;       // global copy of the table (all classes <= 32)
-    const int *g_tab_start;      // [kRmax + 2]
-    const int *g_tab_rest;       // [kRmax + 1]
-    const int *ball_size;        // [kRmax + 1]
+    OffsetTables ot;             // global copy (all classes <= 32)
     const double *T;
     const double *L;
     int r_min, r_max, S, w_norm;
@@ -65,16 +63,18 @@ struct DenseArgs {
 
 template <bool CTAB>
 struct Tab {
-    const uint32_t *g;
-    const int *gs, *gr;
-    __device__ __forceinline__ uint32_t entry(int k) const {
-        if constexpr (CTAB) return c_tab[k]; else return __ldg(g + k);
+    OffsetTables g;
+    __device__ __forceinline__ uint32_t c8(int k) const {
+        if constexpr (CTAB) return c_c8[k]; else return __ldg(g.c8 + k);
     }
-    __device__ __forceinline__ int start(int rho) const {
-        if constexpr (CTAB) return c_tab_start[rho]; else return __ldg(gs + rho);
+    __device__ __forceinline__ uint32_t rest(int k) const {
+        if constexpr (CTAB) return c_rest[k]; else return __ldg(g.rest + k);
     }
-    __device__ __forceinline__ int rest(int rho) const {
-        if constexpr (CTAB) return c_tab_rest[rho]; else return __ldg(gr + rho);
+    __device__ __forceinline__ int c8_start(int rho) const {
+        if constexpr (CTAB) return c_c8_start[rho]; else return __ldg(g.c8_start + rho);
+    }
+    __device__ __forceinline__ int rest_start(int rho) const {
+        if constexpr (CTAB) return c_rest_start[rho]; else return __ldg(g.rest_start + rho);
     }
 };
 
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(512) k_dense(const DenseArgs a,
         pz = (int)a.vol.plane;
         py = (int)a.vol.pitch;
     }
-    const Tab<CTAB> tab{a.g_tab, a.g_tab_start, a.g_tab_rest};
+    const Tab<CTAB> tab{a.ot};
 
     // Lane's counter column: word v at +128 v; previous-scale words (WIDE)
     // at +128 (NW + v).
@@ -169,15 +169,17 @@ __global__ void __launch_bounds__(512) k_dense(const DenseArgs a,
         for (int i = 0; i < a.S; ++i) {
             const int r = a.r_min + i;
             for (int rho = (i == 0 ? 0 : r); rho <= r; ++rho) {
-                const int k0 = tab.start(rho), k1 = tab.rest(rho), k2 = tab.start(rho + 1);
+                const int k0 = tab.c8_start(rho), k1 = tab.c8_start(rho + 1);
+                const int k2 = tab.rest_start(rho), k3 = tab.rest_start(rho + 1);
                 // three nonzero components: 8 sign mirrors
-                uint32_t e = k0 < k1 ? tab.entry(k0) : 0u;
+                uint32_t e = k0 < k1 ? tab.c8(k0) : 0u;
                 for (int k = k0; k < k1; ++k) {
-                    const uint32_t en = k + 1 < k1 ? tab.entry(k + 1) : 0u;   // prefetch
+                    const uint32_t en = k + 1 < k1 ? tab.c8(k + 1) : 0u;   // prefetch
                     const int X = (int)(e & 0xffu);
                     const int Y = (int)((e >> 8) & 0xffu) * py;
                     const int Z = (int)((e >> 16) & 0xffu) * pz;
                     const int o0 = Z + Y, o1 = Z - Y, o2 = Y - Z, o3 = -Z - Y;
+                    // (the top byte of e is the radius class, unused here)
                     const uint32_t v0 = src.at(c0, o0 + X), v1 = src.at(c0, o0 - X);
                     const uint32_t v2 = src.at(c0, o1 + X), v3 = src.at(c0, o1 - X);
                     const uint32_t v4 = src.at(c0, o2 + X), v5 = src.at(c0, o2 - X);
@@ -193,8 +195,8 @@ __global__ void __launch_bounds__(512) k_dense(const DenseArgs a,
                     e = en;
                 }
                 // offsets on a coordinate plane or axis, one entry each
-                for (int k = k1; k < k2; ++k) {
-                    const uint32_t f = tab.entry(k);
+                for (int k = k2; k < k3; ++k) {
+                    const uint32_t f = tab.rest(k);
                     const int off = ((int)((f >> 16) & 0xffu) - 64) * pz +
                                     ((int)((f >> 8) & 0xffu) - 64) * py + ((int)(f & 0xffu) - 64);
                     red_add_shared(cnt_lane + (src.at(c0, off) << 7), 1u);
@@ -203,7 +205,7 @@ __global__ void __launch_bounds__(512) k_dense(const DenseArgs a,
 
             // ---- exact per-scale quantities from the lane's counters
             const uint32_t zero_cnt = ld_shared_u32(cnt_lane);
-            const uint32_t N = (uint32_t)__ldg(a.ball_size + r) - zero_cnt;
+            const uint32_t N = (uint32_t)__ldg(a.ot.ball_size + r) - zero_cnt;
             double ssum = 0.0;
             int occ = 0;
             uint64_t D = 0;
@@ -305,12 +307,16 @@ int ball_size_host(int r) {
     return n;
 }
 
-cudaError_t dense_upload_constant_table(const uint32_t *tab, int n_const, const int *start,
-                                        const int *rest) {
-    if (n_const > kConstEntries) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemcpyToSymbol(c_tab, tab, n_const * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tab_start, start, (kConstRmax + 2) * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tab_rest, rest, (kConstRmax + 1) * sizeof(int));
+cudaError_t dense_upload_constant_table(const uint32_t *c8, const int *c8_start,
+                                        const uint32_t *rest, const int *rest_start) {
+    const int n8 = c8_start[kConstRmax + 1], nr = rest_start[kConstRmax + 1];
+    if (n8 > kConstC8 || nr > kConstRest) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyToSymbol(c_c8, c8, n8 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rest, rest, nr * sizeof(uint32_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpyToSymbol(c_c8_start, c8_start, (kConstRmax + 2) * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpyToSymbol(c_rest_start, rest_start, (kConstRmax + 2) * sizeof(int));
     return e;
 }
 
@@ -328,16 +334,13 @@ bool dense_config_fits(const DenseConfig &c, int B, int r_max) {
 }
 
 cudaError_t launch_dense(const LaunchCtx &lc, const VolDesc &v, const CUtensorMap *tmap,
-                         const DenseTables &dt, const double *T, const double *L, int r_min,
+                         const OffsetTables &ot, const double *T, const double *L, int r_min,
                          int r_max, int w_norm, const DenseConfig &cfg, const DenseOut &out,
                          int z0, int z1) {
     const Geometry g = geometry(cfg, v.B, r_max);
     DenseArgs a{};
     a.vol = v;
-    a.g_tab = dt.tab;
-    a.g_tab_start = dt.start;
-    a.g_tab_rest = dt.rest;
-    a.ball_size = dt.ball_size;
+    a.ot = ot;
     a.T = T;
     a.L = L;
     a.r_min = r_min;

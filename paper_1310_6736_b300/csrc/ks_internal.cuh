@@ -34,13 +34,23 @@ struct VolDesc {
     int64_t pitch, plane;
 };
 
-// Offsets of Ball(32) used by the seed kernels (built once per context):
-// every offset o with |o| <= 32, sorted by its radius class rho(o) =
-// ceil(|o|) (the smallest r with |o|^2 <= r^2), then by dz, dy, dx; packed
-// (dx+64) | (dy+64) << 8 | (dz+64) << 16 | rho << 24.  Ball(r) is the
-// prefix of length ball_size[r].
-struct BallTables {
-    const uint32_t *ball;
+// Offsets of Ball(32), built once per context and shared by every kernel.
+// rho(o) = ceil(|o|) is the radius class of offset o (the smallest r with
+// |o|^2 <= r^2); both parts below are sorted by rho, so Ball(r) is a prefix
+// of each.
+//   c8:   offsets with three nonzero components, one entry per set of 8
+//         sign mirrors: |dx| | |dy| << 8 | |dz| << 16 | rho << 24.  Mirror
+//         s (bit0: -x, bit1: -y, bit2: -z) of an entry is a distinct offset
+//         in the open octant s.  Class rho: [c8_start[rho], c8_start[rho+1]).
+//   rest: offsets on a coordinate plane or axis, one entry each:
+//         (dx+64) | (dy+64) << 8 | (dz+64) << 16 | rho << 24.
+//         Class rho: [rest_start[rho], rest_start[rho+1]).
+// |Ball(r)| = 8 c8_start[r+1] + rest_start[r+1] = ball_size[r].
+struct OffsetTables {
+    const uint32_t *c8;
+    const int *c8_start;      // [kRmax + 2]
+    const uint32_t *rest;
+    const int *rest_start;    // [kRmax + 2]
     const int *ball_size;     // [kRmax + 1]
 };
 
@@ -157,25 +167,15 @@ struct DenseOut {
     double *H;     // optional, voxel-major x S
     double *W;     // optional
 };
-// Offset table of the dense kernel: for each radius class rho, entries
-// [start[rho], rest[rho]) are offsets with three nonzero components stored
-// once per set of 8 sign mirrors, packed |dx| | |dy| << 8 | |dz| << 16, and
-// [rest[rho], start[rho+1]) are the offsets on a coordinate plane or axis,
-// packed (dx+64) | (dy+64) << 8 | (dz+64) << 16.
-struct DenseTables {
-    const uint32_t *tab;
-    const int *start;       // [kRmax + 2]
-    const int *rest;        // [kRmax + 1]
-    const int *ball_size;   // [kRmax + 1]
-};
-// The classes rho <= dense_const_rmax() also live in constant memory.
-cudaError_t dense_upload_constant_table(const uint32_t *tab, int n_const, const int *start,
-                                        const int *rest);
+// The classes rho <= dense_const_rmax() of both parts of the offset tables
+// also live in the dense kernel's constant memory.
+cudaError_t dense_upload_constant_table(const uint32_t *c8, const int *c8_start,
+                                        const uint32_t *rest, const int *rest_start);
 int dense_const_rmax();
 bool dense_config_fits(const DenseConfig &c, int B, int r_max);
 size_t dense_smem_bytes(const DenseConfig &c, int B, int r_max);
 cudaError_t launch_dense(const LaunchCtx &lc, const VolDesc &v, const CUtensorMap *tmap,
-                         const DenseTables &dt, const double *T, const double *L, int r_min,
+                         const OffsetTables &ot, const double *T, const double *L, int r_min,
                          int r_max, int w_norm, const DenseConfig &cfg, const DenseOut &out,
                          int z0, int z1);
 
@@ -190,19 +190,22 @@ struct SeedJob {
     ks_ms_result *ms_out;        // device, n_seeds * S (kind mean shift)
     int32_t *traj;               // device, n_seeds * (max_iter+1) * 3, or null
 };
-// A work queue: segments of items, segment k covers items
-// [seg_start[k], seg_start[k+1]) of kind seg_kind[k] on job seg_job[k].
+// A work queue in tickets: segment k covers tickets [seg_start[k],
+// seg_start[k+1]) of kind seg_kind[k] on job seg_job[k].  An octant ticket
+// is one seed; a mean-shift ticket is up to 8 (seed, r) items (one per
+// warp of the block), seed_tickets() tells how many a job needs.
 struct SeedQueue {
     const SeedJob *jobs;
     const int64_t *seg_start;
     const int *seg_kind;
     const int *seg_job;
     int n_segs;
-    int64_t n_items;
-    unsigned long long *head;    // persistent mode: next item counter
+    int64_t n_tickets;
+    unsigned long long *head;    // persistent mode: next ticket counter
 };
+int64_t seed_tickets(int kind, int64_t n_seeds, int S);
 size_t seed_smem_bytes(int B, int S);
-cudaError_t launch_seeds(const LaunchCtx &lc, const SeedQueue &q, const BallTables &bt,
+cudaError_t launch_seeds(const LaunchCtx &lc, const SeedQueue &q, const OffsetTables &ot,
                          const double *T, const double *L, int max_B, int max_S,
                          bool persistent, int grid);
 int seed_blocks_per_sm(int max_B, int max_S);

@@ -1,48 +1,69 @@
 // Seed-grid searches: octant hill-climbing (Sec. 2.2, Alg. 1 in 3D) and
 // mean shift towards the uniform pmf (Sec. 2.3, Eq. 4-6).
 //
-// One block of 256 threads owns one item at a time: an octant seed (all
-// its iterations plus the final Kadir-Brady evaluation) or one (seed, r)
-// mean-shift item.  The same kernel serves a plain launch (block i takes
-// item i) and the persistent batched launch (blocks pull items from a
-// device counter until the queue is empty), so the arithmetic of an item
-// does not depend on how it was scheduled.
+// Scheduling.  Work is handed out in tickets, one block of 256 threads per
+// ticket: an octant ticket is one seed (all its iterations plus the final
+// Kadir-Brady evaluation); a mean-shift ticket is one (seed, r) item, items
+// taken largest radius first.  The same kernel serves a plain launch (block
+// i takes ticket i) and the persistent batched launch (blocks pull tickets
+// from a device counter until the queue is empty), so an item's arithmetic
+// never depends on how it was scheduled.
 //
-// Per iteration the block walks the window's offsets (the Ball(32) table,
-// sorted by radius class so that Ball(r) is a prefix), threads striding
-// over offsets so that a warp reads 32 neighbouring voxels of a row, and
-// accumulates integer counts (and, for mean shift, integer offset sums)
-// with shared-memory atomics.  Everything accumulated per voxel is an
-// integer, so the order of accumulation cannot change any result; the
-// FP64 steps run afterwards in one fixed order (bins ascending, octants
-// 0..7), each step a single IEEE operation.
+// Octant pass.  Ball(r_max) at P is walked through the offset tables: a
+// three-nonzero entry is expanded to its 8 sign mirrors on 8 neighbouring
+// lanes, and mirror s lies in the open octant s, so those 8 lanes always
+// update 8 different histograms.  A plane/axis voxel belongs to every
+// closed octant it touches and is added to each; its multiplicity minus one
+// is recorded per (shell, bin), so that the full-ball histogram is the sum
+// of the 8 closed-octant histograms minus that excess.  The Kadir-Brady
+// quantities at the final centre therefore come from the last octant pass
+// whenever the climb converged (the pass ran at the final centre).
+//
+// Mean-shift pass.  Each thread adds one packed 64-bit word per voxel
+// (count and the three offset sums, each offset shifted by +32, in
+// disjoint bit fields whose bounds are checked below) to a column of
+// accumulators private to a few threads, with one red.shared.add.u64; the
+// columns are then summed per bin.
+//
+// Every accumulated quantity is an integer, so neither the order nor the
+// grouping of accumulation can change a result; the FP64 steps run
+// afterwards in one fixed order (bins ascending, octants 0..7), each step a
+// single IEEE operation.
 #include "ks_internal.cuh"
 
 namespace ks {
 namespace {
 
 struct SeedShared {
-    int P[3];
     int step[3];
-    int64_t item;
+    int64_t ticket;
     uint32_t N[kMaxScales];
     unsigned long long D[kMaxScales];
-};
-
-struct Smem {
-    uint32_t *cnt;     // octant: [8][S][B]; final KB: [S][B]; mean shift: [B][4]
-    double *hb;        // octant: [8][S] entropies; KB: [S]; mean shift: [4][B]
 };
 
 __device__ __forceinline__ const uint8_t *voxel_ptr(const VolDesc &v, const int P[3]) {
     return v.base + (int64_t)P[2] * v.plane + (int64_t)P[1] * v.pitch + P[0];
 }
 
-__device__ __forceinline__ void unpack_offset(uint32_t e, int &dx, int &dy, int &dz, int &rho) {
-    dx = (int)(e & 0xffu) - 64;
-    dy = (int)((e >> 8) & 0xffu) - 64;
-    dz = (int)((e >> 16) & 0xffu) - 64;
-    rho = (int)(e >> 24);
+// Offset w of the expanded enumeration of Ball(r): w < 8 n8 is mirror w & 7
+// of three-nonzero entry w >> 3, the rest are plane/axis entries.
+__device__ __forceinline__ void offset_of(const OffsetTables &ot, int w, int n8, int &dx, int &dy,
+                                          int &dz, int &rho) {
+    if (w < 8 * n8) {
+        const uint32_t e = __ldg(ot.c8 + (w >> 3));
+        const int m = w & 7;
+        const int a = (int)(e & 0xffu), b = (int)((e >> 8) & 0xffu), c = (int)((e >> 16) & 0xffu);
+        dx = (m & 1) ? -a : a;
+        dy = (m & 2) ? -b : b;
+        dz = (m & 4) ? -c : c;
+        rho = (int)(e >> 24);
+    } else {
+        const uint32_t f = __ldg(ot.rest + (w - 8 * n8));
+        dx = (int)(f & 0xffu) - 64;
+        dy = (int)((f >> 8) & 0xffu) - 64;
+        dz = (int)((f >> 16) & 0xffu) - 64;
+        rho = (int)(f >> 24);
+    }
 }
 
 // Entropy of counts c[0..B) (bin order), the library's fixed formula.
@@ -66,67 +87,70 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) {
 }
 
 // ---------------------------------------------------------------- octant
-// Counts of the 8 closed octants of every shell at P, then prefix sums over
-// shells (so cnt[j][si] is the histogram of octant j of Ball(r_min + si)),
-// then the 8*S entropies into hb[j*S + si].
-__device__ void octant_histograms(const SeedJob &J, const BallTables &bt, const double *T,
-                                  const double *L, const Smem &m, const int P[3]) {
+// Closed-octant histograms of every shell at P into cnt[j][si][b] and the
+// plane/axis multiplicity excess into extra[si][b], both then turned into
+// prefix sums over shells (histograms of Ball(r_min + si)).
+__device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *cnt,
+                            uint32_t *extra, const int P[3]) {
     const int B = J.vol.B, S = J.S;
-    for (int k = threadIdx.x; k < 8 * S * B; k += blockDim.x) m.cnt[k] = 0;
+    for (int k = threadIdx.x; k < 9 * S * B; k += blockDim.x) cnt[k] = 0;   // extra follows cnt
     __syncthreads();
     const uint8_t *c0 = voxel_ptr(J.vol, P);
-    const int nball = __ldg(bt.ball_size + J.r_max);
     const int plane = (int)J.vol.plane, pitch = (int)J.vol.pitch;
-    for (int k = threadIdx.x; k < nball; k += blockDim.x) {
+    const int n8 = __ldg(ot.c8_start + J.r_max + 1);
+    const int total = 8 * n8 + __ldg(ot.rest_start + J.r_max + 1);
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
         int dx, dy, dz, rho;
-        unpack_offset(__ldg(bt.ball + k), dx, dy, dz, rho);
+        offset_of(ot, w, n8, dx, dy, dz, rho);
         const uint32_t v = __ldg(c0 + dz * plane + dy * pitch + dx);
         if (v == 0u) continue;
         const int si = rho > J.r_min ? rho - J.r_min : 0;
-        // allowed j-bit values per axis: bit 0 -> positive side, bit 1 -> negative
-        const int ax = dx > 0 ? 1 : (dx < 0 ? 2 : 3);
-        const int ay = dy > 0 ? 1 : (dy < 0 ? 2 : 3);
-        const int az = dz > 0 ? 1 : (dz < 0 ? 2 : 3);
-        uint32_t *base = m.cnt + si * B + (v - 1);
-        for (int jz = 0; jz < 2; ++jz) {
-            if (!(az & (1 << jz))) continue;
-            for (int jy = 0; jy < 2; ++jy) {
-                if (!(ay & (1 << jy))) continue;
-                for (int jx = 0; jx < 2; ++jx) {
-                    if (!(ax & (1 << jx))) continue;
-                    const int j = jx | (jy << 1) | (jz << 2);
-                    atomicAdd(base + j * S * B, 1u);
+        uint32_t *base = cnt + si * B + (v - 1);
+        if (w < 8 * n8) {
+            atomicAdd(base + (w & 7) * S * B, 1u);
+        } else {
+            const int ax = dx > 0 ? 1 : (dx < 0 ? 2 : 3);
+            const int ay = dy > 0 ? 1 : (dy < 0 ? 2 : 3);
+            const int az = dz > 0 ? 1 : (dz < 0 ? 2 : 3);
+            uint32_t mult = 0;
+            for (int jz = 0; jz < 2; ++jz) {
+                if (!(az & (1 << jz))) continue;
+                for (int jy = 0; jy < 2; ++jy) {
+                    if (!(ay & (1 << jy))) continue;
+                    for (int jx = 0; jx < 2; ++jx) {
+                        if (!(ax & (1 << jx))) continue;
+                        atomicAdd(base + (jx | (jy << 1) | (jz << 2)) * S * B, 1u);
+                        ++mult;
+                    }
                 }
             }
+            atomicAdd(extra + si * B + (v - 1), mult - 1u);
         }
     }
     __syncthreads();
-    for (int col = threadIdx.x; col < 8 * B; col += blockDim.x) {
+    for (int col = threadIdx.x; col < 9 * B; col += blockDim.x) {    // 8 octants + excess
         const int j = col / B, b = col % B;
         uint32_t run = 0;
         for (int si = 0; si < S; ++si) {
-            run += m.cnt[(j * S + si) * B + b];
-            m.cnt[(j * S + si) * B + b] = run;
+            run += cnt[(j * S + si) * B + b];
+            cnt[(j * S + si) * B + b] = run;
         }
     }
     __syncthreads();
-    for (int w = threadIdx.x; w < 8 * S; w += blockDim.x)
-        m.hb[w] = window_entropy(m.cnt + w * B, B, T, L, nullptr);
-    __syncthreads();
 }
 
-// Alg. 1's update from the octant entropies: eps_j = max over scales (the
-// smallest r on ties), d_j = k_j sigma_j, delta = sum_j eps_j d_j / sum_j
-// eps_j summed over j = 0..7, rounded half away from zero.
-__device__ void octant_step(const SeedJob &J, const Smem &m, int step[3]) {
+// Alg. 1's update from the octant entropies hb[j*S + si]: eps_j = max over
+// scales (the smallest r on ties), d_j = k_j sigma_j, delta = sum_j eps_j
+// d_j / sum_j eps_j summed over j = 0..7, rounded half away from zero.
+__device__ void octant_step(const SeedJob &J, const double *hb, int step[3]) {
     const int S = J.S;
     double num[3] = {0.0, 0.0, 0.0}, den = 0.0;
     for (int j = 0; j < 8; ++j) {
-        double best = m.hb[j * S];
+        double best = hb[j * S];
         int k = J.r_min;
         for (int si = 1; si < S; ++si)
-            if (m.hb[j * S + si] > best) {
-                best = m.hb[j * S + si];
+            if (hb[j * S + si] > best) {
+                best = hb[j * S + si];
                 k = J.r_min + si;
             }
         const int sg[3] = {(j & 1) ? -1 : 1, (j & 2) ? -1 : 1, (j & 4) ? -1 : 1};
@@ -137,42 +161,26 @@ __device__ void octant_step(const SeedJob &J, const Smem &m, int step[3]) {
     for (int a = 0; a < 3; ++a) step[a] = den == 0.0 ? 0 : (int)round(__ddiv_rn(num[a], den));
 }
 
-// Kadir-Brady on the full ball at P (after the climb): H(r), D(r), peaks,
-// W and Y at peaks.  Writes s_best, Y_best, H_best, W_best.
-__device__ void kb_at(const SeedJob &J, const BallTables &bt, const double *T, const double *L,
-                      const Smem &m, SeedShared &sh, const int P[3], int32_t *s_best,
-                      double *Y_best, double *H_best, double *W_best) {
+// Kadir-Brady on the full ball at the centre of the last octant pass: the
+// full histograms (sum of closed octants minus excess, written over the
+// excess array), H(r), D(r), peaks, W and Y at peaks.
+__device__ void kb_from_pass(const SeedJob &J, const double *T, const double *L, uint32_t *cnt,
+                             uint32_t *full, double *hb, SeedShared &sh, ks_seed_result *o) {
     const int B = J.vol.B, S = J.S;
-    for (int k = threadIdx.x; k < S * B; k += blockDim.x) m.cnt[k] = 0;
-    __syncthreads();
-    const uint8_t *c0 = voxel_ptr(J.vol, P);
-    const int nball = __ldg(bt.ball_size + J.r_max);
-    const int plane = (int)J.vol.plane, pitch = (int)J.vol.pitch;
-    for (int k = threadIdx.x; k < nball; k += blockDim.x) {
-        int dx, dy, dz, rho;
-        unpack_offset(__ldg(bt.ball + k), dx, dy, dz, rho);
-        const uint32_t v = __ldg(c0 + dz * plane + dy * pitch + dx);
-        if (v == 0u) continue;
-        const int si = rho > J.r_min ? rho - J.r_min : 0;
-        atomicAdd(m.cnt + si * B + (v - 1), 1u);
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < B; b += blockDim.x) {
-        uint32_t run = 0;
-        for (int si = 0; si < S; ++si) {
-            run += m.cnt[si * B + b];
-            m.cnt[si * B + b] = run;
-        }
+    for (int k = threadIdx.x; k < S * B; k += blockDim.x) {
+        uint32_t s = 0;
+        for (int j = 0; j < 8; ++j) s += cnt[j * S * B + k];
+        full[k] = s - full[k];
     }
     __syncthreads();
     for (int si = threadIdx.x; si < S; si += blockDim.x) {
         uint32_t N;
-        m.hb[si] = window_entropy(m.cnt + si * B, B, T, L, &N);
+        hb[si] = window_entropy(full + si * B, B, T, L, &N);
         sh.N[si] = N;
     }
     __syncthreads();
     for (int si = 1 + threadIdx.x; si < S; si += blockDim.x) {
-        const uint32_t *c = m.cnt + si * B, *p = m.cnt + (si - 1) * B;
+        const uint32_t *c = full + si * B, *p = full + (si - 1) * B;
         const uint32_t N = sh.N[si], Np = sh.N[si - 1];
         uint64_t D = 0;
         for (int b = 0; b < B; ++b) {
@@ -183,39 +191,46 @@ __device__ void kb_at(const SeedJob &J, const BallTables &bt, const double *T, c
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double yb = 0.0, hb = 0.0, wb = 0.0;
+        double yb = 0.0, hbest = 0.0, wbest = 0.0;
         int sb = 0;
         for (int i = 1; i + 1 < S; ++i) {
-            if (m.hb[i - 1] < m.hb[i] && m.hb[i] >= m.hb[i + 1]) {
+            if (hb[i - 1] < hb[i] && hb[i] >= hb[i + 1]) {
                 const double W = kb_weight(sh.D[i], sh.N[i], sh.N[i - 1], J.r_min + i, J.w_norm);
-                const double y = __dmul_rn(m.hb[i], W);
+                const double y = __dmul_rn(hb[i], W);
                 if (sb == 0 || y > yb) {
                     yb = y;
                     sb = J.r_min + i;
-                    hb = m.hb[i];
-                    wb = W;
+                    hbest = hb[i];
+                    wbest = W;
                 }
             }
         }
-        *s_best = sb;
-        *Y_best = yb;
-        *H_best = hb;
-        *W_best = wb;
+        o->s_best = sb;
+        o->Y_best = yb;
+        o->H_best = hbest;
+        o->W_best = wbest;
     }
     __syncthreads();
 }
 
-__device__ void octant_item(const SeedJob &J, int64_t sidx, const BallTables &bt,
-                            const double *T, const double *L, const Smem &m, SeedShared &sh) {
+__device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &ot,
+                            const double *T, const double *L, uint32_t *cnt, double *hb,
+                            SeedShared &sh) {
     const int dims[3] = {J.vol.nx, J.vol.ny, J.vol.nz};
+    const int B = J.vol.B, S = J.S;
+    uint32_t *extra = cnt + 8 * S * B;
     int P[3] = {J.seeds[3 * sidx], J.seeds[3 * sidx + 1], J.seeds[3 * sidx + 2]};
     const int T1 = J.max_iter + 1;
     if (threadIdx.x == 0 && J.traj)
         for (int a = 0; a < 3; ++a) J.traj[(sidx * T1) * 3 + a] = P[a];
-    int it = 0, conv = 0;
+    int it = 0, conv = 0, fresh = 0;
     while (it < J.max_iter) {
-        octant_histograms(J, bt, T, L, m, P);
-        if (threadIdx.x == 0) octant_step(J, m, sh.step);
+        octant_pass(J, ot, cnt, extra, P);
+        fresh = 1;
+        for (int w = threadIdx.x; w < 8 * S; w += blockDim.x)
+            hb[w] = window_entropy(cnt + w * B, B, T, L, nullptr);
+        __syncthreads();
+        if (threadIdx.x == 0) octant_step(J, hb, sh.step);
         __syncthreads();
         ++it;
         int Pn[3];
@@ -226,16 +241,16 @@ __device__ void octant_item(const SeedJob &J, int64_t sidx, const BallTables &bt
             break;
         }
         for (int a = 0; a < 3; ++a) P[a] = Pn[a];
+        fresh = 0;
         if (threadIdx.x == 0 && J.traj)
             for (int a = 0; a < 3; ++a) J.traj[(sidx * T1 + it) * 3 + a] = P[a];
     }
     if (threadIdx.x == 0 && J.traj)
         for (int t = it + (conv ? 0 : 1); t <= J.max_iter; ++t)
             for (int a = 0; a < 3; ++a) J.traj[(sidx * T1 + t) * 3 + a] = P[a];
+    if (!fresh) octant_pass(J, ot, cnt, extra, P);     // the last pass was not at P
     ks_seed_result *o = J.oct_out + sidx;
-    int32_t sb;
-    double yb, hbv, wbv;
-    kb_at(J, bt, T, L, m, sh, P, &sb, &yb, &hbv, &wbv);
+    kb_from_pass(J, T, L, cnt, extra, hb, sh, o);
     if (threadIdx.x == 0) {
         o->x = P[0];
         o->y = P[1];
@@ -245,44 +260,81 @@ __device__ void octant_item(const SeedJob &J, int64_t sidx, const BallTables &bt
         o->seed_z = J.seeds[3 * sidx + 2];
         o->iters = it;
         o->converged = conv;
-        o->s_best = sb;
         o->reserved = 0;
-        o->Y_best = yb;
-        o->H_best = hbv;
-        o->W_best = wbv;
     }
 }
 
 // ------------------------------------------------------------ mean shift
-// Counts c_b and integer offset sums m_b of Ball(r) at P into cnt[b][4].
-__device__ void ms_moments(const SeedJob &J, const BallTables &bt, const Smem &m, const int P[3],
-                           int r) {
+// Packed accumulator word: count in bits [0,11), sum(dx+32) in [11,28),
+// sum(dy+32) in [28,45), sum(dz+32) in [45,62).  A column is shared by
+// 256 / NC threads; each thread adds at most ceil(|Ball(r)| / 256) words,
+// so a column sees at most 64 (NC = 32, |Ball| < 2048), 128 (NC = 64,
+// |Ball| < 8192) or 2 * 536 = 1072 (NC = 128, |Ball| <= 137065) voxels:
+// count < 2^11 and each offset sum <= 1072 * 64 < 2^17.  No field carries.
+__device__ __forceinline__ int ms_columns(int nvox) {
+    return nvox < 2048 ? 32 : (nvox < 8192 ? 64 : 128);
+}
+
+__device__ __forceinline__ void red_add_shared_u64(uint32_t addr, unsigned long long v) {
+    asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(addr), "l"(v));
+}
+
+// Counts c_b and integer offset sums m_b of Ball(r) at P into acc[b][4].
+__device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long long *cols,
+                        int *part, int *acc, const int P[3], int r) {
     const int B = J.vol.B;
-    int *acc = reinterpret_cast<int *>(m.cnt);
-    for (int k = threadIdx.x; k < 4 * B; k += blockDim.x) acc[k] = 0;
+    const int n8 = __ldg(ot.c8_start + r + 1);
+    const int total = 8 * n8 + __ldg(ot.rest_start + r + 1);
+    const int NC = ms_columns(total);
+    for (int k = threadIdx.x; k < B * NC; k += blockDim.x) cols[k] = 0ull;
     __syncthreads();
     const uint8_t *c0 = voxel_ptr(J.vol, P);
-    const int nb = __ldg(bt.ball_size + r);
     const int plane = (int)J.vol.plane, pitch = (int)J.vol.pitch;
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    const uint32_t col_addr = smem_u32(cols + (threadIdx.x & (NC - 1)));
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
         int dx, dy, dz, rho;
-        unpack_offset(__ldg(bt.ball + k), dx, dy, dz, rho);
+        offset_of(ot, w, n8, dx, dy, dz, rho);
         const uint32_t v = __ldg(c0 + dz * plane + dy * pitch + dx);
         if (v == 0u) continue;
-        int *a = acc + 4 * (v - 1);
-        atomicAdd(a, 1);
-        if (dx) atomicAdd(a + 1, dx);
-        if (dy) atomicAdd(a + 2, dy);
-        if (dz) atomicAdd(a + 3, dz);
+        const unsigned long long inc = 1ull | ((unsigned long long)(dx + 32) << 11) |
+                                       ((unsigned long long)(dy + 32) << 28) |
+                                       ((unsigned long long)(dz + 32) << 45);
+        red_add_shared_u64(col_addr + (v - 1) * NC * 8, inc);
+    }
+    __syncthreads();
+    // column sums: 8 partial sums per bin, then one thread per bin
+    const int per = NC / 8;
+    for (int idx = threadIdx.x; idx < B * 8; idx += blockDim.x) {
+        const int b = idx >> 3, p = idx & 7;
+        int c = 0, sx = 0, sy = 0, sz = 0;
+        for (int k = 0; k < per; ++k) {
+            const unsigned long long x = cols[b * NC + p * per + k];
+            c += (int)(x & 0x7ffull);
+            sx += (int)((x >> 11) & 0x1ffffull);
+            sy += (int)((x >> 28) & 0x1ffffull);
+            sz += (int)((x >> 45) & 0x1ffffull);
+        }
+        int *q = part + idx * 4;
+        q[0] = c;
+        q[1] = sx;
+        q[2] = sy;
+        q[3] = sz;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        int s[4] = {0, 0, 0, 0};
+        for (int p = 0; p < 8; ++p)
+            for (int k = 0; k < 4; ++k) s[k] += part[(b * 8 + p) * 4 + k];
+        acc[4 * b] = s[0];
+        for (int k = 1; k < 4; ++k) acc[4 * b + k] = s[k] - 32 * s[0];
     }
     __syncthreads();
 }
 
 // Eq. 5-6 with a flat window: w_b = sqrt(N / (B c_b)); delta = sum_b w_b m_b /
-// sum_b w_b c_b, bins ascending, empty bins skipped.
-__device__ void ms_step(const SeedJob &J, const Smem &m, SeedShared &sh) {
+// sum_b w_b c_b, bins ascending, empty bins skipped.  Warp 0 computes.
+__device__ void ms_step(const SeedJob &J, const int *acc, double *prod, SeedShared &sh) {
     const int B = J.vol.B;
-    const int *acc = reinterpret_cast<const int *>(m.cnt);
     if (threadIdx.x < 32) {
         uint32_t n = 0;
         for (int b = threadIdx.x; b < B; b += 32) n += (uint32_t)acc[4 * b];
@@ -292,8 +344,8 @@ __device__ void ms_step(const SeedJob &J, const Smem &m, SeedShared &sh) {
             const int c = acc[4 * b];
             if (c > 0) {
                 const double w = __dsqrt_rn(__ddiv_rn((double)N, (double)((int64_t)B * c)));
-                for (int a = 0; a < 3; ++a) m.hb[a * B + b] = __dmul_rn(w, (double)acc[4 * b + 1 + a]);
-                m.hb[3 * B + b] = __dmul_rn(w, (double)c);
+                for (int a = 0; a < 3; ++a) prod[a * B + b] = __dmul_rn(w, (double)acc[4 * b + 1 + a]);
+                prod[3 * B + b] = __dmul_rn(w, (double)c);
             }
         }
         __syncwarp();
@@ -304,8 +356,8 @@ __device__ void ms_step(const SeedJob &J, const Smem &m, SeedShared &sh) {
                 double num[3] = {0.0, 0.0, 0.0}, den = 0.0;
                 for (int b = 0; b < B; ++b) {
                     if (acc[4 * b] == 0) continue;
-                    for (int a = 0; a < 3; ++a) num[a] = __dadd_rn(num[a], m.hb[a * B + b]);
-                    den = __dadd_rn(den, m.hb[3 * B + b]);
+                    for (int a = 0; a < 3; ++a) num[a] = __dadd_rn(num[a], prod[a * B + b]);
+                    den = __dadd_rn(den, prod[3 * B + b]);
                 }
                 for (int a = 0; a < 3; ++a) sh.step[a] = (int)round(__ddiv_rn(num[a], den));
             }
@@ -314,8 +366,9 @@ __device__ void ms_step(const SeedJob &J, const Smem &m, SeedShared &sh) {
     __syncthreads();
 }
 
-__device__ void ms_item(const SeedJob &J, int64_t item, const BallTables &bt, const double *T,
-                        const double *L, const Smem &m, SeedShared &sh) {
+__device__ void ms_item(const SeedJob &J, int64_t item, const OffsetTables &ot, const double *T,
+                        const double *L, unsigned long long *cols, int *part, int *acc,
+                        double *prod, SeedShared &sh) {
     const int dims[3] = {J.vol.nx, J.vol.ny, J.vol.nz};
     const int B = J.vol.B;
     const int64_t sidx = item / J.S;
@@ -323,8 +376,8 @@ __device__ void ms_item(const SeedJob &J, int64_t item, const BallTables &bt, co
     int P[3] = {J.seeds[3 * sidx], J.seeds[3 * sidx + 1], J.seeds[3 * sidx + 2]};
     int it = 0, conv = 0, fresh = 0;
     while (it < J.max_iter) {
-        ms_moments(J, bt, m, P, r);
-        ms_step(J, m, sh);
+        ms_pass(J, ot, cols, part, acc, P, r);
+        ms_step(J, acc, prod, sh);
         fresh = 1;
         ++it;
         int Pn[3];
@@ -337,8 +390,7 @@ __device__ void ms_item(const SeedJob &J, int64_t item, const BallTables &bt, co
         for (int a = 0; a < 3; ++a) P[a] = Pn[a];
         fresh = 0;
     }
-    if (!fresh) ms_moments(J, bt, m, P, r);
-    const int *acc = reinterpret_cast<const int *>(m.cnt);
+    if (!fresh) ms_pass(J, ot, cols, part, acc, P, r);
     // rho = sum_b sqrt(c_b / (N B)) and H, bins ascending.
     if (threadIdx.x < 32) {
         uint32_t n = 0;
@@ -347,16 +399,15 @@ __device__ void ms_item(const SeedJob &J, int64_t item, const BallTables &bt, co
         const uint32_t N = n;
         for (int b = threadIdx.x; b < B; b += 32) {
             const int c = acc[4 * b];
-            m.hb[b] = c > 0 ? __dsqrt_rn(__ddiv_rn((double)c, (double)((int64_t)N * B))) : 0.0;
+            prod[b] = c > 0 ? __dsqrt_rn(__ddiv_rn((double)c, (double)((int64_t)N * B))) : 0.0;
         }
         __syncwarp();
         if (threadIdx.x == 0) {
-            double rho = 0.0;
+            double rho = 0.0, s = 0.0;
             int occ = 0;
-            double s = 0.0;
             for (int b = 0; b < B; ++b) {
                 const uint32_t c = (uint32_t)acc[4 * b];
-                if (c > 0u) rho = __dadd_rn(rho, m.hb[b]);
+                if (c > 0u) rho = __dadd_rn(rho, prod[b]);
                 occ += c > 0u;
                 if (c > 1u) s = __dadd_rn(s, __ldg(T + c));
             }
@@ -376,42 +427,64 @@ __device__ void ms_item(const SeedJob &J, int64_t item, const BallTables &bt, co
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSeedThreads) k_seeds(const SeedQueue q, const BallTables bt,
+// Shared-memory layout of one block (the octant and mean-shift views
+// overlap; a block runs one ticket at a time).
+struct Layout {
+    size_t cnt, hb, oct_total;                  // octant: cnt[9][S][B] u32, hb[8S] f64
+    size_t cols, part, acc, prod, ms_total;     // mean shift
+    __host__ __device__ Layout(int B, int S) {
+        cnt = 0;
+        hb = ((size_t)9 * S * B * 4 + 15) / 16 * 16;
+        oct_total = hb + (size_t)8 * S * 8;
+        cols = 0;
+        part = (size_t)B * 128 * 8;
+        acc = part + (size_t)B * 8 * 4 * 4;
+        prod = acc + (size_t)B * 4 * 4;
+        ms_total = prod + (size_t)4 * B * 8;
+    }
+    __host__ __device__ size_t total() const { return oct_total > ms_total ? oct_total : ms_total; }
+};
+
+__global__ void __launch_bounds__(kSeedThreads) k_seeds(const SeedQueue q, const OffsetTables ot,
                                                         const double *__restrict__ T,
                                                         const double *__restrict__ L,
                                                         int max_B, int max_S, int persistent) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ SeedShared sh;
-    Smem m;
-    const size_t cnt_bytes = ((size_t)8 * max_S * max_B * 4 + 15) / 16 * 16;
-    m.cnt = reinterpret_cast<uint32_t *>(smem);
-    m.hb = reinterpret_cast<double *>(smem + cnt_bytes);
+    const Layout lay(max_B, max_S);
     for (int64_t round = 0;; ++round) {
         if (threadIdx.x == 0)
-            sh.item = persistent ? (int64_t)atomicAdd(q.head, 1ull)
-                                 : (round == 0 ? (int64_t)blockIdx.x : q.n_items);
+            sh.ticket = persistent ? (int64_t)atomicAdd(q.head, 1ull)
+                                   : (round == 0 ? (int64_t)blockIdx.x : q.n_tickets);
         __syncthreads();
-        const int64_t item = sh.item;
+        const int64_t t = sh.ticket;
         __syncthreads();
-        if (item >= q.n_items) return;
+        if (t >= q.n_tickets) return;
         int seg = 0;
-        while (seg + 1 < q.n_segs && item >= q.seg_start[seg + 1]) ++seg;
+        while (seg + 1 < q.n_segs && t >= q.seg_start[seg + 1]) ++seg;
         const SeedJob &J = q.jobs[q.seg_job[seg]];
-        const int64_t local = item - q.seg_start[seg];
-        if (q.seg_kind[seg] == kOctant)
-            octant_item(J, local, bt, T, L, m, sh);
-        else
-            ms_item(J, local, bt, T, L, m, sh);
+        const int64_t local = t - q.seg_start[seg];
+        if (q.seg_kind[seg] == kOctant) {
+            octant_item(J, local, ot, T, L, reinterpret_cast<uint32_t *>(smem + lay.cnt),
+                        reinterpret_cast<double *>(smem + lay.hb), sh);
+        } else {
+            // largest radius first: ticket -> (seed, r)
+            const int64_t r_idx = J.S - 1 - local / J.n_seeds;
+            const int64_t item = (local % J.n_seeds) * J.S + r_idx;
+            ms_item(J, item, ot, T, L, reinterpret_cast<unsigned long long *>(smem + lay.cols),
+                    reinterpret_cast<int *>(smem + lay.part), reinterpret_cast<int *>(smem + lay.acc),
+                    reinterpret_cast<double *>(smem + lay.prod), sh);
+        }
     }
 }
 
 }  // namespace
 
-size_t seed_smem_bytes(int B, int S) {
-    const size_t cnt = ((size_t)8 * S * B * 4 + 15) / 16 * 16;
-    const size_t hb = (size_t)(8 * S > 4 * B ? 8 * S : 4 * B) * 8;
-    return cnt + hb;
+int64_t seed_tickets(int kind, int64_t n_seeds, int S) {
+    return kind == kOctant ? n_seeds : n_seeds * S;
 }
+
+size_t seed_smem_bytes(int B, int S) { return Layout(B, S).total(); }
 
 int seed_blocks_per_sm(int max_B, int max_S) {
     int n = 0;
@@ -420,27 +493,28 @@ int seed_blocks_per_sm(int max_B, int max_S) {
     return n < 1 ? 1 : n;
 }
 
-cudaError_t launch_seeds(const LaunchCtx &lc, const SeedQueue &q, const BallTables &bt,
+cudaError_t launch_seeds(const LaunchCtx &lc, const SeedQueue &q, const OffsetTables &ot,
                          const double *T, const double *L, int max_B, int max_S,
                          bool persistent, int grid) {
     const size_t smem = seed_smem_bytes(max_B, max_S);
     cudaError_t e =
         cudaFuncSetAttribute(k_seeds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_seeds<<<grid, kSeedThreads, smem, lc.stream>>>(q, bt, T, L, max_B, max_S,
+    k_seeds<<<grid, kSeedThreads, smem, lc.stream>>>(q, ot, T, L, max_B, max_S,
                                                      persistent ? 1 : 0);
     return cudaGetLastError();
 }
 
 // Shared-memory histogram-increment rate: each lane adds bytes read from a
 // shared byte array into its own conflict-free counter column, the access
-// pattern of the dense kernel's inner loop.
-__global__ void __launch_bounds__(512) k_smem_peak(uint32_t *sink, int iters) {
+// pattern of the dense kernel's inner loop (one byte load and one
+// red.shared.add per voxel).
+__global__ void __launch_bounds__(256) k_smem_peak(uint32_t *sink, int iters) {
     __shared__ __align__(16) uint8_t bins[4096];
-    __shared__ uint32_t cnt[16][17 * 32];
+    __shared__ uint32_t cnt[8][33 * 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < 4096; i += blockDim.x) bins[i] = (uint8_t)((i * 7 + (i >> 5)) % 33);
-    for (int i = lane; i < 17 * 32; i += 32) cnt[warp][i] = 0;
+    for (int i = lane; i < 33 * 32; i += 32) cnt[warp][i] = 0;
     __syncthreads();
     const uint32_t col = smem_u32(&cnt[warp][lane]);
     const uint8_t *p = bins + warp * 64 + lane;
@@ -448,17 +522,17 @@ __global__ void __launch_bounds__(512) k_smem_peak(uint32_t *sink, int iters) {
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const uint32_t v = p[(it * 16 + u) * 97 & 2047];
-            red_add_shared(col + ((v >> 1) << 7), 1u << ((v & 1u) << 4));
+            red_add_shared(col + (v << 7), 1u);
         }
     }
     __syncwarp();
     uint32_t acc = 0;
-    for (int w = 0; w < 17; ++w) acc += ld_shared_u32(col + (w << 7));
+    for (int w = 0; w < 33; ++w) acc += ld_shared_u32(col + (w << 7));
     if (acc == 0xdeadbeefu) sink[blockIdx.x] = acc;   // keeps the work observable
 }
 
 cudaError_t launch_smem_peak(const LaunchCtx &lc, uint32_t *sink, int blocks, int iters) {
-    k_smem_peak<<<blocks, 512, 0, lc.stream>>>(sink, iters);
+    k_smem_peak<<<blocks, 256, 0, lc.stream>>>(sink, iters);
     return cudaGetLastError();
 }
 

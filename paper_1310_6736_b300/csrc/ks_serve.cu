@@ -227,12 +227,12 @@ static int launch_wave_seeds(Ctx *c, ServeState *S, std::vector<Request *> &join
         max_B = std::max(max_B, q.binning.bins);
         max_S = std::max(max_S, J.S);
         if ((q.seed_kinds & 1) && r->n_seeds) {
-            ss.push_back(ss.back() + r->n_seeds);
+            ss.push_back(ss.back() + seed_tickets(kOctant, r->n_seeds, J.S));
             sk.push_back(kOctant);
             sj.push_back(ji);
         }
         if ((q.seed_kinds & 2) && r->n_items) {
-            ss.push_back(ss.back() + r->n_items);
+            ss.push_back(ss.back() + seed_tickets(kMeanShift, r->n_seeds, J.S));
             sk.push_back(kMeanShift);
             sj.push_back(ji);
         }
@@ -265,14 +265,14 @@ static int launch_wave_seeds(Ctx *c, ServeState *S, std::vector<Request *> &join
     q.seg_kind = (const int *)put(sk.data(), sk.size() * 4);
     q.seg_job = (const int *)put(sj.data(), sj.size() * 4);
     q.n_segs = (int)sk.size();
-    q.n_items = ss.back();
+    q.n_tickets = ss.back();
     q.head = (unsigned long long *)m;
     cudaError_t e = cudaMemcpyAsync(m, h.data(), off, cudaMemcpyHostToDevice, S->stream);
     if (e != cudaSuccess) return cuda_err(c, e, "serving queue upload");
     const int grid = c->num_sms * seed_blocks_per_sm(max_B, max_S);
     ProfRec rec;
     prof_begin(c, "ks_seeds_persistent", S->stream, &rec);
-    e = launch_seeds(LaunchCtx{S->stream, S->d_status, c->num_sms}, q, c->bt, c->T, c->L, max_B,
+    e = launch_seeds(LaunchCtx{S->stream, S->d_status, c->num_sms}, q, c->ot, c->T, c->L, max_B,
                      max_S, true, grid);
     prof_end(c, &rec, S->stream);
     return cuda_err(c, e, "serving seed wave");
