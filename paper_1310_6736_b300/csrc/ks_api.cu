@@ -198,10 +198,37 @@ static int build_ball_tables(Ctx *c) {
         if (8 * s8[r + 1] + sr[r + 1] != c->h_ball_size[r])
             return set_err(c, KS_ECUDA, "internal: offset tables inconsistent");
     if ((int)ball.size() != kTableN) return set_err(c, KS_ECUDA, "internal: ball size");
-    // one allocation: c8 | rest | c8_start | rest_start | ball_size
-    const size_t b8 = h8.size() * 4, br = hr.size() * 4, bs = sizeof(s8);
-    const size_t at_r = (b8 + 255) / 256 * 256, at_s8 = at_r + (br + 255) / 256 * 256;
-    const size_t at_sr = at_s8 + 256, at_bs = at_sr + 256;
+    // x-rows of every Ball(r), longest first
+    std::vector<uint32_t> hw;
+    int swr[kRmax + 2];
+    for (int r = 0; r <= kRmax; ++r) {
+        swr[r] = (int)hw.size();
+        struct Row {
+            int dy, dz, w;
+        };
+        std::vector<Row> rows;
+        int n = 0;
+        for (int dz = -r; dz <= r; ++dz)
+            for (int dy = -r; dy <= r; ++dy) {
+                const int q = r * r - dy * dy - dz * dz;
+                if (q < 0) continue;
+                int w = 0;
+                while ((w + 1) * (w + 1) <= q) ++w;
+                rows.push_back({dy, dz, w});
+                n += 2 * w + 1;
+            }
+        if (n != c->h_ball_size[r]) return set_err(c, KS_ECUDA, "internal: row tables inconsistent");
+        std::stable_sort(rows.begin(), rows.end(), [](const Row &a, const Row &b) { return a.w > b.w; });
+        for (auto &rw : rows)
+            hw.push_back((uint32_t)(rw.dy + 64) | ((uint32_t)(rw.dz + 64) << 8) |
+                         ((uint32_t)rw.w << 16));
+    }
+    swr[kRmax + 1] = (int)hw.size();
+    // one allocation: c8 | rest | rows | c8_start | rest_start | rows_start | ball_size
+    const size_t b8 = h8.size() * 4, br = hr.size() * 4, bw = hw.size() * 4, bs = sizeof(s8);
+    const size_t at_r = (b8 + 255) / 256 * 256, at_w = at_r + (br + 255) / 256 * 256;
+    const size_t at_s8 = at_w + (bw + 255) / 256 * 256;
+    const size_t at_sr = at_s8 + 256, at_sw = at_sr + 256, at_bs = at_sw + 256;
     c->offsets_bytes = at_bs + 256;
     void *p;
     KS_TRY_CUDA(c, dev_alloc(c, &p, c->offsets_bytes));
@@ -211,11 +238,14 @@ static int build_ball_tables(Ctx *c) {
     KS_TRY_CUDA(c, cudaMemcpy(m + at_r, hr.data(), br, cudaMemcpyHostToDevice));
     KS_TRY_CUDA(c, cudaMemcpy(m + at_s8, s8, bs, cudaMemcpyHostToDevice));
     KS_TRY_CUDA(c, cudaMemcpy(m + at_sr, sr, bs, cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(m + at_w, hw.data(), bw, cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(m + at_sw, swr, bs, cudaMemcpyHostToDevice));
     KS_TRY_CUDA(c, cudaMemcpy(m + at_bs, c->h_ball_size, sizeof(c->h_ball_size),
                               cudaMemcpyHostToDevice));
-    c->ot = OffsetTables{(const uint32_t *)m, (const int *)(m + at_s8),
+    c->ot = OffsetTables{(const uint32_t *)m,         (const int *)(m + at_s8),
                          (const uint32_t *)(m + at_r), (const int *)(m + at_sr),
-                         (const int *)(m + at_bs)};
+                         (const int *)(m + at_bs),     (const uint32_t *)(m + at_w),
+                         (const int *)(m + at_sw)};
     // the classes up to dense_const_rmax() also go to constant memory
     KS_TRY_CUDA(c, dense_upload_constant_table(h8.data(), s8, hr.data(), sr));
     return KS_OK;
@@ -225,7 +255,8 @@ static int build_ball_tables(Ctx *c) {
 // ----------------------------------------------------------------- volumes
 size_t volume_bytes(int nx, int ny, int nz) {
     const int64_t pitch = ((int64_t)nx + 2 * kHalo + 15) / 16 * 16;
-    return (size_t)(pitch * (ny + 2 * kHalo) * (nz + 2 * kHalo));
+    // + 256 bytes of slack: row walks read whole aligned 8-byte words
+    return (size_t)(pitch * (ny + 2 * kHalo) * (nz + 2 * kHalo)) + 256;
 }
 
 static size_t dtype_size(int dtype) { return dtype == KS_U8 ? 1 : dtype == KS_I16 ? 2 : 4; }

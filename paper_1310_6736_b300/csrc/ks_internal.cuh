@@ -46,12 +46,18 @@ struct VolDesc {
 //         (dx+64) | (dy+64) << 8 | (dz+64) << 16 | rho << 24.
 //         Class rho: [rest_start[rho], rest_start[rho+1]).
 // |Ball(r)| = 8 c8_start[r+1] + rest_start[r+1] = ball_size[r].
+//   rows: for every r = 0..32, the x-rows of Ball(r): (dy, dz) with
+//         dy^2 + dz^2 <= r^2 and half-length w = floor(sqrt(r^2 - dy^2 -
+//         dz^2)), packed (dy+64) | (dz+64) << 8 | w << 16, longest rows
+//         first.  Ball(r)'s rows: [rows_start[r], rows_start[r+1]).
 struct OffsetTables {
     const uint32_t *c8;
     const int *c8_start;      // [kRmax + 2]
     const uint32_t *rest;
     const int *rest_start;    // [kRmax + 2]
     const int *ball_size;     // [kRmax + 1]
+    const uint32_t *rows;
+    const int *rows_start;    // [kRmax + 2]
 };
 
 // ------------------------------------------------------------------ PTX

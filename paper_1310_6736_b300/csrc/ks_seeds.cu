@@ -9,15 +9,18 @@
 // from a device counter until the queue is empty), so an item's arithmetic
 // never depends on how it was scheduled.
 //
-// Octant pass.  Ball(r_max) at P is walked through the offset tables: a
-// three-nonzero entry is expanded to its 8 sign mirrors on 8 neighbouring
-// lanes, and mirror s lies in the open octant s, so those 8 lanes always
-// update 8 different histograms.  A plane/axis voxel belongs to every
-// closed octant it touches and is added to each; its multiplicity minus one
-// is recorded per (shell, bin), so that the full-ball histogram is the sum
-// of the 8 closed-octant histograms minus that excess.  The Kadir-Brady
-// quantities at the final centre therefore come from the last octant pass
-// whenever the climb converged (the pass ran at the final centre).
+// Window walk.  A pass walks Ball(r) at P row by row: each thread takes one
+// x-row (dy, dz, half-length w) at a time and streams its 2w+1 bins, which
+// are consecutive bytes, so a thread's loads mostly hit L1 and the voxel
+// offset is just the loop counter.
+//
+// Octant pass.  A voxel off the coordinate planes lies in exactly one open
+// octant and costs one shared-memory atomic.  A plane/axis voxel belongs to
+// every closed octant it touches and is added to each; its multiplicity
+// minus one is recorded per (shell, bin), so that the full-ball histogram
+// is the sum of the 8 closed-octant histograms minus that excess.  The
+// Kadir-Brady quantities at the final centre therefore come from the last
+// octant pass whenever the climb converged (the pass ran at that centre).
 //
 // Mean-shift pass.  Each thread adds one packed 64-bit word per voxel
 // (count and the three offset sums, each offset shifted by +32, in
@@ -45,24 +48,24 @@ __device__ __forceinline__ const uint8_t *voxel_ptr(const VolDesc &v, const int 
     return v.base + (int64_t)P[2] * v.plane + (int64_t)P[1] * v.pitch + P[0];
 }
 
-// Offset w of the expanded enumeration of Ball(r): w < 8 n8 is mirror w & 7
-// of three-nonzero entry w >> 3, the rest are plane/axis entries.
-__device__ __forceinline__ void offset_of(const OffsetTables &ot, int w, int n8, int &dx, int &dy,
-                                          int &dz, int &rho) {
-    if (w < 8 * n8) {
-        const uint32_t e = __ldg(ot.c8 + (w >> 3));
-        const int m = w & 7;
-        const int a = (int)(e & 0xffu), b = (int)((e >> 8) & 0xffu), c = (int)((e >> 16) & 0xffu);
-        dx = (m & 1) ? -a : a;
-        dy = (m & 2) ? -b : b;
-        dz = (m & 4) ? -c : c;
-        rho = (int)(e >> 24);
-    } else {
-        const uint32_t f = __ldg(ot.rest + (w - 8 * n8));
-        dx = (int)(f & 0xffu) - 64;
-        dy = (int)((f >> 8) & 0xffu) - 64;
-        dz = (int)((f >> 16) & 0xffu) - 64;
-        rho = (int)(f >> 24);
+// Streams the 2w+1 bins starting at p with aligned 8-byte loads and calls
+// f(t, v) for the bin v at p + t.  The loads cover at most 7 bytes before
+// p and 7 bytes after p + 2w: with |offset| <= 32 that stays inside the
+// halo-padded allocation, which ends in 256 bytes of slack.
+template <typename F>
+__device__ __forceinline__ void walk_row(const uint8_t *p, int w, F &&f) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const unsigned long long *q = reinterpret_cast<const unsigned long long *>(a & ~uintptr_t(7));
+    const int off = (int)(a & 7u);
+    const int n = 2 * w + 1;
+    const int nw = (off + n + 7) >> 3;
+    for (int k = 0; k < nw; ++k) {
+        const unsigned long long word = __ldg(q + k);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int t = k * 8 + b - off;
+            if (t >= 0 && t < n) f(t, (uint32_t)(word >> (8 * b)) & 0xffu);
+        }
     }
 }
 
@@ -91,41 +94,49 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) {
 // plane/axis multiplicity excess into extra[si][b], both then turned into
 // prefix sums over shells (histograms of Ball(r_min + si)).
 __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *cnt,
-                            uint32_t *extra, const int P[3]) {
+                            uint32_t *extra, const uint8_t *rho_of, const int P[3]) {
     const int B = J.vol.B, S = J.S;
     for (int k = threadIdx.x; k < 9 * S * B; k += blockDim.x) cnt[k] = 0;   // extra follows cnt
     __syncthreads();
     const uint8_t *c0 = voxel_ptr(J.vol, P);
     const int plane = (int)J.vol.plane, pitch = (int)J.vol.pitch;
-    const int n8 = __ldg(ot.c8_start + J.r_max + 1);
-    const int total = 8 * n8 + __ldg(ot.rest_start + J.r_max + 1);
-    for (int w = threadIdx.x; w < total; w += blockDim.x) {
-        int dx, dy, dz, rho;
-        offset_of(ot, w, n8, dx, dy, dz, rho);
-        const uint32_t v = __ldg(c0 + dz * plane + dy * pitch + dx);
-        if (v == 0u) continue;
-        const int si = rho > J.r_min ? rho - J.r_min : 0;
-        uint32_t *base = cnt + si * B + (v - 1);
-        if (w < 8 * n8) {
-            atomicAdd(base + (w & 7) * S * B, 1u);
-        } else {
-            const int ax = dx > 0 ? 1 : (dx < 0 ? 2 : 3);
-            const int ay = dy > 0 ? 1 : (dy < 0 ? 2 : 3);
-            const int az = dz > 0 ? 1 : (dz < 0 ? 2 : 3);
-            uint32_t mult = 0;
-            for (int jz = 0; jz < 2; ++jz) {
-                if (!(az & (1 << jz))) continue;
-                for (int jy = 0; jy < 2; ++jy) {
-                    if (!(ay & (1 << jy))) continue;
-                    for (int jx = 0; jx < 2; ++jx) {
-                        if (!(ax & (1 << jx))) continue;
-                        atomicAdd(base + (jx | (jy << 1) | (jz << 2)) * S * B, 1u);
-                        ++mult;
+    const uint32_t *rows = ot.rows + __ldg(ot.rows_start + J.r_max);
+    const int nrows = __ldg(ot.rows_start + J.r_max + 1) - __ldg(ot.rows_start + J.r_max);
+    // one x-row of Ball(r_max) per thread at a time
+    for (int ri = threadIdx.x; ri < nrows; ri += blockDim.x) {
+        const uint32_t e = __ldg(rows + ri);
+        const int dy = (int)(e & 0xffu) - 64, dz = (int)((e >> 8) & 0xffu) - 64;
+        const int w = (int)(e >> 16);
+        const int rr = dy * dy + dz * dz;
+        const bool on_plane = dy == 0 || dz == 0;
+        const int jyz = (dy < 0 ? 2 : 0) | (dz < 0 ? 4 : 0);
+        walk_row(c0 + dz * plane + dy * pitch - w, w, [&](int t, uint32_t v) {
+            if (v == 0u) return;
+            const int dx = t - w;
+            const int rho = rho_of[dx * dx + rr];           // radius class ceil(|o|)
+            const int si = rho > J.r_min ? rho - J.r_min : 0;
+            uint32_t *base = cnt + si * B + (v - 1);
+            if (dx != 0 && !on_plane) {                     // inside one open octant
+                atomicAdd(base + (jyz | (dx < 0 ? 1 : 0)) * S * B, 1u);
+            } else {                                        // on a coordinate plane or axis
+                const int ax = dx > 0 ? 1 : (dx < 0 ? 2 : 3);
+                const int ay = dy > 0 ? 1 : (dy < 0 ? 2 : 3);
+                const int az = dz > 0 ? 1 : (dz < 0 ? 2 : 3);
+                uint32_t mult = 0;
+                for (int jz = 0; jz < 2; ++jz) {
+                    if (!(az & (1 << jz))) continue;
+                    for (int jy = 0; jy < 2; ++jy) {
+                        if (!(ay & (1 << jy))) continue;
+                        for (int jx = 0; jx < 2; ++jx) {
+                            if (!(ax & (1 << jx))) continue;
+                            atomicAdd(base + (jx | (jy << 1) | (jz << 2)) * S * B, 1u);
+                            ++mult;
+                        }
                     }
                 }
+                atomicAdd(extra + si * B + (v - 1), mult - 1u);
             }
-            atomicAdd(extra + si * B + (v - 1), mult - 1u);
-        }
+        });
     }
     __syncthreads();
     for (int col = threadIdx.x; col < 9 * B; col += blockDim.x) {    // 8 octants + excess
@@ -142,23 +153,41 @@ __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *
 // Alg. 1's update from the octant entropies hb[j*S + si]: eps_j = max over
 // scales (the smallest r on ties), d_j = k_j sigma_j, delta = sum_j eps_j
 // d_j / sum_j eps_j summed over j = 0..7, rounded half away from zero.
+// Called by warp 0: lane j < 8 finds eps_j and k_j, lane 0 forms the sums.
 __device__ void octant_step(const SeedJob &J, const double *hb, int step[3]) {
     const int S = J.S;
-    double num[3] = {0.0, 0.0, 0.0}, den = 0.0;
-    for (int j = 0; j < 8; ++j) {
-        double best = hb[j * S];
-        int k = J.r_min;
-        for (int si = 1; si < S; ++si)
-            if (hb[j * S + si] > best) {
-                best = hb[j * S + si];
+    const int lane = threadIdx.x & 31;
+    double best = 0.0;
+    int k = J.r_min;
+    if (lane < 8) {
+        best = hb[lane * S];
+        for (int si = 1; si < S; ++si) {
+            const double h = hb[lane * S + si];
+            if (h > best) {
+                best = h;
                 k = J.r_min + si;
             }
-        const int sg[3] = {(j & 1) ? -1 : 1, (j & 2) ? -1 : 1, (j & 4) ? -1 : 1};
-        for (int a = 0; a < 3; ++a)
-            num[a] = __dadd_rn(num[a], __dmul_rn(best, (double)(k * sg[a])));
-        den = __dadd_rn(den, best);
+        }
     }
-    for (int a = 0; a < 3; ++a) step[a] = den == 0.0 ? 0 : (int)round(__ddiv_rn(num[a], den));
+    double eps[8];
+    int kopt[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        eps[j] = __shfl_sync(0xffffffffu, best, j);
+        kopt[j] = __shfl_sync(0xffffffffu, k, j);
+    }
+    if (lane == 0) {
+        double num[3] = {0.0, 0.0, 0.0}, den = 0.0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int sg[3] = {(j & 1) ? -1 : 1, (j & 2) ? -1 : 1, (j & 4) ? -1 : 1};
+            for (int a = 0; a < 3; ++a)
+                num[a] = __dadd_rn(num[a], __dmul_rn(eps[j], (double)(kopt[j] * sg[a])));
+            den = __dadd_rn(den, eps[j]);
+        }
+        for (int a = 0; a < 3; ++a)
+            step[a] = den == 0.0 ? 0 : (int)round(__ddiv_rn(num[a], den));
+    }
 }
 
 // Kadir-Brady on the full ball at the centre of the last octant pass: the
@@ -214,7 +243,8 @@ __device__ void kb_from_pass(const SeedJob &J, const double *T, const double *L,
 }
 
 __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &ot,
-                            const double *T, const double *L, uint32_t *cnt, double *hb,
+                            const double *T, const double *L, const uint8_t *rho_of,
+                            uint32_t *cnt, double *hb,
                             SeedShared &sh) {
     const int dims[3] = {J.vol.nx, J.vol.ny, J.vol.nz};
     const int B = J.vol.B, S = J.S;
@@ -225,12 +255,12 @@ __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &
         for (int a = 0; a < 3; ++a) J.traj[(sidx * T1) * 3 + a] = P[a];
     int it = 0, conv = 0, fresh = 0;
     while (it < J.max_iter) {
-        octant_pass(J, ot, cnt, extra, P);
+        octant_pass(J, ot, cnt, extra, rho_of, P);
         fresh = 1;
         for (int w = threadIdx.x; w < 8 * S; w += blockDim.x)
             hb[w] = window_entropy(cnt + w * B, B, T, L, nullptr);
         __syncthreads();
-        if (threadIdx.x == 0) octant_step(J, hb, sh.step);
+        if (threadIdx.x < 32) octant_step(J, hb, sh.step);
         __syncthreads();
         ++it;
         int Pn[3];
@@ -248,7 +278,7 @@ __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &
     if (threadIdx.x == 0 && J.traj)
         for (int t = it + (conv ? 0 : 1); t <= J.max_iter; ++t)
             for (int a = 0; a < 3; ++a) J.traj[(sidx * T1 + t) * 3 + a] = P[a];
-    if (!fresh) octant_pass(J, ot, cnt, extra, P);     // the last pass was not at P
+    if (!fresh) octant_pass(J, ot, cnt, extra, rho_of, P);     // the last pass was not at P
     ks_seed_result *o = J.oct_out + sidx;
     kb_from_pass(J, T, L, cnt, extra, hb, sh, o);
     if (threadIdx.x == 0) {
@@ -267,10 +297,11 @@ __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &
 // ------------------------------------------------------------ mean shift
 // Packed accumulator word: count in bits [0,11), sum(dx+32) in [11,28),
 // sum(dy+32) in [28,45), sum(dz+32) in [45,62).  A column is shared by
-// 256 / NC threads; each thread adds at most ceil(|Ball(r)| / 256) words,
-// so a column sees at most 64 (NC = 32, |Ball| < 2048), 128 (NC = 64,
-// |Ball| < 8192) or 2 * 536 = 1072 (NC = 128, |Ball| <= 137065) voxels:
-// count < 2^11 and each offset sum <= 1072 * 64 < 2^17.  No field carries.
+// 256 / NC threads and a thread walks ceil(rows / 256) rows of at most
+// 2r+1 voxels, so a column sees at most 8*1*15 = 120 voxels (NC = 32,
+// r <= 7), 4*2*25 = 200 (NC = 64, r <= 12) or 2*13*65 = 1690 (NC = 128,
+// r <= 32, at most 3217 rows): count < 2^11 and each offset sum
+// <= 1690 * 64 < 2^17.  No field carries into the next.
 __device__ __forceinline__ int ms_columns(int nvox) {
     return nvox < 2048 ? 32 : (nvox < 8192 ? 64 : 128);
 }
@@ -283,23 +314,28 @@ __device__ __forceinline__ void red_add_shared_u64(uint32_t addr, unsigned long 
 __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long long *cols,
                         int *part, int *acc, const int P[3], int r) {
     const int B = J.vol.B;
-    const int n8 = __ldg(ot.c8_start + r + 1);
-    const int total = 8 * n8 + __ldg(ot.rest_start + r + 1);
-    const int NC = ms_columns(total);
+    const int NC = ms_columns(__ldg(ot.ball_size + r));
     for (int k = threadIdx.x; k < B * NC; k += blockDim.x) cols[k] = 0ull;
     __syncthreads();
     const uint8_t *c0 = voxel_ptr(J.vol, P);
     const int plane = (int)J.vol.plane, pitch = (int)J.vol.pitch;
     const uint32_t col_addr = smem_u32(cols + (threadIdx.x & (NC - 1)));
-    for (int w = threadIdx.x; w < total; w += blockDim.x) {
-        int dx, dy, dz, rho;
-        offset_of(ot, w, n8, dx, dy, dz, rho);
-        const uint32_t v = __ldg(c0 + dz * plane + dy * pitch + dx);
-        if (v == 0u) continue;
-        const unsigned long long inc = 1ull | ((unsigned long long)(dx + 32) << 11) |
-                                       ((unsigned long long)(dy + 32) << 28) |
-                                       ((unsigned long long)(dz + 32) << 45);
-        red_add_shared_u64(col_addr + (v - 1) * NC * 8, inc);
+    const uint32_t *rows = ot.rows + __ldg(ot.rows_start + r);
+    const int nrows = __ldg(ot.rows_start + r + 1) - __ldg(ot.rows_start + r);
+    // one x-row of Ball(r) per thread at a time; voxel t of a row has
+    // dx = t - w, so its packed word is the row's word plus t << 11
+    for (int ri = threadIdx.x; ri < nrows; ri += blockDim.x) {
+        const uint32_t e = __ldg(rows + ri);
+        const int dy = (int)(e & 0xffu) - 64, dz = (int)((e >> 8) & 0xffu) - 64;
+        const int w = (int)(e >> 16);
+        const unsigned long long row_inc = 1ull | ((unsigned long long)(32 - w) << 11) |
+                                           ((unsigned long long)(dy + 32) << 28) |
+                                           ((unsigned long long)(dz + 32) << 45);
+        walk_row(c0 + dz * plane + dy * pitch - w, w, [&](int t, uint32_t v) {
+            if (v != 0u)
+                red_add_shared_u64(col_addr + (v - 1) * NC * 8,
+                                   row_inc + ((unsigned long long)t << 11));
+        });
     }
     __syncthreads();
     // column sums: 8 partial sums per bin, then one thread per bin
@@ -340,28 +376,27 @@ __device__ void ms_step(const SeedJob &J, const int *acc, double *prod, SeedShar
         for (int b = threadIdx.x; b < B; b += 32) n += (uint32_t)acc[4 * b];
         for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
         const uint32_t N = n;
+        // Empty bins get products of +0.0: adding them leaves every partial
+        // sum unchanged (no sum is -0.0), so the loops below need no branch
+        // and still equal the sums over the occupied bins in bin order.
         for (int b = threadIdx.x; b < B; b += 32) {
             const int c = acc[4 * b];
             if (c > 0) {
                 const double w = __dsqrt_rn(__ddiv_rn((double)N, (double)((int64_t)B * c)));
                 for (int a = 0; a < 3; ++a) prod[a * B + b] = __dmul_rn(w, (double)acc[4 * b + 1 + a]);
                 prod[3 * B + b] = __dmul_rn(w, (double)c);
+            } else {
+                for (int a = 0; a < 4; ++a) prod[a * B + b] = 0.0;
             }
         }
         __syncwarp();
-        if (threadIdx.x == 0) {
-            if (N == 0) {
-                sh.step[0] = sh.step[1] = sh.step[2] = 0;
-            } else {
-                double num[3] = {0.0, 0.0, 0.0}, den = 0.0;
-                for (int b = 0; b < B; ++b) {
-                    if (acc[4 * b] == 0) continue;
-                    for (int a = 0; a < 3; ++a) num[a] = __dadd_rn(num[a], prod[a * B + b]);
-                    den = __dadd_rn(den, prod[3 * B + b]);
-                }
-                for (int a = 0; a < 3; ++a) sh.step[a] = (int)round(__ddiv_rn(num[a], den));
-            }
-        }
+        // lane a < 4 sums chain a (three numerators, the denominator)
+        double s = 0.0;
+        if (threadIdx.x < 4)
+            for (int b = 0; b < B; ++b) s = __dadd_rn(s, prod[threadIdx.x * B + b]);
+        const double den = __shfl_sync(0xffffffffu, s, 3);
+        if (threadIdx.x < 3)
+            sh.step[threadIdx.x] = N == 0 ? 0 : (int)round(__ddiv_rn(s, den));
     }
     __syncthreads();
 }
@@ -451,6 +486,12 @@ __global__ void __launch_bounds__(kSeedThreads) k_seeds(const SeedQueue q, const
                                                         int max_B, int max_S, int persistent) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ SeedShared sh;
+    __shared__ uint8_t rho_of[kRmax * kRmax + 1];    // ceil(sqrt(d2)) for d2 <= 32^2
+    for (int d2 = threadIdx.x; d2 <= kRmax * kRmax; d2 += blockDim.x) {
+        int r = 0;
+        while (r * r < d2) ++r;
+        rho_of[d2] = (uint8_t)r;
+    }
     const Layout lay(max_B, max_S);
     for (int64_t round = 0;; ++round) {
         if (threadIdx.x == 0)
@@ -465,7 +506,7 @@ __global__ void __launch_bounds__(kSeedThreads) k_seeds(const SeedQueue q, const
         const SeedJob &J = q.jobs[q.seg_job[seg]];
         const int64_t local = t - q.seg_start[seg];
         if (q.seg_kind[seg] == kOctant) {
-            octant_item(J, local, ot, T, L, reinterpret_cast<uint32_t *>(smem + lay.cnt),
+            octant_item(J, local, ot, T, L, rho_of, reinterpret_cast<uint32_t *>(smem + lay.cnt),
                         reinterpret_cast<double *>(smem + lay.hb), sh);
         } else {
             // largest radius first: ticket -> (seed, r)
