@@ -306,6 +306,12 @@ def run_ks(args):
             "clocks": clocks,
             "peaks_source": peak_kind,
         }
+    if rank == 0 and not args.no_extras:
+        # short forms of the batched and serving workloads (full sizes:
+        # --mode batch / --mode serve)
+        line["config"]["batched"] = run_batched(ctx, ks, synth, count=64, max_dim=128, reps=2)
+        line["config"]["serving"] = run_serving(ks.Context, ks, synth, rate=50.0, count=120,
+                                                pool=12, max_dim=96)
     if rank == 0 and not args.no_cpu_baseline:
         v_cpu, threads, desc, dt = oracle_sample(w, budget_s=args.ref_budget)
         line["cpu_baseline"] = {"value": v_cpu, "unit": "window-entropies/s", "cores": threads,
@@ -356,6 +362,156 @@ def run_case(args):
     return 0
 
 
+def run_batched(ctx, ks, synth, count=64, max_dim=None, reps=3):
+    """Batched form: `count` uneven volumes (uint8 spheres / int16 MR-like),
+    octant climb + mean shift for every grid seed of every volume, as one
+    persistent graph-captured launch vs one plain launch pair per volume.
+    Both produce host results.  Returns a dict of volumes/s and timings."""
+    import torch
+    ws = synth.batch_volumes(seed=3, count=count, max_dim=max_dim)
+    vols = [ctx.create_volume(w.volume, w.binning) for w in ws]
+    ps = [ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter) for w in ws]
+    ctx.batch_seeds(vols, ps, kinds=3, use_graph=True)          # capture + warm
+    for v, p in zip(vols, ps):
+        ctx.seed_climb(v, p)
+        ctx.meanshift(v, p)
+    plain, batched = [], []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        outs = [(ctx.seed_climb(v, p), ctx.meanshift(v, p)) for v, p in zip(vols, ps)]
+        torch.cuda.synchronize()
+        plain.append(time.perf_counter() - t)
+        t = time.perf_counter()
+        octs, mss = ctx.batch_seeds(vols, ps, kinds=3, use_graph=True)
+        torch.cuda.synchronize()
+        batched.append(time.perf_counter() - t)
+    same = all(np.array_equal(o[0], a) and np.array_equal(o[1], b)
+               for o, a, b in zip(outs, octs, mss))
+    we = 0
+    for (o, m), p in zip(outs, ps):
+        S = p.r_max - p.r_min + 1
+        we += int(o["iters"].sum()) * 8 * S + len(o) * S + int(m["iters"].sum()) + \
+            int((m["converged"] == 0).sum())
+    for v in vols:
+        ctx.release_volume(v)
+    tp, tb = min(plain), min(batched)
+    return {"volumes": count, "max_dim": max_dim or 256, "seeds": int(sum(len(o[0]) for o in outs)),
+            "window_entropies": we, "plain_s": tp, "batched_s": tb,
+            "volumes_per_s_plain": count / tp, "volumes_per_s_batched": count / tb,
+            "window_entropies_per_s_batched": we / tb, "speedup": tp / tb,
+            "identical_results": bool(same)}
+
+
+def run_serving(ctx_factory, ks, synth, rate=50.0, count=200, pool=24, max_dim=None,
+                dense_frac=0.3, seed=4):
+    """Serving form: a Poisson stream of `count` requests at `rate`/s, each a
+    volume from a pool drawn like the batched form, asking for both seed
+    schemes (70%) or the dense sweep (30%), replayed in real time against
+    the continuous-batching loop (ks_submit / ks_poll).  The plain
+    sequential path (one request at a time through the synchronous calls,
+    queueing in arrival order) is timed on the same requests.  Returns p50/p99
+    latency and volumes/s for both."""
+    import threading
+    reqs = synth.request_stream(seed=seed, count=count, rate=rate, dense_frac=dense_frac)
+    ws = synth.batch_volumes(seed=seed + 100, count=pool, max_dim=max_dim)
+    kinds = [ks.KS_REQ_DENSE if r["kind"] == "dense" else ks.KS_REQ_SEEDS for r in reqs]
+    picks = [r["vol_seed"] % pool for r in reqs]
+    ctx = ctx_factory()
+    # warm-up (autotuner, graph of nothing): one of each kind per pool entry type
+    for i in range(min(pool, 4)):
+        w = ws[i]
+        for k in (ks.KS_REQ_SEEDS, ks.KS_REQ_DENSE):
+            rid = ctx.submit(w.volume, w.binning,
+                             ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter), kind=k)
+            ctx.poll(rid, -1)
+            ctx.release_result(rid)
+    ids = [None] * count
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            now = time.perf_counter() - t0
+            if r["t"] > now:
+                time.sleep(r["t"] - now)
+            w = ws[picks[i]]
+            ids[i] = ctx.submit(w.volume, w.binning,
+                                ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter),
+                                kind=kinds[i])
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    lat = []
+    t_first, t_last = None, 0.0
+    for i in range(count):
+        st, res = ctx.poll(ids[i], -1)
+        assert st == ks.KS_OK, st
+        lat.append((res["t_done_us"] - res["t_submit_us"]) * 1e-3)
+        t_first = res["t_submit_us"] if t_first is None else min(t_first, res["t_submit_us"])
+        t_last = max(t_last, res["t_done_us"])
+        ctx.release_result(ids[i])
+    span = (t_last - t_first) * 1e-6
+    ctx.close()
+    # plain sequential path: service time of each request alone, then an
+    # arrival-order queue
+    ctx = ctx_factory()
+    service = {}
+    for i in range(count):
+        key = (picks[i], kinds[i])
+        if key in service:
+            continue
+        w = ws[picks[i]]
+        p = ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter)
+        for rep in range(2):
+            import torch
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            v = ctx.create_volume(w.volume, w.binning)
+            if kinds[i] == ks.KS_REQ_DENSE:
+                ctx.dense_saliency(v, p, w.volume.shape)
+            else:
+                ctx.seed_climb(v, p)
+                ctx.meanshift(v, p)
+            ctx.release_volume(v)
+            service[key] = time.perf_counter() - t
+    ctx.close()
+    finish, seq_lat = 0.0, []
+    for i, r in enumerate(reqs):
+        finish = max(finish, r["t"]) + service[(picks[i], kinds[i])]
+        seq_lat.append((finish - r["t"]) * 1e3)
+    seq_span = finish - reqs[0]["t"]
+    return {"rate_per_s": rate, "requests": count, "pool_volumes": pool,
+            "max_dim": max_dim or 256, "dense_fraction": dense_frac,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "volumes_per_s": count / span,
+            "sequential_p50_ms": float(np.percentile(seq_lat, 50)),
+            "sequential_p99_ms": float(np.percentile(seq_lat, 99)),
+            "sequential_volumes_per_s": count / seq_span}
+
+
+def run_mode(args):
+    import torch
+    from paper_1310_6736_b300 import build, ks, synth
+    build.build()
+    torch.cuda.set_device(0)
+    if args.mode == "batch":
+        ctx = ks.Context()
+        r = run_batched(ctx, ks, synth, count=args.count, max_dim=args.max_dim or None)
+        ctx.close()
+        line = {"metric": "volumes/s (batched vs plain)", "value": r["volumes_per_s_batched"],
+                "unit": "volumes/s", "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+                "config": {"workload": "batch of uneven uint8/int16 volumes", **r}}
+    else:
+        rows = [run_serving(ks.Context, ks, synth, rate=rate, count=args.count,
+                            max_dim=args.max_dim or None) for rate in args.rates]
+        line = {"metric": "p50/p99 latency and volumes/s (continuous batching vs sequential)",
+                "value": rows[0]["p50_ms"], "unit": "ms (p50)", "higher_is_better": False,
+                "n_gpus": 1, "data": "synthetic", "config": {"serving": rows}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def ks_ball_size(r):
     d = np.arange(-r, r + 1)
     return int(((d[:, None, None] ** 2 + d[None, :, None] ** 2 + d[None, None, :] ** 2)
@@ -375,11 +531,20 @@ def main():
                     help="run one part of the step only (profiling)")
     ap.add_argument("--dense-config", default="",
                     help="force the dense launch shape: path,warps,tile_y,tile_z")
+    ap.add_argument("--mode", choices=["step", "batch", "serve"], default="step",
+                    help="batch: batched vs plain launches; serve: request-stream latency")
+    ap.add_argument("--count", type=int, default=64, help="volumes (batch) or requests (serve)")
+    ap.add_argument("--max-dim", type=int, default=0, help="cap on each volume dimension")
+    ap.add_argument("--rates", type=float, nargs="+", default=[20.0, 50.0, 100.0])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="step mode: skip the short batched and serving measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.case:
         return run_case(args)
+    if args.mode != "step":
+        return run_mode(args)
     return run_ks(args)
 
 

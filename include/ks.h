@@ -284,6 +284,14 @@ int ks_dense_config(ks_ctx *ctx, int bins, int r_max, int *path, int *warps,
  * that call. */
 int ks_force_dense_config(int path, int warps, int tile_y, int tile_z);
 
+/* Failure-detection self-test: one thread waits on a device barrier that
+ * nothing will complete, gives up after `polls` polls (1..2^20), records
+ * the timeout in the context's status word and exits -- the same bounded
+ * wait the dense kernel uses for its TMA brick.  Returns KS_ETIMEDOUT (the
+ * status the host reads back); the context stays usable and the next
+ * ks_sync returns KS_OK.  The paper has no counterpart. */
+int ks_selftest_wait_timeout(ks_ctx *ctx, int polls);
+
 /* ------------------------------------------------ allocation-free binning */
 
 /* The float32 binning of ks_create_volume (KS_BIN_AFFINE_F32) for callers

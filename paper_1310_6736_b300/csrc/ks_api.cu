@@ -476,6 +476,76 @@ static int check_status(Ctx *c) {
 using namespace ks;
 
 namespace ks {
+// at most one class per segment; a class is 4 arrays, each 256-byte aligned
+size_t plan_bytes_bound(size_t n_segs) { return 2048 + n_segs * (4 * 256 + 32); }
+
+std::vector<ClassLaunch> plan_class_queues(Ctx *c, const std::vector<SeedJob> &jobs,
+                                           const SeedJob *dev_jobs,
+                                           const std::vector<std::pair<int, int>> &segs,
+                                           std::vector<uint8_t> &image, size_t plan_at,
+                                           uint8_t *dev_base) {
+    // classes in order of first appearance
+    std::vector<std::pair<int, int>> keys;
+    std::vector<std::vector<int>> members;
+    for (size_t s = 0; s < segs.size(); ++s) {
+        const SeedJob &J = jobs[segs[s].first];
+        const std::pair<int, int> k{J.vol.B, J.S};
+        size_t ci = 0;
+        while (ci < keys.size() && keys[ci] != k) ++ci;
+        if (ci == keys.size()) {
+            keys.push_back(k);
+            members.emplace_back();
+        }
+        members[ci].push_back((int)s);
+    }
+    std::vector<ClassLaunch> out;
+    size_t off = plan_at;
+    auto put = [&](const void *src, size_t n) {
+        const size_t at = off;
+        if (image.size() < at + n) image.resize(at + n, 0);
+        if (n) std::memcpy(image.data() + at, src, n);
+        off = (at + n + 255) / 256 * 256;
+        return dev_base + at;
+    };
+    for (size_t ci = 0; ci < keys.size(); ++ci) {
+        std::vector<int64_t> ss{0};
+        std::vector<int> sk, sj;
+        for (int s : members[ci]) {
+            const int job = segs[s].first, kind = segs[s].second;
+            ss.push_back(ss.back() + seed_tickets(kind, jobs[job].n_seeds, jobs[job].S));
+            sk.push_back(kind);
+            sj.push_back(job);
+        }
+        ClassLaunch L{};
+        const unsigned long long zero = 0;
+        L.q.head = (unsigned long long *)put(&zero, sizeof(zero));
+        L.q.jobs = dev_jobs;
+        L.q.seg_start = (const int64_t *)put(ss.data(), ss.size() * 8);
+        L.q.seg_kind = (const int *)put(sk.data(), sk.size() * 4);
+        L.q.seg_job = (const int *)put(sj.data(), sj.size() * 4);
+        L.q.n_segs = (int)sk.size();
+        L.q.n_tickets = ss.back();
+        L.max_B = keys[ci].first;
+        L.max_S = keys[ci].second;
+        L.grid = c->num_sms * seed_blocks_per_sm(L.max_B, L.max_S);
+        out.push_back(L);
+    }
+    return out;
+}
+
+cudaError_t launch_class_queues(Ctx *c, cudaStream_t s, int *d_status,
+                                const std::vector<ClassLaunch> &cls) {
+    for (const ClassLaunch &L : cls) {
+        if (L.q.n_tickets == 0) continue;
+        cudaError_t e = cudaMemsetAsync(L.q.head, 0, 8, s);
+        if (e == cudaSuccess)
+            e = launch_seeds(LaunchCtx{s, d_status, c->num_sms}, L.q, c->ot, c->T, c->L, L.max_B,
+                             L.max_S, true, L.grid);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 struct BatchGraph {
     std::vector<int64_t> key;
     cudaGraphExec_t exec = nullptr;
@@ -484,9 +554,7 @@ struct BatchGraph {
     size_t oct_off = 0, ms_off = 0;
     std::vector<int64_t> n_oct, n_ms;
     std::vector<size_t> oct_at, ms_at;
-    int max_B = 0, max_S = 0;
-    SeedQueue q{};
-    int grid = 0;
+    std::vector<ClassLaunch> classes;
 };
 }  // namespace ks
 static std::mutex g_graph_mu;
@@ -894,18 +962,14 @@ int ks_batch_seeds(ks_ctx *ctx, const ks_vol *vols, const ks_params *params, int
             nb->ms_at.push_back(ms_bytes);
             oct_bytes += nb->n_oct.back() * sizeof(ks_seed_result);
             ms_bytes += nb->n_ms.back() * sizeof(ks_ms_result);
-            nb->max_B = std::max(nb->max_B, vs[i]->binning.bins);
-            nb->max_S = std::max(nb->max_S, S);
         }
         std::vector<SeedJob> jobs(n_vols);
-        std::vector<int64_t> ss{0};
-        std::vector<int> sk, sj;
         const size_t jobs_at = 0, seg_at = (n_vols * sizeof(SeedJob) + 255) / 256 * 256;
-        const size_t segs_bytes = (2 * n_vols + 1) * 8 + 2 * (2 * n_vols) * 4 + 64;
+        const size_t segs_bytes = plan_bytes_bound(2 * (size_t)n_vols);
         const size_t seeds_at = seg_at + (segs_bytes + 255) / 256 * 256;
         nb->oct_off = seeds_at + (seed_bytes + 255) / 256 * 256;
         nb->ms_off = nb->oct_off + (oct_bytes + 255) / 256 * 256;
-        nb->bytes = nb->ms_off + ms_bytes + 256 + 256;   // + head counter
+        nb->bytes = nb->ms_off + ms_bytes + 256;
         void *p;
         cudaError_t e = dev_alloc(c, &p, nb->bytes);
         if (e != cudaSuccess) return cuda_err(c, e, "batch buffers");
@@ -929,40 +993,24 @@ int ks_batch_seeds(ks_ctx *ctx, const ks_vol *vols, const ks_params *params, int
             J.traj = nullptr;
             so += (seeds[i].size() * 4 + 15) / 16 * 16;
         }
-        // octant segments first (the longest items), then mean shift
+        // octant segments first (the longest items), then mean shift; one
+        // persistent launch per (bins, scales) class
+        std::vector<std::pair<int, int>> segs;
         for (int kind = 0; kind < 2; ++kind)
-            for (int i = 0; i < n_vols; ++i) {
-                const int64_t n = kind == 0 ? nb->n_oct[i] : nb->n_ms[i];
-                if (!n) continue;
-                ss.push_back(ss.back() + seed_tickets(kind == 0 ? kOctant : kMeanShift,
-                                                      jobs[i].n_seeds, jobs[i].S));
-                sk.push_back(kind == 0 ? kOctant : kMeanShift);
-                sj.push_back(i);
-            }
+            for (int i = 0; i < n_vols; ++i)
+                if (kind == 0 ? nb->n_oct[i] : nb->n_ms[i])
+                    segs.push_back({i, kind == 0 ? kOctant : kMeanShift});
         std::memcpy(host.data() + jobs_at, jobs.data(), n_vols * sizeof(SeedJob));
-        size_t o = seg_at;
-        std::memcpy(host.data() + o, ss.data(), ss.size() * 8);
-        SeedQueue q{};
-        q.jobs = (const SeedJob *)(m + jobs_at);
-        q.seg_start = (const int64_t *)(m + o);
-        o += (ss.size() * 8 + 15) / 16 * 16;
-        std::memcpy(host.data() + o, sk.data(), sk.size() * 4);
-        q.seg_kind = (const int *)(m + o);
-        o += (sk.size() * 4 + 15) / 16 * 16;
-        std::memcpy(host.data() + o, sj.data(), sj.size() * 4);
-        q.seg_job = (const int *)(m + o);
-        q.n_segs = (int)sk.size();
-        q.n_tickets = ss.back();
-        q.head = (unsigned long long *)(m + nb->bytes - 256);
+        // the plan fits [seg_at, seeds_at): plan_bytes_bound(2 n_vols) was reserved
+        nb->classes = plan_class_queues(c, jobs, (const SeedJob *)(m + jobs_at), segs, host,
+                                        seg_at, m);
         KS_TRY_CUDA(c, cudaMemcpyAsync(m, host.data(), host.size(), cudaMemcpyHostToDevice,
                                        c->stream));
         KS_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
-        // capture [reset head; persistent launch] as a graph
-        const int grid = c->num_sms * seed_blocks_per_sm(nb->max_B, nb->max_S);
+        // capture [reset heads; persistent launches] as a graph
         cudaGraph_t graph;
         KS_TRY_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        cudaMemsetAsync(q.head, 0, 8, c->stream);
-        cudaError_t le = launch_seeds(c->lc(), q, c->ot, c->T, c->L, nb->max_B, nb->max_S, true, grid);
+        cudaError_t le = launch_class_queues(c, c->stream, c->d_status, nb->classes);
         e = cudaStreamEndCapture(c->stream, &graph);
         if (le != cudaSuccess) e = le;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&nb->exec, graph, 0);
@@ -971,8 +1019,6 @@ int ks_batch_seeds(ks_ctx *ctx, const ks_vol *vols, const ks_params *params, int
             dev_free(c, nb->mem, nb->bytes);
             return cuda_err(c, e, "batch graph");
         }
-        nb->q = q;                      // kept for the direct (non-graph) launch
-        nb->grid = grid;
         bg = nb.get();
         std::lock_guard<std::mutex> g(g_graph_mu);
         g_graphs[c].push_back(std::move(nb));
@@ -982,9 +1028,7 @@ int ks_batch_seeds(ks_ctx *ctx, const ks_vol *vols, const ks_params *params, int
     if (use_graph) {
         KS_TRY_CUDA(c, cudaGraphLaunch(bg->exec, c->stream));
     } else {
-        KS_TRY_CUDA(c, cudaMemsetAsync(bg->q.head, 0, 8, c->stream));
-        KS_TRY_CUDA(c, launch_seeds(c->lc(), bg->q, c->ot, c->T, c->L, bg->max_B, bg->max_S, true,
-                                    bg->grid));
+        KS_TRY_CUDA(c, launch_class_queues(c, c->stream, c->d_status, bg->classes));
     }
     prof_end(c, &rec, c->stream);
     for (int i = 0; i < n_vols; ++i) {
@@ -1088,6 +1132,14 @@ int ks_dense_config(ks_ctx *ctx, int bins, int r_max, int *path, int *warps, int
             return KS_OK;
         }
     return KS_ENOTFOUND;
+}
+
+int ks_selftest_wait_timeout(ks_ctx *ctx, int polls) {
+    if (!ctx || polls < 1 || polls > (1 << 20)) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    c->launches++;
+    KS_TRY_CUDA(c, launch_wait_selftest(c->lc(), polls));
+    return check_status(c);
 }
 
 // Force the dense launch configuration for every context (path < 0: back

@@ -100,6 +100,24 @@ int run_dense(Ctx *c, cudaStream_t s, Volume *v, const ks_params *p, const Dense
               int z0, int z1);
 void serve_shutdown(Ctx *c);
 
+// Persistent seed launches grouped by (bins, scales): each class gets its
+// own ticket queue and a shared-memory layout sized for it alone.
+struct ClassLaunch {
+    SeedQueue q;
+    int max_B, max_S, grid;
+};
+size_t plan_bytes_bound(size_t n_segs);
+// segs: (job index, kind) pairs in processing order.  Writes each class's
+// head counter and segment arrays into `image` from offset plan_at on; the
+// returned queues point into dev_base (the device copy of `image`).
+std::vector<ClassLaunch> plan_class_queues(Ctx *c, const std::vector<SeedJob> &jobs,
+                                           const SeedJob *dev_jobs,
+                                           const std::vector<std::pair<int, int>> &segs,
+                                           std::vector<uint8_t> &image, size_t plan_at,
+                                           uint8_t *dev_base);
+cudaError_t launch_class_queues(Ctx *c, cudaStream_t s, int *d_status,
+                                const std::vector<ClassLaunch> &cls);
+
 }  // namespace ks
 
 struct ks_ctx {

@@ -298,6 +298,25 @@ cudaError_t launch_b(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap 
 
 }  // namespace
 
+// Exercises the bounded-wait path: thread 0 waits on an mbarrier that no
+// copy will ever complete, gives up after `polls` polls, records the
+// timeout in the status word and returns, exactly as k_dense does when its
+// brick does not arrive.
+__global__ void k_wait_selftest(int *status, int polls) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        const uint32_t mbar = smem_u32(&bar);
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+        if (!mbar_wait_bounded(mbar, 0, polls)) atomicOr(status, kStatusTmaTimeout);
+    }
+}
+
+cudaError_t launch_wait_selftest(const LaunchCtx &lc, int polls) {
+    k_wait_selftest<<<1, 32, 0, lc.stream>>>(lc.d_status, polls);
+    return cudaGetLastError();
+}
+
 int ball_size_host(int r) {
     int n = 0;
     for (int dz = -r; dz <= r; ++dz)

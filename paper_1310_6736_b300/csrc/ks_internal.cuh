@@ -173,6 +173,8 @@ struct DenseOut {
     double *H;     // optional, voxel-major x S
     double *W;     // optional
 };
+// Bounded-wait self-test (see ks_selftest_wait_timeout).
+cudaError_t launch_wait_selftest(const LaunchCtx &lc, int polls);
 // The classes rho <= dense_const_rmax() of both parts of the offset tables
 // also live in the dense kernel's constant memory.
 cudaError_t dense_upload_constant_table(const uint32_t *c8, const int *c8_start,

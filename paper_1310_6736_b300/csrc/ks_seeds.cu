@@ -528,9 +528,12 @@ int64_t seed_tickets(int kind, int64_t n_seeds, int S) {
 size_t seed_smem_bytes(int B, int S) { return Layout(B, S).total(); }
 
 int seed_blocks_per_sm(int max_B, int max_S) {
+    // the occupancy query honours the kernel's dynamic shared-memory limit,
+    // so raise it to this layout's size first
+    const size_t smem = seed_smem_bytes(max_B, max_S);
+    cudaFuncSetAttribute(k_seeds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seeds, kSeedThreads,
-                                                  seed_smem_bytes(max_B, max_S));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seeds, kSeedThreads, smem);
     return n < 1 ? 1 : n;
 }
 

@@ -71,7 +71,8 @@ struct ServeState {
     int64_t next_id = 1;
     bool stop = false;
     std::thread th;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;       // uploads, binning, seed waves
+    cudaStream_t stream2 = nullptr;      // dense slabs, concurrent with the seeds
     int *d_status = nullptr;
     size_t reserved = 0;
     void *qmem = nullptr;
@@ -161,11 +162,13 @@ static int setup(Ctx *c, ServeState *S, Request *r) {
     return KS_OK;
 }
 
-// Dense slab height for one wave: about 4e9 window-voxel updates.
+// Dense slab height for one wave: about 3e10 window-voxel updates (roughly
+// 12 ms of the dense kernel), so a large sweep advances in a few waves while
+// requests that arrive meanwhile still join within one slab's time.
 static int dense_slab(const Request *r) {
     const ks_request &q = r->desc;
     const double per_plane = (double)q.nx * q.ny * ball_size_host(q.params.r_max);
-    int planes = (int)std::max(1.0, 4e9 / per_plane);
+    int planes = (int)std::max(1.0, 3e10 / per_plane);
     return std::min(planes, q.nz);
 }
 
@@ -205,9 +208,7 @@ static void retire(Ctx *c, ServeState *S, Request *r) {
 
 static int launch_wave_seeds(Ctx *c, ServeState *S, std::vector<Request *> &joiners) {
     std::vector<SeedJob> jobs;
-    std::vector<int64_t> ss{0};
-    std::vector<int> sk, sj;
-    int max_B = 2, max_S = 1;
+    std::vector<std::pair<int, int>> segs;
     for (Request *r : joiners) {
         const ks_request &q = r->desc;
         SeedJob J{};
@@ -224,21 +225,12 @@ static int launch_wave_seeds(Ctx *c, ServeState *S, std::vector<Request *> &join
         J.traj = nullptr;
         const int ji = (int)jobs.size();
         jobs.push_back(J);
-        max_B = std::max(max_B, q.binning.bins);
-        max_S = std::max(max_S, J.S);
-        if ((q.seed_kinds & 1) && r->n_seeds) {
-            ss.push_back(ss.back() + seed_tickets(kOctant, r->n_seeds, J.S));
-            sk.push_back(kOctant);
-            sj.push_back(ji);
-        }
-        if ((q.seed_kinds & 2) && r->n_items) {
-            ss.push_back(ss.back() + seed_tickets(kMeanShift, r->n_seeds, J.S));
-            sk.push_back(kMeanShift);
-            sj.push_back(ji);
-        }
+        if ((q.seed_kinds & 1) && r->n_seeds) segs.push_back({ji, kOctant});
+        if ((q.seed_kinds & 2) && r->n_items) segs.push_back({ji, kMeanShift});
     }
-    if (sk.empty()) return KS_OK;
-    const size_t need = 256 + jobs.size() * sizeof(SeedJob) + ss.size() * 8 + sk.size() * 8 + 256;
+    if (segs.empty()) return KS_OK;
+    const size_t jobs_bytes = (jobs.size() * sizeof(SeedJob) + 255) / 256 * 256;
+    const size_t need = jobs_bytes + plan_bytes_bound(segs.size());
     if (S->qbytes < need) {
         cudaStreamSynchronize(S->stream);
         dev_free(c, S->qmem, S->qbytes);
@@ -250,30 +242,16 @@ static int launch_wave_seeds(Ctx *c, ServeState *S, std::vector<Request *> &join
         S->qmem = p;
         S->qbytes = need * 2;
     }
-    std::vector<uint8_t> h(need, 0);
+    std::vector<uint8_t> h(jobs_bytes, 0);
     uint8_t *m = (uint8_t *)S->qmem;
-    size_t off = 256;
-    auto put = [&](const void *src, size_t n) {
-        const size_t at = off;
-        std::memcpy(h.data() + at, src, n);
-        off += (n + 15) / 16 * 16;
-        return m + at;
-    };
-    SeedQueue q{};
-    q.jobs = (const SeedJob *)put(jobs.data(), jobs.size() * sizeof(SeedJob));
-    q.seg_start = (const int64_t *)put(ss.data(), ss.size() * 8);
-    q.seg_kind = (const int *)put(sk.data(), sk.size() * 4);
-    q.seg_job = (const int *)put(sj.data(), sj.size() * 4);
-    q.n_segs = (int)sk.size();
-    q.n_tickets = ss.back();
-    q.head = (unsigned long long *)m;
-    cudaError_t e = cudaMemcpyAsync(m, h.data(), off, cudaMemcpyHostToDevice, S->stream);
+    std::memcpy(h.data(), jobs.data(), jobs.size() * sizeof(SeedJob));
+    const std::vector<ClassLaunch> cls =
+        plan_class_queues(c, jobs, (const SeedJob *)m, segs, h, jobs_bytes, m);
+    cudaError_t e = cudaMemcpyAsync(m, h.data(), h.size(), cudaMemcpyHostToDevice, S->stream);
     if (e != cudaSuccess) return cuda_err(c, e, "serving queue upload");
-    const int grid = c->num_sms * seed_blocks_per_sm(max_B, max_S);
     ProfRec rec;
     prof_begin(c, "ks_seeds_persistent", S->stream, &rec);
-    e = launch_seeds(LaunchCtx{S->stream, S->d_status, c->num_sms}, q, c->ot, c->T, c->L, max_B,
-                     max_S, true, grid);
+    e = launch_class_queues(c, S->stream, S->d_status, cls);
     prof_end(c, &rec, S->stream);
     return cuda_err(c, e, "serving seed wave");
 }
@@ -331,10 +309,12 @@ static void scheduler(Ctx *c) {
             const int z0 = r->dense_next_z, z1 = std::min(r->desc.nz, z0 + dense_slab(r));
             if (z0 >= z1) continue;
             const DenseOut o{r->d_Y, r->d_s, nullptr, nullptr};
-            r->status = run_dense(c, S->stream, r->v, &r->desc.params, o, z0, z1);
+            r->status = run_dense(c, S->stream2, r->v, &r->desc.params, o, z0, z1);
             r->dense_next_z = z1;
         }
         cudaError_t e = cudaStreamSynchronize(S->stream);
+        const cudaError_t e2 = cudaStreamSynchronize(S->stream2);
+        if (e == cudaSuccess) e = e2;
         int h = 0;
         if (e == cudaSuccess) e = cudaMemcpy(&h, S->d_status, 4, cudaMemcpyDeviceToHost);
         S->waves++;
@@ -363,9 +343,14 @@ static ServeState *ensure_serve(Ctx *c) {
     if (c->serve) return c->serve;
     auto S = std::make_unique<ServeState>();
     if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    if (cudaStreamCreateWithFlags(&S->stream2, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamDestroy(S->stream);
+        return nullptr;
+    }
     void *p;
     if (cudaMalloc(&p, 256) != cudaSuccess) {
         cudaStreamDestroy(S->stream);
+        cudaStreamDestroy(S->stream2);
         return nullptr;
     }
     cudaMemset(p, 0, 256);
@@ -385,10 +370,12 @@ void serve_shutdown(Ctx *c) {
     S->cv_work.notify_all();
     if (S->th.joinable()) S->th.join();
     cudaStreamSynchronize(S->stream);
+    cudaStreamSynchronize(S->stream2);
     for (auto &kv : S->all) free_device(c, kv.second.get());
     dev_free(c, S->qmem, S->qbytes);
     cudaFree(S->d_status);
     cudaStreamDestroy(S->stream);
+    cudaStreamDestroy(S->stream2);
     delete S;
     c->serve = nullptr;
 }

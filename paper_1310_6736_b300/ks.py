@@ -96,6 +96,7 @@ SIGNATURES = {
                              C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ks_force_dense_config": (_I, [_I, _I, _I, _I]),
     "ks_bin_f32_noalloc": (_I, [_P, _I, _I, _I, _I, _P, _P]),
+    "ks_selftest_wait_timeout": (_I, [_P, _I]),
 }
 
 _lib = None
