@@ -272,14 +272,16 @@ int ks_kernel_time(ks_ctx *ctx, const char *prefix, double *ms_total, int64_t *l
 int ks_measure_smem_peak(ks_ctx *ctx, double *increments_per_s);
 
 /* Dense-sweep launch configuration chosen for (bins, r_max) by the
- * autotuner: path 0 = TMA brick in shared memory, 1 = direct L2 reads;
- * warps per block; tile rows in y and z. */
+ * autotuner: path 0 = TMA brick in shared memory, 1 = direct L2 reads,
+ * 2 = direct L2 reads with two centres (x and x + 32) per thread; warps per
+ * block; tile rows in y and z. */
 int ks_dense_config(ks_ctx *ctx, int bins, int r_max, int *path, int *warps,
                     int *tile_y, int *tile_z);
 
 /* Force the dense launch configuration for every context of the process
  * (tests use it to cover both paths); path < 0 returns to the autotuner.
- * KS_EINVAL: path > 1, warps outside [1, 16] or tile_y * tile_z != warps.
+ * KS_EINVAL: path > 2, warps outside [1, 16] ([1, 8] for path 2) or
+ * tile_y * tile_z != warps.
  * A forced shape that does not fit a given (bins, r_max) is ignored for
  * that call. */
 int ks_force_dense_config(int path, int warps, int tile_y, int tile_z);

@@ -9,6 +9,12 @@
 //            memory by one TMA 3D tile load (out-of-range voxels arrive as
 //            0 = not counted); PATH 1 = bins are read through L1/L2 straight
 //            from the halo-padded volume.  The autotuner picks per shape.
+//   CPL    = centres per lane on PATH 1 (launch path 2 = two): with two, a
+//            warp covers 64 centres of a row (lane l: x0 + l and x0 + l + 32)
+//            so one table decode and one address serve two loads that differ
+//            by an immediate.  Centres past nx are evaluated (their reads stay
+//            inside the zeroed halo and the allocation's slack) but not
+//            written.
 //   scale  = built incrementally: shell r (offsets o with ceil|o| == r, and
 //            everything up to r_min for the first scale) is added to the
 //            counts of r-1.
@@ -18,15 +24,16 @@
 //            offset on a coordinate plane or axis, stored with its signs.
 //            For r_max <= 25 the tables sit in constant memory (warp-uniform
 //            reads through the constant cache), beyond that in global memory.
-//   counts = each lane owns a column of 32-bit words in shared memory
+//   counts = each centre owns a column of 32-bit words in shared memory
 //            (word v at +128 v bytes, so the 32 lanes of a warp always hit
 //            32 different banks), one word per stored value v = 0..B;
 //            v = 0 (not counted) is a dummy word, so the update has no
 //            branch: it is one shared-memory reduction (red.shared.add).
-//   FP64   = after each shell one pass over the lane's counters computes the
-//            bin-order entropy sum and the exact integer D of W against the
-//            previous scale's counts (a second column of the same layout,
-//            refreshed in the same pass).  W and Y are evaluated only at
+//   FP64   = after each shell one pass over the centre's counters computes
+//            the bin-order entropy sum and the exact integer D of W against
+//            the previous scale's counts (words after the counters, refreshed
+//            in the same pass; two 16-bit counts per word when every count
+//            fits, |Ball(25)| = 65267).  W and Y are evaluated only at
 //            entropy peaks.
 #include <type_traits>
 
@@ -87,24 +94,33 @@ struct Src<0> {              // brick in shared memory, byte offsets from smem
 };
 template <>
 struct Src<1> {              // halo-padded volume in global memory
-    const uint8_t *vol;
-    __device__ __forceinline__ uint32_t at(int64_t base, int off) const {
-        return __ldg(vol + (base + off));
+    __device__ __forceinline__ uint32_t at(const uint8_t *p, int off) const {
+        return __ldg(p + off);
     }
 };
 
-template <int B, bool WIDE, int PATH>
-__global__ void __launch_bounds__(512) k_dense(const DenseArgs a,
-                                               const __grid_constant__ CUtensorMap tmap) {
+// Counter words of one centre: NW 32-bit counters (stored values 0..B),
+// then the previous scale's counts, as 16-bit pairs when every count fits
+// (|Ball(r_max)| <= 65535, i.e. r_max <= 25) and as 32-bit words otherwise.
+template <int B, bool WIDE>
+struct Words {
+    static constexpr int kNW = B + 1;
+    static constexpr int kNP = WIDE ? B + 1 : (B + 2) / 2;
+    static constexpr int kPerCentre = kNW + kNP;
+};
+
+template <int B, bool WIDE, int PATH, int CPL>
+__global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
+    k_dense(const DenseArgs a, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ int s_ok;
     constexpr bool CTAB = !WIDE;                 // r_max <= 25: table in constant memory
-    constexpr int NW = B + 1;                    // counter words per lane
-    constexpr int NPREV = NW;                    // previous-scale words
+    constexpr int NW = Words<B, WIDE>::kNW;      // counter words per centre
+    constexpr int NP = Words<B, WIDE>::kNP;      // previous-scale words per centre
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    const int tx0 = blockIdx.x * 32, ty0 = blockIdx.y * a.ty, tz0 = a.z0 + blockIdx.z * a.tz;
+    const int tx0 = blockIdx.x * 32 * CPL, ty0 = blockIdx.y * a.ty, tz0 = a.z0 + blockIdx.z * a.tz;
     const int R = a.r_max;
 
     Src<PATH> src;
@@ -132,39 +148,46 @@ __global__ void __launch_bounds__(512) k_dense(const DenseArgs a,
         pz = a.bx * a.by;
         py = a.bx;
     } else {
-        src.vol = a.vol.base;
         pz = (int)a.vol.plane;
         py = (int)a.vol.pitch;
     }
     const Tab<CTAB> tab{a.ot};
 
-    // Lane's counter column: word v at +128 v; previous-scale words (WIDE)
-    // at +128 (NW + v).
-    const uint32_t cnt_lane = smem_u32(smem + a.cnt_off) + (warp * (NW + NPREV) * 32 + lane) * 4;
+    // Counter columns: centre j of the lane has word w at
+    // cnt_lane + 128 (j * (NW + NP) + w).
+    const uint32_t cnt_lane =
+        smem_u32(smem + a.cnt_off) + (warp * CPL * (NW + NP) * 32 + lane) * 4;
     const int nrows = a.ty * a.tz;
 
     for (int row = warp; row < nrows; row += nwarps) {
         const int cy = ty0 + row % a.ty, cz = tz0 + row / a.ty;
         if (cy >= a.vol.ny || cz >= a.z1) continue;              // warp-uniform
+        // Lane centres cx + 32 j.  The source address of centre j is the
+        // centre-0 address plus 32 j (an immediate); centres past nx are
+        // computed but not written.
         const int cx = tx0 + lane;
-        const bool live = cx < a.vol.nx;
-        // lane's centre as an offset into the source
-        using Base = typename std::conditional<PATH == 0, int, int64_t>::type;
+        using Base = typename std::conditional<PATH == 0, int, const uint8_t *>::type;
         Base c0;
         if constexpr (PATH == 0)
             c0 = (cz - tz0 + R) * pz + (cy - ty0 + R) * py + (a.padx + lane);
         else
-            c0 = (int64_t)cz * a.vol.plane + (int64_t)cy * a.vol.pitch + (live ? cx : a.vol.nx - 1);
+            c0 = a.vol.base + (int64_t)cz * a.vol.plane + (int64_t)cy * a.vol.pitch +
+                 (CPL == 1 && cx >= a.vol.nx ? a.vol.nx - 1 : cx);
 
 #pragma unroll 4
-        for (int w = 0; w < NW + NPREV; ++w) st_shared_u32(cnt_lane + (w << 7), 0u);
+        for (int w = 0; w < CPL * (NW + NP); ++w) st_shared_u32(cnt_lane + (w << 7), 0u);
 
-        double hm1 = 0.0, hm2 = 0.0;      // H at scale index i-1, i-2
-        uint32_t nm1 = 0, nm2 = 0;        // N at i-1, i-2
-        uint64_t dm1 = 0;                 // D at i-1
-        double yb = 0.0;
-        int sb = 0;
-        const int64_t oidx = ((int64_t)cz * a.vol.ny + cy) * a.vol.nx + cx;
+        double hm1[CPL], hm2[CPL], yb[CPL];     // H at scale index i-1, i-2; best Y
+        uint32_t nm1[CPL], nm2[CPL];            // N at i-1, i-2
+        uint64_t dm1[CPL];                      // D at i-1
+        int sb[CPL];
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+            hm1[j] = hm2[j] = yb[j] = 0.0;
+            nm1[j] = nm2[j] = 0;
+            dm1[j] = 0;
+            sb[j] = 0;
+        }
 
         for (int i = 0; i < a.S; ++i) {
             const int r = a.r_min + i;
@@ -172,26 +195,28 @@ __global__ void __launch_bounds__(512) k_dense(const DenseArgs a,
                 const int k0 = tab.c8_start(rho), k1 = tab.c8_start(rho + 1);
                 const int k2 = tab.rest_start(rho), k3 = tab.rest_start(rho + 1);
                 // three nonzero components: 8 sign mirrors
-                uint32_t e = k0 < k1 ? tab.c8(k0) : 0u;
+                // (an entry after the last one of a class always exists, in
+                // the constant and in the global table, so the prefetch of
+                // entry k + 1 needs no guard)
+                uint32_t e = tab.c8(k0);
                 for (int k = k0; k < k1; ++k) {
-                    const uint32_t en = k + 1 < k1 ? tab.c8(k + 1) : 0u;   // prefetch
+                    const uint32_t en = tab.c8(k + 1);
+                    // (the top byte of e is the radius class, unused here)
                     const int X = (int)(e & 0xffu);
                     const int Y = (int)((e >> 8) & 0xffu) * py;
                     const int Z = (int)((e >> 16) & 0xffu) * pz;
-                    const int o0 = Z + Y, o1 = Z - Y, o2 = Y - Z, o3 = -Z - Y;
-                    // (the top byte of e is the radius class, unused here)
-                    const uint32_t v0 = src.at(c0, o0 + X), v1 = src.at(c0, o0 - X);
-                    const uint32_t v2 = src.at(c0, o1 + X), v3 = src.at(c0, o1 - X);
-                    const uint32_t v4 = src.at(c0, o2 + X), v5 = src.at(c0, o2 - X);
-                    const uint32_t v6 = src.at(c0, o3 + X), v7 = src.at(c0, o3 - X);
-                    red_add_shared(cnt_lane + (v0 << 7), 1u);
-                    red_add_shared(cnt_lane + (v1 << 7), 1u);
-                    red_add_shared(cnt_lane + (v2 << 7), 1u);
-                    red_add_shared(cnt_lane + (v3 << 7), 1u);
-                    red_add_shared(cnt_lane + (v4 << 7), 1u);
-                    red_add_shared(cnt_lane + (v5 << 7), 1u);
-                    red_add_shared(cnt_lane + (v6 << 7), 1u);
-                    red_add_shared(cnt_lane + (v7 << 7), 1u);
+                    const int o[8] = {Z + Y + X, Z + Y - X, Z - Y + X, Z - Y - X,
+                                      Y - Z + X, Y - Z - X, -Z - Y + X, -Z - Y - X};
+                    uint32_t v[8][CPL];
+#pragma unroll
+                    for (int m = 0; m < 8; ++m)
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j) v[m][j] = src.at(c0, o[m] + 32 * j);
+#pragma unroll
+                    for (int m = 0; m < 8; ++m)
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j)
+                            red_add_shared(cnt_lane + ((j * (NW + NP) + v[m][j]) << 7), 1u);
                     e = en;
                 }
                 // offsets on a coordinate plane or axis, one entry each
@@ -199,48 +224,84 @@ __global__ void __launch_bounds__(512) k_dense(const DenseArgs a,
                     const uint32_t f = tab.rest(k);
                     const int off = ((int)((f >> 16) & 0xffu) - 64) * pz +
                                     ((int)((f >> 8) & 0xffu) - 64) * py + ((int)(f & 0xffu) - 64);
-                    red_add_shared(cnt_lane + (src.at(c0, off) << 7), 1u);
-                }
-            }
-
-            // ---- exact per-scale quantities from the lane's counters
-            const uint32_t zero_cnt = ld_shared_u32(cnt_lane);
-            const uint32_t N = (uint32_t)__ldg(a.ot.ball_size + r) - zero_cnt;
-            double ssum = 0.0;
-            int occ = 0;
-            uint64_t D = 0;
 #pragma unroll
-            for (int v = 1; v <= B; ++v) {
-                const uint32_t c = ld_shared_u32(cnt_lane + (v << 7));
-                const uint32_t p = ld_shared_u32(cnt_lane + ((NW + v) << 7));
-                st_shared_u32(cnt_lane + ((NW + v) << 7), c);
-                occ += c > 0u;
-                if (c > 1u) ssum = __dadd_rn(ssum, __ldg(a.T + c));
-                const int64_t d = (int64_t)c * nm1 - (int64_t)p * N;
-                D += (uint64_t)(d < 0 ? -d : d);
-            }
-            const double H = entropy_from_sum(ssum, N, occ, a.L);
-
-            if (i >= 2 && hm2 < hm1 && hm1 >= H) {                // peak at scale i-1
-                const double W = kb_weight(dm1, nm1, nm2, r - 1, a.w_norm);
-                const double y = __dmul_rn(hm1, W);
-                if (sb == 0 || y > yb) {
-                    yb = y;
-                    sb = r - 1;
+                    for (int j = 0; j < CPL; ++j)
+                        red_add_shared(cnt_lane + ((j * (NW + NP) + src.at(c0, off + 32 * j)) << 7),
+                                       1u);
                 }
             }
-            if (live && a.out.H) a.out.H[oidx * a.S + i] = H;
-            if (live && a.out.W)
-                a.out.W[oidx * a.S + i] = i == 0 ? 0.0 : kb_weight(D, N, nm1, r, a.w_norm);
-            hm2 = hm1;
-            hm1 = H;
-            nm2 = nm1;
-            nm1 = N;
-            dm1 = D;
+
+            // ---- exact per-scale quantities from each centre's counters
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                const uint32_t col = cnt_lane + ((j * (NW + NP)) << 7);
+                const uint32_t N = (uint32_t)__ldg(a.ot.ball_size + r) - ld_shared_u32(col);
+                double ssum = 0.0;
+                int occ = 0;
+                uint64_t D = 0;
+                auto term = [&](uint32_t c, uint32_t p) {
+                    occ += c > 0u;
+                    if (c > 1u) ssum = __dadd_rn(ssum, __ldg(a.T + c));
+                    const int64_t d = (int64_t)c * nm1[j] - (int64_t)p * N;
+                    D += (uint64_t)(d < 0 ? -d : d);
+                };
+                if constexpr (WIDE) {
+#pragma unroll
+                    for (int vv = 1; vv <= B; ++vv) {
+                        const uint32_t c = ld_shared_u32(col + (vv << 7));
+                        const uint32_t p = ld_shared_u32(col + ((NW + vv) << 7));
+                        st_shared_u32(col + ((NW + vv) << 7), c);
+                        term(c, p);
+                    }
+                } else {
+                    // previous counts as 16-bit pairs: word w holds values 2w, 2w+1
+#pragma unroll
+                    for (int w = 0; w < NP; ++w) {
+                        const uint32_t pw = ld_shared_u32(col + ((NW + w) << 7));
+                        uint32_t c_lo = 0, c_hi = 0;
+                        if (2 * w >= 1 && 2 * w <= B) {
+                            c_lo = ld_shared_u32(col + ((2 * w) << 7));
+                            term(c_lo, pw & 0xffffu);
+                        }
+                        if (2 * w + 1 <= B) {
+                            c_hi = ld_shared_u32(col + ((2 * w + 1) << 7));
+                            term(c_hi, pw >> 16);
+                        }
+                        st_shared_u32(col + ((NW + w) << 7), c_lo | (c_hi << 16));
+                    }
+                }
+                const double H = entropy_from_sum(ssum, N, occ, a.L);
+
+                if (i >= 2 && hm2[j] < hm1[j] && hm1[j] >= H) {   // peak at scale i-1
+                    const double W = kb_weight(dm1[j], nm1[j], nm2[j], r - 1, a.w_norm);
+                    const double y = __dmul_rn(hm1[j], W);
+                    if (sb[j] == 0 || y > yb[j]) {
+                        yb[j] = y;
+                        sb[j] = r - 1;
+                    }
+                }
+                const int cxj = cx + 32 * j;
+                if (cxj < a.vol.nx && (a.out.H || a.out.W)) {
+                    const int64_t oidx = ((int64_t)cz * a.vol.ny + cy) * a.vol.nx + cxj;
+                    if (a.out.H) a.out.H[oidx * a.S + i] = H;
+                    if (a.out.W)
+                        a.out.W[oidx * a.S + i] = i == 0 ? 0.0 : kb_weight(D, N, nm1[j], r, a.w_norm);
+                }
+                hm2[j] = hm1[j];
+                hm1[j] = H;
+                nm2[j] = nm1[j];
+                nm1[j] = N;
+                dm1[j] = D;
+            }
         }
-        if (live) {
-            a.out.Y[oidx] = yb;
-            a.out.s[oidx] = (uint8_t)sb;
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+            const int cxj = cx + 32 * j;
+            if (cxj < a.vol.nx) {
+                const int64_t oidx = ((int64_t)cz * a.vol.ny + cy) * a.vol.nx + cxj;
+                a.out.Y[oidx] = yb[j];
+                a.out.s[oidx] = (uint8_t)sb[j];
+            }
         }
     }
 }
@@ -256,10 +317,14 @@ struct Geometry {
     size_t brick, cnt_off, cnt_bytes, mbar_off, total;
 };
 
+int centres_per_lane(const DenseConfig &c) { return c.path == 2 ? 2 : 1; }
+
 Geometry geometry(const DenseConfig &c, int B_, int r_max) {
     Geometry g{};
     const int B = template_bins(B_);
-    const int words = (B + 1) * 2;          // counts + previous-scale counts
+    // counts + previous-scale counts (16-bit pairs unless wide), per centre
+    const int words =
+        centres_per_lane(c) * ((B + 1) + (is_wide(r_max) ? B + 1 : (B + 2) / 2));
     g.padx = (r_max + 15) / 16 * 16;
     g.bx = (g.padx + 32 + r_max + 15) / 16 * 16;
     g.by = c.ty + 2 * r_max;
@@ -272,14 +337,15 @@ Geometry geometry(const DenseConfig &c, int B_, int r_max) {
     return g;
 }
 
-template <int B, bool WIDE, int PATH>
+template <int B, bool WIDE, int PATH, int CPL>
 cudaError_t launch_t(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap *tmap,
                      const DenseConfig &cfg, size_t smem) {
-    auto kern = k_dense<B, WIDE, PATH>;
+    auto kern = k_dense<B, WIDE, PATH, CPL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((a.vol.nx + 31) / 32, (a.vol.ny + a.ty - 1) / a.ty, (a.z1 - a.z0 + a.tz - 1) / a.tz);
+    dim3 grid((a.vol.nx + 32 * CPL - 1) / (32 * CPL), (a.vol.ny + a.ty - 1) / a.ty,
+              (a.z1 - a.z0 + a.tz - 1) / a.tz);
     CUtensorMap dummy{};
     kern<<<grid, cfg.warps * 32, smem, lc.stream>>>(a, tmap ? *tmap : dummy);
     return cudaGetLastError();
@@ -290,10 +356,13 @@ cudaError_t launch_b(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap 
                      const DenseConfig &cfg, size_t smem) {
     const bool wide = is_wide(a.r_max);
     if (cfg.path == 0)
-        return wide ? launch_t<B, true, 0>(lc, a, tmap, cfg, smem)
-                    : launch_t<B, false, 0>(lc, a, tmap, cfg, smem);
-    return wide ? launch_t<B, true, 1>(lc, a, tmap, cfg, smem)
-                : launch_t<B, false, 1>(lc, a, tmap, cfg, smem);
+        return wide ? launch_t<B, true, 0, 1>(lc, a, tmap, cfg, smem)
+                    : launch_t<B, false, 0, 1>(lc, a, tmap, cfg, smem);
+    if (cfg.path == 1)
+        return wide ? launch_t<B, true, 1, 1>(lc, a, tmap, cfg, smem)
+                    : launch_t<B, false, 1, 1>(lc, a, tmap, cfg, smem);
+    return wide ? launch_t<B, true, 1, 2>(lc, a, tmap, cfg, smem)
+                : launch_t<B, false, 1, 2>(lc, a, tmap, cfg, smem);
 }
 
 }  // namespace
@@ -346,7 +415,8 @@ size_t dense_smem_bytes(const DenseConfig &c, int B, int r_max) {
 }
 
 bool dense_config_fits(const DenseConfig &c, int B, int r_max) {
-    if (c.warps < 1 || c.warps > 16 || c.ty * c.tz != c.warps) return false;
+    if (c.path < 0 || c.path > 2) return false;
+    if (c.warps < 1 || c.warps > (c.path == 2 ? 8 : 16) || c.ty * c.tz != c.warps) return false;
     const Geometry g = geometry(c, B, r_max);
     if (c.path == 0 && (g.bx > 256 || g.by > 256 || g.bz > 256)) return false;
     return g.total + 1024 <= 227 * 1024;   // leave room for static shared memory
