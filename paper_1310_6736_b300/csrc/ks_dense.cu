@@ -29,6 +29,9 @@
 //            32 different banks), one word per stored value v = 0..B;
 //            v = 0 (not counted) is a dummy word, so the update has no
 //            branch: it is one shared-memory reduction (red.shared.add).
+//            With two centres per lane and r_max <= 25 both centres share
+//            the column as 16-bit halves (every count is <= |Ball(25)| =
+//            65267), which halves the counter memory and raises occupancy.
 //   FP64   = after each shell one pass over the centre's counters computes
 //            the bin-order entropy sum and the exact integer D of W against
 //            the previous scale's counts (words after the counters, refreshed
@@ -99,14 +102,28 @@ struct Src<1> {              // halo-padded volume in global memory
     }
 };
 
-// Counter words of one centre: NW 32-bit counters (stored values 0..B),
-// then the previous scale's counts, as 16-bit pairs when every count fits
-// (|Ball(r_max)| <= 65535, i.e. r_max <= 25) and as 32-bit words otherwise.
-template <int B, bool WIDE>
+// Shared-memory words of one lane.  Counters: one word per stored value
+// v = 0..B.  When every count fits in 16 bits (|Ball(r_max)| <= 65535, i.e.
+// r_max <= 25) the two centres of a two-centre lane share each word (centre
+// j in bits 16j..16j+15, so an update adds 1 << 16j); otherwise each centre
+// has its own 32-bit column.  After the counters come the previous scale's
+// counts of each centre: 16-bit pairs (values 2w, 2w+1 in word w) when they
+// fit, 32-bit words otherwise.
+template <int B, bool WIDE, int CPL>
 struct Words {
-    static constexpr int kNW = B + 1;
-    static constexpr int kNP = WIDE ? B + 1 : (B + 2) / 2;
-    static constexpr int kPerCentre = kNW + kNP;
+    static constexpr bool kPack = CPL == 2 && !WIDE;
+    static constexpr int kNW = B + 1;                          // counter words per column
+    static constexpr int kNP = WIDE ? B + 1 : (B + 2) / 2;     // previous words per centre
+    static constexpr int kCols = kPack ? 1 : CPL;              // counter columns
+    static constexpr int kPerLane = kCols * kNW + CPL * kNP;
+    // word index of centre j's counter of value v / previous word w
+    __host__ __device__ static constexpr int cnt(int j, int v) {
+        return (kPack ? 0 : j * kNW) + v;
+    }
+    __host__ __device__ static constexpr int prev(int j, int w) {
+        return kCols * kNW + j * kNP + w;
+    }
+    __host__ __device__ static constexpr uint32_t inc(int j) { return kPack ? 1u << (16 * j) : 1u; }
 };
 
 template <int B, bool WIDE, int PATH, int CPL>
@@ -114,9 +131,9 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
     k_dense(const DenseArgs a, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ int s_ok;
+    using Wd = Words<B, WIDE, CPL>;
     constexpr bool CTAB = !WIDE;                 // r_max <= 25: table in constant memory
-    constexpr int NW = Words<B, WIDE>::kNW;      // counter words per centre
-    constexpr int NP = Words<B, WIDE>::kNP;      // previous-scale words per centre
+    constexpr int NP = Wd::kNP;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -153,10 +170,10 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
     }
     const Tab<CTAB> tab{a.ot};
 
-    // Counter columns: centre j of the lane has word w at
-    // cnt_lane + 128 (j * (NW + NP) + w).
-    const uint32_t cnt_lane =
-        smem_u32(smem + a.cnt_off) + (warp * CPL * (NW + NP) * 32 + lane) * 4;
+    // Lane's words: word w at cnt_lane + 128 w (the 32 lanes of a warp sit
+    // in 32 different banks).
+    const uint32_t cnt_lane = smem_u32(smem + a.cnt_off) + (warp * Wd::kPerLane * 32 + lane) * 4;
+    auto word = [&](int w) { return cnt_lane + ((uint32_t)w << 7); };
     const int nrows = a.ty * a.tz;
 
     for (int row = warp; row < nrows; row += nwarps) {
@@ -175,7 +192,7 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
                  (CPL == 1 && cx >= a.vol.nx ? a.vol.nx - 1 : cx);
 
 #pragma unroll 4
-        for (int w = 0; w < CPL * (NW + NP); ++w) st_shared_u32(cnt_lane + (w << 7), 0u);
+        for (int w = 0; w < Wd::kPerLane; ++w) st_shared_u32(word(w), 0u);
 
         double hm1[CPL], hm2[CPL], yb[CPL];     // H at scale index i-1, i-2; best Y
         uint32_t nm1[CPL], nm2[CPL];            // N at i-1, i-2
@@ -216,26 +233,31 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
                     for (int m = 0; m < 8; ++m)
 #pragma unroll
                         for (int j = 0; j < CPL; ++j)
-                            red_add_shared(cnt_lane + ((j * (NW + NP) + v[m][j]) << 7), 1u);
+                            red_add_shared(word(Wd::cnt(j, v[m][j])), Wd::inc(j));
                     e = en;
                 }
                 // offsets on a coordinate plane or axis, one entry each
+#pragma unroll 2
                 for (int k = k2; k < k3; ++k) {
                     const uint32_t f = tab.rest(k);
                     const int off = ((int)((f >> 16) & 0xffu) - 64) * pz +
                                     ((int)((f >> 8) & 0xffu) - 64) * py + ((int)(f & 0xffu) - 64);
+                    uint32_t v[CPL];
 #pragma unroll
-                    for (int j = 0; j < CPL; ++j)
-                        red_add_shared(cnt_lane + ((j * (NW + NP) + src.at(c0, off + 32 * j)) << 7),
-                                       1u);
+                    for (int j = 0; j < CPL; ++j) v[j] = src.at(c0, off + 32 * j);
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j) red_add_shared(word(Wd::cnt(j, v[j])), Wd::inc(j));
                 }
             }
 
             // ---- exact per-scale quantities from each centre's counters
 #pragma unroll
             for (int j = 0; j < CPL; ++j) {
-                const uint32_t col = cnt_lane + ((j * (NW + NP)) << 7);
-                const uint32_t N = (uint32_t)__ldg(a.ot.ball_size + r) - ld_shared_u32(col);
+                auto count = [&](int v) -> uint32_t {
+                    const uint32_t x = ld_shared_u32(word(Wd::cnt(j, v)));
+                    return Wd::kPack ? (x >> (16 * j)) & 0xffffu : x;
+                };
+                const uint32_t N = (uint32_t)__ldg(a.ot.ball_size + r) - count(0);
                 double ssum = 0.0;
                 int occ = 0;
                 uint64_t D = 0;
@@ -248,26 +270,26 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
                 if constexpr (WIDE) {
 #pragma unroll
                     for (int vv = 1; vv <= B; ++vv) {
-                        const uint32_t c = ld_shared_u32(col + (vv << 7));
-                        const uint32_t p = ld_shared_u32(col + ((NW + vv) << 7));
-                        st_shared_u32(col + ((NW + vv) << 7), c);
+                        const uint32_t c = count(vv);
+                        const uint32_t p = ld_shared_u32(word(Wd::prev(j, vv)));
+                        st_shared_u32(word(Wd::prev(j, vv)), c);
                         term(c, p);
                     }
                 } else {
                     // previous counts as 16-bit pairs: word w holds values 2w, 2w+1
 #pragma unroll
                     for (int w = 0; w < NP; ++w) {
-                        const uint32_t pw = ld_shared_u32(col + ((NW + w) << 7));
+                        const uint32_t pw = ld_shared_u32(word(Wd::prev(j, w)));
                         uint32_t c_lo = 0, c_hi = 0;
                         if (2 * w >= 1 && 2 * w <= B) {
-                            c_lo = ld_shared_u32(col + ((2 * w) << 7));
+                            c_lo = count(2 * w);
                             term(c_lo, pw & 0xffffu);
                         }
                         if (2 * w + 1 <= B) {
-                            c_hi = ld_shared_u32(col + ((2 * w + 1) << 7));
+                            c_hi = count(2 * w + 1);
                             term(c_hi, pw >> 16);
                         }
-                        st_shared_u32(col + ((NW + w) << 7), c_lo | (c_hi << 16));
+                        st_shared_u32(word(Wd::prev(j, w)), c_lo | (c_hi << 16));
                     }
                 }
                 const double H = entropy_from_sum(ssum, N, occ, a.L);
@@ -322,9 +344,10 @@ int centres_per_lane(const DenseConfig &c) { return c.path == 2 ? 2 : 1; }
 Geometry geometry(const DenseConfig &c, int B_, int r_max) {
     Geometry g{};
     const int B = template_bins(B_);
-    // counts + previous-scale counts (16-bit pairs unless wide), per centre
-    const int words =
-        centres_per_lane(c) * ((B + 1) + (is_wide(r_max) ? B + 1 : (B + 2) / 2));
+    // counter columns + previous-scale counts per lane (layout of Words)
+    const int cpl = centres_per_lane(c);
+    const bool wide = is_wide(r_max);
+    const int words = (cpl == 2 && !wide ? 1 : cpl) * (B + 1) + cpl * (wide ? B + 1 : (B + 2) / 2);
     g.padx = (r_max + 15) / 16 * 16;
     g.bx = (g.padx + 32 + r_max + 15) / 16 * 16;
     g.by = c.ty + 2 * r_max;
