@@ -34,6 +34,12 @@ METRIC = "window-entropies/s"
 WORKLOAD = "pet128"
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_dense launch on the
+# pet128 workload (launch path 2, profiles/k_dense_pet128.md): the padded bin
+# volume is read once; the Y and s outputs stay in L2.
+DENSE_DRAM_BYTES = 3_741_440
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -292,7 +298,8 @@ def run_ks(args):
                                                 or (None,) * 4))},
             "roofline": {"bound": "smem", "achieved": achieved / 1e9,
                          "peak": smem_peak / 1e9, "unit": "Gupdates/s",
-                         "frac": achieved / smem_peak, "traffic": None,
+                         "frac": achieved / smem_peak, "traffic": DENSE_DRAM_BYTES,
+                         "traffic_unit": "bytes per launch (dram read + write, ncu)",
                          "kernel": "k_dense", "peak_source":
                              "shared-memory histogram-increment micro-kernel, measured live",
                          "kernel_ms": dense_ms / max(1, dense_n),
