@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -198,7 +199,10 @@ static int build_ball_tables(Ctx *c) {
         if (8 * s8[r + 1] + sr[r + 1] != c->h_ball_size[r])
             return set_err(c, KS_ECUDA, "internal: offset tables inconsistent");
     if ((int)ball.size() != kTableN) return set_err(c, KS_ECUDA, "internal: ball size");
-    // x-rows of every Ball(r), longest first
+    // x-rows of every Ball(r): rows off both planes y = 0 and z = 0 first,
+    // then the rows on one of them; longest first within each group (a
+    // block hands rows out round robin, so a warp takes rows of one kind
+    // and of similar length)
     std::vector<uint32_t> hw;
     int swr[kRmax + 2];
     for (int r = 0; r <= kRmax; ++r) {
@@ -218,7 +222,10 @@ static int build_ball_tables(Ctx *c) {
                 n += 2 * w + 1;
             }
         if (n != c->h_ball_size[r]) return set_err(c, KS_ECUDA, "internal: row tables inconsistent");
-        std::stable_sort(rows.begin(), rows.end(), [](const Row &a, const Row &b) { return a.w > b.w; });
+        std::stable_sort(rows.begin(), rows.end(), [](const Row &a, const Row &b) {
+            const bool pa = a.dy == 0 || a.dz == 0, pb = b.dy == 0 || b.dz == 0;
+            return pa != pb ? pb : a.w > b.w;
+        });
         for (auto &rw : rows)
             hw.push_back((uint32_t)(rw.dy + 64) | ((uint32_t)(rw.dz + 64) << 8) |
                          ((uint32_t)rw.w << 16));
@@ -488,11 +495,11 @@ std::vector<ClassLaunch> plan_class_queues(Ctx *c, const std::vector<SeedJob> &j
                                            std::vector<uint8_t> &image, size_t plan_at,
                                            uint8_t *dev_base) {
     // classes in order of first appearance
-    std::vector<std::pair<int, int>> keys;
+    std::vector<std::array<int, 3>> keys;      // (bins, scales, kind)
     std::vector<std::vector<int>> members;
     for (size_t s = 0; s < segs.size(); ++s) {
         const SeedJob &J = jobs[segs[s].first];
-        const std::pair<int, int> k{J.vol.B, J.S};
+        const std::array<int, 3> k{J.vol.B, J.S, segs[s].second};
         size_t ci = 0;
         while (ci < keys.size() && keys[ci] != k) ++ci;
         if (ci == keys.size()) {
@@ -513,12 +520,16 @@ std::vector<ClassLaunch> plan_class_queues(Ctx *c, const std::vector<SeedJob> &j
     for (size_t ci = 0; ci < keys.size(); ++ci) {
         std::vector<int64_t> ss{0};
         std::vector<int> sk, sj;
-        for (int s : members[ci]) {
-            const int job = segs[s].first, kind = segs[s].second;
-            ss.push_back(ss.back() + seed_tickets(kind, jobs[job].n_seeds, jobs[job].S));
+        auto add = [&](int job, int kind) {
+            ss.push_back(ss.back() + seed_tickets(kind, jobs[job].n_seeds, jobs[job].r_min, jobs[job].S));
             sk.push_back(kind);
             sj.push_back(job);
-        }
+        };
+        // a mean-shift job becomes a block-path and a warp-path segment; the
+        // warp-path segments of the class go last
+        for (int s : members[ci]) add(segs[s].first, segs[s].second);
+        if (keys[ci][2] == kMeanShift)
+            for (int s : members[ci]) add(segs[s].first, kMsWarp);
         ClassLaunch L{};
         const unsigned long long zero = 0;
         L.q.head = (unsigned long long *)put(&zero, sizeof(zero));
@@ -528,9 +539,10 @@ std::vector<ClassLaunch> plan_class_queues(Ctx *c, const std::vector<SeedJob> &j
         L.q.seg_job = (const int *)put(sj.data(), sj.size() * 4);
         L.q.n_segs = (int)sk.size();
         L.q.n_tickets = ss.back();
-        L.max_B = keys[ci].first;
-        L.max_S = keys[ci].second;
-        L.grid = c->num_sms * seed_blocks_per_sm(L.max_B, L.max_S);
+        L.max_B = keys[ci][0];
+        L.max_S = keys[ci][1];
+        L.kinds = 1 << keys[ci][2];
+        L.grid = c->num_sms * seed_blocks_per_sm(L.max_B, L.max_S, L.kinds);
         out.push_back(L);
     }
     return out;
@@ -543,7 +555,7 @@ cudaError_t launch_class_queues(Ctx *c, cudaStream_t s, int *d_status,
         cudaError_t e = cudaMemsetAsync(L.q.head, 0, 8, s);
         if (e == cudaSuccess)
             e = launch_seeds(LaunchCtx{s, d_status, c->num_sms}, L.q, c->ot, c->T, c->L, L.max_B,
-                             L.max_S, true, L.grid);
+                             L.max_S, L.kinds, true, L.grid);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -834,12 +846,14 @@ static int upload_queue(Ctx *c, const std::vector<SeedJob> &jobs, const std::vec
     return KS_OK;
 }
 
-static int run_queue(Ctx *c, const SeedQueue &q, int max_B, int max_S, bool persistent) {
+static int run_queue(Ctx *c, const SeedQueue &q, int max_B, int max_S, int kinds, bool persistent) {
     if (q.n_tickets == 0) return KS_OK;
-    const int grid = persistent ? c->num_sms * seed_blocks_per_sm(max_B, max_S) : (int)q.n_tickets;
+    const int grid =
+        persistent ? c->num_sms * seed_blocks_per_sm(max_B, max_S, kinds) : (int)q.n_tickets;
     ProfRec rec;
     prof_begin(c, persistent ? "ks_seeds_persistent" : "ks_seeds", c->stream, &rec);
-    cudaError_t e = launch_seeds(c->lc(), q, c->ot, c->T, c->L, max_B, max_S, persistent, grid);
+    cudaError_t e =
+        launch_seeds(c->lc(), q, c->ot, c->T, c->L, max_B, max_S, kinds, persistent, grid);
     prof_end(c, &rec, c->stream);
     return cuda_err(c, e, "seed launch");
 }
@@ -885,9 +899,19 @@ static int seed_common(Ctx *c, ks_vol vol, const ks_params *p, const int32_t *se
     J.ms_out = kind == kMeanShift ? (ks_ms_result *)dout : nullptr;
     J.traj = kind == kOctant ? dtraj : nullptr;
     SeedQueue q{};
-    st = upload_queue(c, {J}, {0, seed_tickets(kind, ns, S)}, {kind}, {0}, &q);
-    if (st) return st;
-    st = run_queue(c, q, v->binning.bins, S, false);
+    if (kind == kOctant) {
+        // one block per seed
+        st = upload_queue(c, {J}, {0, ns}, {kOctant}, {0}, &q);
+        if (st) return st;
+        st = run_queue(c, q, v->binning.bins, S, 1 << kOctant, false);
+    } else {
+        // block-path items, then warp-path items, on a persistent launch
+        const int64_t nb = seed_tickets(kMeanShift, ns, p->r_min, S);
+        const int64_t nw = seed_tickets(kMsWarp, ns, p->r_min, S);
+        st = upload_queue(c, {J}, {0, nb, nb + nw}, {kMeanShift, kMsWarp}, {0, 0}, &q);
+        if (st) return st;
+        st = run_queue(c, q, v->binning.bins, S, 1 << kMeanShift, true);
+    }
     if (st) return st;
     if (!out_on_device && n_items) {
         KS_TRY_CUDA(c, cudaMemcpyAsync(out, dout, n_items * rec, cudaMemcpyDeviceToHost, c->stream));

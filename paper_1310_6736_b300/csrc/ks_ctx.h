@@ -100,11 +100,11 @@ int run_dense(Ctx *c, cudaStream_t s, Volume *v, const ks_params *p, const Dense
               int z0, int z1);
 void serve_shutdown(Ctx *c);
 
-// Persistent seed launches grouped by (bins, scales): each class gets its
-// own ticket queue and a shared-memory layout sized for it alone.
+// Persistent seed launches grouped by (bins, scales, kind): each class gets
+// its own ticket queue and a shared-memory layout sized for it alone.
 struct ClassLaunch {
     SeedQueue q;
-    int max_B, max_S, grid;
+    int max_B, max_S, kinds, grid;
 };
 size_t plan_bytes_bound(size_t n_segs);
 // segs: (job index, kind) pairs in processing order.  Writes each class's

@@ -48,8 +48,10 @@ struct VolDesc {
 // |Ball(r)| = 8 c8_start[r+1] + rest_start[r+1] = ball_size[r].
 //   rows: for every r = 0..32, the x-rows of Ball(r): (dy, dz) with
 //         dy^2 + dz^2 <= r^2 and half-length w = floor(sqrt(r^2 - dy^2 -
-//         dz^2)), packed (dy+64) | (dz+64) << 8 | w << 16, longest rows
-//         first.  Ball(r)'s rows: [rows_start[r], rows_start[r+1]).
+//         dz^2)), packed (dy+64) | (dz+64) << 8 | w << 16; rows with
+//         dy != 0 and dz != 0 first, then the rows on the plane y = 0 or
+//         z = 0, longest first within each group.  Ball(r)'s rows:
+//         [rows_start[r], rows_start[r+1]).
 struct OffsetTables {
     const uint32_t *c8;
     const int *c8_start;      // [kRmax + 2]
@@ -189,7 +191,11 @@ cudaError_t launch_dense(const LaunchCtx &lc, const VolDesc &v, const CUtensorMa
                          int z0, int z1);
 
 // ks_seeds.cu
-enum ItemKind { kOctant = 0, kMeanShift = 1 };
+// Ticket kinds of a queue segment: an octant seed; a mean-shift (seed, r)
+// item with r > 20 run by a whole block; one with r <= 20 run by one warp.
+// A launch's kinds mask has bit kOctant and/or bit kMeanShift (the latter
+// covering both mean-shift kinds).
+enum ItemKind { kOctant = 0, kMeanShift = 1, kMsWarp = 2 };
 struct SeedJob {
     VolDesc vol;
     int r_min, r_max, S, max_iter, w_norm;
@@ -200,9 +206,10 @@ struct SeedJob {
     int32_t *traj;               // device, n_seeds * (max_iter+1) * 3, or null
 };
 // A work queue in tickets: segment k covers tickets [seg_start[k],
-// seg_start[k+1]) of kind seg_kind[k] on job seg_job[k].  An octant ticket
-// is one seed; a mean-shift ticket is up to 8 (seed, r) items (one per
-// warp of the block), seed_tickets() tells how many a job needs.
+// seg_start[k+1]) of kind seg_kind[k] on job seg_job[k]; seed_tickets()
+// tells how many tickets of a kind a job needs.  kMsWarp segments must come
+// after every other segment of their queue, and a queue holding them must
+// be run persistently (blocks switch to per-warp ticket draws there).
 struct SeedQueue {
     const SeedJob *jobs;
     const int64_t *seg_start;
@@ -212,12 +219,13 @@ struct SeedQueue {
     int64_t n_tickets;
     unsigned long long *head;    // persistent mode: next ticket counter
 };
-int64_t seed_tickets(int kind, int64_t n_seeds, int S);
-size_t seed_smem_bytes(int B, int S);
+int64_t seed_tickets(int kind, int64_t n_seeds, int r_min, int S);
+// kinds: bit k set when a launch carries tickets of kind k
+size_t seed_smem_bytes(int B, int S, int kinds);
 cudaError_t launch_seeds(const LaunchCtx &lc, const SeedQueue &q, const OffsetTables &ot,
-                         const double *T, const double *L, int max_B, int max_S,
+                         const double *T, const double *L, int max_B, int max_S, int kinds,
                          bool persistent, int grid);
-int seed_blocks_per_sm(int max_B, int max_S);
+int seed_blocks_per_sm(int max_B, int max_S, int kinds);
 
 // Micro-kernel: shared-memory increment rate (see ks_measure_smem_peak).
 cudaError_t launch_smem_peak(const LaunchCtx &lc, uint32_t *sink, int blocks, int iters);

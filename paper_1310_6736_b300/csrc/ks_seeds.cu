@@ -52,8 +52,46 @@ __device__ __forceinline__ const uint8_t *voxel_ptr(const VolDesc &v, const int 
 // f(t, v) for the bin v at p + t.  The loads cover at most 7 bytes before
 // p and 7 bytes after p + 2w: with |offset| <= 32 that stays inside the
 // halo-padded allocation, which ends in 256 bytes of slack.
+// The first and the last word are masked byte by byte; the words between
+// them are whole and need no test.
+__device__ __forceinline__ uint32_t byte_of(unsigned long long word, int b) {
+    const uint32_t h = b < 4 ? (uint32_t)word : (uint32_t)(word >> 32);
+    return (h >> (8 * (b & 3))) & 0xffu;
+}
+
 template <typename F>
 __device__ __forceinline__ void walk_row(const uint8_t *p, int w, F &&f) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const unsigned long long *q = reinterpret_cast<const unsigned long long *>(a & ~uintptr_t(7));
+    const int off = (int)(a & 7u);
+    const int n = 2 * w + 1;
+    const int last = (off + n - 1) >> 3;                // index of the last word
+    {
+        const unsigned long long word = __ldg(q);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int t = b - off;
+            if (t >= 0 && t < n) f(t, byte_of(word, b));
+        }
+    }
+    for (int k = 1; k < last; ++k) {
+        const unsigned long long word = __ldg(q + k);
+        const int t0 = 8 * k - off;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) f(t0 + b, byte_of(word, b));
+    }
+    if (last > 0) {
+        const unsigned long long word = __ldg(q + last);
+        const int t0 = 8 * last - off;
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            if (t0 + b < n) f(t0 + b, byte_of(word, b));
+    }
+}
+
+// The same walk with every byte masked (one loop, smaller code).
+template <typename F>
+__device__ __forceinline__ void walk_row_masked(const uint8_t *p, int w, F &&f) {
     const uintptr_t a = reinterpret_cast<uintptr_t>(p);
     const unsigned long long *q = reinterpret_cast<const unsigned long long *>(a & ~uintptr_t(7));
     const int off = (int)(a & 7u);
@@ -64,25 +102,51 @@ __device__ __forceinline__ void walk_row(const uint8_t *p, int w, F &&f) {
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
             const int t = k * 8 + b - off;
-            if (t >= 0 && t < n) f(t, (uint32_t)(word >> (8 * b)) & 0xffu);
+            if (t >= 0 && t < n) f(t, byte_of(word, b));
         }
     }
 }
 
-// Entropy of counts c[0..B) (bin order), the library's fixed formula.
+// Entropy of counts c[0..B) (bin order), the library's fixed formula.  The
+// counts and their table values are gathered eight bins at a time, so the
+// table loads of a group are in flight together; the additions still run
+// one at a time in bin order.
 __device__ double window_entropy(const uint32_t *c, int B, const double *T, const double *L,
                                  uint32_t *N_out) {
     uint32_t N = 0;
     int occ = 0;
     double s = 0.0;
-    for (int b = 0; b < B; ++b) {
-        const uint32_t x = c[b];
-        N += x;
-        occ += x > 0u;
-        if (x > 1u) s = __dadd_rn(s, __ldg(T + x));
+    for (int b0 = 0; b0 < B; b0 += 8) {
+        uint32_t x[8];
+        double t[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = b0 + k < B ? c[b0 + k] : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t[k] = __ldg(T + x[k]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            N += x[k];
+            occ += x[k] > 0u;
+            if (x[k] > 1u) s = __dadd_rn(s, t[k]);
+        }
     }
     if (N_out) *N_out = N;
     return entropy_from_sum(s, N, occ, L);
+}
+
+// s + p[0] + p[1] + ... + p[n-1], left to right from s = +0.0, with the
+// operands read eight at a time (p in shared memory, n a multiple of 8 or
+// padded with +0.0 up to one).
+__device__ __forceinline__ double chain_sum(const double *p, int n) {
+    double s = 0.0;
+    for (int b0 = 0; b0 < n; b0 += 8) {
+        double t[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t[k] = p[b0 + k];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s = __dadd_rn(s, t[k]);
+    }
+    return s;
 }
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) {
@@ -90,38 +154,55 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) {
 }
 
 // ---------------------------------------------------------------- octant
-// Closed-octant histograms of every shell at P into cnt[j][si][b] and the
-// plane/axis multiplicity excess into extra[si][b], both then turned into
-// prefix sums over shells (histograms of Ball(r_min + si)).
+// Closed-octant histograms of every shell at P into cnt[j][si][v] and the
+// plane/axis multiplicity excess into extra[si][v] (j = 8), both then turned
+// into prefix sums over shells (histograms of Ball(r_min + si)).  Each
+// histogram has B + 1 words indexed by the stored value v; word 0 (not
+// counted) is a dummy that is never read, so a voxel costs no branch.
+// soff[d2] is the byte offset si * (B + 1) * 4 of the shell of an offset
+// with |o|^2 = d2.
 __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *cnt,
-                            uint32_t *extra, const uint8_t *rho_of, const int P[3]) {
-    const int B = J.vol.B, S = J.S;
-    for (int k = threadIdx.x; k < 9 * S * B; k += blockDim.x) cnt[k] = 0;   // extra follows cnt
+                            const uint32_t *soff, const int P[3]) {
+    const int B = J.vol.B, S = J.S, Bs = B + 1;
+    const uint32_t SB4 = (uint32_t)(S * Bs * 4);          // bytes per octant
+    for (int k = threadIdx.x; k < 9 * S * Bs; k += blockDim.x) cnt[k] = 0;
     __syncthreads();
     const uint8_t *c0 = voxel_ptr(J.vol, P);
     const int plane = (int)J.vol.plane, pitch = (int)J.vol.pitch;
+    const uint32_t cnt_s = smem_u32(cnt), extra_s = cnt_s + 8 * SB4, soff_s = smem_u32(soff);
     const uint32_t *rows = ot.rows + __ldg(ot.rows_start + J.r_max);
     const int nrows = __ldg(ot.rows_start + J.r_max + 1) - __ldg(ot.rows_start + J.r_max);
-    // one x-row of Ball(r_max) per thread at a time
+    // one x-row of Ball(r_max) per thread at a time (rows off the planes
+    // y = 0 and z = 0 come first in the table, so warps rarely mix kinds)
     for (int ri = threadIdx.x; ri < nrows; ri += blockDim.x) {
         const uint32_t e = __ldg(rows + ri);
         const int dy = (int)(e & 0xffu) - 64, dz = (int)((e >> 8) & 0xffu) - 64;
         const int w = (int)(e >> 16);
         const int rr = dy * dy + dz * dz;
-        const bool on_plane = dy == 0 || dz == 0;
+        const uint8_t *p = c0 + dz * plane + dy * pitch - w;
         const int jyz = (dy < 0 ? 2 : 0) | (dz < 0 ? 4 : 0);
-        walk_row(c0 + dz * plane + dy * pitch - w, w, [&](int t, uint32_t v) {
-            if (v == 0u) return;
-            const int dx = t - w;
-            const int rho = rho_of[dx * dx + rr];           // radius class ceil(|o|)
-            const int si = rho > J.r_min ? rho - J.r_min : 0;
-            uint32_t *base = cnt + si * B + (v - 1);
-            if (dx != 0 && !on_plane) {                     // inside one open octant
-                atomicAdd(base + (jyz | (dx < 0 ? 1 : 0)) * S * B, 1u);
-            } else {                                        // on a coordinate plane or axis
+        if (dy != 0 && dz != 0) {
+            // dx < 0: open octant jyz | 1; dx >= 0: octant jyz.  The voxel
+            // dx = 0 lies on the plane x = 0 and so also in octant jyz | 1
+            // (multiplicity 2): added there, with its excess, after the walk.
+            const uint32_t base_l = cnt_s + (uint32_t)(jyz | 1) * SB4, base_r = cnt_s + jyz * SB4;
+            walk_row(p, w, [&](int t, uint32_t v) {
+                const int dx = t - w;
+                red_add_shared((dx < 0 ? base_l : base_r) + ld_shared_u32(soff_s + 4 * (dx * dx + rr)) +
+                                   (v << 2),
+                               1u);
+            });
+            const uint32_t a0 = ld_shared_u32(soff_s + 4 * rr) + ((uint32_t)__ldg(p + w) << 2);
+            red_add_shared(base_l + a0, 1u);
+            red_add_shared(extra_s + a0, 1u);
+        } else {
+            // on the plane y = 0 or z = 0: every closed octant the voxel touches
+            const int ay = dy > 0 ? 1 : (dy < 0 ? 2 : 3);
+            const int az = dz > 0 ? 1 : (dz < 0 ? 2 : 3);
+            walk_row(p, w, [&](int t, uint32_t v) {
+                const int dx = t - w;
                 const int ax = dx > 0 ? 1 : (dx < 0 ? 2 : 3);
-                const int ay = dy > 0 ? 1 : (dy < 0 ? 2 : 3);
-                const int az = dz > 0 ? 1 : (dz < 0 ? 2 : 3);
+                const uint32_t a = ld_shared_u32(soff_s + 4 * (dx * dx + rr)) + (v << 2);
                 uint32_t mult = 0;
                 for (int jz = 0; jz < 2; ++jz) {
                     if (!(az & (1 << jz))) continue;
@@ -129,22 +210,22 @@ __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *
                         if (!(ay & (1 << jy))) continue;
                         for (int jx = 0; jx < 2; ++jx) {
                             if (!(ax & (1 << jx))) continue;
-                            atomicAdd(base + (jx | (jy << 1) | (jz << 2)) * S * B, 1u);
+                            red_add_shared(cnt_s + (uint32_t)(jx | (jy << 1) | (jz << 2)) * SB4 + a, 1u);
                             ++mult;
                         }
                     }
                 }
-                atomicAdd(extra + si * B + (v - 1), mult - 1u);
-            }
-        });
+                red_add_shared(extra_s + a, mult - 1u);
+            });
+        }
     }
     __syncthreads();
-    for (int col = threadIdx.x; col < 9 * B; col += blockDim.x) {    // 8 octants + excess
-        const int j = col / B, b = col % B;
+    for (int col = threadIdx.x; col < 9 * Bs; col += blockDim.x) {    // 8 octants + excess
+        const int j = col / Bs, b = col % Bs;
         uint32_t run = 0;
         for (int si = 0; si < S; ++si) {
-            run += cnt[(j * S + si) * B + b];
-            cnt[(j * S + si) * B + b] = run;
+            run += cnt[(j * S + si) * Bs + b];
+            cnt[(j * S + si) * Bs + b] = run;
         }
     }
     __syncthreads();
@@ -192,24 +273,25 @@ __device__ void octant_step(const SeedJob &J, const double *hb, int step[3]) {
 
 // Kadir-Brady on the full ball at the centre of the last octant pass: the
 // full histograms (sum of closed octants minus excess, written over the
-// excess array), H(r), D(r), peaks, W and Y at peaks.
+// excess array), H(r), D(r), peaks, W and Y at peaks.  Histograms have
+// B + 1 words, word 0 the not-counted dummy.
 __device__ void kb_from_pass(const SeedJob &J, const double *T, const double *L, uint32_t *cnt,
                              uint32_t *full, double *hb, SeedShared &sh, ks_seed_result *o) {
-    const int B = J.vol.B, S = J.S;
-    for (int k = threadIdx.x; k < S * B; k += blockDim.x) {
+    const int B = J.vol.B, S = J.S, Bs = B + 1;
+    for (int k = threadIdx.x; k < S * Bs; k += blockDim.x) {
         uint32_t s = 0;
-        for (int j = 0; j < 8; ++j) s += cnt[j * S * B + k];
+        for (int j = 0; j < 8; ++j) s += cnt[j * S * Bs + k];
         full[k] = s - full[k];
     }
     __syncthreads();
     for (int si = threadIdx.x; si < S; si += blockDim.x) {
         uint32_t N;
-        hb[si] = window_entropy(full + si * B, B, T, L, &N);
+        hb[si] = window_entropy(full + si * Bs + 1, B, T, L, &N);
         sh.N[si] = N;
     }
     __syncthreads();
     for (int si = 1 + threadIdx.x; si < S; si += blockDim.x) {
-        const uint32_t *c = full + si * B, *p = full + (si - 1) * B;
+        const uint32_t *c = full + si * Bs + 1, *p = full + (si - 1) * Bs + 1;
         const uint32_t N = sh.N[si], Np = sh.N[si - 1];
         uint64_t D = 0;
         for (int b = 0; b < B; ++b) {
@@ -244,21 +326,26 @@ __device__ void kb_from_pass(const SeedJob &J, const double *T, const double *L,
 
 __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &ot,
                             const double *T, const double *L, const uint8_t *rho_of,
-                            uint32_t *cnt, double *hb,
-                            SeedShared &sh) {
+                            uint32_t *soff, uint32_t *cnt, double *hb, SeedShared &sh) {
     const int dims[3] = {J.vol.nx, J.vol.ny, J.vol.nz};
-    const int B = J.vol.B, S = J.S;
-    uint32_t *extra = cnt + 8 * S * B;
+    const int B = J.vol.B, S = J.S, Bs = B + 1;
+    uint32_t *extra = cnt + 8 * S * Bs;
+    // shell byte offsets of this job: si = max(rho - r_min, 0)
+    for (int d2 = threadIdx.x; d2 <= J.r_max * J.r_max; d2 += blockDim.x) {
+        const int rho = rho_of[d2];
+        soff[d2] = (uint32_t)((rho > J.r_min ? rho - J.r_min : 0) * Bs * 4);
+    }
+    __syncthreads();
     int P[3] = {J.seeds[3 * sidx], J.seeds[3 * sidx + 1], J.seeds[3 * sidx + 2]};
     const int T1 = J.max_iter + 1;
     if (threadIdx.x == 0 && J.traj)
         for (int a = 0; a < 3; ++a) J.traj[(sidx * T1) * 3 + a] = P[a];
     int it = 0, conv = 0, fresh = 0;
     while (it < J.max_iter) {
-        octant_pass(J, ot, cnt, extra, rho_of, P);
+        octant_pass(J, ot, cnt, soff, P);
         fresh = 1;
         for (int w = threadIdx.x; w < 8 * S; w += blockDim.x)
-            hb[w] = window_entropy(cnt + w * B, B, T, L, nullptr);
+            hb[w] = window_entropy(cnt + w * Bs + 1, B, T, L, nullptr);
         __syncthreads();
         if (threadIdx.x < 32) octant_step(J, hb, sh.step);
         __syncthreads();
@@ -278,7 +365,7 @@ __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &
     if (threadIdx.x == 0 && J.traj)
         for (int t = it + (conv ? 0 : 1); t <= J.max_iter; ++t)
             for (int a = 0; a < 3; ++a) J.traj[(sidx * T1 + t) * 3 + a] = P[a];
-    if (!fresh) octant_pass(J, ot, cnt, extra, rho_of, P);     // the last pass was not at P
+    if (!fresh) octant_pass(J, ot, cnt, soff, P);     // the last pass was not at P
     ks_seed_result *o = J.oct_out + sidx;
     kb_from_pass(J, T, L, cnt, extra, hb, sh, o);
     if (threadIdx.x == 0) {
@@ -296,12 +383,27 @@ __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &
 
 // ------------------------------------------------------------ mean shift
 // Packed accumulator word: count in bits [0,11), sum(dx+32) in [11,28),
-// sum(dy+32) in [28,45), sum(dz+32) in [45,62).  A column is shared by
-// 256 / NC threads and a thread walks ceil(rows / 256) rows of at most
-// 2r+1 voxels, so a column sees at most 8*1*15 = 120 voxels (NC = 32,
-// r <= 7), 4*2*25 = 200 (NC = 64, r <= 12) or 2*13*65 = 1690 (NC = 128,
-// r <= 32, at most 3217 rows): count < 2^11 and each offset sum
-// <= 1690 * 64 < 2^17.  No field carries into the next.
+// sum(dy+32) in [28,45), sum(dz+32) in [45,62).  Stored value v >= 1 has
+// columns (v - 1) * NC .. v * NC - 1; a not-counted voxel (v = 0) is
+// skipped.
+//
+// Block path (r > kWarpMsRmax): a column is shared by 256 / NC threads and
+// a thread walks ceil(rows / 256) rows of at most 2r+1 voxels, so a column
+// sees at most 8*1*15 = 120 voxels (NC = 32, r <= 7), 4*2*25 = 200 (NC =
+// 64, r <= 12) or 2*13*65 = 1690 (NC = 128, r <= 32, at most 3217 rows).
+// Warp path (r <= kWarpMsRmax = 20): one warp per item, one column per
+// lane, and a lane walks ceil(rows / 32) <= 40 rows (Ball(20) has 1257) of
+// at most 41 voxels: at most 1640 voxels.  Either way count < 2^11 and
+// each offset sum <= 1690 * 64 < 2^17, so no field carries into the next.
+constexpr int kWarpMsRmax = 20;
+constexpr int kRowWords = 6;           // 8-byte words that cover a row of Ball(r <= 20)
+
+__host__ __device__ inline int ms_block_radii(int r_min, int S) {
+    const int lo = r_min > kWarpMsRmax + 1 ? r_min : kWarpMsRmax + 1;
+    const int r_max = r_min + S - 1;
+    return r_max >= lo ? r_max - lo + 1 : 0;
+}
+
 __device__ __forceinline__ int ms_columns(int nvox) {
     return nvox < 2048 ? 32 : (nvox < 8192 ? 64 : 128);
 }
@@ -310,7 +412,18 @@ __device__ __forceinline__ void red_add_shared_u64(uint32_t addr, unsigned long 
     asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(addr), "l"(v));
 }
 
-// Counts c_b and integer offset sums m_b of Ball(r) at P into acc[b][4].
+// The packed word of voxel t of row e (dy, dz, half-length w) is the row's
+// word plus t << 11.
+__device__ __forceinline__ unsigned long long ms_row_word(uint32_t e, int *dy, int *dz, int *w) {
+    *dy = (int)(e & 0xffu) - 64;
+    *dz = (int)((e >> 8) & 0xffu) - 64;
+    *w = (int)(e >> 16);
+    return 1ull | ((unsigned long long)(32 - *w) << 11) | ((unsigned long long)(*dy + 32) << 28) |
+           ((unsigned long long)(*dz + 32) << 45);
+}
+
+// Block path: counts c_b and integer offset sums m_b of Ball(r) at P into
+// acc[b][4].
 __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long long *cols,
                         int *part, int *acc, const int P[3], int r) {
     const int B = J.vol.B;
@@ -322,16 +435,10 @@ __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long 
     const uint32_t col_addr = smem_u32(cols + (threadIdx.x & (NC - 1)));
     const uint32_t *rows = ot.rows + __ldg(ot.rows_start + r);
     const int nrows = __ldg(ot.rows_start + r + 1) - __ldg(ot.rows_start + r);
-    // one x-row of Ball(r) per thread at a time; voxel t of a row has
-    // dx = t - w, so its packed word is the row's word plus t << 11
     for (int ri = threadIdx.x; ri < nrows; ri += blockDim.x) {
-        const uint32_t e = __ldg(rows + ri);
-        const int dy = (int)(e & 0xffu) - 64, dz = (int)((e >> 8) & 0xffu) - 64;
-        const int w = (int)(e >> 16);
-        const unsigned long long row_inc = 1ull | ((unsigned long long)(32 - w) << 11) |
-                                           ((unsigned long long)(dy + 32) << 28) |
-                                           ((unsigned long long)(dz + 32) << 45);
-        walk_row(c0 + dz * plane + dy * pitch - w, w, [&](int t, uint32_t v) {
+        int dy, dz, w;
+        const unsigned long long row_inc = ms_row_word(__ldg(rows + ri), &dy, &dz, &w);
+        walk_row_masked(c0 + dz * plane + dy * pitch - w, w, [&](int t, uint32_t v) {
             if (v != 0u)
                 red_add_shared_u64(col_addr + (v - 1) * NC * 8,
                                    row_inc + ((unsigned long long)t << 11));
@@ -367,52 +474,199 @@ __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long 
     __syncthreads();
 }
 
-// Eq. 5-6 with a flat window: w_b = sqrt(N / (B c_b)); delta = sum_b w_b m_b /
-// sum_b w_b c_b, bins ascending, empty bins skipped.  Warp 0 computes.
-__device__ void ms_step(const SeedJob &J, const int *acc, double *prod, SeedShared &sh) {
-    const int B = J.vol.B;
-    if (threadIdx.x < 32) {
-        uint32_t n = 0;
-        for (int b = threadIdx.x; b < B; b += 32) n += (uint32_t)acc[4 * b];
-        for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-        const uint32_t N = n;
-        // Empty bins get products of +0.0: adding them leaves every partial
-        // sum unchanged (no sum is -0.0), so the loops below need no branch
-        // and still equal the sums over the occupied bins in bin order.
-        for (int b = threadIdx.x; b < B; b += 32) {
-            const int c = acc[4 * b];
-            if (c > 0) {
-                const double w = __dsqrt_rn(__ddiv_rn((double)N, (double)((int64_t)B * c)));
-                for (int a = 0; a < 3; ++a) prod[a * B + b] = __dmul_rn(w, (double)acc[4 * b + 1 + a]);
-                prod[3 * B + b] = __dmul_rn(w, (double)c);
-            } else {
-                for (int a = 0; a < 4; ++a) prod[a * B + b] = 0.0;
+// Warp path: the same sums with one column per lane.  cols holds B * 32
+// words; acc (B * 4 ints) is written over its start once the columns have
+// been read.
+__device__ void ms_pass_warp(const SeedJob &J, const OffsetTables &ot, unsigned long long *cols,
+                             int *acc, const int P[3], int r) {
+    const int B = J.vol.B, lane = threadIdx.x & 31;
+    for (int k = lane; k < B * 32; k += 32) cols[k] = 0ull;
+    __syncwarp();
+    const uint8_t *c0 = voxel_ptr(J.vol, P);
+    const int plane = (int)J.vol.plane, pitch = (int)J.vol.pitch;
+    const uint32_t col_addr = smem_u32(cols + lane);
+    const uint32_t *rows = ot.rows + __ldg(ot.rows_start + r);
+    const int nrows = __ldg(ot.rows_start + r + 1) - __ldg(ot.rows_start + r);
+    // A lane's rows are lane, lane + 32, ...: the words of the next row are
+    // loaded before the current row is counted, so one row's loads are
+    // always in flight.  A row of Ball(r <= 20) has at most 41 voxels, which
+    // with up to 7 bytes of alignment fit in kRowWords aligned words; the
+    // bytes read past the row stay inside the halo-padded allocation.
+    auto fetch = [&](int ri, uint32_t &e, int &off, unsigned long long (&wd)[kRowWords]) {
+        e = __ldg(rows + ri);
+        const int dy = (int)(e & 0xffu) - 64, dz = (int)((e >> 8) & 0xffu) - 64;
+        const int w = (int)(e >> 16);
+        const uintptr_t a = reinterpret_cast<uintptr_t>(c0 + dz * plane + dy * pitch - w);
+        off = (int)(a & 7u);
+        const unsigned long long *q =
+            reinterpret_cast<const unsigned long long *>(a & ~uintptr_t(7));
+#pragma unroll
+        for (int k = 0; k < kRowWords; ++k) wd[k] = __ldg(q + k);
+    };
+    int ri = lane, off = 0;
+    uint32_t e = 0;
+    unsigned long long wd[kRowWords];
+    if (ri < nrows) fetch(ri, e, off, wd);
+    while (ri < nrows) {
+        const int rn = ri + 32;
+        int offn = 0;
+        uint32_t en = 0;
+        unsigned long long wn[kRowWords];
+        if (rn < nrows) fetch(rn, en, offn, wn);
+        int dy, dz, w;
+        const unsigned long long row_inc = ms_row_word(e, &dy, &dz, &w);
+        // voxel t adds row_inc + (t << 11); that addition stays inside the
+        // low 32 bits, which hold 1 + (32 - w + t) << 11 + ((dy + 32) & 15)
+        // << 28 <= 1 + 2^17 + 15 * 2^28 < 2^32 (t <= 2w, w <= 32)
+        const uint32_t row_lo = (uint32_t)row_inc, row_hi = (uint32_t)(row_inc >> 32);
+        const int n = 2 * w + 1;
+        const uint32_t col_m1 = col_addr - 32 * 8;      // value v's word: col_m1 + 256 v
+#pragma unroll
+        for (int k = 0; k < kRowWords; ++k) {
+            // bytes [lo, hi) of word k belong to the row; the others are
+            // zeroed and so read as "not counted"
+            const int lo = off - 8 * k, hi = off + n - 8 * k;
+            if (hi <= 0) break;
+            unsigned long long x = wd[k];
+            if (lo > 0) x &= ~0ull << (8 * lo);           // word 0 only: lo = off <= 7
+            if (hi < 8) x &= (1ull << (8 * hi)) - 1ull;
+            // byte b is voxel t = 8k + b - off (mod 2^32 arithmetic)
+            const uint32_t lo_k = row_lo + ((uint32_t)(8 * k - off) << 11);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const uint32_t v = byte_of(x, b);
+                if (v != 0u)
+                    red_add_shared_u64(col_m1 + (v << 8), ((unsigned long long)row_hi << 32) |
+                                                              (lo_k + ((uint32_t)b << 11)));
             }
         }
-        __syncwarp();
-        // lane a < 4 sums chain a (three numerators, the denominator)
-        double s = 0.0;
-        if (threadIdx.x < 4)
-            for (int b = 0; b < B; ++b) s = __dadd_rn(s, prod[threadIdx.x * B + b]);
-        const double den = __shfl_sync(0xffffffffu, s, 3);
-        if (threadIdx.x < 3)
-            sh.step[threadIdx.x] = N == 0 ? 0 : (int)round(__ddiv_rn(s, den));
+        e = en;
+        off = offn;
+#pragma unroll
+        for (int k = 0; k < kRowWords; ++k) wd[k] = wn[k];
+        ri = rn;
     }
-    __syncthreads();
+    __syncwarp();
+    // lane b sums bins b and b + 32 over the 32 columns, starting at its
+    // own column so that the lanes' reads fall in different banks
+    int s[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int b = lane + 32 * h;
+        if (b < B) {
+            for (int k = 0; k < 32; ++k) {
+                const unsigned long long x = cols[b * 32 + ((k + lane) & 31)];
+                s[h][0] += (int)(x & 0x7ffull);
+                s[h][1] += (int)((x >> 11) & 0x1ffffull);
+                s[h][2] += (int)((x >> 28) & 0x1ffffull);
+                s[h][3] += (int)((x >> 45) & 0x1ffffull);
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int b = lane + 32 * h;
+        if (b < B) {
+            acc[4 * b] = s[h][0];
+            for (int k = 1; k < 4; ++k) acc[4 * b + k] = s[h][k] - 32 * s[h][0];
+        }
+    }
+    __syncwarp();
+}
+
+// Eq. 5-6 with a flat window, run by one whole warp: w_b = sqrt(N / (B c_b));
+// delta = sum_b w_b m_b / sum_b w_b c_b, bins ascending, empty bins skipped.
+// prod holds 4 * Bp doubles.  Every lane returns the same delta.
+__device__ void ms_delta_warp(int B, const int *acc, double *prod, int step[3]) {
+    const int lane = threadIdx.x & 31, Bp = (B + 7) & ~7;
+    uint32_t n = 0;
+    for (int b = lane; b < B; b += 32) n += (uint32_t)acc[4 * b];
+    for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    const uint32_t N = n;
+    // Empty bins (and the padding up to Bp) get products of +0.0: adding
+    // them leaves every partial sum unchanged (no sum is -0.0), so the
+    // chains below need no branch and still equal the sums over the
+    // occupied bins in bin order.
+    for (int b = lane; b < Bp; b += 32) {
+        const int c = b < B ? acc[4 * b] : 0;
+        if (c > 0) {
+            const double w = __dsqrt_rn(__ddiv_rn((double)N, (double)((int64_t)B * c)));
+            for (int a = 0; a < 3; ++a) prod[a * Bp + b] = __dmul_rn(w, (double)acc[4 * b + 1 + a]);
+            prod[3 * Bp + b] = __dmul_rn(w, (double)c);
+        } else {
+            for (int a = 0; a < 4; ++a) prod[a * Bp + b] = 0.0;
+        }
+    }
+    __syncwarp();
+    // lane a < 4 sums chain a (three numerators, the denominator)
+    const double s = lane < 4 ? chain_sum(prod + lane * Bp, Bp) : 0.0;
+    const double den = __shfl_sync(0xffffffffu, s, 3);
+    const int d = lane < 3 && N != 0 ? (int)round(__ddiv_rn(s, den)) : 0;
+    for (int a = 0; a < 3; ++a) step[a] = __shfl_sync(0xffffffffu, d, a);
+    __syncwarp();
+}
+
+// The item's result, run by one whole warp: rho = sum_b sqrt(c_b / (N B))
+// and H, bins ascending.  Per bin the terms are formed in parallel (+0.0
+// for the bins a sum skips: empty bins for rho, c <= 1 for the entropy sum,
+// whose table values are +0.0), then lanes 0 and 1 add up one chain each.
+__device__ void ms_result_warp(const SeedJob &J, int64_t item, const int *acc, double *prod,
+                               const double *T, const double *L, const int P[3], int r, int it,
+                               int conv) {
+    const int B = J.vol.B, Bp = (B + 7) & ~7, lane = threadIdx.x & 31;
+    uint32_t n = 0;
+    int occ = 0;
+    for (int b = lane; b < B; b += 32) {
+        n += (uint32_t)acc[4 * b];
+        occ += acc[4 * b] > 0;
+    }
+    for (int o = 16; o; o >>= 1) {
+        n += __shfl_xor_sync(0xffffffffu, n, o);
+        occ += __shfl_xor_sync(0xffffffffu, occ, o);
+    }
+    const uint32_t N = n;
+    for (int b = lane; b < Bp; b += 32) {
+        const int c = b < B ? acc[4 * b] : 0;
+        prod[b] = c > 0 ? __dsqrt_rn(__ddiv_rn((double)c, (double)((int64_t)N * B))) : 0.0;
+        prod[Bp + b] = c > 1 ? __ldg(T + c) : 0.0;
+    }
+    __syncwarp();
+    const double chain = lane < 2 ? chain_sum(prod + lane * Bp, Bp) : 0.0;
+    const double s = __shfl_sync(0xffffffffu, chain, 1);
+    if (lane == 0) {
+        ks_ms_result *o = J.ms_out + item;
+        o->x = P[0];
+        o->y = P[1];
+        o->z = P[2];
+        o->r = r;
+        o->seed = (int32_t)(item / J.S);
+        o->iters = it;
+        o->converged = conv;
+        o->reserved = 0;
+        o->rho = chain;
+        o->H = entropy_from_sum(s, N, occ, L);
+    }
+    __syncwarp();
 }
 
 __device__ void ms_item(const SeedJob &J, int64_t item, const OffsetTables &ot, const double *T,
                         const double *L, unsigned long long *cols, int *part, int *acc,
                         double *prod, SeedShared &sh) {
     const int dims[3] = {J.vol.nx, J.vol.ny, J.vol.nz};
-    const int B = J.vol.B;
     const int64_t sidx = item / J.S;
     const int r = J.r_min + (int)(item % J.S);
     int P[3] = {J.seeds[3 * sidx], J.seeds[3 * sidx + 1], J.seeds[3 * sidx + 2]};
     int it = 0, conv = 0, fresh = 0;
     while (it < J.max_iter) {
         ms_pass(J, ot, cols, part, acc, P, r);
-        ms_step(J, acc, prod, sh);
+        if (threadIdx.x < 32) {
+            int d[3];
+            ms_delta_warp(J.vol.B, acc, prod, d);
+            if (threadIdx.x == 0)
+                for (int a = 0; a < 3; ++a) sh.step[a] = d[a];
+        }
+        __syncthreads();
         fresh = 1;
         ++it;
         int Pn[3];
@@ -426,73 +680,94 @@ __device__ void ms_item(const SeedJob &J, int64_t item, const OffsetTables &ot, 
         fresh = 0;
     }
     if (!fresh) ms_pass(J, ot, cols, part, acc, P, r);
-    // rho = sum_b sqrt(c_b / (N B)) and H, bins ascending.
-    if (threadIdx.x < 32) {
-        uint32_t n = 0;
-        for (int b = threadIdx.x; b < B; b += 32) n += (uint32_t)acc[4 * b];
-        for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-        const uint32_t N = n;
-        for (int b = threadIdx.x; b < B; b += 32) {
-            const int c = acc[4 * b];
-            prod[b] = c > 0 ? __dsqrt_rn(__ddiv_rn((double)c, (double)((int64_t)N * B))) : 0.0;
-        }
-        __syncwarp();
-        if (threadIdx.x == 0) {
-            double rho = 0.0, s = 0.0;
-            int occ = 0;
-            for (int b = 0; b < B; ++b) {
-                const uint32_t c = (uint32_t)acc[4 * b];
-                if (c > 0u) rho = __dadd_rn(rho, prod[b]);
-                occ += c > 0u;
-                if (c > 1u) s = __dadd_rn(s, __ldg(T + c));
-            }
-            ks_ms_result *o = J.ms_out + item;
-            o->x = P[0];
-            o->y = P[1];
-            o->z = P[2];
-            o->r = r;
-            o->seed = (int32_t)sidx;
-            o->iters = it;
-            o->converged = conv;
-            o->reserved = 0;
-            o->rho = rho;
-            o->H = entropy_from_sum(s, N, occ, L);
-        }
-    }
+    if (threadIdx.x < 32) ms_result_warp(J, item, acc, prod, T, L, P, r, it, conv);
     __syncthreads();
 }
 
+// One item on one warp; region is the warp's own B * 256 bytes.
+__device__ void ms_item_warp(const SeedJob &J, int64_t item, const OffsetTables &ot,
+                             const double *T, const double *L, unsigned long long *region) {
+    const int dims[3] = {J.vol.nx, J.vol.ny, J.vol.nz};
+    const int B = J.vol.B;
+    int *acc = reinterpret_cast<int *>(region);
+    double *prod = reinterpret_cast<double *>(reinterpret_cast<uint8_t *>(region) +
+                                              ((B * 16 + 15) & ~15));
+    const int64_t sidx = item / J.S;
+    const int r = J.r_min + (int)(item % J.S);
+    int P[3] = {J.seeds[3 * sidx], J.seeds[3 * sidx + 1], J.seeds[3 * sidx + 2]};
+    int it = 0, conv = 0, fresh = 0;
+    while (it < J.max_iter) {
+        ms_pass_warp(J, ot, region, acc, P, r);
+        int d[3];
+        ms_delta_warp(B, acc, prod, d);
+        fresh = 1;
+        ++it;
+        int Pn[3];
+        for (int a = 0; a < 3; ++a) Pn[a] = clampi(P[a] + d[a], 0, dims[a] - 1);
+        if (Pn[0] == P[0] && Pn[1] == P[1] && Pn[2] == P[2]) {
+            conv = 1;
+            break;
+        }
+        for (int a = 0; a < 3; ++a) P[a] = Pn[a];
+        fresh = 0;
+    }
+    if (!fresh) ms_pass_warp(J, ot, region, acc, P, r);
+    ms_result_warp(J, item, acc, prod, T, L, P, r, it, conv);
+}
+
 // Shared-memory layout of one block (the octant and mean-shift views
-// overlap; a block runs one ticket at a time).
+// overlap; a block runs one ticket at a time).  kinds: bit k set when the
+// launch carries tickets of kind k.
 struct Layout {
-    size_t cnt, hb, oct_total;                  // octant: cnt[9][S][B] u32, hb[8S] f64
-    size_t cols, part, acc, prod, ms_total;     // mean shift
-    __host__ __device__ Layout(int B, int S) {
+    size_t cnt, hb, oct_total;                  // octant: cnt[9][S][B+1] u32, hb[8S] f64
+    size_t cols, part, acc, prod, msb_total;    // mean shift, block path
+    size_t msw, msw_stride, msw_total;          // mean shift, warp path: 8 regions
+    int kinds;
+    __host__ __device__ Layout(int B, int S, int kinds_) : kinds(kinds_) {
         cnt = 0;
-        hb = ((size_t)9 * S * B * 4 + 15) / 16 * 16;
+        hb = ((size_t)9 * S * (B + 1) * 4 + 15) / 16 * 16;
         oct_total = hb + (size_t)8 * S * 8;
         cols = 0;
         part = (size_t)B * 128 * 8;
         acc = part + (size_t)B * 8 * 4 * 4;
         prod = acc + (size_t)B * 4 * 4;
-        ms_total = prod + (size_t)4 * B * 8;
+        msb_total = prod + (size_t)4 * ((B + 7) & ~7) * 8;   // 4 chains of Bp doubles
+        // a warp region holds B * 32 column words, later acc (16 B bytes)
+        // and 4 chains of Bp doubles: 16 B + 32 (B + 7) <= 256 B for B >= 2
+        msw = 0;
+        msw_stride = (size_t)B * 256;
+        msw_total = msw + (kSeedThreads / 32) * msw_stride;
     }
-    __host__ __device__ size_t total() const { return oct_total > ms_total ? oct_total : ms_total; }
+    __host__ __device__ size_t total() const {
+        size_t t = 0;
+        if (kinds & (1 << kOctant)) t = oct_total;
+        if (kinds & (1 << kMeanShift)) {
+            t = msb_total > t ? msb_total : t;
+            t = msw_total > t ? msw_total : t;
+        }
+        return t;
+    }
 };
 
-__global__ void __launch_bounds__(kSeedThreads) k_seeds(const SeedQueue q, const OffsetTables ot,
+// KINDS: bit k set when the launch carries tickets of kind k; one
+// instantiation per combination, so each gets its own register allocation.
+template <int KINDS>
+__global__ void __launch_bounds__(kSeedThreads, KINDS == 1 ? 4 : (KINDS == 2 ? 3 : 1)) k_seeds(const SeedQueue q, const OffsetTables ot,
                                                         const double *__restrict__ T,
                                                         const double *__restrict__ L,
                                                         int max_B, int max_S, int persistent) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ SeedShared sh;
     __shared__ uint8_t rho_of[kRmax * kRmax + 1];    // ceil(sqrt(d2)) for d2 <= 32^2
-    for (int d2 = threadIdx.x; d2 <= kRmax * kRmax; d2 += blockDim.x) {
-        int r = 0;
-        while (r * r < d2) ++r;
-        rho_of[d2] = (uint8_t)r;
-    }
-    const Layout lay(max_B, max_S);
+    __shared__ uint32_t soff[kRmax * kRmax + 1];     // octant tickets: shell byte offsets
+    if (KINDS & (1 << kOctant))
+        for (int d2 = threadIdx.x; d2 <= kRmax * kRmax; d2 += blockDim.x) {
+            int r = 0;
+            while (r * r < d2) ++r;
+            rho_of[d2] = (uint8_t)r;
+        }
+    const Layout lay(max_B, max_S, KINDS);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int64_t round = 0;; ++round) {
         if (threadIdx.x == 0)
             sh.ticket = persistent ? (int64_t)atomicAdd(q.head, 1ull)
@@ -506,46 +781,97 @@ __global__ void __launch_bounds__(kSeedThreads) k_seeds(const SeedQueue q, const
         const SeedJob &J = q.jobs[q.seg_job[seg]];
         const int64_t local = t - q.seg_start[seg];
         if (q.seg_kind[seg] == kOctant) {
-            octant_item(J, local, ot, T, L, rho_of, reinterpret_cast<uint32_t *>(smem + lay.cnt),
-                        reinterpret_cast<double *>(smem + lay.hb), sh);
+            if constexpr ((KINDS & (1 << kOctant)) != 0)
+                octant_item(J, local, ot, T, L, rho_of, soff,
+                            reinterpret_cast<uint32_t *>(smem + lay.cnt),
+                            reinterpret_cast<double *>(smem + lay.hb), sh);
+            continue;
+        }
+        if constexpr ((KINDS & (1 << kMeanShift)) == 0) {
+            continue;
         } else {
-            // largest radius first: ticket -> (seed, r)
-            const int64_t r_idx = J.S - 1 - local / J.n_seeds;
+        if (q.seg_kind[seg] == kMeanShift) {
+            // one item of a radius above kWarpMsRmax on the whole block,
+            // largest radius first
+            const int S_big = ms_block_radii(J.r_min, J.S);
+            const int64_t r_idx = J.S - 1 - local / J.n_seeds;   // >= J.S - S_big
+            (void)S_big;
             const int64_t item = (local % J.n_seeds) * J.S + r_idx;
             ms_item(J, item, ot, T, L, reinterpret_cast<unsigned long long *>(smem + lay.cols),
                     reinterpret_cast<int *>(smem + lay.part), reinterpret_cast<int *>(smem + lay.acc),
                     reinterpret_cast<double *>(smem + lay.prod), sh);
+            continue;
+        }
+        // kMsWarp: items of radii <= kWarpMsRmax, one per warp.  Their
+        // segments follow every other segment of the queue, so from the
+        // first such ticket on each warp draws its own tickets and the block
+        // never synchronises again: an item that takes long holds only its
+        // own warp.  (Without a persistent queue a block runs its one ticket
+        // on warp 0.)
+        unsigned long long *region =
+            reinterpret_cast<unsigned long long *>(smem + lay.msw + warp * lay.msw_stride);
+        int64_t tw = warp == 0 ? t : -1;
+        int sw = seg;
+        for (;;) {
+            if (tw < 0) {
+                if (!persistent) break;
+                unsigned long long x = 0;
+                if (lane == 0) x = atomicAdd(q.head, 1ull);
+                tw = (int64_t)__shfl_sync(0xffffffffu, x, 0);
+            }
+            if (tw >= q.n_tickets) break;
+            while (sw + 1 < q.n_segs && tw >= q.seg_start[sw + 1]) ++sw;
+            const SeedJob &Jw = q.jobs[q.seg_job[sw]];
+            const int64_t lw = tw - q.seg_start[sw];
+            // largest radius first, consecutive seeds side by side (their
+            // windows overlap, so concurrent warps share L1 lines)
+            const int S_small = Jw.S - ms_block_radii(Jw.r_min, Jw.S);
+            const int64_t r_idx = S_small - 1 - lw / Jw.n_seeds;
+            ms_item_warp(Jw, (lw % Jw.n_seeds) * Jw.S + r_idx, ot, T, L, region);
+            tw = -1;
+        }
+        return;
         }
     }
 }
 
 }  // namespace
 
-int64_t seed_tickets(int kind, int64_t n_seeds, int S) {
-    return kind == kOctant ? n_seeds : n_seeds * S;
+int64_t seed_tickets(int kind, int64_t n_seeds, int r_min, int S) {
+    if (kind == kOctant) return n_seeds;
+    const int S_big = ms_block_radii(r_min, S);
+    return n_seeds * (kind == kMeanShift ? S_big : S - S_big);
 }
 
-size_t seed_smem_bytes(int B, int S) { return Layout(B, S).total(); }
+size_t seed_smem_bytes(int B, int S, int kinds) { return Layout(B, S, kinds).total(); }
 
-int seed_blocks_per_sm(int max_B, int max_S) {
+using SeedKernel = void (*)(const SeedQueue, const OffsetTables, const double *, const double *,
+                            int, int, int);
+static SeedKernel seed_kernel(int kinds) {
+    return kinds == (1 << kOctant) ? k_seeds<1 << kOctant>
+           : kinds == (1 << kMeanShift) ? k_seeds<1 << kMeanShift>
+                                        : k_seeds<(1 << kOctant) | (1 << kMeanShift)>;
+}
+
+int seed_blocks_per_sm(int max_B, int max_S, int kinds) {
     // the occupancy query honours the kernel's dynamic shared-memory limit,
     // so raise it to this layout's size first
-    const size_t smem = seed_smem_bytes(max_B, max_S);
-    cudaFuncSetAttribute(k_seeds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = seed_smem_bytes(max_B, max_S, kinds);
+    const SeedKernel k = seed_kernel(kinds);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seeds, kSeedThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kSeedThreads, smem);
     return n < 1 ? 1 : n;
 }
 
 cudaError_t launch_seeds(const LaunchCtx &lc, const SeedQueue &q, const OffsetTables &ot,
-                         const double *T, const double *L, int max_B, int max_S,
+                         const double *T, const double *L, int max_B, int max_S, int kinds,
                          bool persistent, int grid) {
-    const size_t smem = seed_smem_bytes(max_B, max_S);
-    cudaError_t e =
-        cudaFuncSetAttribute(k_seeds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = seed_smem_bytes(max_B, max_S, kinds);
+    const SeedKernel k = seed_kernel(kinds);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_seeds<<<grid, kSeedThreads, smem, lc.stream>>>(q, ot, T, L, max_B, max_S,
-                                                     persistent ? 1 : 0);
+    k<<<grid, kSeedThreads, smem, lc.stream>>>(q, ot, T, L, max_B, max_S, persistent ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -250,6 +250,17 @@ def test_seeds_mr256_sampled(ctx, ko, ks_mod):
     _ms_vs_oracle(ctx, ko, ks_mod, w, seeds=seeds[:20])
 
 
+def test_meanshift_radii_across_warp_and_block_paths(ctx, ko, ks_mod):
+    """Radii 17..23: items with r <= 20 run one per warp, the others one per
+    block, in one launch; 5 bins (not a multiple of 8), ragged last ticket."""
+    rng = np.random.default_rng(11)
+    vol = rng.integers(0, 5, size=(30, 36, 40)).astype(np.uint8)
+    vol[:, :, :13] = 2                       # a flat slab beside the noise
+    w = synth.Workload("mixed", vol, {"kind": 0, "bins": 5, "shift": 0, "lo": 0, "hi": 4},
+                       17, 23, 9, 12)
+    _ms_vs_oracle(ctx, ko, ks_mod, w)
+
+
 def test_seed_edge_cases(ctx, ko, ks_mod):
     ks = ks_mod
     # constant volume: every seed converges at once; excluded voxels only: N = 0
