@@ -192,7 +192,8 @@ cudaError_t launch_dense(const LaunchCtx &lc, const VolDesc &v, const CUtensorMa
 
 // ks_seeds.cu
 // Ticket kinds of a queue segment: an octant seed; a mean-shift (seed, r)
-// item with r > 20 run by a whole block; one with r <= 20 run by one warp.
+// item run by a whole block (r > 20 or more than 32 bins); one run by a
+// single warp (r <= 20 and at most 32 bins).
 // A launch's kinds mask has bit kOctant and/or bit kMeanShift (the latter
 // covering both mean-shift kinds).
 enum ItemKind { kOctant = 0, kMeanShift = 1, kMsWarp = 2 };
@@ -219,7 +220,7 @@ struct SeedQueue {
     int64_t n_tickets;
     unsigned long long *head;    // persistent mode: next ticket counter
 };
-int64_t seed_tickets(int kind, int64_t n_seeds, int r_min, int S);
+int64_t seed_tickets(int kind, int64_t n_seeds, int r_min, int S, int B);
 // kinds: bit k set when a launch carries tickets of kind k
 size_t seed_smem_bytes(int B, int S, int kinds);
 cudaError_t launch_seeds(const LaunchCtx &lc, const SeedQueue &q, const OffsetTables &ot,

@@ -387,18 +387,23 @@ __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &
 // columns (v - 1) * NC .. v * NC - 1; a not-counted voxel (v = 0) is
 // skipped.
 //
-// Block path (r > kWarpMsRmax): a column is shared by 256 / NC threads and
-// a thread walks ceil(rows / 256) rows of at most 2r+1 voxels, so a column
-// sees at most 8*1*15 = 120 voxels (NC = 32, r <= 7), 4*2*25 = 200 (NC =
+// Block path (r > kWarpMsRmax or B > kWarpMsBmax): a column is shared by
+// 256 / NC threads and a thread walks ceil(rows / 256) rows of at most 2r+1
+// voxels, so a column sees at most 8*1*15 = 120 voxels (NC = 32, r <= 7), 4*2*25 = 200 (NC =
 // 64, r <= 12) or 2*13*65 = 1690 (NC = 128, r <= 32, at most 3217 rows).
 // Warp path (r <= kWarpMsRmax = 20): one warp per item, one column per
 // lane, and a lane walks ceil(rows / 32) <= 40 rows (Ball(20) has 1257) of
 // at most 41 voxels: at most 1640 voxels.  Either way count < 2^11 and
 // each offset sum <= 1690 * 64 < 2^17, so no field carries into the next.
 constexpr int kWarpMsRmax = 20;
+constexpr int kWarpMsBmax = 32;
 constexpr int kRowWords = 6;           // 8-byte words that cover a row of Ball(r <= 20)
 
-__host__ __device__ inline int ms_block_radii(int r_min, int S) {
+// Radii run on the block path: those above kWarpMsRmax, or all of them
+// when B > kWarpMsBmax (a warp's columns would take B * 256 bytes, and
+// eight such regions would starve the block path of occupancy).
+__host__ __device__ inline int ms_block_radii(int r_min, int S, int B) {
+    if (B > kWarpMsBmax) return S;
     const int lo = r_min > kWarpMsRmax + 1 ? r_min : kWarpMsRmax + 1;
     const int r_max = r_min + S - 1;
     return r_max >= lo ? r_max - lo + 1 : 0;
@@ -736,7 +741,7 @@ struct Layout {
         // and 4 chains of Bp doubles: 16 B + 32 (B + 7) <= 256 B for B >= 2
         msw = 0;
         msw_stride = (size_t)B * 256;
-        msw_total = msw + (kSeedThreads / 32) * msw_stride;
+        msw_total = B <= kWarpMsBmax ? msw + (kSeedThreads / 32) * msw_stride : 0;
     }
     __host__ __device__ size_t total() const {
         size_t t = 0;
@@ -752,7 +757,7 @@ struct Layout {
 // KINDS: bit k set when the launch carries tickets of kind k; one
 // instantiation per combination, so each gets its own register allocation.
 template <int KINDS>
-__global__ void __launch_bounds__(kSeedThreads, KINDS == 1 ? 4 : (KINDS == 2 ? 3 : 1)) k_seeds(const SeedQueue q, const OffsetTables ot,
+__global__ void __launch_bounds__(kSeedThreads, KINDS == 1 ? 4 : (KINDS == 2 ? 2 : 1)) k_seeds(const SeedQueue q, const OffsetTables ot,
                                                         const double *__restrict__ T,
                                                         const double *__restrict__ L,
                                                         int max_B, int max_S, int persistent) {
@@ -793,9 +798,7 @@ __global__ void __launch_bounds__(kSeedThreads, KINDS == 1 ? 4 : (KINDS == 2 ? 3
         if (q.seg_kind[seg] == kMeanShift) {
             // one item of a radius above kWarpMsRmax on the whole block,
             // largest radius first
-            const int S_big = ms_block_radii(J.r_min, J.S);
-            const int64_t r_idx = J.S - 1 - local / J.n_seeds;   // >= J.S - S_big
-            (void)S_big;
+            const int64_t r_idx = J.S - 1 - local / J.n_seeds;   // a block-path radius
             const int64_t item = (local % J.n_seeds) * J.S + r_idx;
             ms_item(J, item, ot, T, L, reinterpret_cast<unsigned long long *>(smem + lay.cols),
                     reinterpret_cast<int *>(smem + lay.part), reinterpret_cast<int *>(smem + lay.acc),
@@ -825,7 +828,7 @@ __global__ void __launch_bounds__(kSeedThreads, KINDS == 1 ? 4 : (KINDS == 2 ? 3
             const int64_t lw = tw - q.seg_start[sw];
             // largest radius first, consecutive seeds side by side (their
             // windows overlap, so concurrent warps share L1 lines)
-            const int S_small = Jw.S - ms_block_radii(Jw.r_min, Jw.S);
+            const int S_small = Jw.S - ms_block_radii(Jw.r_min, Jw.S, Jw.vol.B);
             const int64_t r_idx = S_small - 1 - lw / Jw.n_seeds;
             ms_item_warp(Jw, (lw % Jw.n_seeds) * Jw.S + r_idx, ot, T, L, region);
             tw = -1;
@@ -837,9 +840,9 @@ __global__ void __launch_bounds__(kSeedThreads, KINDS == 1 ? 4 : (KINDS == 2 ? 3
 
 }  // namespace
 
-int64_t seed_tickets(int kind, int64_t n_seeds, int r_min, int S) {
+int64_t seed_tickets(int kind, int64_t n_seeds, int r_min, int S, int B) {
     if (kind == kOctant) return n_seeds;
-    const int S_big = ms_block_radii(r_min, S);
+    const int S_big = ms_block_radii(r_min, S, B);
     return n_seeds * (kind == kMeanShift ? S_big : S - S_big);
 }
 
