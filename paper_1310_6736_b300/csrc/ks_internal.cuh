@@ -19,7 +19,8 @@ constexpr int kRmax = 32;            // largest supported window radius
 constexpr int kTableN = 137065;      // |Ball(32)|: largest possible count
 constexpr int kMaxBins = 64;
 constexpr int kMaxScales = kRmax;    // r_max - r_min + 1 <= 32
-constexpr int kSeedThreads = 256;    // block size of the seed kernels
+constexpr int kSeedThreads = 256;    // block size of the mean-shift (and mixed) seed kernels
+constexpr int kOctThreads = 256;     // block size of the octant-only seed kernel
 
 // Device status word bits (ctx->d_status); read back by ks_sync.
 constexpr int kStatusTmaTimeout = 1;

@@ -220,12 +220,21 @@ __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *
         }
     }
     __syncthreads();
+    // prefix over shells per (octant, value) column, eight shells at a time:
+    // the eight loads are issued before any store of the group
     for (int col = threadIdx.x; col < 9 * Bs; col += blockDim.x) {    // 8 octants + excess
         const int j = col / Bs, b = col % Bs;
+        uint32_t *p = cnt + j * S * Bs + b;
         uint32_t run = 0;
-        for (int si = 0; si < S; ++si) {
-            run += cnt[(j * S + si) * Bs + b];
-            cnt[(j * S + si) * Bs + b] = run;
+        for (int s0 = 0; s0 < S; s0 += 8) {
+            uint32_t x[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] = s0 + k < S ? p[(s0 + k) * Bs] : 0u;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                run += x[k];
+                if (s0 + k < S) p[(s0 + k) * Bs] = run;
+            }
         }
     }
     __syncthreads();
@@ -757,7 +766,9 @@ struct Layout {
 // KINDS: bit k set when the launch carries tickets of kind k; one
 // instantiation per combination, so each gets its own register allocation.
 template <int KINDS>
-__global__ void __launch_bounds__(kSeedThreads, KINDS == 1 ? 4 : (KINDS == 2 ? 2 : 1)) k_seeds(const SeedQueue q, const OffsetTables ot,
+__global__ void __launch_bounds__(KINDS == 1 ? kOctThreads : kSeedThreads,
+                                  KINDS == 1 ? 4 : (KINDS == 2 ? 2 : 1))
+    k_seeds(const SeedQueue q, const OffsetTables ot,
                                                         const double *__restrict__ T,
                                                         const double *__restrict__ L,
                                                         int max_B, int max_S, int persistent) {
@@ -850,6 +861,8 @@ size_t seed_smem_bytes(int B, int S, int kinds) { return Layout(B, S, kinds).tot
 
 using SeedKernel = void (*)(const SeedQueue, const OffsetTables, const double *, const double *,
                             int, int, int);
+static int seed_threads(int kinds) { return kinds == (1 << kOctant) ? kOctThreads : kSeedThreads; }
+
 static SeedKernel seed_kernel(int kinds) {
     return kinds == (1 << kOctant) ? k_seeds<1 << kOctant>
            : kinds == (1 << kMeanShift) ? k_seeds<1 << kMeanShift>
@@ -863,7 +876,7 @@ int seed_blocks_per_sm(int max_B, int max_S, int kinds) {
     const SeedKernel k = seed_kernel(kinds);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kSeedThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, seed_threads(kinds), smem);
     return n < 1 ? 1 : n;
 }
 
@@ -874,7 +887,7 @@ cudaError_t launch_seeds(const LaunchCtx &lc, const SeedQueue &q, const OffsetTa
     const SeedKernel k = seed_kernel(kinds);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, kSeedThreads, smem, lc.stream>>>(q, ot, T, L, max_B, max_S, persistent ? 1 : 0);
+    k<<<grid, seed_threads(kinds), smem, lc.stream>>>(q, ot, T, L, max_B, max_S, persistent ? 1 : 0);
     return cudaGetLastError();
 }
 
