@@ -202,6 +202,8 @@ def run_ks(args):
     n_vox = nx * ny * nz
     S = w.r_max - w.r_min + 1
     params = ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter)
+    if args.dense_config:                               # pin the dense launch shape
+        ks.force_dense_config(*[int(x) for x in args.dense_config.split(",")])
     ctx = ks.Context()
     stream = torch.cuda.current_stream()
     raw_dev = torch.from_numpy(w.volume).cuda()
@@ -297,7 +299,9 @@ def run_ks(args):
                        "step_ms_p99": float(np.percentile(step_ms, 99)),
                        "parallelism": f"{ws} independent volume(s), one per GPU",
                        "dense_launch": dict(zip(("path", "warps", "tile_y", "tile_z"),
-                                                ctx.dense_config(w.binning["bins"], w.r_max)
+                                                ([int(x) for x in args.dense_config.split(",")]
+                                                 if args.dense_config else
+                                                 ctx.dense_config(w.binning["bins"], w.r_max))
                                                 or (None,) * 4))},
             "roofline": {"bound": "smem", "achieved": achieved / 1e9,
                          "peak": smem_peak / 1e9, "unit": "Gupdates/s",
