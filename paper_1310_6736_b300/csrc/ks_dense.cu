@@ -15,6 +15,9 @@
 //            by an immediate.  Centres past nx are evaluated (their reads stay
 //            inside the zeroed halo and the allocation's slack) but not
 //            written.
+//   PATH 3 = (launch path 3, r_max <= 25) four adjacent centres per lane,
+//            128 per warp, whose four bins per offset come from two aligned
+//            32-bit loads and a funnel shift (k_dense4).
 //   scale  = built incrementally: shell r (offsets o with ceil|o| == r, and
 //            everything up to r_min for the first scale) is added to the
 //            counts of r-1.
@@ -104,27 +107,107 @@ struct Src<1> {              // halo-padded volume in global memory
 
 // Shared-memory words of one lane.  Counters: one word per stored value
 // v = 0..B.  When every count fits in 16 bits (|Ball(r_max)| <= 65535, i.e.
-// r_max <= 25) the two centres of a two-centre lane share each word (centre
-// j in bits 16j..16j+15, so an update adds 1 << 16j); otherwise each centre
-// has its own 32-bit column.  After the counters come the previous scale's
-// counts of each centre: 16-bit pairs (values 2w, 2w+1 in word w) when they
-// fit, 32-bit words otherwise.
+// r_max <= 25) two centres of a lane share each word (centre j in bits
+// 16 (j & 1) .. 16 (j & 1) + 15 of pair j >> 1, so an update adds
+// 1 << 16 (j & 1)); otherwise each centre has its own 32-bit column.  After
+// the counters come the previous scale's counts of each centre: 16-bit
+// pairs (values 2w, 2w+1 in word w) when they fit, 32-bit words otherwise.
 template <int B, bool WIDE, int CPL>
 struct Words {
-    static constexpr bool kPack = CPL == 2 && !WIDE;
+    static constexpr bool kPack = CPL >= 2 && !WIDE;
     static constexpr int kNW = B + 1;                          // counter words per column
     static constexpr int kNP = WIDE ? B + 1 : (B + 2) / 2;     // previous words per centre
-    static constexpr int kCols = kPack ? 1 : CPL;              // counter columns
+    static constexpr int kCols = kPack ? CPL / 2 : CPL;        // counter columns
     static constexpr int kPerLane = kCols * kNW + CPL * kNP;
     // word index of centre j's counter of value v / previous word w
     __host__ __device__ static constexpr int cnt(int j, int v) {
-        return (kPack ? 0 : j * kNW) + v;
+        return (kPack ? (j >> 1) : j) * kNW + v;
     }
     __host__ __device__ static constexpr int prev(int j, int w) {
         return kCols * kNW + j * kNP + w;
     }
-    __host__ __device__ static constexpr uint32_t inc(int j) { return kPack ? 1u << (16 * j) : 1u; }
+    __host__ __device__ static constexpr uint32_t inc(int j) {
+        return kPack ? 1u << (16 * (j & 1)) : 1u;
+    }
 };
+
+// Running state of one centre over the scales: H at scale index i-1 and
+// i-2, N at i-1 and i-2, D at i-1, and the best Y and its scale so far.
+struct ScaleState {
+    double hm1, hm2, yb;
+    uint32_t nm1, nm2;
+    uint64_t dm1;
+    int sb;
+};
+
+// After the shell of scale r (index i): the centre's exact N, the bin-order
+// entropy sum, D against the previous scale's counts (refreshed in the same
+// pass), H, the peak test at scale r - 1 and the optional H/W outputs.
+template <int B, bool WIDE, int CPL>
+__device__ __forceinline__ void scale_step(const DenseArgs &a, uint32_t cnt_lane, int j, int i,
+                                           int r, ScaleState &st, int64_t oidx, bool live) {
+    using Wd = Words<B, WIDE, CPL>;
+    constexpr int NP = Wd::kNP;
+    auto word = [&](int w) { return cnt_lane + ((uint32_t)w << 7); };
+    auto count = [&](int v) -> uint32_t {
+        const uint32_t x = ld_shared_u32(word(Wd::cnt(j, v)));
+        return Wd::kPack ? (x >> (16 * (j & 1))) & 0xffffu : x;
+    };
+    const uint32_t N = (uint32_t)__ldg(a.ot.ball_size + r) - count(0);
+    double ssum = 0.0;
+    int occ = 0;
+    uint64_t D = 0;
+    auto term = [&](uint32_t c, uint32_t p) {
+        occ += c > 0u;
+        if (c > 1u) ssum = __dadd_rn(ssum, __ldg(a.T + c));
+        const int64_t d = (int64_t)c * st.nm1 - (int64_t)p * N;
+        D += (uint64_t)(d < 0 ? -d : d);
+    };
+    if constexpr (WIDE) {
+#pragma unroll
+        for (int vv = 1; vv <= B; ++vv) {
+            const uint32_t c = count(vv);
+            const uint32_t p = ld_shared_u32(word(Wd::prev(j, vv)));
+            st_shared_u32(word(Wd::prev(j, vv)), c);
+            term(c, p);
+        }
+    } else {
+        // previous counts as 16-bit pairs: word w holds values 2w, 2w+1
+#pragma unroll
+        for (int w = 0; w < NP; ++w) {
+            const uint32_t pw = ld_shared_u32(word(Wd::prev(j, w)));
+            uint32_t c_lo = 0, c_hi = 0;
+            if (2 * w >= 1 && 2 * w <= B) {
+                c_lo = count(2 * w);
+                term(c_lo, pw & 0xffffu);
+            }
+            if (2 * w + 1 <= B) {
+                c_hi = count(2 * w + 1);
+                term(c_hi, pw >> 16);
+            }
+            st_shared_u32(word(Wd::prev(j, w)), c_lo | (c_hi << 16));
+        }
+    }
+    const double H = entropy_from_sum(ssum, N, occ, a.L);
+
+    if (i >= 2 && st.hm2 < st.hm1 && st.hm1 >= H) {   // peak at scale i-1
+        const double W = kb_weight(st.dm1, st.nm1, st.nm2, r - 1, a.w_norm);
+        const double y = __dmul_rn(st.hm1, W);
+        if (st.sb == 0 || y > st.yb) {
+            st.yb = y;
+            st.sb = r - 1;
+        }
+    }
+    if (live && (a.out.H || a.out.W)) {
+        if (a.out.H) a.out.H[oidx * a.S + i] = H;
+        if (a.out.W) a.out.W[oidx * a.S + i] = i == 0 ? 0.0 : kb_weight(D, N, st.nm1, r, a.w_norm);
+    }
+    st.hm2 = st.hm1;
+    st.hm1 = H;
+    st.nm2 = st.nm1;
+    st.nm1 = N;
+    st.dm1 = D;
+}
 
 template <int B, bool WIDE, int PATH, int CPL>
 __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
@@ -133,7 +216,6 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
     __shared__ int s_ok;
     using Wd = Words<B, WIDE, CPL>;
     constexpr bool CTAB = !WIDE;                 // r_max <= 25: table in constant memory
-    constexpr int NP = Wd::kNP;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -194,17 +276,10 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
 #pragma unroll 4
         for (int w = 0; w < Wd::kPerLane; ++w) st_shared_u32(word(w), 0u);
 
-        double hm1[CPL], hm2[CPL], yb[CPL];     // H at scale index i-1, i-2; best Y
-        uint32_t nm1[CPL], nm2[CPL];            // N at i-1, i-2
-        uint64_t dm1[CPL];                      // D at i-1
-        int sb[CPL];
+        ScaleState st[CPL];
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) {
-            hm1[j] = hm2[j] = yb[j] = 0.0;
-            nm1[j] = nm2[j] = 0;
-            dm1[j] = 0;
-            sb[j] = 0;
-        }
+        for (int j = 0; j < CPL; ++j) st[j] = ScaleState{0.0, 0.0, 0.0, 0u, 0u, 0ull, 0};
+        const int64_t orow = ((int64_t)cz * a.vol.ny + cy) * a.vol.nx;
 
         for (int i = 0; i < a.S; ++i) {
             const int r = a.r_min + i;
@@ -249,80 +324,118 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
                     for (int j = 0; j < CPL; ++j) red_add_shared(word(Wd::cnt(j, v[j])), Wd::inc(j));
                 }
             }
-
             // ---- exact per-scale quantities from each centre's counters
 #pragma unroll
-            for (int j = 0; j < CPL; ++j) {
-                auto count = [&](int v) -> uint32_t {
-                    const uint32_t x = ld_shared_u32(word(Wd::cnt(j, v)));
-                    return Wd::kPack ? (x >> (16 * j)) & 0xffffu : x;
-                };
-                const uint32_t N = (uint32_t)__ldg(a.ot.ball_size + r) - count(0);
-                double ssum = 0.0;
-                int occ = 0;
-                uint64_t D = 0;
-                auto term = [&](uint32_t c, uint32_t p) {
-                    occ += c > 0u;
-                    if (c > 1u) ssum = __dadd_rn(ssum, __ldg(a.T + c));
-                    const int64_t d = (int64_t)c * nm1[j] - (int64_t)p * N;
-                    D += (uint64_t)(d < 0 ? -d : d);
-                };
-                if constexpr (WIDE) {
-#pragma unroll
-                    for (int vv = 1; vv <= B; ++vv) {
-                        const uint32_t c = count(vv);
-                        const uint32_t p = ld_shared_u32(word(Wd::prev(j, vv)));
-                        st_shared_u32(word(Wd::prev(j, vv)), c);
-                        term(c, p);
-                    }
-                } else {
-                    // previous counts as 16-bit pairs: word w holds values 2w, 2w+1
-#pragma unroll
-                    for (int w = 0; w < NP; ++w) {
-                        const uint32_t pw = ld_shared_u32(word(Wd::prev(j, w)));
-                        uint32_t c_lo = 0, c_hi = 0;
-                        if (2 * w >= 1 && 2 * w <= B) {
-                            c_lo = count(2 * w);
-                            term(c_lo, pw & 0xffffu);
-                        }
-                        if (2 * w + 1 <= B) {
-                            c_hi = count(2 * w + 1);
-                            term(c_hi, pw >> 16);
-                        }
-                        st_shared_u32(word(Wd::prev(j, w)), c_lo | (c_hi << 16));
-                    }
-                }
-                const double H = entropy_from_sum(ssum, N, occ, a.L);
-
-                if (i >= 2 && hm2[j] < hm1[j] && hm1[j] >= H) {   // peak at scale i-1
-                    const double W = kb_weight(dm1[j], nm1[j], nm2[j], r - 1, a.w_norm);
-                    const double y = __dmul_rn(hm1[j], W);
-                    if (sb[j] == 0 || y > yb[j]) {
-                        yb[j] = y;
-                        sb[j] = r - 1;
-                    }
-                }
-                const int cxj = cx + 32 * j;
-                if (cxj < a.vol.nx && (a.out.H || a.out.W)) {
-                    const int64_t oidx = ((int64_t)cz * a.vol.ny + cy) * a.vol.nx + cxj;
-                    if (a.out.H) a.out.H[oidx * a.S + i] = H;
-                    if (a.out.W)
-                        a.out.W[oidx * a.S + i] = i == 0 ? 0.0 : kb_weight(D, N, nm1[j], r, a.w_norm);
-                }
-                hm2[j] = hm1[j];
-                hm1[j] = H;
-                nm2[j] = nm1[j];
-                nm1[j] = N;
-                dm1[j] = D;
-            }
+            for (int j = 0; j < CPL; ++j)
+                scale_step<B, WIDE, CPL>(a, cnt_lane, j, i, r, st[j], orow + cx + 32 * j,
+                                         cx + 32 * j < a.vol.nx);
         }
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
             const int cxj = cx + 32 * j;
             if (cxj < a.vol.nx) {
-                const int64_t oidx = ((int64_t)cz * a.vol.ny + cy) * a.vol.nx + cxj;
-                a.out.Y[oidx] = yb[j];
-                a.out.s[oidx] = (uint8_t)sb[j];
+                a.out.Y[orow + cxj] = st[j].yb;
+                a.out.s[orow + cxj] = (uint8_t)st[j].sb;
+            }
+        }
+    }
+}
+
+// Launch path 3 (r_max <= 25): lane l of a warp takes the four adjacent
+// centres x0 + 4l .. x0 + 4l + 3 of a row, so a warp covers 128 centres.
+// For an offset o the four bins are the bytes x0 + 4l + o .. + 3: two
+// aligned 32-bit loads (the row start is 16-byte aligned, so the
+// misalignment s = o & 3 is the same for every lane) and a funnel shift
+// give all four, and one warp-wide load fetches 128 consecutive bytes
+// instead of 32.  The centres' counters are packed in pairs.  Reads reach
+// from 3 bytes before x0 + o to 7 bytes after x0 + 127 + o: for |o| <= r_max
+// that stays inside the zeroed halo, the neighbouring row or the
+// allocation's 256 bytes of slack.
+template <int B>
+__global__ void __launch_bounds__(256) k_dense4(const DenseArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    constexpr int CPL = 4;
+    using Wd = Words<B, false, CPL>;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int tx0 = blockIdx.x * 128, ty0 = blockIdx.y * a.ty, tz0 = a.z0 + blockIdx.z * a.tz;
+    const int pz = (int)a.vol.plane, py = (int)a.vol.pitch;
+    const Tab<true> tab{a.ot};
+    const uint32_t cnt_lane = smem_u32(smem + a.cnt_off) + (warp * Wd::kPerLane * 32 + lane) * 4;
+    auto word = [&](int w) { return cnt_lane + ((uint32_t)w << 7); };
+    // the four bins of offset o, centre j in byte j
+    auto bins4 = [](const uint8_t *p, int o) -> uint32_t {
+        const int s = o & 3;
+        const uint32_t *q = reinterpret_cast<const uint32_t *>(p + (o - s));
+        return __funnelshift_r(__ldg(q), __ldg(q + 1), 8 * s);
+    };
+    auto add4 = [&](uint32_t b4) {
+#pragma unroll
+        for (int j = 0; j < CPL; ++j)       // byte j of b4, zero-extended
+            red_add_shared(word(Wd::cnt(j, __byte_perm(b4, 0u, 0x4440u + j))), Wd::inc(j));
+    };
+    const int nrows = a.ty * a.tz;
+
+    for (int row = warp; row < nrows; row += nwarps) {
+        const int cy = ty0 + row % a.ty, cz = tz0 + row / a.ty;
+        if (cy >= a.vol.ny || cz >= a.z1) continue;              // warp-uniform
+        const int cx = tx0 + 4 * lane;                           // centres cx .. cx + 3
+        const uint8_t *c0 = a.vol.base + (int64_t)cz * a.vol.plane + (int64_t)cy * a.vol.pitch + cx;
+
+#pragma unroll 4
+        for (int w = 0; w < Wd::kPerLane; ++w) st_shared_u32(word(w), 0u);
+
+        ScaleState st[CPL];
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) st[j] = ScaleState{0.0, 0.0, 0.0, 0u, 0u, 0ull, 0};
+        const int64_t orow = ((int64_t)cz * a.vol.ny + cy) * a.vol.nx;
+
+        for (int i = 0; i < a.S; ++i) {
+            const int r = a.r_min + i;
+            for (int rho = (i == 0 ? 0 : r); rho <= r; ++rho) {
+                const int k0 = tab.c8_start(rho), k1 = tab.c8_start(rho + 1);
+                const int k2 = tab.rest_start(rho), k3 = tab.rest_start(rho + 1);
+                uint32_t e = tab.c8(k0);
+                for (int k = k0; k < k1; ++k) {
+                    const uint32_t en = tab.c8(k + 1);
+                    const int X = (int)(e & 0xffu);
+                    const int Y = (int)((e >> 8) & 0xffu) * py;
+                    const int Z = (int)((e >> 16) & 0xffu) * pz;
+                    // pitch and plane are multiples of 16, so the
+                    // misalignment of a mirror depends only on the sign of X
+                    const int sp = X & 3, sm = (-X) & 3;
+                    const int Xa = X - sp, Xc = X + sm;          // X rounded down / up to 4
+                    const int oa[8] = {Z + Y + Xa, Z + Y - Xc, Z - Y + Xa, Z - Y - Xc,
+                                       Y - Z + Xa, Y - Z - Xc, -Z - Y + Xa, -Z - Y - Xc};
+                    uint32_t b[8];
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        const uint32_t *q = reinterpret_cast<const uint32_t *>(c0 + oa[m]);
+                        b[m] = __funnelshift_r(__ldg(q), __ldg(q + 1), 8 * ((m & 1) ? sm : sp));
+                    }
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) add4(b[m]);
+                    e = en;
+                }
+#pragma unroll 2
+                for (int k = k2; k < k3; ++k) {
+                    const uint32_t f = tab.rest(k);
+                    const int off = ((int)((f >> 16) & 0xffu) - 64) * pz +
+                                    ((int)((f >> 8) & 0xffu) - 64) * py + ((int)(f & 0xffu) - 64);
+                    add4(bins4(c0, off));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < CPL; ++j)
+                scale_step<B, false, CPL>(a, cnt_lane, j, i, r, st[j], orow + cx + j,
+                                          cx + j < a.vol.nx);
+        }
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+            if (cx + j < a.vol.nx) {
+                a.out.Y[orow + cx + j] = st[j].yb;
+                a.out.s[orow + cx + j] = (uint8_t)st[j].sb;
             }
         }
     }
@@ -339,7 +452,7 @@ struct Geometry {
     size_t brick, cnt_off, cnt_bytes, mbar_off, total;
 };
 
-int centres_per_lane(const DenseConfig &c) { return c.path == 2 ? 2 : 1; }
+int centres_per_lane(const DenseConfig &c) { return c.path == 3 ? 4 : (c.path == 2 ? 2 : 1); }
 
 Geometry geometry(const DenseConfig &c, int B_, int r_max) {
     Geometry g{};
@@ -347,7 +460,7 @@ Geometry geometry(const DenseConfig &c, int B_, int r_max) {
     // counter columns + previous-scale counts per lane (layout of Words)
     const int cpl = centres_per_lane(c);
     const bool wide = is_wide(r_max);
-    const int words = (cpl == 2 && !wide ? 1 : cpl) * (B + 1) + cpl * (wide ? B + 1 : (B + 2) / 2);
+    const int words = (cpl >= 2 && !wide ? cpl / 2 : cpl) * (B + 1) + cpl * (wide ? B + 1 : (B + 2) / 2);
     g.padx = (r_max + 15) / 16 * 16;
     g.bx = (g.padx + 32 + r_max + 15) / 16 * 16;
     g.by = c.ty + 2 * r_max;
@@ -375,9 +488,22 @@ cudaError_t launch_t(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap 
 }
 
 template <int B>
+cudaError_t launch_adj4(const LaunchCtx &lc, const DenseArgs &a, const DenseConfig &cfg,
+                        size_t smem) {
+    auto kern = k_dense4<B>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.vol.nx + 127) / 128, (a.vol.ny + a.ty - 1) / a.ty, (a.z1 - a.z0 + a.tz - 1) / a.tz);
+    kern<<<grid, cfg.warps * 32, smem, lc.stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int B>
 cudaError_t launch_b(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap *tmap,
                      const DenseConfig &cfg, size_t smem) {
     const bool wide = is_wide(a.r_max);
+    if (cfg.path == 3) return wide ? cudaErrorInvalidValue : launch_adj4<B>(lc, a, cfg, smem);
     if (cfg.path == 0)
         return wide ? launch_t<B, true, 0, 1>(lc, a, tmap, cfg, smem)
                     : launch_t<B, false, 0, 1>(lc, a, tmap, cfg, smem);
@@ -438,8 +564,9 @@ size_t dense_smem_bytes(const DenseConfig &c, int B, int r_max) {
 }
 
 bool dense_config_fits(const DenseConfig &c, int B, int r_max) {
-    if (c.path < 0 || c.path > 2) return false;
-    if (c.warps < 1 || c.warps > (c.path == 2 ? 8 : 16) || c.ty * c.tz != c.warps) return false;
+    if (c.path < 0 || c.path > 3) return false;
+    if (c.path == 3 && is_wide(r_max)) return false;      // counts need 16-bit packing
+    if (c.warps < 1 || c.warps > (c.path >= 2 ? 8 : 16) || c.ty * c.tz != c.warps) return false;
     const Geometry g = geometry(c, B, r_max);
     if (c.path == 0 && (g.bx > 256 || g.by > 256 || g.bz > 256)) return false;
     return g.total + 1024 <= 227 * 1024;   // leave room for static shared memory

@@ -167,8 +167,9 @@ cudaError_t launch_bin_f32(const LaunchCtx &lc, const float *raw, int nx, int ny
 // ks_dense.cu
 struct DenseConfig {
     int path;      // 0 = TMA brick in shared memory, 1 = direct loads (L1/L2),
-                   // 2 = direct loads, two centres per lane
-    int warps;     // warps per block (each warp owns one row of 32 or 64 centres)
+                   // 2 = direct loads, two centres per lane (x, x + 32),
+                   // 3 = four adjacent centres per lane (r_max <= 25)
+    int warps;     // warps per block (each warp owns one row of 32, 64 or 128 centres)
     int ty, tz;    // tile rows in y and z (ty * tz = warps)
 };
 struct DenseOut {
