@@ -90,6 +90,46 @@ static void *scratch(Ctx *c, int slot, size_t bytes, cudaError_t *err) {
     return s.p;
 }
 
+// Volume allocations released through the API go to a small pool and are
+// reused by the next volume of exactly the same size created on the
+// context's stream, so a loop over same-sized volumes allocates (and frees,
+// which synchronises the device) only once.
+constexpr size_t kVolPoolMax = 4;
+constexpr size_t kVolPoolBytes = size_t(2) << 30;
+
+static void *vol_pool_take(Ctx *c, size_t bytes) {
+    std::lock_guard<std::mutex> g(c->mu);
+    for (size_t i = 0; i < c->vol_pool.size(); ++i)
+        if (c->vol_pool[i].first == bytes) {
+            void *p = c->vol_pool[i].second;
+            c->vol_pool.erase(c->vol_pool.begin() + i);
+            return p;
+        }
+    return nullptr;
+}
+
+static void vol_pool_put(Ctx *c, void *p, size_t bytes) {
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        size_t held = 0;
+        for (auto &e : c->vol_pool) held += e.first;
+        if (c->vol_pool.size() < kVolPoolMax && held + bytes <= kVolPoolBytes) {
+            c->vol_pool.emplace_back(bytes, p);
+            return;
+        }
+    }
+    dev_free(c, p, bytes);
+}
+
+static void vol_pool_flush(Ctx *c) {
+    std::vector<std::pair<size_t, void *>> all;
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        all.swap(c->vol_pool);
+    }
+    for (auto &e : all) dev_free(c, e.second, e.first);
+}
+
 static void scratch_release_all(Ctx *c) {
     std::lock_guard<std::mutex> g(g_scratch_mu);
     auto it = g_scratch.find(c);
@@ -290,8 +330,16 @@ int create_volume_on(Ctx *c, cudaStream_t s, const void *data, int is_device, in
     v->pitch = ((int64_t)nx + 2 * kHalo + 15) / 16 * 16;
     v->plane = v->pitch * (ny + 2 * kHalo);
     v->bytes = volume_bytes(nx, ny, nz);
-    void *p;
-    KS_TRY_CUDA(c, dev_alloc(c, &p, v->bytes));
+    const bool own = s == c->stream;       // API call on the context's stream
+    void *p = own ? vol_pool_take(c, v->bytes) : nullptr;
+    if (!p) {
+        cudaError_t ea = dev_alloc(c, &p, v->bytes);
+        if (ea == cudaErrorMemoryAllocation) {     // the pool may hold the room
+            vol_pool_flush(c);
+            ea = dev_alloc(c, &p, v->bytes);
+        }
+        KS_TRY_CUDA(c, ea);
+    }
     v->alloc = (uint8_t *)p;
     cudaError_t e = cudaMemsetAsync(v->alloc, 0, v->bytes, s);
     uint8_t *base = v->alloc + kHalo * v->plane + kHalo * v->pitch + kHalo;
@@ -299,9 +347,14 @@ int create_volume_on(Ctx *c, cudaStream_t s, const void *data, int is_device, in
     const size_t raw_bytes = (size_t)nx * ny * nz * dtype_size(dtype);
     void *staging = nullptr;
     if (e == cudaSuccess && !is_device) {
-        e = dev_alloc(c, &staging, raw_bytes);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(staging, data, raw_bytes, cudaMemcpyHostToDevice, s);
-        raw = staging;
+        // the context's stream keeps a staging buffer; other streams (the
+        // serving loop) take a fresh one
+        if (own)
+            raw = scratch(c, kScRaw, raw_bytes, &e);
+        else if ((e = dev_alloc(c, &staging, raw_bytes)) == cudaSuccess)
+            raw = staging;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(const_cast<void *>(raw), data, raw_bytes, cudaMemcpyHostToDevice, s);
     }
     if (e == cudaSuccess) {
         ProfRec rec;
@@ -692,6 +745,7 @@ int ks_destroy(ks_ctx *ctx) {
     for (auto &kv : c->vols) dev_free(c, kv.second->alloc, kv.second->bytes);
     c->vols.clear();
     scratch_release_all(c);
+    vol_pool_flush(c);
     for (auto &r : c->prof) {
         if (r.a) cudaEventDestroy(r.a);
         if (r.b) cudaEventDestroy(r.b);
@@ -746,7 +800,7 @@ int ks_release_volume(ks_ctx *ctx, ks_vol vol) {
         c->vols.erase(it);
     }
     cudaStreamSynchronize(c->stream);
-    dev_free(c, v->alloc, v->bytes);
+    vol_pool_put(c, v->alloc, v->bytes);
     return KS_OK;
 }
 

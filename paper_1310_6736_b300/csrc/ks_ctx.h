@@ -70,7 +70,9 @@ struct Ctx {
     float2 *d_minmax = nullptr;
     int minmax_blocks = 0;
     // volumes
-    std::mutex mu;                         // guards vols, next_vol, err, prof, tune
+    std::mutex mu;                         // guards vols, next_vol, err, prof, tune, vol_pool
+    // released volume allocations kept for reuse by calls on `stream`
+    std::vector<std::pair<size_t, void *>> vol_pool;
     std::map<int64_t, std::unique_ptr<Volume>> vols;
     int64_t next_vol = 1;
     std::string err;

@@ -240,9 +240,18 @@ class Context:
         s = np.ascontiguousarray(seeds, dtype=np.int32).reshape(-1, 3)
         return C.c_void_p(s.ctypes.data), s.shape[0], s
 
-    def seed_climb(self, v, params, seeds=None, want_traj=False):
+    def seed_climb(self, v, params, seeds=None, want_traj=False, out=None):
+        """Octant climb.  out=None: host SEED_RESULT array (and trajectories
+        when want_traj).  out=a CUDA tensor of at least n * 64 bytes: the
+        records stay on the device; returns their count n."""
         sp, ns, keep = self._seeds_arg(seeds)
         n = ns if seeds is not None else self.seed_count(v, params)
+        if out is not None:
+            if want_traj:
+                raise ValueError("trajectories are returned with host outputs only")
+            return self._seeds_to_device(lib().ks_seed_climb, "ks_seed_climb", v, params, sp, ns,
+                                         out, n * SEED_RESULT.itemsize, SEED_RESULT.itemsize,
+                                         extra=(None,))
         out = np.zeros(max(n, 1), SEED_RESULT)
         traj = np.zeros((max(n, 1), params.max_iter + 1, 3), np.int32) if want_traj else None
         got = C.c_int64()
@@ -253,16 +262,31 @@ class Context:
         out = out[:got.value]
         return (out, traj[:got.value]) if want_traj else out
 
-    def meanshift(self, v, params, seeds=None):
+    def meanshift(self, v, params, seeds=None, out=None):
+        """Mean shift for every (seed, r).  out=None: host MS_RESULT array.
+        out=a CUDA tensor of at least n * S * 48 bytes: the records stay on
+        the device; returns their count n * S."""
         sp, ns, keep = self._seeds_arg(seeds)
         n = ns if seeds is not None else self.seed_count(v, params)
         S = params.r_max - params.r_min + 1
+        if out is not None:
+            return self._seeds_to_device(lib().ks_meanshift, "ks_meanshift", v, params, sp, ns,
+                                         out, n * S * MS_RESULT.itemsize, MS_RESULT.itemsize)
         out = np.zeros(max(n * S, 1), MS_RESULT)
         got = C.c_int64()
         self._check(lib().ks_meanshift(self.h, int(v), C.byref(params), sp, ns,
                                        C.c_void_p(out.ctypes.data), out.shape[0], C.byref(got), 0),
                     "ks_meanshift")
         return out[:got.value]
+
+    def _seeds_to_device(self, fn, name, v, params, sp, ns, out, need, rec, extra=()):
+        if not out.is_cuda or out.numel() * out.element_size() < need:
+            raise ValueError(f"{name}: out must be a CUDA tensor of at least {need} bytes")
+        got = C.c_int64()
+        cap = out.numel() * out.element_size() // rec
+        self._check(fn(self.h, int(v), C.byref(params), sp, ns, C.c_void_p(out.data_ptr()), cap,
+                       C.byref(got), *extra, 1), name)
+        return got.value
 
     def batch_seeds(self, vols, params, kinds=3, use_graph=True):
         n = len(vols)
