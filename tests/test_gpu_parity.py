@@ -282,6 +282,59 @@ def test_seed_edge_cases(ctx, ko, ks_mod):
     _ms_vs_oracle(ctx, ko, ks, w3)
 
 
+def test_seed_device_outputs_equal_host_outputs(ctx, ks_mod):
+    """out= (device tensors) gives the same records as the host-output calls."""
+    import torch
+    ks = ks_mod
+    w = synth.workload("spheres48")
+    v = ctx.create_volume(w.volume, w.binning)
+    p = _params(ks, w)
+    o, m = ctx.seed_climb(v, p), ctx.meanshift(v, p)
+    od = torch.zeros(len(o) * ks.SEED_RESULT.itemsize, dtype=torch.uint8, device="cuda")
+    md = torch.zeros(len(m) * ks.MS_RESULT.itemsize + 48, dtype=torch.uint8, device="cuda")
+    assert ctx.seed_climb(v, p, out=od) == len(o)
+    assert ctx.meanshift(v, p, out=md) == len(m)
+    ctx.release_volume(v)
+    assert np.array_equal(od.cpu().numpy().view(ks.SEED_RESULT), o)
+    assert np.array_equal(md.cpu().numpy()[:len(m) * ks.MS_RESULT.itemsize].view(ks.MS_RESULT), m)
+    with pytest.raises(ValueError):
+        ctx.meanshift(ctx.create_volume(w.volume, w.binning), p, out=od[:16])
+
+
+def test_released_volume_memory_is_reused_cleanly(ks_mod, ko):
+    """A released volume's allocation is reused by the next volume of the same
+    size: its halo must still read as not counted, and volumes of other sizes
+    (and a tight budget) must still work."""
+    ks = ks_mod
+    a = synth.workload("spheres48")
+    rng = np.random.default_rng(2)
+    other = rng.integers(0, 256, size=a.volume.shape).astype(np.uint8)   # every bin occupied
+    pa = _params(ks, a)
+    budget = 3 * (56 + 64) ** 2 * (48 + 64) + (64 << 20)    # tables + a few volumes
+    c = ks.Context(hbm_budget_bytes=budget)
+    try:
+        first = None
+        for vol in (other, a.volume, other, a.volume):
+            v = c.create_volume(vol, a.binning)
+            Y, s = c.dense_saliency(v, pa, vol.shape)
+            c.release_volume(v)
+            if vol is a.volume:
+                if first is None:
+                    first = (Y, s)
+                else:
+                    assert np.array_equal(s, first[1]) and np.array_equal(Y, first[0])
+        Yo, so = ko.dense(ko.bin_volume(a.volume, a.binning), a.binning["bins"], a.r_min, a.r_max)
+        assert np.array_equal(first[1], so)
+        close(first[0], Yo)
+        # a different size after the pool holds the first one
+        small = a.volume[:20, :30, :40].copy()
+        v = c.create_volume(small, a.binning)
+        assert np.array_equal(c.volume_bins(v, small.shape), ko.bin_volume(small, a.binning))
+        c.release_volume(v)
+    finally:
+        c.close()
+
+
 # ---------------------------------------------------- batched and serving
 def test_batch_equals_plain_calls(ctx, ks_mod):
     ks = ks_mod
