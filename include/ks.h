@@ -111,6 +111,15 @@ typedef struct ks_ms_result {
     double rho, H;
 } ks_ms_result;
 
+/* A candidate salient region: centre, scale r (0 = none), the index of the
+ * seed or item it came from, and the window's entropy H and inter-scale pdf
+ * change W at that centre and scale.  40 bytes. */
+typedef struct ks_candidate {
+    int32_t x, y, z, r;
+    int32_t source, reserved;
+    double H, W;
+} ks_candidate;
+
 /* ---------------------------------------------------------------- context */
 
 /* Create a context on CUDA device `device` using stream `cuda_stream`
@@ -191,6 +200,36 @@ int ks_meanshift(ks_ctx *ctx, ks_vol vol, const ks_params *params,
                  const int32_t *seeds_xyz, int64_t n_seeds,
                  ks_ms_result *out, int64_t capacity, int64_t *n_out,
                  int out_on_device);
+
+/* Kadir-Brady at listed centres: the dense sweep's quantities at n centres
+ * given as int32 xyz triples (0 <= x < nx etc.): Y_best, s_best and, when
+ * H / W are not NULL, H(r) and W(r) for every scale (n x S, centre-major;
+ * W(r_min) = 0).  `on_device` applies to xyz and to every output.  Results
+ * equal the dense sweep's at the same voxels.  Errors: KS_EINVAL (a centre
+ * outside the volume, bad params, NULL buffers), KS_ENOTFOUND. */
+int ks_dense_points(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_t *xyz,
+                    int64_t n, double *Y_best, uint8_t *s_best, double *H, double *W,
+                    int on_device);
+
+/* Candidates from the seed searches.  Octant: one per seed result, at its
+ * final centre with r = s_best, H_best and W_best (r = 0 when no entropy
+ * peak was found).  Mean shift: one per item, at its final centre and its
+ * radius r, with H(r) and W(r) evaluated there by ks_dense_points.
+ * `on_device` applies to the results and to `out` (n entries). */
+int ks_octant_candidates(ks_ctx *ctx, const ks_seed_result *res, int64_t n, ks_candidate *out,
+                         int on_device);
+int ks_meanshift_candidates(ks_ctx *ctx, ks_vol vol, const ks_params *params,
+                            const ks_ms_result *res, int64_t n, ks_candidate *out,
+                            int on_device);
+
+/* Selection of salient regions (Sec. 2.3, end; Sec. 3.1): keep candidates
+ * with r > 0 and H > h_min; merge candidates with the same (x, y, z, r) into
+ * the one with the smallest source; order by W descending, then H
+ * descending, then z, y, x, r ascending; write the first min(top_k, #kept)
+ * to `out` and their number to *n_out.  1 <= top_k <= 256 (the paper keeps
+ * 20).  `on_device` applies to `in` and `out`.  Errors: KS_EINVAL. */
+int ks_select_salient(ks_ctx *ctx, const ks_candidate *in, int64_t n, double h_min, int top_k,
+                      ks_candidate *out, int64_t *n_out, int on_device);
 
 /* ---------------------------------------------------------- batched form */
 

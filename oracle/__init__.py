@@ -260,3 +260,49 @@ def ms_window(bins, B, p, r):
 
 def max_threads():
     return lib().ko_max_threads()
+
+
+# ----------------------------------------------------------------- selection
+# Selection of salient regions among converged seeds (Sec. 2.3, end: maxima
+# whose entropy is above a threshold are kept and ranked by the change of
+# the pdf at their scale; Sec. 3.1: the 20 with the highest pdf difference).
+# Candidates are records with fields x, y, z, r, source, H, W (r = 0: no
+# scale).  Readings: "above" is strict (H > h_min); candidates with the same
+# (x, y, z, r) are one region, represented by the smallest source; the order
+# is W descending, then H descending, then z, y, x, r ascending.
+
+def octant_candidates(res):
+    """One candidate per octant seed result: the final centre with r = s,
+    H and W of the Kadir-Brady evaluation there (`res` as octant_climb
+    returns it); source = the seed's index."""
+    xyz = np.asarray(res["xyz"])
+    n = len(xyz)
+    return [dict(x=int(xyz[i, 0]), y=int(xyz[i, 1]), z=int(xyz[i, 2]), r=int(res["s"][i]),
+                 source=i, H=float(res["H"][i]), W=float(res["W"][i])) for i in range(n)]
+
+
+def meanshift_candidates(bins, B, r_min, r_max, res, radii, w_norm=0):
+    """One candidate per mean-shift item: its final centre and radius, with
+    H(r) and W(r) of the dense definition evaluated there (`res` as
+    meanshift returns it, `radii` the item radii); source = the item index."""
+    xyz = np.asarray(res["xyz"], np.int32).reshape(-1, 3)
+    _, _, H, W = dense(bins, B, r_min, r_max, w_norm=w_norm, centres=xyz, want_hw=True)
+    out = []
+    for i in range(len(xyz)):
+        si = int(radii[i]) - r_min
+        out.append(dict(x=int(xyz[i, 0]), y=int(xyz[i, 1]), z=int(xyz[i, 2]), r=int(radii[i]),
+                        source=i, H=float(H[i, si]), W=float(W[i, si])))
+    return out
+
+
+def select_salient(cands, h_min=0.0, top_k=20):
+    """The selection, step by step: threshold, merge, order, take top_k."""
+    kept = [c for c in cands if c["r"] > 0 and c["H"] > h_min]
+    regions = {}
+    for c in kept:
+        key = (c["x"], c["y"], c["z"], c["r"])
+        if key not in regions or c["source"] < regions[key]["source"]:
+            regions[key] = c
+    ordered = sorted(regions.values(),
+                     key=lambda c: (-c["W"], -c["H"], c["z"], c["y"], c["x"], c["r"]))
+    return ordered[:top_k]

@@ -65,7 +65,8 @@ struct Scratch {
     size_t bytes = 0;
 };
 enum ScratchSlot {
-    kScRaw, kScSeeds, kScOct, kScMs, kScTraj, kScY, kScS, kScH, kScW, kScTune, kScCount
+    kScRaw, kScSeeds, kScOct, kScMs, kScTraj, kScY, kScS, kScH, kScW, kScTune, kScPts,
+    kScSelIn, kScSelOut, kScCount
 };
 static std::mutex g_scratch_mu;
 static std::unordered_map<Ctx *, std::vector<Scratch>> g_scratch;
@@ -528,6 +529,10 @@ static int check_status(Ctx *c) {
     if (h) {
         cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
         cudaStreamSynchronize(c->stream);
+        if (h & kStatusBadInput)
+            return set_err(c, KS_EINVAL, "a listed centre lies outside the volume");
+        if (h & kStatusMisaligned)
+            return set_err(c, KS_ECUDA, "dense brick: misaligned shared-memory layout (no copy issued)");
         return set_err(c, KS_ETIMEDOUT, "a bounded device wait gave up (status " +
                                             std::to_string(h) + ")");
     }
@@ -856,6 +861,159 @@ int ks_dense_saliency_ex(ks_ctx *ctx, ks_vol vol, const ks_params *params, doubl
 int ks_dense_saliency(ks_ctx *ctx, ks_vol vol, const ks_params *params, double *Y,
                       uint8_t *s_best, int out_on_device) {
     return ks_dense_saliency_ex(ctx, vol, params, Y, s_best, nullptr, nullptr, out_on_device);
+}
+
+int ks_dense_points(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_t *xyz,
+                    int64_t n, double *Y, uint8_t *s_best, double *H, double *W, int on_device) {
+    if (!ctx) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    std::string why;
+    int st = validate_params(params, &why);
+    if (st) return set_err(c, st, why);
+    if (n < 0) return set_err(c, KS_EINVAL, "n < 0");
+    if (n > 0 && (!xyz || !Y || !s_best)) return set_err(c, KS_EINVAL, "xyz / Y_best / s_best is NULL");
+    Volume *v = find_volume(c, vol);
+    if (!v) return set_err(c, KS_ENOTFOUND, "unknown volume");
+    if (n == 0) return KS_OK;
+    const int S = params->r_max - params->r_min + 1;
+    DenseOut o{Y, s_best, H, W};
+    const int32_t *dxyz = xyz;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+        int32_t *p = (int32_t *)scratch(c, kScPts, (size_t)n * 12, &e);
+        if (p) e = cudaMemcpyAsync(p, xyz, (size_t)n * 12, cudaMemcpyHostToDevice, c->stream);
+        dxyz = p;
+        if (e == cudaSuccess) o.Y = (double *)scratch(c, kScY, (size_t)n * 8, &e);
+        if (o.Y) o.s = (uint8_t *)scratch(c, kScS, (size_t)n, &e);
+        if (o.s && H) o.H = (double *)scratch(c, kScH, (size_t)n * S * 8, &e);
+        if (e == cudaSuccess && W) o.W = (double *)scratch(c, kScW, (size_t)n * S * 8, &e);
+        if (e != cudaSuccess) return cuda_err(c, e, "point inputs / outputs");
+    }
+    ProfRec rec;
+    prof_begin(c, "ks_dense_points", c->stream, &rec);
+    e = launch_dense_points(c->lc(), v->desc, c->ot, c->T, c->L, params->r_min, params->r_max,
+                            params->w_norm, dxyz, n, o);
+    prof_end(c, &rec, c->stream);
+    KS_TRY_CUDA(c, e);
+    if (!on_device) {
+        KS_TRY_CUDA(c, cudaMemcpyAsync(Y, o.Y, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
+        KS_TRY_CUDA(c, cudaMemcpyAsync(s_best, o.s, (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+        if (H) KS_TRY_CUDA(c, cudaMemcpyAsync(H, o.H, (size_t)n * S * 8, cudaMemcpyDeviceToHost, c->stream));
+        if (W) KS_TRY_CUDA(c, cudaMemcpyAsync(W, o.W, (size_t)n * S * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    return check_status(c);
+}
+
+int ks_octant_candidates(ks_ctx *ctx, const ks_seed_result *res, int64_t n, ks_candidate *out,
+                         int on_device) {
+    if (!ctx) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    if (n < 0 || (n > 0 && (!res || !out))) return set_err(c, KS_EINVAL, "bad candidate buffers");
+    if (n == 0) return KS_OK;
+    const ks_seed_result *dres = res;
+    ks_candidate *dout = out;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+        void *pin = scratch(c, kScOct, (size_t)n * sizeof(ks_seed_result), &e);
+        if (pin) e = cudaMemcpyAsync(pin, res, (size_t)n * sizeof(ks_seed_result),
+                                     cudaMemcpyHostToDevice, c->stream);
+        dres = (const ks_seed_result *)pin;
+        if (e == cudaSuccess) dout = (ks_candidate *)scratch(c, kScSelOut, (size_t)n * sizeof(ks_candidate), &e);
+        if (e != cudaSuccess) return cuda_err(c, e, "candidate buffers");
+    }
+    ProfRec rec;
+    prof_begin(c, "ks_select", c->stream, &rec);
+    e = launch_oct_candidates(c->lc(), dres, n, dout);
+    prof_end(c, &rec, c->stream);
+    KS_TRY_CUDA(c, e);
+    if (!on_device)
+        KS_TRY_CUDA(c, cudaMemcpyAsync(out, dout, (size_t)n * sizeof(ks_candidate),
+                                       cudaMemcpyDeviceToHost, c->stream));
+    return check_status(c);
+}
+
+int ks_meanshift_candidates(ks_ctx *ctx, ks_vol vol, const ks_params *params,
+                            const ks_ms_result *res, int64_t n, ks_candidate *out, int on_device) {
+    if (!ctx) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    std::string why;
+    int st = validate_params(params, &why);
+    if (st) return set_err(c, st, why);
+    if (n < 0 || (n > 0 && (!res || !out))) return set_err(c, KS_EINVAL, "bad candidate buffers");
+    Volume *v = find_volume(c, vol);
+    if (!v) return set_err(c, KS_ENOTFOUND, "unknown volume");
+    if (n == 0) return KS_OK;
+    const int S = params->r_max - params->r_min + 1;
+    cudaError_t e = cudaSuccess;
+    const ks_ms_result *dres = res;
+    ks_candidate *dout = out;
+    if (!on_device) {
+        void *pin = scratch(c, kScMs, (size_t)n * sizeof(ks_ms_result), &e);
+        if (pin) e = cudaMemcpyAsync(pin, res, (size_t)n * sizeof(ks_ms_result),
+                                     cudaMemcpyHostToDevice, c->stream);
+        dres = (const ks_ms_result *)pin;
+        if (e == cudaSuccess) dout = (ks_candidate *)scratch(c, kScSelOut, (size_t)n * sizeof(ks_candidate), &e);
+        if (e != cudaSuccess) return cuda_err(c, e, "candidate buffers");
+    }
+    // final centres -> H and W of every scale there -> the item's own scale
+    int32_t *xyz = (int32_t *)scratch(c, kScPts, (size_t)n * 12, &e);
+    double *Y = e == cudaSuccess ? (double *)scratch(c, kScY, (size_t)n * 8, &e) : nullptr;
+    uint8_t *sb = e == cudaSuccess ? (uint8_t *)scratch(c, kScS, (size_t)n, &e) : nullptr;
+    double *H = e == cudaSuccess ? (double *)scratch(c, kScH, (size_t)n * S * 8, &e) : nullptr;
+    double *W = e == cudaSuccess ? (double *)scratch(c, kScW, (size_t)n * S * 8, &e) : nullptr;
+    if (e != cudaSuccess) return cuda_err(c, e, "candidate scratch");
+    ProfRec rec;
+    prof_begin(c, "ks_select", c->stream, &rec);
+    e = launch_ms_xyz(c->lc(), dres, n, xyz);
+    if (e == cudaSuccess)
+        e = launch_dense_points(c->lc(), v->desc, c->ot, c->T, c->L, params->r_min, params->r_max,
+                                params->w_norm, xyz, n, DenseOut{Y, sb, H, W});
+    if (e == cudaSuccess)
+        e = launch_ms_candidates(c->lc(), dres, n, H, W, params->r_min, S, dout);
+    prof_end(c, &rec, c->stream);
+    KS_TRY_CUDA(c, e);
+    if (!on_device)
+        KS_TRY_CUDA(c, cudaMemcpyAsync(out, dout, (size_t)n * sizeof(ks_candidate),
+                                       cudaMemcpyDeviceToHost, c->stream));
+    return check_status(c);
+}
+
+int ks_select_salient(ks_ctx *ctx, const ks_candidate *in, int64_t n, double h_min, int top_k,
+                      ks_candidate *out, int64_t *n_out, int on_device) {
+    if (!ctx) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    if (!n_out || n < 0 || (n > 0 && (!in || !out)))
+        return set_err(c, KS_EINVAL, "bad selection buffers");
+    if (top_k < 1 || top_k > 256) return set_err(c, KS_EINVAL, "top_k must be in [1, 256]");
+    if (n > (int64_t)1 << 30) return set_err(c, KS_EINVAL, "more than 2^30 candidates");
+    *n_out = 0;
+    if (n == 0) return KS_OK;
+    cudaError_t e = cudaSuccess;
+    const ks_candidate *din = in;
+    if (!on_device) {
+        void *p = scratch(c, kScSelIn, (size_t)n * sizeof(ks_candidate), &e);
+        if (p) e = cudaMemcpyAsync(p, in, (size_t)n * sizeof(ks_candidate), cudaMemcpyHostToDevice,
+                                   c->stream);
+        din = (const ks_candidate *)p;
+        if (e != cudaSuccess) return cuda_err(c, e, "selection input");
+    }
+    // scratch: hash table + two candidate lists, then top_k results and a counter
+    const size_t sb = select_scratch_bytes(n);
+    uint8_t *work = (uint8_t *)scratch(c, kScTune, sb + 256 * sizeof(ks_candidate) + 512, &e);
+    if (e != cudaSuccess) return cuda_err(c, e, "selection scratch");
+    ks_candidate *res = (ks_candidate *)(work + (sb + 255) / 256 * 256);
+    unsigned long long *cnt = (unsigned long long *)(res + 256);
+    int64_t k = 0;
+    ProfRec rec;
+    prof_begin(c, "ks_select", c->stream, &rec);
+    e = launch_select(c->lc(), din, n, h_min, top_k, work, on_device ? out : res, cnt, &k);
+    prof_end(c, &rec, c->stream);
+    KS_TRY_CUDA(c, e);
+    if (!on_device && k)
+        KS_TRY_CUDA(c, cudaMemcpyAsync(out, res, (size_t)k * sizeof(ks_candidate),
+                                       cudaMemcpyDeviceToHost, c->stream));
+    *n_out = k;
+    return check_status(c);
 }
 
 int ks_seed_count(ks_ctx *ctx, ks_vol vol, const ks_params *params, int64_t *n) {

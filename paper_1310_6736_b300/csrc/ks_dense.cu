@@ -72,6 +72,8 @@ struct DenseArgs {
     uint32_t cnt_off, mbar_off;
     DenseOut out;
     int *status;
+    const int32_t *pts;          // listed centres (k_points)
+    int64_t npts;
 };
 
 template <bool CTAB>
@@ -226,6 +228,14 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
     int pz, py;
     if constexpr (PATH == 0) {
         const uint32_t mbar = smem_u32(smem + a.mbar_off);
+        // the TMA destination must be 128-byte aligned, the mbarrier 8-byte
+        // aligned and the tensor map 64-byte aligned: checked once per block,
+        // reported instead of issuing a copy that would fault
+        if (((smem_u32(smem) & 127u) | (mbar & 7u) |
+             ((uint32_t)reinterpret_cast<uintptr_t>(&tmap) & 63u)) != 0u) {
+            if (threadIdx.x == 0) atomicOr(a.status, kStatusMisaligned);
+            return;
+        }
         if (threadIdx.x == 0) {
             mbar_init(mbar, 1);
             fence_mbar_init();
@@ -441,6 +451,73 @@ __global__ void __launch_bounds__(256) k_dense4(const DenseArgs a) {
     }
 }
 
+// Kadir-Brady at listed centres: lane = one centre taken from the list,
+// with the dense kernels' shell-incremental counting and scale steps.  The
+// centres are scattered, so every load is the lane's own.  A centre outside
+// the volume flags kStatusBadInput; its lane then walks voxel (0,0,0), so
+// that every read stays inside the halo, and writes nothing.
+template <int B, bool WIDE>
+__global__ void __launch_bounds__(128) k_points(const DenseArgs a) {
+    // (every kernel of this file declares the dynamic buffer with the same
+    // 1024-byte alignment: the declarations share one symbol, and the TMA
+    // brick of k_dense needs a 128-byte aligned base)
+    extern __shared__ __align__(1024) uint8_t smem[];
+    using Wd = Words<B, WIDE, 1>;
+    constexpr bool CTAB = !WIDE;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t pt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool have = pt < a.npts;
+    int x = 0, y = 0, z = 0;
+    if (have) {
+        x = a.pts[3 * pt];
+        y = a.pts[3 * pt + 1];
+        z = a.pts[3 * pt + 2];
+    }
+    const bool ok = have && x >= 0 && x < a.vol.nx && y >= 0 && y < a.vol.ny && z >= 0 &&
+                    z < a.vol.nz;
+    if (have && !ok) atomicOr(a.status, kStatusBadInput);
+    if (!ok) x = y = z = 0;
+    const int pz = (int)a.vol.plane, py = (int)a.vol.pitch;
+    const uint8_t *c0 = a.vol.base + (int64_t)z * a.vol.plane + (int64_t)y * a.vol.pitch + x;
+    const Tab<CTAB> tab{a.ot};
+    const uint32_t cnt_lane = smem_u32(smem) + (warp * Wd::kPerLane * 32 + lane) * 4;
+    auto word = [&](int w) { return cnt_lane + ((uint32_t)w << 7); };
+#pragma unroll 4
+    for (int w = 0; w < Wd::kPerLane; ++w) st_shared_u32(word(w), 0u);
+    ScaleState st{0.0, 0.0, 0.0, 0u, 0u, 0ull, 0};
+    for (int i = 0; i < a.S; ++i) {
+        const int r = a.r_min + i;
+        for (int rho = (i == 0 ? 0 : r); rho <= r; ++rho) {
+            const int k0 = tab.c8_start(rho), k1 = tab.c8_start(rho + 1);
+            const int k2 = tab.rest_start(rho), k3 = tab.rest_start(rho + 1);
+            for (int k = k0; k < k1; ++k) {
+                const uint32_t e = tab.c8(k);
+                const int X = (int)(e & 0xffu);
+                const int Y = (int)((e >> 8) & 0xffu) * py;
+                const int Z = (int)((e >> 16) & 0xffu) * pz;
+                const int o[8] = {Z + Y + X, Z + Y - X, Z - Y + X, Z - Y - X,
+                                  Y - Z + X, Y - Z - X, -Z - Y + X, -Z - Y - X};
+                uint32_t v[8];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) v[m] = __ldg(c0 + o[m]);
+#pragma unroll
+                for (int m = 0; m < 8; ++m) red_add_shared(word(Wd::cnt(0, v[m])), 1u);
+            }
+            for (int k = k2; k < k3; ++k) {
+                const uint32_t f = tab.rest(k);
+                const int off = ((int)((f >> 16) & 0xffu) - 64) * pz +
+                                ((int)((f >> 8) & 0xffu) - 64) * py + ((int)(f & 0xffu) - 64);
+                red_add_shared(word(Wd::cnt(0, __ldg(c0 + off))), 1u);
+            }
+        }
+        scale_step<B, WIDE, 1>(a, cnt_lane, 0, i, r, st, pt, ok);
+    }
+    if (ok) {
+        a.out.Y[pt] = st.yb;
+        a.out.s[pt] = (uint8_t)st.sb;
+    }
+}
+
 int template_bins(int B) {
     return B <= 2 ? 2 : B <= 4 ? 4 : B <= 8 ? 8 : B <= 16 ? 16 : B <= 32 ? 32 : 64;
 }
@@ -558,6 +635,51 @@ cudaError_t dense_upload_constant_table(const uint32_t *c8, const int *c8_start,
 }
 
 int dense_const_rmax() { return kConstRmax; }
+
+namespace {
+template <int B>
+cudaError_t launch_points_b(const LaunchCtx &lc, const DenseArgs &a) {
+    constexpr int kWarps = 4;
+    const bool wide = is_wide(a.r_max);
+    const size_t smem = (size_t)kWarps * 32 * 4 *
+                        (wide ? Words<B, true, 1>::kPerLane : Words<B, false, 1>::kPerLane);
+    auto kern = wide ? k_points<B, true> : k_points<B, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (a.npts + kWarps * 32 - 1) / (kWarps * 32);
+    kern<<<(unsigned)blocks, kWarps * 32, smem, lc.stream>>>(a);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_dense_points(const LaunchCtx &lc, const VolDesc &v, const OffsetTables &ot,
+                                const double *T, const double *L, int r_min, int r_max,
+                                int w_norm, const int32_t *xyz, int64_t n, const DenseOut &out) {
+    if (n <= 0) return cudaSuccess;
+    DenseArgs a{};
+    a.vol = v;
+    a.ot = ot;
+    a.T = T;
+    a.L = L;
+    a.r_min = r_min;
+    a.r_max = r_max;
+    a.S = r_max - r_min + 1;
+    a.w_norm = w_norm;
+    a.out = out;
+    a.status = lc.d_status;
+    a.pts = xyz;
+    a.npts = n;
+    switch (template_bins(v.B)) {
+        case 2: return launch_points_b<2>(lc, a);
+        case 4: return launch_points_b<4>(lc, a);
+        case 8: return launch_points_b<8>(lc, a);
+        case 16: return launch_points_b<16>(lc, a);
+        case 32: return launch_points_b<32>(lc, a);
+        case 64: return launch_points_b<64>(lc, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 size_t dense_smem_bytes(const DenseConfig &c, int B, int r_max) {
     return geometry(c, B, r_max).total;

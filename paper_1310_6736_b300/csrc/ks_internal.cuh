@@ -25,6 +25,8 @@ constexpr int kOctThreads = 256;     // block size of the octant-only seed kerne
 // Device status word bits (ctx->d_status); read back by ks_sync.
 constexpr int kStatusTmaTimeout = 1;
 constexpr int kStatusQueueTimeout = 2;
+constexpr int kStatusBadInput = 4;     // a listed centre lies outside its volume
+constexpr int kStatusMisaligned = 8;   // a TMA brick's shared-memory layout was misaligned
 
 // A resident bin volume as the kernels see it.  base points at voxel
 // (0,0,0); voxel (x,y,z) is base[z*plane + y*pitch + x] for
@@ -187,6 +189,11 @@ cudaError_t dense_upload_constant_table(const uint32_t *c8, const int *c8_start,
 int dense_const_rmax();
 bool dense_config_fits(const DenseConfig &c, int B, int r_max);
 size_t dense_smem_bytes(const DenseConfig &c, int B, int r_max);
+// Kadir-Brady at n listed centres (xyz int32 triples on the device); a
+// centre outside the volume is skipped and sets kStatusBadInput.
+cudaError_t launch_dense_points(const LaunchCtx &lc, const VolDesc &v, const OffsetTables &ot,
+                                const double *T, const double *L, int r_min, int r_max,
+                                int w_norm, const int32_t *xyz, int64_t n, const DenseOut &out);
 cudaError_t launch_dense(const LaunchCtx &lc, const VolDesc &v, const CUtensorMap *tmap,
                          const OffsetTables &ot, const double *T, const double *L, int r_min,
                          int r_max, int w_norm, const DenseConfig &cfg, const DenseOut &out,
@@ -229,6 +236,20 @@ cudaError_t launch_seeds(const LaunchCtx &lc, const SeedQueue &q, const OffsetTa
                          const double *T, const double *L, int max_B, int max_S, int kinds,
                          bool persistent, int grid);
 int seed_blocks_per_sm(int max_B, int max_S, int kinds);
+
+// ks_select.cu: candidates and the device selection (ks_select_salient).
+cudaError_t launch_oct_candidates(const LaunchCtx &lc, const ks_seed_result *in, int64_t n,
+                                  ks_candidate *out);
+cudaError_t launch_ms_xyz(const LaunchCtx &lc, const ks_ms_result *in, int64_t n, int32_t *xyz);
+cudaError_t launch_ms_candidates(const LaunchCtx &lc, const ks_ms_result *in, int64_t n,
+                                 const double *H, const double *W, int r_min, int S,
+                                 ks_candidate *out);
+size_t select_scratch_bytes(int64_t n);
+// Writes the first min(top_k, #survivors) candidates to `out` (device) and
+// their count to *n_out; synchronises the stream once.
+cudaError_t launch_select(const LaunchCtx &lc, const ks_candidate *in, int64_t n, double h_min,
+                          int top_k, void *scratch, ks_candidate *out,
+                          unsigned long long *d_count, int64_t *n_out);
 
 // Micro-kernel: shared-memory increment rate (see ks_measure_smem_peak).
 cudaError_t launch_smem_peak(const LaunchCtx &lc, uint32_t *sink, int blocks, int iters);

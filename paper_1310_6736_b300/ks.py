@@ -60,7 +60,9 @@ SEED_RESULT = np.dtype([("x", "<i4"), ("y", "<i4"), ("z", "<i4"), ("seed_x", "<i
 MS_RESULT = np.dtype([("x", "<i4"), ("y", "<i4"), ("z", "<i4"), ("r", "<i4"), ("seed", "<i4"),
                       ("iters", "<i4"), ("converged", "<i4"), ("reserved", "<i4"),
                       ("rho", "<f8"), ("H", "<f8")])
-assert SEED_RESULT.itemsize == 64 and MS_RESULT.itemsize == 48
+CANDIDATE = np.dtype([("x", "<i4"), ("y", "<i4"), ("z", "<i4"), ("r", "<i4"),
+                      ("source", "<i4"), ("reserved", "<i4"), ("H", "<f8"), ("W", "<f8")])
+assert SEED_RESULT.itemsize == 64 and MS_RESULT.itemsize == 48 and CANDIDATE.itemsize == 40
 
 # Every symbol include/ks.h declares, with (restype, argtypes).
 _P, _I, _I64, _D, _SZ = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_size_t
@@ -82,6 +84,10 @@ SIGNATURES = {
                            C.POINTER(C.c_int64), _P, _I]),
     "ks_meanshift": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _I64,
                           C.POINTER(C.c_int64), _I]),
+    "ks_dense_points": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _P, _P, _P, _I]),
+    "ks_octant_candidates": (_I, [_P, _P, _I64, _P, _I]),
+    "ks_meanshift_candidates": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _I]),
+    "ks_select_salient": (_I, [_P, _P, _I64, _D, _I, _P, C.POINTER(C.c_int64), _I]),
     "ks_batch_seeds": (_I, [_P, _P, _P, _I, _I, _P, _P, _I]),
     "ks_submit": (_I, [_P, C.POINTER(ks_request), C.POINTER(C.c_int64)]),
     "ks_poll": (_I, [_P, _I64, _I64, C.POINTER(ks_result)]),
@@ -287,6 +293,48 @@ class Context:
         self._check(fn(self.h, int(v), C.byref(params), sp, ns, C.c_void_p(out.data_ptr()), cap,
                        C.byref(got), *extra, 1), name)
         return got.value
+
+    def dense_points(self, v, params, xyz, want_hw=False):
+        """Kadir-Brady at listed centres ((n, 3) int xyz): (Y_best, s_best[, H, W])."""
+        xyz = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+        n = xyz.shape[0]
+        S = params.r_max - params.r_min + 1
+        Y = np.zeros(n, np.float64)
+        s = np.zeros(n, np.uint8)
+        H = np.zeros((n, S), np.float64) if want_hw else None
+        W = np.zeros((n, S), np.float64) if want_hw else None
+        self._check(lib().ks_dense_points(
+            self.h, int(v), C.byref(params), C.c_void_p(xyz.ctypes.data), n,
+            C.c_void_p(Y.ctypes.data), C.c_void_p(s.ctypes.data),
+            C.c_void_p(H.ctypes.data) if want_hw else None,
+            C.c_void_p(W.ctypes.data) if want_hw else None, 0), "ks_dense_points")
+        return (Y, s, H, W) if want_hw else (Y, s)
+
+    def octant_candidates(self, res):
+        res = np.ascontiguousarray(res, dtype=SEED_RESULT)
+        out = np.zeros(max(len(res), 1), CANDIDATE)
+        self._check(lib().ks_octant_candidates(self.h, C.c_void_p(res.ctypes.data), len(res),
+                                               C.c_void_p(out.ctypes.data), 0),
+                    "ks_octant_candidates")
+        return out[:len(res)]
+
+    def meanshift_candidates(self, v, params, res):
+        res = np.ascontiguousarray(res, dtype=MS_RESULT)
+        out = np.zeros(max(len(res), 1), CANDIDATE)
+        self._check(lib().ks_meanshift_candidates(self.h, int(v), C.byref(params),
+                                                  C.c_void_p(res.ctypes.data), len(res),
+                                                  C.c_void_p(out.ctypes.data), 0),
+                    "ks_meanshift_candidates")
+        return out[:len(res)]
+
+    def select_salient(self, cands, h_min=0.0, top_k=20):
+        cands = np.ascontiguousarray(cands, dtype=CANDIDATE)
+        out = np.zeros(top_k, CANDIDATE)
+        got = C.c_int64()
+        self._check(lib().ks_select_salient(self.h, C.c_void_p(cands.ctypes.data), len(cands),
+                                            float(h_min), int(top_k), C.c_void_p(out.ctypes.data),
+                                            C.byref(got), 0), "ks_select_salient")
+        return out[:got.value]
 
     def batch_seeds(self, vols, params, kinds=3, use_graph=True):
         n = len(vols)

@@ -401,3 +401,92 @@ def test_errors_are_reported_not_raised_across_abi(ctx, ks_mod):
         small.create_volume(big, w.binning)
     assert e.value.status == ks.KS_ENOMEM
     small.close()
+
+
+# ------------------------------------------------ points and selection
+def test_dense_points_equal_oracle_centres(ctx, ko, ks_mod):
+    ks = ks_mod
+    for name, n in (("pet128", 700), ("mr256", 120), ("spheres48", 300)):
+        w = synth.workload(name)
+        v = ctx.create_volume(w.volume, w.binning)
+        p = _params(ks, w)
+        rng = np.random.default_rng(len(name))
+        nx, ny, nz = w.dims
+        cen = np.stack([rng.integers(0, nx, n), rng.integers(0, ny, n), rng.integers(0, nz, n)],
+                       1).astype(np.int32)
+        cen[:4] = [[0, 0, 0], [nx - 1, ny - 1, nz - 1], [0, ny - 1, nz // 2], [nx - 1, 0, 0]]
+        Y, s, H, W = ctx.dense_points(v, p, cen, want_hw=True)
+        b = ko.bin_volume(w.volume, w.binning)
+        Yo, so, Ho, Wo = ko.dense(b, w.binning["bins"], w.r_min, w.r_max, centres=cen, want_hw=True)
+        assert np.array_equal(s, so)
+        close(Y, Yo)
+        close(H, Ho)
+        close(W, Wo)
+        with pytest.raises(ks.KsError):
+            ctx.dense_points(v, p, np.array([[nx, 0, 0]], np.int32))
+        ctx.dense_points(v, p, cen[:3])            # the context is usable afterwards
+        ctx.release_volume(v)
+
+
+def _cand_list(arr):
+    return [dict(x=int(c["x"]), y=int(c["y"]), z=int(c["z"]), r=int(c["r"]),
+                 source=int(c["source"]), H=float(c["H"]), W=float(c["W"])) for c in arr]
+
+
+def _same_cands(got, ref):
+    got = _cand_list(got)
+    assert [(c["x"], c["y"], c["z"], c["r"], c["source"]) for c in got] == \
+        [(c["x"], c["y"], c["z"], c["r"], c["source"]) for c in ref]
+    close([c["H"] for c in got], [c["H"] for c in ref])
+    close([c["W"] for c in got], [c["W"] for c in ref])
+
+
+def test_candidates_and_selection_equal_oracle(ctx, ko, ks_mod):
+    ks = ks_mod
+    w = synth.workload("pet128")
+    v = ctx.create_volume(w.volume, w.binning)
+    p = _params(ks, w)
+    b = ko.bin_volume(w.volume, w.binning)
+    B = w.binning["bins"]
+    sd = ko.seed_grid(w.dims, w.stride)
+    # octant: candidates from the GPU results equal the oracle's
+    o = ctx.seed_climb(v, p)
+    oref = ko.octant_climb(b, B, w.r_min, w.r_max, sd, w.max_iter)
+    oc = ctx.octant_candidates(o)
+    _same_cands(oc, ko.octant_candidates(oref))
+    # mean shift: every item's final centre and radius, W evaluated there
+    m = ctx.meanshift(v, p)
+    mref = ko.meanshift(b, B, w.r_min, w.r_max, sd, w.max_iter)
+    mc = ctx.meanshift_candidates(v, p, m)
+    _same_cands(mc, ko.meanshift_candidates(b, B, w.r_min, w.r_max, mref, m["r"]))
+    # the item's H at its own radius is the mean-shift kernel's final H
+    close(mc["H"], m["H"])
+    for cands in (oc, mc):
+        ref_all = _cand_list(cands)
+        for h_min, top_k in ((0.0, 20), (2.5, 20), (0.0, 1), (0.0, 256)):
+            got = ctx.select_salient(cands, h_min=h_min, top_k=top_k)
+            _same_cands(got, ko.select_salient(ref_all, h_min=h_min, top_k=top_k))
+    ctx.release_volume(v)
+
+
+def test_selection_many_ties_and_duplicates(ctx, ko, ks_mod):
+    ks = ks_mod
+    rng = np.random.default_rng(17)
+    n = 50000                                        # several rounds of 1024-entry sorts
+    c = np.zeros(n, ks.CANDIDATE)
+    c["x"] = rng.integers(0, 6, n)
+    c["y"] = rng.integers(0, 6, n)
+    c["z"] = rng.integers(0, 40, n)
+    c["r"] = rng.integers(0, 4, n)
+    c["source"] = rng.permutation(n)
+    key = ((c["z"] * 6 + c["y"]) * 6 + c["x"]) * 4 + c["r"]
+    # H and W are functions of the region, with many equal values
+    c["W"] = (key % 7) * 0.125
+    c["H"] = (key % 5) * 0.5
+    ref_all = _cand_list(c)
+    for h_min, top_k in ((0.0, 256), (0.75, 20), (-1.0, 7)):
+        got = ctx.select_salient(c, h_min=h_min, top_k=top_k)
+        _same_cands(got, ko.select_salient(ref_all, h_min=h_min, top_k=top_k))
+    assert len(ctx.select_salient(c[:0], top_k=5)) == 0
+    with pytest.raises(ks.KsError):
+        ctx.select_salient(c[:10], top_k=257)
