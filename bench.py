@@ -338,6 +338,7 @@ def run_ks(args):
     if rank == 0 and not args.no_extras:
         # short forms of the batched and serving workloads (full sizes:
         # --mode batch / --mode serve)
+        line["config"]["selection"] = run_selection(ctx, ks, w, params)
         line["config"]["batched"] = run_batched(ctx, ks, synth, count=64, max_dim=128, reps=2)
         line["config"]["serving"] = run_serving(ks.Context, ks, synth, rate=50.0, count=120,
                                                 pool=12, max_dim=96)
@@ -389,6 +390,37 @@ def run_case(args):
                       "dense_config": ctx.dense_config(w.binning["bins"], w.r_max)}), flush=True)
     ctx.close()
     return 0
+
+
+def run_selection(ctx, ks, w, params, reps=5):
+    """Selection of salient regions after the seed searches (threshold,
+    merge of equal regions, order by W, top 20) on the step's workload:
+    candidate building for both schemes (mean shift: Kadir-Brady at every
+    item's final centre) and the selection itself, host wall time of the
+    synchronous calls, median of `reps`."""
+    v = ctx.create_volume(w.volume, w.binning)
+    o, m = ctx.seed_climb(v, params), ctx.meanshift(v, params)
+    t = {"octant_candidates": [], "meanshift_candidates": [], "select_octant": [],
+         "select_meanshift": []}
+    for _ in range(reps + 1):
+        t0 = time.perf_counter()
+        oc = ctx.octant_candidates(o)
+        t1 = time.perf_counter()
+        mc = ctx.meanshift_candidates(v, params, m)
+        t2 = time.perf_counter()
+        so = ctx.select_salient(oc, h_min=0.0, top_k=20)
+        t3 = time.perf_counter()
+        sm = ctx.select_salient(mc, h_min=0.0, top_k=20)
+        t4 = time.perf_counter()
+        for k, dt in zip(t, (t1 - t0, t2 - t1, t3 - t2, t4 - t3)):
+            t[k].append(dt)
+    ctx.release_volume(v)
+    out = {k + "_ms": 1e3 * statistics.median(x[1:]) for k, x in t.items()}
+    out.update({"octant_candidates": len(oc), "meanshift_candidates": len(mc),
+                "selected_octant": len(so), "selected_meanshift": len(sm),
+                "top_W_octant": float(so["W"][0]) if len(so) else None,
+                "top_W_meanshift": float(sm["W"][0]) if len(sm) else None})
+    return out
 
 
 def run_batched(ctx, ks, synth, count=64, max_dim=None, reps=3):

@@ -955,21 +955,27 @@ int ks_meanshift_candidates(ks_ctx *ctx, ks_vol vol, const ks_params *params,
         if (e == cudaSuccess) dout = (ks_candidate *)scratch(c, kScSelOut, (size_t)n * sizeof(ks_candidate), &e);
         if (e != cudaSuccess) return cuda_err(c, e, "candidate buffers");
     }
-    // final centres -> H and W of every scale there -> the item's own scale
-    int32_t *xyz = (int32_t *)scratch(c, kScPts, (size_t)n * 12, &e);
+    // distinct final centres -> H and W of every scale there -> each item's
+    // own scale (many items converge to the same centre)
+    const size_t cb = ms_centres_scratch_bytes(n);
+    uint8_t *work = (uint8_t *)scratch(c, kScPts, cb + 256, &e);
     double *Y = e == cudaSuccess ? (double *)scratch(c, kScY, (size_t)n * 8, &e) : nullptr;
     uint8_t *sb = e == cudaSuccess ? (uint8_t *)scratch(c, kScS, (size_t)n, &e) : nullptr;
     double *H = e == cudaSuccess ? (double *)scratch(c, kScH, (size_t)n * S * 8, &e) : nullptr;
     double *W = e == cudaSuccess ? (double *)scratch(c, kScW, (size_t)n * S * 8, &e) : nullptr;
     if (e != cudaSuccess) return cuda_err(c, e, "candidate scratch");
+    const int32_t *xyz = nullptr;
+    const int *centre = nullptr;
+    int64_t m = 0;
     ProfRec rec;
     prof_begin(c, "ks_select", c->stream, &rec);
-    e = launch_ms_xyz(c->lc(), dres, n, xyz);
+    e = launch_ms_centres(c->lc(), dres, n, work, (unsigned long long *)(work + cb), &xyz, &centre,
+                          &m);
     if (e == cudaSuccess)
         e = launch_dense_points(c->lc(), v->desc, c->ot, c->T, c->L, params->r_min, params->r_max,
-                                params->w_norm, xyz, n, DenseOut{Y, sb, H, W});
+                                params->w_norm, xyz, m, DenseOut{Y, sb, H, W});
     if (e == cudaSuccess)
-        e = launch_ms_candidates(c->lc(), dres, n, H, W, params->r_min, S, dout);
+        e = launch_ms_candidates(c->lc(), dres, n, centre, H, W, params->r_min, S, dout);
     prof_end(c, &rec, c->stream);
     KS_TRY_CUDA(c, e);
     if (!on_device)

@@ -451,70 +451,127 @@ __global__ void __launch_bounds__(256) k_dense4(const DenseArgs a) {
     }
 }
 
-// Kadir-Brady at listed centres: lane = one centre taken from the list,
-// with the dense kernels' shell-incremental counting and scale steps.  The
-// centres are scattered, so every load is the lane's own.  A centre outside
-// the volume flags kStatusBadInput; its lane then walks voxel (0,0,0), so
-// that every read stays inside the halo, and writes nothing.
+// Kadir-Brady at listed centres: one warp per centre.  The lanes split the
+// offset entries of each shell and count into lane-private columns (word v
+// of lane l at +128 v + 4 l); after the shells of a scale, lane b gathers
+// bin b from the 32 columns (starting at column b, so the reads fall in 32
+// banks) into its running count c_b, and zeroes its column.  The scale step
+// then runs on the whole warp: every lane forms the same bin-order entropy
+// sum from shuffled table values (T[0] = T[1] = +0.0, so adding them leaves
+// the sum as the skipping form has it), D is an exact integer reduction, and
+// H, W, the peak test and Y are the same FP64 steps as in scale_step.  A
+// centre outside the volume flags kStatusBadInput and is skipped.
 template <int B, bool WIDE>
 __global__ void __launch_bounds__(128) k_points(const DenseArgs a) {
     // (every kernel of this file declares the dynamic buffer with the same
     // 1024-byte alignment: the declarations share one symbol, and the TMA
     // brick of k_dense needs a 128-byte aligned base)
     extern __shared__ __align__(1024) uint8_t smem[];
-    using Wd = Words<B, WIDE, 1>;
     constexpr bool CTAB = !WIDE;
+    constexpr int NB = (B + 32) / 32;               // bins 0..B, lane l holds l + 32 k
+    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t pt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool have = pt < a.npts;
-    int x = 0, y = 0, z = 0;
-    if (have) {
-        x = a.pts[3 * pt];
-        y = a.pts[3 * pt + 1];
-        z = a.pts[3 * pt + 2];
-    }
-    const bool ok = have && x >= 0 && x < a.vol.nx && y >= 0 && y < a.vol.ny && z >= 0 &&
-                    z < a.vol.nz;
-    if (have && !ok) atomicOr(a.status, kStatusBadInput);
-    if (!ok) x = y = z = 0;
+    const int wpb = blockDim.x >> 5;
     const int pz = (int)a.vol.plane, py = (int)a.vol.pitch;
-    const uint8_t *c0 = a.vol.base + (int64_t)z * a.vol.plane + (int64_t)y * a.vol.pitch + x;
     const Tab<CTAB> tab{a.ot};
-    const uint32_t cnt_lane = smem_u32(smem) + (warp * Wd::kPerLane * 32 + lane) * 4;
-    auto word = [&](int w) { return cnt_lane + ((uint32_t)w << 7); };
-#pragma unroll 4
-    for (int w = 0; w < Wd::kPerLane; ++w) st_shared_u32(word(w), 0u);
-    ScaleState st{0.0, 0.0, 0.0, 0u, 0u, 0ull, 0};
-    for (int i = 0; i < a.S; ++i) {
-        const int r = a.r_min + i;
-        for (int rho = (i == 0 ? 0 : r); rho <= r; ++rho) {
-            const int k0 = tab.c8_start(rho), k1 = tab.c8_start(rho + 1);
-            const int k2 = tab.rest_start(rho), k3 = tab.rest_start(rho + 1);
-            for (int k = k0; k < k1; ++k) {
-                const uint32_t e = tab.c8(k);
-                const int X = (int)(e & 0xffu);
-                const int Y = (int)((e >> 8) & 0xffu) * py;
-                const int Z = (int)((e >> 16) & 0xffu) * pz;
-                const int o[8] = {Z + Y + X, Z + Y - X, Z - Y + X, Z - Y - X,
-                                  Y - Z + X, Y - Z - X, -Z - Y + X, -Z - Y - X};
-                uint32_t v[8];
-#pragma unroll
-                for (int m = 0; m < 8; ++m) v[m] = __ldg(c0 + o[m]);
-#pragma unroll
-                for (int m = 0; m < 8; ++m) red_add_shared(word(Wd::cnt(0, v[m])), 1u);
-            }
-            for (int k = k2; k < k3; ++k) {
-                const uint32_t f = tab.rest(k);
-                const int off = ((int)((f >> 16) & 0xffu) - 64) * pz +
-                                ((int)((f >> 8) & 0xffu) - 64) * py + ((int)(f & 0xffu) - 64);
-                red_add_shared(word(Wd::cnt(0, __ldg(c0 + off))), 1u);
-            }
+    const uint32_t col = smem_u32(smem) + (warp * (B + 1) * 32 + lane) * 4;
+    const uint32_t cols = smem_u32(smem) + warp * (B + 1) * 32 * 4;
+    for (int w = 0; w <= B; ++w) st_shared_u32(col + ((uint32_t)w << 7), 0u);
+    __syncwarp();
+    for (int64_t pt = (int64_t)blockIdx.x * wpb + warp; pt < a.npts; pt += (int64_t)gridDim.x * wpb) {
+        const int x = a.pts[3 * pt], y = a.pts[3 * pt + 1], z = a.pts[3 * pt + 2];
+        if (x < 0 || x >= a.vol.nx || y < 0 || y >= a.vol.ny || z < 0 || z >= a.vol.nz) {
+            if (lane == 0) atomicOr(a.status, kStatusBadInput);
+            continue;                                                  // warp-uniform
         }
-        scale_step<B, WIDE, 1>(a, cnt_lane, 0, i, r, st, pt, ok);
-    }
-    if (ok) {
-        a.out.Y[pt] = st.yb;
-        a.out.s[pt] = (uint8_t)st.sb;
+        const uint8_t *c0 = a.vol.base + (int64_t)z * a.vol.plane + (int64_t)y * a.vol.pitch + x;
+        uint32_t c[NB], p[NB];                       // running and previous counts
+#pragma unroll
+        for (int k = 0; k < NB; ++k) c[k] = p[k] = 0u;
+        ScaleState st{0.0, 0.0, 0.0, 0u, 0u, 0ull, 0};
+        for (int i = 0; i < a.S; ++i) {
+            const int r = a.r_min + i;
+            for (int rho = (i == 0 ? 0 : r); rho <= r; ++rho) {
+                const int k1 = tab.c8_start(rho + 1), k3 = tab.rest_start(rho + 1);
+                for (int k = tab.c8_start(rho) + lane; k < k1; k += 32) {
+                    const uint32_t e = tab.c8(k);
+                    const int X = (int)(e & 0xffu);
+                    const int Y = (int)((e >> 8) & 0xffu) * py;
+                    const int Z = (int)((e >> 16) & 0xffu) * pz;
+                    const int o[8] = {Z + Y + X, Z + Y - X, Z - Y + X, Z - Y - X,
+                                      Y - Z + X, Y - Z - X, -Z - Y + X, -Z - Y - X};
+                    uint32_t v[8];
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) v[m] = __ldg(c0 + o[m]);
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) red_add_shared(col + (v[m] << 7), 1u);
+                }
+                for (int k = tab.rest_start(rho) + lane; k < k3; k += 32) {
+                    const uint32_t f = tab.rest(k);
+                    const int off = ((int)((f >> 16) & 0xffu) - 64) * pz +
+                                    ((int)((f >> 8) & 0xffu) - 64) * py + ((int)(f & 0xffu) - 64);
+                    red_add_shared(col + ((uint32_t)__ldg(c0 + off) << 7), 1u);
+                }
+            }
+            __syncwarp();
+            // gather: lane b adds bin b of every column, then zeroes its own column
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const int bb = lane + 32 * k;
+                if (bb <= B) {
+                    uint32_t sum = 0;
+                    for (int l = 0; l < 32; ++l)
+                        sum += ld_shared_u32(cols + ((uint32_t)bb << 7) + 4 * ((l + lane) & 31));
+                    p[k] = c[k];
+                    c[k] += sum;
+                }
+            }
+            __syncwarp();
+            for (int w = 0; w <= B; ++w) st_shared_u32(col + ((uint32_t)w << 7), 0u);
+            __syncwarp();
+            // scale step on the whole warp (bin 0 = not counted)
+            const uint32_t N = (uint32_t)__ldg(a.ot.ball_size + r) - __shfl_sync(full, c[0], 0);
+            int occ = 0;
+            int64_t d = 0;
+            double t[NB];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const int bb = lane + 32 * k;
+                const bool real = bb >= 1 && bb <= B;
+                occ += __popc(__ballot_sync(full, real && c[k] > 0u));
+                const int64_t dd = real ? (int64_t)c[k] * st.nm1 - (int64_t)p[k] * N : 0;
+                d += dd < 0 ? -dd : dd;
+                t[k] = real ? __ldg(a.T + c[k]) : 0.0;
+            }
+#pragma unroll
+            for (int off = 16; off; off >>= 1) d += __shfl_xor_sync(full, d, off);
+            const uint64_t D = (uint64_t)d;
+            double ssum = 0.0;
+#pragma unroll
+            for (int bb = 1; bb <= B; ++bb) ssum = __dadd_rn(ssum, __shfl_sync(full, t[bb >> 5], bb & 31));
+            const double H = entropy_from_sum(ssum, N, occ, a.L);
+            if (i >= 2 && st.hm2 < st.hm1 && st.hm1 >= H) {      // peak at scale i-1
+                const double Wp = kb_weight(st.dm1, st.nm1, st.nm2, r - 1, a.w_norm);
+                const double yv = __dmul_rn(st.hm1, Wp);
+                if (st.sb == 0 || yv > st.yb) {
+                    st.yb = yv;
+                    st.sb = r - 1;
+                }
+            }
+            if (lane == 0) {
+                if (a.out.H) a.out.H[pt * a.S + i] = H;
+                if (a.out.W) a.out.W[pt * a.S + i] = i == 0 ? 0.0 : kb_weight(D, N, st.nm1, r, a.w_norm);
+            }
+            st.hm2 = st.hm1;
+            st.hm1 = H;
+            st.nm2 = st.nm1;
+            st.nm1 = N;
+            st.dm1 = D;
+        }
+        if (lane == 0) {
+            a.out.Y[pt] = st.yb;
+            a.out.s[pt] = (uint8_t)st.sb;
+        }
     }
 }
 
@@ -639,16 +696,15 @@ int dense_const_rmax() { return kConstRmax; }
 namespace {
 template <int B>
 cudaError_t launch_points_b(const LaunchCtx &lc, const DenseArgs &a) {
-    constexpr int kWarps = 4;
-    const bool wide = is_wide(a.r_max);
-    const size_t smem = (size_t)kWarps * 32 * 4 *
-                        (wide ? Words<B, true, 1>::kPerLane : Words<B, false, 1>::kPerLane);
-    auto kern = wide ? k_points<B, true> : k_points<B, false>;
+    constexpr int kWarps = 4;                       // one centre per warp at a time
+    const size_t smem = (size_t)kWarps * 32 * 4 * (B + 1);
+    auto kern = is_wide(a.r_max) ? k_points<B, true> : k_points<B, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = (a.npts + kWarps * 32 - 1) / (kWarps * 32);
-    kern<<<(unsigned)blocks, kWarps * 32, smem, lc.stream>>>(a);
+    const int64_t need = (a.npts + kWarps - 1) / kWarps;
+    const int64_t cap = (int64_t)lc.num_sms * 16;
+    kern<<<(unsigned)(need < cap ? need : cap), kWarps * 32, smem, lc.stream>>>(a);
     return cudaGetLastError();
 }
 }  // namespace

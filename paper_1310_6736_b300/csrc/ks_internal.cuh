@@ -240,10 +240,16 @@ int seed_blocks_per_sm(int max_B, int max_S, int kinds);
 // ks_select.cu: candidates and the device selection (ks_select_salient).
 cudaError_t launch_oct_candidates(const LaunchCtx &lc, const ks_seed_result *in, int64_t n,
                                   ks_candidate *out);
-cudaError_t launch_ms_xyz(const LaunchCtx &lc, const ks_ms_result *in, int64_t n, int32_t *xyz);
+// The distinct final centres of mean-shift results (*m of them, listed at
+// *xyz) and, per item, the number of its centre (*centre); both inside
+// `scratch` (ms_centres_scratch_bytes(n)); synchronises the stream once.
+size_t ms_centres_scratch_bytes(int64_t n);
+cudaError_t launch_ms_centres(const LaunchCtx &lc, const ks_ms_result *in, int64_t n,
+                              void *scratch, unsigned long long *d_count, const int32_t **xyz,
+                              const int **centre, int64_t *m);
 cudaError_t launch_ms_candidates(const LaunchCtx &lc, const ks_ms_result *in, int64_t n,
-                                 const double *H, const double *W, int r_min, int S,
-                                 ks_candidate *out);
+                                 const int *centre, const double *H, const double *W, int r_min,
+                                 int S, ks_candidate *out);
 size_t select_scratch_bytes(int64_t n);
 // Writes the first min(top_k, #survivors) candidates to `out` (device) and
 // their count to *n_out; synchronises the stream once.

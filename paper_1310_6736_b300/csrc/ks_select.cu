@@ -149,24 +149,60 @@ __global__ void k_oct_cands(const ks_seed_result *in, int64_t n, ks_candidate *o
     }
 }
 
-// Mean-shift results -> the list of their final centres.
-__global__ void k_ms_xyz(const ks_ms_result *in, int64_t n, int32_t *xyz) {
+// Distinct final centres of mean-shift results: insert every centre's key
+// (x, y, z) into the hash table ...
+__global__ void k_ms_centre_keys(const ks_ms_result *in, int64_t n, unsigned long long *keys,
+                                 uint32_t mask) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        xyz[3 * i] = in[i].x;
-        xyz[3 * i + 1] = in[i].y;
-        xyz[3 * i + 2] = in[i].z;
+        const unsigned long long k = ((unsigned long long)(uint16_t)in[i].x) |
+                                     ((unsigned long long)(uint16_t)in[i].y << 16) |
+                                     ((unsigned long long)(uint16_t)in[i].z << 32);
+        uint32_t s = hash_slot(k, mask);
+        for (uint32_t probe = 0; probe <= mask; ++probe) {
+            const unsigned long long prev = atomicCAS(keys + s, kEmpty, k);
+            if (prev == kEmpty || prev == k) break;
+            s = (s + 1) & mask;
+        }
     }
 }
 
-// Mean-shift results + H, W of every scale at their final centres ->
-// candidates at each item's own scale.
-__global__ void k_ms_cands(const ks_ms_result *in, int64_t n, const double *H, const double *W,
-                           int r_min, int S, ks_candidate *out) {
+// ... number the occupied slots and list their centres ...
+__global__ void k_ms_centre_list(const unsigned long long *keys, uint32_t slots, int *idx,
+                                 int32_t *xyz, unsigned long long *count) {
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < slots; s += gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[s];
+        if (k == kEmpty) continue;
+        const int j = (int)atomicAdd(count, 1ull);
+        idx[s] = j;
+        xyz[3 * j] = (int32_t)(k & 0xffffu);
+        xyz[3 * j + 1] = (int32_t)((k >> 16) & 0xffffu);
+        xyz[3 * j + 2] = (int32_t)((k >> 32) & 0xffffu);
+    }
+}
+
+// ... and give every item the number of its centre.
+__global__ void k_ms_centre_of(const ks_ms_result *in, int64_t n, const unsigned long long *keys,
+                               const int *idx, uint32_t mask, int *centre) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = ((unsigned long long)(uint16_t)in[i].x) |
+                                     ((unsigned long long)(uint16_t)in[i].y << 16) |
+                                     ((unsigned long long)(uint16_t)in[i].z << 32);
+        uint32_t s = hash_slot(k, mask);
+        for (uint32_t probe = 0; probe <= mask && keys[s] != k; ++probe) s = (s + 1) & mask;
+        centre[i] = idx[s];
+    }
+}
+
+// Mean-shift results + H, W of every scale at their distinct final centres
+// -> candidates at each item's own scale.
+__global__ void k_ms_cands(const ks_ms_result *in, int64_t n, const int *centre, const double *H,
+                           const double *W, int r_min, int S, ks_candidate *out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const ks_ms_result m = in[i];
-        const int si = m.r - r_min;
+        const int64_t si = (int64_t)centre[i] * S + (m.r - r_min);
         ks_candidate c;
         c.x = m.x;
         c.y = m.y;
@@ -174,8 +210,8 @@ __global__ void k_ms_cands(const ks_ms_result *in, int64_t n, const double *H, c
         c.r = m.r;
         c.source = (int32_t)i;
         c.reserved = 0;
-        c.H = H[i * S + si];
-        c.W = W[i * S + si];
+        c.H = H[si];
+        c.W = W[si];
         out[i] = c;
     }
 }
@@ -190,19 +226,47 @@ cudaError_t launch_oct_candidates(const LaunchCtx &lc, const ks_seed_result *in,
     return cudaGetLastError();
 }
 
-cudaError_t launch_ms_xyz(const LaunchCtx &lc, const ks_ms_result *in, int64_t n, int32_t *xyz) {
+size_t ms_centres_scratch_bytes(int64_t n) {
+    uint32_t slots = 1024;
+    while (slots < 2 * (uint64_t)n) slots <<= 1;
+    return (size_t)slots * 12 + (size_t)n * 16 + 512;
+}
+
+cudaError_t launch_ms_centres(const LaunchCtx &lc, const ks_ms_result *in, int64_t n,
+                              void *scratch, unsigned long long *d_count, const int32_t **xyz,
+                              const int **centre, int64_t *m) {
+    *m = 0;
     if (n == 0) return cudaSuccess;
+    uint32_t slots = 1024;
+    while (slots < 2 * (uint64_t)n) slots <<= 1;
+    uint8_t *p = (uint8_t *)scratch;
+    unsigned long long *keys = (unsigned long long *)p;
+    int *idx = (int *)(p + (size_t)slots * 8);
+    int32_t *list = (int32_t *)(p + (((size_t)slots * 12 + 255) / 256) * 256);
+    int *cen = (int *)(list + 3 * n + 64);
+    cudaError_t e = cudaMemsetAsync(keys, 0xff, (size_t)slots * 8, lc.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_count, 0, 8, lc.stream);
+    if (e != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)lc.num_sms * 8);
-    k_ms_xyz<<<grid, 256, 0, lc.stream>>>(in, n, xyz);
-    return cudaGetLastError();
+    const int sgrid = (int)std::min<int64_t>((slots + 255) / 256, (int64_t)lc.num_sms * 8);
+    k_ms_centre_keys<<<grid, 256, 0, lc.stream>>>(in, n, keys, slots - 1);
+    k_ms_centre_list<<<sgrid, 256, 0, lc.stream>>>(keys, slots, idx, list, d_count);
+    k_ms_centre_of<<<grid, 256, 0, lc.stream>>>(in, n, keys, idx, slots - 1, cen);
+    unsigned long long mm = 0;
+    e = cudaMemcpyAsync(&mm, d_count, 8, cudaMemcpyDeviceToHost, lc.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lc.stream);
+    *xyz = list;
+    *centre = cen;
+    *m = (int64_t)mm;
+    return e;
 }
 
 cudaError_t launch_ms_candidates(const LaunchCtx &lc, const ks_ms_result *in, int64_t n,
-                                 const double *H, const double *W, int r_min, int S,
-                                 ks_candidate *out) {
+                                 const int *centre, const double *H, const double *W, int r_min,
+                                 int S, ks_candidate *out) {
     if (n == 0) return cudaSuccess;
     const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)lc.num_sms * 8);
-    k_ms_cands<<<grid, 256, 0, lc.stream>>>(in, n, H, W, r_min, S, out);
+    k_ms_cands<<<grid, 256, 0, lc.stream>>>(in, n, centre, H, W, r_min, S, out);
     return cudaGetLastError();
 }
 
