@@ -490,3 +490,32 @@ def test_selection_many_ties_and_duplicates(ctx, ko, ks_mod):
     assert len(ctx.select_salient(c[:0], top_k=5)) == 0
     with pytest.raises(ks.KsError):
         ctx.select_salient(c[:10], top_k=257)
+
+
+def test_window_level_workload_equals_oracle(ctx, ko, ks_mod):
+    """The MR workload with the tumour window level (voxels outside [800,
+    2047] not counted): binning, both seed schemes on sampled seeds and the
+    Kadir-Brady quantities at sampled centres equal the oracle's."""
+    ks = ks_mod
+    w = synth.workload("mr256w")
+    v = ctx.create_volume(w.volume, w.binning)
+    b = ko.bin_volume(w.volume, w.binning)
+    assert np.array_equal(ctx.volume_bins(v, w.volume.shape), b)
+    assert (b == 0).mean() > 0.5                      # most voxels fall outside the window
+    ctx.release_volume(v)
+    grid = ko.seed_grid(w.dims, w.stride)
+    rng = np.random.default_rng(5)
+    seeds = grid[rng.choice(len(grid), 40, replace=False)].astype(np.int32)
+    _oct_vs_oracle(ctx, ko, ks, w, seeds=seeds, traj=True)
+    _ms_vs_oracle(ctx, ko, ks, w, seeds=seeds[:12])
+    v = ctx.create_volume(w.volume, w.binning)
+    nx, ny, nz = w.dims
+    cen = np.stack([rng.integers(0, nx, 200), rng.integers(0, ny, 200), rng.integers(0, nz, 200)],
+                   1).astype(np.int32)
+    Y, s, H, W = ctx.dense_points(v, _params(ks, w), cen, want_hw=True)
+    ctx.release_volume(v)
+    Yo, so, Ho, Wo = ko.dense(b, w.binning["bins"], w.r_min, w.r_max, centres=cen, want_hw=True)
+    assert np.array_equal(s, so)
+    close(Y, Yo)
+    close(H, Ho)
+    close(W, Wo)
