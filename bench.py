@@ -378,6 +378,8 @@ def run_case(args):
             ctx.dense_saliency(v, params, (nz, ny, nx), out=(Y, sb))
         elif args.case == "octant":
             ctx.seed_climb(v, params)
+        elif args.case == "quadrant":
+            ctx.seed_climb(v, params, planar=True)
         elif args.case == "meanshift":
             ctx.meanshift(v, params)
         elif args.case == "bin":
@@ -660,7 +662,7 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0,
                     help="seconds of oracle work per reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["dense", "octant", "meanshift", "bin"],
+    ap.add_argument("--case", choices=["dense", "octant", "quadrant", "meanshift", "bin"],
                     help="run one part of the step only (profiling)")
     ap.add_argument("--dense-config", default="",
                     help="force the dense launch shape: path,warps,tile_y,tile_z")

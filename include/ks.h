@@ -196,6 +196,17 @@ int ks_seed_climb(ks_ctx *ctx, ks_vol vol, const ks_params *params,
 /* Mean shift to the uniform pmf (Sec. 2.3, Eq. 4-6) for every (seed, r)
  * item, r = r_min..r_max, item = seed * S + (r - r_min).  Seeds as in
  * ks_seed_climb.  Writes one ks_ms_result per item. */
+/* Quadrant hill-climbing: Alg. 1 as printed, in 2D (Sec. 2.2), run in the
+ * z-slice of each seed.  Windows are the disks {dx^2 + dy^2 <= k^2, dz = 0};
+ * the four closed quadrants j = 0..3 (bit0: x<0, bit1: y<0) give eps_j and
+ * k_j as in ks_seed_climb, the step sum_j eps_j k_j sigma_j / sum_j eps_j
+ * has no z component, and s_best / Y_best / H_best / W_best are evaluated
+ * on the disks at the final centre.  Arguments and results as for
+ * ks_seed_climb. */
+int ks_quadrant_climb(ks_ctx *ctx, ks_vol vol, const ks_params *params,
+                      const int32_t *seeds_xyz, int64_t n_seeds, ks_seed_result *out,
+                      int64_t capacity, int64_t *n_out, int32_t *traj, int out_on_device);
+
 int ks_meanshift(ks_ctx *ctx, ks_vol vol, const ks_params *params,
                  const int32_t *seeds_xyz, int64_t n_seeds,
                  ks_ms_result *out, int64_t capacity, int64_t *n_out,

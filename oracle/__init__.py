@@ -61,11 +61,13 @@ def lib():
                 "ko_seed_grid": (I64, [I32, I32, I32, I32, P]),
                 "ko_octant_climb": (None, [P, I32, I32, I32, I32, I32, I32, I32, I32, P, P,
                                            P, I64, I32, P, P, P, P, P, P, P, P]),
+                "ko_quadrant_climb": (None, [P, I32, I32, I32, I32, I32, I32, I32, I32, P, P,
+                                             P, I64, I32, P, P, P, P, P, P, P, P]),
                 "ko_meanshift": (None, [P, I32, I32, I32, I32, I32, I32, I32, P, P, P, I64,
                                         I32, P, P, P, P, P]),
                 "ko_octant_counts": (None, [P, I32, I32, I32, I32, I32, I32, I32, I32, I32, P]),
                 "ko_octant_one_step": (None, [P, I32, I32, I32, I32, I32, I32, P, P, I32, I32,
-                                              I32, P]),
+                                              I32, I32, P]),
                 "ko_ms_window": (None, [P, I32, I32, I32, I32, I32, I32, I32, I32, P, P]),
                 "ko_max_threads": (I32, []),
             }
@@ -199,7 +201,9 @@ def seed_grid(dims, stride):
 
 
 def octant_climb(bins, B, r_min, r_max, seeds, max_iter=20, w_norm=0, nthreads=0,
-                 want_traj=False):
+                 want_traj=False, planar=False):
+    """Octant climb (3D form of Alg. 1); planar=True: the quadrant climb of
+    Alg. 1 as printed, with disk windows in each seed's z-slice."""
     bins = np.ascontiguousarray(bins, dtype=np.uint8)
     nx, ny, nz = _dims(bins)
     seeds = np.ascontiguousarray(seeds, dtype=np.int32).reshape(-1, 3)
@@ -211,7 +215,8 @@ def octant_climb(bins, B, r_min, r_max, seeds, max_iter=20, w_norm=0, nthreads=0
         "H": np.zeros(n), "W": np.zeros(n),
     }
     traj = np.zeros((n, max_iter + 1, 3), np.int32) if want_traj else None
-    lib().ko_octant_climb(_p(bins), nx, ny, nz, B, r_min, r_max, max_iter, w_norm, _p(T), _p(L),
+    fn = lib().ko_quadrant_climb if planar else lib().ko_octant_climb
+    fn(_p(bins), nx, ny, nz, B, r_min, r_max, max_iter, w_norm, _p(T), _p(L),
                           _p(seeds), n, int(nthreads), _p(out["xyz"]), _p(out["iters"]),
                           _p(out["converged"]), _p(traj) if want_traj else None, _p(out["Y"]),
                           _p(out["s"]), _p(out["H"]), _p(out["W"]))
@@ -220,13 +225,13 @@ def octant_climb(bins, B, r_min, r_max, seeds, max_iter=20, w_norm=0, nthreads=0
     return out
 
 
-def octant_one_step(bins, B, r_min, r_max, p):
+def octant_one_step(bins, B, r_min, r_max, p, planar=False):
     bins = np.ascontiguousarray(bins, dtype=np.uint8)
     nx, ny, nz = _dims(bins)
     T, L = tables(ball_size(r_max))
     st = np.zeros(3, np.int32)
     lib().ko_octant_one_step(_p(bins), nx, ny, nz, B, r_min, r_max, _p(T), _p(L), int(p[0]),
-                             int(p[1]), int(p[2]), _p(st))
+                             int(p[1]), int(p[2]), int(planar), _p(st))
     return st
 
 

@@ -196,14 +196,16 @@ static int ko_shell_of(int d2, int r_min)
     return r;
 }
 
-/* Ball(r_max) offsets ordered by shell (stable within a shell: dz, dy, dx). */
-static ko_off *ko_ball_by_shell(int r_min, int r_max, int64_t *count)
+/* Ball(r_max) offsets ordered by shell (stable within a shell: dz, dy, dx).
+ * planar = 1 keeps only the offsets with dz = 0: the disk of radius r_max
+ * in the centre's z-slice (the 2D windows of Alg. 1 as printed). */
+static ko_off *ko_ball_by_shell_p(int r_min, int r_max, int planar, int64_t *count)
 {
     int64_t n = 0;
     for (int dz = -r_max; dz <= r_max; ++dz)
         for (int dy = -r_max; dy <= r_max; ++dy)
             for (int dx = -r_max; dx <= r_max; ++dx)
-                if (dx * dx + dy * dy + dz * dz <= r_max * r_max) ++n;
+                if (dx * dx + dy * dy + dz * dz <= r_max * r_max && (!planar || dz == 0)) ++n;
     ko_off *o = (ko_off *)malloc(sizeof(ko_off) * (size_t)(n > 0 ? n : 1));
     int64_t k = 0;
     for (int r = r_min; r <= r_max; ++r)
@@ -211,6 +213,7 @@ static ko_off *ko_ball_by_shell(int r_min, int r_max, int64_t *count)
             for (int dy = -r_max; dy <= r_max; ++dy)
                 for (int dx = -r_max; dx <= r_max; ++dx) {
                     int d2 = dx * dx + dy * dy + dz * dz;
+                    if (planar && dz != 0) continue;
                     if (d2 <= r_max * r_max && ko_shell_of(d2, r_min) == r) {
                         o[k].dx = dx; o[k].dy = dy; o[k].dz = dz; o[k].shell = r;
                         ++k;
@@ -218,6 +221,11 @@ static ko_off *ko_ball_by_shell(int r_min, int r_max, int64_t *count)
                 }
     *count = n;
     return o;
+}
+
+static ko_off *ko_ball_by_shell(int r_min, int r_max, int64_t *count)
+{
+    return ko_ball_by_shell_p(r_min, r_max, 0, count);
 }
 
 static void ko_kb_core(const uint8_t *bins, int nx, int ny, int nz, int B,
@@ -350,10 +358,13 @@ static int ko_in_octant(int j, int dx, int dy, int dz)
     return 1;
 }
 
+/* nj = 8: the octants of Ball(k); nj = 4 with a disk `ball`: the four
+ * closed quadrants j = 0..3 of Alg. 1 as printed (bit0: x<0, bit1: y<0),
+ * whose weighted sum gives a step with no z component. */
 static void ko_octant_step(const uint8_t *bins, int nx, int ny, int nz, int B,
                            int r_min, int r_max, const double *T, const double *L,
                            const ko_off *ball, int64_t nball,
-                           const int P[3], int step[3], int64_t *cnt /* 8*B */)
+                           const int P[3], int step[3], int64_t *cnt /* 8*B */, int nj)
 {
     int S = r_max - r_min + 1;
     double eps[8];
@@ -374,31 +385,31 @@ static void ko_octant_step(const uint8_t *bins, int nx, int ny, int nz, int B,
                     if (ko_in_octant(j, dx, dy, dz)) cnt[j * B + s - 1] += 1;
             ++k;
         }
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < nj; ++j) {
             double e = ko_entropy(cnt + j * B, B, T, L);
             if (i == 0 || e > eps[j]) { eps[j] = e; kopt[j] = r; }
         }
     }
     double num[3] = {0.0, 0.0, 0.0}, den = 0.0;
-    for (int j = 0; j < 8; ++j) {
-        int sg[3] = {(j & 1) ? -1 : 1, (j & 2) ? -1 : 1, (j & 4) ? -1 : 1};
+    for (int j = 0; j < nj; ++j) {
+        /* the quadrant form's sigma_j has no z component */
+        int sg[3] = {(j & 1) ? -1 : 1, (j & 2) ? -1 : 1, nj == 8 ? ((j & 4) ? -1 : 1) : 0};
         for (int a = 0; a < 3; ++a) num[a] = num[a] + eps[j] * (double)(kopt[j] * sg[a]);
         den = den + eps[j];
     }
     for (int a = 0; a < 3; ++a) step[a] = den == 0.0 ? 0 : ko_round(num[a] / den);
 }
 
-void ko_octant_climb(const uint8_t *bins, int nx, int ny, int nz, int B,
+static void ko_climb(const uint8_t *bins, int nx, int ny, int nz, int B,
                      int r_min, int r_max, int max_iter, int w_norm,
                      const double *T, const double *L,
-                     const int32_t *seeds, int64_t nseeds, int nthreads,
-                     int32_t *final_xyz, int32_t *iters, int32_t *converged,
-                     int32_t *traj /* nseeds x (max_iter+1) x 3, or NULL */,
+                     const int32_t *seeds, int64_t nseeds, int nthreads, int planar,
+                     int32_t *final_xyz, int32_t *iters, int32_t *converged, int32_t *traj,
                      double *Y_best, int32_t *s_best, double *H_best, double *W_best)
 {
     int S = r_max - r_min + 1;
     int64_t nball = 0;
-    ko_off *ball = ko_ball_by_shell(r_min, r_max, &nball);
+    ko_off *ball = ko_ball_by_shell_p(r_min, r_max, planar, &nball);
     int dim[3] = {nx, ny, nz};
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -419,7 +430,8 @@ void ko_octant_climb(const uint8_t *bins, int nx, int ny, int nz, int B,
             if (traj) for (int a = 0; a < 3; ++a) traj[(i * (max_iter + 1)) * 3 + a] = P[a];
             while (it < max_iter) {
                 int step[3], Pn[3];
-                ko_octant_step(bins, nx, ny, nz, B, r_min, r_max, T, L, ball, nball, P, step, cnt);
+                ko_octant_step(bins, nx, ny, nz, B, r_min, r_max, T, L, ball, nball, P, step, cnt,
+                               planar ? 4 : 8);
                 ++it;
                 for (int a = 0; a < 3; ++a) Pn[a] = ko_clampi(P[a] + step[a], 0, dim[a] - 1);
                 if (Pn[0] == P[0] && Pn[1] == P[1] && Pn[2] == P[2]) { conv = 1; break; }
@@ -443,6 +455,38 @@ void ko_octant_climb(const uint8_t *bins, int nx, int ny, int nz, int B,
         free(cnt); free(cur); free(prev); free(H); free(W);
     }
     free(ball);
+}
+
+void ko_octant_climb(const uint8_t *bins, int nx, int ny, int nz, int B,
+                     int r_min, int r_max, int max_iter, int w_norm,
+                     const double *T, const double *L,
+                     const int32_t *seeds, int64_t nseeds, int nthreads,
+                     int32_t *final_xyz, int32_t *iters, int32_t *converged,
+                     int32_t *traj /* nseeds x (max_iter+1) x 3, or NULL */,
+                     double *Y_best, int32_t *s_best, double *H_best, double *W_best)
+{
+    ko_climb(bins, nx, ny, nz, B, r_min, r_max, max_iter, w_norm, T, L, seeds, nseeds, nthreads,
+             0, final_xyz, iters, converged, traj, Y_best, s_best, H_best, W_best);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Quadrant hill-climbing: Alg. 1 as printed, in 2D (Sec. 2.2), run in the   */
+/* z-slice of each seed.  Windows are disks {dx^2 + dy^2 <= k^2, dz = 0};    */
+/* quadrant j = 0..3 (bit0: x<0, bit1: y<0) is closed as in the 3D form; the */
+/* step is sum_j eps_j k_j sigma_j / sum_j eps_j over the four quadrants     */
+/* (d_j = k_j sigma_j = sqrt2 k_j along the quadrant's diagonal direction),   */
+/* so P moves within its slice.  The Kadir-Brady evaluation at the final P   */
+/* uses the same disks.                                                      */
+/* ------------------------------------------------------------------------ */
+void ko_quadrant_climb(const uint8_t *bins, int nx, int ny, int nz, int B,
+                       int r_min, int r_max, int max_iter, int w_norm,
+                       const double *T, const double *L,
+                       const int32_t *seeds, int64_t nseeds, int nthreads,
+                       int32_t *final_xyz, int32_t *iters, int32_t *converged, int32_t *traj,
+                       double *Y_best, int32_t *s_best, double *H_best, double *W_best)
+{
+    ko_climb(bins, nx, ny, nz, B, r_min, r_max, max_iter, w_norm, T, L, seeds, nseeds, nthreads,
+             1, final_xyz, iters, converged, traj, Y_best, s_best, H_best, W_best);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -561,16 +605,18 @@ void ko_octant_counts(const uint8_t *bins, int nx, int ny, int nz, int B,
             }
 }
 
-/* One octant step at P (the rounded move, before clamping). */
+/* One octant (planar = 0) or quadrant (planar = 1) step at P (the rounded
+ * move, before clamping). */
 void ko_octant_one_step(const uint8_t *bins, int nx, int ny, int nz, int B,
                         int r_min, int r_max, const double *T, const double *L,
-                        int px, int py, int pz, int32_t *step_out)
+                        int px, int py, int pz, int planar, int32_t *step_out)
 {
     int64_t nball = 0;
-    ko_off *ball = ko_ball_by_shell(r_min, r_max, &nball);
+    ko_off *ball = ko_ball_by_shell_p(r_min, r_max, planar, &nball);
     int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * 8 * B);
     int P[3] = {px, py, pz}, step[3];
-    ko_octant_step(bins, nx, ny, nz, B, r_min, r_max, T, L, ball, nball, P, step, cnt);
+    ko_octant_step(bins, nx, ny, nz, B, r_min, r_max, T, L, ball, nball, P, step, cnt,
+                   planar ? 4 : 8);
     for (int a = 0; a < 3; ++a) step_out[a] = step[a];
     free(cnt);
     free(ball);

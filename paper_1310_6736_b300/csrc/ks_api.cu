@@ -1116,7 +1116,7 @@ static int run_queue(Ctx *c, const SeedQueue &q, int max_B, int max_S, int kinds
 
 static int seed_common(Ctx *c, ks_vol vol, const ks_params *p, const int32_t *seeds_xyz,
                        int64_t n_seeds, int kind, void *out, int64_t capacity, int64_t *n_out,
-                       int32_t *traj, int out_on_device) {
+                       int32_t *traj, int out_on_device, int planar = 0) {
     std::string why;
     int st = validate_params(p, &why);
     if (st) return set_err(c, st, why);
@@ -1144,6 +1144,7 @@ static int seed_common(Ctx *c, ks_vol vol, const ks_params *p, const int32_t *se
     if (e != cudaSuccess) return cuda_err(c, e, "seed outputs");
     SeedJob J{};
     J.vol = v->desc;
+    J.planar = planar;
     J.r_min = p->r_min;
     J.r_max = p->r_max;
     J.S = S;
@@ -1187,6 +1188,14 @@ int ks_seed_climb(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_
     if (!ctx) return KS_EINVAL;
     return seed_common(&ctx->impl, vol, params, seeds_xyz, n_seeds, kOctant, out, capacity, n_out,
                        traj, out_on_device);
+}
+
+int ks_quadrant_climb(ks_ctx *ctx, ks_vol vol, const ks_params *params,
+                      const int32_t *seeds_xyz, int64_t n_seeds, ks_seed_result *out,
+                      int64_t capacity, int64_t *n_out, int32_t *traj, int out_on_device) {
+    if (!ctx) return KS_EINVAL;
+    return seed_common(&ctx->impl, vol, params, seeds_xyz, n_seeds, kOctant, out, capacity, n_out,
+                       traj, out_on_device, 1);
 }
 
 int ks_meanshift(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_t *seeds_xyz,

@@ -214,6 +214,8 @@ struct SeedJob {
     ks_seed_result *oct_out;     // device, n_seeds (kind octant)
     ks_ms_result *ms_out;        // device, n_seeds * S (kind mean shift)
     int32_t *traj;               // device, n_seeds * (max_iter+1) * 3, or null
+    int planar;                  // octant kind: 1 = the quadrant climb (disks in the
+                                 // seed's z-slice, four quadrants), 0 = octants
 };
 // A work queue in tickets: segment k covers tickets [seg_start[k],
 // seg_start[k+1]) of kind seg_kind[k] on job seg_job[k]; seed_tickets()

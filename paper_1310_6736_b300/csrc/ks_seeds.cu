@@ -177,6 +177,7 @@ __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *
     for (int ri = threadIdx.x; ri < nrows; ri += blockDim.x) {
         const uint32_t e = __ldg(rows + ri);
         const int dy = (int)(e & 0xffu) - 64, dz = (int)((e >> 8) & 0xffu) - 64;
+        if (J.planar && dz != 0) continue;          // quadrant climb: the disk dz = 0 only
         const int w = (int)(e >> 16);
         const int rr = dy * dy + dz * dz;
         const uint8_t *p = c0 + dz * plane + dy * pitch - w;
@@ -267,10 +268,15 @@ __device__ void octant_step(const SeedJob &J, const double *hb, int step[3]) {
         kopt[j] = __shfl_sync(0xffffffffu, k, j);
     }
     if (lane == 0) {
+        // quadrant climb: the four quadrants j = 0..3 (closed on the plane
+        // z = 0, so their histograms are the disk's), sigma without z
+        const int nj = J.planar ? 4 : 8;
         double num[3] = {0.0, 0.0, 0.0}, den = 0.0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const int sg[3] = {(j & 1) ? -1 : 1, (j & 2) ? -1 : 1, (j & 4) ? -1 : 1};
+            if (j >= nj) break;
+            const int sg[3] = {(j & 1) ? -1 : 1, (j & 2) ? -1 : 1,
+                               J.planar ? 0 : ((j & 4) ? -1 : 1)};
             for (int a = 0; a < 3; ++a)
                 num[a] = __dadd_rn(num[a], __dmul_rn(eps[j], (double)(kopt[j] * sg[a])));
             den = __dadd_rn(den, eps[j]);

@@ -82,6 +82,8 @@ SIGNATURES = {
     "ks_seed_count": (_I, [_P, _I64, C.POINTER(ks_params), C.POINTER(C.c_int64)]),
     "ks_seed_climb": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _I64,
                            C.POINTER(C.c_int64), _P, _I]),
+    "ks_quadrant_climb": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _I64,
+                               C.POINTER(C.c_int64), _P, _I]),
     "ks_meanshift": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _I64,
                           C.POINTER(C.c_int64), _I]),
     "ks_dense_points": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _P, _P, _P, _I]),
@@ -246,25 +248,27 @@ class Context:
         s = np.ascontiguousarray(seeds, dtype=np.int32).reshape(-1, 3)
         return C.c_void_p(s.ctypes.data), s.shape[0], s
 
-    def seed_climb(self, v, params, seeds=None, want_traj=False, out=None):
-        """Octant climb.  out=None: host SEED_RESULT array (and trajectories
-        when want_traj).  out=a CUDA tensor of at least n * 64 bytes: the
-        records stay on the device; returns their count n."""
+    def seed_climb(self, v, params, seeds=None, want_traj=False, out=None, planar=False):
+        """Octant climb (planar=True: the quadrant climb of Alg. 1 as printed,
+        disks in each seed's z-slice).  out=None: host SEED_RESULT array (and
+        trajectories when want_traj).  out=a CUDA tensor of at least n * 64
+        bytes: the records stay on the device; returns their count n."""
+        fn, name = ((lib().ks_quadrant_climb, "ks_quadrant_climb") if planar else
+                    (lib().ks_seed_climb, "ks_seed_climb"))
         sp, ns, keep = self._seeds_arg(seeds)
         n = ns if seeds is not None else self.seed_count(v, params)
         if out is not None:
             if want_traj:
                 raise ValueError("trajectories are returned with host outputs only")
-            return self._seeds_to_device(lib().ks_seed_climb, "ks_seed_climb", v, params, sp, ns,
+            return self._seeds_to_device(fn, name, v, params, sp, ns,
                                          out, n * SEED_RESULT.itemsize, SEED_RESULT.itemsize,
                                          extra=(None,))
         out = np.zeros(max(n, 1), SEED_RESULT)
         traj = np.zeros((max(n, 1), params.max_iter + 1, 3), np.int32) if want_traj else None
         got = C.c_int64()
-        self._check(lib().ks_seed_climb(self.h, int(v), C.byref(params), sp, ns,
-                                        C.c_void_p(out.ctypes.data), out.shape[0], C.byref(got),
-                                        C.c_void_p(traj.ctypes.data) if want_traj else None, 0),
-                    "ks_seed_climb")
+        self._check(fn(self.h, int(v), C.byref(params), sp, ns,
+                       C.c_void_p(out.ctypes.data), out.shape[0], C.byref(got),
+                       C.c_void_p(traj.ctypes.data) if want_traj else None, 0), name)
         out = out[:got.value]
         return (out, traj[:got.value]) if want_traj else out
 

@@ -519,3 +519,28 @@ def test_window_level_workload_equals_oracle(ctx, ko, ks_mod):
     close(Y, Yo)
     close(H, Ho)
     close(W, Wo)
+
+
+@pytest.mark.parametrize("name", ["spheres48", "pet128"])
+def test_quadrant_climb_equals_oracle(ctx, ko, ks_mod, name):
+    """Alg. 1 as printed (2D quadrants, disks in each seed's slice): every
+    grid seed, final centres, iterations, trajectories and the disk
+    Kadir-Brady evaluation bit-exact against the oracle."""
+    ks = ks_mod
+    w = synth.workload(name)
+    v = ctx.create_volume(w.volume, w.binning)
+    got, gtraj = ctx.seed_climb(v, _params(ks, w), want_traj=True, planar=True)
+    ctx.release_volume(v)
+    b = ko.bin_volume(w.volume, w.binning)
+    sd = ko.seed_grid(w.dims, w.stride)
+    ref = ko.octant_climb(b, w.binning["bins"], w.r_min, w.r_max, sd, w.max_iter,
+                          want_traj=True, planar=True)
+    assert np.array_equal(np.stack([got["x"], got["y"], got["z"]], 1), ref["xyz"])
+    assert np.array_equal(got["z"], sd[:, 2])                      # stays in its slice
+    assert np.array_equal(got["iters"], ref["iters"])
+    assert np.array_equal(got["converged"], ref["converged"])
+    assert np.array_equal(got["s_best"], ref["s"])
+    assert np.array_equal(gtraj, ref["traj"])
+    close(got["Y_best"], ref["Y"])
+    close(got["H_best"], ref["H"])
+    close(got["W_best"], ref["W"])
