@@ -69,6 +69,9 @@ def lib():
                 "ko_octant_one_step": (None, [P, I32, I32, I32, I32, I32, I32, P, P, I32, I32,
                                               I32, I32, P]),
                 "ko_ms_window": (None, [P, I32, I32, I32, I32, I32, I32, I32, I32, P, P]),
+                "ko_ab_kernel": (C.c_float, [C.c_float]),
+                "ko_abmsod": (None, [P, I32, I32, I32, I32, I32, I32, I32, P, I64, I32, P, P, P,
+                                     P, P]),
                 "ko_max_threads": (I32, []),
             }
             for name, (res, args) in sig.items():
@@ -311,3 +314,26 @@ def select_salient(cands, h_min=0.0, top_k=20):
     ordered = sorted(regions.values(),
                      key=lambda c: (-c["W"], -c["H"], c["z"], c["y"], c["x"], c["r"]))
     return ordered[:top_k]
+
+
+# -------------------------------------------------------------------- ABMSOD
+def ab_kernel(d):
+    """exp(-d/2) as the ABMSOD definition evaluates it (binary32)."""
+    return float(lib().ko_ab_kernel(float(d)))
+
+
+def abmsod(bins, B, r_min, r_max, seeds, max_iter=20, nthreads=0):
+    """Adaptive-bandwidth mean shift (Alg. 2, Eq. 7) for every (seed, r)
+    item (seed-major): best centre x (FP64), bandwidth H (00 01 02 11 12 22),
+    best Bhattacharyya coefficient rho, iterations and whether the search
+    stopped at a decrease of rho (see ks_oracle.c)."""
+    bins = np.ascontiguousarray(bins, dtype=np.uint8)
+    nx, ny, nz = _dims(bins)
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32).reshape(-1, 3)
+    n = seeds.shape[0] * (r_max - r_min + 1)
+    out = {"x": np.zeros((n, 3)), "H": np.zeros((n, 6)), "rho": np.zeros(n),
+           "iters": np.zeros(n, np.int32), "stopped": np.zeros(n, np.int32)}
+    lib().ko_abmsod(_p(bins), nx, ny, nz, B, r_min, r_max, max_iter, _p(seeds), seeds.shape[0],
+                    int(nthreads), _p(out["x"]), _p(out["H"]), _p(out["rho"]), _p(out["iters"]),
+                    _p(out["stopped"]))
+    return out

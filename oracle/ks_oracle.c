@@ -638,3 +638,248 @@ int ko_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adaptive-bandwidth mean shift (ABMSOD; Sec. 2.3, Alg. 2, Eq. 7) towards  */
+/* the uniform target HQ_b = 1/B.                                            */
+/*                                                                          */
+/* A candidate is a centre x (FP64 vector) with a bandwidth matrix H (FP64, */
+/* symmetric positive definite).  Its window is the ellipsoid               */
+/* { s : d(s) = (s-x)^T H^-1 (s-x) <= 1 } of counted voxels; each voxel     */
+/* carries the kernel k(s) = exp(-d(s)/2) (Alg. 2's c exp(-d/2)).  One      */
+/* iteration:                                                                */
+/*   1. HP_b = (sum of k over bin b) / (sum of k)  at (x, H)                 */
+/*      w_b  = sqrt(HQ_b / HP_b)                                             */
+/*   2. x' = x + sum_s k w o / sum_s k w,  o = s - x  (Eq. 6 with the       */
+/*      Gaussian profile: -k' is proportional to k); clamp to the volume    */
+/*   3. HP' and w' at (x', H)                                                */
+/*   4. H' = (n+2) sum_s w' o' o'^T / sum_s w',  o' = s - x', n = 3 (Eq. 7;  */
+/*      the factor keeps the window of a homogeneous region at its size:    */
+/*      the second moment of a uniform ellipsoid is H / (n+2)); then every  */
+/*      diagonal entry below 1 is raised to 1 and H is scaled down so that  */
+/*      no diagonal entry exceeds 32^2 (the window stays within 32 voxels)  */
+/*   5. bhat = sum_b sqrt(HQ_b HP'_b) (bin order); the best bhat so far      */
+/*      keeps its (x', H'); the search stops at the first bhat below the    */
+/*      best (Alg. 2's THRESHOLD read as 0) or after max_iter iterations.   */
+/* Candidates start at each seed with H = r^2 I for r = r_min..r_max.       */
+/*                                                                          */
+/* Arithmetic: per voxel in binary32 in one fixed order (offset rounded     */
+/* from the FP64 difference, the quadratic form, k by a degree-9 Taylor     */
+/* polynomial in Horner form); every sum over voxels is an exact int64 sum  */
+/* of the terms rounded to a fixed-point grid (2^-20 for k, 2^-16 for the   */
+/* position terms and w', 2^-12 for the second moments), so the result does */
+/* not depend on the order of summation; the per-bin and per-candidate     */
+/* steps are FP64, one IEEE operation at a time.                            */
+/* ------------------------------------------------------------------------ */
+#define AB_QK 1048576.0f   /* 2^20 */
+#define AB_QX 65536.0f     /* 2^16 */
+#define AB_QH 4096.0f      /* 2^12 */
+#define AB_HMAX 1024.0     /* 32^2 */
+
+/* exp(-d/2) for 0 <= d <= 1: sum_{k=0..9} t^k / k!, t = -d/2, Horner form.
+ * The truncation error is below 3e-10, under half a binary32 ulp. */
+float ko_ab_kernel(float d)
+{
+    const float c[10] = {1.0f, 1.0f, 0.5f, 0.16666666666666666f, 0.041666666666666664f,
+                         0.008333333333333333f, 0.001388888888888889f, 1.984126984126984e-04f,
+                         2.48015873015873e-05f, 2.755731922398589e-06f};
+    const float t = -0.5f * d;
+    float p = c[9];
+    for (int k = 8; k >= 0; --k) p = p * t + c[k];
+    return p;
+}
+
+typedef struct {
+    double x[3];
+    double H[6];                    /* 00 01 02 11 12 22 */
+    float hi[6];                    /* H^-1 rounded to binary32 */
+    int lo[3], hi_[3];              /* voxel box of the window */
+} ko_ab_win;
+
+static int ko_ab_setup(ko_ab_win *w, const double x[3], const double H[6])
+{
+    for (int a = 0; a < 3; ++a) w->x[a] = x[a];
+    for (int k = 0; k < 6; ++k) w->H[k] = H[k];
+    const double a00 = H[0], a01 = H[1], a02 = H[2], a11 = H[3], a12 = H[4], a22 = H[5];
+    const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22,
+                 c02 = a01 * a12 - a02 * a11, c11 = a00 * a22 - a02 * a02,
+                 c12 = a01 * a02 - a00 * a12, c22 = a00 * a11 - a01 * a01;
+    const double det = a00 * c00 + a01 * c01 + a02 * c02;
+    if (!(det > 0.0)) return 0;
+    w->hi[0] = (float)(c00 / det); w->hi[1] = (float)(c01 / det); w->hi[2] = (float)(c02 / det);
+    w->hi[3] = (float)(c11 / det); w->hi[4] = (float)(c12 / det); w->hi[5] = (float)(c22 / det);
+    const double dg[3] = {a00, a11, a22};
+    for (int a = 0; a < 3; ++a) {
+        const double e = sqrt(dg[a]);
+        w->lo[a] = (int)ceil(x[a] - e);
+        w->hi_[a] = (int)floor(x[a] + e);
+    }
+    return 1;
+}
+
+/* d(s) and the binary32 offsets of voxel s; returns d */
+static inline float ko_ab_d(const ko_ab_win *w, int sx, int sy, int sz, float o[3])
+{
+    o[0] = (float)((double)sx - w->x[0]);
+    o[1] = (float)((double)sy - w->x[1]);
+    o[2] = (float)((double)sz - w->x[2]);
+    const float *h = w->hi;
+    const float u0 = h[0] * o[0] + h[1] * o[1] + h[2] * o[2];
+    const float u1 = h[1] * o[0] + h[3] * o[1] + h[4] * o[2];
+    const float u2 = h[2] * o[0] + h[4] * o[1] + h[5] * o[2];
+    return o[0] * u0 + o[1] * u1 + o[2] * u2;
+}
+
+static inline int64_t ko_q(float v, float q) { return (int64_t)llrintf(v * q); }
+
+/* pass 1: per-bin kernel sums P[b] (b = 0..B-1) and their total */
+static int64_t ko_ab_hist(const uint8_t *bins, int nx, int ny, int nz, int B, const ko_ab_win *w,
+                          int64_t *P)
+{
+    for (int b = 0; b < B; ++b) P[b] = 0;
+    int64_t K = 0;
+    for (int sz = w->lo[2]; sz <= w->hi_[2]; ++sz)
+        for (int sy = w->lo[1]; sy <= w->hi_[1]; ++sy)
+            for (int sx = w->lo[0]; sx <= w->hi_[0]; ++sx) {
+                const int v = ko_at(bins, nx, ny, nz, sx, sy, sz);
+                if (!v) continue;
+                float o[3];
+                const float d = ko_ab_d(w, sx, sy, sz, o);
+                if (!(d <= 1.0f)) continue;
+                const int64_t k = ko_q(ko_ab_kernel(d), AB_QK);
+                P[v - 1] += k;
+                K += k;
+            }
+    return K;
+}
+
+/* binary32 voxel weights w_b = sqrt((1/B) / (P_b / K)) (0 for empty bins) */
+static void ko_ab_weights(const int64_t *P, int64_t K, int B, float *wf)
+{
+    const double hq = 1.0 / (double)B;
+    for (int b = 0; b < B; ++b)
+        wf[b] = P[b] > 0 ? (float)sqrt(hq / ((double)P[b] / (double)K)) : 0.0f;
+}
+
+void ko_abmsod(const uint8_t *bins, int nx, int ny, int nz, int B,
+               int r_min, int r_max, int max_iter,
+               const int32_t *seeds, int64_t nseeds, int nthreads,
+               double *x_out /* items x 3 */, double *H_out /* items x 6 */,
+               double *rho_out, int32_t *iters_out, int32_t *stopped_out)
+{
+    const int S = r_max - r_min + 1;
+    const int dim[3] = {nx, ny, nz};
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        int64_t *P = (int64_t *)malloc(sizeof(int64_t) * B);
+        float *wf = (float *)malloc(sizeof(float) * B);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t item = 0; item < nseeds * S; ++item) {
+            const int64_t si = item / S;
+            const int r = r_min + (int)(item % S);
+            double x[3] = {seeds[3 * si], seeds[3 * si + 1], seeds[3 * si + 2]};
+            double H[6] = {(double)r * r, 0.0, 0.0, (double)r * r, 0.0, (double)r * r};
+            double x_opt[3] = {x[0], x[1], x[2]}, H_opt[6];
+            for (int k = 0; k < 6; ++k) H_opt[k] = H[k];
+            double best = 0.0;
+            int it = 0, stopped = 0;
+            while (it < max_iter) {
+                ko_ab_win w;
+                if (!ko_ab_setup(&w, x, H)) break;
+                const int64_t K = ko_ab_hist(bins, nx, ny, nz, B, &w, P);
+                if (K == 0) break;
+                ko_ab_weights(P, K, B, wf);
+                /* 2. position */
+                int64_t num[3] = {0, 0, 0}, den = 0;
+                for (int sz = w.lo[2]; sz <= w.hi_[2]; ++sz)
+                    for (int sy = w.lo[1]; sy <= w.hi_[1]; ++sy)
+                        for (int sx = w.lo[0]; sx <= w.hi_[0]; ++sx) {
+                            const int v = ko_at(bins, nx, ny, nz, sx, sy, sz);
+                            if (!v) continue;
+                            float o[3];
+                            const float d = ko_ab_d(&w, sx, sy, sz, o);
+                            if (!(d <= 1.0f)) continue;
+                            const float t = ko_ab_kernel(d) * wf[v - 1];
+                            for (int a = 0; a < 3; ++a) num[a] += ko_q(t * o[a], AB_QX);
+                            den += ko_q(t, AB_QX);
+                        }
+                double xn[3];
+                for (int a = 0; a < 3; ++a) {
+                    const double dl = den > 0 ? (double)num[a] / (double)den : 0.0;
+                    double v = x[a] + dl;
+                    if (v < 0.0) v = 0.0;
+                    if (v > (double)(dim[a] - 1)) v = (double)(dim[a] - 1);
+                    xn[a] = v;
+                }
+                /* 3. histogram and weights at x' */
+                ko_ab_win w2;
+                if (!ko_ab_setup(&w2, xn, H)) break;
+                const int64_t K2 = ko_ab_hist(bins, nx, ny, nz, B, &w2, P);
+                ++it;
+                if (K2 == 0) break;
+                ko_ab_weights(P, K2, B, wf);
+                /* 4. bandwidth */
+                int64_t M[6] = {0, 0, 0, 0, 0, 0}, Ws = 0;
+                for (int sz = w2.lo[2]; sz <= w2.hi_[2]; ++sz)
+                    for (int sy = w2.lo[1]; sy <= w2.hi_[1]; ++sy)
+                        for (int sx = w2.lo[0]; sx <= w2.hi_[0]; ++sx) {
+                            const int v = ko_at(bins, nx, ny, nz, sx, sy, sz);
+                            if (!v) continue;
+                            float o[3];
+                            const float d = ko_ab_d(&w2, sx, sy, sz, o);
+                            if (!(d <= 1.0f)) continue;
+                            const float t = wf[v - 1];
+                            M[0] += ko_q(t * (o[0] * o[0]), AB_QH);
+                            M[1] += ko_q(t * (o[0] * o[1]), AB_QH);
+                            M[2] += ko_q(t * (o[0] * o[2]), AB_QH);
+                            M[3] += ko_q(t * (o[1] * o[1]), AB_QH);
+                            M[4] += ko_q(t * (o[1] * o[2]), AB_QH);
+                            M[5] += ko_q(t * (o[2] * o[2]), AB_QH);
+                            Ws += ko_q(t, AB_QX);
+                        }
+                double Hn[6];
+                for (int k = 0; k < 6; ++k)
+                    Hn[k] = Ws > 0 ? (5.0 * ((double)M[k] / (double)AB_QH)) / ((double)Ws / (double)AB_QX)
+                                   : H[k];
+                const int dg[3] = {0, 3, 5};
+                double m = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    if (Hn[dg[a]] < 1.0) Hn[dg[a]] = 1.0;
+                    if (Hn[dg[a]] > m) m = Hn[dg[a]];
+                }
+                if (m > AB_HMAX) {
+                    const double sc = AB_HMAX / m;
+                    for (int k = 0; k < 6; ++k) Hn[k] = Hn[k] * sc;
+                    for (int a = 0; a < 3; ++a)   /* rounding of m * sc */
+                        if (Hn[dg[a]] > AB_HMAX) Hn[dg[a]] = AB_HMAX;
+                }
+                /* 5. Bhattacharyya coefficient at x' */
+                const double hq = 1.0 / (double)B;
+                double bh = 0.0;
+                for (int b = 0; b < B; ++b)
+                    if (P[b] > 0) bh = bh + sqrt(hq * ((double)P[b] / (double)K2));
+                const double delta = best - bh;
+                if (bh > best) {
+                    best = bh;
+                    for (int a = 0; a < 3; ++a) x_opt[a] = xn[a];
+                    for (int k = 0; k < 6; ++k) H_opt[k] = Hn[k];
+                }
+                if (delta > 0.0) { stopped = 1; break; }
+                for (int a = 0; a < 3; ++a) x[a] = xn[a];
+                for (int k = 0; k < 6; ++k) H[k] = Hn[k];
+            }
+            for (int a = 0; a < 3; ++a) x_out[3 * item + a] = x_opt[a];
+            for (int k = 0; k < 6; ++k) H_out[6 * item + k] = H_opt[k];
+            rho_out[item] = best;
+            iters_out[item] = it;
+            stopped_out[item] = stopped;
+        }
+        free(P);
+        free(wf);
+    }
+}
