@@ -111,6 +111,19 @@ typedef struct ks_ms_result {
     double rho, H;
 } ks_ms_result;
 
+/* One adaptive-bandwidth mean-shift candidate (Sec. 2.3, Alg. 2): the best
+ * centre x over the iterations (FP64 voxel coordinates), its bandwidth
+ * matrix H (entries 00 01 02 11 12 22) and Bhattacharyya coefficient rho to
+ * the uniform pmf; the seed index, the starting radius r (H = r^2 I at the
+ * start), the iterations run, and stopped = 1 when the search ended at a
+ * fall of rho (0: iteration limit or an empty window).  96 bytes. */
+typedef struct ks_abmsod_result {
+    double x[3];
+    double H[6];
+    double rho;
+    int32_t seed, r, iters, stopped;
+} ks_abmsod_result;
+
 /* A candidate salient region: centre, scale r (0 = none), the index of the
  * seed or item it came from, and the window's entropy H and inter-scale pdf
  * change W at that centre and scale.  40 bytes. */
@@ -193,9 +206,6 @@ int ks_seed_climb(ks_ctx *ctx, ks_vol vol, const ks_params *params,
                   ks_seed_result *out, int64_t capacity, int64_t *n_out,
                   int32_t *traj, int out_on_device);
 
-/* Mean shift to the uniform pmf (Sec. 2.3, Eq. 4-6) for every (seed, r)
- * item, r = r_min..r_max, item = seed * S + (r - r_min).  Seeds as in
- * ks_seed_climb.  Writes one ks_ms_result per item. */
 /* Quadrant hill-climbing: Alg. 1 as printed, in 2D (Sec. 2.2), run in the
  * z-slice of each seed.  Windows are the disks {dx^2 + dy^2 <= k^2, dz = 0};
  * the four closed quadrants j = 0..3 (bit0: x<0, bit1: y<0) give eps_j and
@@ -207,10 +217,32 @@ int ks_quadrant_climb(ks_ctx *ctx, ks_vol vol, const ks_params *params,
                       const int32_t *seeds_xyz, int64_t n_seeds, ks_seed_result *out,
                       int64_t capacity, int64_t *n_out, int32_t *traj, int out_on_device);
 
+/* Mean shift to the uniform pmf (Sec. 2.3, Eq. 4-6) for every (seed, r)
+ * item, r = r_min..r_max, item = seed * S + (r - r_min).  Seeds as in
+ * ks_seed_climb.  Writes one ks_ms_result per item. */
 int ks_meanshift(ks_ctx *ctx, ks_vol vol, const ks_params *params,
                  const int32_t *seeds_xyz, int64_t n_seeds,
                  ks_ms_result *out, int64_t capacity, int64_t *n_out,
                  int out_on_device);
+
+/* Adaptive-bandwidth mean shift (ABMSOD; Sec. 2.3, Alg. 2, Eq. 6-7) to the
+ * uniform pmf HQ_b = 1/B for every (seed, r) item, r = r_min..r_max, item =
+ * seed * S + (r - r_min), starting at the seed with H = r^2 I.  The window
+ * is the ellipsoid d(s) = (s-x)^T H^-1 (s-x) <= 1 of counted voxels, each
+ * weighted by k = exp(-d/2).  An iteration: w_b = sqrt(HQ_b / HP_b) from the
+ * kernel histogram HP at (x, H); x' = x + sum k w (s-x) / sum k w, clamped
+ * to the volume; HP' and w' at (x', H); H' = 5 (sum w' (s-x')(s-x')^T /
+ * sum w' + I/12) (Eq. 7 with the factor n + 2 that keeps a homogeneous
+ * ellipsoid's bandwidth, and the second moment I/12 of a unit voxel, which
+ * keeps H' positive definite), diagonal entries raised to >= 1 and H'
+ * scaled so that none exceeds 32^2; rho = sum_b sqrt(HQ_b HP'_b).  The largest rho so far keeps
+ * its (x', H'); the search stops at the first fall of rho or after
+ * params->max_iter iterations.  Per-voxel terms are binary32 and all voxel
+ * sums are exact fixed-point int64 sums, so results are reproducible
+ * bit for bit.  Seeds, capacity and errors as in ks_meanshift. */
+int ks_abmsod(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_t *seeds_xyz,
+              int64_t n_seeds, ks_abmsod_result *out, int64_t capacity, int64_t *n_out,
+              int out_on_device);
 
 /* Kadir-Brady at listed centres: the dense sweep's quantities at n centres
  * given as int32 xyz triples (0 <= x < nx etc.): Y_best, s_best and, when

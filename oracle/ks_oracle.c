@@ -653,28 +653,36 @@ int ko_max_threads(void)
 /*   2. x' = x + sum_s k w o / sum_s k w,  o = s - x  (Eq. 6 with the       */
 /*      Gaussian profile: -k' is proportional to k); clamp to the volume    */
 /*   3. HP' and w' at (x', H)                                                */
-/*   4. H' = (n+2) sum_s w' o' o'^T / sum_s w',  o' = s - x', n = 3 (Eq. 7;  */
-/*      the factor keeps the window of a homogeneous region at its size:    */
-/*      the second moment of a uniform ellipsoid is H / (n+2)); then every  */
-/*      diagonal entry below 1 is raised to 1 and H is scaled down so that  */
-/*      no diagonal entry exceeds 32^2 (the window stays within 32 voxels)  */
+/*   4. H' = (n+2) (sum_s w' o' o'^T / sum_s w' + I/12),  o' = s - x',     */
+/*      n = 3 (Eq. 7; the factor keeps the window of a homogeneous region   */
+/*      at its size: the second moment of a uniform ellipsoid is H/(n+2);   */
+/*      I/12 is the second moment of a unit voxel about its centre, which   */
+/*      keeps H positive definite when the window's voxels lie on a line or */
+/*      a plane); then every diagonal entry below 1 is raised to 1 and H is */
+/*      scaled down so that no diagonal entry exceeds 32^2 (the window      */
+/*      stays within 32 voxels)                                             */
 /*   5. bhat = sum_b sqrt(HQ_b HP'_b) (bin order); the best bhat so far      */
 /*      keeps its (x', H'); the search stops at the first bhat below the    */
 /*      best (Alg. 2's THRESHOLD read as 0) or after max_iter iterations.   */
 /* Candidates start at each seed with H = r^2 I for r = r_min..r_max.       */
+/* A voxel is in the window when 0 <= d(s) <= 1: d < 0 (or not a number)   */
+/* arises only from the binary32 rounding of the inverse of a nearly        */
+/* singular H, and such voxels are left out.                                */
 /*                                                                          */
-/* Arithmetic: per voxel in binary32 in one fixed order (offset rounded     */
-/* from the FP64 difference, the quadratic form, k by a degree-9 Taylor     */
-/* polynomial in Horner form); every sum over voxels is an exact int64 sum  */
-/* of the terms rounded to a fixed-point grid (2^-20 for k, 2^-16 for the   */
-/* position terms and w', 2^-12 for the second moments), so the result does */
+/* Arithmetic: per voxel in binary32 in one fixed order (offset o_a =      */
+/* (s_a - floor(x_a)) - frac(x_a) with frac(x_a) rounded to binary32, the   */
+/* quadratic form, k by a degree-9 Taylor polynomial in Horner form); every */
+/* sum over voxels is an exact int64 sum of the terms rounded to nearest    */
+/* (ties to even) on a fixed-point grid (2^-16 for k, 2^-12 for the         */
+/* position terms and w', 2^-8 for the second moments), so the result does  */
 /* not depend on the order of summation; the per-bin and per-candidate     */
 /* steps are FP64, one IEEE operation at a time.                            */
 /* ------------------------------------------------------------------------ */
-#define AB_QK 1048576.0f   /* 2^20 */
-#define AB_QX 65536.0f     /* 2^16 */
-#define AB_QH 4096.0f      /* 2^12 */
+#define AB_QK 65536.0f     /* 2^16 */
+#define AB_QX 4096.0f      /* 2^12 */
+#define AB_QH 256.0f       /* 2^8 */
 #define AB_HMAX 1024.0     /* 32^2 */
+#define AB_VOXEL (5.0 / 12.0)   /* (n+2) x the second moment of a unit voxel */
 
 /* exp(-d/2) for 0 <= d <= 1: sum_{k=0..9} t^k / k!, t = -d/2, Horner form.
  * The truncation error is below 3e-10, under half a binary32 ulp. */
@@ -693,6 +701,8 @@ typedef struct {
     double x[3];
     double H[6];                    /* 00 01 02 11 12 22 */
     float hi[6];                    /* H^-1 rounded to binary32 */
+    int n[3];                       /* floor(x) */
+    float f[3];                     /* x - floor(x), rounded to binary32 */
     int lo[3], hi_[3];              /* voxel box of the window */
 } ko_ab_win;
 
@@ -710,6 +720,9 @@ static int ko_ab_setup(ko_ab_win *w, const double x[3], const double H[6])
     w->hi[3] = (float)(c11 / det); w->hi[4] = (float)(c12 / det); w->hi[5] = (float)(c22 / det);
     const double dg[3] = {a00, a11, a22};
     for (int a = 0; a < 3; ++a) {
+        const double fl = floor(x[a]);
+        w->n[a] = (int)fl;
+        w->f[a] = (float)(x[a] - fl);   /* exact in FP64 for x >= 0 */
         const double e = sqrt(dg[a]);
         w->lo[a] = (int)ceil(x[a] - e);
         w->hi_[a] = (int)floor(x[a] + e);
@@ -720,9 +733,9 @@ static int ko_ab_setup(ko_ab_win *w, const double x[3], const double H[6])
 /* d(s) and the binary32 offsets of voxel s; returns d */
 static inline float ko_ab_d(const ko_ab_win *w, int sx, int sy, int sz, float o[3])
 {
-    o[0] = (float)((double)sx - w->x[0]);
-    o[1] = (float)((double)sy - w->x[1]);
-    o[2] = (float)((double)sz - w->x[2]);
+    o[0] = (float)(sx - w->n[0]) - w->f[0];
+    o[1] = (float)(sy - w->n[1]) - w->f[1];
+    o[2] = (float)(sz - w->n[2]) - w->f[2];
     const float *h = w->hi;
     const float u0 = h[0] * o[0] + h[1] * o[1] + h[2] * o[2];
     const float u1 = h[1] * o[0] + h[3] * o[1] + h[4] * o[2];
@@ -745,7 +758,7 @@ static int64_t ko_ab_hist(const uint8_t *bins, int nx, int ny, int nz, int B, co
                 if (!v) continue;
                 float o[3];
                 const float d = ko_ab_d(w, sx, sy, sz, o);
-                if (!(d <= 1.0f)) continue;
+                if (!(d >= 0.0f && d <= 1.0f)) continue;
                 const int64_t k = ko_q(ko_ab_kernel(d), AB_QK);
                 P[v - 1] += k;
                 K += k;
@@ -803,7 +816,7 @@ void ko_abmsod(const uint8_t *bins, int nx, int ny, int nz, int B,
                             if (!v) continue;
                             float o[3];
                             const float d = ko_ab_d(&w, sx, sy, sz, o);
-                            if (!(d <= 1.0f)) continue;
+                            if (!(d >= 0.0f && d <= 1.0f)) continue;
                             const float t = ko_ab_kernel(d) * wf[v - 1];
                             for (int a = 0; a < 3; ++a) num[a] += ko_q(t * o[a], AB_QX);
                             den += ko_q(t, AB_QX);
@@ -832,7 +845,7 @@ void ko_abmsod(const uint8_t *bins, int nx, int ny, int nz, int B,
                             if (!v) continue;
                             float o[3];
                             const float d = ko_ab_d(&w2, sx, sy, sz, o);
-                            if (!(d <= 1.0f)) continue;
+                            if (!(d >= 0.0f && d <= 1.0f)) continue;
                             const float t = wf[v - 1];
                             M[0] += ko_q(t * (o[0] * o[0]), AB_QH);
                             M[1] += ko_q(t * (o[0] * o[1]), AB_QH);
@@ -849,6 +862,7 @@ void ko_abmsod(const uint8_t *bins, int nx, int ny, int nz, int B,
                 const int dg[3] = {0, 3, 5};
                 double m = 0.0;
                 for (int a = 0; a < 3; ++a) {
+                    Hn[dg[a]] = Hn[dg[a]] + AB_VOXEL;
                     if (Hn[dg[a]] < 1.0) Hn[dg[a]] = 1.0;
                     if (Hn[dg[a]] > m) m = Hn[dg[a]];
                 }

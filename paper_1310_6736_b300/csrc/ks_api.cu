@@ -66,7 +66,7 @@ struct Scratch {
 };
 enum ScratchSlot {
     kScRaw, kScSeeds, kScOct, kScMs, kScTraj, kScY, kScS, kScH, kScW, kScTune, kScPts,
-    kScSelIn, kScSelOut, kScCount
+    kScSelIn, kScSelOut, kScAb, kScTicket, kScCount
 };
 static std::mutex g_scratch_mu;
 static std::unordered_map<Ctx *, std::vector<Scratch>> g_scratch;
@@ -1204,6 +1204,47 @@ int ks_meanshift(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_t
     if (!ctx) return KS_EINVAL;
     return seed_common(&ctx->impl, vol, params, seeds_xyz, n_seeds, kMeanShift, out, capacity,
                        n_out, nullptr, out_on_device);
+}
+
+int ks_abmsod(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_t *seeds_xyz,
+              int64_t n_seeds, ks_abmsod_result *out, int64_t capacity, int64_t *n_out,
+              int out_on_device) {
+    if (!ctx) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    std::string why;
+    int st = validate_params(params, &why);
+    if (st) return set_err(c, st, why);
+    if (!out || !n_out) return set_err(c, KS_EINVAL, "out / n_out is NULL");
+    if (seeds_xyz && n_seeds < 0) return set_err(c, KS_EINVAL, "n_seeds < 0");
+    Volume *v = find_volume(c, vol);
+    if (!v) return set_err(c, KS_ENOTFOUND, "unknown volume");
+    std::vector<int32_t> hs;
+    int32_t *ds;
+    st = seeds_to_device(c, v, params, seeds_xyz, n_seeds, &hs, &ds);
+    if (st) return st;
+    const int64_t ns = (int64_t)hs.size() / 3;
+    const int S = params->r_max - params->r_min + 1;
+    const int64_t n_items = ns * S;
+    *n_out = n_items;
+    if (capacity < n_items) return set_err(c, KS_EINVAL, "output capacity too small");
+    if (n_items == 0) return KS_OK;
+    cudaError_t e = cudaSuccess;
+    ks_abmsod_result *dout = out;
+    if (!out_on_device)
+        dout = (ks_abmsod_result *)scratch(c, kScAb, n_items * sizeof(ks_abmsod_result), &e);
+    unsigned long long *ticket =
+        e == cudaSuccess ? (unsigned long long *)scratch(c, kScTicket, 16, &e) : nullptr;
+    if (e != cudaSuccess) return cuda_err(c, e, "abmsod outputs");
+    ProfRec rec;
+    prof_begin(c, "ks_abmsod", c->stream, &rec);
+    e = launch_abmsod(c->lc(), v->desc, ds, ns, params->r_min, params->r_max, params->max_iter,
+                      dout, ticket);
+    prof_end(c, &rec, c->stream);
+    KS_TRY_CUDA(c, e);
+    if (!out_on_device)
+        KS_TRY_CUDA(c, cudaMemcpyAsync(out, dout, n_items * sizeof(ks_abmsod_result),
+                                       cudaMemcpyDeviceToHost, c->stream));
+    return check_status(c);
 }
 
 }  // extern "C"

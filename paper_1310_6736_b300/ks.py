@@ -62,7 +62,10 @@ MS_RESULT = np.dtype([("x", "<i4"), ("y", "<i4"), ("z", "<i4"), ("r", "<i4"), ("
                       ("rho", "<f8"), ("H", "<f8")])
 CANDIDATE = np.dtype([("x", "<i4"), ("y", "<i4"), ("z", "<i4"), ("r", "<i4"),
                       ("source", "<i4"), ("reserved", "<i4"), ("H", "<f8"), ("W", "<f8")])
+AB_RESULT = np.dtype([("x", "<f8", (3,)), ("H", "<f8", (6,)), ("rho", "<f8"), ("seed", "<i4"),
+                      ("r", "<i4"), ("iters", "<i4"), ("stopped", "<i4")])
 assert SEED_RESULT.itemsize == 64 and MS_RESULT.itemsize == 48 and CANDIDATE.itemsize == 40
+assert AB_RESULT.itemsize == 96
 
 # Every symbol include/ks.h declares, with (restype, argtypes).
 _P, _I, _I64, _D, _SZ = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_size_t
@@ -86,6 +89,8 @@ SIGNATURES = {
                                C.POINTER(C.c_int64), _P, _I]),
     "ks_meanshift": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _I64,
                           C.POINTER(C.c_int64), _I]),
+    "ks_abmsod": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _I64,
+                       C.POINTER(C.c_int64), _I]),
     "ks_dense_points": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _P, _P, _P, _I]),
     "ks_octant_candidates": (_I, [_P, _P, _I64, _P, _I]),
     "ks_meanshift_candidates": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _I]),
@@ -287,6 +292,23 @@ class Context:
         self._check(lib().ks_meanshift(self.h, int(v), C.byref(params), sp, ns,
                                        C.c_void_p(out.ctypes.data), out.shape[0], C.byref(got), 0),
                     "ks_meanshift")
+        return out[:got.value]
+
+    def abmsod(self, v, params, seeds=None, out=None):
+        """Adaptive-bandwidth mean shift for every (seed, r).  out=None: host
+        AB_RESULT array.  out=a CUDA tensor of at least n * S * 96 bytes: the
+        records stay on the device; returns their count n * S."""
+        sp, ns, keep = self._seeds_arg(seeds)
+        n = ns if seeds is not None else self.seed_count(v, params)
+        S = params.r_max - params.r_min + 1
+        if out is not None:
+            return self._seeds_to_device(lib().ks_abmsod, "ks_abmsod", v, params, sp, ns,
+                                         out, n * S * AB_RESULT.itemsize, AB_RESULT.itemsize)
+        out = np.zeros(max(n * S, 1), AB_RESULT)
+        got = C.c_int64()
+        self._check(lib().ks_abmsod(self.h, int(v), C.byref(params), sp, ns,
+                                    C.c_void_p(out.ctypes.data), out.shape[0], C.byref(got), 0),
+                    "ks_abmsod")
         return out[:got.value]
 
     def _seeds_to_device(self, fn, name, v, params, sp, ns, out, need, rec, extra=()):

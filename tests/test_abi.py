@@ -48,11 +48,12 @@ def test_struct_layouts_match_binding(tmp_path):
     from paper_1310_6736_b300 import ks
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ks.h"\nint main(){'
-                    'printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(ks_seed_result),'
+                    'printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(ks_seed_result),'
                     'sizeof(ks_ms_result), sizeof(ks_request), sizeof(ks_result),'
                     'offsetof(ks_seed_result, Y_best), offsetof(ks_ms_result, rho),'
                     'offsetof(ks_request, kind), sizeof(ks_candidate),'
-                    'offsetof(ks_candidate, H));}')
+                    'offsetof(ks_candidate, H), sizeof(ks_abmsod_result),'
+                    'offsetof(ks_abmsod_result, rho), offsetof(ks_abmsod_result, stopped));}')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(prog)],
                    check=True)
@@ -61,7 +62,9 @@ def test_struct_layouts_match_binding(tmp_path):
     assert got == [ks.SEED_RESULT.itemsize, ks.MS_RESULT.itemsize, C.sizeof(ks.ks_request),
                    C.sizeof(ks.ks_result), ks.SEED_RESULT.fields["Y_best"][1],
                    ks.MS_RESULT.fields["rho"][1], ks.ks_request.kind.offset,
-                   ks.CANDIDATE.itemsize, ks.CANDIDATE.fields["H"][1]]
+                   ks.CANDIDATE.itemsize, ks.CANDIDATE.fields["H"][1],
+                   ks.AB_RESULT.itemsize, ks.AB_RESULT.fields["rho"][1],
+                   ks.AB_RESULT.fields["stopped"][1]]
 
 
 def test_error_strings_and_no_device_path(libks):

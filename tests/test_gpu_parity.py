@@ -544,3 +544,94 @@ def test_quadrant_climb_equals_oracle(ctx, ko, ks_mod, name):
     close(got["Y_best"], ref["Y"])
     close(got["H_best"], ref["H"])
     close(got["W_best"], ref["W"])
+
+
+# ----------------------------------------------------------------- ABMSOD
+def _ab_vs_oracle(ctx, ko, ks, w, seeds=None, max_iter=None):
+    """Adaptive-bandwidth mean shift (Alg. 2, Eq. 7): every item's best
+    centre, bandwidth, rho, iteration count and stop flag bit-exact against
+    the oracle (binary32 voxel terms and exact fixed-point sums on both
+    sides)."""
+    v = ctx.create_volume(w.volume, w.binning)
+    it = w.max_iter if max_iter is None else max_iter
+    p = ks.make_params(w.r_min, w.r_max, w.stride, it)
+    got = ctx.abmsod(v, p, seeds=seeds)
+    ctx.release_volume(v)
+    b = ko.bin_volume(w.volume, w.binning)
+    sd = ko.seed_grid(w.dims, w.stride) if seeds is None else np.asarray(seeds, np.int32)
+    ref = ko.abmsod(b, w.binning["bins"], w.r_min, w.r_max, sd, it)
+    S = w.r_max - w.r_min + 1
+    assert np.array_equal(got["seed"], np.repeat(np.arange(len(sd)), S))
+    assert np.array_equal(got["r"], np.tile(np.arange(w.r_min, w.r_max + 1), len(sd)))
+    assert np.array_equal(got["iters"], ref["iters"])
+    assert np.array_equal(got["stopped"], ref["stopped"])
+    assert np.array_equal(got["x"].view(np.uint64), ref["x"].view(np.uint64))
+    assert np.array_equal(got["H"].view(np.uint64), ref["H"].view(np.uint64))
+    assert np.array_equal(got["rho"].view(np.uint64), ref["rho"].view(np.uint64))
+    return got, ref
+
+
+def test_abmsod_spheres48_all_items(ctx, ko, ks_mod):
+    got, _ = _ab_vs_oracle(ctx, ko, ks_mod, synth.workload("spheres48"))
+    assert (got["stopped"] == 1).any() and (got["iters"] == 20).any()
+
+
+def test_abmsod_pet128_sampled_seeds(ctx, ko, ks_mod):
+    """pet128 at its full size: every 8th grid seed at all 17 radii (the
+    launch shape of the full grid, fewer items for the oracle)."""
+    w = synth.workload("pet128")
+    grid = ko.seed_grid(w.dims, w.stride)
+    _ab_vs_oracle(ctx, ko, ks_mod, w, seeds=grid[::8].copy())
+
+
+def test_abmsod_64_bins_and_edges(ctx, ko, ks_mod):
+    """mr256 (64 bins: two bins per lane), radii up to 32 (windows up to 65
+    voxels wide, at the halo), seeds on the volume's corners and faces."""
+    w = synth.workload("mr256")
+    grid = ko.seed_grid(w.dims, w.stride)
+    rng = np.random.default_rng(5)
+    pick = grid[rng.choice(len(grid), 6, replace=False)]
+    edge = np.array([[0, 0, 0], [255, 255, 159], [128, 0, 80], [255, 130, 0]], np.int32)
+    seeds = np.concatenate([pick, edge]).astype(np.int32)
+    w.r_min, w.r_max = 22, 32
+    _ab_vs_oracle(ctx, ko, ks_mod, w, seeds=seeds, max_iter=6)
+
+
+def test_abmsod_window_level_and_edge_cases(ctx, ko, ks_mod):
+    """Uncounted voxels (window level), a constant volume (HP = e_b every
+    iteration), an all-uncounted volume (empty windows), ragged small
+    volumes, max_iter 0 and 1, a single seed."""
+    ks = ks_mod
+    w = synth.workload("mr256w")
+    grid = ko.seed_grid(w.dims, w.stride)
+    _ab_vs_oracle(ctx, ko, ks, w, seeds=grid[::97].copy(), max_iter=5)
+    vol = np.full((20, 21, 22), 77, np.uint8)
+    wc = synth.Workload("const", vol, {"kind": 0, "bins": 16, "shift": 4, "lo": 0, "hi": 255},
+                        2, 6, 5, 7)
+    got, _ = _ab_vs_oracle(ctx, ko, ks, wc)
+    assert (got["rho"] == 0.25).all()
+    we = synth.Workload("empty", vol, {"kind": 2, "bins": 8, "shift": 4, "lo": 200, "hi": 255},
+                        1, 4, 7, 3)
+    got, _ = _ab_vs_oracle(ctx, ko, ks, we)
+    assert (got["iters"] == 0).all() and (got["rho"] == 0.0).all()
+    rng = np.random.default_rng(8)
+    vr = rng.integers(0, 7, size=(9, 13, 31)).astype(np.uint8)
+    wr = synth.Workload("ragged", vr, {"kind": 0, "bins": 7, "shift": 0, "lo": 0, "hi": 6},
+                        1, 5, 4, 9)
+    _ab_vs_oracle(ctx, ko, ks, wr)
+    _ab_vs_oracle(ctx, ko, ks, wr, max_iter=0)
+    _ab_vs_oracle(ctx, ko, ks, wr, max_iter=1)
+    _ab_vs_oracle(ctx, ko, ks, synth.workload("spheres48"), seeds=np.array([[24, 20, 30]]))
+
+
+def test_abmsod_device_output_equals_host(ctx, ks_mod):
+    import torch
+    ks = ks_mod
+    w = synth.workload("spheres48")
+    v = ctx.create_volume(w.volume, w.binning)
+    p = _params(ks, w)
+    a = ctx.abmsod(v, p)
+    d = torch.zeros(len(a) * ks.AB_RESULT.itemsize, dtype=torch.uint8, device="cuda")
+    assert ctx.abmsod(v, p, out=d) == len(a)
+    ctx.release_volume(v)
+    assert np.array_equal(d.cpu().numpy().view(ks.AB_RESULT), a)

@@ -35,7 +35,8 @@ def test_homogeneous_region_closed_form(r):
     """One bin everywhere: HP = e_b, so rho = sqrt(1/B) every iteration; the
     window is symmetric about an integer centre, so the centre never moves;
     rho never rises after the first iteration, so the best bandwidth is the
-    first update, 5 E[o o^T] over the lattice ball = diag(5 S2 / N)."""
+    first update, 5 (E[o o^T] + I/12) over the lattice ball
+    = diag(5 S2 / N + 5/12)."""
     B = 4
     n = 2 * r + 24
     bins = np.full((n, n, n), 2, np.uint8)
@@ -52,7 +53,7 @@ def test_homogeneous_region_closed_form(r):
     for k in (1, 2, 4):
         assert H[k] == 0.0
     for k in (0, 3, 5):
-        assert H[k] == pytest.approx(5.0 * S2 / N, rel=1e-14)
+        assert H[k] == pytest.approx(5.0 * S2 / N + 5.0 / 12.0, rel=1e-14)
     # the r + 1 item sees the same region: same rho and a fixed centre
     assert res["rho"][1] == 0.5
     assert np.array_equal(res["x"][1], seed[0].astype(float))
@@ -110,7 +111,7 @@ def _fp64_iteration(bins, B, seed, r):
     o2, d2, b2, gap = window(xn)
     _, hp2, w2 = weights(d2, b2)
     ww = w2[b2]
-    Hn = 5.0 * np.einsum("i,ia,ib->ab", ww, o2, o2) / ww.sum()
+    Hn = 5.0 * (np.einsum("i,ia,ib->ab", ww, o2, o2) / ww.sum() + np.eye(3) / 12.0)
     for a in range(3):
         Hn[a, a] = max(Hn[a, a], 1.0)
     rho = np.sqrt(hp2 / B).sum()
@@ -208,3 +209,33 @@ def test_uncounted_region_is_empty_window():
         assert res["iters"][i] == 0 and res["rho"][i] == 0.0
         assert np.array_equal(res["x"][i], [10.0, 10.0, 12.0])
         assert np.array_equal(res["H"][i], [r * r, 0, 0, r * r, 0, r * r])
+
+
+def test_thin_structures_keep_the_search_well_defined():
+    """Counted voxels only on an oblique plane or along a line: the voxel
+    second moments are (nearly) singular, and the unit-voxel term I/12
+    keeps every bandwidth positive definite (smallest eigenvalue >= 5/12
+    up to the scaling to 32^2); rho stays in [0, 1] (Cauchy-Schwarz), H
+    finite with diagonal in [1, 32^2]."""
+    n = 40
+    zz, yy, xx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    plane = np.abs(3 * xx - 2 * yy + zz - 40) <= 1
+    rng = np.random.default_rng(2)
+    bins = np.where(plane, rng.integers(1, 5, size=plane.shape), 0).astype(np.uint8)
+    pts = np.argwhere(plane)[::97][:, ::-1].astype(np.int32)
+    line = np.zeros_like(bins)
+    for t in range(-12, 13):
+        line[20 + t // 2, 20 - t, 20 + t] = 1 + (t & 3)
+    lpts = np.array([[20 + t, 20 - t, 20 + t // 2] for t in range(-9, 10, 3)], np.int32)
+    for vol, sd in ((bins, pts), (line, lpts)):
+        res = ko.abmsod(vol, 4, 6, 14, sd, max_iter=12)
+        assert np.all(np.isfinite(res["rho"]))
+        assert np.all(res["rho"] >= 0) and np.all(res["rho"] <= 1)
+        assert np.all(np.isfinite(res["H"])) and np.all(np.isfinite(res["x"]))
+        for k in (0, 3, 5):
+            assert np.all(res["H"][:, k] >= 1.0) and np.all(res["H"][:, k] <= 1024.0)
+        assert np.all(res["iters"] >= 1)
+        for H in res["H"]:
+            Hm = np.array([[H[0], H[1], H[2]], [H[1], H[3], H[4]], [H[2], H[4], H[5]]])
+            scale = min(1.0, 1024.0 / max(H[0], H[3], H[5]))
+            assert np.linalg.eigvalsh(Hm).min() >= 5.0 / 12.0 * scale * (1 - 1e-9) - 1e-9
