@@ -116,12 +116,15 @@ typedef struct ks_ms_result {
  * matrix H (entries 00 01 02 11 12 22) and Bhattacharyya coefficient rho to
  * the uniform pmf; the seed index, the starting radius r (H = r^2 I at the
  * start), the iterations run, and stopped = 1 when the search ended at a
- * fall of rho (0: iteration limit or an empty window).  96 bytes. */
+ * fall of rho (0: iteration limit or an empty window); voxels: the window
+ * voxels of every kernel histogram the item evaluated (each is visited
+ * again by the position or bandwidth sums of the same window).  104 bytes. */
 typedef struct ks_abmsod_result {
     double x[3];
     double H[6];
     double rho;
     int32_t seed, r, iters, stopped;
+    int64_t voxels;
 } ks_abmsod_result;
 
 /* A candidate salient region: centre, scale r (0 = none), the index of the

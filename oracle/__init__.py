@@ -70,8 +70,9 @@ def lib():
                                               I32, I32, P]),
                 "ko_ms_window": (None, [P, I32, I32, I32, I32, I32, I32, I32, I32, P, P]),
                 "ko_ab_kernel": (C.c_float, [C.c_float]),
+                "ko_ab_window_check": (None, [P, P, P]),
                 "ko_abmsod": (None, [P, I32, I32, I32, I32, I32, I32, I32, P, I64, I32, P, P, P,
-                                     P, P]),
+                                     P, P, P]),
                 "ko_max_threads": (I32, []),
             }
             for name, (res, args) in sig.items():
@@ -325,15 +326,27 @@ def ab_kernel(d):
 def abmsod(bins, B, r_min, r_max, seeds, max_iter=20, nthreads=0):
     """Adaptive-bandwidth mean shift (Alg. 2, Eq. 7) for every (seed, r)
     item (seed-major): best centre x (FP64), bandwidth H (00 01 02 11 12 22),
-    best Bhattacharyya coefficient rho, iterations and whether the search
-    stopped at a decrease of rho (see ks_oracle.c)."""
+    best Bhattacharyya coefficient rho, iterations, whether the search
+    stopped at a decrease of rho, and the window voxels of every kernel
+    histogram evaluated (see ks_oracle.c)."""
     bins = np.ascontiguousarray(bins, dtype=np.uint8)
     nx, ny, nz = _dims(bins)
     seeds = np.ascontiguousarray(seeds, dtype=np.int32).reshape(-1, 3)
     n = seeds.shape[0] * (r_max - r_min + 1)
     out = {"x": np.zeros((n, 3)), "H": np.zeros((n, 6)), "rho": np.zeros(n),
-           "iters": np.zeros(n, np.int32), "stopped": np.zeros(n, np.int32)}
+           "iters": np.zeros(n, np.int32), "stopped": np.zeros(n, np.int32),
+           "voxels": np.zeros(n, np.int64)}
     lib().ko_abmsod(_p(bins), nx, ny, nz, B, r_min, r_max, max_iter, _p(seeds), seeds.shape[0],
                     int(nthreads), _p(out["x"]), _p(out["H"]), _p(out["rho"]), _p(out["iters"]),
-                    _p(out["stopped"]))
+                    _p(out["stopped"]), _p(out["voxels"]))
     return out
+
+
+def ab_window_check(x, H):
+    """(box voxels with 0 <= d <= 1, those inside their row's span) for the
+    window (x, H) in a volume of counted voxels."""
+    x = np.ascontiguousarray(x, np.float64)
+    H = np.ascontiguousarray(H, np.float64)
+    out = np.zeros(2, np.int64)
+    lib().ko_ab_window_check(_p(x), _p(H), _p(out))
+    return int(out[0]), int(out[1])

@@ -661,31 +661,39 @@ int ko_max_threads(void)
 /*      a plane); then every diagonal entry below 1 is raised to 1 and H is */
 /*      scaled down so that no diagonal entry exceeds 32^2 (the window      */
 /*      stays within 32 voxels)                                             */
-/*   5. bhat = sum_b sqrt(HQ_b HP'_b) (bin order); the best bhat so far      */
-/*      keeps its (x', H'); the search stops at the first bhat below the    */
-/*      best (Alg. 2's THRESHOLD read as 0) or after max_iter iterations.   */
+/*   5. rho = sum_b sqrt(HQ_b HP'_b); the best rho so far keeps its         */
+/*      (x', H'); the search stops at the first rho below the best (Alg.    */
+/*      2's THRESHOLD read as 0) or after max_iter iterations.              */
 /* Candidates start at each seed with H = r^2 I for r = r_min..r_max.       */
-/* A voxel is in the window when 0 <= d(s) <= 1: d < 0 (or not a number)   */
-/* arises only from the binary32 rounding of the inverse of a nearly        */
-/* singular H, and such voxels are left out.                                */
 /*                                                                          */
-/* Arithmetic: per voxel in binary32 in one fixed order (offset o_a =      */
-/* (s_a - floor(x_a)) - frac(x_a) with frac(x_a) rounded to binary32, the   */
-/* quadratic form, k by a degree-9 Taylor polynomial in Horner form); every */
-/* sum over voxels is an exact int64 sum of the terms rounded to nearest    */
-/* (ties to even) on a fixed-point grid (2^-16 for k, 2^-12 for the         */
-/* position terms and w', 2^-8 for the second moments), so the result does  */
-/* not depend on the order of summation; the per-bin and per-candidate     */
-/* steps are FP64, one IEEE operation at a time.                            */
+/* Arithmetic.  The window's voxels are found row by row: for the x-row at  */
+/* offsets (o_y, o_z), d as a function of o_x is the quadratic              */
+/* h00 o_x^2 + 2 beta o_x + gamma, and the row's span is where it is at     */
+/* most 1 + 1/16 (binary32 root formula); a voxel of the span is in the     */
+/* window when 0 <= d(s) <= 1 with d evaluated in binary32 (d < 0, or not a */
+/* number, arises only from rounding and is left out).  Offsets are         */
+/* o_a = (s_a - floor(x_a)) - frac(x_a), frac(x_a) rounded to binary32; H^-1 */
+/* is the adjugate times 1/det in FP64, rounded to binary32; k is the       */
+/* degree-9 Taylor polynomial of exp(-d/2) in Horner form with fused        */
+/* multiply-adds.  Every sum over voxels is an exact int64 sum of terms     */
+/* rounded to nearest (ties to even) on a fixed-point grid (2^-16 for k,    */
+/* 2^-12 for the position terms and w', 2^-8 for the second moments), so    */
+/* no result depends on the order of summation.  Per bin: w_b =             */
+/* sqrt(K / (B P_b)) rounded to binary32 and sqrt(P_b) in FP64; rho =       */
+/* (sum_b sqrt(P_b)) / sqrt(B K), the sum over 64 zero-padded slots as a    */
+/* pairwise tree (slot i + m added to slot i, m = 32, 16, ..., 1); H' =     */
+/* 80 M / W (= 5 (M / 2^8) / (W / 2^12)) in FP64.                           */
 /* ------------------------------------------------------------------------ */
 #define AB_QK 65536.0f     /* 2^16 */
 #define AB_QX 4096.0f      /* 2^12 */
 #define AB_QH 256.0f       /* 2^8 */
 #define AB_HMAX 1024.0     /* 32^2 */
 #define AB_VOXEL (5.0 / 12.0)   /* (n+2) x the second moment of a unit voxel */
+#define AB_SLACK 1.0625f   /* the row span covers d <= 1 + 1/16 */
 
-/* exp(-d/2) for 0 <= d <= 1: sum_{k=0..9} t^k / k!, t = -d/2, Horner form.
- * The truncation error is below 3e-10, under half a binary32 ulp. */
+/* exp(-d/2) for 0 <= d <= 1: sum_{k=0..9} t^k / k!, t = -d/2, Horner form
+ * with fused multiply-adds.  The truncation error is below 3e-10, under
+ * half a binary32 ulp. */
 float ko_ab_kernel(float d)
 {
     const float c[10] = {1.0f, 1.0f, 0.5f, 0.16666666666666666f, 0.041666666666666664f,
@@ -693,92 +701,141 @@ float ko_ab_kernel(float d)
                          2.48015873015873e-05f, 2.755731922398589e-06f};
     const float t = -0.5f * d;
     float p = c[9];
-    for (int k = 8; k >= 0; --k) p = p * t + c[k];
+    for (int k = 8; k >= 0; --k) p = fmaf(p, t, c[k]);
     return p;
 }
 
 typedef struct {
     double x[3];
-    double H[6];                    /* 00 01 02 11 12 22 */
-    float hi[6];                    /* H^-1 rounded to binary32 */
+    float h[6];                     /* H^-1 rounded to binary32: 00 01 02 11 12 22 */
     int n[3];                       /* floor(x) */
     float f[3];                     /* x - floor(x), rounded to binary32 */
-    int lo[3], hi_[3];              /* voxel box of the window */
+    int lo[3], hi[3];               /* voxel box of the window */
 } ko_ab_win;
 
 static int ko_ab_setup(ko_ab_win *w, const double x[3], const double H[6])
 {
-    for (int a = 0; a < 3; ++a) w->x[a] = x[a];
-    for (int k = 0; k < 6; ++k) w->H[k] = H[k];
     const double a00 = H[0], a01 = H[1], a02 = H[2], a11 = H[3], a12 = H[4], a22 = H[5];
     const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22,
                  c02 = a01 * a12 - a02 * a11, c11 = a00 * a22 - a02 * a02,
                  c12 = a01 * a02 - a00 * a12, c22 = a00 * a11 - a01 * a01;
     const double det = a00 * c00 + a01 * c01 + a02 * c02;
     if (!(det > 0.0)) return 0;
-    w->hi[0] = (float)(c00 / det); w->hi[1] = (float)(c01 / det); w->hi[2] = (float)(c02 / det);
-    w->hi[3] = (float)(c11 / det); w->hi[4] = (float)(c12 / det); w->hi[5] = (float)(c22 / det);
+    const double inv = 1.0 / det;
+    w->h[0] = (float)(c00 * inv); w->h[1] = (float)(c01 * inv); w->h[2] = (float)(c02 * inv);
+    w->h[3] = (float)(c11 * inv); w->h[4] = (float)(c12 * inv); w->h[5] = (float)(c22 * inv);
     const double dg[3] = {a00, a11, a22};
     for (int a = 0; a < 3; ++a) {
+        w->x[a] = x[a];
         const double fl = floor(x[a]);
         w->n[a] = (int)fl;
         w->f[a] = (float)(x[a] - fl);   /* exact in FP64 for x >= 0 */
         const double e = sqrt(dg[a]);
         w->lo[a] = (int)ceil(x[a] - e);
-        w->hi_[a] = (int)floor(x[a] + e);
+        w->hi[a] = (int)floor(x[a] + e);
     }
     return 1;
 }
 
-/* d(s) and the binary32 offsets of voxel s; returns d */
-static inline float ko_ab_d(const ko_ab_win *w, int sx, int sy, int sz, float o[3])
+/* The span [*ja, *jb] of j = s_x - floor(x_x) in the x-row at offsets
+ * (o1, o2), clipped to the box; returns 0 for an empty row. */
+static int ko_ab_span(const ko_ab_win *w, float o1, float o2, int *ja, int *jb)
 {
-    o[0] = (float)(sx - w->n[0]) - w->f[0];
-    o[1] = (float)(sy - w->n[1]) - w->f[1];
-    o[2] = (float)(sz - w->n[2]) - w->f[2];
-    const float *h = w->hi;
-    const float u0 = h[0] * o[0] + h[1] * o[1] + h[2] * o[2];
-    const float u1 = h[1] * o[0] + h[3] * o[1] + h[4] * o[2];
-    const float u2 = h[2] * o[0] + h[4] * o[1] + h[5] * o[2];
-    return o[0] * u0 + o[1] * u1 + o[2] * u2;
+    const float *h = w->h;
+    const float beta = h[1] * o1 + h[2] * o2;
+    const float gamma = (h[3] * o1 + (2.0f * h[4]) * o2) * o1 + (h[5] * o2) * o2;
+    const float disc = beta * beta - h[0] * (gamma - AB_SLACK);
+    if (!(disc >= 0.0f)) return 0;
+    const float sq = sqrtf(disc);
+    const float ulo = (-beta - sq) / h[0], uhi = (sq - beta) / h[0];
+    const float a = fmaxf(ceilf(ulo + w->f[0]), (float)(w->lo[0] - w->n[0]));
+    const float b = fminf(floorf(uhi + w->f[0]), (float)(w->hi[0] - w->n[0]));
+    if (!(a <= b)) return 0;
+    *ja = (int)a;
+    *jb = (int)b;
+    return 1;
 }
 
 static inline int64_t ko_q(float v, float q) { return (int64_t)llrintf(v * q); }
 
-/* pass 1: per-bin kernel sums P[b] (b = 0..B-1) and their total */
-static int64_t ko_ab_hist(const uint8_t *bins, int nx, int ny, int nz, int B, const ko_ab_win *w,
-                          int64_t *P)
+enum { AB_HIST = 0, AB_POS = 1, AB_MOM = 2 };
+
+/* One pass over the window.  AB_HIST: P[b] += q(k, 2^16), returns K and
+ * adds the window's voxel count to *nvox.  AB_POS: acc[0..2] += q(k w o_a,
+ * 2^12), acc[3] += q(k w, 2^12).  AB_MOM: acc[0..5] += q(w (o_a o_b), 2^8)
+ * (00 01 02 11 12 22), acc[6] += q(w, 2^12). */
+static int64_t ko_ab_pass(const uint8_t *bins, int nx, int ny, int nz, int B, const ko_ab_win *w,
+                          int kind, const float *wf, int64_t *P, int64_t *acc, int64_t *nvox)
 {
-    for (int b = 0; b < B; ++b) P[b] = 0;
     int64_t K = 0;
-    for (int sz = w->lo[2]; sz <= w->hi_[2]; ++sz)
-        for (int sy = w->lo[1]; sy <= w->hi_[1]; ++sy)
-            for (int sx = w->lo[0]; sx <= w->hi_[0]; ++sx) {
-                const int v = ko_at(bins, nx, ny, nz, sx, sy, sz);
+    if (kind == AB_HIST)
+        for (int b = 0; b < B; ++b) P[b] = 0;
+    else
+        for (int k = 0; k < 7; ++k) acc[k] = 0;
+    const float *h = w->h;
+    for (int sz = w->lo[2]; sz <= w->hi[2]; ++sz)
+        for (int sy = w->lo[1]; sy <= w->hi[1]; ++sy) {
+            const float o1 = (float)(sy - w->n[1]) - w->f[1];
+            const float o2 = (float)(sz - w->n[2]) - w->f[2];
+            int ja, jb;
+            if (!ko_ab_span(w, o1, o2, &ja, &jb)) continue;
+            for (int j = ja; j <= jb; ++j) {
+                const int v = ko_at(bins, nx, ny, nz, w->n[0] + j, sy, sz);
                 if (!v) continue;
-                float o[3];
-                const float d = ko_ab_d(w, sx, sy, sz, o);
+                const float o0 = (float)j - w->f[0];
+                const float u0 = h[0] * o0 + h[1] * o1 + h[2] * o2;
+                const float u1 = h[1] * o0 + h[3] * o1 + h[4] * o2;
+                const float u2 = h[2] * o0 + h[4] * o1 + h[5] * o2;
+                const float d = o0 * u0 + o1 * u1 + o2 * u2;
                 if (!(d >= 0.0f && d <= 1.0f)) continue;
-                const int64_t k = ko_q(ko_ab_kernel(d), AB_QK);
-                P[v - 1] += k;
-                K += k;
+                if (kind == AB_HIST) {
+                    const int64_t k = ko_q(ko_ab_kernel(d), AB_QK);
+                    P[v - 1] += k;
+                    K += k;
+                    ++*nvox;
+                } else if (kind == AB_POS) {
+                    const float t = ko_ab_kernel(d) * wf[v - 1];
+                    acc[0] += ko_q(t * o0, AB_QX);
+                    acc[1] += ko_q(t * o1, AB_QX);
+                    acc[2] += ko_q(t * o2, AB_QX);
+                    acc[3] += ko_q(t, AB_QX);
+                } else {
+                    const float t = wf[v - 1];
+                    acc[0] += ko_q(t * (o0 * o0), AB_QH);
+                    acc[1] += ko_q(t * (o0 * o1), AB_QH);
+                    acc[2] += ko_q(t * (o0 * o2), AB_QH);
+                    acc[3] += ko_q(t * (o1 * o1), AB_QH);
+                    acc[4] += ko_q(t * (o1 * o2), AB_QH);
+                    acc[5] += ko_q(t * (o2 * o2), AB_QH);
+                    acc[6] += ko_q(t, AB_QX);
+                }
             }
+        }
     return K;
 }
 
-/* binary32 voxel weights w_b = sqrt((1/B) / (P_b / K)) (0 for empty bins) */
+/* binary32 voxel weights w_b = sqrt(K / (B P_b)) (0 for empty bins) */
 static void ko_ab_weights(const int64_t *P, int64_t K, int B, float *wf)
 {
-    const double hq = 1.0 / (double)B;
     for (int b = 0; b < B; ++b)
-        wf[b] = P[b] > 0 ? (float)sqrt(hq / ((double)P[b] / (double)K)) : 0.0f;
+        wf[b] = P[b] > 0 ? (float)sqrt((double)K / ((double)B * (double)P[b])) : 0.0f;
+}
+
+/* rho = (sum_b sqrt(P_b)) / sqrt(B K), pairwise over 64 zero-padded slots */
+static double ko_ab_rho(const int64_t *P, int64_t K, int B)
+{
+    double t[64];
+    for (int b = 0; b < 64; ++b) t[b] = b < B && P[b] > 0 ? sqrt((double)P[b]) : 0.0;
+    for (int m = 32; m >= 1; m >>= 1)
+        for (int i = 0; i < m; ++i) t[i] = t[i] + t[i + m];
+    return t[0] / sqrt((double)B * (double)K);
 }
 
 void ko_abmsod(const uint8_t *bins, int nx, int ny, int nz, int B,
                int r_min, int r_max, int max_iter,
                const int32_t *seeds, int64_t nseeds, int nthreads,
                double *x_out /* items x 3 */, double *H_out /* items x 6 */,
-               double *rho_out, int32_t *iters_out, int32_t *stopped_out)
+               double *rho_out, int32_t *iters_out, int32_t *stopped_out, int64_t *voxels_out)
 {
     const int S = r_max - r_min + 1;
     const int dim[3] = {nx, ny, nz};
@@ -801,29 +858,18 @@ void ko_abmsod(const uint8_t *bins, int nx, int ny, int nz, int B,
             for (int k = 0; k < 6; ++k) H_opt[k] = H[k];
             double best = 0.0;
             int it = 0, stopped = 0;
+            int64_t nvox = 0, acc[7];
             while (it < max_iter) {
                 ko_ab_win w;
                 if (!ko_ab_setup(&w, x, H)) break;
-                const int64_t K = ko_ab_hist(bins, nx, ny, nz, B, &w, P);
+                const int64_t K = ko_ab_pass(bins, nx, ny, nz, B, &w, AB_HIST, NULL, P, NULL, &nvox);
                 if (K == 0) break;
                 ko_ab_weights(P, K, B, wf);
-                /* 2. position */
-                int64_t num[3] = {0, 0, 0}, den = 0;
-                for (int sz = w.lo[2]; sz <= w.hi_[2]; ++sz)
-                    for (int sy = w.lo[1]; sy <= w.hi_[1]; ++sy)
-                        for (int sx = w.lo[0]; sx <= w.hi_[0]; ++sx) {
-                            const int v = ko_at(bins, nx, ny, nz, sx, sy, sz);
-                            if (!v) continue;
-                            float o[3];
-                            const float d = ko_ab_d(&w, sx, sy, sz, o);
-                            if (!(d >= 0.0f && d <= 1.0f)) continue;
-                            const float t = ko_ab_kernel(d) * wf[v - 1];
-                            for (int a = 0; a < 3; ++a) num[a] += ko_q(t * o[a], AB_QX);
-                            den += ko_q(t, AB_QX);
-                        }
+                /* 2. position (Eq. 6) */
+                ko_ab_pass(bins, nx, ny, nz, B, &w, AB_POS, wf, NULL, acc, NULL);
                 double xn[3];
                 for (int a = 0; a < 3; ++a) {
-                    const double dl = den > 0 ? (double)num[a] / (double)den : 0.0;
+                    const double dl = acc[3] > 0 ? (double)acc[a] / (double)acc[3] : 0.0;
                     double v = x[a] + dl;
                     if (v < 0.0) v = 0.0;
                     if (v > (double)(dim[a] - 1)) v = (double)(dim[a] - 1);
@@ -832,33 +878,15 @@ void ko_abmsod(const uint8_t *bins, int nx, int ny, int nz, int B,
                 /* 3. histogram and weights at x' */
                 ko_ab_win w2;
                 if (!ko_ab_setup(&w2, xn, H)) break;
-                const int64_t K2 = ko_ab_hist(bins, nx, ny, nz, B, &w2, P);
+                const int64_t K2 = ko_ab_pass(bins, nx, ny, nz, B, &w2, AB_HIST, NULL, P, NULL, &nvox);
                 ++it;
                 if (K2 == 0) break;
                 ko_ab_weights(P, K2, B, wf);
-                /* 4. bandwidth */
-                int64_t M[6] = {0, 0, 0, 0, 0, 0}, Ws = 0;
-                for (int sz = w2.lo[2]; sz <= w2.hi_[2]; ++sz)
-                    for (int sy = w2.lo[1]; sy <= w2.hi_[1]; ++sy)
-                        for (int sx = w2.lo[0]; sx <= w2.hi_[0]; ++sx) {
-                            const int v = ko_at(bins, nx, ny, nz, sx, sy, sz);
-                            if (!v) continue;
-                            float o[3];
-                            const float d = ko_ab_d(&w2, sx, sy, sz, o);
-                            if (!(d >= 0.0f && d <= 1.0f)) continue;
-                            const float t = wf[v - 1];
-                            M[0] += ko_q(t * (o[0] * o[0]), AB_QH);
-                            M[1] += ko_q(t * (o[0] * o[1]), AB_QH);
-                            M[2] += ko_q(t * (o[0] * o[2]), AB_QH);
-                            M[3] += ko_q(t * (o[1] * o[1]), AB_QH);
-                            M[4] += ko_q(t * (o[1] * o[2]), AB_QH);
-                            M[5] += ko_q(t * (o[2] * o[2]), AB_QH);
-                            Ws += ko_q(t, AB_QX);
-                        }
+                /* 4. bandwidth (Eq. 7) */
+                ko_ab_pass(bins, nx, ny, nz, B, &w2, AB_MOM, wf, NULL, acc, NULL);
                 double Hn[6];
                 for (int k = 0; k < 6; ++k)
-                    Hn[k] = Ws > 0 ? (5.0 * ((double)M[k] / (double)AB_QH)) / ((double)Ws / (double)AB_QX)
-                                   : H[k];
+                    Hn[k] = acc[6] > 0 ? (80.0 * (double)acc[k]) / (double)acc[6] : H[k];
                 const int dg[3] = {0, 3, 5};
                 double m = 0.0;
                 for (int a = 0; a < 3; ++a) {
@@ -873,10 +901,7 @@ void ko_abmsod(const uint8_t *bins, int nx, int ny, int nz, int B,
                         if (Hn[dg[a]] > AB_HMAX) Hn[dg[a]] = AB_HMAX;
                 }
                 /* 5. Bhattacharyya coefficient at x' */
-                const double hq = 1.0 / (double)B;
-                double bh = 0.0;
-                for (int b = 0; b < B; ++b)
-                    if (P[b] > 0) bh = bh + sqrt(hq * ((double)P[b] / (double)K2));
+                const double bh = ko_ab_rho(P, K2, B);
                 const double delta = best - bh;
                 if (bh > best) {
                     best = bh;
@@ -892,8 +917,38 @@ void ko_abmsod(const uint8_t *bins, int nx, int ny, int nz, int B,
             rho_out[item] = best;
             iters_out[item] = it;
             stopped_out[item] = stopped;
+            voxels_out[item] = nvox;
         }
         free(P);
         free(wf);
     }
+}
+
+/* Window membership two ways, for a uniform volume of counted voxels:
+ * out[0] = voxels of the box with 0 <= d <= 1, out[1] = those of them that
+ * lie in their row's span (equal when the spans lose nothing). */
+void ko_ab_window_check(const double x[3], const double H[6], int64_t out[2])
+{
+    ko_ab_win w;
+    out[0] = out[1] = 0;
+    if (!ko_ab_setup(&w, x, H)) return;
+    const float *h = w.h;
+    for (int sz = w.lo[2]; sz <= w.hi[2]; ++sz)
+        for (int sy = w.lo[1]; sy <= w.hi[1]; ++sy) {
+            const float o1 = (float)(sy - w.n[1]) - w.f[1];
+            const float o2 = (float)(sz - w.n[2]) - w.f[2];
+            int ja = 1, jb = 0;
+            ko_ab_span(&w, o1, o2, &ja, &jb);
+            for (int sx = w.lo[0]; sx <= w.hi[0]; ++sx) {
+                const int j = sx - w.n[0];
+                const float o0 = (float)j - w.f[0];
+                const float u0 = h[0] * o0 + h[1] * o1 + h[2] * o2;
+                const float u1 = h[1] * o0 + h[3] * o1 + h[4] * o2;
+                const float u2 = h[2] * o0 + h[4] * o1 + h[5] * o2;
+                const float d = o0 * u0 + o1 * u1 + o2 * u2;
+                if (!(d >= 0.0f && d <= 1.0f)) continue;
+                out[0] += 1;
+                out[1] += (j >= ja && j <= jb);
+            }
+        }
 }

@@ -63,9 +63,9 @@ MS_RESULT = np.dtype([("x", "<i4"), ("y", "<i4"), ("z", "<i4"), ("r", "<i4"), ("
 CANDIDATE = np.dtype([("x", "<i4"), ("y", "<i4"), ("z", "<i4"), ("r", "<i4"),
                       ("source", "<i4"), ("reserved", "<i4"), ("H", "<f8"), ("W", "<f8")])
 AB_RESULT = np.dtype([("x", "<f8", (3,)), ("H", "<f8", (6,)), ("rho", "<f8"), ("seed", "<i4"),
-                      ("r", "<i4"), ("iters", "<i4"), ("stopped", "<i4")])
+                      ("r", "<i4"), ("iters", "<i4"), ("stopped", "<i4"), ("voxels", "<i8")])
 assert SEED_RESULT.itemsize == 64 and MS_RESULT.itemsize == 48 and CANDIDATE.itemsize == 40
-assert AB_RESULT.itemsize == 96
+assert AB_RESULT.itemsize == 104
 
 # Every symbol include/ks.h declares, with (restype, argtypes).
 _P, _I, _I64, _D, _SZ = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_size_t
@@ -296,7 +296,7 @@ class Context:
 
     def abmsod(self, v, params, seeds=None, out=None):
         """Adaptive-bandwidth mean shift for every (seed, r).  out=None: host
-        AB_RESULT array.  out=a CUDA tensor of at least n * S * 96 bytes: the
+        AB_RESULT array.  out=a CUDA tensor of at least n * S * 104 bytes: the
         records stay on the device; returns their count n * S."""
         sp, ns, keep = self._seeds_arg(seeds)
         n = ns if seeds is not None else self.seed_count(v, params)

@@ -53,7 +53,7 @@ def test_struct_layouts_match_binding(tmp_path):
                     'offsetof(ks_seed_result, Y_best), offsetof(ks_ms_result, rho),'
                     'offsetof(ks_request, kind), sizeof(ks_candidate),'
                     'offsetof(ks_candidate, H), sizeof(ks_abmsod_result),'
-                    'offsetof(ks_abmsod_result, rho), offsetof(ks_abmsod_result, stopped));}')
+                    'offsetof(ks_abmsod_result, rho), offsetof(ks_abmsod_result, voxels));}')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(prog)],
                    check=True)
@@ -64,7 +64,7 @@ def test_struct_layouts_match_binding(tmp_path):
                    ks.MS_RESULT.fields["rho"][1], ks.ks_request.kind.offset,
                    ks.CANDIDATE.itemsize, ks.CANDIDATE.fields["H"][1],
                    ks.AB_RESULT.itemsize, ks.AB_RESULT.fields["rho"][1],
-                   ks.AB_RESULT.fields["stopped"][1]]
+                   ks.AB_RESULT.fields["voxels"][1]]
 
 
 def test_error_strings_and_no_device_path(libks):

@@ -565,6 +565,7 @@ def _ab_vs_oracle(ctx, ko, ks, w, seeds=None, max_iter=None):
     assert np.array_equal(got["r"], np.tile(np.arange(w.r_min, w.r_max + 1), len(sd)))
     assert np.array_equal(got["iters"], ref["iters"])
     assert np.array_equal(got["stopped"], ref["stopped"])
+    assert np.array_equal(got["voxels"], ref["voxels"])
     assert np.array_equal(got["x"].view(np.uint64), ref["x"].view(np.uint64))
     assert np.array_equal(got["H"].view(np.uint64), ref["H"].view(np.uint64))
     assert np.array_equal(got["rho"].view(np.uint64), ref["rho"].view(np.uint64))

@@ -57,6 +57,9 @@ def test_homogeneous_region_closed_form(r):
     # the r + 1 item sees the same region: same rho and a fixed centre
     assert res["rho"][1] == 0.5
     assert np.array_equal(res["x"][1], seed[0].astype(float))
+    # one iteration evaluates the ball twice (at x and at x' = x)
+    one = ko.abmsod(bins, B, r, r + 1, seed, max_iter=1)
+    assert one["voxels"][0] == 2 * len(pts)
 
 
 @pytest.mark.parametrize("e", [(2, 1, 0), (-1, 0, 3), (0, -2, -2)])
@@ -239,3 +242,23 @@ def test_thin_structures_keep_the_search_well_defined():
             Hm = np.array([[H[0], H[1], H[2]], [H[1], H[3], H[4]], [H[2], H[4], H[5]]])
             scale = min(1.0, 1024.0 / max(H[0], H[3], H[5]))
             assert np.linalg.eigvalsh(Hm).min() >= 5.0 / 12.0 * scale * (1 - 1e-9) - 1e-9
+
+
+def test_row_spans_hold_every_window_voxel():
+    """The row span (the root interval of d <= 1 + 1/16 along x) contains
+    every voxel of the bounding box with 0 <= d <= 1, for round, flat,
+    elongated and oblique bandwidths (condition numbers up to ~2500)."""
+    rng = np.random.default_rng(4)
+    checked = 0
+    for _ in range(300):
+        Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        lam = np.exp(rng.uniform(np.log(5.0 / 12.0), np.log(1024.0), 3))
+        Hm = Q @ np.diag(lam) @ Q.T
+        scale = min(1.0, 1024.0 / Hm.diagonal().max())
+        Hm = Hm * scale
+        H = np.array([Hm[0, 0], Hm[0, 1], Hm[0, 2], Hm[1, 1], Hm[1, 2], Hm[2, 2]])
+        x = rng.uniform(40.0, 60.0, 3)
+        box, span = ko.ab_window_check(x, H)
+        assert box == span and box > 0, (x, H, box, span)
+        checked += 1
+    assert checked == 300
