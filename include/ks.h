@@ -372,6 +372,13 @@ int ks_dense_config(ks_ctx *ctx, int bins, int r_max, int *path, int *warps,
  * that call. */
 int ks_force_dense_config(int path, int warps, int tile_y, int tile_z);
 
+/* ABMSOD work split for every context of the process: items whose starting
+ * radius is at least r_team run on a whole thread block (8 warps share each
+ * window pass), smaller ones on one warp each.  r_team <= 0 restores the
+ * default (12); r_team > 32 puts every item on one warp.  Results do not
+ * depend on the split.  KS_EINVAL: r_team > 33. */
+int ks_set_abmsod_team_radius(int r_team);
+
 /* Failure-detection self-test: one thread waits on a device barrier that
  * nothing will complete, gives up after `polls` polls (1..2^20), records
  * the timeout in the context's status word and exits -- the same bounded

@@ -669,9 +669,13 @@ int ko_max_threads(void)
 /* Arithmetic.  The window's voxels are found row by row: for the x-row at  */
 /* offsets (o_y, o_z), d as a function of o_x is the quadratic              */
 /* h00 o_x^2 + 2 beta o_x + gamma, and the row's span is where it is at     */
-/* most 1 + 1/16 (binary32 root formula); a voxel of the span is in the     */
+/* most 1 + 1/16 (binary32 root formula, the division by h00 done as a      */
+/* product with 1/h00); a voxel of the span is in the                       */
 /* window when 0 <= d(s) <= 1 with d evaluated in binary32 (d < 0, or not a */
-/* number, arises only from rounding and is left out).  Offsets are         */
+/* number, arises only from rounding and is left out).  The rows are those  */
+/* of the box [floor(x_a) - E_a, floor(x_a) + E_a] clipped to the volume,   */
+/* E_a = ceil(sqrt(H_aa)) in binary32 (voxels outside the volume are not    */
+/* counted).  Offsets are                                                   */
 /* o_a = (s_a - floor(x_a)) - frac(x_a), frac(x_a) rounded to binary32; H^-1 */
 /* is the adjugate times 1/det in FP64, rounded to binary32; k is the       */
 /* degree-9 Taylor polynomial of exp(-d/2) in Horner form with fused        */
@@ -679,7 +683,8 @@ int ko_max_threads(void)
 /* rounded to nearest (ties to even) on a fixed-point grid (2^-16 for k,    */
 /* 2^-12 for the position terms and w', 2^-8 for the second moments), so    */
 /* no result depends on the order of summation.  Per bin: w_b =             */
-/* sqrt(K / (B P_b)) rounded to binary32 and sqrt(P_b) in FP64; rho =       */
+/* sqrt(K / (B P_b)) in binary32 (K, B, P_b rounded to binary32) and        */
+/* sqrt(P_b) in FP64; rho =                                                 */
 /* (sum_b sqrt(P_b)) / sqrt(B K), the sum over 64 zero-padded slots as a    */
 /* pairwise tree (slot i + m added to slot i, m = 32, 16, ..., 1); H' =     */
 /* 80 M / W (= 5 (M / 2^8) / (W / 2^12)) in FP64.                           */
@@ -713,7 +718,7 @@ typedef struct {
     int lo[3], hi[3];               /* voxel box of the window */
 } ko_ab_win;
 
-static int ko_ab_setup(ko_ab_win *w, const double x[3], const double H[6])
+static int ko_ab_setup(ko_ab_win *w, const double x[3], const double H[6], const int dim[3])
 {
     const double a00 = H[0], a01 = H[1], a02 = H[2], a11 = H[3], a12 = H[4], a22 = H[5];
     const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22,
@@ -730,9 +735,9 @@ static int ko_ab_setup(ko_ab_win *w, const double x[3], const double H[6])
         const double fl = floor(x[a]);
         w->n[a] = (int)fl;
         w->f[a] = (float)(x[a] - fl);   /* exact in FP64 for x >= 0 */
-        const double e = sqrt(dg[a]);
-        w->lo[a] = (int)ceil(x[a] - e);
-        w->hi[a] = (int)floor(x[a] + e);
+        const int E = (int)ceilf(sqrtf((float)dg[a]));
+        w->lo[a] = w->n[a] - E > 0 ? w->n[a] - E : 0;
+        w->hi[a] = w->n[a] + E < dim[a] - 1 ? w->n[a] + E : dim[a] - 1;
     }
     return 1;
 }
@@ -747,7 +752,8 @@ static int ko_ab_span(const ko_ab_win *w, float o1, float o2, int *ja, int *jb)
     const float disc = beta * beta - h[0] * (gamma - AB_SLACK);
     if (!(disc >= 0.0f)) return 0;
     const float sq = sqrtf(disc);
-    const float ulo = (-beta - sq) / h[0], uhi = (sq - beta) / h[0];
+    const float ih0 = 1.0f / h[0];
+    const float ulo = (-beta - sq) * ih0, uhi = (sq - beta) * ih0;
     const float a = fmaxf(ceilf(ulo + w->f[0]), (float)(w->lo[0] - w->n[0]));
     const float b = fminf(floorf(uhi + w->f[0]), (float)(w->hi[0] - w->n[0]));
     if (!(a <= b)) return 0;
@@ -818,7 +824,7 @@ static int64_t ko_ab_pass(const uint8_t *bins, int nx, int ny, int nz, int B, co
 static void ko_ab_weights(const int64_t *P, int64_t K, int B, float *wf)
 {
     for (int b = 0; b < B; ++b)
-        wf[b] = P[b] > 0 ? (float)sqrt((double)K / ((double)B * (double)P[b])) : 0.0f;
+        wf[b] = P[b] > 0 ? sqrtf((float)K / ((float)B * (float)P[b])) : 0.0f;
 }
 
 /* rho = (sum_b sqrt(P_b)) / sqrt(B K), pairwise over 64 zero-padded slots */
@@ -861,7 +867,7 @@ void ko_abmsod(const uint8_t *bins, int nx, int ny, int nz, int B,
             int64_t nvox = 0, acc[7];
             while (it < max_iter) {
                 ko_ab_win w;
-                if (!ko_ab_setup(&w, x, H)) break;
+                if (!ko_ab_setup(&w, x, H, dim)) break;
                 const int64_t K = ko_ab_pass(bins, nx, ny, nz, B, &w, AB_HIST, NULL, P, NULL, &nvox);
                 if (K == 0) break;
                 ko_ab_weights(P, K, B, wf);
@@ -877,7 +883,7 @@ void ko_abmsod(const uint8_t *bins, int nx, int ny, int nz, int B,
                 }
                 /* 3. histogram and weights at x' */
                 ko_ab_win w2;
-                if (!ko_ab_setup(&w2, xn, H)) break;
+                if (!ko_ab_setup(&w2, xn, H, dim)) break;
                 const int64_t K2 = ko_ab_pass(bins, nx, ny, nz, B, &w2, AB_HIST, NULL, P, NULL, &nvox);
                 ++it;
                 if (K2 == 0) break;
@@ -930,8 +936,9 @@ void ko_abmsod(const uint8_t *bins, int nx, int ny, int nz, int B,
 void ko_ab_window_check(const double x[3], const double H[6], int64_t out[2])
 {
     ko_ab_win w;
+    const int dim[3] = {1 << 20, 1 << 20, 1 << 20};
     out[0] = out[1] = 0;
-    if (!ko_ab_setup(&w, x, H)) return;
+    if (!ko_ab_setup(&w, x, H, dim)) return;
     const float *h = w.h;
     for (int sz = w.lo[2]; sz <= w.hi[2]; ++sz)
         for (int sy = w.lo[1]; sy <= w.hi[1]; ++sy) {

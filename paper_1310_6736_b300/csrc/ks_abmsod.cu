@@ -1,14 +1,17 @@
 // Adaptive-bandwidth mean shift (ABMSOD; Sec. 2.3, Alg. 2, Eq. 7) towards
 // the uniform target pmf HQ_b = 1/B.
 //
-// One warp per (seed, r) item, drawn from a persistent ticket queue with
-// the largest starting radius first.  An iteration makes four passes over
-// the voxels of the current ellipsoid { s : (s-x)^T H^-1 (s-x) <= 1 }:
+// Items (seed, r) come from two persistent ticket queues, largest starting
+// radius first: items with r >= r_team are taken by a whole block (8 warps
+// share every pass, the first warp does the per-item steps), the others by
+// one warp each.  An iteration makes four passes over the voxels of the
+// current ellipsoid { s : (s-x)^T H^-1 (s-x) <= 1 }:
 //   1. kernel histogram at (x, H) -> w_b = sqrt(HQ_b / HP_b)
 //   2. Eq. 6 sums  sum k w o, sum k w            -> x'
 //   3. kernel histogram at (x', H) -> w'_b, rho = sum_b sqrt(HQ_b HP'_b)
 //   4. Eq. 7 sums  sum w' o o^T, sum w'         -> H' = 5 (M / sum w' + I/12)
-// A pass takes the bounding box's x-rows 32 at a time: lane j finds row j's
+// A pass takes the bounding box's x-rows 32 at a time (the warps of a team
+// take every T-th batch): lane j finds row j's
 // span (the root interval of d <= 1 + 1/16 along x), a warp scan packs the
 // spans end to end, and the lanes then walk the packed voxels 32 at a time;
 // each lane finds its row from a 32-bit mask of the row starts in its step
@@ -68,6 +71,26 @@ __device__ __forceinline__ int64_t ab_q(float y) {
     return __float2ll_rn(y);
 }
 
+// Conversions between small integers (|i| < 2^21) and binary32 through the
+// same bit pattern (the conversion instructions issue at a small fraction of
+// the FP32 rate on this part): the float 1.5 * 2^23 + i has the bits
+// 0x4B400000 + i, and subtracting 1.5 * 2^23 from it is exact.
+__device__ __forceinline__ float ab_i2f(int i) {
+    return __fsub_rn(__int_as_float(0x4B400000 + i), 12582912.0f);
+}
+__device__ __forceinline__ int ab_ceil(float y) {
+    const float m = __fadd_rn(y, 12582912.0f);   // rint(y) + 1.5 * 2^23
+    int r = __float_as_int(m) - 0x4B400000;
+    if (__fsub_rn(m, 12582912.0f) < y) ++r;
+    return r;
+}
+__device__ __forceinline__ int ab_floor(float y) {
+    const float m = __fadd_rn(y, 12582912.0f);
+    int r = __float_as_int(m) - 0x4B400000;
+    if (__fsub_rn(m, 12582912.0f) > y) --r;
+    return r;
+}
+
 __device__ __forceinline__ int64_t warp_sum_i64(int64_t v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -75,11 +98,11 @@ __device__ __forceinline__ int64_t warp_sum_i64(int64_t v) {
 }
 
 // The bandwidth part of a window: H^-1 rounded to binary32 (adjugate times
-// 1/det in FP64) and the box half-widths sqrt(H_aa).  Returns false when H
-// is not positive definite (det <= 0).
+// 1/det in FP64) and the box half-widths E_a = ceil(sqrt(H_aa)) in
+// binary32.  Returns false when H is not positive definite (det <= 0).
 struct AbShape {
     float h[6];
-    double e[3];
+    int E[3];
 };
 __device__ __forceinline__ bool ab_shape(const double H[6], AbShape &sh) {
     const double a00 = H[0], a01 = H[1], a02 = H[2], a11 = H[3], a12 = H[4], a22 = H[5];
@@ -99,34 +122,33 @@ __device__ __forceinline__ bool ab_shape(const double H[6], AbShape &sh) {
     sh.h[3] = __double2float_rn(__dmul_rn(c11, inv));
     sh.h[4] = __double2float_rn(__dmul_rn(c12, inv));
     sh.h[5] = __double2float_rn(__dmul_rn(c22, inv));
-    sh.e[0] = __dsqrt_rn(a00);
-    sh.e[1] = __dsqrt_rn(a11);
-    sh.e[2] = __dsqrt_rn(a22);
+    sh.E[0] = (int)ceilf(__fsqrt_rn(__double2float_rn(a00)));
+    sh.E[1] = (int)ceilf(__fsqrt_rn(__double2float_rn(a11)));
+    sh.E[2] = (int)ceilf(__fsqrt_rn(__double2float_rn(a22)));
     return true;
 }
 
-// The centre part: floor(x), frac(x) rounded to binary32, and the voxel box
-// [lo, hi].  Returns false when the box would leave the halo (not reachable:
-// the centre stays in the volume and every diagonal entry of H is at most
-// 32^2).
-struct AbWin {
-    int n[3];
+// A window as the passes read it: H^-1, floor(x), frac(x) rounded to
+// binary32, and the voxel box [floor(x) - E, floor(x) + E] clipped to the
+// volume (voxels outside it are not counted).
+struct AbWinS {
+    float h[6];
     float f[3];
+    int n[3];
     int lo[3], hi[3];
 };
-__device__ __forceinline__ bool ab_place(const double x[3], const AbShape &sh, const int dim[3],
-                                         AbWin &w) {
-    bool ok = true;
+__device__ __forceinline__ void ab_place(const double x[3], const AbShape &sh, const int dim[3],
+                                         AbWinS &w) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w.h[k] = sh.h[k];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const double fl = floor(x[a]);
         w.n[a] = (int)fl;
         w.f[a] = __double2float_rn(__dsub_rn(x[a], fl));
-        w.lo[a] = (int)ceil(__dsub_rn(x[a], sh.e[a]));
-        w.hi[a] = (int)floor(__dadd_rn(x[a], sh.e[a]));
-        ok = ok && w.lo[a] >= -kHalo && w.hi[a] < dim[a] + kHalo && w.hi[a] >= w.lo[a];
+        w.lo[a] = max(w.n[a] - sh.E[a], 0);
+        w.hi[a] = min(w.n[a] + sh.E[a], dim[a] - 1);
     }
-    return ok;
 }
 
 enum AbPass { kPassHist = 0, kPassPos = 1, kPassMom = 2 };
@@ -139,40 +161,43 @@ struct AbSums {
 };
 
 // One row of a batch, in the warp's table: where its voxels start in the
-// packed order, its first voxel's byte offset from the pass base, the
-// binary32 value of its first j = s_x - floor(x_x), and its (o_y, o_z).
+// packed order, its first voxel's byte offset from the pass base, its first
+// j = s_x - floor(x_x), and its (o_y, o_z).
 struct AbRow {
     int start, off;
-    float fj, o1;
-    float o2, pad0, pad1, pad2;
+    int ja;
+    float o1, o2;
+    int pad0, pad1, pad2;
 };
 
 // One pass of the warp over the window's voxels.
 template <int PASS>
-__device__ __forceinline__ void ab_pass(const VolDesc &v, const AbShape &sh, const AbWin &w,
-                                        uint32_t *col, const float *wf, AbRow *tab, int lane,
+__device__ __forceinline__ void ab_pass(const VolDesc &v, const AbWinS &w, uint32_t *col,
+                                        const float *wf, AbRow *tab, int lane, int wt, int T,
                                         AbSums &acc) {
 #pragma unroll
     for (int k = 0; k < 7; ++k) acc.s[k] = 0;
-    const float h0 = sh.h[0], h1 = sh.h[1], h2 = sh.h[2], h3 = sh.h[3], h4 = sh.h[4],
-                h5 = sh.h[5];
+    const float h0 = w.h[0], h1 = w.h[1], h2 = w.h[2], h3 = w.h[3], h4 = w.h[4], h5 = w.h[5];
     const float f0 = w.f[0], f1 = w.f[1], f2 = w.f[2];
     const int e1 = w.hi[1] - w.lo[1] + 1;
     const int nrows = e1 * (w.hi[2] - w.lo[2] + 1);
-    const float jlo = (float)(w.lo[0] - w.n[0]), jhi = (float)(w.hi[0] - w.n[0]);
+    const float jlo = ab_i2f(w.lo[0] - w.n[0]), jhi = ab_i2f(w.hi[0] - w.n[0]);
+    const float ih0 = __frcp_rn(h0);
     const int pitch = (int)v.pitch, plane = (int)v.plane;
     // byte offsets below are relative to voxel (n_x, lo_y, lo_z)
     const uint8_t *base = v.base + (int64_t)w.lo[2] * v.plane + (int64_t)w.lo[1] * v.pitch + w.n[0];
-    // lane's row (iy, iz) and the 32-row step
-    int iy = lane % e1, iz = lane / e1;
-    const int dy = 32 % e1, dz = 32 / e1;
+    // lane's row (iy, iz) and the step of 32 T rows (this warp takes every
+    // T-th batch of 32 rows)
+    const int row0 = wt * 32 + lane;
+    int iy = row0 % e1, iz = row0 / e1;
+    const int dy = (32 * T) % e1, dz = (32 * T) / e1;
     const unsigned lt = (1u << lane) - 1u;
-    for (int rb = 0; rb < nrows; rb += 32) {
+    for (int rb = wt * 32; rb < nrows; rb += 32 * T) {
         int len = 0, ja = 0, off = 0;
         float o1 = 0.0f, o2 = 0.0f;
         if (rb + lane < nrows) {
-            o1 = __fsub_rn((float)(w.lo[1] + iy - w.n[1]), f1);
-            o2 = __fsub_rn((float)(w.lo[2] + iz - w.n[2]), f2);
+            o1 = __fsub_rn(ab_i2f(w.lo[1] + iy - w.n[1]), f1);
+            o2 = __fsub_rn(ab_i2f(w.lo[2] + iz - w.n[2]), f2);
             const float beta = __fadd_rn(__fmul_rn(h1, o1), __fmul_rn(h2, o2));
             const float gamma = __fadd_rn(
                 __fmul_rn(__fadd_rn(__fmul_rn(h3, o1), __fmul_rn(__fmul_rn(2.0f, h4), o2)), o1),
@@ -181,13 +206,18 @@ __device__ __forceinline__ void ab_pass(const VolDesc &v, const AbShape &sh, con
                 __fsub_rn(__fmul_rn(beta, beta), __fmul_rn(h0, __fsub_rn(gamma, kSlack)));
             if (disc >= 0.0f) {
                 const float sq = __fsqrt_rn(disc);
-                const float ulo = __fdiv_rn(__fsub_rn(-beta, sq), h0);
-                const float uhi = __fdiv_rn(__fsub_rn(sq, beta), h0);
-                const float a = fmaxf(ceilf(__fadd_rn(ulo, f0)), jlo);
-                const float b = fminf(floorf(__fadd_rn(uhi, f0)), jhi);
+                // ceil / floor of the clamped roots (equal to the clamped
+                // ceil / floor whenever the span is not empty)
+                const float ya = fminf(
+                    fmaxf(__fadd_rn(__fmul_rn(__fsub_rn(-beta, sq), ih0), f0), jlo),
+                    __fadd_rn(jhi, 1.0f));
+                const float yb = fmaxf(
+                    fminf(__fadd_rn(__fmul_rn(__fsub_rn(sq, beta), ih0), f0), jhi),
+                    __fsub_rn(jlo, 1.0f));
+                const int a = ab_ceil(ya), b = ab_floor(yb);
                 if (a <= b) {
-                    ja = (int)a;
-                    len = (int)b - ja + 1;
+                    ja = a;
+                    len = b - a + 1;
                     off = iz * plane + iy * pitch + ja;
                 }
             }
@@ -212,12 +242,15 @@ __device__ __forceinline__ void ab_pass(const VolDesc &v, const AbShape &sh, con
             AbRow &rw = tab[__popc(nonempty & lt)];
             rw.start = start;
             rw.off = off;
-            rw.fj = (float)ja;
+            rw.ja = ja;
             rw.o1 = o1;
             rw.o2 = o2;
         }
         __syncwarp();
         int before = 0;   // nonempty rows that start before this step
+        // int32 partial sums of the batch: a batch has at most 32 rows of at
+        // most 65 voxels, so a lane adds at most 65 terms below 2^22 here
+        int a32[7] = {0, 0, 0, 0, 0, 0, 0};
         for (int p0 = 0; p0 < total; p0 += 32) {
             const unsigned m = __reduce_or_sync(
                 0xffffffffu, (len > 0 && start >= p0 && start < p0 + 32) ? 1u << (start - p0) : 0u);
@@ -228,7 +261,7 @@ __device__ __forceinline__ void ab_pass(const VolDesc &v, const AbShape &sh, con
                 const int kk = p - rw.start;
                 const int b = __ldg(base + rw.off + kk);
                 if (b) {
-                    const float o0 = __fsub_rn(__fadd_rn(rw.fj, (float)kk), f0);
+                    const float o0 = __fsub_rn(ab_i2f(rw.ja + kk), f0);
                     const float r1 = rw.o1, r2 = rw.o2;
                     const float u0 = __fadd_rn(__fadd_rn(__fmul_rn(h0, o0), __fmul_rn(h1, r1)),
                                                __fmul_rn(h2, r2));
@@ -239,30 +272,63 @@ __device__ __forceinline__ void ab_pass(const VolDesc &v, const AbShape &sh, con
                     const float d = __fadd_rn(__fadd_rn(__fmul_rn(o0, u0), __fmul_rn(r1, u1)),
                                               __fmul_rn(r2, u2));
                     if (d >= 0.0f && d <= 1.0f) {
+                        // |o_a| <= 33, so the terms stay below 2^22 when
+                        // k w < 30 (position) or w < 15 (moments); heavier
+                        // rare-bin terms go straight to the int64 sums
                         if (PASS == kPassHist) {
                             col[(b - 1) * 32] += (uint32_t)ab_rint_small(__fmul_rn(ab_kernel(d), kQK));
-                            acc.s[0] += 1;
+                            a32[0] += 1;
                         } else if (PASS == kPassPos) {
                             const float tk = __fmul_rn(ab_kernel(d), wf[b - 1]);
-                            acc.s[0] += ab_q(__fmul_rn(__fmul_rn(tk, o0), kQX));
-                            acc.s[1] += ab_q(__fmul_rn(__fmul_rn(tk, r1), kQX));
-                            acc.s[2] += ab_q(__fmul_rn(__fmul_rn(tk, r2), kQX));
-                            acc.s[3] += ab_q(__fmul_rn(tk, kQX));
+                            const float y0 = __fmul_rn(__fmul_rn(tk, o0), kQX);
+                            const float y1 = __fmul_rn(__fmul_rn(tk, r1), kQX);
+                            const float y2 = __fmul_rn(__fmul_rn(tk, r2), kQX);
+                            const float y3 = __fmul_rn(tk, kQX);
+                            if (tk < 30.0f) {
+                                a32[0] += ab_rint_small(y0);
+                                a32[1] += ab_rint_small(y1);
+                                a32[2] += ab_rint_small(y2);
+                                a32[3] += ab_rint_small(y3);
+                            } else {
+                                acc.s[0] += ab_q(y0);
+                                acc.s[1] += ab_q(y1);
+                                acc.s[2] += ab_q(y2);
+                                acc.s[3] += ab_q(y3);
+                            }
                         } else {
                             const float tw = wf[b - 1];
-                            acc.s[0] += ab_q(__fmul_rn(__fmul_rn(tw, __fmul_rn(o0, o0)), kQH));
-                            acc.s[1] += ab_q(__fmul_rn(__fmul_rn(tw, __fmul_rn(o0, r1)), kQH));
-                            acc.s[2] += ab_q(__fmul_rn(__fmul_rn(tw, __fmul_rn(o0, r2)), kQH));
-                            acc.s[3] += ab_q(__fmul_rn(__fmul_rn(tw, __fmul_rn(r1, r1)), kQH));
-                            acc.s[4] += ab_q(__fmul_rn(__fmul_rn(tw, __fmul_rn(r1, r2)), kQH));
-                            acc.s[5] += ab_q(__fmul_rn(__fmul_rn(tw, __fmul_rn(r2, r2)), kQH));
-                            acc.s[6] += ab_q(__fmul_rn(tw, kQX));
+                            const float y0 = __fmul_rn(__fmul_rn(tw, __fmul_rn(o0, o0)), kQH);
+                            const float y1 = __fmul_rn(__fmul_rn(tw, __fmul_rn(o0, r1)), kQH);
+                            const float y2 = __fmul_rn(__fmul_rn(tw, __fmul_rn(o0, r2)), kQH);
+                            const float y3 = __fmul_rn(__fmul_rn(tw, __fmul_rn(r1, r1)), kQH);
+                            const float y4 = __fmul_rn(__fmul_rn(tw, __fmul_rn(r1, r2)), kQH);
+                            const float y5 = __fmul_rn(__fmul_rn(tw, __fmul_rn(r2, r2)), kQH);
+                            const float y6 = __fmul_rn(tw, kQX);
+                            if (tw < 15.0f) {
+                                a32[0] += ab_rint_small(y0);
+                                a32[1] += ab_rint_small(y1);
+                                a32[2] += ab_rint_small(y2);
+                                a32[3] += ab_rint_small(y3);
+                                a32[4] += ab_rint_small(y4);
+                                a32[5] += ab_rint_small(y5);
+                                a32[6] += ab_rint_small(y6);
+                            } else {
+                                acc.s[0] += ab_q(y0);
+                                acc.s[1] += ab_q(y1);
+                                acc.s[2] += ab_q(y2);
+                                acc.s[3] += ab_q(y3);
+                                acc.s[4] += ab_q(y4);
+                                acc.s[5] += ab_q(y5);
+                                acc.s[6] += ab_q(y6);
+                            }
                         }
                     }
                 }
             }
             before += __popc(m);
         }
+#pragma unroll
+        for (int k = 0; k < 7; ++k) acc.s[k] += a32[k];
         __syncwarp();   // the table is rewritten by the next batch
     }
     if (PASS != kPassHist) {
@@ -271,18 +337,54 @@ __device__ __forceinline__ void ab_pass(const VolDesc &v, const AbShape &sh, con
     }
 }
 
-// Histogram pass + per-bin step (adds this lane's window voxels to nvox):
-// P_b from the lane columns (read and cleared), K = sum P_b, weights
-// wf_b = (float) sqrt(K / (B P_b)) into shared memory, and, when want_rho,
-// rho = (sum_b sqrt(P_b)) / sqrt(B K) with the bins paired (b, b + 32) and
-// then summed by a butterfly (the pairwise tree of the definition).
-// Returns K.
-__device__ __forceinline__ int64_t ab_hist(const VolDesc &v, const AbShape &sh, const AbWin &w,
-                                           uint32_t *cols, float *wf, AbRow *tab, int lane,
-                                           int B, bool want_rho, double &rho, int64_t &nvox) {
+struct AbJob {
+    VolDesc vol;
+    const int32_t *seeds;
+    int64_t n_seeds;
+    int r_min, S, max_iter;
+    int S_team;                    // radii taken by a whole block: ri >= S - S_team
+    ks_abmsod_result *out;
+    unsigned long long *tickets;   // [0]: block items, [1]: warp items
+    int *status;
+};
+
+// Item state (the team leader's copy is the team's).
+struct AbState {
+    double x[3], H[6];     // current centre and bandwidth
+    double xn[3], Hn[6];   // this iteration's update
+    double xo[3], Ho[6];   // best so far
+    double best;
+};
+
+// Per-warp shared memory.
+struct __align__(16) AbWarpMem {
+    AbRow tab[32];         // this warp's row table
+    AbState st;            // item state (leader's copy)
+    AbWinS win;            // current window (leader's copy)
+    int flag;              // leader -> team: 0 go on, 1 leave the loop, 2 stopped
+    int pad;
+    int64_t nv;            // this warp's window voxels of the item
+    int64_t P[kMaxBins];   // this warp's per-bin sums of the last histogram
+    int64_t red[8];        // this warp's pass sums
+    float wf[kMaxBins];    // weights (leader's copy)
+};
+
+template <int T>
+__device__ __forceinline__ void team_sync() {
+    if (T == 1)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+
+// Histogram pass of one warp: the lane columns are summed (and cleared)
+// into mine->P[b] for bins b = lane, lane + 32; returns this lane's window
+// voxels.
+__device__ __forceinline__ int64_t ab_hist_part(const VolDesc &v, const AbWinS &w, uint32_t *cols,
+                                                AbRow *tab, int lane, int wt, int T, int B,
+                                                AbWarpMem *mine) {
     AbSums cnt;
-    ab_pass<kPassHist>(v, sh, w, cols + lane, nullptr, tab, lane, cnt);
-    nvox += cnt.s[0];
+    ab_pass<kPassHist>(v, w, cols + lane, nullptr, tab, lane, wt, T, cnt);
     __syncwarp();
     int64_t P0 = 0, P1 = 0;
     if (lane < B) {
@@ -292,6 +394,7 @@ __device__ __forceinline__ int64_t ab_hist(const VolDesc &v, const AbShape &sh, 
             P0 += c[j];
             c[j] = 0u;
         }
+        mine->P[lane] = P0;
     }
     if (lane + 32 < B) {
         uint32_t *c = cols + (lane + 32) * 32;
@@ -300,137 +403,161 @@ __device__ __forceinline__ int64_t ab_hist(const VolDesc &v, const AbShape &sh, 
             P1 += c[j];
             c[j] = 0u;
         }
+        mine->P[lane + 32] = P1;
+    }
+    return cnt.s[0];
+}
+
+// Leader: team totals P_b (bins lane, lane + 32), K, binary32 weights
+// wf_b = sqrt(K / (B P_b)) into lead->wf and, when want_rho, rho =
+// (sum_b sqrt(P_b)) / sqrt(B K) with the bins paired (b, b + 32) and then
+// summed by a butterfly (the pairwise tree of the definition).  Returns K.
+__device__ __forceinline__ int64_t ab_bins(AbWarpMem *team, int T, int lane, int B, bool want_rho,
+                                           double &rho) {
+    AbWarpMem *lead = team;
+    int64_t P0 = 0, P1 = 0;
+    for (int t = 0; t < T; ++t) {
+        if (lane < B) P0 += team[t].P[lane];
+        if (lane + 32 < B) P1 += team[t].P[lane + 32];
     }
     const int64_t K = warp_sum_i64(P0 + P1);
     rho = 0.0;
     if (K > 0) {
-        const double dK = (double)K, dB = (double)B;
+        const float Kf = __ll2float_rn(K), Bf = (float)B;
         if (lane < B)
-            wf[lane] = P0 > 0 ? __double2float_rn(__dsqrt_rn(__ddiv_rn(dK, __dmul_rn(dB, (double)P0))))
-                              : 0.0f;
+            lead->wf[lane] =
+                P0 > 0 ? __fsqrt_rn(__fdiv_rn(Kf, __fmul_rn(Bf, __ll2float_rn(P0)))) : 0.0f;
         if (lane + 32 < B)
-            wf[lane + 32] =
-                P1 > 0 ? __double2float_rn(__dsqrt_rn(__ddiv_rn(dK, __dmul_rn(dB, (double)P1))))
-                       : 0.0f;
+            lead->wf[lane + 32] =
+                P1 > 0 ? __fsqrt_rn(__fdiv_rn(Kf, __fmul_rn(Bf, __ll2float_rn(P1)))) : 0.0f;
         if (want_rho) {
             double t = __dadd_rn(P0 > 0 ? __dsqrt_rn((double)P0) : 0.0,
                                  P1 > 0 ? __dsqrt_rn((double)P1) : 0.0);
 #pragma unroll
             for (int m = 16; m >= 1; m >>= 1) t = __dadd_rn(t, __shfl_xor_sync(0xffffffffu, t, m));
-            rho = __ddiv_rn(t, __dsqrt_rn(__dmul_rn(dB, dK)));
+            rho = __ddiv_rn(t, __dsqrt_rn(__dmul_rn((double)B, (double)K)));
         }
     }
-    __syncwarp();
     return K;
 }
 
-struct AbJob {
-    VolDesc vol;
-    const int32_t *seeds;
-    int64_t n_seeds;
-    int r_min, S, max_iter;
-    ks_abmsod_result *out;
-    unsigned long long *ticket;
-    int *status;
-};
+// Leader: write a window into lead->win (lane 0).
+__device__ __forceinline__ void ab_publish(AbWarpMem *lead, const AbWinS &w, int lane) {
+    if (lane == 0) lead->win = w;
+}
 
-// Per-warp item state in shared memory (keeps the FP64 state out of the
-// registers of the voxel passes).  Every lane writes the same values.
-struct AbState {
-    double x[3], H[6];     // current centre and bandwidth
-    double xn[3], Hn[6];   // this iteration's update
-    double xo[3], Ho[6];   // best so far
-    double best;
-};
-
-constexpr size_t kAbFixedBytes = kAbWarps * (sizeof(AbState) + 32 * sizeof(AbRow));
-
-__global__ void __launch_bounds__(kAbWarps * 32, 4) k_abmsod(const AbJob J) {
-    extern __shared__ __align__(16) uint32_t ab_smem[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+// One item (seed si, radius index ri) by a team of T warps; wt = this
+// warp's index in the team, team = the team's first warp memory.
+template <int T>
+__device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWarpMem *team,
+                                     uint32_t *cols, int wt, int lane) {
+    AbWarpMem *lead = team, *mine = team + wt;
+    const bool leader = wt == 0;
     const int B = J.vol.B;
-    // per block: the warps' states, their row tables, then per warp B x 32
-    // lane columns and B weights
-    AbState *stt = reinterpret_cast<AbState *>(ab_smem) + wid;
-    AbRow *tab = reinterpret_cast<AbRow *>(ab_smem + kAbWarps * sizeof(AbState) / 4) + wid * 32;
-    uint32_t *cols = ab_smem + kAbFixedBytes / 4 + (size_t)wid * (B * 32 + B);
-    float *wf = reinterpret_cast<float *>(cols + B * 32);
-    for (int i = lane; i < B * 32; i += 32) cols[i] = 0u;
-    __syncwarp();
+    const int r = J.r_min + ri;
     const int dim[3] = {J.vol.nx, J.vol.ny, J.vol.nz};
-    const int64_t n_items = J.n_seeds * J.S;
-    for (;;) {
-        unsigned long long tk = 0;
-        if (lane == 0) tk = atomicAdd(J.ticket, 1ull);
-        tk = __shfl_sync(0xffffffffu, tk, 0);
-        if ((int64_t)tk >= n_items) break;
-        // largest radius first
-        const int ri = J.S - 1 - (int)((int64_t)tk / J.n_seeds);
-        const int64_t si = (int64_t)tk % J.n_seeds;
-        const int r = J.r_min + ri;
+    AbState *st = &lead->st;
+    if (leader) {
         const double r2 = (double)(r * r);
         if (lane < 3) {
             const double c = (double)J.seeds[3 * si + lane];
-            stt->x[lane] = c;
-            stt->xo[lane] = c;
+            st->x[lane] = c;
+            st->xo[lane] = c;
         }
         if (lane < 6) {
             const double h = (lane == 0 || lane == 3 || lane == 5) ? r2 : 0.0;
-            stt->H[lane] = h;
-            stt->Ho[lane] = h;
+            st->H[lane] = h;
+            st->Ho[lane] = h;
         }
-        if (lane == 0) stt->best = 0.0;
-        __syncwarp();
-        int it = 0, stopped = 0;
-        int64_t nvox = 0;
-        while (it < J.max_iter) {
-            AbShape sh;
-            if (!ab_shape(stt->H, sh)) break;
-            AbWin w;
-            if (!ab_place(stt->x, sh, dim, w)) {
-                if (lane == 0) atomicOr(J.status, kStatusBadInput);
-                break;
+        if (lane == 0) st->best = 0.0;
+    }
+    int64_t nvl = 0;
+    int it = 0, stopped = 0;
+    AbShape sh;            // leader only
+    double rho = 0.0;      // leader only
+    while (it < J.max_iter) {
+        // window at (x, H)
+        if (leader) {
+            __syncwarp();
+            const bool ok = ab_shape(st->H, sh);
+            if (ok) {
+                AbWinS w;
+                ab_place(st->x, sh, dim, w);
+                ab_publish(lead, w, lane);
             }
-            double rho;
-            const int64_t K = ab_hist(J.vol, sh, w, cols, wf, tab, lane, B, false, rho, nvox);
-            if (K == 0) break;
-            {
-                AbSums sp;
-                ab_pass<kPassPos>(J.vol, sh, w, nullptr, wf, tab, lane, sp);
-                if (lane < 3) {
-                    const int64_t num = lane == 0 ? sp.s[0] : (lane == 1 ? sp.s[1] : sp.s[2]);
-                    const int dm = lane == 0 ? dim[0] : (lane == 1 ? dim[1] : dim[2]);
-                    const double dl =
-                        sp.s[3] > 0 ? __ddiv_rn((double)num, (double)sp.s[3]) : 0.0;
-                    double vv = __dadd_rn(stt->x[lane], dl);
-                    if (vv < 0.0) vv = 0.0;
-                    if (vv > (double)(dm - 1)) vv = (double)(dm - 1);
-                    stt->xn[lane] = vv;
+            if (lane == 0) lead->flag = ok ? 0 : 1;
+        }
+        team_sync<T>();
+        if (lead->flag) break;
+        AbWinS w = lead->win;
+        nvl += ab_hist_part(J.vol, w, cols, mine->tab, lane, wt, T, B, mine);
+        team_sync<T>();
+        if (leader) {
+            const int64_t K = ab_bins(team, T, lane, B, false, rho);
+            if (lane == 0) lead->flag = K == 0 ? 1 : 0;
+        }
+        team_sync<T>();
+        if (lead->flag) break;
+        {
+            AbSums sp;
+            ab_pass<kPassPos>(J.vol, w, nullptr, lead->wf, mine->tab, lane, wt, T, sp);
+            if (lane < 4) mine->red[lane] = lane == 0 ? sp.s[0] : lane == 1 ? sp.s[1]
+                                                      : lane == 2 ? sp.s[2] : sp.s[3];
+        }
+        team_sync<T>();
+        if (leader) {
+            if (lane < 3) {
+                int64_t num = 0, den = 0;
+                for (int t = 0; t < T; ++t) {
+                    num += team[t].red[lane];
+                    den += team[t].red[3];
                 }
-            }
-            __syncwarp();   // xn written; wf is rewritten by the next histogram
-            if (!ab_place(stt->xn, sh, dim, w)) {
-                if (lane == 0) atomicOr(J.status, kStatusBadInput);
-                break;
-            }
-            const int64_t K2 = ab_hist(J.vol, sh, w, cols, wf, tab, lane, B, true, rho, nvox);
-            ++it;
-            if (K2 == 0) break;
-            {
-                AbSums sm;
-                ab_pass<kPassMom>(J.vol, sh, w, nullptr, wf, tab, lane, sm);
-                int64_t mk = sm.s[0];
-#pragma unroll
-                for (int k = 1; k < 6; ++k) mk = lane == k ? sm.s[k] : mk;
-                if (lane < 6)
-                    stt->Hn[lane] = sm.s[6] > 0 ? __ddiv_rn(__dmul_rn(80.0, (double)mk),
-                                                            (double)sm.s[6])
-                                                : stt->H[lane];
+                const int dm = lane == 0 ? dim[0] : (lane == 1 ? dim[1] : dim[2]);
+                const double dl = den > 0 ? __ddiv_rn((double)num, (double)den) : 0.0;
+                double vv = __dadd_rn(st->x[lane], dl);
+                if (vv < 0.0) vv = 0.0;
+                if (vv > (double)(dm - 1)) vv = (double)(dm - 1);
+                st->xn[lane] = vv;
             }
             __syncwarp();
-            // regularise H' (lane 0)
+            AbWinS w2;
+            ab_place(st->xn, sh, dim, w2);
+            ab_publish(lead, w2, lane);
+        }
+        team_sync<T>();
+        w = lead->win;
+        nvl += ab_hist_part(J.vol, w, cols, mine->tab, lane, wt, T, B, mine);
+        team_sync<T>();
+        ++it;
+        if (leader) {
+            const int64_t K2 = ab_bins(team, T, lane, B, true, rho);
+            if (lane == 0) lead->flag = K2 == 0 ? 1 : 0;
+        }
+        team_sync<T>();
+        if (lead->flag) break;
+        {
+            AbSums sm;
+            ab_pass<kPassMom>(J.vol, w, nullptr, lead->wf, mine->tab, lane, wt, T, sm);
+            int64_t mk = sm.s[0];
+#pragma unroll
+            for (int k = 1; k < 7; ++k) mk = lane == k ? sm.s[k] : mk;
+            if (lane < 7) mine->red[lane] = mk;
+        }
+        team_sync<T>();
+        if (leader) {
+            if (lane < 6) {
+                int64_t mk = 0, ws = 0;
+                for (int t = 0; t < T; ++t) {
+                    mk += team[t].red[lane];
+                    ws += team[t].red[6];
+                }
+                st->Hn[lane] =
+                    ws > 0 ? __ddiv_rn(__dmul_rn(80.0, (double)mk), (double)ws) : st->H[lane];
+            }
+            __syncwarp();
             if (lane == 0) {
-                double *Hn = stt->Hn;
+                // regularise H'
+                double *Hn = st->Hn;
                 double m = 0.0;
                 const int dg[3] = {0, 3, 5};
 #pragma unroll
@@ -447,50 +574,93 @@ __global__ void __launch_bounds__(kAbWarps * 32, 4) k_abmsod(const AbJob J) {
                     for (int a = 0; a < 3; ++a)
                         if (Hn[dg[a]] > kHmax) Hn[dg[a]] = kHmax;
                 }
+                // best so far; stop at a fall of rho
+                const double delta = __dsub_rn(st->best, rho);
+                if (rho > st->best) {
+                    st->best = rho;
+                    for (int a = 0; a < 3; ++a) st->xo[a] = st->xn[a];
+                    for (int k = 0; k < 6; ++k) st->Ho[k] = Hn[k];
+                }
+                if (delta > 0.0) {
+                    lead->flag = 2;
+                } else {
+                    lead->flag = 0;
+                    for (int a = 0; a < 3; ++a) st->x[a] = st->xn[a];
+                    for (int k = 0; k < 6; ++k) st->H[k] = Hn[k];
+                }
             }
-            __syncwarp();
-            const double best = stt->best;
-            const double delta = __dsub_rn(best, rho);
-            const bool better = rho > best;
-            __syncwarp();
-            if (better) {
-                if (lane < 3) stt->xo[lane] = stt->xn[lane];
-                if (lane < 6) stt->Ho[lane] = stt->Hn[lane];
-                if (lane == 0) stt->best = rho;
-            }
-            if (delta > 0.0) {
-                stopped = 1;
-                __syncwarp();
-                break;
-            }
-            if (lane < 3) stt->x[lane] = stt->xn[lane];
-            if (lane < 6) stt->H[lane] = stt->Hn[lane];
-            __syncwarp();
         }
-        __syncwarp();
-        nvox = warp_sum_i64(nvox);
+        team_sync<T>();
+        if (lead->flag) {
+            stopped = 1;
+            break;
+        }
+    }
+    nvl = warp_sum_i64(nvl);
+    if (lane == 0) mine->nv = nvl;
+    team_sync<T>();
+    if (leader) {
+        int64_t nv = 0;
+        for (int t = 0; t < T; ++t) nv += team[t].nv;
         ks_abmsod_result &o = J.out[si * J.S + ri];
-        if (lane < 3) o.x[lane] = stt->xo[lane];
-        if (lane < 6) o.H[lane] = stt->Ho[lane];
+        if (lane < 3) o.x[lane] = st->xo[lane];
+        if (lane < 6) o.H[lane] = st->Ho[lane];
         if (lane == 0) {
-            o.rho = stt->best;
+            o.rho = st->best;
             o.seed = (int32_t)si;
             o.r = r;
             o.iters = it;
             o.stopped = stopped;
-            o.voxels = nvox;
+            o.voxels = nv;
         }
-        __syncwarp();
+    }
+    team_sync<T>();   // the team's memory is reused by the next item
+}
+
+__global__ void __launch_bounds__(kAbWarps * 32, 4) k_abmsod(const AbJob J) {
+    extern __shared__ __align__(16) uint8_t ab_smem[];
+    __shared__ unsigned long long s_ticket;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int B = J.vol.B;
+    // per block: the warps' memories, then per warp B x 32 lane columns
+    AbWarpMem *mems = reinterpret_cast<AbWarpMem *>(ab_smem);
+    uint32_t *cols = reinterpret_cast<uint32_t *>(ab_smem + kAbWarps * sizeof(AbWarpMem)) +
+                     (size_t)wid * B * 32;
+    for (int i = lane; i < B * 32; i += 32) cols[i] = 0u;
+    __syncwarp();
+    const int64_t ns = J.n_seeds;
+    // block items: radii index S - S_team .. S - 1, largest first
+    const int64_t n_team = ns * J.S_team;
+    for (;;) {
+        if (threadIdx.x == 0) s_ticket = atomicAdd(&J.tickets[0], 1ull);
+        __syncthreads();
+        const int64_t tk = (int64_t)s_ticket;
+        __syncthreads();
+        if (tk >= n_team) break;
+        ab_item<kAbWarps>(J, tk % ns, J.S - 1 - (int)(tk / ns), mems, cols, wid, lane);
+    }
+    // warp items: radii index 0 .. S - S_team - 1, largest first
+    const int S_warp = J.S - J.S_team;
+    const int64_t n_warp = ns * S_warp;
+    for (;;) {
+        unsigned long long tk = 0;
+        if (lane == 0) tk = atomicAdd(&J.tickets[1], 1ull);
+        tk = __shfl_sync(0xffffffffu, tk, 0);
+        if ((int64_t)tk >= n_warp) break;
+        ab_item<1>(J, (int64_t)tk % ns, S_warp - 1 - (int)((int64_t)tk / ns), mems + wid, cols, 0,
+                   lane);
     }
 }
 
 }  // namespace
 
-size_t abmsod_smem_bytes(int B) { return kAbFixedBytes + (size_t)kAbWarps * (B * 32 + B) * 4; }
+size_t abmsod_smem_bytes(int B) {
+    return kAbWarps * sizeof(AbWarpMem) + (size_t)kAbWarps * B * 32 * 4;
+}
 
 cudaError_t launch_abmsod(const LaunchCtx &lc, const VolDesc &v, const int32_t *seeds,
-                          int64_t n_seeds, int r_min, int r_max, int max_iter,
-                          ks_abmsod_result *out, unsigned long long *ticket) {
+                          int64_t n_seeds, int r_min, int r_max, int max_iter, int r_team,
+                          ks_abmsod_result *out, unsigned long long *tickets) {
     const int S = r_max - r_min + 1;
     const int64_t n_items = n_seeds * S;
     if (n_items == 0) return cudaSuccess;
@@ -504,9 +674,10 @@ cudaError_t launch_abmsod(const LaunchCtx &lc, const VolDesc &v, const int32_t *
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_abmsod, kAbWarps * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    const int64_t want = (n_items + kAbWarps - 1) / kAbWarps;
-    const int grid = (int)std::min<int64_t>(want, (int64_t)lc.num_sms * per_sm);
-    e = cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), lc.stream);
+    const int S_team = std::min(S, std::max(0, r_max - r_team + 1));
+    const int64_t want = n_seeds * S_team + (n_seeds * (S - S_team) + kAbWarps - 1) / kAbWarps;
+    const int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)lc.num_sms * per_sm);
+    e = cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned long long), lc.stream);
     if (e != cudaSuccess) return e;
     AbJob J;
     J.vol = v;
@@ -515,8 +686,9 @@ cudaError_t launch_abmsod(const LaunchCtx &lc, const VolDesc &v, const int32_t *
     J.r_min = r_min;
     J.S = S;
     J.max_iter = max_iter;
+    J.S_team = S_team;
     J.out = out;
-    J.ticket = ticket;
+    J.tickets = tickets;
     J.status = lc.d_status;
     k_abmsod<<<grid, kAbWarps * 32, smem, lc.stream>>>(J);
     return cudaGetLastError();

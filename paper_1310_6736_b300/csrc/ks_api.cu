@@ -441,6 +441,9 @@ static std::vector<DenseConfig> dense_candidates(int B, int r_max) {
 }
 
 static int g_forced_path = -1, g_forced_warps = 0, g_forced_ty = 0, g_forced_tz = 0;
+// ABMSOD: items with a starting radius >= this run on a whole block.
+constexpr int kAbmsodTeamRadius = 12;
+static int g_abmsod_team_radius = kAbmsodTeamRadius;
 
 static int launch_dense_cfg(Ctx *c, cudaStream_t s, Volume *v, int r_min, int r_max, int w_norm,
                             const DenseConfig &cfg, const DenseOut &out, int z0, int z1) {
@@ -1238,7 +1241,7 @@ int ks_abmsod(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_t *s
     ProfRec rec;
     prof_begin(c, "ks_abmsod", c->stream, &rec);
     e = launch_abmsod(c->lc(), v->desc, ds, ns, params->r_min, params->r_max, params->max_iter,
-                      dout, ticket);
+                      g_abmsod_team_radius, dout, ticket);
     prof_end(c, &rec, c->stream);
     KS_TRY_CUDA(c, e);
     if (!out_on_device)
@@ -1477,6 +1480,12 @@ int ks_selftest_wait_timeout(ks_ctx *ctx, int polls) {
 
 // Force the dense launch configuration for every context (path < 0: back
 // to the autotuner).  Returns KS_EINVAL for a shape that can never fit.
+int ks_set_abmsod_team_radius(int r_team) {
+    if (r_team > kRmax + 1) return KS_EINVAL;
+    g_abmsod_team_radius = r_team <= 0 ? kAbmsodTeamRadius : r_team;
+    return KS_OK;
+}
+
 int ks_force_dense_config(int path, int warps, int ty, int tz) {
     if (path < 0) {
         g_forced_path = -1;

@@ -166,13 +166,14 @@ cudaError_t launch_bin_f32(const LaunchCtx &lc, const float *raw, int nx, int ny
                            int bins, uint8_t *base, int64_t pitch, int64_t plane,
                            float2 *scratch, int scratch_blocks);
 
-// ks_abmsod.cu: adaptive-bandwidth mean shift, one warp per (seed, r) item
-// (item = seed * S + r - r_min), persistent over a ticket counter that the
-// launch zeroes.
+// ks_abmsod.cu: adaptive-bandwidth mean shift for every (seed, r) item
+// (record seed * S + r - r_min); items with r >= r_team run on a whole
+// block, the others on one warp each; persistent over two ticket counters
+// (tickets[0..1]) that the launch zeroes.
 size_t abmsod_smem_bytes(int B);
 cudaError_t launch_abmsod(const LaunchCtx &lc, const VolDesc &v, const int32_t *seeds,
-                          int64_t n_seeds, int r_min, int r_max, int max_iter,
-                          ks_abmsod_result *out, unsigned long long *ticket);
+                          int64_t n_seeds, int r_min, int r_max, int max_iter, int r_team,
+                          ks_abmsod_result *out, unsigned long long *tickets);
 
 // ks_dense.cu
 struct DenseConfig {

@@ -108,6 +108,7 @@ SIGNATURES = {
     "ks_dense_config": (_I, [_P, _I, _I, C.POINTER(C.c_int), C.POINTER(C.c_int),
                              C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ks_force_dense_config": (_I, [_I, _I, _I, _I]),
+    "ks_set_abmsod_team_radius": (_I, [_I]),
     "ks_bin_f32_noalloc": (_I, [_P, _I, _I, _I, _I, _P, _P]),
     "ks_selftest_wait_timeout": (_I, [_P, _I]),
 }
@@ -444,6 +445,13 @@ class Context:
         vals = [C.c_int() for _ in range(4)]
         st = lib().ks_dense_config(self.h, int(bins), int(r_max), *[C.byref(v) for v in vals])
         return None if st != KS_OK else tuple(v.value for v in vals)
+
+
+def set_abmsod_team_radius(r_team):
+    """Items with starting radius >= r_team run on a whole block (0: default)."""
+    st = lib().ks_set_abmsod_team_radius(int(r_team))
+    if st:
+        raise KsError(st, "ks_set_abmsod_team_radius")
 
 
 def force_dense_config(path, warps=0, ty=0, tz=0):

@@ -636,3 +636,22 @@ def test_abmsod_device_output_equals_host(ctx, ks_mod):
     assert ctx.abmsod(v, p, out=d) == len(a)
     ctx.release_volume(v)
     assert np.array_equal(d.cpu().numpy().view(ks.AB_RESULT), a)
+
+
+def test_abmsod_team_split_does_not_change_results(ctx, ko, ks_mod):
+    """Every item on one warp, every item on a whole block, and the default
+    split give the same records (and equal the oracle)."""
+    ks = ks_mod
+    w = synth.workload("spheres48")
+    grid = ko.seed_grid(w.dims, w.stride)[::5].copy()
+    outs = []
+    try:
+        for rt in (33, 1, 6, 0):
+            ks.set_abmsod_team_radius(rt)
+            outs.append(_ab_vs_oracle(ctx, ko, ks, w, seeds=grid)[0])
+    finally:
+        ks.set_abmsod_team_radius(0)
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    with pytest.raises(ks.KsError):
+        ks.set_abmsod_team_radius(34)
