@@ -374,9 +374,11 @@ int ks_force_dense_config(int path, int warps, int tile_y, int tile_z);
 
 /* ABMSOD work split for every context of the process: items whose starting
  * radius is at least r_team run on a whole thread block (8 warps share each
- * window pass), smaller ones on one warp each.  r_team <= 0 restores the
- * default (12); r_team > 32 puts every item on one warp.  Results do not
- * depend on the split.  KS_EINVAL: r_team > 33. */
+ * window pass), smaller ones on one warp each; r_team > 32 puts every item
+ * on one warp.  r_team <= 0 restores the default, decided per call: r_team
+ * = 12 when the call has fewer than 4 items per resident warp, else every
+ * item on one warp.  Results do not depend on the split.  KS_EINVAL:
+ * r_team > 33. */
 int ks_set_abmsod_team_radius(int r_team);
 
 /* Failure-detection self-test: one thread waits on a device barrier that

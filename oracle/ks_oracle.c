@@ -670,9 +670,10 @@ int ko_max_threads(void)
 /* offsets (o_y, o_z), d as a function of o_x is the quadratic              */
 /* h00 o_x^2 + 2 beta o_x + gamma, and the row's span is where it is at     */
 /* most 1 + 1/16 (binary32 root formula, the division by h00 done as a      */
-/* product with 1/h00); a voxel of the span is in the                       */
-/* window when 0 <= d(s) <= 1 with d evaluated in binary32 (d < 0, or not a */
-/* number, arises only from rounding and is left out).  The rows are those  */
+/* product with 1/h00); a voxel of the span is in the window when           */
+/* -1/16 <= d <= 1, d evaluated along the row in binary32 as                */
+/* (h00 o_x + 2 beta) o_x + gamma with fused multiply-adds (beta and gamma  */
+/* once per row; d < 0 arises only from rounding).  The rows are those      */
 /* of the box [floor(x_a) - E_a, floor(x_a) + E_a] clipped to the volume,   */
 /* E_a = ceil(sqrt(H_aa)) in binary32 (voxels outside the volume are not    */
 /* counted).  Offsets are                                                   */
@@ -742,13 +743,17 @@ static int ko_ab_setup(ko_ab_win *w, const double x[3], const double H[6], const
     return 1;
 }
 
-/* The span [*ja, *jb] of j = s_x - floor(x_x) in the x-row at offsets
- * (o1, o2), clipped to the box; returns 0 for an empty row. */
-static int ko_ab_span(const ko_ab_win *w, float o1, float o2, int *ja, int *jb)
+/* The x-row at offsets (o1, o2): d = (h00 o_x + b2) o_x + g along it, and
+ * the span [*ja, *jb] of j = s_x - floor(x_x), clipped to the box; returns
+ * 0 for an empty row. */
+static int ko_ab_span(const ko_ab_win *w, float o1, float o2, float *b2, float *g, int *ja,
+                      int *jb)
 {
     const float *h = w->h;
     const float beta = h[1] * o1 + h[2] * o2;
     const float gamma = (h[3] * o1 + (2.0f * h[4]) * o2) * o1 + (h[5] * o2) * o2;
+    *b2 = beta + beta;
+    *g = gamma;
     const float disc = beta * beta - h[0] * (gamma - AB_SLACK);
     if (!(disc >= 0.0f)) return 0;
     const float sq = sqrtf(disc);
@@ -784,16 +789,14 @@ static int64_t ko_ab_pass(const uint8_t *bins, int nx, int ny, int nz, int B, co
             const float o1 = (float)(sy - w->n[1]) - w->f[1];
             const float o2 = (float)(sz - w->n[2]) - w->f[2];
             int ja, jb;
-            if (!ko_ab_span(w, o1, o2, &ja, &jb)) continue;
+            float b2, g;
+            if (!ko_ab_span(w, o1, o2, &b2, &g, &ja, &jb)) continue;
             for (int j = ja; j <= jb; ++j) {
                 const int v = ko_at(bins, nx, ny, nz, w->n[0] + j, sy, sz);
                 if (!v) continue;
                 const float o0 = (float)j - w->f[0];
-                const float u0 = h[0] * o0 + h[1] * o1 + h[2] * o2;
-                const float u1 = h[1] * o0 + h[3] * o1 + h[4] * o2;
-                const float u2 = h[2] * o0 + h[4] * o1 + h[5] * o2;
-                const float d = o0 * u0 + o1 * u1 + o2 * u2;
-                if (!(d >= 0.0f && d <= 1.0f)) continue;
+                const float d = fmaf(fmaf(h[0], o0, b2), o0, g);
+                if (!(d >= -0.0625f && d <= 1.0f)) continue;
                 if (kind == AB_HIST) {
                     const int64_t k = ko_q(ko_ab_kernel(d), AB_QK);
                     P[v - 1] += k;
@@ -931,8 +934,9 @@ void ko_abmsod(const uint8_t *bins, int nx, int ny, int nz, int B,
 }
 
 /* Window membership two ways, for a uniform volume of counted voxels:
- * out[0] = voxels of the box with 0 <= d <= 1, out[1] = those of them that
- * lie in their row's span (equal when the spans lose nothing). */
+ * out[0] = voxels of the box whose quadratic form o^T H^-1 o (binary32, no
+ * row form) is in [0, 1], out[1] = those of them that lie in their row's
+ * span (equal when the spans lose nothing). */
 void ko_ab_window_check(const double x[3], const double H[6], int64_t out[2])
 {
     ko_ab_win w;
@@ -945,10 +949,12 @@ void ko_ab_window_check(const double x[3], const double H[6], int64_t out[2])
             const float o1 = (float)(sy - w.n[1]) - w.f[1];
             const float o2 = (float)(sz - w.n[2]) - w.f[2];
             int ja = 1, jb = 0;
-            ko_ab_span(&w, o1, o2, &ja, &jb);
+            float b2, g;
+            ko_ab_span(&w, o1, o2, &b2, &g, &ja, &jb);
             for (int sx = w.lo[0]; sx <= w.hi[0]; ++sx) {
                 const int j = sx - w.n[0];
                 const float o0 = (float)j - w.f[0];
+                /* d as the quadratic form, independent of the row form */
                 const float u0 = h[0] * o0 + h[1] * o1 + h[2] * o2;
                 const float u1 = h[1] * o0 + h[3] * o1 + h[4] * o2;
                 const float u2 = h[2] * o0 + h[4] * o1 + h[5] * o2;

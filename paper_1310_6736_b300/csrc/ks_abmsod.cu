@@ -16,7 +16,9 @@
 // spans end to end, and the lanes then walk the packed voxels 32 at a time;
 // each lane finds its row from a 32-bit mask of the row starts in its step
 // (one warp OR-reduction) and a per-warp table of the batch's rows.
-// Per-voxel terms are binary32 in one fixed operation order; every sum over
+// Along a row d is (h00 o_x + 2 beta) o_x + gamma (two fused multiply-adds,
+// beta and gamma once per row).  Per-voxel terms are binary32 in one fixed
+// operation order; every sum over
 // voxels is an exact int64 sum of the terms rounded to nearest on a
 // fixed-point grid (2^-16 for k, 2^-12 for the position terms and w', 2^-8
 // for the second moments), so the warp's summation order does not change
@@ -162,12 +164,13 @@ struct AbSums {
 
 // One row of a batch, in the warp's table: where its voxels start in the
 // packed order, its first voxel's byte offset from the pass base, its first
-// j = s_x - floor(x_x), and its (o_y, o_z).
+// j = s_x - floor(x_x), its (o_y, o_z) and the row form of d.
 struct AbRow {
     int start, off;
     int ja;
     float o1, o2;
-    int pad0, pad1, pad2;
+    float b2, g;   // d = (h00 o_x + b2) o_x + g along the row
+    int pad;
 };
 
 // One pass of the warp over the window's voxels.
@@ -181,6 +184,7 @@ __device__ __forceinline__ void ab_pass(const VolDesc &v, const AbWinS &w, uint3
     const float f0 = w.f[0], f1 = w.f[1], f2 = w.f[2];
     const int e1 = w.hi[1] - w.lo[1] + 1;
     const int nrows = e1 * (w.hi[2] - w.lo[2] + 1);
+    const uint32_t col_s = PASS == kPassHist ? smem_u32(col) : 0u;
     const float jlo = ab_i2f(w.lo[0] - w.n[0]), jhi = ab_i2f(w.hi[0] - w.n[0]);
     const float ih0 = __frcp_rn(h0);
     const int pitch = (int)v.pitch, plane = (int)v.plane;
@@ -194,7 +198,7 @@ __device__ __forceinline__ void ab_pass(const VolDesc &v, const AbWinS &w, uint3
     const unsigned lt = (1u << lane) - 1u;
     for (int rb = wt * 32; rb < nrows; rb += 32 * T) {
         int len = 0, ja = 0, off = 0;
-        float o1 = 0.0f, o2 = 0.0f;
+        float o1 = 0.0f, o2 = 0.0f, b2 = 0.0f, g = 0.0f;
         if (rb + lane < nrows) {
             o1 = __fsub_rn(ab_i2f(w.lo[1] + iy - w.n[1]), f1);
             o2 = __fsub_rn(ab_i2f(w.lo[2] + iz - w.n[2]), f2);
@@ -202,6 +206,8 @@ __device__ __forceinline__ void ab_pass(const VolDesc &v, const AbWinS &w, uint3
             const float gamma = __fadd_rn(
                 __fmul_rn(__fadd_rn(__fmul_rn(h3, o1), __fmul_rn(__fmul_rn(2.0f, h4), o2)), o1),
                 __fmul_rn(__fmul_rn(h5, o2), o2));
+            b2 = __fadd_rn(beta, beta);
+            g = gamma;
             const float disc =
                 __fsub_rn(__fmul_rn(beta, beta), __fmul_rn(h0, __fsub_rn(gamma, kSlack)));
             if (disc >= 0.0f) {
@@ -245,12 +251,18 @@ __device__ __forceinline__ void ab_pass(const VolDesc &v, const AbWinS &w, uint3
             rw.ja = ja;
             rw.o1 = o1;
             rw.o2 = o2;
+            rw.b2 = b2;
+            rw.g = g;
         }
         __syncwarp();
         int before = 0;   // nonempty rows that start before this step
         // int32 partial sums of the batch: a batch has at most 32 rows of at
-        // most 65 voxels, so a lane adds at most 65 terms below 2^22 here
-        int a32[7] = {0, 0, 0, 0, 0, 0, 0};
+        // most 65 voxels, so a lane adds at most 65 terms below 2^22 here.
+        // Each term is added as the bit pattern of y + 1.5 * 2^23 (that is
+        // 0x4B400000 + rint(y)); the n * 0x4B400000 is taken off at the end
+        // of the batch, modulo 2^32, which is exact as the sum fits int32.
+        uint32_t a32[7] = {0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        uint32_t n32 = 0u;
         for (int p0 = 0; p0 < total; p0 += 32) {
             const unsigned m = __reduce_or_sync(
                 0xffffffffu, (len > 0 && start >= p0 && start < p0 + 32) ? 1u << (start - p0) : 0u);
@@ -263,21 +275,15 @@ __device__ __forceinline__ void ab_pass(const VolDesc &v, const AbWinS &w, uint3
                 if (b) {
                     const float o0 = __fsub_rn(ab_i2f(rw.ja + kk), f0);
                     const float r1 = rw.o1, r2 = rw.o2;
-                    const float u0 = __fadd_rn(__fadd_rn(__fmul_rn(h0, o0), __fmul_rn(h1, r1)),
-                                               __fmul_rn(h2, r2));
-                    const float u1 = __fadd_rn(__fadd_rn(__fmul_rn(h1, o0), __fmul_rn(h3, r1)),
-                                               __fmul_rn(h4, r2));
-                    const float u2 = __fadd_rn(__fadd_rn(__fmul_rn(h2, o0), __fmul_rn(h4, r1)),
-                                               __fmul_rn(h5, r2));
-                    const float d = __fadd_rn(__fadd_rn(__fmul_rn(o0, u0), __fmul_rn(r1, u1)),
-                                              __fmul_rn(r2, u2));
-                    if (d >= 0.0f && d <= 1.0f) {
+                    const float d = __fmaf_rn(__fmaf_rn(h0, o0, rw.b2), o0, rw.g);
+                    if (d >= -0.0625f && d <= 1.0f) {
                         // |o_a| <= 33, so the terms stay below 2^22 when
                         // k w < 30 (position) or w < 15 (moments); heavier
                         // rare-bin terms go straight to the int64 sums
                         if (PASS == kPassHist) {
-                            col[(b - 1) * 32] += (uint32_t)ab_rint_small(__fmul_rn(ab_kernel(d), kQK));
-                            a32[0] += 1;
+                            red_add_shared(col_s + (uint32_t)(b - 1) * 128u,
+                                           (uint32_t)ab_rint_small(__fmul_rn(ab_kernel(d), kQK)));
+                            n32 += 1u;
                         } else if (PASS == kPassPos) {
                             const float tk = __fmul_rn(ab_kernel(d), wf[b - 1]);
                             const float y0 = __fmul_rn(__fmul_rn(tk, o0), kQX);
@@ -285,10 +291,11 @@ __device__ __forceinline__ void ab_pass(const VolDesc &v, const AbWinS &w, uint3
                             const float y2 = __fmul_rn(__fmul_rn(tk, r2), kQX);
                             const float y3 = __fmul_rn(tk, kQX);
                             if (tk < 30.0f) {
-                                a32[0] += ab_rint_small(y0);
-                                a32[1] += ab_rint_small(y1);
-                                a32[2] += ab_rint_small(y2);
-                                a32[3] += ab_rint_small(y3);
+                                a32[0] += __float_as_uint(__fadd_rn(y0, 12582912.0f));
+                                a32[1] += __float_as_uint(__fadd_rn(y1, 12582912.0f));
+                                a32[2] += __float_as_uint(__fadd_rn(y2, 12582912.0f));
+                                a32[3] += __float_as_uint(__fadd_rn(y3, 12582912.0f));
+                                n32 += 1u;
                             } else {
                                 acc.s[0] += ab_q(y0);
                                 acc.s[1] += ab_q(y1);
@@ -305,13 +312,14 @@ __device__ __forceinline__ void ab_pass(const VolDesc &v, const AbWinS &w, uint3
                             const float y5 = __fmul_rn(__fmul_rn(tw, __fmul_rn(r2, r2)), kQH);
                             const float y6 = __fmul_rn(tw, kQX);
                             if (tw < 15.0f) {
-                                a32[0] += ab_rint_small(y0);
-                                a32[1] += ab_rint_small(y1);
-                                a32[2] += ab_rint_small(y2);
-                                a32[3] += ab_rint_small(y3);
-                                a32[4] += ab_rint_small(y4);
-                                a32[5] += ab_rint_small(y5);
-                                a32[6] += ab_rint_small(y6);
+                                a32[0] += __float_as_uint(__fadd_rn(y0, 12582912.0f));
+                                a32[1] += __float_as_uint(__fadd_rn(y1, 12582912.0f));
+                                a32[2] += __float_as_uint(__fadd_rn(y2, 12582912.0f));
+                                a32[3] += __float_as_uint(__fadd_rn(y3, 12582912.0f));
+                                a32[4] += __float_as_uint(__fadd_rn(y4, 12582912.0f));
+                                a32[5] += __float_as_uint(__fadd_rn(y5, 12582912.0f));
+                                a32[6] += __float_as_uint(__fadd_rn(y6, 12582912.0f));
+                                n32 += 1u;
                             } else {
                                 acc.s[0] += ab_q(y0);
                                 acc.s[1] += ab_q(y1);
@@ -327,8 +335,13 @@ __device__ __forceinline__ void ab_pass(const VolDesc &v, const AbWinS &w, uint3
             }
             before += __popc(m);
         }
+        if (PASS == kPassHist) {
+            acc.s[0] += n32;
+        } else {
+            const uint32_t off32 = n32 * 0x4B400000u;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) acc.s[k] += a32[k];
+            for (int k = 0; k < 7; ++k) acc.s[k] += (int32_t)(a32[k] - off32);
+        }
         __syncwarp();   // the table is rewritten by the next batch
     }
     if (PASS != kPassHist) {
@@ -660,7 +673,7 @@ size_t abmsod_smem_bytes(int B) {
 
 cudaError_t launch_abmsod(const LaunchCtx &lc, const VolDesc &v, const int32_t *seeds,
                           int64_t n_seeds, int r_min, int r_max, int max_iter, int r_team,
-                          ks_abmsod_result *out, unsigned long long *tickets) {
+                          int r_auto, ks_abmsod_result *out, unsigned long long *tickets) {
     const int S = r_max - r_min + 1;
     const int64_t n_items = n_seeds * S;
     if (n_items == 0) return cudaSuccess;
@@ -674,6 +687,10 @@ cudaError_t launch_abmsod(const LaunchCtx &lc, const VolDesc &v, const int32_t *
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_abmsod, kAbWarps * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
+    if (r_team <= 0) {
+        const int64_t warps = (int64_t)lc.num_sms * per_sm * kAbWarps;
+        r_team = n_items < 4 * warps ? r_auto : kRmax + 1;
+    }
     const int S_team = std::min(S, std::max(0, r_max - r_team + 1));
     const int64_t want = n_seeds * S_team + (n_seeds * (S - S_team) + kAbWarps - 1) / kAbWarps;
     const int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)lc.num_sms * per_sm);

@@ -441,9 +441,10 @@ static std::vector<DenseConfig> dense_candidates(int B, int r_max) {
 }
 
 static int g_forced_path = -1, g_forced_warps = 0, g_forced_ty = 0, g_forced_tz = 0;
-// ABMSOD: items with a starting radius >= this run on a whole block.
+// ABMSOD: items with a starting radius >= this run on a whole block when
+// the launch has few items per resident warp (0: decided per launch).
 constexpr int kAbmsodTeamRadius = 12;
-static int g_abmsod_team_radius = kAbmsodTeamRadius;
+static int g_abmsod_team_radius = 0;
 
 static int launch_dense_cfg(Ctx *c, cudaStream_t s, Volume *v, int r_min, int r_max, int w_norm,
                             const DenseConfig &cfg, const DenseOut &out, int z0, int z1) {
@@ -1241,7 +1242,7 @@ int ks_abmsod(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_t *s
     ProfRec rec;
     prof_begin(c, "ks_abmsod", c->stream, &rec);
     e = launch_abmsod(c->lc(), v->desc, ds, ns, params->r_min, params->r_max, params->max_iter,
-                      g_abmsod_team_radius, dout, ticket);
+                      g_abmsod_team_radius, kAbmsodTeamRadius, dout, ticket);
     prof_end(c, &rec, c->stream);
     KS_TRY_CUDA(c, e);
     if (!out_on_device)
@@ -1482,7 +1483,7 @@ int ks_selftest_wait_timeout(ks_ctx *ctx, int polls) {
 // to the autotuner).  Returns KS_EINVAL for a shape that can never fit.
 int ks_set_abmsod_team_radius(int r_team) {
     if (r_team > kRmax + 1) return KS_EINVAL;
-    g_abmsod_team_radius = r_team <= 0 ? kAbmsodTeamRadius : r_team;
+    g_abmsod_team_radius = r_team <= 0 ? 0 : r_team;
     return KS_OK;
 }
 

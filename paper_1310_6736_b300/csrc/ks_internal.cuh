@@ -169,11 +169,13 @@ cudaError_t launch_bin_f32(const LaunchCtx &lc, const float *raw, int nx, int ny
 // ks_abmsod.cu: adaptive-bandwidth mean shift for every (seed, r) item
 // (record seed * S + r - r_min); items with r >= r_team run on a whole
 // block, the others on one warp each; persistent over two ticket counters
-// (tickets[0..1]) that the launch zeroes.
+// (tickets[0..1]) that the launch zeroes.  r_team = 0: r_auto when the
+// launch has fewer than 4 items per resident warp, else every item on one
+// warp (the small items then fill in behind the large ones).
 size_t abmsod_smem_bytes(int B);
 cudaError_t launch_abmsod(const LaunchCtx &lc, const VolDesc &v, const int32_t *seeds,
                           int64_t n_seeds, int r_min, int r_max, int max_iter, int r_team,
-                          ks_abmsod_result *out, unsigned long long *tickets);
+                          int r_auto, ks_abmsod_result *out, unsigned long long *tickets);
 
 // ks_dense.cu
 struct DenseConfig {

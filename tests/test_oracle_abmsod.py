@@ -162,8 +162,9 @@ def test_one_iteration_matches_fp64_evaluation():
 def test_axis_swap_symmetry():
     """Swapping x and y in the volume and the seeds swaps the centre and the
     H entries (00 <-> 11, 02 <-> 12); rho and the iteration count agree.
-    The binary32 evaluation is symmetric term by term; only the FP64
-    determinant is summed in another order, so a rare item may differ."""
+    The evaluation walks x-rows, so the swap changes the rounding only:
+    agreement to rounding level, with a rare item allowed to take another
+    path."""
     bins = _blob_volume(11)
     B = 4
     rng = np.random.default_rng(3)
@@ -172,9 +173,9 @@ def test_axis_swap_symmetry():
     bt = np.ascontiguousarray(bins.transpose(0, 2, 1))
     st = seeds[:, [1, 0, 2]].copy()
     b = ko.abmsod(bt, B, 3, 6, st, max_iter=8)
-    same = ((a["x"] == b["x"][:, [1, 0, 2]]).all(1) &
-            (a["H"] == b["H"][:, [3, 1, 4, 0, 2, 5]]).all(1) &
-            (a["rho"] == b["rho"]) & (a["iters"] == b["iters"]))
+    same = ((np.abs(a["x"] - b["x"][:, [1, 0, 2]]) < 1e-4).all(1) &
+            (np.abs(a["H"] - b["H"][:, [3, 1, 4, 0, 2, 5]]) < 1e-3 * (1 + np.abs(a["H"]))).all(1) &
+            (np.abs(a["rho"] - b["rho"]) < 1e-6) & (a["iters"] == b["iters"]))
     assert same.mean() >= 0.95, same.mean()
 
 
