@@ -339,6 +339,7 @@ def run_ks(args):
         # short forms of the batched and serving workloads (full sizes:
         # --mode batch / --mode serve)
         line["config"]["selection"] = run_selection(ctx, ks, w, params)
+        line["config"]["abmsod"] = abmsod_summary(ctx, ks, w, params)
         line["config"]["batched"] = run_batched(ctx, ks, synth, count=64, max_dim=128, reps=2)
         line["config"]["serving"] = run_serving(ks.Context, ks, synth, rate=50.0, count=120,
                                                 pool=12, max_dim=96)
@@ -616,11 +617,157 @@ def run_serving(ctx_factory, ks, synth, rate=50.0, count=200, pool=24, max_dim=N
             "sequential_volumes_per_s": count / seq_span}
 
 
+# FP32 and INT32 lane operations the ABMSOD definition takes per window
+# voxel of a kernel histogram, with the sums pass that reuses the window:
+# histogram 16 (offset 1, d 2, kernel 10, rounding 2, sum 1), position sums
+# 29, bandwidth sums 36; the two halves of an iteration give 45 and 52.
+AB_OPS_PER_VOXEL = 48.5
+
+
+def abmsod_summary(ctx, ks, w, params, reps=3):
+    """ABMSOD (Alg. 2) for every (grid seed, r) of the step's volume: device
+    time of one ks_abmsod call (median of reps, CUDA events)."""
+    import torch
+    v = ctx.create_volume(w.volume, w.binning)
+    n = ctx.seed_count(v, params) * (w.r_max - w.r_min + 1)
+    out = torch.empty(n * ks.AB_RESULT.itemsize, dtype=torch.uint8, device="cuda")
+    ctx.abmsod(v, params, out=out)
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.abmsod(v, params, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    rec = out.cpu().numpy().view(ks.AB_RESULT)
+    ctx.release_volume(v)
+    ms = statistics.median(ts)
+    return {"candidates": n, "iterations": int(rec["iters"].sum()),
+            "window_voxels": int(rec["voxels"].sum()), "ms": ms,
+            "candidate_iterations_per_s": int(rec["iters"].sum()) / (ms * 1e-3),
+            "full_measurement": "python bench.py --mode abmsod"}
+
+
+def run_abmsod(args):
+    """Adaptive-bandwidth mean shift (Alg. 2, Eq. 7) for every (grid seed, r)
+    of the PET-shaped workload, device-resident inputs and outputs; one
+    step = one ks_abmsod call over all 2048 x 17 candidates."""
+    import torch
+    from paper_1310_6736_b300 import build, ks, synth
+    build.build()
+    torch.cuda.set_device(0)
+    w = synth.workload(WORKLOAD)
+    params = ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter)
+    ctx = ks.Context()
+    stream = torch.cuda.current_stream()
+    raw_dev = torch.from_numpy(w.volume).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    v = ctx.create_volume(raw_dev, w.binning)
+    n_items = ctx.seed_count(v, params) * (w.r_max - w.r_min + 1)
+    out = torch.empty(n_items * ks.AB_RESULT.itemsize, dtype=torch.uint8, device="cuda")
+    host = ctx.abmsod(v, params)
+    iters, voxels = int(host["iters"].sum()), int(host["voxels"].sum())
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        ctx.abmsod(v, params, out=out)
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    launches0 = ctx.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with Clocks(0) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            ctx.abmsod(v, params, out=out)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    launches = ctx.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    k_ms, k_n = ctx.kernel_time("ks_abmsod")
+    ctx.set_profiling(False)
+    same = np.array_equal(out.cpu().numpy().view(ks.AB_RESULT), host)
+    ctx.release_volume(v)
+    ms = statistics.median(step_ms)
+    # end to end through the C ABI: host volume in, host records out
+    e2e = []
+    for i in range(2 + max(3, min(args.steps, 10))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vh = ctx.create_volume(w.volume, w.binning)
+        ctx.abmsod(vh, params)
+        ctx.release_volume(vh)
+        torch.cuda.synchronize()
+        if i >= 2:
+            e2e.append(time.perf_counter() - t0)
+    clocks = clk.summary()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 128 * (clocks["sm_max_mhz"] or 2032.0) * 1e6
+    kernel_s = k_ms / max(1, k_n) * 1e-3
+    achieved = AB_OPS_PER_VOXEL * voxels / kernel_s
+    line = {
+        "metric": "ABMSOD candidate-iterations/s", "value": iters / (ms * 1e-3),
+        "unit": "candidate-iterations/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 voxel terms, i64 sums, f64 per item",
+        "data": "synthetic",
+        "config": {"workload": "pet128: 128x128x64 float32 PET-shaped volume, 32 bins; ABMSOD "
+                               "for every (grid seed, r), stride 8 (2048 seeds), r = 4..20, "
+                               f"max {w.max_iter} iterations",
+                   "candidates": n_items, "iterations": iters, "window_voxels": voxels,
+                   "window_voxels_per_s": voxels / (ms * 1e-3),
+                   "candidates_per_s": n_items / (ms * 1e-3),
+                   "step_ms_p50": ms, "step_ms_max": max(step_ms),
+                   "l2": "flushed between steps (256 MB write)",
+                   "outputs": "device-resident records; equal to the host-output run: " +
+                              str(bool(same))},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                     "unit": "T lane-ops/s", "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_abmsod", "kernel_ms": k_ms / max(1, k_n),
+                     "ops_per_window_voxel": AB_OPS_PER_VOXEL,
+                     "peak_source": f"{sms} SMs x 128 FP32/INT32 lanes x max SM clock"},
+        "e2e": {"value": iters / statistics.median(e2e), "unit": "candidate-iterations/s",
+                "h2d_bytes_per_step": int(w.volume.nbytes),
+                "d2h_bytes_per_step": n_items * ks.AB_RESULT.itemsize},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        b = oracle.bin_volume(w.volume, w.binning)
+        seeds = oracle.seed_grid(w.dims, w.stride)
+        rng = np.random.default_rng(0)
+        threads = oracle.max_threads()
+        n = 8
+        t0 = time.perf_counter()
+        r = oracle.abmsod(b, w.binning["bins"], w.r_min, w.r_max,
+                          seeds[rng.choice(len(seeds), n, replace=False)], w.max_iter,
+                          nthreads=threads)
+        dt = time.perf_counter() - t0
+        n = int(min(len(seeds), max(n, n * args.ref_budget / max(dt, 1e-3))))
+        pick = seeds[rng.choice(len(seeds), n, replace=False)]
+        t0 = time.perf_counter()
+        r = oracle.abmsod(b, w.binning["bins"], w.r_min, w.r_max, pick, w.max_iter,
+                          nthreads=threads)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": int(r["iters"].sum()) / dt,
+                                "unit": "candidate-iterations/s", "cores": threads,
+                                "kind": "oracle",
+                                "sample": f"{n} random grid seeds x {w.r_max - w.r_min + 1} radii "
+                                          f"of the {WORKLOAD} workload, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_mode(args):
     import torch
     from paper_1310_6736_b300 import build, ks, synth
     build.build()
     torch.cuda.set_device(0)
+    if args.mode == "abmsod":
+        return run_abmsod(args)
     if args.mode == "window":
         ctx = ks.Context()
         rows = [run_window(ctx, ks, synth, name) for name in ("mr256", "mr256w")]
@@ -666,9 +813,11 @@ def main():
                     help="run one part of the step only (profiling)")
     ap.add_argument("--dense-config", default="",
                     help="force the dense launch shape: path,warps,tile_y,tile_z")
-    ap.add_argument("--mode", choices=["step", "batch", "serve", "window"], default="step",
+    ap.add_argument("--mode", choices=["step", "batch", "serve", "window", "abmsod"],
+                    default="step",
                     help="batch: batched vs plain launches; serve: request-stream latency; "
-                         "window: full range vs tumour window level on the MR workload")
+                         "window: full range vs tumour window level on the MR workload; "
+                         "abmsod: adaptive-bandwidth mean shift on the PET-shaped workload")
     ap.add_argument("--count", type=int, default=64, help="volumes (batch) or requests (serve)")
     ap.add_argument("--max-dim", type=int, default=0, help="cap on each volume dimension")
     ap.add_argument("--rates", type=float, nargs="+", default=[20.0, 50.0, 100.0])
