@@ -163,13 +163,16 @@ struct AbSums {
 };
 
 // One row of a batch, in the warp's table: where its voxels start in the
-// packed order, its first voxel's byte offset from the pass base, its first
-// j = s_x - floor(x_x), its (o_y, o_z) and the row form of d.
+// packed order, and, relative to that start, its first voxel's byte offset
+// from the pass base and the bit pattern of the binary32 1.5 * 2^23 + j of
+// its first j = s_x - floor(x_x) (so voxel p of the packed order is at
+// offp + p with j bits jp + p); the row form of d and its (o_y, o_z).
 struct AbRow {
-    int start, off;
-    int ja;
-    float o1, o2;
+    int start;
+    int offp;      // byte offset of the row's first voxel minus start
+    int jp;        // 0x4B400000 + (its first j) - start
     float b2, g;   // d = (h00 o_x + b2) o_x + g along the row
+    float o1, o2;
     int pad;
 };
 
@@ -247,15 +250,14 @@ __device__ __forceinline__ void ab_pass(const VolDesc &v, const AbWinS &w, uint3
         if (len > 0) {
             AbRow &rw = tab[__popc(nonempty & lt)];
             rw.start = start;
-            rw.off = off;
-            rw.ja = ja;
+            rw.offp = off - start;
+            rw.jp = 0x4B400000 + ja - start;
             rw.o1 = o1;
             rw.o2 = o2;
             rw.b2 = b2;
             rw.g = g;
         }
         __syncwarp();
-        int before = 0;   // nonempty rows that start before this step
         // int32 partial sums of the batch: a batch has at most 32 rows of at
         // most 65 voxels, so a lane adds at most 65 terms below 2^22 here.
         // Each term is added as the bit pattern of y + 1.5 * 2^23 (that is
@@ -263,77 +265,94 @@ __device__ __forceinline__ void ab_pass(const VolDesc &v, const AbWinS &w, uint3
         // of the batch, modulo 2^32, which is exact as the sum fits int32.
         uint32_t a32[7] = {0u, 0u, 0u, 0u, 0u, 0u, 0u};
         uint32_t n32 = 0u;
-        for (int p0 = 0; p0 < total; p0 += 32) {
-            const unsigned m = __reduce_or_sync(
-                0xffffffffu, (len > 0 && start >= p0 && start < p0 + 32) ? 1u << (start - p0) : 0u);
-            const int p = p0 + lane;
-            if (p < total) {
-                const int k = before + __popc(m & (lt | (1u << lane))) - 1;
-                const AbRow &rw = tab[k];
-                const int kk = p - rw.start;
-                const int b = __ldg(base + rw.off + kk);
-                if (b) {
-                    const float o0 = __fsub_rn(ab_i2f(rw.ja + kk), f0);
-                    const float r1 = rw.o1, r2 = rw.o2;
-                    const float d = __fmaf_rn(__fmaf_rn(h0, o0, rw.b2), o0, rw.g);
-                    if (d >= -0.0625f && d <= 1.0f) {
-                        // |o_a| <= 33, so the terms stay below 2^22 when
-                        // k w < 30 (position) or w < 15 (moments); heavier
-                        // rare-bin terms go straight to the int64 sums
-                        if (PASS == kPassHist) {
-                            red_add_shared(col_s + (uint32_t)(b - 1) * 128u,
-                                           (uint32_t)ab_rint_small(__fmul_rn(ab_kernel(d), kQK)));
-                            n32 += 1u;
-                        } else if (PASS == kPassPos) {
-                            const float tk = __fmul_rn(ab_kernel(d), wf[b - 1]);
-                            const float y0 = __fmul_rn(__fmul_rn(tk, o0), kQX);
-                            const float y1 = __fmul_rn(__fmul_rn(tk, r1), kQX);
-                            const float y2 = __fmul_rn(__fmul_rn(tk, r2), kQX);
-                            const float y3 = __fmul_rn(tk, kQX);
-                            if (tk < 30.0f) {
-                                a32[0] += __float_as_uint(__fadd_rn(y0, 12582912.0f));
-                                a32[1] += __float_as_uint(__fadd_rn(y1, 12582912.0f));
-                                a32[2] += __float_as_uint(__fadd_rn(y2, 12582912.0f));
-                                a32[3] += __float_as_uint(__fadd_rn(y3, 12582912.0f));
-                                n32 += 1u;
-                            } else {
-                                acc.s[0] += ab_q(y0);
-                                acc.s[1] += ab_q(y1);
-                                acc.s[2] += ab_q(y2);
-                                acc.s[3] += ab_q(y3);
-                            }
-                        } else {
-                            const float tw = wf[b - 1];
-                            const float y0 = __fmul_rn(__fmul_rn(tw, __fmul_rn(o0, o0)), kQH);
-                            const float y1 = __fmul_rn(__fmul_rn(tw, __fmul_rn(o0, r1)), kQH);
-                            const float y2 = __fmul_rn(__fmul_rn(tw, __fmul_rn(o0, r2)), kQH);
-                            const float y3 = __fmul_rn(__fmul_rn(tw, __fmul_rn(r1, r1)), kQH);
-                            const float y4 = __fmul_rn(__fmul_rn(tw, __fmul_rn(r1, r2)), kQH);
-                            const float y5 = __fmul_rn(__fmul_rn(tw, __fmul_rn(r2, r2)), kQH);
-                            const float y6 = __fmul_rn(tw, kQX);
-                            if (tw < 15.0f) {
-                                a32[0] += __float_as_uint(__fadd_rn(y0, 12582912.0f));
-                                a32[1] += __float_as_uint(__fadd_rn(y1, 12582912.0f));
-                                a32[2] += __float_as_uint(__fadd_rn(y2, 12582912.0f));
-                                a32[3] += __float_as_uint(__fadd_rn(y3, 12582912.0f));
-                                a32[4] += __float_as_uint(__fadd_rn(y4, 12582912.0f));
-                                a32[5] += __float_as_uint(__fadd_rn(y5, 12582912.0f));
-                                a32[6] += __float_as_uint(__fadd_rn(y6, 12582912.0f));
-                                n32 += 1u;
-                            } else {
-                                acc.s[0] += ab_q(y0);
-                                acc.s[1] += ab_q(y1);
-                                acc.s[2] += ab_q(y2);
-                                acc.s[3] += ab_q(y3);
-                                acc.s[4] += ab_q(y4);
-                                acc.s[5] += ab_q(y5);
-                                acc.s[6] += ab_q(y6);
-                            }
-                        }
-                    }
+        // one window voxel: packed position p of row rw, stored bin b > 0
+        auto voxel = [&](const AbRow &rw, int p, int b) {
+            const float o0 = __fsub_rn(__fsub_rn(__int_as_float(rw.jp + p), 12582912.0f), f0);
+            const float d = __fmaf_rn(__fmaf_rn(h0, o0, rw.b2), o0, rw.g);
+            if (!(d >= -0.0625f && d <= 1.0f)) return;
+            const float r1 = rw.o1, r2 = rw.o2;
+            // |o_a| <= 33, so the terms stay below 2^22 when k w < 30
+            // (position) or w < 15 (moments); heavier rare-bin terms go
+            // straight to the int64 sums
+            if (PASS == kPassHist) {
+                red_add_shared(col_s + (uint32_t)(b - 1) * 128u,
+                               (uint32_t)ab_rint_small(__fmul_rn(ab_kernel(d), kQK)));
+                n32 += 1u;
+            } else if (PASS == kPassPos) {
+                // wf holds 2^12 w (exact scaling, so (k w o) 2^12 = k (2^12 w) o)
+                const float tk = __fmul_rn(ab_kernel(d), wf[b - 1]);
+                const float y0 = __fmul_rn(tk, o0);
+                const float y1 = __fmul_rn(tk, r1);
+                const float y2 = __fmul_rn(tk, r2);
+                const float y3 = tk;
+                if (tk < 30.0f * kQX) {
+                    a32[0] += __float_as_uint(__fadd_rn(y0, 12582912.0f));
+                    a32[1] += __float_as_uint(__fadd_rn(y1, 12582912.0f));
+                    a32[2] += __float_as_uint(__fadd_rn(y2, 12582912.0f));
+                    a32[3] += __float_as_uint(__fadd_rn(y3, 12582912.0f));
+                    n32 += 1u;
+                } else {
+                    acc.s[0] += ab_q(y0);
+                    acc.s[1] += ab_q(y1);
+                    acc.s[2] += ab_q(y2);
+                    acc.s[3] += ab_q(y3);
+                }
+            } else {
+                // wf holds 2^8 w (exact scaling)
+                const float tw = wf[b - 1];
+                const float y0 = __fmul_rn(tw, __fmul_rn(o0, o0));
+                const float y1 = __fmul_rn(tw, __fmul_rn(o0, r1));
+                const float y2 = __fmul_rn(tw, __fmul_rn(o0, r2));
+                const float y3 = __fmul_rn(tw, __fmul_rn(r1, r1));
+                const float y4 = __fmul_rn(tw, __fmul_rn(r1, r2));
+                const float y5 = __fmul_rn(tw, __fmul_rn(r2, r2));
+                const float y6 = __fmul_rn(tw, kQX / kQH);
+                if (tw < 15.0f * kQH) {
+                    a32[0] += __float_as_uint(__fadd_rn(y0, 12582912.0f));
+                    a32[1] += __float_as_uint(__fadd_rn(y1, 12582912.0f));
+                    a32[2] += __float_as_uint(__fadd_rn(y2, 12582912.0f));
+                    a32[3] += __float_as_uint(__fadd_rn(y3, 12582912.0f));
+                    a32[4] += __float_as_uint(__fadd_rn(y4, 12582912.0f));
+                    a32[5] += __float_as_uint(__fadd_rn(y5, 12582912.0f));
+                    a32[6] += __float_as_uint(__fadd_rn(y6, 12582912.0f));
+                    n32 += 1u;
+                } else {
+                    acc.s[0] += ab_q(y0);
+                    acc.s[1] += ab_q(y1);
+                    acc.s[2] += ab_q(y2);
+                    acc.s[3] += ab_q(y3);
+                    acc.s[4] += ab_q(y4);
+                    acc.s[5] += ab_q(y5);
+                    acc.s[6] += ab_q(y6);
                 }
             }
-            before += __popc(m);
+        };
+        // walk the packed voxels 64 at a time (two per lane, both loads in
+        // flight together); a lane's row is found from the 32-bit masks of
+        // the row starts in each half
+        const unsigned le = lt | (1u << lane);
+        int before = 0;        // nonempty rows that start before this step
+        int sp = start;        // start - p0
+        for (int p0 = 0; p0 < total; p0 += 64) {
+            const unsigned m0 = __reduce_or_sync(
+                0xffffffffu, len > 0 && (unsigned)sp < 32u ? 1u << sp : 0u);
+            const unsigned m1 = __reduce_or_sync(
+                0xffffffffu, len > 0 && (unsigned)(sp - 32) < 32u ? 1u << (sp - 32) : 0u);
+            sp -= 64;
+            const int c0 = __popc(m0);
+            const int pa = p0 + lane, pb = pa + 32;
+            int ka = 0, kb = 0, ba = 0, bb = 0;
+            if (pa < total) {
+                ka = before + __popc(m0 & le) - 1;
+                ba = __ldg(base + tab[ka].offp + pa);
+            }
+            if (pb < total) {
+                kb = before + c0 + __popc(m1 & le) - 1;
+                bb = __ldg(base + tab[kb].offp + pb);
+            }
+            if (ba) voxel(tab[ka], pa, ba);
+            if (bb) voxel(tab[kb], pb, bb);
+            before += c0 + __popc(m1);
         }
         if (PASS == kPassHist) {
             acc.s[0] += n32;
@@ -422,11 +441,13 @@ __device__ __forceinline__ int64_t ab_hist_part(const VolDesc &v, const AbWinS &
 }
 
 // Leader: team totals P_b (bins lane, lane + 32), K, binary32 weights
-// wf_b = sqrt(K / (B P_b)) into lead->wf and, when want_rho, rho =
+// w_b = sqrt(K / (B P_b)) times the power of two `scale` (exact: the sums
+// passes fold their fixed-point scale into the weight) into lead->wf and,
+// when want_rho, rho =
 // (sum_b sqrt(P_b)) / sqrt(B K) with the bins paired (b, b + 32) and then
 // summed by a butterfly (the pairwise tree of the definition).  Returns K.
 __device__ __forceinline__ int64_t ab_bins(AbWarpMem *team, int T, int lane, int B, bool want_rho,
-                                           double &rho) {
+                                           float scale, double &rho) {
     AbWarpMem *lead = team;
     int64_t P0 = 0, P1 = 0;
     for (int t = 0; t < T; ++t) {
@@ -438,11 +459,12 @@ __device__ __forceinline__ int64_t ab_bins(AbWarpMem *team, int T, int lane, int
     if (K > 0) {
         const float Kf = __ll2float_rn(K), Bf = (float)B;
         if (lane < B)
-            lead->wf[lane] =
-                P0 > 0 ? __fsqrt_rn(__fdiv_rn(Kf, __fmul_rn(Bf, __ll2float_rn(P0)))) : 0.0f;
+            lead->wf[lane] = P0 > 0 ? __fmul_rn(__fsqrt_rn(__fdiv_rn(Kf, __fmul_rn(Bf, __ll2float_rn(P0)))), scale)
+                                    : 0.0f;
         if (lane + 32 < B)
             lead->wf[lane + 32] =
-                P1 > 0 ? __fsqrt_rn(__fdiv_rn(Kf, __fmul_rn(Bf, __ll2float_rn(P1)))) : 0.0f;
+                P1 > 0 ? __fmul_rn(__fsqrt_rn(__fdiv_rn(Kf, __fmul_rn(Bf, __ll2float_rn(P1)))), scale)
+                       : 0.0f;
         if (want_rho) {
             double t = __dadd_rn(P0 > 0 ? __dsqrt_rn((double)P0) : 0.0,
                                  P1 > 0 ? __dsqrt_rn((double)P1) : 0.0);
@@ -506,7 +528,7 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
         nvl += ab_hist_part(J.vol, w, cols, mine->tab, lane, wt, T, B, mine);
         team_sync<T>();
         if (leader) {
-            const int64_t K = ab_bins(team, T, lane, B, false, rho);
+            const int64_t K = ab_bins(team, T, lane, B, false, kQX, rho);
             if (lane == 0) lead->flag = K == 0 ? 1 : 0;
         }
         team_sync<T>();
@@ -543,7 +565,7 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
         team_sync<T>();
         ++it;
         if (leader) {
-            const int64_t K2 = ab_bins(team, T, lane, B, true, rho);
+            const int64_t K2 = ab_bins(team, T, lane, B, true, kQH, rho);
             if (lane == 0) lead->flag = K2 == 0 ? 1 : 0;
         }
         team_sync<T>();
