@@ -623,6 +623,11 @@ def run_serving(ctx_factory, ks, synth, rate=50.0, count=200, pool=24, max_dim=N
 # 29, bandwidth sums 36; the two halves of an iteration give 45 and 52.
 AB_OPS_PER_VOXEL = 48.5
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_abmsod launch on the
+# pet128 workload (profiles/k_abmsod_pet128.md, median of 10 launches): the
+# bin volume is read about once, the 34,816 records are written.
+AB_DRAM_BYTES = 3_740_000
+
 
 def abmsod_summary(ctx, ks, w, params, reps=3):
     """ABMSOD (Alg. 2) for every (grid seed, r) of the step's volume: device
@@ -723,7 +728,8 @@ def run_abmsod(args):
                    "outputs": "device-resident records; equal to the host-output run: " +
                               str(bool(same))},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                     "unit": "T lane-ops/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "T lane-ops/s", "frac": achieved / peak, "traffic": AB_DRAM_BYTES,
+                     "traffic_unit": "bytes per launch (dram read + write, ncu)",
                      "kernel": "k_abmsod", "kernel_ms": k_ms / max(1, k_n),
                      "ops_per_window_voxel": AB_OPS_PER_VOXEL,
                      "peak_source": f"{sms} SMs x 128 FP32/INT32 lanes x max SM clock"},
