@@ -669,13 +669,22 @@ def run_abmsod(args):
     raw_dev = torch.from_numpy(w.volume).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     v = ctx.create_volume(raw_dev, w.binning)
-    n_items = ctx.seed_count(v, params) * (w.r_max - w.r_min + 1)
+    grid = None
+    if args.seed_step > 1:        # a smaller case of the same launch (profiling)
+        nz, ny, nx = w.volume.shape
+        h = w.stride // 2
+        zz, yy, xx = np.meshgrid(np.arange(h, nz, w.stride), np.arange(h, ny, w.stride),
+                                 np.arange(h, nx, w.stride), indexing="ij")
+        grid = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], 1).astype(np.int32)
+        grid = grid[::args.seed_step].copy()
+    n_seeds = len(grid) if grid is not None else ctx.seed_count(v, params)
+    n_items = n_seeds * (w.r_max - w.r_min + 1)
     out = torch.empty(n_items * ks.AB_RESULT.itemsize, dtype=torch.uint8, device="cuda")
-    host = ctx.abmsod(v, params)
+    host = ctx.abmsod(v, params, seeds=grid)
     iters, voxels = int(host["iters"].sum()), int(host["voxels"].sum())
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
-        ctx.abmsod(v, params, out=out)
+        ctx.abmsod(v, params, seeds=grid, out=out)
     torch.cuda.synchronize()
     ctx.set_profiling(True)
     launches0 = ctx.launch_count()
@@ -685,7 +694,7 @@ def run_abmsod(args):
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
-            ctx.abmsod(v, params, out=out)
+            ctx.abmsod(v, params, seeds=grid, out=out)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
     launches = ctx.launch_count() - launches0
@@ -701,7 +710,7 @@ def run_abmsod(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         vh = ctx.create_volume(w.volume, w.binning)
-        ctx.abmsod(vh, params)
+        ctx.abmsod(vh, params, seeds=grid)
         ctx.release_volume(vh)
         torch.cuda.synchronize()
         if i >= 2:
@@ -825,6 +834,8 @@ def main():
                          "window: full range vs tumour window level on the MR workload; "
                          "abmsod: adaptive-bandwidth mean shift on the PET-shaped workload")
     ap.add_argument("--count", type=int, default=64, help="volumes (batch) or requests (serve)")
+    ap.add_argument("--seed-step", type=int, default=1,
+                    help="abmsod mode: every n-th grid seed only (a smaller case for profilers)")
     ap.add_argument("--max-dim", type=int, default=0, help="cap on each volume dimension")
     ap.add_argument("--rates", type=float, nargs="+", default=[20.0, 50.0, 100.0])
     ap.add_argument("--no-extras", action="store_true",
