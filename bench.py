@@ -134,20 +134,29 @@ def oracle_sample(w, budget_s=12.0, nthreads=0):
     sm = seeds[rng.choice(len(seeds), n_m, replace=False)]
     m = oracle.meanshift(b, B, w.r_min, w.r_max, sm, w.max_iter, nthreads=threads)
     t3 = time.perf_counter()
-    # scale each part to ~budget/3 seconds
-    k_c = max(1.0, budget_s / 3 / max(t1 - t0, 1e-3))
+    # scale each part to ~budget/3 seconds (the seed parts are capped at the
+    # whole grid; the dense sample takes up what they leave), then rescale
+    # once if the sample ran well short of the budget
+    per_c = max(t1 - t0, 1e-3) / n_c
     k_o = max(1.0, budget_s / 3 / max(t2 - t1, 1e-3))
     k_m = max(1.0, budget_s / 3 / max(t3 - t2, 1e-3))
-    n_c, n_o, n_m = int(n_c * k_c), min(len(seeds), int(n_o * k_o)), min(len(seeds), int(n_m * k_m))
-    cen = np.stack([rng.integers(0, nx, n_c), rng.integers(0, ny, n_c),
-                    rng.integers(0, nz, n_c)], 1).astype(np.int32)
-    so = seeds[rng.choice(len(seeds), n_o, replace=False)]
-    sm = seeds[rng.choice(len(seeds), n_m, replace=False)]
-    t0 = time.perf_counter()
-    oracle.dense(b, B, w.r_min, w.r_max, centres=cen, nthreads=threads)
-    o = oracle.octant_climb(b, B, w.r_min, w.r_max, so, w.max_iter, nthreads=threads)
-    m = oracle.meanshift(b, B, w.r_min, w.r_max, sm, w.max_iter, nthreads=threads)
-    dt = time.perf_counter() - t0
+    n_o, n_m = min(len(seeds), int(n_o * k_o)), min(len(seeds), int(n_m * k_m))
+    t_seeds = (t2 - t1) * n_o / 32 + (t3 - t2) * n_m / 16
+    n_c = max(n_c, int(max(budget_s / 3, budget_s - t_seeds) / per_c))
+    for attempt in range(2):
+        cen = np.stack([rng.integers(0, nx, n_c), rng.integers(0, ny, n_c),
+                        rng.integers(0, nz, n_c)], 1).astype(np.int32)
+        so = seeds[rng.choice(len(seeds), n_o, replace=False)]
+        sm = seeds[rng.choice(len(seeds), n_m, replace=False)]
+        t0 = time.perf_counter()
+        oracle.dense(b, B, w.r_min, w.r_max, centres=cen, nthreads=threads)
+        t_d = time.perf_counter() - t0
+        o = oracle.octant_climb(b, B, w.r_min, w.r_max, so, w.max_iter, nthreads=threads)
+        m = oracle.meanshift(b, B, w.r_min, w.r_max, sm, w.max_iter, nthreads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= 0.6 * budget_s or attempt == 1:
+            break
+        n_c = int(n_c * max(1.0, (budget_s - (dt - t_d)) / max(t_d, 1e-3)))
     we = n_c * S + int(o["iters"].sum()) * 8 * S + len(so) * S + int(m["iters"].sum()) + \
         int((m["converged"] == 0).sum())
     desc = (f"{n_c} random dense centres, {n_o} octant seeds and {n_m} mean-shift seeds "
@@ -754,18 +763,16 @@ def run_abmsod(args):
         seeds = oracle.seed_grid(w.dims, w.stride)
         rng = np.random.default_rng(0)
         threads = oracle.max_threads()
-        n = 8
-        t0 = time.perf_counter()
-        r = oracle.abmsod(b, w.binning["bins"], w.r_min, w.r_max,
-                          seeds[rng.choice(len(seeds), n, replace=False)], w.max_iter,
-                          nthreads=threads)
-        dt = time.perf_counter() - t0
-        n = int(min(len(seeds), max(n, n * args.ref_budget / max(dt, 1e-3))))
-        pick = seeds[rng.choice(len(seeds), n, replace=False)]
-        t0 = time.perf_counter()
-        r = oracle.abmsod(b, w.binning["bins"], w.r_min, w.r_max, pick, w.max_iter,
-                          nthreads=threads)
-        dt = time.perf_counter() - t0
+        n = 4 * threads
+        for attempt in range(3):      # calibrate, then about ref_budget seconds
+            pick = seeds[rng.choice(len(seeds), n, replace=False)]
+            t0 = time.perf_counter()
+            r = oracle.abmsod(b, w.binning["bins"], w.r_min, w.r_max, pick, w.max_iter,
+                              nthreads=threads)
+            dt = time.perf_counter() - t0
+            if attempt > 0 and (dt >= 0.6 * args.ref_budget or n == len(seeds)):
+                break
+            n = int(min(len(seeds), max(n, n * args.ref_budget / max(dt, 1e-3))))
         line["cpu_baseline"] = {"value": int(r["iters"].sum()) / dt,
                                 "unit": "candidate-iterations/s", "cores": threads,
                                 "kind": "oracle",
@@ -821,7 +828,7 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ks", choices=["ks", "reference"])
-    ap.add_argument("--ref-budget", type=float, default=12.0,
+    ap.add_argument("--ref-budget", type=float, default=15.0,
                     help="seconds of oracle work per reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", choices=["dense", "octant", "quadrant", "meanshift", "bin"],
