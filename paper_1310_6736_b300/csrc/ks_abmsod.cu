@@ -178,7 +178,7 @@ struct AbRow {
 
 // One pass of the warp over the window's voxels.
 template <int PASS>
-__device__ __forceinline__ void ab_pass(const VolDesc &v, const AbWinS &w, uint32_t *col,
+__device__ __noinline__ void ab_pass(const VolDesc &v, const AbWinS &w, uint32_t *col,
                                         const float *wf, AbRow *tab, int lane, int wt, int T,
                                         AbSums &acc) {
 #pragma unroll
