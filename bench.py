@@ -673,6 +673,7 @@ def run_abmsod(args):
     torch.cuda.set_device(0)
     w = synth.workload(WORKLOAD)
     params = ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter)
+    ks.set_abmsod_team_radius(args.team_radius)
     ctx = ks.Context()
     stream = torch.cuda.current_stream()
     raw_dev = torch.from_numpy(w.volume).cuda()
@@ -843,6 +844,9 @@ def main():
     ap.add_argument("--count", type=int, default=64, help="volumes (batch) or requests (serve)")
     ap.add_argument("--seed-step", type=int, default=1,
                     help="abmsod mode: every n-th grid seed only (a smaller case for profilers)")
+    ap.add_argument("--team-radius", type=int, default=0,
+                    help="abmsod mode: ks_set_abmsod_team_radius (0: the library's per-launch "
+                         "choice; 33: every item on one warp)")
     ap.add_argument("--max-dim", type=int, default=0, help="cap on each volume dimension")
     ap.add_argument("--rates", type=float, nargs="+", default=[20.0, 50.0, 100.0])
     ap.add_argument("--no-extras", action="store_true",
