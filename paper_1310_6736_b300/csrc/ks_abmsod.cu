@@ -524,7 +524,7 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
         }
         team_sync<T>();
         if (lead->flag) break;
-        AbWinS w = lead->win;
+        const AbWinS &w = lead->win;   // rewritten only after the next team sync
         nvl += ab_hist_part(J.vol, w, cols, mine->tab, lane, wt, T, B, mine);
         team_sync<T>();
         if (leader) {
@@ -560,7 +560,6 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
             ab_publish(lead, w2, lane);
         }
         team_sync<T>();
-        w = lead->win;
         nvl += ab_hist_part(J.vol, w, cols, mine->tab, lane, wt, T, B, mine);
         team_sync<T>();
         ++it;
@@ -652,7 +651,7 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
     team_sync<T>();   // the team's memory is reused by the next item
 }
 
-__global__ void __launch_bounds__(kAbWarps * 32, 4) k_abmsod(const AbJob J) {
+__global__ void __launch_bounds__(kAbWarps * 32, 4) k_abmsod(const __grid_constant__ AbJob J) {
     extern __shared__ __align__(16) uint8_t ab_smem[];
     __shared__ unsigned long long s_ticket;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
