@@ -138,6 +138,7 @@ struct AbWinS {
     float f[3];
     int n[3];
     int lo[3], hi[3];
+    int E[3];
 };
 __device__ __forceinline__ void ab_place(const double x[3], const AbShape &sh, const int dim[3],
                                          AbWinS &w) {
@@ -145,6 +146,7 @@ __device__ __forceinline__ void ab_place(const double x[3], const AbShape &sh, c
     for (int k = 0; k < 6; ++k) w.h[k] = sh.h[k];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
+        w.E[a] = sh.E[a];
         const double fl = floor(x[a]);
         w.n[a] = (int)fl;
         w.f[a] = __double2float_rn(__dsub_rn(x[a], fl));
@@ -178,9 +180,10 @@ struct AbRow {
 
 // One pass of the warp over the window's voxels.
 template <int PASS>
-__device__ __noinline__ void ab_pass(const VolDesc &v, const AbWinS &w, uint32_t *col,
+__device__ __noinline__ int64_t ab_pass(const VolDesc &v, const AbWinS &w, uint32_t *col,
                                         const float *wf, AbRow *tab, int lane, int wt, int T,
-                                        AbSums &acc) {
+                                        int64_t *red) {
+    AbSums acc;
 #pragma unroll
     for (int k = 0; k < 7; ++k) acc.s[k] = 0;
     const float h0 = w.h[0], h1 = w.h[1], h2 = w.h[2], h3 = w.h[3], h4 = w.h[4], h5 = w.h[5];
@@ -364,9 +367,15 @@ __device__ __noinline__ void ab_pass(const VolDesc &v, const AbWinS &w, uint32_t
         __syncwarp();   // the table is rewritten by the next batch
     }
     if (PASS != kPassHist) {
+        int64_t mine = 0;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) acc.s[k] = warp_sum_i64(acc.s[k]);
+        for (int k = 0; k < (PASS == kPassPos ? 4 : 7); ++k) {
+            const int64_t t = warp_sum_i64(acc.s[k]);
+            mine = lane == k ? t : mine;
+        }
+        if (lane < (PASS == kPassPos ? 4 : 7)) red[lane] = mine;
     }
+    return PASS == kPassHist ? acc.s[0] : 0;
 }
 
 struct AbJob {
@@ -386,6 +395,7 @@ struct AbState {
     double xn[3], Hn[6];   // this iteration's update
     double xo[3], Ho[6];   // best so far
     double best;
+    double rho;            // this iteration's rho at x'
 };
 
 // Per-warp shared memory.
@@ -415,8 +425,7 @@ __device__ __forceinline__ void team_sync() {
 __device__ __forceinline__ int64_t ab_hist_part(const VolDesc &v, const AbWinS &w, uint32_t *cols,
                                                 AbRow *tab, int lane, int wt, int T, int B,
                                                 AbWarpMem *mine) {
-    AbSums cnt;
-    ab_pass<kPassHist>(v, w, cols + lane, nullptr, tab, lane, wt, T, cnt);
+    const int64_t nv = ab_pass<kPassHist>(v, w, cols + lane, nullptr, tab, lane, wt, T, nullptr);
     __syncwarp();
     int64_t P0 = 0, P1 = 0;
     if (lane < B) {
@@ -437,7 +446,7 @@ __device__ __forceinline__ int64_t ab_hist_part(const VolDesc &v, const AbWinS &
         }
         mine->P[lane + 32] = P1;
     }
-    return cnt.s[0];
+    return nv;
 }
 
 // Leader: team totals P_b (bins lane, lane + 32), K, binary32 weights
@@ -506,14 +515,15 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
         }
         if (lane == 0) st->best = 0.0;
     }
-    int64_t nvl = 0;
+    if (lane == 0) mine->nv = 0;
     int it = 0, stopped = 0;
-    AbShape sh;            // leader only
-    double rho = 0.0;      // leader only
+    // the per-item values live in shared memory across the window passes
+    // (the passes are calls; registers held across them would be spilled)
     while (it < J.max_iter) {
         // window at (x, H)
         if (leader) {
             __syncwarp();
+            AbShape sh;
             const bool ok = ab_shape(st->H, sh);
             if (ok) {
                 AbWinS w;
@@ -525,19 +535,20 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
         team_sync<T>();
         if (lead->flag) break;
         const AbWinS &w = lead->win;   // rewritten only after the next team sync
-        nvl += ab_hist_part(J.vol, w, cols, mine->tab, lane, wt, T, B, mine);
+        {
+            const int64_t nv = warp_sum_i64(ab_hist_part(J.vol, w, cols, mine->tab, lane, wt, T, B, mine));
+            if (lane == 0) mine->nv += nv;
+        }
         team_sync<T>();
         if (leader) {
+            double rho;
             const int64_t K = ab_bins(team, T, lane, B, false, kQX, rho);
             if (lane == 0) lead->flag = K == 0 ? 1 : 0;
         }
         team_sync<T>();
         if (lead->flag) break;
         {
-            AbSums sp;
-            ab_pass<kPassPos>(J.vol, w, nullptr, lead->wf, mine->tab, lane, wt, T, sp);
-            if (lane < 4) mine->red[lane] = lane == 0 ? sp.s[0] : lane == 1 ? sp.s[1]
-                                                      : lane == 2 ? sp.s[2] : sp.s[3];
+            ab_pass<kPassPos>(J.vol, w, nullptr, lead->wf, mine->tab, lane, wt, T, mine->red);
         }
         team_sync<T>();
         if (leader) {
@@ -555,27 +566,35 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
                 st->xn[lane] = vv;
             }
             __syncwarp();
+            AbShape sh;   // the bandwidth part of the current window
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sh.h[k] = lead->win.h[k];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) sh.E[a] = lead->win.E[a];
+            __syncwarp();
             AbWinS w2;
             ab_place(st->xn, sh, dim, w2);
             ab_publish(lead, w2, lane);
         }
         team_sync<T>();
-        nvl += ab_hist_part(J.vol, w, cols, mine->tab, lane, wt, T, B, mine);
+        {
+            const int64_t nv = warp_sum_i64(ab_hist_part(J.vol, w, cols, mine->tab, lane, wt, T, B, mine));
+            if (lane == 0) mine->nv += nv;
+        }
         team_sync<T>();
         ++it;
         if (leader) {
+            double rho;
             const int64_t K2 = ab_bins(team, T, lane, B, true, kQH, rho);
-            if (lane == 0) lead->flag = K2 == 0 ? 1 : 0;
+            if (lane == 0) {
+                lead->flag = K2 == 0 ? 1 : 0;
+                st->rho = rho;
+            }
         }
         team_sync<T>();
         if (lead->flag) break;
         {
-            AbSums sm;
-            ab_pass<kPassMom>(J.vol, w, nullptr, lead->wf, mine->tab, lane, wt, T, sm);
-            int64_t mk = sm.s[0];
-#pragma unroll
-            for (int k = 1; k < 7; ++k) mk = lane == k ? sm.s[k] : mk;
-            if (lane < 7) mine->red[lane] = mk;
+            ab_pass<kPassMom>(J.vol, w, nullptr, lead->wf, mine->tab, lane, wt, T, mine->red);
         }
         team_sync<T>();
         if (leader) {
@@ -609,6 +628,7 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
                         if (Hn[dg[a]] > kHmax) Hn[dg[a]] = kHmax;
                 }
                 // best so far; stop at a fall of rho
+                const double rho = st->rho;
                 const double delta = __dsub_rn(st->best, rho);
                 if (rho > st->best) {
                     st->best = rho;
@@ -630,8 +650,6 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
             break;
         }
     }
-    nvl = warp_sum_i64(nvl);
-    if (lane == 0) mine->nv = nvl;
     team_sync<T>();
     if (leader) {
         int64_t nv = 0;
