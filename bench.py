@@ -365,8 +365,20 @@ def run_ks(args):
     return 0
 
 
+def _grid_subset(w, step):
+    """Every step-th seed of the workload's grid (x fastest, as the library
+    lays the grid out): a smaller case of the same launch for profilers."""
+    nz, ny, nx = w.volume.shape
+    h = w.stride // 2
+    zz, yy, xx = np.meshgrid(np.arange(h, nz, w.stride), np.arange(h, ny, w.stride),
+                             np.arange(h, nx, w.stride), indexing="ij")
+    grid = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], 1).astype(np.int32)
+    return grid[::step].copy()
+
+
 def run_case(args):
-    """Run one part of the step (for profilers): --case dense|octant|meanshift|bin."""
+    """Run one part of the step (for profilers): --case dense|octant|meanshift|bin.
+    --seed-step n: every n-th grid seed only (seed cases)."""
     import torch
     from paper_1310_6736_b300 import build, ks, synth
     build.build()
@@ -380,6 +392,7 @@ def run_case(args):
     Y = torch.empty((nz, ny, nx), dtype=torch.float64, device="cuda")
     sb = torch.empty((nz, ny, nx), dtype=torch.uint8, device="cuda")
     v = ctx.create_volume(raw_dev, w.binning)
+    seeds = _grid_subset(w, args.seed_step) if args.seed_step > 1 else None
     t = []
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize()
@@ -387,11 +400,11 @@ def run_case(args):
         if args.case == "dense":
             ctx.dense_saliency(v, params, (nz, ny, nx), out=(Y, sb))
         elif args.case == "octant":
-            ctx.seed_climb(v, params)
+            ctx.seed_climb(v, params, seeds=seeds)
         elif args.case == "quadrant":
-            ctx.seed_climb(v, params, planar=True)
+            ctx.seed_climb(v, params, seeds=seeds, planar=True)
         elif args.case == "meanshift":
-            ctx.meanshift(v, params)
+            ctx.meanshift(v, params, seeds=seeds)
         elif args.case == "bin":
             ctx.release_volume(v)
             v = ctx.create_volume(raw_dev, w.binning)
@@ -681,12 +694,7 @@ def run_abmsod(args):
     v = ctx.create_volume(raw_dev, w.binning)
     grid = None
     if args.seed_step > 1:        # a smaller case of the same launch (profiling)
-        nz, ny, nx = w.volume.shape
-        h = w.stride // 2
-        zz, yy, xx = np.meshgrid(np.arange(h, nz, w.stride), np.arange(h, ny, w.stride),
-                                 np.arange(h, nx, w.stride), indexing="ij")
-        grid = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], 1).astype(np.int32)
-        grid = grid[::args.seed_step].copy()
+        grid = _grid_subset(w, args.seed_step)
     n_seeds = len(grid) if grid is not None else ctx.seed_count(v, params)
     n_items = n_seeds * (w.r_max - w.r_min + 1)
     out = torch.empty(n_items * ks.AB_RESULT.itemsize, dtype=torch.uint8, device="cuda")
@@ -712,6 +720,24 @@ def run_abmsod(args):
     k_ms, k_n = ctx.kernel_time("ks_abmsod")
     ctx.set_profiling(False)
     same = np.array_equal(out.cpu().numpy().view(ks.AB_RESULT), host)
+    # the paper's LV-detection shape (Sec. 3.1): 400 candidate positions
+    # scattered at random over the volume, here each at every radius
+    rng = np.random.default_rng(11)
+    nz, ny, nx = w.volume.shape
+    scatter = np.stack([rng.integers(0, nx, 400), rng.integers(0, ny, 400),
+                        rng.integers(0, nz, 400)], 1).astype(np.int32)
+    sc_out = torch.empty(400 * (w.r_max - w.r_min + 1) * ks.AB_RESULT.itemsize,
+                         dtype=torch.uint8, device="cuda")
+    ctx.abmsod(v, params, seeds=scatter, out=sc_out)
+    sc_ms = []
+    for _ in range(5):
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.abmsod(v, params, seeds=scatter, out=sc_out)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        sc_ms.append(a.elapsed_time(b_))
+    sc_rec = sc_out.cpu().numpy().view(ks.AB_RESULT)
     ctx.release_volume(v)
     ms = statistics.median(step_ms)
     # end to end through the C ABI: host volume in, host records out
@@ -745,7 +771,12 @@ def run_abmsod(args):
                    "step_ms_p50": ms, "step_ms_max": max(step_ms),
                    "l2": "flushed between steps (256 MB write)",
                    "outputs": "device-resident records; equal to the host-output run: " +
-                              str(bool(same))},
+                              str(bool(same)),
+                   "scattered_400": {"candidates": len(sc_rec),
+                                     "iterations": int(sc_rec["iters"].sum()),
+                                     "ms": statistics.median(sc_ms),
+                                     "paper": "4.1 s per PET volume on a Tesla C2050 for about "
+                                              "400 candidates x 10 iterations (context only)"}},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "T lane-ops/s", "frac": achieved / peak, "traffic": AB_DRAM_BYTES,
                      "traffic_unit": "bytes per launch (dram read + write, ncu)",
@@ -843,7 +874,8 @@ def main():
                          "abmsod: adaptive-bandwidth mean shift on the PET-shaped workload")
     ap.add_argument("--count", type=int, default=64, help="volumes (batch) or requests (serve)")
     ap.add_argument("--seed-step", type=int, default=1,
-                    help="abmsod mode: every n-th grid seed only (a smaller case for profilers)")
+                    help="abmsod mode and seed cases: every n-th grid seed only (a smaller case "
+                         "for profilers)")
     ap.add_argument("--team-radius", type=int, default=0,
                     help="abmsod mode: ks_set_abmsod_team_radius (0: the library's per-launch "
                          "choice; 33: every item on one warp)")
