@@ -465,31 +465,33 @@ __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long 
         });
     }
     __syncthreads();
-    // column sums: 8 partial sums per bin, then one thread per bin
-    const int per = NC / 8;
-    for (int idx = threadIdx.x; idx < B * 8; idx += blockDim.x) {
-        const int b = idx >> 3, p = idx & 7;
+    // column sums: warp w takes bins w, w + 8, ...; lane l reads columns l,
+    // l + 32, ... of the bin (consecutive lanes, consecutive words: no bank
+    // conflicts) and the warp adds the unpacked fields with shuffles
+    (void)part;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int b = threadIdx.x >> 5; b < B; b += nw) {
         int c = 0, sx = 0, sy = 0, sz = 0;
-        for (int k = 0; k < per; ++k) {
-            const unsigned long long x = cols[b * NC + p * per + k];
+        for (int k = lane; k < NC; k += 32) {
+            const unsigned long long x = cols[b * NC + k];
             c += (int)(x & 0x7ffull);
             sx += (int)((x >> 11) & 0x1ffffull);
             sy += (int)((x >> 28) & 0x1ffffull);
             sz += (int)((x >> 45) & 0x1ffffull);
         }
-        int *q = part + idx * 4;
-        q[0] = c;
-        q[1] = sx;
-        q[2] = sy;
-        q[3] = sz;
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < B; b += blockDim.x) {
-        int s[4] = {0, 0, 0, 0};
-        for (int p = 0; p < 8; ++p)
-            for (int k = 0; k < 4; ++k) s[k] += part[(b * 8 + p) * 4 + k];
-        acc[4 * b] = s[0];
-        for (int k = 1; k < 4; ++k) acc[4 * b + k] = s[k] - 32 * s[0];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        }
+        if (lane == 0) {
+            acc[4 * b] = c;
+            acc[4 * b + 1] = sx - 32 * c;
+            acc[4 * b + 2] = sy - 32 * c;
+            acc[4 * b + 3] = sz - 32 * c;
+        }
     }
     __syncthreads();
 }
