@@ -410,6 +410,12 @@ __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &
 // lane, and a lane walks ceil(rows / 32) <= 40 rows (Ball(20) has 1257) of
 // at most 41 voxels: at most 1640 voxels.  Either way count < 2^11 and
 // each offset sum <= 1690 * 64 < 2^17, so no field carries into the next.
+// The warp path uses two 32-bit words per column instead (a 64-bit shared
+// reduction costs about 2.5 times a 32-bit one on this part): word A holds
+// the count in bits [0,11) and sum(dx+20) in [11,28); word B holds
+// sum(dy+20) in [0,16) and sum(dz+20) in [16,32).  A row contributes at
+// most (2w+1)(|dy|+20) <= 1056 to a dy sum (the maximum over Ball(20)'s
+// rows, at dy = 12), so 40 rows stay below 2^16; the same for dz.
 constexpr int kWarpMsRmax = 20;
 constexpr int kWarpMsBmax = 32;
 constexpr int kRowWords = 6;           // 8-byte words that cover a row of Ball(r <= 20)
@@ -502,11 +508,14 @@ __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long 
 __device__ void ms_pass_warp(const SeedJob &J, const OffsetTables &ot, unsigned long long *cols,
                              int *acc, const int P[3], int r) {
     const int B = J.vol.B, lane = threadIdx.x & 31;
-    for (int k = lane; k < B * 32; k += 32) cols[k] = 0ull;
+    // words A of bin b at colA[b * 32 + lane], words B at colA[(B + b) * 32 + lane]
+    uint32_t *colA = reinterpret_cast<uint32_t *>(cols);
+    for (int k = lane; k < 2 * B * 32; k += 32) colA[k] = 0u;
     __syncwarp();
     const uint8_t *c0 = voxel_ptr(J.vol, P);
     const int plane = (int)J.vol.plane, pitch = (int)J.vol.pitch;
-    const uint32_t col_addr = smem_u32(cols + lane);
+    const uint32_t a_addr = smem_u32(colA + lane) - 32 * 4;      // value v: a_addr + 128 v
+    const uint32_t b_addr = a_addr + (uint32_t)B * 32 * 4;
     const uint32_t *rows = ot.rows + __ldg(ot.rows_start + r);
     const int nrows = __ldg(ot.rows_start + r + 1) - __ldg(ot.rows_start + r);
     // A lane's rows are lane, lane + 32, ...: the words of the next row are
@@ -535,14 +544,13 @@ __device__ void ms_pass_warp(const SeedJob &J, const OffsetTables &ot, unsigned 
         uint32_t en = 0;
         unsigned long long wn[kRowWords];
         if (rn < nrows) fetch(rn, en, offn, wn);
-        int dy, dz, w;
-        const unsigned long long row_inc = ms_row_word(e, &dy, &dz, &w);
-        // voxel t adds row_inc + (t << 11); that addition stays inside the
-        // low 32 bits, which hold 1 + (32 - w + t) << 11 + ((dy + 32) & 15)
-        // << 28 <= 1 + 2^17 + 15 * 2^28 < 2^32 (t <= 2w, w <= 32)
-        const uint32_t row_lo = (uint32_t)row_inc, row_hi = (uint32_t)(row_inc >> 32);
+        const int dy = (int)(e & 0xffu) - 64, dz = (int)((e >> 8) & 0xffu) - 64;
+        const int w = (int)(e >> 16);
         const int n = 2 * w + 1;
-        const uint32_t col_m1 = col_addr - 32 * 8;      // value v's word: col_m1 + 256 v
+        // voxel t of the row (dx = t - w) adds 1 + (t - w + 20) << 11 to A
+        // and the row constant (dy + 20) | (dz + 20) << 16 to B
+        const uint32_t row_a = 1u + ((uint32_t)(20 - w) << 11);
+        const uint32_t row_b = (uint32_t)(dy + 20) | ((uint32_t)(dz + 20) << 16);
 #pragma unroll
         for (int k = 0; k < kRowWords; ++k) {
             // bytes [lo, hi) of word k belong to the row; the others are
@@ -553,13 +561,14 @@ __device__ void ms_pass_warp(const SeedJob &J, const OffsetTables &ot, unsigned 
             if (lo > 0) x &= ~0ull << (8 * lo);           // word 0 only: lo = off <= 7
             if (hi < 8) x &= (1ull << (8 * hi)) - 1ull;
             // byte b is voxel t = 8k + b - off (mod 2^32 arithmetic)
-            const uint32_t lo_k = row_lo + ((uint32_t)(8 * k - off) << 11);
+            const uint32_t a_k = row_a + ((uint32_t)(8 * k - off) << 11);
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
                 const uint32_t v = byte_of(x, b);
-                if (v != 0u)
-                    red_add_shared_u64(col_m1 + (v << 8), ((unsigned long long)row_hi << 32) |
-                                                              (lo_k + ((uint32_t)b << 11)));
+                if (v != 0u) {
+                    red_add_shared(a_addr + (v << 7), a_k + ((uint32_t)b << 11));
+                    red_add_shared(b_addr + (v << 7), row_b);
+                }
             }
         }
         e = en;
@@ -577,11 +586,12 @@ __device__ void ms_pass_warp(const SeedJob &J, const OffsetTables &ot, unsigned 
         const int b = lane + 32 * h;
         if (b < B) {
             for (int k = 0; k < 32; ++k) {
-                const unsigned long long x = cols[b * 32 + ((k + lane) & 31)];
-                s[h][0] += (int)(x & 0x7ffull);
-                s[h][1] += (int)((x >> 11) & 0x1ffffull);
-                s[h][2] += (int)((x >> 28) & 0x1ffffull);
-                s[h][3] += (int)((x >> 45) & 0x1ffffull);
+                const uint32_t xa = colA[b * 32 + ((k + lane) & 31)];
+                const uint32_t xb = colA[(B + b) * 32 + ((k + lane) & 31)];
+                s[h][0] += (int)(xa & 0x7ffu);
+                s[h][1] += (int)(xa >> 11);
+                s[h][2] += (int)(xb & 0xffffu);
+                s[h][3] += (int)(xb >> 16);
             }
         }
     }
@@ -591,7 +601,7 @@ __device__ void ms_pass_warp(const SeedJob &J, const OffsetTables &ot, unsigned 
         const int b = lane + 32 * h;
         if (b < B) {
             acc[4 * b] = s[h][0];
-            for (int k = 1; k < 4; ++k) acc[4 * b + k] = s[h][k] - 32 * s[h][0];
+            for (int k = 1; k < 4; ++k) acc[4 * b + k] = s[h][k] - 20 * s[h][0];
         }
     }
     __syncwarp();
