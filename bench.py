@@ -646,9 +646,10 @@ def run_serving(ctx_factory, ks, synth, rate=50.0, count=200, pool=24, max_dim=N
 AB_OPS_PER_VOXEL = 48.5
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_abmsod launch on the
-# pet128 workload (profiles/k_abmsod_pet128.md, median of 10 launches): the
-# bin volume is read about once, the 34,816 records are written.
-AB_DRAM_BYTES = 3_740_000
+# pet128 workload (profiles/k_abmsod_pet128.md, medians over 17 launches):
+# the touched part of the bin volume is read about once, the 34,816 records
+# are written.
+AB_DRAM_BYTES = 4_410_000
 
 
 def abmsod_summary(ctx, ks, w, params, reps=3):
