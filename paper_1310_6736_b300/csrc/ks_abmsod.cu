@@ -10,22 +10,25 @@
 //   2. Eq. 6 sums  sum k w o, sum k w            -> x'
 //   3. kernel histogram at (x', H) -> w'_b, rho = sum_b sqrt(HQ_b HP'_b)
 //   4. Eq. 7 sums  sum w' o o^T, sum w'         -> H' = 5 (M / sum w' + I/12)
-// A pass takes the bounding box's x-rows 32 at a time (the warps of a team
-// take every T-th batch): lane j finds row j's
-// span (the root interval of d <= 1 + 1/16 along x), a warp scan packs the
-// spans end to end, and the lanes then walk the packed voxels 32 at a time;
-// each lane finds its row from a 32-bit mask of the row starts in its step
-// (one warp OR-reduction) and a per-warp table of the batch's rows.
-// Along a row d is (h00 o_x + 2 beta) o_x + gamma (two fused multiply-adds,
-// beta and gamma once per row).  Per-voxel terms are binary32 in one fixed
-// operation order; every sum over
-// voxels is an exact int64 sum of the terms rounded to nearest on a
-// fixed-point grid (2^-16 for k, 2^-12 for the position terms and w', 2^-8
-// for the second moments), so the warp's summation order does not change
-// the result.  Histogram sums live in lane-private u32 columns in shared
-// memory (no atomics, no bank conflicts).  Everything per bin or per item is
-// FP64, one IEEE operation at a time, computed redundantly by all lanes so
-// the warp's control flow stays uniform.
+// A pass takes the box's x-rows 32 at a time (the warps of a team take
+// every T-th batch): lane j finds row j's span (the root interval of
+// d <= 1 + 1/16 along x), a warp scan packs the spans end to end, and the
+// lanes walk the packed voxels, two per lane per step; a lane finds its
+// row from a 32-bit mask of the row starts in its half-step (one warp
+// OR-reduction) and a per-warp table of the batch's rows.  Along a row d is
+// (h00 o_x + 2 beta) o_x + gamma (two fused multiply-adds, beta and gamma
+// once per row).  Per-voxel terms are binary32 in one fixed operation
+// order; every sum over voxels is an exact integer sum of the terms rounded
+// to nearest on a fixed-point grid (2^-16 for k, 2^-12 for the position
+// terms and w', 2^-8 for the second moments), so the summation order does
+// not change the result: histogram sums go to lane-private u32 columns in
+// shared memory (shared reductions, no bank conflicts), the position and
+// moment terms to int32 sums per batch of rows, then int64.  The passes are
+// non-inlined functions shared by both item paths (smaller code), and the
+// per-item values live in shared memory across them.  Everything per bin
+// or per item is FP64, one IEEE operation at a time, done by the item's
+// first warp with its lanes computing the same values, so that the warp's
+// control flow stays uniform.
 #include <algorithm>
 
 #include "ks_internal.cuh"
