@@ -48,48 +48,16 @@ __device__ __forceinline__ const uint8_t *voxel_ptr(const VolDesc &v, const int 
     return v.base + (int64_t)P[2] * v.plane + (int64_t)P[1] * v.pitch + P[0];
 }
 
-// Streams the 2w+1 bins starting at p with aligned 8-byte loads and calls
-// f(t, v) for the bin v at p + t.  The loads cover at most 7 bytes before
-// p and 7 bytes after p + 2w: with |offset| <= 32 that stays inside the
-// halo-padded allocation, which ends in 256 bytes of slack.
-// The first and the last word are masked byte by byte; the words between
-// them are whole and need no test.
+// Byte b of an 8-byte word.
 __device__ __forceinline__ uint32_t byte_of(unsigned long long word, int b) {
     const uint32_t h = b < 4 ? (uint32_t)word : (uint32_t)(word >> 32);
     return (h >> (8 * (b & 3))) & 0xffu;
 }
 
-template <typename F>
-__device__ __forceinline__ void walk_row(const uint8_t *p, int w, F &&f) {
-    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-    const unsigned long long *q = reinterpret_cast<const unsigned long long *>(a & ~uintptr_t(7));
-    const int off = (int)(a & 7u);
-    const int n = 2 * w + 1;
-    const int last = (off + n - 1) >> 3;                // index of the last word
-    {
-        const unsigned long long word = __ldg(q);
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const int t = b - off;
-            if (t >= 0 && t < n) f(t, byte_of(word, b));
-        }
-    }
-    for (int k = 1; k < last; ++k) {
-        const unsigned long long word = __ldg(q + k);
-        const int t0 = 8 * k - off;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) f(t0 + b, byte_of(word, b));
-    }
-    if (last > 0) {
-        const unsigned long long word = __ldg(q + last);
-        const int t0 = 8 * last - off;
-#pragma unroll
-        for (int b = 0; b < 8; ++b)
-            if (t0 + b < n) f(t0 + b, byte_of(word, b));
-    }
-}
-
-// The same walk with every byte masked (one loop, smaller code).
+// Streams the 2w+1 bins starting at p with aligned 8-byte loads and calls
+// f(t, v) for the bin v at p + t (every byte masked).  The loads cover at
+// most 7 bytes before p and 7 bytes after p + 2w: with |offset| <= 32 that
+// stays inside the halo-padded allocation, which ends in 256 bytes of slack.
 template <typename F>
 __device__ __forceinline__ void walk_row_masked(const uint8_t *p, int w, F &&f) {
     const uintptr_t a = reinterpret_cast<uintptr_t>(p);
@@ -159,66 +127,67 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) {
 // into prefix sums over shells (histograms of Ball(r_min + si)).  Each
 // histogram has B + 1 words indexed by the stored value v; word 0 (not
 // counted) is a dummy that is never read, so a voxel costs no branch.
-// soff[d2] is the byte offset si * (B + 1) * 4 of the shell of an offset
-// with |o|^2 = d2.
+// The walk runs over the offset tables of Ball(r_max): an entry with three
+// nonzero components stands for its 8 sign mirrors, and mirror m (bit0 -x,
+// bit1 -y, bit2 -z) lies in the open octant m, so one entry gives one
+// voxel to each octant, all in the entry's shell; an offset on a
+// coordinate plane or axis lies in every closed octant it touches.
 __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *cnt,
-                            const uint32_t *soff, const int P[3]) {
+                            const int P[3]) {
     const int B = J.vol.B, S = J.S, Bs = B + 1;
     const uint32_t SB4 = (uint32_t)(S * Bs * 4);          // bytes per octant
     for (int k = threadIdx.x; k < 9 * S * Bs; k += blockDim.x) cnt[k] = 0;
     __syncthreads();
     const uint8_t *c0 = voxel_ptr(J.vol, P);
     const int plane = (int)J.vol.plane, pitch = (int)J.vol.pitch;
-    const uint32_t cnt_s = smem_u32(cnt), extra_s = cnt_s + 8 * SB4, soff_s = smem_u32(soff);
-    const uint32_t *rows = ot.rows + __ldg(ot.rows_start + J.r_max);
-    const int nrows = __ldg(ot.rows_start + J.r_max + 1) - __ldg(ot.rows_start + J.r_max);
-    // one x-row of Ball(r_max) per thread at a time (rows off the planes
-    // y = 0 and z = 0 come first in the table, so warps rarely mix kinds)
-    for (int ri = threadIdx.x; ri < nrows; ri += blockDim.x) {
-        const uint32_t e = __ldg(rows + ri);
-        const int dy = (int)(e & 0xffu) - 64, dz = (int)((e >> 8) & 0xffu) - 64;
-        if (J.planar && dz != 0) continue;          // quadrant climb: the disk dz = 0 only
-        const int w = (int)(e >> 16);
-        const int rr = dy * dy + dz * dz;
-        const uint8_t *p = c0 + dz * plane + dy * pitch - w;
-        const int jyz = (dy < 0 ? 2 : 0) | (dz < 0 ? 4 : 0);
-        if (dy != 0 && dz != 0) {
-            // dx < 0: open octant jyz | 1; dx >= 0: octant jyz.  The voxel
-            // dx = 0 lies on the plane x = 0 and so also in octant jyz | 1
-            // (multiplicity 2): added there, with its excess, after the walk.
-            const uint32_t base_l = cnt_s + (uint32_t)(jyz | 1) * SB4, base_r = cnt_s + jyz * SB4;
-            walk_row(p, w, [&](int t, uint32_t v) {
-                const int dx = t - w;
-                red_add_shared((dx < 0 ? base_l : base_r) + ld_shared_u32(soff_s + 4 * (dx * dx + rr)) +
-                                   (v << 2),
-                               1u);
-            });
-            const uint32_t a0 = ld_shared_u32(soff_s + 4 * rr) + ((uint32_t)__ldg(p + w) << 2);
-            red_add_shared(base_l + a0, 1u);
-            red_add_shared(extra_s + a0, 1u);
-        } else {
-            // on the plane y = 0 or z = 0: every closed octant the voxel touches
-            const int ay = dy > 0 ? 1 : (dy < 0 ? 2 : 3);
-            const int az = dz > 0 ? 1 : (dz < 0 ? 2 : 3);
-            walk_row(p, w, [&](int t, uint32_t v) {
-                const int dx = t - w;
-                const int ax = dx > 0 ? 1 : (dx < 0 ? 2 : 3);
-                const uint32_t a = ld_shared_u32(soff_s + 4 * (dx * dx + rr)) + (v << 2);
-                uint32_t mult = 0;
-                for (int jz = 0; jz < 2; ++jz) {
-                    if (!(az & (1 << jz))) continue;
-                    for (int jy = 0; jy < 2; ++jy) {
-                        if (!(ay & (1 << jy))) continue;
-                        for (int jx = 0; jx < 2; ++jx) {
-                            if (!(ax & (1 << jx))) continue;
-                            red_add_shared(cnt_s + (uint32_t)(jx | (jy << 1) | (jz << 2)) * SB4 + a, 1u);
-                            ++mult;
-                        }
-                    }
-                }
-                red_add_shared(extra_s + a, mult - 1u);
-            });
+    const uint32_t cnt_s = smem_u32(cnt), extra_s = cnt_s + 8 * SB4;
+    auto shell = [&](int rho) {   // byte offset of the shell of radius class rho
+        return (uint32_t)((rho > J.r_min ? rho - J.r_min : 0) * Bs * 4);
+    };
+    // three nonzero components (none on the disk dz = 0 of the quadrant climb)
+    if (!J.planar) {
+        const int n8 = __ldg(ot.c8_start + J.r_max + 1);
+        for (int k = threadIdx.x; k < n8; k += blockDim.x) {
+            const uint32_t e = __ldg(ot.c8 + k);
+            const int X = (int)(e & 0xffu);
+            const int Y = (int)((e >> 8) & 0xffu) * pitch;
+            const int Z = (int)((e >> 16) & 0xffu) * plane;
+            const uint32_t base = cnt_s + shell((int)(e >> 24));
+            const int o[8] = {Z + Y + X, Z + Y - X, Z - Y + X, Z - Y - X,
+                              Y - Z + X, Y - Z - X, -Z - Y + X, -Z - Y - X};
+            uint32_t v[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[m] = __ldg(c0 + o[m]);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) red_add_shared(base + (uint32_t)m * SB4 + (v[m] << 2), 1u);
         }
+    }
+    // on a coordinate plane or axis: every closed octant the voxel touches,
+    // and the excess multiplicity
+    const int nr = __ldg(ot.rest_start + J.r_max + 1);
+    for (int k = threadIdx.x; k < nr; k += blockDim.x) {
+        const uint32_t f = __ldg(ot.rest + k);
+        const int dx = (int)(f & 0xffu) - 64, dy = (int)((f >> 8) & 0xffu) - 64,
+                  dz = (int)((f >> 16) & 0xffu) - 64;
+        if (J.planar && dz != 0) continue;          // quadrant climb: the disk dz = 0 only
+        const uint32_t a =
+            shell((int)(f >> 24)) + ((uint32_t)__ldg(c0 + dz * plane + dy * pitch + dx) << 2);
+        const int ax = dx > 0 ? 1 : (dx < 0 ? 2 : 3);
+        const int ay = dy > 0 ? 1 : (dy < 0 ? 2 : 3);
+        const int az = dz > 0 ? 1 : (dz < 0 ? 2 : 3);
+        uint32_t mult = 0;
+        for (int jz = 0; jz < 2; ++jz) {
+            if (!(az & (1 << jz))) continue;
+            for (int jy = 0; jy < 2; ++jy) {
+                if (!(ay & (1 << jy))) continue;
+                for (int jx = 0; jx < 2; ++jx) {
+                    if (!(ax & (1 << jx))) continue;
+                    red_add_shared(cnt_s + (uint32_t)(jx | (jy << 1) | (jz << 2)) * SB4 + a, 1u);
+                    ++mult;
+                }
+            }
+        }
+        red_add_shared(extra_s + a, mult - 1u);
     }
     __syncthreads();
     // prefix over shells per (octant, value) column, eight shells at a time:
@@ -340,24 +309,18 @@ __device__ void kb_from_pass(const SeedJob &J, const double *T, const double *L,
 }
 
 __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &ot,
-                            const double *T, const double *L, const uint8_t *rho_of,
-                            uint32_t *soff, uint32_t *cnt, double *hb, SeedShared &sh) {
+                            const double *T, const double *L, uint32_t *cnt, double *hb,
+                            SeedShared &sh) {
     const int dims[3] = {J.vol.nx, J.vol.ny, J.vol.nz};
     const int B = J.vol.B, S = J.S, Bs = B + 1;
     uint32_t *extra = cnt + 8 * S * Bs;
-    // shell byte offsets of this job: si = max(rho - r_min, 0)
-    for (int d2 = threadIdx.x; d2 <= J.r_max * J.r_max; d2 += blockDim.x) {
-        const int rho = rho_of[d2];
-        soff[d2] = (uint32_t)((rho > J.r_min ? rho - J.r_min : 0) * Bs * 4);
-    }
-    __syncthreads();
     int P[3] = {J.seeds[3 * sidx], J.seeds[3 * sidx + 1], J.seeds[3 * sidx + 2]};
     const int T1 = J.max_iter + 1;
     if (threadIdx.x == 0 && J.traj)
         for (int a = 0; a < 3; ++a) J.traj[(sidx * T1) * 3 + a] = P[a];
     int it = 0, conv = 0, fresh = 0;
     while (it < J.max_iter) {
-        octant_pass(J, ot, cnt, soff, P);
+        octant_pass(J, ot, cnt, P);
         fresh = 1;
         for (int w = threadIdx.x; w < 8 * S; w += blockDim.x)
             hb[w] = window_entropy(cnt + w * Bs + 1, B, T, L, nullptr);
@@ -380,7 +343,7 @@ __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &
     if (threadIdx.x == 0 && J.traj)
         for (int t = it + (conv ? 0 : 1); t <= J.max_iter; ++t)
             for (int a = 0; a < 3; ++a) J.traj[(sidx * T1 + t) * 3 + a] = P[a];
-    if (!fresh) octant_pass(J, ot, cnt, soff, P);     // the last pass was not at P
+    if (!fresh) octant_pass(J, ot, cnt, P);     // the last pass was not at P
     ks_seed_result *o = J.oct_out + sidx;
     kb_from_pass(J, T, L, cnt, extra, hb, sh, o);
     if (threadIdx.x == 0) {
@@ -792,14 +755,6 @@ __global__ void __launch_bounds__(KINDS == 1 ? kOctThreads : kSeedThreads,
                                                         int max_B, int max_S, int persistent) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ SeedShared sh;
-    __shared__ uint8_t rho_of[kRmax * kRmax + 1];    // ceil(sqrt(d2)) for d2 <= 32^2
-    __shared__ uint32_t soff[kRmax * kRmax + 1];     // octant tickets: shell byte offsets
-    if (KINDS & (1 << kOctant))
-        for (int d2 = threadIdx.x; d2 <= kRmax * kRmax; d2 += blockDim.x) {
-            int r = 0;
-            while (r * r < d2) ++r;
-            rho_of[d2] = (uint8_t)r;
-        }
     const Layout lay(max_B, max_S, KINDS);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int64_t round = 0;; ++round) {
@@ -816,7 +771,7 @@ __global__ void __launch_bounds__(KINDS == 1 ? kOctThreads : kSeedThreads,
         const int64_t local = t - q.seg_start[seg];
         if (q.seg_kind[seg] == kOctant) {
             if constexpr ((KINDS & (1 << kOctant)) != 0)
-                octant_item(J, local, ot, T, L, rho_of, soff,
+                octant_item(J, local, ot, T, L,
                             reinterpret_cast<uint32_t *>(smem + lay.cnt),
                             reinterpret_cast<double *>(smem + lay.hb), sh);
             continue;
