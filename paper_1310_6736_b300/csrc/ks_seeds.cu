@@ -147,19 +147,31 @@ __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *
     // three nonzero components (none on the disk dz = 0 of the quadrant climb)
     if (!J.planar) {
         const int n8 = __ldg(ot.c8_start + J.r_max + 1);
-        for (int k = threadIdx.x; k < n8; k += blockDim.x) {
-            const uint32_t e = __ldg(ot.c8 + k);
-            const int X = (int)(e & 0xffu);
-            const int Y = (int)((e >> 8) & 0xffu) * pitch;
-            const int Z = (int)((e >> 16) & 0xffu) * plane;
-            const uint32_t base = cnt_s + shell((int)(e >> 24));
-            const int o[8] = {Z + Y + X, Z + Y - X, Z - Y + X, Z - Y - X,
-                              Y - Z + X, Y - Z - X, -Z - Y + X, -Z - Y - X};
-            uint32_t v[8];
+        // two entries per round: their 16 loads are in flight together
+        for (int k = threadIdx.x; k < n8; k += 2 * blockDim.x) {
+            const int k2 = k + blockDim.x;
+            const uint32_t e0 = __ldg(ot.c8 + k);
+            const uint32_t e1 = k2 < n8 ? __ldg(ot.c8 + k2) : 0u;   // 0: the centre, v unused
+            uint32_t v[2][8], base[2];
 #pragma unroll
-            for (int m = 0; m < 8; ++m) v[m] = __ldg(c0 + o[m]);
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t e = h ? e1 : e0;
+                const int X = (int)(e & 0xffu);
+                const int Y = (int)((e >> 8) & 0xffu) * pitch;
+                const int Z = (int)((e >> 16) & 0xffu) * plane;
+                base[h] = cnt_s + shell((int)(e >> 24));
+                const int o[8] = {Z + Y + X, Z + Y - X, Z - Y + X, Z - Y - X,
+                                  Y - Z + X, Y - Z - X, -Z - Y + X, -Z - Y - X};
 #pragma unroll
-            for (int m = 0; m < 8; ++m) red_add_shared(base + (uint32_t)m * SB4 + (v[m] << 2), 1u);
+                for (int m = 0; m < 8; ++m) v[h][m] = __ldg(c0 + o[m]);
+            }
+#pragma unroll
+            for (int m = 0; m < 8; ++m) red_add_shared(base[0] + (uint32_t)m * SB4 + (v[0][m] << 2), 1u);
+            if (k2 < n8) {
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    red_add_shared(base[1] + (uint32_t)m * SB4 + (v[1][m] << 2), 1u);
+            }
         }
     }
     // on a coordinate plane or axis: every closed octant the voxel touches,
