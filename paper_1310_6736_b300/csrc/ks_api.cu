@@ -272,12 +272,37 @@ static int build_ball_tables(Ctx *c) {
                          ((uint32_t)rw.w << 16));
     }
     swr[kRmax + 1] = (int)hw.size();
-    // one allocation: c8 | rest | rows | c8_start | rest_start | rows_start | ball_size
+    // mean-shift block path: may its per-voxel sums go into two 32-bit
+    // words for radius r?  Column c of a bin sees the rows i = c mod NC
+    // (threads t = c mod NC walk rows t, t + 256, ...); a row adds 2w + 1 to
+    // the count, (2w + 1) r to sum(dx + r), (2w + 1)(dy + r) and
+    // (2w + 1)(dz + r) to the other two.
+    uint8_t ms32[kRmax + 1];
+    for (int r = 0; r <= kRmax; ++r) {
+        const int NC = ms_columns(c->h_ball_size[r]);
+        std::vector<int64_t> sc(NC, 0), sx(NC, 0), sy(NC, 0), sz(NC, 0);
+        for (int i = swr[r]; i < swr[r + 1]; ++i) {
+            const uint32_t e = hw[i];
+            const int dy = (int)(e & 0xffu) - 64, dz = (int)((e >> 8) & 0xffu) - 64;
+            const int n = 2 * (int)(e >> 16) + 1, col = (i - swr[r]) % NC;
+            sc[col] += n;
+            sx[col] += (int64_t)n * r;
+            sy[col] += (int64_t)n * (dy + r);
+            sz[col] += (int64_t)n * (dz + r);
+        }
+        bool ok = true;
+        for (int col = 0; col < NC; ++col)
+            ok = ok && sc[col] < (1 << 11) && sx[col] < (1 << 17) && sy[col] < (1 << 16) &&
+                 sz[col] < (1 << 16);
+        ms32[r] = ok ? 1 : 0;
+    }
+    // one allocation: c8 | rest | rows | c8_start | rest_start | rows_start | ball_size | ms32
     const size_t b8 = h8.size() * 4, br = hr.size() * 4, bw = hw.size() * 4, bs = sizeof(s8);
     const size_t at_r = (b8 + 255) / 256 * 256, at_w = at_r + (br + 255) / 256 * 256;
     const size_t at_s8 = at_w + (bw + 255) / 256 * 256;
     const size_t at_sr = at_s8 + 256, at_sw = at_sr + 256, at_bs = at_sw + 256;
-    c->offsets_bytes = at_bs + 256;
+    const size_t at_m32 = at_bs + 256;
+    c->offsets_bytes = at_m32 + 256;
     void *p;
     KS_TRY_CUDA(c, dev_alloc(c, &p, c->offsets_bytes));
     c->d_offsets = p;
@@ -290,10 +315,11 @@ static int build_ball_tables(Ctx *c) {
     KS_TRY_CUDA(c, cudaMemcpy(m + at_sw, swr, bs, cudaMemcpyHostToDevice));
     KS_TRY_CUDA(c, cudaMemcpy(m + at_bs, c->h_ball_size, sizeof(c->h_ball_size),
                               cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(m + at_m32, ms32, sizeof(ms32), cudaMemcpyHostToDevice));
     c->ot = OffsetTables{(const uint32_t *)m,         (const int *)(m + at_s8),
                          (const uint32_t *)(m + at_r), (const int *)(m + at_sr),
                          (const int *)(m + at_bs),     (const uint32_t *)(m + at_w),
-                         (const int *)(m + at_sw)};
+                         (const int *)(m + at_sw),     (const uint8_t *)(m + at_m32)};
     // the classes up to dense_const_rmax() also go to constant memory
     KS_TRY_CUDA(c, dense_upload_constant_table(h8.data(), s8, hr.data(), sr));
     return KS_OK;

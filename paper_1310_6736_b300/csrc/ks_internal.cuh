@@ -55,6 +55,10 @@ struct VolDesc {
 //         dy != 0 and dz != 0 first, then the rows on the plane y = 0 or
 //         z = 0, longest first within each group.  Ball(r)'s rows:
 //         [rows_start[r], rows_start[r+1]).
+//   ms32: for every r = 0..32, 1 when the mean-shift block path may add
+//         its per-voxel sums as two 32-bit words (every column's count,
+//         sum(dx + r), sum(dy + r), sum(dz + r) below 2^11, 2^17, 2^16, 2^16
+//         with the rows dealt out as the block path deals them), else 0.
 struct OffsetTables {
     const uint32_t *c8;
     const int *c8_start;      // [kRmax + 2]
@@ -63,7 +67,13 @@ struct OffsetTables {
     const int *ball_size;     // [kRmax + 1]
     const uint32_t *rows;
     const int *rows_start;    // [kRmax + 2]
+    const uint8_t *ms32;      // [kRmax + 1]
 };
+
+// Columns per bin of the mean-shift block path for a window of nvox voxels.
+__host__ __device__ inline int ms_columns(int nvox) {
+    return nvox < 2048 ? 32 : (nvox < 8192 ? 64 : 128);
+}
 
 // ------------------------------------------------------------------ PTX
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {

@@ -405,10 +405,6 @@ __host__ __device__ inline int ms_block_radii(int r_min, int S, int B) {
     return r_max >= lo ? r_max - lo + 1 : 0;
 }
 
-__device__ __forceinline__ int ms_columns(int nvox) {
-    return nvox < 2048 ? 32 : (nvox < 8192 ? 64 : 128);
-}
-
 __device__ __forceinline__ void red_add_shared_u64(uint32_t addr, unsigned long long v) {
     asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(addr), "l"(v));
 }
@@ -429,21 +425,42 @@ __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long 
                         int *part, int *acc, const int P[3], int r) {
     const int B = J.vol.B;
     const int NC = ms_columns(__ldg(ot.ball_size + r));
+    // two 32-bit words per column where the row sums fit (ot.ms32), else
+    // one 64-bit word; the column area is B * NC * 8 bytes either way
+    const bool w32 = __ldg(ot.ms32 + r) != 0;
     for (int k = threadIdx.x; k < B * NC; k += blockDim.x) cols[k] = 0ull;
     __syncthreads();
     const uint8_t *c0 = voxel_ptr(J.vol, P);
     const int plane = (int)J.vol.plane, pitch = (int)J.vol.pitch;
-    const uint32_t col_addr = smem_u32(cols + (threadIdx.x & (NC - 1)));
+    const int col = threadIdx.x & (NC - 1);
+    const uint32_t col_addr = smem_u32(cols + col);
+    // 32-bit words: A of value v at a_addr + 4 NC v, B at b_addr + 4 NC v
+    uint32_t *colA = reinterpret_cast<uint32_t *>(cols);
+    const uint32_t a_addr = smem_u32(colA + col) - 4u * (uint32_t)NC;
+    const uint32_t b_addr = a_addr + 4u * (uint32_t)(B * NC);
     const uint32_t *rows = ot.rows + __ldg(ot.rows_start + r);
     const int nrows = __ldg(ot.rows_start + r + 1) - __ldg(ot.rows_start + r);
     for (int ri = threadIdx.x; ri < nrows; ri += blockDim.x) {
         int dy, dz, w;
         const unsigned long long row_inc = ms_row_word(__ldg(rows + ri), &dy, &dz, &w);
-        walk_row_masked(c0 + dz * plane + dy * pitch - w, w, [&](int t, uint32_t v) {
-            if (v != 0u)
-                red_add_shared_u64(col_addr + (v - 1) * NC * 8,
-                                   row_inc + ((unsigned long long)t << 11));
-        });
+        if (w32) {
+            // voxel t (dx = t - w) adds 1 + (t - w + r) << 11 to A and
+            // (dy + r) | (dz + r) << 16 to B
+            const uint32_t row_a = 1u + ((uint32_t)(r - w) << 11);
+            const uint32_t row_b = (uint32_t)(dy + r) | ((uint32_t)(dz + r) << 16);
+            walk_row_masked(c0 + dz * plane + dy * pitch - w, w, [&](int t, uint32_t v) {
+                if (v != 0u) {
+                    red_add_shared(a_addr + v * 4u * (uint32_t)NC, row_a + ((uint32_t)t << 11));
+                    red_add_shared(b_addr + v * 4u * (uint32_t)NC, row_b);
+                }
+            });
+        } else {
+            walk_row_masked(c0 + dz * plane + dy * pitch - w, w, [&](int t, uint32_t v) {
+                if (v != 0u)
+                    red_add_shared_u64(col_addr + (v - 1) * NC * 8,
+                                       row_inc + ((unsigned long long)t << 11));
+            });
+        }
     }
     __syncthreads();
     // column sums: warp w takes bins w, w + 8, ...; lane l reads columns l,
@@ -451,14 +468,23 @@ __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long 
     // conflicts) and the warp adds the unpacked fields with shuffles
     (void)part;
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int off = w32 ? r : 32;   // the offset added to dx, dy, dz
     for (int b = threadIdx.x >> 5; b < B; b += nw) {
         int c = 0, sx = 0, sy = 0, sz = 0;
         for (int k = lane; k < NC; k += 32) {
-            const unsigned long long x = cols[b * NC + k];
-            c += (int)(x & 0x7ffull);
-            sx += (int)((x >> 11) & 0x1ffffull);
-            sy += (int)((x >> 28) & 0x1ffffull);
-            sz += (int)((x >> 45) & 0x1ffffull);
+            if (w32) {
+                const uint32_t xa = colA[b * NC + k], xb = colA[(B + b) * NC + k];
+                c += (int)(xa & 0x7ffu);
+                sx += (int)(xa >> 11);
+                sy += (int)(xb & 0xffffu);
+                sz += (int)(xb >> 16);
+            } else {
+                const unsigned long long x = cols[b * NC + k];
+                c += (int)(x & 0x7ffull);
+                sx += (int)((x >> 11) & 0x1ffffull);
+                sy += (int)((x >> 28) & 0x1ffffull);
+                sz += (int)((x >> 45) & 0x1ffffull);
+            }
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
@@ -469,9 +495,9 @@ __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long 
         }
         if (lane == 0) {
             acc[4 * b] = c;
-            acc[4 * b + 1] = sx - 32 * c;
-            acc[4 * b + 2] = sy - 32 * c;
-            acc[4 * b + 3] = sz - 32 * c;
+            acc[4 * b + 1] = sx - off * c;
+            acc[4 * b + 2] = sy - off * c;
+            acc[4 * b + 3] = sz - off * c;
         }
     }
     __syncthreads();
