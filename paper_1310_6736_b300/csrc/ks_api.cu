@@ -637,50 +637,16 @@ std::vector<ClassLaunch> plan_class_queues(Ctx *c, const std::vector<SeedJob> &j
     return out;
 }
 
-cudaError_t fork_join_create(ForkJoin *f) {
-    cudaError_t e = cudaStreamCreateWithFlags(&f->aux, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->join, cudaEventDisableTiming);
-    if (e != cudaSuccess) fork_join_destroy(f);
-    return e;
-}
-
-void fork_join_destroy(ForkJoin *f) {
-    if (f->aux) cudaStreamSynchronize(f->aux);
-    if (f->fork) cudaEventDestroy(f->fork);
-    if (f->join) cudaEventDestroy(f->join);
-    if (f->aux) cudaStreamDestroy(f->aux);
-    *f = ForkJoin{};
-}
-
 cudaError_t launch_class_queues(Ctx *c, cudaStream_t s, int *d_status,
-                                const std::vector<ClassLaunch> &cls, const ForkJoin *fj) {
-    bool oct = false, ms = false;
-    for (const ClassLaunch &L : cls) {
-        if (L.q.n_tickets == 0) continue;
-        (L.kinds == (1 << kOctant) ? oct : ms) = true;
-    }
-    const bool split = fj && fj->aux && oct && ms;
+                                const std::vector<ClassLaunch> &cls) {
     cudaError_t e = cudaSuccess;
-    if (split) {
-        e = cudaEventRecord(fj->fork, s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(fj->aux, fj->fork, 0);
-        if (e != cudaSuccess) return e;
-    }
     for (const ClassLaunch &L : cls) {
         if (L.q.n_tickets == 0) continue;
-        const cudaStream_t st = split && L.kinds != (1 << kOctant) ? fj->aux : s;
-        e = cudaMemsetAsync(L.q.head, 0, 8, st);
+        e = cudaMemsetAsync(L.q.head, 0, 8, s);
         if (e == cudaSuccess)
-            e = launch_seeds(LaunchCtx{st, d_status, c->num_sms}, L.q, c->ot, c->T, c->L, L.max_B,
+            e = launch_seeds(LaunchCtx{s, d_status, c->num_sms}, L.q, c->ot, c->T, c->L, L.max_B,
                              L.max_S, L.kinds, true, L.grid);
         if (e != cudaSuccess) break;
-    }
-    if (split) {
-        // join even after an error, so that a capture still ends cleanly
-        const cudaError_t j = cudaEventRecord(fj->join, fj->aux);
-        const cudaError_t w = j == cudaSuccess ? cudaStreamWaitEvent(s, fj->join, 0) : j;
-        if (e == cudaSuccess) e = w;
     }
     return e;
 }
@@ -741,7 +707,6 @@ int ks_init(ks_ctx **out, size_t budget, void *stream, int device) {
             c->own_stream = true;
         }
     }
-    if (e == cudaSuccess) e = fork_join_create(&c->fj);
     void *p = nullptr;
     if (e == cudaSuccess) e = dev_alloc(c, &p, 256);
     c->d_status = (int *)p;
@@ -802,7 +767,6 @@ int ks_destroy(ks_ctx *ctx) {
         }
     }
     dev_free(c, c->batch_mem, c->batch_mem_bytes);
-    fork_join_destroy(&c->fj);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete ctx;
     return KS_OK;
@@ -1373,7 +1337,7 @@ int ks_batch_seeds(ks_ctx *ctx, const ks_vol *vols, const ks_params *params, int
         // capture [reset heads; persistent launches] as a graph
         cudaGraph_t graph;
         KS_TRY_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t le = launch_class_queues(c, c->stream, c->d_status, nb->classes, &c->fj);
+        cudaError_t le = launch_class_queues(c, c->stream, c->d_status, nb->classes);
         e = cudaStreamEndCapture(c->stream, &graph);
         if (le != cudaSuccess) e = le;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&nb->exec, graph, 0);
@@ -1391,7 +1355,7 @@ int ks_batch_seeds(ks_ctx *ctx, const ks_vol *vols, const ks_params *params, int
     if (use_graph) {
         KS_TRY_CUDA(c, cudaGraphLaunch(bg->exec, c->stream));
     } else {
-        KS_TRY_CUDA(c, launch_class_queues(c, c->stream, c->d_status, bg->classes, &c->fj));
+        KS_TRY_CUDA(c, launch_class_queues(c, c->stream, c->d_status, bg->classes));
     }
     prof_end(c, &rec, c->stream);
     for (int i = 0; i < n_vols; ++i) {

@@ -34,16 +34,6 @@ struct ProfRec {
 struct Request;        // serving (ks_serve.cu)
 struct ServeState;
 
-// A second stream with a fork and a join event: work forked onto aux runs
-// concurrently with the origin stream's and is joined back before the
-// origin continues (valid inside a stream capture too).
-struct ForkJoin {
-    cudaStream_t aux = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
-};
-cudaError_t fork_join_create(ForkJoin *f);
-void fork_join_destroy(ForkJoin *f);
-
 struct DenseTuneKey {
     int B, r_max, size_class;
     bool operator<(const DenseTuneKey &o) const {
@@ -84,8 +74,6 @@ struct Ctx {
     void *batch_mem = nullptr;
     size_t batch_mem_bytes = 0;
     unsigned long long *d_head = nullptr;
-    // octant and mean-shift class launches run side by side on stream and fj.aux
-    ForkJoin fj;
     // serving
     ServeState *serve = nullptr;           // owned; released by serve_shutdown
 
@@ -129,10 +117,11 @@ std::vector<ClassLaunch> plan_class_queues(Ctx *c, const std::vector<SeedJob> &j
                                            const std::vector<std::pair<int, int>> &segs,
                                            std::vector<uint8_t> &image, size_t plan_at,
                                            uint8_t *dev_base);
-// Octant classes run on s; with fj, mean-shift classes run concurrently on
-// fj->aux, joined back into s before it continues.
+// The classes run one after another on s, each a persistent launch over its
+// queue (running the octant and mean-shift classes side by side on two
+// streams made the batch slower: they compete for the same SMs).
 cudaError_t launch_class_queues(Ctx *c, cudaStream_t s, int *d_status,
-                                const std::vector<ClassLaunch> &cls, const ForkJoin *fj);
+                                const std::vector<ClassLaunch> &cls);
 
 }  // namespace ks
 

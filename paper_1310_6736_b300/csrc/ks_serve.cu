@@ -73,7 +73,6 @@ struct ServeState {
     std::thread th;
     cudaStream_t stream = nullptr;       // uploads, binning, seed waves
     cudaStream_t stream2 = nullptr;      // dense slabs, concurrent with the seeds
-    ForkJoin fj;                         // mean-shift classes beside the octant ones
     int *d_status = nullptr;
     size_t reserved = 0;
     void *qmem = nullptr;
@@ -252,7 +251,7 @@ static int launch_wave_seeds(Ctx *c, ServeState *S, std::vector<Request *> &join
     if (e != cudaSuccess) return cuda_err(c, e, "serving queue upload");
     ProfRec rec;
     prof_begin(c, "ks_seeds_persistent", S->stream, &rec);
-    e = launch_class_queues(c, S->stream, S->d_status, cls, &S->fj);
+    e = launch_class_queues(c, S->stream, S->d_status, cls);
     prof_end(c, &rec, S->stream);
     return cuda_err(c, e, "serving seed wave");
 }
@@ -349,8 +348,7 @@ static ServeState *ensure_serve(Ctx *c) {
         return nullptr;
     }
     void *p;
-    if (fork_join_create(&S->fj) != cudaSuccess || cudaMalloc(&p, 256) != cudaSuccess) {
-        fork_join_destroy(&S->fj);
+    if (cudaMalloc(&p, 256) != cudaSuccess) {
         cudaStreamDestroy(S->stream);
         cudaStreamDestroy(S->stream2);
         return nullptr;
@@ -376,7 +374,6 @@ void serve_shutdown(Ctx *c) {
     for (auto &kv : S->all) free_device(c, kv.second.get());
     dev_free(c, S->qmem, S->qbytes);
     cudaFree(S->d_status);
-    fork_join_destroy(&S->fj);
     cudaStreamDestroy(S->stream);
     cudaStreamDestroy(S->stream2);
     delete S;
