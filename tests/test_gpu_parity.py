@@ -655,3 +655,14 @@ def test_abmsod_team_split_does_not_change_results(ctx, ko, ks_mod):
         assert np.array_equal(o, outs[0])
     with pytest.raises(ks.KsError):
         ks.set_abmsod_team_radius(34)
+    # radii up to 20: large windows on one warp and on whole blocks
+    w = synth.workload("pet128")
+    grid = ko.seed_grid(w.dims, w.stride)[::16].copy()
+    outs = []
+    try:
+        for rt in (33, 1):
+            ks.set_abmsod_team_radius(rt)
+            outs.append(_ab_vs_oracle(ctx, ko, ks, w, seeds=grid, max_iter=8)[0])
+    finally:
+        ks.set_abmsod_team_radius(0)
+    assert np.array_equal(outs[0], outs[1])
