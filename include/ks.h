@@ -359,14 +359,15 @@ int ks_measure_smem_peak(ks_ctx *ctx, double *increments_per_s);
 /* Dense-sweep launch configuration chosen for (bins, r_max) by the
  * autotuner: path 0 = TMA brick in shared memory, 1 = direct L2 reads,
  * 2 = direct L2 reads with two centres (x and x + 32) per thread, 3 = four
- * adjacent centres per thread (r_max <= 25 only); warps per block; tile rows
- * in y and z. */
+ * adjacent centres per thread (r_max <= 25 only), 4 = path 3 with the
+ * previous-scale counts in tensor memory (r_max <= 25, bins <= 32, and not
+ * 8 or fewer); warps per block; tile rows in y and z. */
 int ks_dense_config(ks_ctx *ctx, int bins, int r_max, int *path, int *warps,
                     int *tile_y, int *tile_z);
 
 /* Force the dense launch configuration for every context of the process
  * (tests use it to cover both paths); path < 0 returns to the autotuner.
- * KS_EINVAL: path > 3, warps outside [1, 16] ([1, 8] for paths 2 and 3) or
+ * KS_EINVAL: path > 4, warps outside [1, 16] ([1, 8] for paths 2 to 4) or
  * tile_y * tile_z != warps.
  * A forced shape that does not fit a given (bins, r_max) is ignored for
  * that call. */

@@ -458,7 +458,7 @@ static std::vector<DenseConfig> dense_candidates(int B, int r_max) {
     std::vector<DenseConfig> out;
     const int shapes[][3] = {{1, 1, 1}, {2, 2, 1}, {2, 1, 2}, {4, 4, 1}, {4, 2, 2}, {8, 8, 1}, {8, 4, 2}, {8, 2, 4},
                              {16, 16, 1}, {16, 4, 4}, {16, 8, 2}, {16, 2, 8}};
-    for (int path = 0; path < 4; ++path)
+    for (int path = 0; path < 5; ++path)
         for (auto &s : shapes) {
             DenseConfig c{path, s[0], s[1], s[2]};
             if (dense_config_fits(c, B, r_max)) out.push_back(c);
@@ -1482,7 +1482,7 @@ int ks_force_dense_config(int path, int warps, int ty, int tz) {
         g_forced_path = -1;
         return KS_OK;
     }
-    if (path > 3 || warps < 1 || warps > (path >= 2 ? 8 : 16) || ty * tz != warps)
+    if (path > 4 || warps < 1 || warps > (path >= 2 ? 8 : 16) || ty * tz != warps)
         return KS_EINVAL;
     g_forced_path = path;
     g_forced_warps = warps;

@@ -18,6 +18,8 @@
 //   PATH 3 = (launch path 3, r_max <= 25) four adjacent centres per lane,
 //            128 per warp, whose four bins per offset come from two aligned
 //            32-bit loads and a funnel shift (k_dense4).
+//   PATH 4 = (launch path 4, 16 or 32 bins, r_max <= 25) PATH 3 with the
+//            previous-scale counts in tensor memory (k_dense4<B, true>).
 //   scale  = built incrementally: shell r (offsets o with ceil|o| == r, and
 //            everything up to r_min for the first scale) is added to the
 //            counts of r-1.
@@ -107,6 +109,83 @@ struct Src<1> {              // halo-padded volume in global memory
     }
 };
 
+// ---- tensor memory (TMEM) as per-thread storage for launch path 4
+// A block allocates 128 columns per group of four warps; warp w owns TMEM
+// lanes 32 (w & 3) .. 32 (w & 3) + 31 (the lane quarter its position in the
+// warpgroup may address) of columns 128 (w >> 2) .. + 127, and thread l of
+// the warp owns row 32 (w & 3) + l of them.  The 32x32b shape moves one
+// 32-bit word per thread and column.
+__device__ __forceinline__ void tm_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(dst_smem), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tm_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tm_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tm_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tm_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// The previous-scale words of one centre: NP = 17 (32 bins) or 9 (16 bins)
+// consecutive columns from ta.  A load waits for its data inside the same
+// asm statement, so no use of the registers can be scheduled before it.
+template <int NP>
+__device__ __forceinline__ void tm_load_prev(uint32_t ta, uint32_t (&v)[NP]) {
+    static_assert(NP == 17 || NP == 9, "TMEM previous words: 16 or 32 bins");
+    if constexpr (NP == 17) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+            "%10, %11, %12, %13, %14, %15}, [%17];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%16}, [%18];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+              "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+              "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16])
+            : "r"(ta), "r"(ta + 16u)
+            : "memory");
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%9];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%8}, [%10];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+              "=r"(v[6]), "=r"(v[7]), "=r"(v[8])
+            : "r"(ta), "r"(ta + 8u)
+            : "memory");
+    }
+}
+// Stores complete asynchronously; tm_wait_st before the next load of the
+// same columns.
+template <int NP>
+__device__ __forceinline__ void tm_store_prev(uint32_t ta, const uint32_t (&v)[NP]) {
+    static_assert(NP == 17 || NP == 9, "TMEM previous words: 16 or 32 bins");
+    if constexpr (NP == 17) {
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9, %10, "
+            "%11, %12, %13, %14, %15, %16, %17};\n\t"
+            "tcgen05.st.sync.aligned.32x32b.x1.b32 [%1], {%18};"
+            ::"r"(ta), "r"(ta + 16u), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]),
+              "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]),
+              "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16])
+            : "memory");
+    } else {
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9};\n\t"
+            "tcgen05.st.sync.aligned.32x32b.x1.b32 [%1], {%10};"
+            ::"r"(ta), "r"(ta + 8u), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]),
+              "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8])
+            : "memory");
+    }
+}
+__host__ __device__ constexpr int tm_columns(int warps) { return 128 * ((warps + 3) / 4); }
+
 // Shared-memory words of one lane.  Counters: one word per stored value
 // v = 0..B.  When every count fits in 16 bits (|Ball(r_max)| <= 65535, i.e.
 // r_max <= 25) two centres of a lane share each word (centre j in bits
@@ -114,13 +193,14 @@ struct Src<1> {              // halo-padded volume in global memory
 // 1 << 16 (j & 1)); otherwise each centre has its own 32-bit column.  After
 // the counters come the previous scale's counts of each centre: 16-bit
 // pairs (values 2w, 2w+1 in word w) when they fit, 32-bit words otherwise.
-template <int B, bool WIDE, int CPL>
+template <int B, bool WIDE, int CPL, bool TM = false>
 struct Words {
     static constexpr bool kPack = CPL >= 2 && !WIDE;
     static constexpr int kNW = B + 1;                          // counter words per column
     static constexpr int kNP = WIDE ? B + 1 : (B + 2) / 2;     // previous words per centre
     static constexpr int kCols = kPack ? CPL / 2 : CPL;        // counter columns
-    static constexpr int kPerLane = kCols * kNW + CPL * kNP;
+    // with TM the previous counts live in tensor memory, not here
+    static constexpr int kPerLane = kCols * kNW + (TM ? 0 : CPL * kNP);
     // word index of centre j's counter of value v / previous word w
     __host__ __device__ static constexpr int cnt(int j, int v) {
         return (kPack ? (j >> 1) : j) * kNW + v;
@@ -145,10 +225,12 @@ struct ScaleState {
 // After the shell of scale r (index i): the centre's exact N, the bin-order
 // entropy sum, D against the previous scale's counts (refreshed in the same
 // pass), H, the peak test at scale r - 1 and the optional H/W outputs.
-template <int B, bool WIDE, int CPL>
+// With TM the previous counts are the NP words at TMEM address tprev.
+template <int B, bool WIDE, int CPL, bool TM = false>
 __device__ __forceinline__ void scale_step(const DenseArgs &a, uint32_t cnt_lane, int j, int i,
-                                           int r, ScaleState &st, int64_t oidx, bool live) {
-    using Wd = Words<B, WIDE, CPL>;
+                                           int r, ScaleState &st, int64_t oidx, bool live,
+                                           uint32_t tprev = 0u) {
+    using Wd = Words<B, WIDE, CPL, TM>;
     constexpr int NP = Wd::kNP;
     auto word = [&](int w) { return cnt_lane + ((uint32_t)w << 7); };
     auto count = [&](int v) -> uint32_t {
@@ -175,9 +257,14 @@ __device__ __forceinline__ void scale_step(const DenseArgs &a, uint32_t cnt_lane
         }
     } else {
         // previous counts as 16-bit pairs: word w holds values 2w, 2w+1
+        uint32_t pv[NP];
+        if constexpr (TM) {
+            __syncwarp();                  // tcgen05 loads and stores are warp-wide
+            tm_load_prev<NP>(tprev, pv);
+        }
 #pragma unroll
         for (int w = 0; w < NP; ++w) {
-            const uint32_t pw = ld_shared_u32(word(Wd::prev(j, w)));
+            const uint32_t pw = TM ? pv[w] : ld_shared_u32(word(Wd::prev(j, w)));
             uint32_t c_lo = 0, c_hi = 0;
             if (2 * w >= 1 && 2 * w <= B) {
                 c_lo = count(2 * w);
@@ -187,7 +274,14 @@ __device__ __forceinline__ void scale_step(const DenseArgs &a, uint32_t cnt_lane
                 c_hi = count(2 * w + 1);
                 term(c_hi, pw >> 16);
             }
-            st_shared_u32(word(Wd::prev(j, w)), c_lo | (c_hi << 16));
+            if constexpr (TM)
+                pv[w] = c_lo | (c_hi << 16);
+            else
+                st_shared_u32(word(Wd::prev(j, w)), c_lo | (c_hi << 16));
+        }
+        if constexpr (TM) {
+            __syncwarp();
+            tm_store_prev<NP>(tprev, pv);
         }
     }
     const double H = entropy_from_sum(ssum, N, occ, a.L);
@@ -361,14 +455,30 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
 // from 3 bytes before x0 + o to 7 bytes after x0 + 127 + o: for |o| <= r_max
 // that stays inside the zeroed halo, the neighbouring row or the
 // allocation's 256 bytes of slack.
-template <int B>
-__global__ void __launch_bounds__(256) k_dense4(const DenseArgs a) {
+//
+// Launch path 4 (TM, 16 or 32 bins): the same kernel with each centre's
+// previous-scale counts in tensor memory (32 columns per centre, rows as
+// described at tm_alloc) instead of shared memory.  That halves the shared
+// memory per lane (66 instead of 134 words for 32 bins), so 16 warps fit on
+// an SM instead of 12; the host keeps the blocks per SM within the 512
+// TMEM columns, so the allocation never waits.
+template <int B, bool TM>
+__global__ void __launch_bounds__(256, TM ? 2 : 1) k_dense4(const DenseArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint32_t s_tmem;
     constexpr int CPL = 4;
-    using Wd = Words<B, false, CPL>;
+    using Wd = Words<B, false, CPL, TM>;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
+    uint32_t tm_base = 0u;
+    if constexpr (TM) {
+        if (warp == 0) tm_alloc(smem_u32(&s_tmem), (uint32_t)tm_columns(nwarps));
+        tm_fence_before();
+        __syncthreads();
+        tm_fence_after();
+        tm_base = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(128 * (warp >> 2));
+    }
     const int tx0 = blockIdx.x * 128, ty0 = blockIdx.y * a.ty, tz0 = a.z0 + blockIdx.z * a.tz;
     const int pz = (int)a.vol.plane, py = (int)a.vol.pitch;
     const Tab<true> tab{a.ot};
@@ -395,6 +505,16 @@ __global__ void __launch_bounds__(256) k_dense4(const DenseArgs a) {
 
 #pragma unroll 4
         for (int w = 0; w < Wd::kPerLane; ++w) st_shared_u32(word(w), 0u);
+        if constexpr (TM) {
+            constexpr int NP = Wd::kNP;
+            uint32_t z[NP];
+#pragma unroll
+            for (int w = 0; w < NP; ++w) z[w] = 0u;
+            __syncwarp();
+            tm_wait_st();                  // the previous row's last stores
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) tm_store_prev<NP>(tm_base + 32u * j, z);
+        }
 
         ScaleState st[CPL];
 #pragma unroll
@@ -436,10 +556,14 @@ __global__ void __launch_bounds__(256) k_dense4(const DenseArgs a) {
                     add4(bins4(c0, off));
                 }
             }
+            if constexpr (TM) {
+                __syncwarp();
+                tm_wait_st();              // the previous scale's stores
+            }
 #pragma unroll
             for (int j = 0; j < CPL; ++j)
-                scale_step<B, false, CPL>(a, cnt_lane, j, i, r, st[j], orow + cx + j,
-                                          cx + j < a.vol.nx);
+                scale_step<B, false, CPL, TM>(a, cnt_lane, j, i, r, st[j], orow + cx + j,
+                                              cx + j < a.vol.nx, tm_base + 32u * j);
         }
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
@@ -448,6 +572,13 @@ __global__ void __launch_bounds__(256) k_dense4(const DenseArgs a) {
                 a.out.s[orow + cx + j] = (uint8_t)st[j].sb;
             }
         }
+    }
+    if constexpr (TM) {
+        tm_wait_st();
+        tm_fence_before();
+        __syncthreads();
+        tm_fence_after();
+        if (warp == 0) tm_dealloc(s_tmem, (uint32_t)tm_columns(nwarps));
     }
 }
 
@@ -586,7 +717,7 @@ struct Geometry {
     size_t brick, cnt_off, cnt_bytes, mbar_off, total;
 };
 
-int centres_per_lane(const DenseConfig &c) { return c.path == 3 ? 4 : (c.path == 2 ? 2 : 1); }
+int centres_per_lane(const DenseConfig &c) { return c.path >= 3 ? 4 : (c.path == 2 ? 2 : 1); }
 
 Geometry geometry(const DenseConfig &c, int B_, int r_max) {
     Geometry g{};
@@ -594,7 +725,8 @@ Geometry geometry(const DenseConfig &c, int B_, int r_max) {
     // counter columns + previous-scale counts per lane (layout of Words)
     const int cpl = centres_per_lane(c);
     const bool wide = is_wide(r_max);
-    const int words = (cpl >= 2 && !wide ? cpl / 2 : cpl) * (B + 1) + cpl * (wide ? B + 1 : (B + 2) / 2);
+    const int words = (cpl >= 2 && !wide ? cpl / 2 : cpl) * (B + 1) +
+                      (c.path == 4 ? 0 : cpl * (wide ? B + 1 : (B + 2) / 2));
     g.padx = (r_max + 15) / 16 * 16;
     g.bx = (g.padx + 32 + r_max + 15) / 16 * 16;
     g.by = c.ty + 2 * r_max;
@@ -621,13 +753,29 @@ cudaError_t launch_t(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap 
     return cudaGetLastError();
 }
 
-template <int B>
+template <int B, bool TM>
 cudaError_t launch_adj4(const LaunchCtx &lc, const DenseArgs &a, const DenseConfig &cfg,
                         size_t smem) {
-    auto kern = k_dense4<B>;
+    auto kern = k_dense4<B, TM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
+    if constexpr (TM) {
+        // Pad the dynamic shared memory until the blocks that fit on an SM
+        // hold at most its 512 TMEM columns, so no tcgen05.alloc waits for
+        // another block's columns.
+        const int limit = 512 / tm_columns(cfg.warps);
+        for (;;) {
+            int nb = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, cfg.warps * 32, smem);
+            if (e != cudaSuccess) return e;
+            if (nb <= limit) break;
+            smem += 1024;
+            if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+    }
     dim3 grid((a.vol.nx + 127) / 128, (a.vol.ny + a.ty - 1) / a.ty, (a.z1 - a.z0 + a.tz - 1) / a.tz);
     kern<<<grid, cfg.warps * 32, smem, lc.stream>>>(a);
     return cudaGetLastError();
@@ -637,7 +785,12 @@ template <int B>
 cudaError_t launch_b(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap *tmap,
                      const DenseConfig &cfg, size_t smem) {
     const bool wide = is_wide(a.r_max);
-    if (cfg.path == 3) return wide ? cudaErrorInvalidValue : launch_adj4<B>(lc, a, cfg, smem);
+    if (cfg.path == 3) return wide ? cudaErrorInvalidValue : launch_adj4<B, false>(lc, a, cfg, smem);
+    if (cfg.path == 4) {
+        if constexpr (B == 16 || B == 32)
+            return wide ? cudaErrorInvalidValue : launch_adj4<B, true>(lc, a, cfg, smem);
+        return cudaErrorInvalidValue;
+    }
     if (cfg.path == 0)
         return wide ? launch_t<B, true, 0, 1>(lc, a, tmap, cfg, smem)
                     : launch_t<B, false, 0, 1>(lc, a, tmap, cfg, smem);
@@ -742,8 +895,9 @@ size_t dense_smem_bytes(const DenseConfig &c, int B, int r_max) {
 }
 
 bool dense_config_fits(const DenseConfig &c, int B, int r_max) {
-    if (c.path < 0 || c.path > 3) return false;
-    if (c.path == 3 && is_wide(r_max)) return false;      // counts need 16-bit packing
+    if (c.path < 0 || c.path > 4) return false;
+    if (c.path >= 3 && is_wide(r_max)) return false;      // counts need 16-bit packing
+    if (c.path == 4 && template_bins(B) != 16 && template_bins(B) != 32) return false;
     if (c.warps < 1 || c.warps > (c.path >= 2 ? 8 : 16) || c.ty * c.tz != c.warps) return false;
     const Geometry g = geometry(c, B, r_max);
     if (c.path == 0 && (g.bx > 256 || g.by > 256 || g.bz > 256)) return false;

@@ -74,7 +74,9 @@ def test_error_strings_and_no_device_path(libks):
     assert lib.ks_strerror(12345) == b"unknown status"
     assert lib.ks_destroy(None) == ks.KS_OK
     assert lib.ks_force_dense_config(0, 3, 2, 2) == ks.KS_EINVAL
-    assert lib.ks_force_dense_config(4, 8, 4, 2) == ks.KS_EINVAL
+    assert lib.ks_force_dense_config(5, 8, 4, 2) == ks.KS_EINVAL
+    assert lib.ks_force_dense_config(4, 4, 2, 2) == ks.KS_OK
+    assert lib.ks_force_dense_config(4, 16, 4, 4) == ks.KS_EINVAL
     assert lib.ks_force_dense_config(3, 16, 4, 4) == ks.KS_EINVAL
     assert lib.ks_force_dense_config(3, 4, 2, 2) == ks.KS_OK
     assert lib.ks_force_dense_config(2, 16, 4, 4) == ks.KS_EINVAL

@@ -113,7 +113,8 @@ def _dense_vs_oracle(ctx, ko, ks, bins_vol_raw, binning, r_min, r_max, w_norm=0,
 
 @pytest.mark.parametrize("cfg", [None, (0, 16, 4, 4), (0, 8, 2, 4), (0, 4, 4, 1), (1, 16, 4, 4),
                                  (1, 8, 8, 1), (2, 8, 4, 2), (2, 4, 1, 4), (3, 4, 2, 2),
-                                 (3, 1, 1, 1), (3, 8, 2, 4)])
+                                 (3, 1, 1, 1), (3, 8, 2, 4), (4, 4, 2, 2), (4, 1, 1, 1),
+                                 (4, 8, 2, 4), (4, 2, 1, 2)])
 def test_dense_spheres48_full_volume(ctx, ko, ks_mod, cfg):
     ks = ks_mod
     try:
@@ -133,7 +134,7 @@ def test_dense_spheres48_full_volume(ctx, ko, ks_mod, cfg):
     ((70, 3, 2), 16, 2, 12, 0),      # thin slab, radius larger than the volume
     ((75, 6, 4), 8, 24, 28, 0),      # r_max > 25: global offset table, 32-bit previous counts
 ])
-@pytest.mark.parametrize("path", [0, 1, 2, 3])
+@pytest.mark.parametrize("path", [0, 1, 2, 3, 4])
 def test_dense_random_volumes(ctx, ko, ks_mod, case, path):
     ks = ks_mod
     dims, B, r_min, r_max, wn = case
