@@ -26,7 +26,9 @@
 //   offsets= per radius class rho, the offsets with three nonzero
 //            components, stored once per set of 8 sign mirrors as (|dx|,
 //            |dy|, |dz|) and expanded with warp-uniform arithmetic, then every
-//            offset on a coordinate plane or axis, stored with its signs.
+//            offset on a coordinate plane or axis, stored with its signs
+//            (the four-centre kernel takes the plane offsets as sets of 4
+//            sign mirrors, the same way).
 //            For r_max <= 25 the tables sit in constant memory (warp-uniform
 //            reads through the constant cache), beyond that in global memory.
 //   counts = each centre owns a column of 32-bit words in shared memory
@@ -44,6 +46,7 @@
 //            fits, |Ball(25)| = 65267).  W and Y are evaluated only at
 //            entropy peaks.
 #include <type_traits>
+#include <vector>
 
 #include "ks_internal.cuh"
 
@@ -54,12 +57,25 @@ constexpr int kTmaPollLimit = 1 << 20;
 constexpr int kConstRmax = 25;            // largest r_max whose tables fit
 constexpr int kConstC8 = 7500;            // three-nonzero entries with rho <= 25: 7442
 constexpr int kConstRest = 5800;          // plane/axis entries with rho <= 25: 5731
+constexpr int kConstC4 = 1400;            // plane entries, one per 4 sign mirrors: 1395
+constexpr int kConstC1 = 160;             // axis offsets and the origin with rho <= 25: 151
 
 // Offset tables of radius classes 0..kConstRmax (layout as OffsetTables).
 __constant__ uint32_t c_c8[kConstC8];
 __constant__ uint32_t c_rest[kConstRest];
 __constant__ int c_c8_start[kConstRmax + 2];
 __constant__ int c_rest_start[kConstRmax + 2];
+// The rest entries again for the four-centre kernel, regrouped by mirrors:
+//   c4: offsets with exactly two nonzero components, one entry per set of 4
+//       sign mirrors: |dx| | |dy| << 8 | |dz| << 16 | plane << 24, plane 0
+//       for dz = 0, 1 for dy = 0, 2 for dx = 0;
+//   c1: offsets on an axis and the origin, one entry each, encoded as rest.
+// 4 (c4_start[rho+1] - c4_start[rho]) + c1_start[rho+1] - c1_start[rho] =
+// rest_start[rho+1] - rest_start[rho].
+__constant__ uint32_t c_c4[kConstC4];
+__constant__ uint32_t c_c1[kConstC1];
+__constant__ int c_c4_start[kConstRmax + 2];
+__constant__ int c_c1_start[kConstRmax + 2];
 
 struct DenseArgs {
     VolDesc vol;
@@ -525,7 +541,6 @@ __global__ void __launch_bounds__(256, TM ? 2 : 1) k_dense4(const DenseArgs a) {
             const int r = a.r_min + i;
             for (int rho = (i == 0 ? 0 : r); rho <= r; ++rho) {
                 const int k0 = tab.c8_start(rho), k1 = tab.c8_start(rho + 1);
-                const int k2 = tab.rest_start(rho), k3 = tab.rest_start(rho + 1);
                 uint32_t e = tab.c8(k0);
                 for (int k = k0; k < k1; ++k) {
                     const uint32_t en = tab.c8(k + 1);
@@ -548,9 +563,34 @@ __global__ void __launch_bounds__(256, TM ? 2 : 1) k_dense4(const DenseArgs a) {
                     for (int m = 0; m < 8; ++m) add4(b[m]);
                     e = en;
                 }
-#pragma unroll 2
-                for (int k = k2; k < k3; ++k) {
-                    const uint32_t f = tab.rest(k);
+                // offsets on a coordinate plane: 4 sign mirrors per entry,
+                // +-A +-C with C the component along the row when it is
+                // nonzero (plane 0 or 1), else the y part (a multiple of 16)
+                const int k4 = c_c4_start[rho], k5 = c_c4_start[rho + 1];
+                uint32_t g = c_c4[k4];
+                for (int k = k4; k < k5; ++k) {
+                    const uint32_t gn = c_c4[k + 1];
+                    const int pl = (int)(g >> 24);
+                    const int Yv = (int)((g >> 8) & 0xffu) * py;
+                    const int Zv = (int)((g >> 16) & 0xffu) * pz;
+                    const int A = pl == 0 ? Yv : Zv;
+                    const int C = pl == 2 ? Yv : (int)(g & 0xffu);
+                    const int sp = C & 3, sm = (-C) & 3;
+                    const int Ca = C - sp, Cc = C + sm;
+                    const int oa[4] = {A + Ca, A - Cc, -A + Ca, -A - Cc};
+                    uint32_t b[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const uint32_t *q = reinterpret_cast<const uint32_t *>(c0 + oa[m]);
+                        b[m] = __funnelshift_r(__ldg(q), __ldg(q + 1), 8 * ((m & 1) ? sm : sp));
+                    }
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) add4(b[m]);
+                    g = gn;
+                }
+                // offsets on an axis and the origin, one entry each
+                for (int k = c_c1_start[rho]; k < c_c1_start[rho + 1]; ++k) {
+                    const uint32_t f = c_c1[k];
                     const int off = ((int)((f >> 16) & 0xffu) - 64) * pz +
                                     ((int)((f >> 8) & 0xffu) - 64) * py + ((int)(f & 0xffu) - 64);
                     add4(bins4(c0, off));
@@ -835,12 +875,45 @@ cudaError_t dense_upload_constant_table(const uint32_t *c8, const int *c8_start,
                                         const uint32_t *rest, const int *rest_start) {
     const int n8 = c8_start[kConstRmax + 1], nr = rest_start[kConstRmax + 1];
     if (n8 > kConstC8 || nr > kConstRest) return cudaErrorInvalidValue;
+    // regroup the rest entries of every class into 4-mirror sets and the rest
+    std::vector<uint32_t> h4, h1;
+    int s4[kConstRmax + 2], s1[kConstRmax + 2];
+    for (int rho = 0; rho <= kConstRmax; ++rho) {
+        s4[rho] = (int)h4.size();
+        s1[rho] = (int)h1.size();
+        int n4 = 0;
+        for (int k = rest_start[rho]; k < rest_start[rho + 1]; ++k) {
+            const uint32_t f = rest[k];
+            const int d[3] = {(int)(f & 0xffu) - 64, (int)((f >> 8) & 0xffu) - 64,
+                              (int)((f >> 16) & 0xffu) - 64};
+            const int nz = (d[0] != 0) + (d[1] != 0) + (d[2] != 0);
+            if (nz <= 1) {
+                h1.push_back(f);
+            } else if (nz == 2) {
+                ++n4;
+                if (d[0] >= 0 && d[1] >= 0 && d[2] >= 0)      // the all-positive mirror
+                    h4.push_back((uint32_t)d[0] | ((uint32_t)d[1] << 8) | ((uint32_t)d[2] << 16) |
+                                 ((uint32_t)(d[2] == 0 ? 0 : (d[1] == 0 ? 1 : 2)) << 24));
+            } else {
+                return cudaErrorInvalidValue;                 // not a rest entry
+            }
+        }
+        if (n4 != 4 * ((int)h4.size() - s4[rho])) return cudaErrorInvalidValue;
+    }
+    s4[kConstRmax + 1] = (int)h4.size();
+    s1[kConstRmax + 1] = (int)h1.size();
+    if ((int)h4.size() + 1 > kConstC4 || (int)h1.size() > kConstC1) return cudaErrorInvalidValue;
+    h4.push_back(0u);                                         // the prefetch past the last entry
     cudaError_t e = cudaMemcpyToSymbol(c_c8, c8, n8 * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rest, rest, nr * sizeof(uint32_t));
     if (e == cudaSuccess)
         e = cudaMemcpyToSymbol(c_c8_start, c8_start, (kConstRmax + 2) * sizeof(int));
     if (e == cudaSuccess)
         e = cudaMemcpyToSymbol(c_rest_start, rest_start, (kConstRmax + 2) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_c4, h4.data(), h4.size() * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_c1, h1.data(), h1.size() * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_c4_start, s4, sizeof(s4));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_c1_start, s1, sizeof(s1));
     return e;
 }
 
