@@ -296,13 +296,35 @@ static int build_ball_tables(Ctx *c) {
                  sz[col] < (1 << 16);
         ms32[r] = ok ? 1 : 0;
     }
-    // one allocation: c8 | rest | rows | c8_start | rest_start | rows_start | ball_size | ms32
+    // Ball(r)'s entries of each kind once more per r, sorted by row (dz, dy,
+    // dx) for walks that take the whole ball at once
+    // (both encodings store dx, dy, dz in bytes 0, 1, 2 as monotone codes)
+    auto by_rows = [](const std::vector<uint32_t> &h, const int *st, std::vector<uint32_t> &out,
+                      int *ost) {
+        for (int r = 0; r <= kRmax; ++r) {
+            ost[r] = (int)out.size();
+            std::vector<uint32_t> e(h.begin(), h.begin() + st[r + 1]);
+            std::stable_sort(e.begin(), e.end(), [](uint32_t a, uint32_t b) {
+                return (a & 0xffffffu) < (b & 0xffffffu);     // (dz, dy, dx)
+            });
+            out.insert(out.end(), e.begin(), e.end());
+        }
+        ost[kRmax + 1] = (int)out.size();
+    };
+    std::vector<uint32_t> h8r, hrr;
+    int s8r[kRmax + 2], srr[kRmax + 2];
+    by_rows(h8, s8, h8r, s8r);
+    by_rows(hr, sr, hrr, srr);
+    // one allocation: c8 | rest | rows | c8_rows | rest_rows | c8_start | rest_start |
+    // rows_start | ball_size | ms32 | c8_rows_start | rest_rows_start
     const size_t b8 = h8.size() * 4, br = hr.size() * 4, bw = hw.size() * 4, bs = sizeof(s8);
+    const size_t b8r = h8r.size() * 4, brr = hrr.size() * 4;
     const size_t at_r = (b8 + 255) / 256 * 256, at_w = at_r + (br + 255) / 256 * 256;
-    const size_t at_s8 = at_w + (bw + 255) / 256 * 256;
+    const size_t at_8r = at_w + (bw + 255) / 256 * 256, at_rr = at_8r + (b8r + 255) / 256 * 256;
+    const size_t at_s8 = at_rr + (brr + 255) / 256 * 256;
     const size_t at_sr = at_s8 + 256, at_sw = at_sr + 256, at_bs = at_sw + 256;
-    const size_t at_m32 = at_bs + 256;
-    c->offsets_bytes = at_m32 + 256;
+    const size_t at_m32 = at_bs + 256, at_s8r = at_m32 + 256, at_srr = at_s8r + 256;
+    c->offsets_bytes = at_srr + 256;
     void *p;
     KS_TRY_CUDA(c, dev_alloc(c, &p, c->offsets_bytes));
     c->d_offsets = p;
@@ -316,10 +338,16 @@ static int build_ball_tables(Ctx *c) {
     KS_TRY_CUDA(c, cudaMemcpy(m + at_bs, c->h_ball_size, sizeof(c->h_ball_size),
                               cudaMemcpyHostToDevice));
     KS_TRY_CUDA(c, cudaMemcpy(m + at_m32, ms32, sizeof(ms32), cudaMemcpyHostToDevice));
-    c->ot = OffsetTables{(const uint32_t *)m,         (const int *)(m + at_s8),
-                         (const uint32_t *)(m + at_r), (const int *)(m + at_sr),
-                         (const int *)(m + at_bs),     (const uint32_t *)(m + at_w),
-                         (const int *)(m + at_sw),     (const uint8_t *)(m + at_m32)};
+    KS_TRY_CUDA(c, cudaMemcpy(m + at_8r, h8r.data(), b8r, cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(m + at_rr, hrr.data(), brr, cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(m + at_s8r, s8r, bs, cudaMemcpyHostToDevice));
+    KS_TRY_CUDA(c, cudaMemcpy(m + at_srr, srr, bs, cudaMemcpyHostToDevice));
+    c->ot = OffsetTables{(const uint32_t *)m,          (const int *)(m + at_s8),
+                         (const uint32_t *)(m + at_r),  (const int *)(m + at_sr),
+                         (const int *)(m + at_bs),      (const uint32_t *)(m + at_w),
+                         (const int *)(m + at_sw),      (const uint8_t *)(m + at_m32),
+                         (const uint32_t *)(m + at_8r), (const int *)(m + at_s8r),
+                         (const uint32_t *)(m + at_rr), (const int *)(m + at_srr)};
     // the classes up to dense_const_rmax() also go to constant memory
     KS_TRY_CUDA(c, dense_upload_constant_table(h8.data(), s8, hr.data(), sr));
     return KS_OK;

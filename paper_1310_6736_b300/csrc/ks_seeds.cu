@@ -145,13 +145,16 @@ __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *
         return (uint32_t)((rho > J.r_min ? rho - J.r_min : 0) * Bs * 4);
     };
     // three nonzero components (none on the disk dz = 0 of the quadrant climb)
+    // Ball(r_max)'s entries sorted by row: the lanes of a warp take
+    // neighbouring voxels of a few rows, so each mirror's loads touch few lines
     if (!J.planar) {
-        const int n8 = __ldg(ot.c8_start + J.r_max + 1);
+        const uint32_t *c8 = ot.c8_rows + __ldg(ot.c8_rows_start + J.r_max);
+        const int n8 = __ldg(ot.c8_rows_start + J.r_max + 1) - __ldg(ot.c8_rows_start + J.r_max);
         // two entries per round: their 16 loads are in flight together
         for (int k = threadIdx.x; k < n8; k += 2 * blockDim.x) {
             const int k2 = k + blockDim.x;
-            const uint32_t e0 = __ldg(ot.c8 + k);
-            const uint32_t e1 = k2 < n8 ? __ldg(ot.c8 + k2) : 0u;   // 0: the centre, v unused
+            const uint32_t e0 = __ldg(c8 + k);
+            const uint32_t e1 = k2 < n8 ? __ldg(c8 + k2) : 0u;   // 0: the centre, v unused
             uint32_t v[2][8], base[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -176,9 +179,10 @@ __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *
     }
     // on a coordinate plane or axis: every closed octant the voxel touches,
     // and the excess multiplicity
-    const int nr = __ldg(ot.rest_start + J.r_max + 1);
+    const uint32_t *rest = ot.rest_rows + __ldg(ot.rest_rows_start + J.r_max);
+    const int nr = __ldg(ot.rest_rows_start + J.r_max + 1) - __ldg(ot.rest_rows_start + J.r_max);
     for (int k = threadIdx.x; k < nr; k += blockDim.x) {
-        const uint32_t f = __ldg(ot.rest + k);
+        const uint32_t f = __ldg(rest + k);
         const int dx = (int)(f & 0xffu) - 64, dy = (int)((f >> 8) & 0xffu) - 64,
                   dz = (int)((f >> 16) & 0xffu) - 64;
         if (J.planar && dz != 0) continue;          // quadrant climb: the disk dz = 0 only
