@@ -298,8 +298,7 @@ static int build_ball_tables(Ctx *c) {
     }
     // Ball(r)'s entries of each kind once more per r, sorted by row (dz, dy,
     // dx) for walks that take the whole ball at once
-    // (both encodings store dx, dy, dz in bytes 0, 1, 2 as monotone codes)
-    auto by_rows = [](const std::vector<uint32_t> &h, const int *st, std::vector<uint32_t> &out,
+        auto by_rows = [](const std::vector<uint32_t> &h, const int *st, std::vector<uint32_t> &out,
                       int *ost) {
         for (int r = 0; r <= kRmax; ++r) {
             ost[r] = (int)out.size();
@@ -311,12 +310,27 @@ static int build_ball_tables(Ctx *c) {
         }
         ost[kRmax + 1] = (int)out.size();
     };
+    // rest offsets once per set of sign mirrors: the all-non-negative member
+    std::vector<uint32_t> hm;
+    int sm[kRmax + 2];
+    for (int rho = 0; rho <= kRmax; ++rho) {
+        sm[rho] = (int)hm.size();
+        for (int k = sr[rho]; k < sr[rho + 1]; ++k) {
+            const uint32_t f = hr[k];
+            const int dx = (int)(f & 0xffu) - 64, dy = (int)((f >> 8) & 0xffu) - 64,
+                      dz = (int)((f >> 16) & 0xffu) - 64;
+            if (dx >= 0 && dy >= 0 && dz >= 0)
+                hm.push_back((uint32_t)dx | ((uint32_t)dy << 8) | ((uint32_t)dz << 16) |
+                             ((uint32_t)rho << 24));
+        }
+    }
+    sm[kRmax + 1] = (int)hm.size();
     std::vector<uint32_t> h8r, hrr;
     int s8r[kRmax + 2], srr[kRmax + 2];
     by_rows(h8, s8, h8r, s8r);
-    by_rows(hr, sr, hrr, srr);
-    // one allocation: c8 | rest | rows | c8_rows | rest_rows | c8_start | rest_start |
-    // rows_start | ball_size | ms32 | c8_rows_start | rest_rows_start
+    by_rows(hm, sm, hrr, srr);
+    // one allocation: c8 | rest | rows | c8_rows | restm_rows | c8_start | rest_start |
+    // rows_start | ball_size | ms32 | c8_rows_start | restm_rows_start
     const size_t b8 = h8.size() * 4, br = hr.size() * 4, bw = hw.size() * 4, bs = sizeof(s8);
     const size_t b8r = h8r.size() * 4, brr = hrr.size() * 4;
     const size_t at_r = (b8 + 255) / 256 * 256, at_w = at_r + (br + 255) / 256 * 256;

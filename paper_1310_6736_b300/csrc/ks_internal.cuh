@@ -59,11 +59,15 @@ struct VolDesc {
 //         its per-voxel sums as two 32-bit words (every column's count,
 //         sum(dx + r), sum(dy + r), sum(dz + r) below 2^11, 2^17, 2^16, 2^16
 //         with the rows dealt out as the block path deals them), else 0.
-//   c8_rows, rest_rows: for every r = 0..32, the c8 and rest entries of
-//         Ball(r) again, sorted by row (dz, dy, dx) instead of by rho, at
-//         [c8_rows_start[r], c8_rows_start[r+1]) and likewise for rest.  A
-//         walk that visits all of Ball(r) at once (the octant pass) gives
-//         consecutive threads neighbouring voxels of one row.
+//   c8_rows: for every r = 0..32, the c8 entries of Ball(r) again, sorted
+//         by row (dz, dy, dx) instead of by rho, at [c8_rows_start[r],
+//         c8_rows_start[r+1]).  A walk that visits all of Ball(r) at once
+//         (the octant pass) gives consecutive threads neighbouring voxels
+//         of one row.
+//   restm_rows: the same for the rest offsets, one entry per set of sign
+//         mirrors encoded like c8 (|dx| | |dy| << 8 | |dz| << 16 |
+//         rho << 24, at least one component 0): its 8 mirrors name every
+//         distinct offset of the set 2^z times, z = its zero components.
 struct OffsetTables {
     const uint32_t *c8;
     const int *c8_start;      // [kRmax + 2]
@@ -75,8 +79,8 @@ struct OffsetTables {
     const uint8_t *ms32;      // [kRmax + 1]
     const uint32_t *c8_rows;
     const int *c8_rows_start;     // [kRmax + 2]
-    const uint32_t *rest_rows;
-    const int *rest_rows_start;   // [kRmax + 2]
+    const uint32_t *restm_rows;
+    const int *restm_rows_start;  // [kRmax + 2]
 };
 
 // Columns per bin of the mean-shift block path for a window of nvox voxels.

@@ -140,7 +140,7 @@ __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *
     __syncthreads();
     const uint8_t *c0 = voxel_ptr(J.vol, P);
     const int plane = (int)J.vol.plane, pitch = (int)J.vol.pitch;
-    const uint32_t cnt_s = smem_u32(cnt), extra_s = cnt_s + 8 * SB4;
+    const uint32_t cnt_s = smem_u32(cnt);
     auto shell = [&](int rho) {   // byte offset of the shell of radius class rho
         return (uint32_t)((rho > J.r_min ? rho - J.r_min : 0) * Bs * 4);
     };
@@ -177,33 +177,32 @@ __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *
             }
         }
     }
-    // on a coordinate plane or axis: every closed octant the voxel touches,
-    // and the excess multiplicity
-    const uint32_t *rest = ot.rest_rows + __ldg(ot.rest_rows_start + J.r_max);
-    const int nr = __ldg(ot.rest_rows_start + J.r_max + 1) - __ldg(ot.rest_rows_start + J.r_max);
+    // On a coordinate plane or axis: one entry per set of sign mirrors.  Its
+    // 8 mirrors name each distinct voxel once per closed octant that voxel
+    // touches (2^z times, z = the zero components), so octant m counts
+    // mirror m as for c8.  The first mirror of each distinct voxel (the
+    // bits of the zero components clear) adds the excess multiplicity
+    // 2^z - 1.  Quadrant climb: the entries on the disk dz = 0 only.
+    const uint32_t *restm = ot.restm_rows + __ldg(ot.restm_rows_start + J.r_max);
+    const int nr = __ldg(ot.restm_rows_start + J.r_max + 1) - __ldg(ot.restm_rows_start + J.r_max);
     for (int k = threadIdx.x; k < nr; k += blockDim.x) {
-        const uint32_t f = __ldg(rest + k);
-        const int dx = (int)(f & 0xffu) - 64, dy = (int)((f >> 8) & 0xffu) - 64,
-                  dz = (int)((f >> 16) & 0xffu) - 64;
-        if (J.planar && dz != 0) continue;          // quadrant climb: the disk dz = 0 only
-        const uint32_t a =
-            shell((int)(f >> 24)) + ((uint32_t)__ldg(c0 + dz * plane + dy * pitch + dx) << 2);
-        const int ax = dx > 0 ? 1 : (dx < 0 ? 2 : 3);
-        const int ay = dy > 0 ? 1 : (dy < 0 ? 2 : 3);
-        const int az = dz > 0 ? 1 : (dz < 0 ? 2 : 3);
-        uint32_t mult = 0;
-        for (int jz = 0; jz < 2; ++jz) {
-            if (!(az & (1 << jz))) continue;
-            for (int jy = 0; jy < 2; ++jy) {
-                if (!(ay & (1 << jy))) continue;
-                for (int jx = 0; jx < 2; ++jx) {
-                    if (!(ax & (1 << jx))) continue;
-                    red_add_shared(cnt_s + (uint32_t)(jx | (jy << 1) | (jz << 2)) * SB4 + a, 1u);
-                    ++mult;
-                }
-            }
-        }
-        red_add_shared(extra_s + a, mult - 1u);
+        const uint32_t f = __ldg(restm + k);
+        const int X = (int)(f & 0xffu), Yb = (int)((f >> 8) & 0xffu), Zb = (int)((f >> 16) & 0xffu);
+        if (J.planar && Zb != 0) continue;
+        const uint32_t zm = (X == 0 ? 1u : 0u) | (Yb == 0 ? 2u : 0u) | (Zb == 0 ? 4u : 0u);
+        const uint32_t excess = (1u << __popc(zm)) - 1u;
+        const int Y = Yb * pitch, Z = Zb * plane;
+        const uint32_t base = cnt_s + shell((int)(f >> 24));
+        const int o[8] = {Z + Y + X, Z + Y - X, Z - Y + X, Z - Y - X,
+                          Y - Z + X, Y - Z - X, -Z - Y + X, -Z - Y - X};
+        uint32_t v[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = __ldg(c0 + o[m]);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) red_add_shared(base + (uint32_t)m * SB4 + (v[m] << 2), 1u);
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+            if ((m & zm) == 0u) red_add_shared(base + 8u * SB4 + (v[m] << 2), excess);
     }
     __syncthreads();
     // prefix over shells per (octant, value) column, eight shells at a time:
