@@ -123,8 +123,9 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) {
 
 // ---------------------------------------------------------------- octant
 // Closed-octant histograms of every shell at P into cnt[j][si][v] and the
-// plane/axis multiplicity excess into extra[si][v] (j = 8), both then turned
-// into prefix sums over shells (histograms of Ball(r_min + si)).  Each
+// plane/axis multiplicity excess into extra[si][v] (j = 8); the octant
+// histograms are then turned into prefix sums over shells (histograms of
+// Ball(r_min + si)), the excess only when kb_from_pass needs it.  Each
 // histogram has B + 1 words indexed by the stored value v; word 0 (not
 // counted) is a dummy that is never read, so a voxel costs no branch.
 // The walk runs over the offset tables of Ball(r_max): an entry with three
@@ -205,10 +206,12 @@ __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *
             if ((m & zm) == 0u) red_add_shared(base + 8u * SB4 + (v[m] << 2), excess);
     }
     __syncthreads();
-    // prefix over shells per (octant, value) column, eight shells at a time:
-    // the eight loads are issued before any store of the group
-    for (int col = threadIdx.x; col < 9 * Bs; col += blockDim.x) {    // 8 octants + excess
-        const int j = col / Bs, b = col % Bs;
+    // prefix over shells per (octant, counted value) column, eight shells at
+    // a time: the eight loads are issued before any store of the group.  The
+    // dummy value 0 is never read, and the excess column is summed by
+    // kb_from_pass, the only reader: 8 B columns, one round for B = 32.
+    for (int col = threadIdx.x; col < 8 * B; col += blockDim.x) {
+        const int j = col / B, b = 1 + col % B;
         uint32_t *p = cnt + j * S * Bs + b;
         uint32_t run = 0;
         for (int s0 = 0; s0 < S; s0 += 8) {
@@ -277,6 +280,15 @@ __device__ void octant_step(const SeedJob &J, const double *hb, int step[3]) {
 __device__ void kb_from_pass(const SeedJob &J, const double *T, const double *L, uint32_t *cnt,
                              uint32_t *full, double *hb, SeedShared &sh, ks_seed_result *o) {
     const int B = J.vol.B, S = J.S, Bs = B + 1;
+    // the excess per shell (left unsummed by the pass) -> per Ball(r)
+    for (int b = 1 + threadIdx.x; b < Bs; b += blockDim.x) {
+        uint32_t run = 0;
+        for (int si = 0; si < S; ++si) {
+            run += full[si * Bs + b];
+            full[si * Bs + b] = run;
+        }
+    }
+    __syncthreads();
     for (int k = threadIdx.x; k < S * Bs; k += blockDim.x) {
         uint32_t s = 0;
         for (int j = 0; j < 8; ++j) s += cnt[j * S * Bs + k];
