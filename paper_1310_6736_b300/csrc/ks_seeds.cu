@@ -801,7 +801,7 @@ struct Layout {
 // instantiation per combination, so each gets its own register allocation.
 template <int KINDS>
 __global__ void __launch_bounds__(KINDS == 1 ? kOctThreads : kSeedThreads,
-                                  KINDS == 1 ? 4 : (KINDS == 2 ? 2 : 1))
+                                  KINDS == 1 ? 6 : (KINDS == 2 ? 2 : 1))
     k_seeds(const SeedQueue q, const OffsetTables ot,
                                                         const double *__restrict__ T,
                                                         const double *__restrict__ L,
