@@ -221,9 +221,11 @@ class Context:
         return out
 
     # ------------------------------------------------------------ hot path
-    def dense_saliency(self, v, params, shape, want_hw=False, out=None):
-        """Dense sweep.  out=None: host numpy outputs.  out=(Y, s) torch CUDA
-        tensors: results stay on the device."""
+    def dense_saliency(self, v, params, shape, want_hw=False, out=None, host_out=None):
+        """Dense sweep.  out=None: host numpy outputs, written into host_out =
+        (Y, s) when given (caller-owned, e.g. pinned, C-contiguous float64 and
+        uint8 arrays of the volume's shape).  out=(Y, s) torch CUDA tensors:
+        results stay on the device."""
         nz, ny, nx = shape
         S = params.r_max - params.r_min + 1
         if out is not None:
@@ -232,8 +234,15 @@ class Context:
                                                 C.c_void_p(Y.data_ptr()), C.c_void_p(s.data_ptr()),
                                                 1), "ks_dense_saliency")
             return Y, s
-        Y = np.empty(shape, np.float64)
-        s = np.empty(shape, np.uint8)
+        if host_out is not None:
+            Y, s = host_out
+            if (Y.shape != tuple(shape) or s.shape != tuple(shape) or Y.dtype != np.float64
+                    or s.dtype != np.uint8 or not Y.flags.c_contiguous
+                    or not s.flags.c_contiguous):
+                raise ValueError("host_out: C-contiguous float64 and uint8 arrays of the volume's shape")
+        else:
+            Y = np.empty(shape, np.float64)
+            s = np.empty(shape, np.uint8)
         H = np.empty((nz * ny * nx, S), np.float64) if want_hw else None
         W = np.empty((nz * ny * nx, S), np.float64) if want_hw else None
         self._check(lib().ks_dense_saliency_ex(
@@ -254,10 +263,20 @@ class Context:
         s = np.ascontiguousarray(seeds, dtype=np.int32).reshape(-1, 3)
         return C.c_void_p(s.ctypes.data), s.shape[0], s
 
-    def seed_climb(self, v, params, seeds=None, want_traj=False, out=None, planar=False):
+    @staticmethod
+    def _host_records(host_out, n, dtype):
+        """A caller-owned record array of at least n entries, or a new one."""
+        if host_out is None:
+            return np.zeros(max(n, 1), dtype)
+        if host_out.dtype != dtype or not host_out.flags.c_contiguous or len(host_out) < max(n, 1):
+            raise ValueError(f"host_out: a C-contiguous array of at least {n} {dtype} records")
+        return host_out
+
+    def seed_climb(self, v, params, seeds=None, want_traj=False, out=None, planar=False,
+                   host_out=None):
         """Octant climb (planar=True: the quadrant climb of Alg. 1 as printed,
         disks in each seed's z-slice).  out=None: host SEED_RESULT array (and
-        trajectories when want_traj).  out=a CUDA tensor of at least n * 64
+        trajectories when want_traj), written into host_out when given.  out=a CUDA tensor of at least n * 64
         bytes: the records stay on the device; returns their count n."""
         fn, name = ((lib().ks_quadrant_climb, "ks_quadrant_climb") if planar else
                     (lib().ks_seed_climb, "ks_seed_climb"))
@@ -269,7 +288,7 @@ class Context:
             return self._seeds_to_device(fn, name, v, params, sp, ns,
                                          out, n * SEED_RESULT.itemsize, SEED_RESULT.itemsize,
                                          extra=(None,))
-        out = np.zeros(max(n, 1), SEED_RESULT)
+        out = self._host_records(host_out, n, SEED_RESULT)
         traj = np.zeros((max(n, 1), params.max_iter + 1, 3), np.int32) if want_traj else None
         got = C.c_int64()
         self._check(fn(self.h, int(v), C.byref(params), sp, ns,
@@ -278,8 +297,9 @@ class Context:
         out = out[:got.value]
         return (out, traj[:got.value]) if want_traj else out
 
-    def meanshift(self, v, params, seeds=None, out=None):
-        """Mean shift for every (seed, r).  out=None: host MS_RESULT array.
+    def meanshift(self, v, params, seeds=None, out=None, host_out=None):
+        """Mean shift for every (seed, r).  out=None: host MS_RESULT array
+        (written into host_out when given).
         out=a CUDA tensor of at least n * S * 48 bytes: the records stay on
         the device; returns their count n * S."""
         sp, ns, keep = self._seeds_arg(seeds)
@@ -288,7 +308,7 @@ class Context:
         if out is not None:
             return self._seeds_to_device(lib().ks_meanshift, "ks_meanshift", v, params, sp, ns,
                                          out, n * S * MS_RESULT.itemsize, MS_RESULT.itemsize)
-        out = np.zeros(max(n * S, 1), MS_RESULT)
+        out = self._host_records(host_out, n * S, MS_RESULT)
         got = C.c_int64()
         self._check(lib().ks_meanshift(self.h, int(v), C.byref(params), sp, ns,
                                        C.c_void_p(out.ctypes.data), out.shape[0], C.byref(got), 0),
