@@ -231,46 +231,55 @@ __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *
 // Alg. 1's update from the octant entropies hb[j*S + si]: eps_j = max over
 // scales (the smallest r on ties), d_j = k_j sigma_j, delta = sum_j eps_j
 // d_j / sum_j eps_j summed over j = 0..7, rounded half away from zero.
-// Called by warp 0: lane j < 8 finds eps_j and k_j, lane 0 forms the sums.
+// Called by warp 0 (every operation of the sequential form, spread over the
+// lanes: 24 products at once, the four chains side by side, three divisions).
 __device__ void octant_step(const SeedJob &J, const double *hb, int step[3]) {
     const int S = J.S;
     const int lane = threadIdx.x & 31;
-    double best = 0.0;
-    int k = J.r_min;
-    if (lane < 8) {
-        best = hb[lane * S];
-        for (int si = 1; si < S; ++si) {
-            const double h = hb[lane * S + si];
-            if (h > best) {
-                best = h;
-                k = J.r_min + si;
-            }
+    // eps_j and k_j: lane 4j + q scans the scales q, q + 4, ... of octant j
+    // (the first of equal values kept), then the four lanes of octant j
+    // combine, the smaller scale winning ties: the same maximum and the same
+    // smallest maximising scale as one scan over all scales
+    const int oj = lane >> 2, q = lane & 3;
+    double best = -1.0;                       // below every entropy (H >= 0)
+    int sb = S;                               // loses every tie
+    for (int si = q; si < S; si += 4) {
+        const double h = hb[oj * S + si];
+        if (h > best) {
+            best = h;
+            sb = si;
         }
     }
-    double eps[8];
-    int kopt[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        eps[j] = __shfl_sync(0xffffffffu, best, j);
-        kopt[j] = __shfl_sync(0xffffffffu, k, j);
-    }
-    if (lane == 0) {
-        // quadrant climb: the four quadrants j = 0..3 (closed on the plane
-        // z = 0, so their histograms are the disk's), sigma without z
-        const int nj = J.planar ? 4 : 8;
-        double num[3] = {0.0, 0.0, 0.0}, den = 0.0;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (j >= nj) break;
-            const int sg[3] = {(j & 1) ? -1 : 1, (j & 2) ? -1 : 1,
-                               J.planar ? 0 : ((j & 4) ? -1 : 1)};
-            for (int a = 0; a < 3; ++a)
-                num[a] = __dadd_rn(num[a], __dmul_rn(eps[j], (double)(kopt[j] * sg[a])));
-            den = __dadd_rn(den, eps[j]);
+    for (int o = 1; o <= 2; o <<= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int os = __shfl_xor_sync(0xffffffffu, sb, o);
+        if (ob > best || (ob == best && os < sb)) {
+            best = ob;
+            sb = os;
         }
-        for (int a = 0; a < 3; ++a)
-            step[a] = den == 0.0 ? 0 : (int)round(__ddiv_rn(num[a], den));
     }
+    // the terms: lane 8a + j holds eps_j k_j sigma_ja (a < 3) or eps_j (a = 3)
+    // quadrant climb: the four quadrants j = 0..3 (closed on the plane z = 0,
+    // so their histograms are the disk's), sigma without z
+    const int nj = J.planar ? 4 : 8;
+    const int ta = lane >> 3, tj = lane & 7;
+    const double eps = __shfl_sync(0xffffffffu, best, 4 * tj);
+    const int kj = J.r_min + __shfl_sync(0xffffffffu, sb, 4 * tj);
+    double term = eps;
+    if (ta < 3) {
+        const int sg = ta == 2 && J.planar ? 0 : (((tj >> ta) & 1) ? -1 : 1);
+        term = __dmul_rn(eps, (double)(kj * sg));
+    }
+    // lane a < 4 adds chain a over j = 0..nj-1 in order: three numerators
+    // and the denominator; lanes a < 3 divide
+    double sum = 0.0;
+    for (int j = 0; j < nj; ++j) {
+        const double t = __shfl_sync(0xffffffffu, term, 8 * (lane & 3) + j);
+        if (lane < 4) sum = __dadd_rn(sum, t);
+    }
+    const double den = __shfl_sync(0xffffffffu, sum, 3);
+    if (lane < 3) step[lane] = den == 0.0 ? 0 : (int)round(__ddiv_rn(sum, den));
 }
 
 // Kadir-Brady on the full ball at the centre of the last octant pass: the
