@@ -94,3 +94,18 @@ def test_binding_refuses_missing_library(monkeypatch, tmp_path):
     monkeypatch.setattr(ks, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(ImportError):
         ks.lib()
+
+
+def test_host_record_arrays_are_checked():
+    """host_out= takes a caller-owned record array (e.g. in pinned memory):
+    the right dtype, C-contiguous, and room for every record."""
+    from paper_1310_6736_b300 import ks
+    ok = np.zeros(5, ks.SEED_RESULT)
+    assert ks.Context._host_records(ok, 5, ks.SEED_RESULT) is ok
+    assert len(ks.Context._host_records(None, 3, ks.MS_RESULT)) == 3
+    with pytest.raises(ValueError):
+        ks.Context._host_records(np.zeros(4, ks.SEED_RESULT), 5, ks.SEED_RESULT)
+    with pytest.raises(ValueError):
+        ks.Context._host_records(np.zeros(5, ks.MS_RESULT), 5, ks.SEED_RESULT)
+    with pytest.raises(ValueError):
+        ks.Context._host_records(np.zeros(10, ks.SEED_RESULT)[::2], 5, ks.SEED_RESULT)

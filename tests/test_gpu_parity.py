@@ -153,6 +153,40 @@ def test_dense_random_volumes(ctx, ko, ks_mod, case, path):
         ks.force_dense_config(-1)
 
 
+def test_host_out_into_pinned_arrays_equals_default_outputs(ctx, ks_mod):
+    """The end-to-end path: the raw volume in pinned host memory and every
+    result written into caller-owned pinned arrays gives the same records and
+    maps as the binding's own host outputs."""
+    import torch
+    ks = ks_mod
+    w = synth.workload("spheres48")
+    p = _params(ks, w)
+    nz, ny, nx = w.volume.shape
+
+    def pinned(nbytes):
+        return torch.empty(nbytes, dtype=torch.uint8, pin_memory=True).numpy()
+
+    vol = pinned(w.volume.nbytes).view(w.volume.dtype).reshape(w.volume.shape)
+    vol[...] = w.volume
+    v = ctx.create_volume(w.volume, w.binning)
+    Y0, s0 = ctx.dense_saliency(v, p, (nz, ny, nx))
+    o0, m0 = ctx.seed_climb(v, p), ctx.meanshift(v, p)
+    ctx.release_volume(v)
+    Y = pinned(nx * ny * nz * 8).view(np.float64).reshape(nz, ny, nx)
+    s = pinned(nx * ny * nz).reshape(nz, ny, nx)
+    o = pinned(len(o0) * ks.SEED_RESULT.itemsize).view(ks.SEED_RESULT)
+    m = pinned(len(m0) * ks.MS_RESULT.itemsize).view(ks.MS_RESULT)
+    v = ctx.create_volume(vol, w.binning)
+    ctx.dense_saliency(v, p, (nz, ny, nx), host_out=(Y, s))
+    got_o = ctx.seed_climb(v, p, host_out=o)
+    got_m = ctx.meanshift(v, p, host_out=m)
+    ctx.release_volume(v)
+    assert np.array_equal(Y, Y0) and np.array_equal(s, s0)
+    assert np.array_equal(got_o, o0) and np.array_equal(got_m, m0)
+    with pytest.raises(ValueError):
+        ctx.dense_saliency(v, p, (nz, ny, nx), host_out=(Y[:, :, :-1], s))
+
+
 def test_dense_pet128_full_size_sampled(ctx, ko, ks_mod):
     """The bench workload (128x128x64 float32, 32 bins, r=4..20) at full size,
     in the autotuned launch configuration; checked on sampled centres."""
