@@ -228,6 +228,24 @@ int ks_meanshift(ks_ctx *ctx, ks_vol vol, const ks_params *params,
                  ks_ms_result *out, int64_t capacity, int64_t *n_out,
                  int out_on_device);
 
+/* The whole detection pass of one volume in one call: the dense Kadir-Brady
+ * sweep (as ks_dense_saliency, Sec. 1 and the opening of Sec. 2.1), the
+ * octant climb (as ks_seed_climb, Alg. 1) and the uniform-target mean shift
+ * (as ks_meanshift, Eq. 4-6) from the default seed grid.  The results are
+ * those of the three separate calls, bit for bit.  The dense sweep runs on
+ * the device's highest-priority stream and the seed searches on its lowest,
+ * both forked from the context's stream and joined to it before return, so
+ * the seed blocks fill the SMs that the dense sweep's last wave leaves free.
+ * Outputs as in the three calls (Y and s_best: nx*ny*nz each; oct: one
+ * record per seed; ms: one per (seed, r)); all on the device or all on the
+ * host (out_on_device).  KS_EINVAL when a capacity is too small (the
+ * counts are still written to n_oct / n_ms). */
+int ks_saliency(ks_ctx *ctx, ks_vol vol, const ks_params *params,
+                double *Y, uint8_t *s_best,
+                ks_seed_result *oct, int64_t oct_capacity, int64_t *n_oct,
+                ks_ms_result *ms, int64_t ms_capacity, int64_t *n_ms,
+                int out_on_device);
+
 /* Adaptive-bandwidth mean shift (ABMSOD; Sec. 2.3, Alg. 2, Eq. 6-7) to the
  * uniform pmf HQ_b = 1/B for every (seed, r) item, r = r_min..r_max, item =
  * seed * S + (r - r_min), starting at the seed with H = r^2 I.  The window

@@ -593,14 +593,17 @@ int run_dense(Ctx *c, cudaStream_t s, Volume *v, const ks_params *p, const Dense
     return launch_dense_cfg(c, s, v, p->r_min, p->r_max, p->w_norm, cfg, dev_out, z0, z1);
 }
 
-static int check_status(Ctx *c) {
+// Waits for stream s (the context's stream by default) and reports the
+// device status word.
+static int check_status(Ctx *c, cudaStream_t s = nullptr) {
+    if (!s) s = c->stream;
     int h = 0;
-    cudaError_t e = cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaError_t e = cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_err(c, e, "sync");
     if (h) {
-        cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
-        cudaStreamSynchronize(c->stream);
+        cudaMemsetAsync(c->d_status, 0, sizeof(int), s);
+        cudaStreamSynchronize(s);
         if (h & kStatusBadInput)
             return set_err(c, KS_EINVAL, "a listed centre lies outside the volume");
         if (h & kStatusMisaligned)
@@ -809,6 +812,13 @@ int ks_destroy(ks_ctx *ctx) {
         }
     }
     dev_free(c, c->batch_mem, c->batch_mem_bytes);
+    for (cudaEvent_t ev : {c->ev_fork, c->ev_hi, c->ev_lo})
+        if (ev) cudaEventDestroy(ev);
+    for (cudaStream_t ps : {c->hi_stream, c->lo_stream})
+        if (ps) {
+            cudaStreamSynchronize(ps);
+            cudaStreamDestroy(ps);
+        }
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete ctx;
     return KS_OK;
@@ -1075,8 +1085,9 @@ namespace ks {
 
 // Shared by ks_seed_climb, ks_meanshift and the batched launch: seeds to the
 // device, one SeedJob, one queue segment.
-static int seeds_to_device(Ctx *c, Volume *v, const ks_params *p, const int32_t *seeds_xyz,
-                           int64_t n_in, std::vector<int32_t> *host, int32_t **dev) {
+static int seeds_to_device(Ctx *c, cudaStream_t s, Volume *v, const ks_params *p,
+                           const int32_t *seeds_xyz, int64_t n_in, std::vector<int32_t> *host,
+                           int32_t **dev) {
     if (seeds_xyz) {
         host->assign(seeds_xyz, seeds_xyz + 3 * n_in);
         for (int64_t i = 0; i < n_in; ++i) {
@@ -1092,7 +1103,7 @@ static int seeds_to_device(Ctx *c, Volume *v, const ks_params *p, const int32_t 
     if (!*dev) return cuda_err(c, e, "seed buffer");
     if (!host->empty())
         KS_TRY_CUDA(c, cudaMemcpyAsync(*dev, host->data(), host->size() * 4,
-                                       cudaMemcpyHostToDevice, c->stream));
+                                       cudaMemcpyHostToDevice, s));
     return KS_OK;
 }
 
@@ -1104,13 +1115,14 @@ struct QueueBuf {
 
 // Lay jobs + segments out in one device buffer (c->batch_mem, grown on
 // demand), copy them, and fill a SeedQueue.
-static int upload_queue(Ctx *c, const std::vector<SeedJob> &jobs, const std::vector<int64_t> &ss,
-                        const std::vector<int> &sk, const std::vector<int> &sj, SeedQueue *q) {
+static int upload_queue(Ctx *c, cudaStream_t s, const std::vector<SeedJob> &jobs,
+                        const std::vector<int64_t> &ss, const std::vector<int> &sk,
+                        const std::vector<int> &sj, SeedQueue *q) {
     const size_t bj = jobs.size() * sizeof(SeedJob);
     const size_t bs = ss.size() * 8, bk = sk.size() * 4, bjj = sj.size() * 4;
     const size_t need = 256 + bj + bs + bk + bjj + 64;
     if (c->batch_mem_bytes < need) {
-        cudaStreamSynchronize(c->stream);
+        cudaStreamSynchronize(s);
         dev_free(c, c->batch_mem, c->batch_mem_bytes);
         c->batch_mem = nullptr;
         c->batch_mem_bytes = 0;
@@ -1134,25 +1146,28 @@ static int upload_queue(Ctx *c, const std::vector<SeedJob> &jobs, const std::vec
     q->n_segs = (int)sk.size();
     q->n_tickets = ss.back();
     q->head = (unsigned long long *)c->batch_mem;
-    KS_TRY_CUDA(c, cudaMemcpyAsync(c->batch_mem, h.data(), off, cudaMemcpyHostToDevice, c->stream));
+    KS_TRY_CUDA(c, cudaMemcpyAsync(c->batch_mem, h.data(), off, cudaMemcpyHostToDevice, s));
     return KS_OK;
 }
 
-static int run_queue(Ctx *c, const SeedQueue &q, int max_B, int max_S, int kinds, bool persistent) {
+static int run_queue(Ctx *c, cudaStream_t s, const SeedQueue &q, int max_B, int max_S, int kinds,
+                     bool persistent) {
     if (q.n_tickets == 0) return KS_OK;
     const int grid =
         persistent ? c->num_sms * seed_blocks_per_sm(max_B, max_S, kinds) : (int)q.n_tickets;
     ProfRec rec;
-    prof_begin(c, persistent ? "ks_seeds_persistent" : "ks_seeds", c->stream, &rec);
+    prof_begin(c, persistent ? "ks_seeds_persistent" : "ks_seeds", s, &rec);
     cudaError_t e =
-        launch_seeds(c->lc(), q, c->ot, c->T, c->L, max_B, max_S, kinds, persistent, grid);
-    prof_end(c, &rec, c->stream);
+        launch_seeds(c->lc(s), q, c->ot, c->T, c->L, max_B, max_S, kinds, persistent, grid);
+    prof_end(c, &rec, s);
     return cuda_err(c, e, "seed launch");
 }
 
 static int seed_common(Ctx *c, ks_vol vol, const ks_params *p, const int32_t *seeds_xyz,
                        int64_t n_seeds, int kind, void *out, int64_t capacity, int64_t *n_out,
-                       int32_t *traj, int out_on_device, int planar = 0) {
+                       int32_t *traj, int out_on_device, int planar = 0,
+                       cudaStream_t s = nullptr) {
+    if (!s) s = c->stream;
     std::string why;
     int st = validate_params(p, &why);
     if (st) return set_err(c, st, why);
@@ -1162,7 +1177,7 @@ static int seed_common(Ctx *c, ks_vol vol, const ks_params *p, const int32_t *se
     if (!v) return set_err(c, KS_ENOTFOUND, "unknown volume");
     std::vector<int32_t> hs;
     int32_t *ds;
-    st = seeds_to_device(c, v, p, seeds_xyz, n_seeds, &hs, &ds);
+    st = seeds_to_device(c, s, v, p, seeds_xyz, n_seeds, &hs, &ds);
     if (st) return st;
     const int64_t ns = (int64_t)hs.size() / 3;
     const int S = p->r_max - p->r_min + 1;
@@ -1194,24 +1209,24 @@ static int seed_common(Ctx *c, ks_vol vol, const ks_params *p, const int32_t *se
     SeedQueue q{};
     if (kind == kOctant) {
         // one block per seed
-        st = upload_queue(c, {J}, {0, ns}, {kOctant}, {0}, &q);
+        st = upload_queue(c, s, {J}, {0, ns}, {kOctant}, {0}, &q);
         if (st) return st;
-        st = run_queue(c, q, v->binning.bins, S, 1 << kOctant, false);
+        st = run_queue(c, s, q, v->binning.bins, S, 1 << kOctant, false);
     } else {
         // block-path items, then warp-path items, on a persistent launch
         const int64_t nb = seed_tickets(kMeanShift, ns, p->r_min, S, J.vol.B);
         const int64_t nw = seed_tickets(kMsWarp, ns, p->r_min, S, J.vol.B);
-        st = upload_queue(c, {J}, {0, nb, nb + nw}, {kMeanShift, kMsWarp}, {0, 0}, &q);
+        st = upload_queue(c, s, {J}, {0, nb, nb + nw}, {kMeanShift, kMsWarp}, {0, 0}, &q);
         if (st) return st;
-        st = run_queue(c, q, v->binning.bins, S, 1 << kMeanShift, true);
+        st = run_queue(c, s, q, v->binning.bins, S, 1 << kMeanShift, true);
     }
     if (st) return st;
     if (!out_on_device && n_items) {
-        KS_TRY_CUDA(c, cudaMemcpyAsync(out, dout, n_items * rec, cudaMemcpyDeviceToHost, c->stream));
+        KS_TRY_CUDA(c, cudaMemcpyAsync(out, dout, n_items * rec, cudaMemcpyDeviceToHost, s));
         if (traj && kind == kOctant)
-            KS_TRY_CUDA(c, cudaMemcpyAsync(traj, dtraj, traj_bytes, cudaMemcpyDeviceToHost, c->stream));
+            KS_TRY_CUDA(c, cudaMemcpyAsync(traj, dtraj, traj_bytes, cudaMemcpyDeviceToHost, s));
     }
-    return check_status(c);
+    return check_status(c, s);
 }
 
 }  // namespace ks
@@ -1242,6 +1257,57 @@ int ks_meanshift(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_t
                        n_out, nullptr, out_on_device);
 }
 
+int ks_saliency(ks_ctx *ctx, ks_vol vol, const ks_params *params, double *Y, uint8_t *s_best,
+                ks_seed_result *oct, int64_t oct_capacity, int64_t *n_oct, ks_ms_result *ms,
+                int64_t ms_capacity, int64_t *n_ms, int out_on_device) {
+    if (!ctx) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    std::string why;
+    int st = validate_params(params, &why);
+    if (st) return set_err(c, st, why);
+    if (!Y || !s_best) return set_err(c, KS_EINVAL, "Y_best / s_best is NULL");
+    Volume *v = find_volume(c, vol);
+    if (!v) return set_err(c, KS_ENOTFOUND, "unknown volume");
+    if (!c->hi_stream) {
+        int least = 0, greatest = 0;
+        KS_TRY_CUDA(c, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        KS_TRY_CUDA(c, cudaStreamCreateWithPriority(&c->hi_stream, cudaStreamNonBlocking, greatest));
+        KS_TRY_CUDA(c, cudaStreamCreateWithPriority(&c->lo_stream, cudaStreamNonBlocking, least));
+        for (cudaEvent_t *ev : {&c->ev_fork, &c->ev_hi, &c->ev_lo})
+            KS_TRY_CUDA(c, cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+    }
+    const size_t n = (size_t)v->nx * v->ny * v->nz;
+    DenseOut o{Y, s_best, nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    if (!out_on_device) {
+        o.Y = (double *)scratch(c, kScY, n * 8, &e);
+        if (o.Y) o.s = (uint8_t *)scratch(c, kScS, n, &e);
+        if (e != cudaSuccess) return cuda_err(c, e, "dense outputs");
+    }
+    KS_TRY_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
+    KS_TRY_CUDA(c, cudaStreamWaitEvent(c->hi_stream, c->ev_fork, 0));
+    KS_TRY_CUDA(c, cudaStreamWaitEvent(c->lo_stream, c->ev_fork, 0));
+    // the dense sweep first, at the highest priority: the seed searches'
+    // blocks are dispatched as its last wave leaves SMs free
+    st = run_dense(c, c->hi_stream, v, params, o, 0, v->nz);
+    if (st == KS_OK && !out_on_device) {
+        KS_TRY_CUDA(c, cudaMemcpyAsync(Y, o.Y, n * 8, cudaMemcpyDeviceToHost, c->hi_stream));
+        KS_TRY_CUDA(c, cudaMemcpyAsync(s_best, o.s, n, cudaMemcpyDeviceToHost, c->hi_stream));
+    }
+    KS_TRY_CUDA(c, cudaEventRecord(c->ev_hi, c->hi_stream));
+    if (st == KS_OK)
+        st = seed_common(c, vol, params, nullptr, 0, kOctant, oct, oct_capacity, n_oct, nullptr,
+                         out_on_device, 0, c->lo_stream);
+    if (st == KS_OK)
+        st = seed_common(c, vol, params, nullptr, 0, kMeanShift, ms, ms_capacity, n_ms, nullptr,
+                         out_on_device, 0, c->lo_stream);
+    KS_TRY_CUDA(c, cudaEventRecord(c->ev_lo, c->lo_stream));
+    KS_TRY_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_hi, 0));
+    KS_TRY_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_lo, 0));
+    const int st2 = check_status(c);
+    return st != KS_OK ? st : st2;
+}
+
 int ks_abmsod(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_t *seeds_xyz,
               int64_t n_seeds, ks_abmsod_result *out, int64_t capacity, int64_t *n_out,
               int out_on_device) {
@@ -1256,7 +1322,7 @@ int ks_abmsod(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_t *s
     if (!v) return set_err(c, KS_ENOTFOUND, "unknown volume");
     std::vector<int32_t> hs;
     int32_t *ds;
-    st = seeds_to_device(c, v, params, seeds_xyz, n_seeds, &hs, &ds);
+    st = seeds_to_device(c, c->stream, v, params, seeds_xyz, n_seeds, &hs, &ds);
     if (st) return st;
     const int64_t ns = (int64_t)hs.size() / 3;
     const int S = params->r_max - params->r_min + 1;

@@ -76,6 +76,10 @@ struct Ctx {
     unsigned long long *d_head = nullptr;
     // serving
     ServeState *serve = nullptr;           // owned; released by serve_shutdown
+    // ks_saliency: the dense sweep on the device's highest-priority stream,
+    // the seed searches on its lowest, forked from and joined to `stream`
+    cudaStream_t hi_stream = nullptr, lo_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_hi = nullptr, ev_lo = nullptr;
 
     LaunchCtx lc(cudaStream_t s = nullptr) const {
         return LaunchCtx{s ? s : stream, d_status, num_sms};

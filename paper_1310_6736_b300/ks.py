@@ -91,6 +91,8 @@ SIGNATURES = {
                           C.POINTER(C.c_int64), _I]),
     "ks_abmsod": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _I64,
                        C.POINTER(C.c_int64), _I]),
+    "ks_saliency": (_I, [_P, _I64, C.POINTER(ks_params), _P, _P, _P, _I64, C.POINTER(C.c_int64),
+                         _P, _I64, C.POINTER(C.c_int64), _I]),
     "ks_dense_points": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _P, _P, _P, _I]),
     "ks_octant_candidates": (_I, [_P, _P, _I64, _P, _I]),
     "ks_meanshift_candidates": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _I]),
@@ -340,6 +342,46 @@ class Context:
         self._check(fn(self.h, int(v), C.byref(params), sp, ns, C.c_void_p(out.data_ptr()), cap,
                        C.byref(got), *extra, 1), name)
         return got.value
+
+    def saliency(self, v, params, shape, out=None, host_out=None):
+        """Dense sweep, octant climb and mean shift of one volume in one call
+        (the dense sweep on a high-priority stream, the seed searches beside
+        it on a low-priority one; results equal the three separate calls).
+        out=(Y, s, oct, ms) torch CUDA tensors (oct and ms as bytes): results
+        stay on the device; returns the record counts.  Otherwise host
+        outputs, written into host_out=(Y, s, oct, ms) when given; returns
+        (Y, s, SEED_RESULT array, MS_RESULT array)."""
+        nz, ny, nx = shape
+        n = self.seed_count(v, params)
+        S = params.r_max - params.r_min + 1
+        n_oct, n_ms = C.c_int64(), C.c_int64()
+        if out is not None:
+            Y, s, o, m = out
+            need = [(Y, nx * ny * nz * 8), (s, nx * ny * nz), (o, n * SEED_RESULT.itemsize),
+                    (m, n * S * MS_RESULT.itemsize)]
+            if any(not t.is_cuda or t.numel() * t.element_size() < b for t, b in need):
+                raise ValueError("saliency: out must be CUDA tensors large enough for every result")
+            self._check(lib().ks_saliency(
+                self.h, int(v), C.byref(params), C.c_void_p(Y.data_ptr()), C.c_void_p(s.data_ptr()),
+                C.c_void_p(o.data_ptr()), o.numel() * o.element_size() // SEED_RESULT.itemsize,
+                C.byref(n_oct), C.c_void_p(m.data_ptr()),
+                m.numel() * m.element_size() // MS_RESULT.itemsize, C.byref(n_ms), 1), "ks_saliency")
+            return n_oct.value, n_ms.value
+        if host_out is not None:
+            Y, s, o, m = host_out
+            if (Y.shape != tuple(shape) or s.shape != tuple(shape) or Y.dtype != np.float64
+                    or s.dtype != np.uint8 or not Y.flags.c_contiguous
+                    or not s.flags.c_contiguous):
+                raise ValueError("host_out: C-contiguous float64 and uint8 arrays of the volume's shape")
+        else:
+            Y, s, o, m = np.empty(shape, np.float64), np.empty(shape, np.uint8), None, None
+        o = self._host_records(o, n, SEED_RESULT)
+        m = self._host_records(m, n * S, MS_RESULT)
+        self._check(lib().ks_saliency(
+            self.h, int(v), C.byref(params), C.c_void_p(Y.ctypes.data), C.c_void_p(s.ctypes.data),
+            C.c_void_p(o.ctypes.data), len(o), C.byref(n_oct), C.c_void_p(m.ctypes.data), len(m),
+            C.byref(n_ms), 0), "ks_saliency")
+        return Y, s, o[:n_oct.value], m[:n_ms.value]
 
     def dense_points(self, v, params, xyz, want_hw=False):
         """Kadir-Brady at listed centres ((n, 3) int xyz): (Y_best, s_best[, H, W])."""

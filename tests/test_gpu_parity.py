@@ -187,6 +187,38 @@ def test_host_out_into_pinned_arrays_equals_default_outputs(ctx, ks_mod):
         ctx.dense_saliency(v, p, (nz, ny, nx), host_out=(Y[:, :, :-1], s))
 
 
+@pytest.mark.parametrize("name", ["spheres48", "pet128"])
+def test_saliency_call_equals_the_three_calls(ctx, ks_mod, name):
+    """ks_saliency (dense sweep on a high-priority stream, seed searches
+    beside it on a low-priority one) gives the three separate calls' results
+    bit for bit, with host and with device outputs."""
+    import torch
+    ks = ks_mod
+    w = synth.workload(name)
+    p = _params(ks, w)
+    shape = w.volume.shape
+    v = ctx.create_volume(w.volume, w.binning)
+    try:
+        Y0, s0 = ctx.dense_saliency(v, p, shape)
+        o0, m0 = ctx.seed_climb(v, p), ctx.meanshift(v, p)
+        Y1, s1, o1, m1 = ctx.saliency(v, p, shape)
+        assert np.array_equal(Y1, Y0) and np.array_equal(s1, s0)
+        assert np.array_equal(o1, o0) and np.array_equal(m1, m0)
+        Yd = torch.empty(shape, dtype=torch.float64, device="cuda")
+        sd = torch.empty(shape, dtype=torch.uint8, device="cuda")
+        od = torch.empty(len(o0) * ks.SEED_RESULT.itemsize, dtype=torch.uint8, device="cuda")
+        md = torch.empty(len(m0) * ks.MS_RESULT.itemsize, dtype=torch.uint8, device="cuda")
+        assert ctx.saliency(v, p, shape, out=(Yd, sd, od, md)) == (len(o0), len(m0))
+        torch.cuda.synchronize()
+        assert np.array_equal(Yd.cpu().numpy(), Y0) and np.array_equal(sd.cpu().numpy(), s0)
+        assert np.array_equal(od.cpu().numpy().view(ks.SEED_RESULT), o0)
+        assert np.array_equal(md.cpu().numpy().view(ks.MS_RESULT), m0)
+        with pytest.raises(ValueError):
+            ctx.saliency(v, p, shape, out=(Yd, sd, od[:64], md))
+    finally:
+        ctx.release_volume(v)
+
+
 def test_dense_pet128_full_size_sampled(ctx, ko, ks_mod):
     """The bench workload (128x128x64 float32, 32 bins, r=4..20) at full size,
     in the autotuned launch configuration; checked on sampled centres."""
