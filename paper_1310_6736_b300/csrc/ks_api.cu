@@ -1166,7 +1166,7 @@ static int run_queue(Ctx *c, cudaStream_t s, const SeedQueue &q, int max_B, int 
 static int seed_common(Ctx *c, ks_vol vol, const ks_params *p, const int32_t *seeds_xyz,
                        int64_t n_seeds, int kind, void *out, int64_t capacity, int64_t *n_out,
                        int32_t *traj, int out_on_device, int planar = 0,
-                       cudaStream_t s = nullptr) {
+                       cudaStream_t s = nullptr, bool wait = true) {
     if (!s) s = c->stream;
     std::string why;
     int st = validate_params(p, &why);
@@ -1226,7 +1226,8 @@ static int seed_common(Ctx *c, ks_vol vol, const ks_params *p, const int32_t *se
         if (traj && kind == kOctant)
             KS_TRY_CUDA(c, cudaMemcpyAsync(traj, dtraj, traj_bytes, cudaMemcpyDeviceToHost, s));
     }
-    return check_status(c, s);
+    // wait = false: the caller joins stream s and checks the status itself
+    return wait ? check_status(c, s) : KS_OK;
 }
 
 }  // namespace ks
@@ -1297,10 +1298,10 @@ int ks_saliency(ks_ctx *ctx, ks_vol vol, const ks_params *params, double *Y, uin
     KS_TRY_CUDA(c, cudaEventRecord(c->ev_hi, c->hi_stream));
     if (st == KS_OK)
         st = seed_common(c, vol, params, nullptr, 0, kOctant, oct, oct_capacity, n_oct, nullptr,
-                         out_on_device, 0, c->lo_stream);
+                         out_on_device, 0, c->lo_stream, false);
     if (st == KS_OK)
         st = seed_common(c, vol, params, nullptr, 0, kMeanShift, ms, ms_capacity, n_ms, nullptr,
-                         out_on_device, 0, c->lo_stream);
+                         out_on_device, 0, c->lo_stream, false);
     KS_TRY_CUDA(c, cudaEventRecord(c->ev_lo, c->lo_stream));
     KS_TRY_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_hi, 0));
     KS_TRY_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_lo, 0));
