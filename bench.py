@@ -850,6 +850,54 @@ def run_abmsod(args):
     return 0
 
 
+def run_bin(args):
+    """Binning alone, an HBM-bound kernel: three raw types on a 512x512x256
+    volume (far above the 126 MB L2).  Per type, the ks_bin kernels' CUDA-event
+    time over --steps calls of ks_create_volume from device memory; the
+    algorithmic bytes are the raw read (float32 also its min/max pass) plus one
+    byte written per voxel."""
+    import torch
+    from paper_1310_6736_b300 import ks
+    nz, ny, nx = 256, 512, 512
+    n = nx * ny * nz
+    peaks, kind = _peaks()
+    ctx = ks.Context()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    cases = [
+        ("uint8, v >> 3 (32 bins)", torch.randint(0, 256, (nz, ny, nx), generator=g,
+                                                  device="cuda", dtype=torch.uint8),
+         {"kind": 0, "bins": 32, "shift": 3, "lo": 0, "hi": 255}, 2),
+        ("int16, clamp to [0, 2047] >> 5 (64 bins)",
+         torch.randint(-100, 2200, (nz, ny, nx), generator=g, device="cuda", dtype=torch.int16),
+         {"kind": 0, "bins": 64, "shift": 5, "lo": 0, "hi": 2047}, 3),
+        ("float32, affine over [vmin, vmax] (32 bins; min/max pass)",
+         torch.rand((nz, ny, nx), generator=g, device="cuda", dtype=torch.float32) * 100.0,
+         {"kind": 1, "bins": 32, "shift": 0, "lo": 0, "hi": 0}, 9),
+    ]
+    rows = []
+    for name, raw, binning, bpv in cases:
+        for _ in range(max(args.warmup, 3)):
+            ctx.release_volume(ctx.create_volume(raw, binning))
+        ctx.set_profiling(True)
+        for _ in range(args.steps):
+            ctx.release_volume(ctx.create_volume(raw, binning))
+        ms, launches = ctx.kernel_time("ks_bin")
+        ctx.set_profiling(False)
+        t = ms / max(1, launches) * 1e-3
+        gbs = n * bpv / t / 1e9
+        rows.append({"raw": name, "voxels": n, "bytes_per_voxel": bpv, "ms": t * 1e3,
+                     "achieved_gbs": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"]})
+    ctx.close()
+    line = {"metric": "binning bandwidth (algorithmic bytes / kernel time)",
+            "value": min(r["frac_of_hbm"] for r in rows), "unit": "fraction of measured HBM copy",
+            "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"{nx}x{ny}x{nz} random volumes", "peak_hbm_gbs": peaks["hbm_gbs"],
+                       "peaks_source": kind, "rows": rows}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_mode(args):
     import torch
     from paper_1310_6736_b300 import build, ks, synth
@@ -857,6 +905,8 @@ def run_mode(args):
     torch.cuda.set_device(0)
     if args.mode == "abmsod":
         return run_abmsod(args)
+    if args.mode == "bin":
+        return run_bin(args)
     if args.mode == "window":
         ctx = ks.Context()
         rows = [run_window(ctx, ks, synth, name) for name in ("mr256", "mr256w")]
@@ -902,7 +952,7 @@ def main():
                     help="run one part of the step only (profiling)")
     ap.add_argument("--dense-config", default="",
                     help="force the dense launch shape: path,warps,tile_y,tile_z")
-    ap.add_argument("--mode", choices=["step", "batch", "serve", "window", "abmsod"],
+    ap.add_argument("--mode", choices=["step", "batch", "serve", "window", "abmsod", "bin"],
                     default="step",
                     help="batch: batched vs plain launches; serve: request-stream latency; "
                          "window: full range vs tumour window level on the MR workload; "

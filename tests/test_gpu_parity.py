@@ -68,7 +68,8 @@ def test_binning_bit_exact(ctx, ko, name):
 
 @pytest.mark.parametrize("dims,dtype", [((37, 23, 19), np.uint8), ((33, 5, 7), np.int16),
                                         ((17, 16, 3), np.float32), ((1, 1, 1), np.uint8),
-                                        ((64, 2, 2), np.int16)])
+                                        ((64, 2, 2), np.int16), ((128, 3, 2), np.uint8),
+                                        ((192, 2, 3), np.int16)])
 def test_binning_ragged_and_kinds(ctx, ko, dims, dtype):
     rng = np.random.default_rng(sum(dims))
     nx, ny, nz = dims
@@ -81,7 +82,14 @@ def test_binning_ragged_and_kinds(ctx, ko, dims, dtype):
                 {"kind": 2, "bins": 40, "shift": 5, "lo": 100, "hi": 1300}]
     else:
         vol = rng.integers(0, 256, size=(nz, ny, nx)).astype(np.uint8)
+        # rows of 64-voxel multiples take the four-run path; the first three
+        # there take the bytewise form (lo = 0, hi >= 255: the clamp never
+        # applies), the next two the general one (hi < 255; lo > 0)
         bins = [{"kind": 0, "bins": 16, "shift": 4, "lo": 0, "hi": 255},
+                {"kind": 0, "bins": 32, "shift": 3, "lo": 0, "hi": 255},
+                {"kind": 0, "bins": 64, "shift": 2, "lo": 0, "hi": 255},
+                {"kind": 0, "bins": 32, "shift": 3, "lo": 0, "hi": 200},
+                {"kind": 0, "bins": 16, "shift": 4, "lo": 10, "hi": 255},
                 {"kind": 2, "bins": 7, "shift": 4, "lo": 30, "hi": 140}]
     for b in bins:
         v = ctx.create_volume(vol, b)
