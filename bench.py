@@ -320,6 +320,8 @@ def run_ks(args):
 
     # ---- roofline of the dominant kernel (dense sweep: shared-memory bound)
     smem_peak = ctx.measure_smem_peak()
+    fp64_rate = ctx.measure_fp64_rate()                # the FP64 sums' pipe, for context
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     upd_per_launch = n_vox * ks_ball_size(w.r_max)     # window-voxel updates per launch
     dense_avg_s = dense_ms / max(1, dense_n) * 1e-3
     achieved = upd_per_launch / dense_avg_s
@@ -366,6 +368,10 @@ def run_ks(args):
                                    "frac": upd_per_launch / (alone_ms / max(1, alone_n) * 1e-3)
                                    / smem_peak,
                                    "launches": alone_n}},
+            "micro_peaks": {"smem_increments_per_s": smem_peak, "fp64_dadd_per_s": fp64_rate,
+                            "fp64_dadd_per_sm_clock": fp64_rate / (n_sms * 1e6 *
+                                                                   (clocks.get("sm_mhz") or 2032.0)),
+                            "how": "ks_measure_smem_peak / ks_measure_fp64_rate micro-kernels"},
             "kernels_note": "event times per launch on its own stream: the seed launches "
                             "start beside the dense sweep and include the wait for free SMs",
             "kernels": {"ks_dense": {"ms": dense_ms, "launches": dense_n},

@@ -374,6 +374,11 @@ int ks_kernel_time(ks_ctx *ctx, const char *prefix, double *ms_total, int64_t *l
  * micro-kernel: the denominator of the histogram kernels' roofline. */
 int ks_measure_smem_peak(ks_ctx *ctx, double *increments_per_s);
 
+/* FP64 addition rate of this device (__dadd_rn lane operations per second):
+ * a micro-kernel of independent addition chains on every SM.  The entropy
+ * sums and the seed steps are FP64 additions in a fixed order. */
+int ks_measure_fp64_rate(ks_ctx *ctx, double *dadd_per_s);
+
 /* Dense-sweep launch configuration chosen for (bins, r_max) by the
  * autotuner: path 0 = TMA brick in shared memory, 1 = direct L2 reads,
  * 2 = direct L2 reads with two centres (x and x + 32) per thread, 3 = four

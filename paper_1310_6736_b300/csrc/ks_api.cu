@@ -1555,6 +1555,35 @@ int ks_measure_smem_peak(ks_ctx *ctx, double *per_s) {
     return KS_OK;
 }
 
+int ks_measure_fp64_rate(ks_ctx *ctx, double *per_s) {
+    if (!ctx || !per_s) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    cudaError_t e;
+    double *sink = (double *)scratch(c, kScTune, 4096 * 8, &e);
+    if (!sink) return cuda_err(c, e, "fp64 rate");
+    const int blocks = c->num_sms * 8, iters = 512;      // 64 warps per SM
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(a, c->stream);
+        c->launches++;
+        e = launch_fp64_peak(c->lc(), sink, blocks, iters);
+        cudaEventRecord(b, c->stream);
+        if (e != cudaSuccess) break;
+        cudaEventSynchronize(b);
+        float ms;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_err(c, e, "fp64 rate");
+    *per_s = (double)blocks * 256.0 * iters * 8.0 / (best * 1e-3);
+    return KS_OK;
+}
+
 int ks_dense_config(ks_ctx *ctx, int bins, int r_max, int *path, int *warps, int *ty, int *tz) {
     if (!ctx || !path || !warps || !ty || !tz) return KS_EINVAL;
     Ctx *c = &ctx->impl;

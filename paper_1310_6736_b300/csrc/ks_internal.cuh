@@ -295,5 +295,6 @@ cudaError_t launch_select(const LaunchCtx &lc, const ks_candidate *in, int64_t n
 
 // Micro-kernel: shared-memory increment rate (see ks_measure_smem_peak).
 cudaError_t launch_smem_peak(const LaunchCtx &lc, uint32_t *sink, int blocks, int iters);
+cudaError_t launch_fp64_peak(const LaunchCtx &lc, double *sink, int blocks, int iters);
 
 }  // namespace ks

@@ -957,4 +957,26 @@ cudaError_t launch_smem_peak(const LaunchCtx &lc, uint32_t *sink, int blocks, in
     return cudaGetLastError();
 }
 
+// FP64 addition rate: every thread runs 8 independent chains of
+// __dadd_rn (the entropy and step sums' operation), so the pipe, not the
+// 8-deep dependency, limits the rate once a few warps are resident.
+__global__ void __launch_bounds__(256) k_fp64_peak(double *sink, int iters, double inc) {
+    double s[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] = (double)(threadIdx.x + k);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s[k] = __dadd_rn(s[k], inc);
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc = __dadd_rn(acc, s[k]);
+    if (acc == -1.0) sink[blockIdx.x] = acc;           // keeps the work observable
+}
+
+cudaError_t launch_fp64_peak(const LaunchCtx &lc, double *sink, int blocks, int iters) {
+    k_fp64_peak<<<blocks, 256, 0, lc.stream>>>(sink, iters, 1.0e-9);
+    return cudaGetLastError();
+}
+
 }  // namespace ks

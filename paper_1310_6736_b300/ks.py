@@ -107,6 +107,7 @@ SIGNATURES = {
     "ks_set_profiling": (_I, [_P, _I]),
     "ks_kernel_time": (_I, [_P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "ks_measure_smem_peak": (_I, [_P, C.POINTER(C.c_double)]),
+    "ks_measure_fp64_rate": (_I, [_P, C.POINTER(C.c_double)]),
     "ks_dense_config": (_I, [_P, _I, _I, C.POINTER(C.c_int), C.POINTER(C.c_int),
                              C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ks_force_dense_config": (_I, [_I, _I, _I, _I]),
@@ -501,6 +502,12 @@ class Context:
     def measure_smem_peak(self):
         r = C.c_double()
         self._check(lib().ks_measure_smem_peak(self.h, C.byref(r)), "ks_measure_smem_peak")
+        return r.value
+
+    def measure_fp64_rate(self):
+        """FP64 additions (lane operations) per second of this device."""
+        r = C.c_double()
+        self._check(lib().ks_measure_fp64_rate(self.h, C.byref(r)), "ks_measure_fp64_rate")
         return r.value
 
     def dense_config(self, bins, r_max):
