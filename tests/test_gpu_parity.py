@@ -227,6 +227,35 @@ def test_saliency_call_equals_the_three_calls(ctx, ks_mod, name):
         ctx.release_volume(v)
 
 
+def test_saliency_reports_a_small_capacity(ctx, ks_mod):
+    """Through the C ABI: a record buffer that is too small gives KS_EINVAL
+    with the needed counts written, and the context stays usable."""
+    import ctypes as C
+    ks = ks_mod
+    w = synth.workload("spheres48")
+    p = _params(ks, w)
+    nz, ny, nx = w.volume.shape
+    v = ctx.create_volume(w.volume, w.binning)
+    try:
+        n = ctx.seed_count(v, p)
+        S = p.r_max - p.r_min + 1
+        Y = np.empty((nz, ny, nx), np.float64)
+        s = np.empty((nz, ny, nx), np.uint8)
+        o = np.zeros(n, ks.SEED_RESULT)
+        m = np.zeros(n * S - 1, ks.MS_RESULT)          # one record short
+        n_oct, n_ms = C.c_int64(-1), C.c_int64(-1)
+        st = ks.lib().ks_saliency(ctx.h, int(v), C.byref(p), C.c_void_p(Y.ctypes.data),
+                                  C.c_void_p(s.ctypes.data), C.c_void_p(o.ctypes.data), n,
+                                  C.byref(n_oct), C.c_void_p(m.ctypes.data), len(m),
+                                  C.byref(n_ms), 0)
+        assert st == ks.KS_EINVAL
+        assert n_oct.value == n and n_ms.value == n * S
+        _, _, o2, m2 = ctx.saliency(v, p, (nz, ny, nx))      # still usable
+        assert len(o2) == n and len(m2) == n * S
+    finally:
+        ctx.release_volume(v)
+
+
 def test_dense_pet128_full_size_sampled(ctx, ko, ks_mod):
     """The bench workload (128x128x64 float32, 32 bins, r=4..20) at full size,
     in the autotuned launch configuration; checked on sampled centres."""
