@@ -12,7 +12,9 @@
 //                  octant and mean-shift items of every request that joined
 //                  since the last wave, plus one z-slab of every dense
 //                  request in progress (dense sweeps advance slab by slab,
-//                  so a large sweep never holds back later arrivals);
+//                  so a large sweep never holds back later arrivals; a
+//                  sweep's slab doubles every 4 waves, so it is not starved
+//                  by them either);
 //               4. retire finished requests: results to host, device memory
 //                  released, waiters woken.
 //   ks_poll     waits for a request with a timeout.
@@ -54,6 +56,7 @@ struct Request {
     int64_t n_seeds = 0, n_items = 0, n_vox = 0;
     bool seeds_launched = false;
     int dense_next_z = 0;
+    int dense_waves = 0;          // waves this dense request has advanced in
     // host results
     std::vector<ks_seed_result> oct;
     std::vector<ks_ms_result> ms;
@@ -306,7 +309,13 @@ static void scheduler(Ctx *c) {
         }
         for (Request *r : act) {
             if (r->status || r->desc.kind != KS_REQ_DENSE || r->canceled) continue;
-            const int z0 = r->dense_next_z, z1 = std::min(r->desc.nz, z0 + dense_slab(r));
+            // a sweep's slab doubles every 4 waves it has taken part in (up to
+            // 64 times the base slab), so a large sweep that keeps sharing
+            // waves with new arrivals still finishes in a few more waves
+            const int grow = std::min(r->dense_waves / 4, 6);
+            r->dense_waves++;
+            const int z0 = r->dense_next_z,
+                      z1 = std::min(r->desc.nz, z0 + (dense_slab(r) << grow));
             if (z0 >= z1) continue;
             const DenseOut o{r->d_Y, r->d_s, nullptr, nullptr};
             r->status = run_dense(c, S->stream2, r->v, &r->desc.params, o, z0, z1);
