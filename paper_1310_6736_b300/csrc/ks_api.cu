@@ -1288,23 +1288,32 @@ int ks_saliency(ks_ctx *ctx, ks_vol vol, const ks_params *params, double *Y, uin
     KS_TRY_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
     KS_TRY_CUDA(c, cudaStreamWaitEvent(c->hi_stream, c->ev_fork, 0));
     KS_TRY_CUDA(c, cudaStreamWaitEvent(c->lo_stream, c->ev_fork, 0));
-    // the dense sweep first, at the highest priority: the seed searches'
-    // blocks are dispatched as its last wave leaves SMs free
+    // From here on every path joins both streams before returning, so no
+    // copy into the caller's buffers is still in flight after an error.
+    // The dense sweep first, at the highest priority: the seed searches'
+    // blocks are dispatched as its last wave leaves SMs free.
     st = run_dense(c, c->hi_stream, v, params, o, 0, v->nz);
     if (st == KS_OK && !out_on_device) {
-        KS_TRY_CUDA(c, cudaMemcpyAsync(Y, o.Y, n * 8, cudaMemcpyDeviceToHost, c->hi_stream));
-        KS_TRY_CUDA(c, cudaMemcpyAsync(s_best, o.s, n, cudaMemcpyDeviceToHost, c->hi_stream));
+        e = cudaMemcpyAsync(Y, o.Y, n * 8, cudaMemcpyDeviceToHost, c->hi_stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s_best, o.s, n, cudaMemcpyDeviceToHost, c->hi_stream);
+        if (e != cudaSuccess) st = cuda_err(c, e, "dense outputs");
     }
-    KS_TRY_CUDA(c, cudaEventRecord(c->ev_hi, c->hi_stream));
     if (st == KS_OK)
         st = seed_common(c, vol, params, nullptr, 0, kOctant, oct, oct_capacity, n_oct, nullptr,
                          out_on_device, 0, c->lo_stream, false);
     if (st == KS_OK)
         st = seed_common(c, vol, params, nullptr, 0, kMeanShift, ms, ms_capacity, n_ms, nullptr,
                          out_on_device, 0, c->lo_stream, false);
-    KS_TRY_CUDA(c, cudaEventRecord(c->ev_lo, c->lo_stream));
-    KS_TRY_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_hi, 0));
-    KS_TRY_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_lo, 0));
+    e = cudaEventRecord(c->ev_hi, c->hi_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_lo, c->lo_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_hi, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_lo, 0);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(c->hi_stream);
+        cudaStreamSynchronize(c->lo_stream);
+        return st != KS_OK ? st : cuda_err(c, e, "join");
+    }
     const int st2 = check_status(c);
     return st != KS_OK ? st : st2;
 }
