@@ -430,12 +430,13 @@ int ks_selftest_wait_timeout(ks_ctx *ctx, int polls);
  * scratch is a 32 KB array compiled into the library (held on every device
  * that loads it, until exit) and shared by all calls: calls whose kernels
  * overlap on the GPU race on it, so serialise them (one stream, or events).
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.
- * Errors: KS_EINVAL for null pointers, dims < 1, bins outside [2, 64], or
- * more than 2^30 voxels (the scratch holds 4096 partials of 2^18 voxels);
- * KS_ECUDA for a launch failure. */
+ * Every call looks up the array's device address in the calling thread's
+ * current context (cudaGetSymbolAddress, which allocates nothing); the
+ * first call in a context may load the library's device code there, so
+ * make that first call before any stream capture.
+ * Errors: KS_EINVAL for null pointers, dims outside [1, 4096] (the limit of
+ * ks_create_volume; a policy limit, since the scratch does not grow with
+ * the volume) or bins outside [2, 64]; KS_ECUDA for a launch failure. */
 int ks_bin_f32_noalloc(const float *in, int nx, int ny, int nz, int bins, uint8_t *out,
                        void *cuda_stream);
 

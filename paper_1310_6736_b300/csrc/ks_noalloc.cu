@@ -12,44 +12,24 @@
 // fixed scratch array compiled into the library.
 //
 // The scratch holds one (min, max) partial per block of the reduction pass.
-// It is a file-scope __device__ array, so every GPU that loads the library
+// The pass is grid-stride, so the number of partials does not grow with the
+// volume: a call uses 4 blocks per SM, at most kNoAllocPartials.  The array
+// is a file-scope __device__ array, so every GPU that loads the library
 // holds its 32 KB until the process exits.  Host code cannot pass the
 // array's name to a kernel (on the host that name is only a stand-in), so
-// the entry point looks up its device address once per device with
-// cudaGetSymbolAddress and caches it.
-#include <mutex>
-
+// every call looks up its device address in the calling thread's current
+// context with cudaGetSymbolAddress, which allocates nothing.  A cached
+// address would go stale when the module is loaded again (after
+// cudaDeviceReset, or in a context the caller created itself).
 #include "ks_internal.cuh"
 
 namespace ks {
 namespace {
 
-constexpr int kNoAllocPartials = 4096;                // scratch entries
-constexpr int64_t kVoxelsPerPartial = int64_t(1) << 18;
-constexpr int64_t kNoAllocMaxVoxels = kNoAllocPartials * kVoxelsPerPartial;   // 2^30
-constexpr int kMaxDevices = 64;
+constexpr int kNoAllocPartials = 4096;     // scratch entries (a 1024-SM part would use them all)
+constexpr int kNoAllocMaxDim = 4096;       // the per-axis limit of ks_create_volume
 
 static __device__ __align__(256) float2 g_noalloc_minmax[kNoAllocPartials];
-
-std::mutex g_mu;
-float2 *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up on
-// the first call for that device).
-cudaError_t scratch_on_current_device(int *device, float2 **out) {
-    cudaError_t e = cudaGetDevice(device);
-    if (e != cudaSuccess) return e;
-    if (*device < 0 || *device >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> g(g_mu);
-    if (!g_scratch_ptr[*device]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_minmax);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[*device] = static_cast<float2 *>(p);
-    }
-    *out = g_scratch_ptr[*device];
-    return cudaSuccess;
-}
 
 }  // namespace
 }  // namespace ks
@@ -58,19 +38,19 @@ extern "C" int ks_bin_f32_noalloc(const float *in, int nx, int ny, int nz, int b
                                   uint8_t *out, void *cuda_stream) {
     using namespace ks;
     if (!in || !out || nx < 1 || ny < 1 || nz < 1 || bins < 2 || bins > kMaxBins) return KS_EINVAL;
-    const int64_t n = (int64_t)nx * ny * nz;
-    if (n > kNoAllocMaxVoxels) return KS_EINVAL;      // more than the scratch can reduce
-    int device = 0;
-    float2 *scratch = nullptr;
-    cudaError_t e = scratch_on_current_device(&device, &scratch);
-    int num_sms = 0;
+    if (nx > kNoAllocMaxDim || ny > kNoAllocMaxDim || nz > kNoAllocMaxDim) return KS_EINVAL;
+    int device = 0, num_sms = 0;
+    void *p = nullptr;
+    cudaError_t e = cudaGetDevice(&device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&p, g_noalloc_minmax);
     if (e != cudaSuccess) return KS_ECUDA;
-    const int parts = (int)((n + kVoxelsPerPartial - 1) / kVoxelsPerPartial);
+    int parts = bin_f32_scratch_blocks(num_sms);
+    if (parts > kNoAllocPartials) parts = kNoAllocPartials;
     // Every block of the reduction pass overwrites its own partial, so the
     // scratch needs no clearing between calls.
     LaunchCtx lc{static_cast<cudaStream_t>(cuda_stream), nullptr, num_sms};
     e = launch_bin_f32(lc, in, nx, ny, nz, bins, out, /*pitch=*/nx, /*plane=*/(int64_t)nx * ny,
-                       scratch, parts);
+                       static_cast<float2 *>(p), parts);
     return e == cudaSuccess ? KS_OK : KS_ECUDA;
 }

@@ -11,6 +11,7 @@ the tests also report how many values are bit-identical.
 import numpy as np
 import pytest
 
+import oracle_checks
 from paper_1310_6736_b300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -440,9 +441,15 @@ def test_released_volume_memory_is_reused_cleanly(ks_mod, ko):
 
 
 # ---------------------------------------------------- batched and serving
-def test_batch_equals_plain_calls(ctx, ks_mod):
+def test_batch_equals_plain_calls_and_oracle(ctx, ko, ks_mod):
+    """The batched launch gives the plain calls' records bit for bit, and
+    every volume's records equal the oracle's.  The batch mixes uint8
+    sphere volumes (r = 2..10) with int16 MR-like volumes (r = 4..32, one
+    of them with 64 bins), so mean shift takes both its warp path and its
+    block path (r > 20 or more than 32 bins)."""
     ks = ks_mod
     ws = synth.batch_volumes(seed=5, count=6, hi=96)
+    assert any(w.volume.dtype == np.int16 and w.binning["bins"] == 64 for w in ws)
     vols = [ctx.create_volume(w.volume, w.binning) for w in ws]
     ps = [_params(ks, w) for w in ws]
     for use_graph in (1, 0, 1):
@@ -450,11 +457,14 @@ def test_batch_equals_plain_calls(ctx, ks_mod):
         for v, p, o, m in zip(vols, ps, octs, mss):
             assert np.array_equal(o, ctx.seed_climb(v, p))
             assert np.array_equal(m, ctx.meanshift(v, p))
+    for w, o, m in zip(ws, octs, mss):
+        oracle_checks.octant_records(ko, w, o)
+        oracle_checks.meanshift_records(ko, w, m)
     for v in vols:
         ctx.release_volume(v)
 
 
-def test_serving_results_alone_equal_mixed(ks_mod):
+def test_serving_results_alone_equal_mixed(ko, ks_mod):
     ks = ks_mod
     ws = synth.batch_volumes(seed=9, count=5, hi=80)
     c1 = ks.Context()
@@ -476,10 +486,16 @@ def test_serving_results_alone_equal_mixed(ks_mod):
             assert (k in a) == (k in res)
             if k in a:
                 assert np.array_equal(a[k], res[k]), k
-    # the plain path gives the same numbers
+    # the plain path gives the same numbers, and so does the oracle
     v = c1.create_volume(ws[0].volume, ws[0].binning)
     assert np.array_equal(alone[0]["oct"], c1.seed_climb(v, _params(ks, ws[0])))
     c1.close()
+    for w, a in zip(ws, alone):
+        if "oct" in a:
+            oracle_checks.octant_records(ko, w, a["oct"])
+            oracle_checks.meanshift_records(ko, w, a["ms"])
+        else:
+            oracle_checks.dense_maps(ko, w, a["Y"], a["s"])
 
 
 def test_errors_are_reported_not_raised_across_abi(ctx, ks_mod):

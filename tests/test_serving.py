@@ -8,6 +8,7 @@ the context stays usable."""
 import numpy as np
 import pytest
 
+import oracle_checks
 from paper_1310_6736_b300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -39,7 +40,10 @@ def test_bounded_device_wait_reports_timeout_and_context_survives(ks_mod):
     ctx.close()
 
 
-def test_many_requests_match_plain_calls(ks_mod):
+def test_many_requests_match_plain_calls_and_oracle(ko, ks_mod):
+    """Eight requests in flight at once: each result equals the plain call's
+    and the oracle's (seed requests in full; dense sweeps of the int16
+    volumes, r = 4..32, on 1500 sampled voxels and the corners)."""
     ks = ks_mod
     ctx = ks.Context()
     ws = synth.batch_volumes(seed=21, count=8, hi=72)
@@ -56,9 +60,12 @@ def test_many_requests_match_plain_calls(ks_mod):
         if kind == ks.KS_REQ_DENSE:
             Y, s = ctx.dense_saliency(v, p, w.volume.shape)
             assert np.array_equal(res["Y"], Y.ravel()) and np.array_equal(res["s"], s.ravel())
+            oracle_checks.dense_maps(ko, w, res["Y"], res["s"], sample=1500, seed=rid)
         else:
             assert np.array_equal(res["oct"], ctx.seed_climb(v, p))
             assert np.array_equal(res["ms"], ctx.meanshift(v, p))
+            oracle_checks.octant_records(ko, w, res["oct"])
+            oracle_checks.meanshift_records(ko, w, res["ms"])
         ctx.release_volume(v)
         assert ctx.release_result(rid) == ks.KS_OK
     ctx.close()

@@ -8,9 +8,10 @@ one entry point that works only in the caller's input and output buffers
 plus a fixed scratch array compiled into the library.  This test calls it
 through the C ABI several times in a row (the scratch keeps the previous
 call's contents) and checks each output byte for byte against the
-allocating path, ks_create_volume + ks_volume_bins.  It lives in its own
-file, collected last, and passes alone in a fresh process as well as after
-the other tests.
+allocating path, ks_create_volume + ks_volume_bins, and checks that the
+calls leave the device's free memory and the torch allocator untouched.
+It lives in its own file, collected last, and passes alone in a fresh
+process as well as after the other tests.
 """
 import ctypes
 
@@ -52,11 +53,47 @@ def test_noalloc_binning_matches_allocating_path():
         ctx.release_volume(v)
         assert np.array_equal(got, ref)
         assert got.min() >= 1 and got.max() <= 32
-    # more voxels than the scratch can reduce (2^31 > 2^30): refused before any launch
-    st = lib.ks_bin_f32_noalloc(ctypes.c_void_p(d_in.data_ptr()), 2048, 1024, 1024, 32,
+    # dims beyond the library's per-axis limit: refused before any launch
+    st = lib.ks_bin_f32_noalloc(ctypes.c_void_p(d_in.data_ptr()), 4097, 4, 4, 32,
                                 ctypes.c_void_p(d_buf.data_ptr()),
                                 ctypes.c_void_p(stream.cuda_stream))
     assert st == ks.KS_EINVAL
     assert lib.ks_bin_f32_noalloc(None, 4, 4, 4, 32, ctypes.c_void_p(d_buf.data_ptr()),
                                   None) == ks.KS_EINVAL
     ctx.close()
+
+
+def test_noalloc_binning_allocates_nothing():
+    """After a first call, further calls leave the device's free memory and
+    the torch allocator's counters unchanged, and give the same bytes."""
+    import torch
+
+    from paper_1310_6736_b300 import build, ks, synth
+
+    assert torch.cuda.is_available()
+    build.build()
+    lib = ks.lib()
+    stream = torch.cuda.current_stream()
+    vol = synth.pet_f32(seed=13, dims=(96, 80, 72))[0]
+    nz, ny, nx = vol.shape
+    d_in = torch.from_numpy(vol).cuda()
+    d_out = torch.zeros(vol.size, dtype=torch.uint8, device="cuda")
+
+    def call():
+        return lib.ks_bin_f32_noalloc(ctypes.c_void_p(d_in.data_ptr()), nx, ny, nz, 32,
+                                      ctypes.c_void_p(d_out.data_ptr()),
+                                      ctypes.c_void_p(stream.cuda_stream))
+
+    assert call() == ks.KS_OK                  # first call: may load the module
+    torch.cuda.synchronize()
+    first = d_out.cpu()
+    free0, _ = torch.cuda.mem_get_info()
+    allocs0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    for _ in range(5):
+        assert call() == ks.KS_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    allocs1 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    assert free1 == free0
+    assert allocs1 == allocs0
+    assert torch.equal(d_out.cpu(), first)
