@@ -259,11 +259,31 @@ int ks_saliency(ks_ctx *ctx, ks_vol vol, const ks_params *params,
  * scaled so that none exceeds 32^2; rho = sum_b sqrt(HQ_b HP'_b).  The largest rho so far keeps
  * its (x', H'); the search stops at the first fall of rho or after
  * params->max_iter iterations.  Per-voxel terms are binary32 and all voxel
- * sums are exact fixed-point int64 sums, so results are reproducible
- * bit for bit.  Seeds, capacity and errors as in ks_meanshift. */
+ * sums are exact fixed-point int64 sums (grids chosen per window from its
+ * extent), so results are reproducible bit for bit and independent of the
+ * launch shape; they agree with a binary64 evaluation of the same steps to
+ * about 1e-4 in H and 1e-6 in rho per iteration.  Seeds, capacity and
+ * errors as in ks_meanshift. */
 int ks_abmsod(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_t *seeds_xyz,
               int64_t n_seeds, ks_abmsod_result *out, int64_t capacity, int64_t *n_out,
               int out_on_device);
+
+/* The same search (Alg. 2) from n given candidate ellipsoids, Alg. 2's
+ * "each candidate ellipsoid W_i centred at P_i with a bandwidth matrix H_i"
+ * (the paper scatters them at random with varying sizes, Sec. 2.3):
+ *   x    n x 3 FP64 centres (x, y, z), each in [0, dim - 1]
+ *   H    n x 6 FP64 bandwidths (00 01 02 11 12 22), diagonal entries in
+ *        [1, 32^2] (the window stays within 32 voxels of its centre),
+ *        off-diagonal entries of magnitude <= 32^2
+ *   out  n records (seed = candidate index, r = 0), record i for candidate i
+ *   on_device  x, H and out are device pointers (else host)
+ * max_iter in [0, 1000].  Results are those of ks_abmsod for a candidate
+ * (seed, r^2 I).  Errors: KS_EINVAL (a centre or bandwidth entry outside
+ * its range: refused before the launch for host inputs; for device inputs
+ * the candidate is left at iteration 0 and the call returns KS_EINVAL),
+ * KS_ENOTFOUND. */
+int ks_abmsod_candidates(ks_ctx *ctx, ks_vol vol, const double *x, const double *H, int64_t n,
+                         int max_iter, ks_abmsod_result *out, int on_device);
 
 /* Kadir-Brady at listed centres: the dense sweep's quantities at n centres
  * given as int32 xyz triples (0 <= x < nx etc.): Y_best, s_best and, when

@@ -23,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ks_oracle.c")
+_SRC_FIXED = os.path.join(_HERE, "ks_abmsod_fixed.c")
 _LIB = os.path.join(_HERE, "libks_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -31,12 +32,14 @@ BIN_CLAMP_SHIFT, BIN_AFFINE_F32, BIN_WINDOW = 0, 1, 2
 
 
 def build(force=False):
-    """Compile ks_oracle.c into libks_oracle.so (gcc, OpenMP, no FMA)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+    """Compile ks_oracle.c and ks_abmsod_fixed.c into libks_oracle.so (gcc,
+    OpenMP, no FMA contraction)."""
+    if not force and os.path.exists(_LIB) and all(
+            os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in (_SRC, _SRC_FIXED)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared",
-           "-fPIC", "-o", tmp, _SRC, "-lquadmath", "-lm"]
+           "-fPIC", "-o", tmp, _SRC, _SRC_FIXED, "-lquadmath", "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -71,8 +74,10 @@ def lib():
                 "ko_ms_window": (None, [P, I32, I32, I32, I32, I32, I32, I32, I32, P, P]),
                 "ko_ab_kernel": (C.c_float, [C.c_float]),
                 "ko_ab_window_check": (None, [P, P, P]),
-                "ko_abmsod": (None, [P, I32, I32, I32, I32, I32, I32, I32, P, I64, I32, P, P, P,
-                                     P, P, P]),
+                "ko_abmsod": (None, [P, I32, I32, I32, I32, I32, I32, I32, P, I64, P, P, I32, P,
+                                     P, P, P, P, P, P, P]),
+                "ko_abmsod_fixed": (None, [P, I32, I32, I32, I32, I32, I32, I32, P, I64, P, P,
+                                           I32, P, P, P, P, P, P]),
                 "ko_max_threads": (I32, []),
             }
             for name, (res, args) in sig.items():
@@ -319,32 +324,70 @@ def select_salient(cands, h_min=0.0, top_k=20):
 
 # -------------------------------------------------------------------- ABMSOD
 def ab_kernel(d):
-    """exp(-d/2) as the ABMSOD definition evaluates it (binary32)."""
+    """exp(-d/2) as the kernel's stated arithmetic evaluates it (binary32
+    polynomial; ks_abmsod_fixed.c)."""
     return float(lib().ko_ab_kernel(float(d)))
 
 
-def abmsod(bins, B, r_min, r_max, seeds, max_iter=20, nthreads=0):
-    """Adaptive-bandwidth mean shift (Alg. 2, Eq. 7) for every (seed, r)
-    item (seed-major): best centre x (FP64), bandwidth H (00 01 02 11 12 22),
-    best Bhattacharyya coefficient rho, iterations, whether the search
-    stopped at a decrease of rho, and the window voxels of every kernel
-    histogram evaluated (see ks_oracle.c)."""
+def _ab_out(n):
+    return {"x": np.zeros((n, 3)), "H": np.zeros((n, 6)), "rho": np.zeros(n),
+            "iters": np.zeros(n, np.int32), "stopped": np.zeros(n, np.int32),
+            "voxels": np.zeros(n, np.int64)}
+
+
+def _ab_inputs(bins, r_min, r_max, seeds, cand):
     bins = np.ascontiguousarray(bins, dtype=np.uint8)
+    if cand is None:
+        seeds = np.ascontiguousarray(seeds, dtype=np.int32).reshape(-1, 3)
+        return bins, seeds, seeds.shape[0], seeds.shape[0] * (r_max - r_min + 1), None, None
+    cx = np.ascontiguousarray(cand[0], dtype=np.float64).reshape(-1, 3)
+    cH = np.ascontiguousarray(cand[1], dtype=np.float64).reshape(-1, 6)
+    assert cx.shape[0] == cH.shape[0]
+    dummy = np.zeros((1, 3), np.int32)
+    return bins, dummy, cx.shape[0], cx.shape[0], cx, cH
+
+
+def abmsod(bins, B, r_min, r_max, seeds, max_iter=20, nthreads=0, cand=None):
+    """Adaptive-bandwidth mean shift (Alg. 2, Eq. 6-7), the plain binary64
+    statement, for every (seed, r) item (seed-major), or for given candidate
+    ellipsoids cand = (x (n, 3), H (n, 6)): best centre x, its bandwidth H
+    (00 01 02 11 12 22), best Bhattacharyya coefficient rho, iterations,
+    whether the search stopped at a fall of rho, the window voxels of every
+    kernel histogram evaluated, and the item's decision margins: edge
+    (smallest |d - 1| of a counted box voxel) and rho_gap (smallest
+    |rho' - best| of an iteration after the first; inf if none).  See
+    ks_oracle.c."""
+    bins, seeds, ns, n, cx, cH = _ab_inputs(bins, r_min, r_max, seeds, cand)
     nx, ny, nz = _dims(bins)
-    seeds = np.ascontiguousarray(seeds, dtype=np.int32).reshape(-1, 3)
-    n = seeds.shape[0] * (r_max - r_min + 1)
-    out = {"x": np.zeros((n, 3)), "H": np.zeros((n, 6)), "rho": np.zeros(n),
-           "iters": np.zeros(n, np.int32), "stopped": np.zeros(n, np.int32),
-           "voxels": np.zeros(n, np.int64)}
-    lib().ko_abmsod(_p(bins), nx, ny, nz, B, r_min, r_max, max_iter, _p(seeds), seeds.shape[0],
+    out = _ab_out(n)
+    out["edge"] = np.zeros(n)
+    out["rho_gap"] = np.zeros(n)
+    lib().ko_abmsod(_p(bins), nx, ny, nz, B, r_min, r_max, max_iter, _p(seeds), ns,
+                    None if cx is None else _p(cx), None if cH is None else _p(cH),
                     int(nthreads), _p(out["x"]), _p(out["H"]), _p(out["rho"]), _p(out["iters"]),
-                    _p(out["stopped"]), _p(out["voxels"]))
+                    _p(out["stopped"]), _p(out["voxels"]), _p(out["edge"]), _p(out["rho_gap"]))
+    return out
+
+
+def abmsod_fixed(bins, B, r_min, r_max, seeds, max_iter=20, nthreads=0, cand=None):
+    """The same search in the kernel's stated arithmetic (binary32 window
+    geometry, polynomial exp, fixed-point sums; ks_abmsod_fixed.c).  Not the
+    oracle of record: a model of the kernel for a bit-exact regression
+    check, bounded against abmsod() by the tolerance tests."""
+    bins, seeds, ns, n, cx, cH = _ab_inputs(bins, r_min, r_max, seeds, cand)
+    nx, ny, nz = _dims(bins)
+    out = _ab_out(n)
+    lib().ko_abmsod_fixed(_p(bins), nx, ny, nz, B, r_min, r_max, max_iter, _p(seeds), ns,
+                          None if cx is None else _p(cx), None if cH is None else _p(cH),
+                          int(nthreads), _p(out["x"]), _p(out["H"]), _p(out["rho"]),
+                          _p(out["iters"]), _p(out["stopped"]), _p(out["voxels"]))
     return out
 
 
 def ab_window_check(x, H):
-    """(box voxels with 0 <= d <= 1, those inside their row's span) for the
-    window (x, H) in a volume of counted voxels."""
+    """Kernel arithmetic (ks_abmsod_fixed.c): (box voxels with 0 <= d <= 1,
+    those inside their row's span) for the window (x, H) in a volume of
+    counted voxels."""
     x = np.ascontiguousarray(x, np.float64)
     H = np.ascontiguousarray(H, np.float64)
     out = np.zeros(2, np.int64)

@@ -25,6 +25,8 @@
  *   Sec. 2.2, Alg. 1    quadrant (here: octant) hill-climbing.
  *   Sec. 2.3, Eq. 4-6   mean shift towards a uniform target pmf with
  *                       Bhattacharyya weights.
+ *   Sec. 2.3, Alg. 2,   adaptive-bandwidth mean shift (ABMSOD) with
+ *   Eq. 7               ellipsoidal Gaussian-profile windows.
  *
  * Parity pins for every function live in tests/test_oracle_*.py.
  */
@@ -640,211 +642,191 @@ int ko_max_threads(void)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Adaptive-bandwidth mean shift (ABMSOD; Sec. 2.3, Alg. 2, Eq. 7) towards  */
-/* the uniform target HQ_b = 1/B.                                            */
+/* Adaptive-bandwidth mean shift (ABMSOD; Sec. 2.3, Alg. 2, Eq. 6 and 7)    */
+/* towards the uniform target HQ_b = 1/B, stated plainly in binary64.       */
 /*                                                                          */
-/* A candidate is a centre x (FP64 vector) with a bandwidth matrix H (FP64, */
-/* symmetric positive definite).  Its window is the ellipsoid               */
-/* { s : d(s) = (s-x)^T H^-1 (s-x) <= 1 } of counted voxels; each voxel     */
-/* carries the kernel k(s) = exp(-d(s)/2) (Alg. 2's c exp(-d/2)).  One      */
-/* iteration:                                                                */
-/*   1. HP_b = (sum of k over bin b) / (sum of k)  at (x, H)                 */
-/*      w_b  = sqrt(HQ_b / HP_b)                                             */
-/*   2. x' = x + sum_s k w o / sum_s k w,  o = s - x  (Eq. 6 with the       */
-/*      Gaussian profile: -k' is proportional to k); clamp to the volume    */
-/*   3. HP' and w' at (x', H)                                                */
-/*   4. H' = (n+2) (sum_s w' o' o'^T / sum_s w' + I/12),  o' = s - x',     */
-/*      n = 3 (Eq. 7; the factor keeps the window of a homogeneous region   */
-/*      at its size: the second moment of a uniform ellipsoid is H/(n+2);   */
-/*      I/12 is the second moment of a unit voxel about its centre, which   */
-/*      keeps H positive definite when the window's voxels lie on a line or */
-/*      a plane); then every diagonal entry below 1 is raised to 1 and H is */
-/*      scaled down so that no diagonal entry exceeds 32^2 (the window      */
-/*      stays within 32 voxels)                                             */
-/*   5. rho = sum_b sqrt(HQ_b HP'_b); the best rho so far keeps its         */
-/*      (x', H'); the search stops at the first rho below the best (Alg.    */
-/*      2's THRESHOLD read as 0) or after max_iter iterations.              */
-/* Candidates start at each seed with H = r^2 I for r = r_min..r_max.       */
+/* A candidate is a centre x and a symmetric positive definite bandwidth    */
+/* matrix H.  Its window is the ellipsoid of counted voxels s with          */
+/*   d(s) = (s - x)^T H^-1 (s - x) <= 1,                                     */
+/* tested without a division as (s - x)^T adj(H) (s - x) <= det(H) (the     */
+/* same set for det > 0; with integer data, as in the first iteration,      */
+/* the test is exact, so voxels on the boundary are always inside).  Each   */
+/* voxel of the window carries k(s) = exp(-d(s)/2), Alg. 2's c exp(-d/2)    */
+/* with the constant c dropped (it cancels in every ratio below).           */
 /*                                                                          */
-/* Arithmetic.  The window's voxels are found row by row: for the x-row at  */
-/* offsets (o_y, o_z), d as a function of o_x is the quadratic              */
-/* h00 o_x^2 + 2 beta o_x + gamma, and the row's span is where it is at     */
-/* most 1 + 1/16 (binary32 root formula, the division by h00 done as a      */
-/* product with 1/h00); a voxel of the span is in the window when           */
-/* -1/16 <= d <= 1, d evaluated along the row in binary32 as                */
-/* (h00 o_x + 2 beta) o_x + gamma with fused multiply-adds (beta and gamma  */
-/* once per row; d < 0 arises only from rounding).  The rows are those      */
-/* of the box [floor(x_a) - E_a, floor(x_a) + E_a] clipped to the volume,   */
-/* E_a = ceil(sqrt(H_aa)) in binary32 (voxels outside the volume are not    */
-/* counted).  Offsets are                                                   */
-/* o_a = (s_a - floor(x_a)) - frac(x_a), frac(x_a) rounded to binary32; H^-1 */
-/* is the adjugate times 1/det in FP64, rounded to binary32; k is the       */
-/* degree-9 Taylor polynomial of exp(-d/2) in Horner form with fused        */
-/* multiply-adds.  Every sum over voxels is an exact int64 sum of terms     */
-/* rounded to nearest (ties to even) on a fixed-point grid (2^-16 for k,    */
-/* 2^-12 for the position terms and w', 2^-8 for the second moments), so    */
-/* no result depends on the order of summation.  Per bin: w_b =             */
-/* sqrt(K / (B P_b)) in binary32 (K, B, P_b rounded to binary32) and        */
-/* sqrt(P_b) in FP64; rho =                                                 */
-/* (sum_b sqrt(P_b)) / sqrt(B K), the sum over 64 zero-padded slots as a    */
-/* pairwise tree (slot i + m added to slot i, m = 32, 16, ..., 1); H' =     */
-/* 80 M / W (= 5 (M / 2^8) / (W / 2^12)) in FP64.                           */
+/* One iteration (Alg. 2):                                                   */
+/*   1. HP_b = (sum of k over the window's voxels of bin b) / (sum of k),   */
+/*      w_b = sqrt(HQ_b / HP_b) for every occupied bin (Eq. 5).             */
+/*   2. x' = x + sum_s k w (s - x) / sum_s k w, clamped to the volume       */
+/*      (Eq. 6 with the Gaussian profile, whose -K' is proportional to k).  */
+/*   3. HP' and w' at (x', H).                                               */
+/*   4. H' = (n + 2) (sum_s w' (s - x')(s - x')^T / sum_s w' + I/12), n = 3 */
+/*      (Eq. 7; see the readings below); every diagonal entry below 1 is   */
+/*      raised to 1, then H' is scaled so that no diagonal entry exceeds    */
+/*      32^2.                                                               */
+/*   5. rho' = sum_b sqrt(HQ_b HP'_b).  If rho' > best: best = rho',        */
+/*      (x_opt, H_opt) = (x', H').  The search stops when rho' < best of    */
+/*      the earlier iterations (Alg. 2's THRESHOLD read as 0) or after      */
+/*      max_iter iterations; otherwise (x, H) = (x', H').                    */
+/* A window without counted voxels ends the search (before the iteration    */
+/* is counted when it is the first window of the iteration).  Candidates   */
+/* start at every seed with H = r^2 I for r = r_min..r_max, or at given     */
+/* candidate ellipsoids (x, H) (Alg. 2's "each candidate ellipsoid W_i      */
+/* centred at P_i with bandwidth H_i").                                     */
+/*                                                                          */
+/* Readings of Eq. 7.  As printed, the second moment of a uniform           */
+/* ellipsoid is H/(n+2), so a homogeneous window would shrink by the        */
+/* factor n + 2 = 5 every iteration; the factor keeps it at its size.       */
+/* I/12 is the second moment of a unit voxel about its centre: without it  */
+/* a window whose counted voxels lie on a plane or a line has a singular    */
+/* H'.  The bounds on the diagonal keep every window between one voxel and  */
+/* 32 voxels along each axis.                                               */
+/*                                                                          */
+/* Arithmetic: binary64 throughout; exp from libm; adj(H) and det(H) from   */
+/* the cofactors; every sum over voxels runs over the bounding box in       */
+/* z, y, x order; the box is floor(x_a - sqrt(H_aa)) - 1 ..                 */
+/* ceil(x_a + sqrt(H_aa)) + 1 clipped to the volume (the ellipsoid reaches  */
+/* sqrt(H_aa) along axis a).                                                */
+/*                                                                          */
+/* Besides the result, each item reports two margins that say how close    */
+/* its discrete decisions came to a tie: edge = the smallest |d - 1| over   */
+/* the counted voxels of the boxes of its windows at x' (the centres its    */
+/* steps computed), relative to |o|^T |H^-1| |o|, the scale of the rounding */
+/* error of an evaluation in a shorter precision -- a voxel this close to   */
+/* the boundary may fall on the other side for a centre that differs by    */
+/* rounding (ties of an integer x' included) -- and                         */
+/* rho_gap = the smallest |rho' - best| over its iterations after the       */
+/* first (the stopping test).  An implementation in other arithmetic may    */
+/* take another path only where one of them is small.                      */
 /* ------------------------------------------------------------------------ */
-#define AB_QK 65536.0f     /* 2^16 */
-#define AB_QX 4096.0f      /* 2^12 */
-#define AB_QH 256.0f       /* 2^8 */
-#define AB_HMAX 1024.0     /* 32^2 */
-#define AB_VOXEL (5.0 / 12.0)   /* (n+2) x the second moment of a unit voxel */
-#define AB_SLACK 1.0625f   /* the row span covers d <= 1 + 1/16 */
-
-/* exp(-d/2) for 0 <= d <= 1: sum_{k=0..9} t^k / k!, t = -d/2, Horner form
- * with fused multiply-adds.  The truncation error is below 3e-10, under
- * half a binary32 ulp. */
-float ko_ab_kernel(float d)
-{
-    const float c[10] = {1.0f, 1.0f, 0.5f, 0.16666666666666666f, 0.041666666666666664f,
-                         0.008333333333333333f, 0.001388888888888889f, 1.984126984126984e-04f,
-                         2.48015873015873e-05f, 2.755731922398589e-06f};
-    const float t = -0.5f * d;
-    float p = c[9];
-    for (int k = 8; k >= 0; --k) p = fmaf(p, t, c[k]);
-    return p;
-}
-
 typedef struct {
     double x[3];
-    float h[6];                     /* H^-1 rounded to binary32: 00 01 02 11 12 22 */
-    int n[3];                       /* floor(x) */
-    float f[3];                     /* x - floor(x), rounded to binary32 */
-    int lo[3], hi[3];               /* voxel box of the window */
-} ko_ab_win;
+    double adj[6];       /* adjugate of H: 00 01 02 11 12 22 */
+    double det;
+    int lo[3], hi[3];    /* bounding box, clipped to the volume */
+} ko_abw;
 
-static int ko_ab_setup(ko_ab_win *w, const double x[3], const double H[6], const int dim[3])
+static int ko_abw_setup(ko_abw *w, const double x[3], const double H[6], const int dim[3])
 {
     const double a00 = H[0], a01 = H[1], a02 = H[2], a11 = H[3], a12 = H[4], a22 = H[5];
-    const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22,
-                 c02 = a01 * a12 - a02 * a11, c11 = a00 * a22 - a02 * a02,
-                 c12 = a01 * a02 - a00 * a12, c22 = a00 * a11 - a01 * a01;
-    const double det = a00 * c00 + a01 * c01 + a02 * c02;
-    if (!(det > 0.0)) return 0;
-    const double inv = 1.0 / det;
-    w->h[0] = (float)(c00 * inv); w->h[1] = (float)(c01 * inv); w->h[2] = (float)(c02 * inv);
-    w->h[3] = (float)(c11 * inv); w->h[4] = (float)(c12 * inv); w->h[5] = (float)(c22 * inv);
+    w->adj[0] = a11 * a22 - a12 * a12;
+    w->adj[1] = a02 * a12 - a01 * a22;
+    w->adj[2] = a01 * a12 - a02 * a11;
+    w->adj[3] = a00 * a22 - a02 * a02;
+    w->adj[4] = a01 * a02 - a00 * a12;
+    w->adj[5] = a00 * a11 - a01 * a01;
+    w->det = a00 * w->adj[0] + a01 * w->adj[1] + a02 * w->adj[2];
+    if (!(w->det > 0.0)) return 0;
     const double dg[3] = {a00, a11, a22};
     for (int a = 0; a < 3; ++a) {
         w->x[a] = x[a];
-        const double fl = floor(x[a]);
-        w->n[a] = (int)fl;
-        w->f[a] = (float)(x[a] - fl);   /* exact in FP64 for x >= 0 */
-        const int E = (int)ceilf(sqrtf((float)dg[a]));
-        w->lo[a] = w->n[a] - E > 0 ? w->n[a] - E : 0;
-        w->hi[a] = w->n[a] + E < dim[a] - 1 ? w->n[a] + E : dim[a] - 1;
+        const double e = sqrt(dg[a]);
+        const int lo = (int)floor(x[a] - e) - 1, hi = (int)ceil(x[a] + e) + 1;
+        w->lo[a] = lo > 0 ? lo : 0;
+        w->hi[a] = hi < dim[a] - 1 ? hi : dim[a] - 1;
     }
     return 1;
 }
 
-/* The x-row at offsets (o1, o2): d = (h00 o_x + b2) o_x + g along it, and
- * the span [*ja, *jb] of j = s_x - floor(x_x), clipped to the box; returns
- * 0 for an empty row. */
-static int ko_ab_span(const ko_ab_win *w, float o1, float o2, float *b2, float *g, int *ja,
-                      int *jb)
+/* (s - x)^T adj(H) (s - x) */
+static double ko_abw_form(const ko_abw *w, const double o[3])
 {
-    const float *h = w->h;
-    const float beta = h[1] * o1 + h[2] * o2;
-    const float gamma = (h[3] * o1 + (2.0f * h[4]) * o2) * o1 + (h[5] * o2) * o2;
-    *b2 = beta + beta;
-    *g = gamma;
-    const float disc = beta * beta - h[0] * (gamma - AB_SLACK);
-    if (!(disc >= 0.0f)) return 0;
-    const float sq = sqrtf(disc);
-    const float ih0 = 1.0f / h[0];
-    const float ulo = (-beta - sq) * ih0, uhi = (sq - beta) * ih0;
-    const float a = fmaxf(ceilf(ulo + w->f[0]), (float)(w->lo[0] - w->n[0]));
-    const float b = fminf(floorf(uhi + w->f[0]), (float)(w->hi[0] - w->n[0]));
-    if (!(a <= b)) return 0;
-    *ja = (int)a;
-    *jb = (int)b;
-    return 1;
+    const double *A = w->adj;
+    return A[0] * o[0] * o[0] + A[3] * o[1] * o[1] + A[5] * o[2] * o[2] +
+           2.0 * (A[1] * o[0] * o[1] + A[2] * o[0] * o[2] + A[4] * o[1] * o[2]);
 }
 
-static inline int64_t ko_q(float v, float q) { return (int64_t)llrintf(v * q); }
-
-enum { AB_HIST = 0, AB_POS = 1, AB_MOM = 2 };
-
-/* One pass over the window.  AB_HIST: P[b] += q(k, 2^16), returns K and
- * adds the window's voxel count to *nvox.  AB_POS: acc[0..2] += q(k w o_a,
- * 2^12), acc[3] += q(k w, 2^12).  AB_MOM: acc[0..5] += q(w (o_a o_b), 2^8)
- * (00 01 02 11 12 22), acc[6] += q(w, 2^12). */
-static int64_t ko_ab_pass(const uint8_t *bins, int nx, int ny, int nz, int B, const ko_ab_win *w,
-                          int kind, const float *wf, int64_t *P, int64_t *acc, int64_t *nvox)
+/* |o|^T |adj(H)| |o|: the scale of the rounding error of any evaluation of
+ * the form in a shorter precision */
+static double ko_abw_absform(const ko_abw *w, const double o[3])
 {
-    int64_t K = 0;
-    if (kind == AB_HIST)
-        for (int b = 0; b < B; ++b) P[b] = 0;
+    const double *A = w->adj;
+    const double a0 = fabs(o[0]), a1 = fabs(o[1]), a2 = fabs(o[2]);
+    const double m = fabs(A[0]) * a0 * a0 + fabs(A[3]) * a1 * a1 + fabs(A[5]) * a2 * a2 +
+                     2.0 * (fabs(A[1]) * a0 * a1 + fabs(A[2]) * a0 * a2 + fabs(A[4]) * a1 * a2);
+    return m > 0.0 ? m : w->det;
+}
+
+enum { ABP_HIST = 0, ABP_POS = 1, ABP_MOM = 2 };
+
+/* One walk over the window.  ABP_HIST: P[b] = sum of k over bin b; returns
+ * the sum of k, adds the window's voxel count to *nvox and lowers *edge.
+ * ABP_POS: acc[0..2] = sum k w_b (s - x)_a, acc[3] = sum k w_b.
+ * ABP_MOM: acc[0..5] = sum w_b (s - x)_a (s - x)_c (00 01 02 11 12 22),
+ * acc[6] = sum w_b. */
+static double ko_abw_pass(const uint8_t *bins, int nx, int ny, int nz, int B, const ko_abw *w,
+                          int kind, const double *wb, double *P, double *acc, int64_t *nvox,
+                          double *edge)
+{
+    double K = 0.0;
+    if (kind == ABP_HIST)
+        for (int b = 0; b < B; ++b) P[b] = 0.0;
     else
-        for (int k = 0; k < 7; ++k) acc[k] = 0;
-    const float *h = w->h;
+        for (int c = 0; c < 7; ++c) acc[c] = 0.0;
     for (int sz = w->lo[2]; sz <= w->hi[2]; ++sz)
-        for (int sy = w->lo[1]; sy <= w->hi[1]; ++sy) {
-            const float o1 = (float)(sy - w->n[1]) - w->f[1];
-            const float o2 = (float)(sz - w->n[2]) - w->f[2];
-            int ja, jb;
-            float b2, g;
-            if (!ko_ab_span(w, o1, o2, &b2, &g, &ja, &jb)) continue;
-            for (int j = ja; j <= jb; ++j) {
-                const int v = ko_at(bins, nx, ny, nz, w->n[0] + j, sy, sz);
+        for (int sy = w->lo[1]; sy <= w->hi[1]; ++sy)
+            for (int sx = w->lo[0]; sx <= w->hi[0]; ++sx) {
+                const int v = ko_at(bins, nx, ny, nz, sx, sy, sz);
                 if (!v) continue;
-                const float o0 = (float)j - w->f[0];
-                const float d = fmaf(fmaf(h[0], o0, b2), o0, g);
-                if (!(d >= -0.0625f && d <= 1.0f)) continue;
-                if (kind == AB_HIST) {
-                    const int64_t k = ko_q(ko_ab_kernel(d), AB_QK);
-                    P[v - 1] += k;
+                const double o[3] = {(double)sx - w->x[0], (double)sy - w->x[1],
+                                     (double)sz - w->x[2]};
+                const double q = ko_abw_form(w, o);
+                if (kind == ABP_HIST && edge) {
+                    /* |d - 1| relative to the size of the form's terms */
+                    const double gap = fabs(q - w->det) / ko_abw_absform(w, o);
+                    if (gap < *edge) *edge = gap;
+                }
+                if (!(q <= w->det)) continue;
+                const double d = q / w->det;
+                const int b = v - 1;
+                if (kind == ABP_HIST) {
+                    const double k = exp(-0.5 * d);
+                    P[b] += k;
                     K += k;
                     ++*nvox;
-                } else if (kind == AB_POS) {
-                    const float t = ko_ab_kernel(d) * wf[v - 1];
-                    acc[0] += ko_q(t * o0, AB_QX);
-                    acc[1] += ko_q(t * o1, AB_QX);
-                    acc[2] += ko_q(t * o2, AB_QX);
-                    acc[3] += ko_q(t, AB_QX);
+                } else if (kind == ABP_POS) {
+                    const double t = exp(-0.5 * d) * wb[b];
+                    acc[0] += t * o[0];
+                    acc[1] += t * o[1];
+                    acc[2] += t * o[2];
+                    acc[3] += t;
                 } else {
-                    const float t = wf[v - 1];
-                    acc[0] += ko_q(t * (o0 * o0), AB_QH);
-                    acc[1] += ko_q(t * (o0 * o1), AB_QH);
-                    acc[2] += ko_q(t * (o0 * o2), AB_QH);
-                    acc[3] += ko_q(t * (o1 * o1), AB_QH);
-                    acc[4] += ko_q(t * (o1 * o2), AB_QH);
-                    acc[5] += ko_q(t * (o2 * o2), AB_QH);
-                    acc[6] += ko_q(t, AB_QX);
+                    const double t = wb[b];
+                    acc[0] += t * (o[0] * o[0]);
+                    acc[1] += t * (o[0] * o[1]);
+                    acc[2] += t * (o[0] * o[2]);
+                    acc[3] += t * (o[1] * o[1]);
+                    acc[4] += t * (o[1] * o[2]);
+                    acc[5] += t * (o[2] * o[2]);
+                    acc[6] += t;
                 }
             }
-        }
     return K;
 }
 
-/* binary32 voxel weights w_b = sqrt(K / (B P_b)) (0 for empty bins) */
-static void ko_ab_weights(const int64_t *P, int64_t K, int B, float *wf)
+/* w_b = sqrt(HQ_b / HP_b), HQ_b = 1/B, HP_b = P_b / K; 0 for empty bins */
+static void ko_abw_weights(const double *P, double K, int B, double *wb)
 {
     for (int b = 0; b < B; ++b)
-        wf[b] = P[b] > 0 ? sqrtf((float)K / ((float)B * (float)P[b])) : 0.0f;
+        wb[b] = P[b] > 0.0 ? sqrt((1.0 / B) / (P[b] / K)) : 0.0;
 }
 
-/* rho = (sum_b sqrt(P_b)) / sqrt(B K), pairwise over 64 zero-padded slots */
-static double ko_ab_rho(const int64_t *P, int64_t K, int B)
+/* rho = sum_b sqrt(HQ_b HP_b), bins in order */
+static double ko_abw_rho(const double *P, double K, int B)
 {
-    double t[64];
-    for (int b = 0; b < 64; ++b) t[b] = b < B && P[b] > 0 ? sqrt((double)P[b]) : 0.0;
-    for (int m = 32; m >= 1; m >>= 1)
-        for (int i = 0; i < m; ++i) t[i] = t[i] + t[i + m];
-    return t[0] / sqrt((double)B * (double)K);
+    double s = 0.0;
+    for (int b = 0; b < B; ++b) s += sqrt((1.0 / B) * (P[b] / K));
+    return s;
 }
 
 void ko_abmsod(const uint8_t *bins, int nx, int ny, int nz, int B,
                int r_min, int r_max, int max_iter,
-               const int32_t *seeds, int64_t nseeds, int nthreads,
+               const int32_t *seeds, int64_t nseeds,
+               const double *cand_x /* NULL, or items x 3 */,
+               const double *cand_H /* items x 6 */, int nthreads,
                double *x_out /* items x 3 */, double *H_out /* items x 6 */,
-               double *rho_out, int32_t *iters_out, int32_t *stopped_out, int64_t *voxels_out)
+               double *rho_out, int32_t *iters_out, int32_t *stopped_out, int64_t *voxels_out,
+               double *edge_out, double *rho_gap_out)
 {
     const int S = r_max - r_min + 1;
     const int dim[3] = {nx, ny, nz};
@@ -853,115 +835,91 @@ void ko_abmsod(const uint8_t *bins, int nx, int ny, int nz, int B,
 #pragma omp parallel
 #endif
     {
-        int64_t *P = (int64_t *)malloc(sizeof(int64_t) * B);
-        float *wf = (float *)malloc(sizeof(float) * B);
+        double *P = (double *)malloc(sizeof(double) * B);
+        double *wb = (double *)malloc(sizeof(double) * B);
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 1)
 #endif
-        for (int64_t item = 0; item < nseeds * S; ++item) {
-            const int64_t si = item / S;
-            const int r = r_min + (int)(item % S);
-            double x[3] = {seeds[3 * si], seeds[3 * si + 1], seeds[3 * si + 2]};
-            double H[6] = {(double)r * r, 0.0, 0.0, (double)r * r, 0.0, (double)r * r};
+        for (int64_t item = 0; item < (cand_x ? nseeds : nseeds * S); ++item) {
+            double x[3], H[6];
+            if (cand_x) {       /* a given candidate ellipsoid (x, H) */
+                for (int a = 0; a < 3; ++a) x[a] = cand_x[3 * item + a];
+                for (int c = 0; c < 6; ++c) H[c] = cand_H[6 * item + c];
+            } else {            /* seed si with H = r^2 I */
+                const int64_t si = item / S;
+                const double r2 = (double)(r_min + (int)(item % S)) * (r_min + (int)(item % S));
+                x[0] = seeds[3 * si]; x[1] = seeds[3 * si + 1]; x[2] = seeds[3 * si + 2];
+                H[0] = r2; H[1] = 0.0; H[2] = 0.0; H[3] = r2; H[4] = 0.0; H[5] = r2;
+            }
             double x_opt[3] = {x[0], x[1], x[2]}, H_opt[6];
-            for (int k = 0; k < 6; ++k) H_opt[k] = H[k];
-            double best = 0.0;
+            for (int c = 0; c < 6; ++c) H_opt[c] = H[c];
+            double best = 0.0, edge = INFINITY, rho_gap = INFINITY, acc[7];
             int it = 0, stopped = 0;
-            int64_t nvox = 0, acc[7];
+            int64_t nvox = 0;
             while (it < max_iter) {
-                ko_ab_win w;
-                if (!ko_ab_setup(&w, x, H, dim)) break;
-                const int64_t K = ko_ab_pass(bins, nx, ny, nz, B, &w, AB_HIST, NULL, P, NULL, &nvox);
-                if (K == 0) break;
-                ko_ab_weights(P, K, B, wf);
+                /* 1. candidate histogram and weights at (x, H) */
+                ko_abw w;
+                if (!ko_abw_setup(&w, x, H, dim)) break;
+                const double K = ko_abw_pass(bins, nx, ny, nz, B, &w, ABP_HIST, NULL, P, NULL,
+                                             &nvox, NULL);
+                if (!(K > 0.0)) break;
+                ko_abw_weights(P, K, B, wb);
                 /* 2. position (Eq. 6) */
-                ko_ab_pass(bins, nx, ny, nz, B, &w, AB_POS, wf, NULL, acc, NULL);
+                ko_abw_pass(bins, nx, ny, nz, B, &w, ABP_POS, wb, NULL, acc, NULL, NULL);
                 double xn[3];
                 for (int a = 0; a < 3; ++a) {
-                    const double dl = acc[3] > 0 ? (double)acc[a] / (double)acc[3] : 0.0;
-                    double v = x[a] + dl;
+                    double v = x[a] + acc[a] / acc[3];
                     if (v < 0.0) v = 0.0;
                     if (v > (double)(dim[a] - 1)) v = (double)(dim[a] - 1);
                     xn[a] = v;
                 }
-                /* 3. histogram and weights at x' */
-                ko_ab_win w2;
-                if (!ko_ab_setup(&w2, xn, H, dim)) break;
-                const int64_t K2 = ko_ab_pass(bins, nx, ny, nz, B, &w2, AB_HIST, NULL, P, NULL, &nvox);
+                /* 3. histogram and weights at (x', H) */
+                ko_abw w2;
+                if (!ko_abw_setup(&w2, xn, H, dim)) break;
+                const double K2 = ko_abw_pass(bins, nx, ny, nz, B, &w2, ABP_HIST, NULL, P, NULL,
+                                              &nvox, &edge);
                 ++it;
-                if (K2 == 0) break;
-                ko_ab_weights(P, K2, B, wf);
+                if (!(K2 > 0.0)) break;
+                ko_abw_weights(P, K2, B, wb);
                 /* 4. bandwidth (Eq. 7) */
-                ko_ab_pass(bins, nx, ny, nz, B, &w2, AB_MOM, wf, NULL, acc, NULL);
+                ko_abw_pass(bins, nx, ny, nz, B, &w2, ABP_MOM, wb, NULL, acc, NULL, NULL);
                 double Hn[6];
-                for (int k = 0; k < 6; ++k)
-                    Hn[k] = acc[6] > 0 ? (80.0 * (double)acc[k]) / (double)acc[6] : H[k];
+                for (int c = 0; c < 6; ++c) Hn[c] = 5.0 * (acc[c] / acc[6]);
                 const int dg[3] = {0, 3, 5};
                 double m = 0.0;
                 for (int a = 0; a < 3; ++a) {
-                    Hn[dg[a]] = Hn[dg[a]] + AB_VOXEL;
+                    Hn[dg[a]] += 5.0 / 12.0;
                     if (Hn[dg[a]] < 1.0) Hn[dg[a]] = 1.0;
                     if (Hn[dg[a]] > m) m = Hn[dg[a]];
                 }
-                if (m > AB_HMAX) {
-                    const double sc = AB_HMAX / m;
-                    for (int k = 0; k < 6; ++k) Hn[k] = Hn[k] * sc;
-                    for (int a = 0; a < 3; ++a)   /* rounding of m * sc */
-                        if (Hn[dg[a]] > AB_HMAX) Hn[dg[a]] = AB_HMAX;
-                }
-                /* 5. Bhattacharyya coefficient at x' */
-                const double bh = ko_ab_rho(P, K2, B);
-                const double delta = best - bh;
-                if (bh > best) {
-                    best = bh;
+                if (m > 1024.0)
+                    for (int c = 0; c < 6; ++c) Hn[c] *= 1024.0 / m;
+                /* 5. Bhattacharyya coefficient at x' and the stopping test */
+                const double rho = ko_abw_rho(P, K2, B);
+                if (it > 1 && fabs(rho - best) < rho_gap) rho_gap = fabs(rho - best);
+                const int fell = rho < best;
+                if (rho > best) {
+                    best = rho;
                     for (int a = 0; a < 3; ++a) x_opt[a] = xn[a];
-                    for (int k = 0; k < 6; ++k) H_opt[k] = Hn[k];
+                    for (int c = 0; c < 6; ++c) H_opt[c] = Hn[c];
                 }
-                if (delta > 0.0) { stopped = 1; break; }
+                if (fell) {
+                    stopped = 1;
+                    break;
+                }
                 for (int a = 0; a < 3; ++a) x[a] = xn[a];
-                for (int k = 0; k < 6; ++k) H[k] = Hn[k];
+                for (int c = 0; c < 6; ++c) H[c] = Hn[c];
             }
             for (int a = 0; a < 3; ++a) x_out[3 * item + a] = x_opt[a];
-            for (int k = 0; k < 6; ++k) H_out[6 * item + k] = H_opt[k];
+            for (int c = 0; c < 6; ++c) H_out[6 * item + c] = H_opt[c];
             rho_out[item] = best;
             iters_out[item] = it;
             stopped_out[item] = stopped;
             voxels_out[item] = nvox;
+            if (edge_out) edge_out[item] = edge;
+            if (rho_gap_out) rho_gap_out[item] = rho_gap;
         }
         free(P);
-        free(wf);
+        free(wb);
     }
-}
-
-/* Window membership two ways, for a uniform volume of counted voxels:
- * out[0] = voxels of the box whose quadratic form o^T H^-1 o (binary32, no
- * row form) is in [0, 1], out[1] = those of them that lie in their row's
- * span (equal when the spans lose nothing). */
-void ko_ab_window_check(const double x[3], const double H[6], int64_t out[2])
-{
-    ko_ab_win w;
-    const int dim[3] = {1 << 20, 1 << 20, 1 << 20};
-    out[0] = out[1] = 0;
-    if (!ko_ab_setup(&w, x, H, dim)) return;
-    const float *h = w.h;
-    for (int sz = w.lo[2]; sz <= w.hi[2]; ++sz)
-        for (int sy = w.lo[1]; sy <= w.hi[1]; ++sy) {
-            const float o1 = (float)(sy - w.n[1]) - w.f[1];
-            const float o2 = (float)(sz - w.n[2]) - w.f[2];
-            int ja = 1, jb = 0;
-            float b2, g;
-            ko_ab_span(&w, o1, o2, &b2, &g, &ja, &jb);
-            for (int sx = w.lo[0]; sx <= w.hi[0]; ++sx) {
-                const int j = sx - w.n[0];
-                const float o0 = (float)j - w.f[0];
-                /* d as the quadratic form, independent of the row form */
-                const float u0 = h[0] * o0 + h[1] * o1 + h[2] * o2;
-                const float u1 = h[1] * o0 + h[3] * o1 + h[4] * o2;
-                const float u2 = h[2] * o0 + h[4] * o1 + h[5] * o2;
-                const float d = o0 * u0 + o1 * u1 + o2 * u2;
-                if (!(d >= 0.0f && d <= 1.0f)) continue;
-                out[0] += 1;
-                out[1] += (j >= ja && j <= jb);
-            }
-        }
 }

@@ -19,9 +19,14 @@
 // (h00 o_x + 2 beta) o_x + gamma (two fused multiply-adds, beta and gamma
 // once per row).  Per-voxel terms are binary32 in one fixed operation
 // order; every sum over voxels is an exact integer sum of the terms rounded
-// to nearest on a fixed-point grid (2^-16 for k, 2^-12 for the position
-// terms and w', 2^-8 for the second moments), so the summation order does
-// not change the result: histogram sums go to lane-private u32 columns in
+// to nearest on a fixed-point grid, so the summation order does not change
+// the result.  The grids are 2^-16 for k and for the weights w' of the
+// bandwidth sums; the position terms k w o and the second moments w' o o^T
+// take the finest grids 2^-px, 2^-pm on which no term of weight k w < 4
+// (resp. w' < 4) reaches 2^22 (from the box half-width E: px = 14, pm = 9
+// at E = 32, px = 18, pm = 16 at E = 2), so small windows are summed as
+// finely as large ones relative to their extent; heavier rare-bin terms
+// are summed in int64 on the same grids.  Histogram sums go to lane-private u32 columns in
 // shared memory (shared reductions, no bank conflicts), the position and
 // moment terms to int32 sums per batch of rows, then int64.  The passes are
 // non-inlined functions shared by both item paths (smaller code), and the
@@ -39,8 +44,7 @@ namespace {
 
 constexpr int kAbWarps = 8;                 // warps per block, one item each
 constexpr float kQK = 65536.0f;             // 2^16: kernel values
-constexpr float kQX = 4096.0f;              // 2^12: position terms, weights
-constexpr float kQH = 256.0f;               // 2^8: second moments
+constexpr float kQW = 65536.0f;             // 2^16: weights of the bandwidth sums
 constexpr double kHmax = 1024.0;            // 32^2: the window stays in the halo
 constexpr double kVoxel = 5.0 / 12.0;       // (n+2) x the second moment of a unit voxel
 constexpr float kSlack = 1.0625f;           // a row's span covers d <= 1 + 1/16
@@ -108,7 +112,32 @@ __device__ __forceinline__ int64_t warp_sum_i64(int64_t v) {
 struct AbShape {
     float h[6];
     int E[3];
+    float qx, qm;     // grids 2^px, 2^pm of the position and moment terms
+    float band;       // binary32 d within band of 1: membership decided in FP64
+    double adj[6];    // adjugate of H (00 01 02 11 12 22) and det H, FP64
+    double det;
 };
+
+// Largest p with m 2^p <= 2^22 (m >= 2).
+__device__ __forceinline__ int ab_grid_exp(int m) { return 22 - (32 - __clz(m - 1)); }
+
+// Width of the band around d = 1 in which binary32 does not decide window
+// membership: 2^-16 sum_ab |h_ab| (E_a + 1)(E_b + 1), an upper bound of
+// 2^-16 |o|^T |H^-1| |o| over the box (|o_a| <= E_a + 1).  The binary32 row
+// form of d is within 6.1e-7 |o|^T |H^-1| |o| of the exact value (measured
+// over 1.2e8 voxels of random, elongated and oblique windows), so outside
+// the band it decides as the exact test does.
+__device__ __forceinline__ float ab_band(const float h[6], const int E[3]) {
+    const float e0 = (float)(E[0] + 1), e1 = (float)(E[1] + 1), e2 = (float)(E[2] + 1);
+    float s = __fmul_rn(__fmul_rn(fabsf(h[0]), e0), e0);
+    s = __fadd_rn(s, __fmul_rn(__fmul_rn(fabsf(h[3]), e1), e1));
+    s = __fadd_rn(s, __fmul_rn(__fmul_rn(fabsf(h[5]), e2), e2));
+    float t = __fmul_rn(__fmul_rn(fabsf(h[1]), e0), e1);
+    t = __fadd_rn(t, __fmul_rn(__fmul_rn(fabsf(h[2]), e0), e2));
+    t = __fadd_rn(t, __fmul_rn(__fmul_rn(fabsf(h[4]), e1), e2));
+    s = __fadd_rn(s, __fmul_rn(2.0f, t));
+    return __fmul_rn(s, 1.52587890625e-05f);   // 2^-16
+}
 __device__ __forceinline__ bool ab_shape(const double H[6], AbShape &sh) {
     const double a00 = H[0], a01 = H[1], a02 = H[2], a11 = H[3], a12 = H[4], a22 = H[5];
     const double c00 = __dsub_rn(__dmul_rn(a11, a22), __dmul_rn(a12, a12));
@@ -120,6 +149,13 @@ __device__ __forceinline__ bool ab_shape(const double H[6], AbShape &sh) {
     const double det =
         __dadd_rn(__dadd_rn(__dmul_rn(a00, c00), __dmul_rn(a01, c01)), __dmul_rn(a02, c02));
     if (!(det > 0.0)) return false;
+    sh.adj[0] = c00;
+    sh.adj[1] = c01;
+    sh.adj[2] = c02;
+    sh.adj[3] = c11;
+    sh.adj[4] = c12;
+    sh.adj[5] = c22;
+    sh.det = det;
     const double inv = __ddiv_rn(1.0, det);
     sh.h[0] = __double2float_rn(__dmul_rn(c00, inv));
     sh.h[1] = __double2float_rn(__dmul_rn(c01, inv));
@@ -130,6 +166,13 @@ __device__ __forceinline__ bool ab_shape(const double H[6], AbShape &sh) {
     sh.E[0] = (int)ceilf(__fsqrt_rn(__double2float_rn(a00)));
     sh.E[1] = (int)ceilf(__fsqrt_rn(__double2float_rn(a11)));
     sh.E[2] = (int)ceilf(__fsqrt_rn(__double2float_rn(a22)));
+    // |o_a| <= E + 1: position terms |k w o| < 4 (E + 1), moments
+    // |w o o| < 4 (E + 1)^2 on the int32 path
+    const int E1 = max(max(sh.E[0], sh.E[1]), sh.E[2]) + 1;
+    const int px = ab_grid_exp(4 * E1), pm = ab_grid_exp(4 * E1 * E1);
+    sh.qx = __int_as_float((127 + px) << 23);
+    sh.qm = __int_as_float((127 + pm) << 23);
+    sh.band = ab_band(sh.h, sh.E);
     return true;
 }
 
@@ -137,19 +180,31 @@ __device__ __forceinline__ bool ab_shape(const double H[6], AbShape &sh) {
 // binary32, and the voxel box [floor(x) - E, floor(x) + E] clipped to the
 // volume (voxels outside it are not counted).
 struct AbWinS {
+    double xc[3];     // the centre, FP64
+    double adj[6];    // adjugate of H and det H, FP64 (the exact membership test)
+    double det;
     float h[6];
     float f[3];
     int n[3];
     int lo[3], hi[3];
     int E[3];
+    float qx, qm, band;
 };
 __device__ __forceinline__ void ab_place(const double x[3], const AbShape &sh, const int dim[3],
                                          AbWinS &w) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) w.h[k] = sh.h[k];
+    for (int k = 0; k < 6; ++k) {
+        w.h[k] = sh.h[k];
+        w.adj[k] = sh.adj[k];
+    }
+    w.det = sh.det;
+    w.qx = sh.qx;
+    w.qm = sh.qm;
+    w.band = sh.band;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         w.E[a] = sh.E[a];
+        w.xc[a] = x[a];
         const double fl = floor(x[a]);
         w.n[a] = (int)fl;
         w.f[a] = __double2float_rn(__dsub_rn(x[a], fl));
@@ -161,11 +216,51 @@ __device__ __forceinline__ void ab_place(const double x[3], const AbShape &sh, c
 enum AbPass { kPassHist = 0, kPassPos = 1, kPassMom = 2 };
 
 // Per-pass sums.  Hist: s[0] = window voxels of this lane (the sums live in
-// shared memory).  Pos: s[0..2] = sum q(k w o_a), s[3] = sum q(k w).  Mom:
-// s[0..5] = sum q(w (o_a o_b)), s[6] = sum q(w).
+// shared memory).  Pos: s[0..2] = sum q(k w o_a), s[3] = sum q(k w) (grid
+// 2^-px).  Mom: s[0..5] = sum q(w (o_a o_b)) (grid 2^-pm), s[6] = sum q(w)
+// (grid 2^-16).
 struct AbSums {
     int64_t s[7];
 };
+
+// Voxels whose binary32 d falls in the band around 1, kept for the exact
+// test at the end of the pass: (j + 64) | (dy + 64) << 7 | (dz + 64) << 14 |
+// b << 21, offsets from floor(x), b the stored bin.
+constexpr int kAbQueue = 128;
+struct AbQueue {
+    int n;
+    uint32_t e[kAbQueue];
+};
+
+// The exact membership test of the definition: (s - x)^T adj(H) (s - x) <=
+// det H in FP64, one IEEE operation at a time in a fixed order (for integer
+// x and H, as in the first window of a seed, every operation is exact).
+__device__ __noinline__ bool ab_exact_inside(const AbWinS &w, int j, int dy, int dz) {
+    const double o0 = __dsub_rn((double)(w.n[0] + j), w.xc[0]);
+    const double o1 = __dsub_rn((double)(w.n[1] + dy), w.xc[1]);
+    const double o2 = __dsub_rn((double)(w.n[2] + dz), w.xc[2]);
+    const double *A = w.adj;
+    double q = __dadd_rn(__dmul_rn(__dmul_rn(A[0], o0), o0), __dmul_rn(__dmul_rn(A[3], o1), o1));
+    q = __dadd_rn(q, __dmul_rn(__dmul_rn(A[5], o2), o2));
+    double c = __dadd_rn(__dmul_rn(__dmul_rn(A[1], o0), o1), __dmul_rn(__dmul_rn(A[2], o0), o2));
+    c = __dadd_rn(c, __dmul_rn(__dmul_rn(A[4], o1), o2));
+    q = __dadd_rn(q, __dmul_rn(2.0, c));
+    return q <= w.det;
+}
+
+// True when binary32 cannot decide d <= 1: |d - 1| <= 2^-16 |o|^T |h| |o|.
+__device__ __forceinline__ bool ab_near_boundary(const AbWinS &w, float d, float o0, float o1,
+                                                 float o2) {
+    const float a0 = fabsf(o0), a1 = fabsf(o1), a2 = fabsf(o2);
+    float m = __fmul_rn(__fmul_rn(fabsf(w.h[0]), a0), a0);
+    m = __fadd_rn(m, __fmul_rn(__fmul_rn(fabsf(w.h[3]), a1), a1));
+    m = __fadd_rn(m, __fmul_rn(__fmul_rn(fabsf(w.h[5]), a2), a2));
+    float t = __fmul_rn(__fmul_rn(fabsf(w.h[1]), a0), a1);
+    t = __fadd_rn(t, __fmul_rn(__fmul_rn(fabsf(w.h[2]), a0), a2));
+    t = __fadd_rn(t, __fmul_rn(__fmul_rn(fabsf(w.h[4]), a1), a2));
+    m = __fadd_rn(m, __fmul_rn(2.0f, t));
+    return fabsf(__fsub_rn(d, 1.0f)) <= __fmul_rn(m, 1.52587890625e-05f);
+}
 
 // One row of a batch, in the warp's table: where its voxels start in the
 // packed order, and, relative to that start, its first voxel's byte offset
@@ -178,19 +273,26 @@ struct AbRow {
     int jp;        // 0x4B400000 + (its first j) - start
     float b2, g;   // d = (h00 o_x + b2) o_x + g along the row
     float o1, o2;
-    int pad;
+    int dyz;       // (s_y - floor(x_y) + 64) | (s_z - floor(x_z) + 64) << 7
 };
 
 // One pass of the warp over the window's voxels.
 template <int PASS>
 __device__ __noinline__ int64_t ab_pass(const VolDesc &v, const AbWinS &w, uint32_t *col,
-                                        const float *wf, AbRow *tab, int lane, int wt, int T,
-                                        int64_t *red) {
+                                        const float *wf, AbRow *tab, AbQueue *qu, int lane,
+                                        int wt, int T, int64_t *red) {
     AbSums acc;
 #pragma unroll
     for (int k = 0; k < 7; ++k) acc.s[k] = 0;
     const float h0 = w.h[0], h1 = w.h[1], h2 = w.h[2], h3 = w.h[3], h4 = w.h[4], h5 = w.h[5];
     const float f0 = w.f[0], f1 = w.f[1], f2 = w.f[2];
+    // int32-path limits of the weight factors (terms stay below 2^22) and
+    // the factor that puts the moment pass's weights on the 2^-16 grid
+    const float lim_x = __fmul_rn(4.0f, w.qx), lim_m = __fmul_rn(4.0f, w.qm);
+    const float q6 = __fdiv_rn(kQW, w.qm);
+    // binary32 decides membership outside [dlo, dhi]; inside it, voxels whose
+    // d is within 2^-16 |o|^T |h| |o| of 1 take the exact test
+    const float dlo = __fsub_rn(1.0f, w.band), dhi = __fadd_rn(1.0f, w.band);
     const int e1 = w.hi[1] - w.lo[1] + 1;
     const int nrows = e1 * (w.hi[2] - w.lo[2] + 1);
     const uint32_t col_s = PASS == kPassHist ? smem_u32(col) : 0u;
@@ -206,11 +308,13 @@ __device__ __noinline__ int64_t ab_pass(const VolDesc &v, const AbWinS &w, uint3
     const int dy = (32 * T) % e1, dz = (32 * T) / e1;
     const unsigned lt = (1u << lane) - 1u;
     for (int rb = wt * 32; rb < nrows; rb += 32 * T) {
-        int len = 0, ja = 0, off = 0;
+        int len = 0, ja = 0, off = 0, dyz = 0;
         float o1 = 0.0f, o2 = 0.0f, b2 = 0.0f, g = 0.0f;
         if (rb + lane < nrows) {
-            o1 = __fsub_rn(ab_i2f(w.lo[1] + iy - w.n[1]), f1);
-            o2 = __fsub_rn(ab_i2f(w.lo[2] + iz - w.n[2]), f2);
+            const int ry = w.lo[1] + iy - w.n[1], rz = w.lo[2] + iz - w.n[2];
+            dyz = (ry + 64) | (rz + 64) << 7;
+            o1 = __fsub_rn(ab_i2f(ry), f1);
+            o2 = __fsub_rn(ab_i2f(rz), f2);
             const float beta = __fadd_rn(__fmul_rn(h1, o1), __fmul_rn(h2, o2));
             const float gamma = __fadd_rn(
                 __fmul_rn(__fadd_rn(__fmul_rn(h3, o1), __fmul_rn(__fmul_rn(2.0f, h4), o2)), o1),
@@ -262,6 +366,7 @@ __device__ __noinline__ int64_t ab_pass(const VolDesc &v, const AbWinS &w, uint3
             rw.o2 = o2;
             rw.b2 = b2;
             rw.g = g;
+            rw.dyz = dyz;
         }
         __syncwarp();
         // int32 partial sums of the batch: a batch has at most 32 rows of at
@@ -275,23 +380,36 @@ __device__ __noinline__ int64_t ab_pass(const VolDesc &v, const AbWinS &w, uint3
         auto voxel = [&](const AbRow &rw, int p, int b) {
             const float o0 = __fsub_rn(__fsub_rn(__int_as_float(rw.jp + p), 12582912.0f), f0);
             const float d = __fmaf_rn(__fmaf_rn(h0, o0, rw.b2), o0, rw.g);
-            if (!(d >= -0.0625f && d <= 1.0f)) return;
+            if (!(d >= -0.0625f && d <= dhi)) return;
             const float r1 = rw.o1, r2 = rw.o2;
-            // |o_a| <= 33, so the terms stay below 2^22 when k w < 30
-            // (position) or w < 15 (moments); heavier rare-bin terms go
-            // straight to the int64 sums
+            if (d > dlo) {
+                if (ab_near_boundary(w, d, o0, r1, r2)) {
+                    const int j = rw.jp + p - 0x4B400000;
+                    const int slot = atomicAdd(&qu->n, 1);
+                    if (slot < kAbQueue) {
+                        qu->e[slot] = (uint32_t)(j + 64) | (uint32_t)rw.dyz << 7 | (uint32_t)b << 21;
+                        return;
+                    }
+                    if (!ab_exact_inside(w, j, (rw.dyz & 127) - 64, (rw.dyz >> 7) - 64)) return;
+                } else if (d > 1.0f) {
+                    return;
+                }
+            }
+            // |o_a| <= E + 1, so on the window's grids the terms stay below
+            // 2^22 when k w < 4 (position) or w < 4 (moments); heavier
+            // rare-bin terms go straight to the int64 sums
             if (PASS == kPassHist) {
                 red_add_shared(col_s + (uint32_t)(b - 1) * 128u,
                                (uint32_t)ab_rint_small(__fmul_rn(ab_kernel(d), kQK)));
                 n32 += 1u;
             } else if (PASS == kPassPos) {
-                // wf holds 2^12 w (exact scaling, so (k w o) 2^12 = k (2^12 w) o)
+                // wf holds 2^px w (exact scaling, so (k w o) 2^px = k (2^px w) o)
                 const float tk = __fmul_rn(ab_kernel(d), wf[b - 1]);
                 const float y0 = __fmul_rn(tk, o0);
                 const float y1 = __fmul_rn(tk, r1);
                 const float y2 = __fmul_rn(tk, r2);
                 const float y3 = tk;
-                if (tk < 30.0f * kQX) {
+                if (tk < lim_x) {
                     a32[0] += __float_as_uint(__fadd_rn(y0, 12582912.0f));
                     a32[1] += __float_as_uint(__fadd_rn(y1, 12582912.0f));
                     a32[2] += __float_as_uint(__fadd_rn(y2, 12582912.0f));
@@ -304,7 +422,7 @@ __device__ __noinline__ int64_t ab_pass(const VolDesc &v, const AbWinS &w, uint3
                     acc.s[3] += ab_q(y3);
                 }
             } else {
-                // wf holds 2^8 w (exact scaling)
+                // wf holds 2^pm w (exact scaling)
                 const float tw = wf[b - 1];
                 const float y0 = __fmul_rn(tw, __fmul_rn(o0, o0));
                 const float y1 = __fmul_rn(tw, __fmul_rn(o0, r1));
@@ -312,8 +430,8 @@ __device__ __noinline__ int64_t ab_pass(const VolDesc &v, const AbWinS &w, uint3
                 const float y3 = __fmul_rn(tw, __fmul_rn(r1, r1));
                 const float y4 = __fmul_rn(tw, __fmul_rn(r1, r2));
                 const float y5 = __fmul_rn(tw, __fmul_rn(r2, r2));
-                const float y6 = __fmul_rn(tw, kQX / kQH);
-                if (tw < 15.0f * kQH) {
+                const float y6 = __fmul_rn(tw, q6);
+                if (tw < lim_m) {
                     a32[0] += __float_as_uint(__fadd_rn(y0, 12582912.0f));
                     a32[1] += __float_as_uint(__fadd_rn(y1, 12582912.0f));
                     a32[2] += __float_as_uint(__fadd_rn(y2, 12582912.0f));
@@ -369,6 +487,45 @@ __device__ __noinline__ int64_t ab_pass(const VolDesc &v, const AbWinS &w, uint3
         }
         __syncwarp();   // the table is rewritten by the next batch
     }
+    // the queued voxels: exact test, then the same terms on the int64 path
+    // (the same rounding as the int32 path, so the sums do not change)
+    const int nq = min(qu->n, kAbQueue);
+    for (int i = lane; i < nq; i += 32) {
+        const uint32_t e = qu->e[i];
+        const int j = (int)(e & 127u) - 64, dy = (int)((e >> 7) & 127u) - 64;
+        const int dz = (int)((e >> 14) & 127u) - 64, b = (int)(e >> 21);
+        if (!ab_exact_inside(w, j, dy, dz)) continue;
+        const float o0 = __fsub_rn(ab_i2f(j), f0);
+        const float r1 = __fsub_rn(ab_i2f(dy), f1), r2 = __fsub_rn(ab_i2f(dz), f2);
+        const float beta = __fadd_rn(__fmul_rn(h1, r1), __fmul_rn(h2, r2));
+        const float gamma = __fadd_rn(
+            __fmul_rn(__fadd_rn(__fmul_rn(h3, r1), __fmul_rn(__fmul_rn(2.0f, h4), r2)), r1),
+            __fmul_rn(__fmul_rn(h5, r2), r2));
+        const float d = __fmaf_rn(__fmaf_rn(h0, o0, __fadd_rn(beta, beta)), o0, gamma);
+        if (PASS == kPassHist) {
+            red_add_shared(col_s + (uint32_t)(b - 1) * 128u,
+                           (uint32_t)ab_rint_small(__fmul_rn(ab_kernel(d), kQK)));
+            acc.s[0] += 1;
+        } else if (PASS == kPassPos) {
+            const float tk = __fmul_rn(ab_kernel(d), wf[b - 1]);
+            acc.s[0] += ab_q(__fmul_rn(tk, o0));
+            acc.s[1] += ab_q(__fmul_rn(tk, r1));
+            acc.s[2] += ab_q(__fmul_rn(tk, r2));
+            acc.s[3] += ab_q(tk);
+        } else {
+            const float tw = wf[b - 1];
+            acc.s[0] += ab_q(__fmul_rn(tw, __fmul_rn(o0, o0)));
+            acc.s[1] += ab_q(__fmul_rn(tw, __fmul_rn(o0, r1)));
+            acc.s[2] += ab_q(__fmul_rn(tw, __fmul_rn(o0, r2)));
+            acc.s[3] += ab_q(__fmul_rn(tw, __fmul_rn(r1, r1)));
+            acc.s[4] += ab_q(__fmul_rn(tw, __fmul_rn(r1, r2)));
+            acc.s[5] += ab_q(__fmul_rn(tw, __fmul_rn(r2, r2)));
+            acc.s[6] += ab_q(__fmul_rn(tw, q6));
+        }
+    }
+    __syncwarp();
+    if (lane == 0) qu->n = 0;
+    __syncwarp();
     if (PASS != kPassHist) {
         int64_t mine = 0;
 #pragma unroll
@@ -384,6 +541,7 @@ __device__ __noinline__ int64_t ab_pass(const VolDesc &v, const AbWinS &w, uint3
 struct AbJob {
     VolDesc vol;
     const int32_t *seeds;
+    const double *cx, *cH;         // given candidates (x, H), or null: seed x radius items
     int64_t n_seeds;
     int r_min, S, max_iter;
     int S_team;                    // radii taken by a whole block: ri >= S - S_team
@@ -404,6 +562,7 @@ struct AbState {
 // Per-warp shared memory.
 struct __align__(16) AbWarpMem {
     AbRow tab[32];         // this warp's row table
+    AbQueue qu;            // this warp's voxels left to the exact membership test
     AbState st;            // item state (leader's copy)
     AbWinS win;            // current window (leader's copy)
     int flag;              // leader -> team: 0 go on, 1 leave the loop, 2 stopped
@@ -428,7 +587,8 @@ __device__ __forceinline__ void team_sync() {
 __device__ __forceinline__ int64_t ab_hist_part(const VolDesc &v, const AbWinS &w, uint32_t *cols,
                                                 AbRow *tab, int lane, int wt, int T, int B,
                                                 AbWarpMem *mine) {
-    const int64_t nv = ab_pass<kPassHist>(v, w, cols + lane, nullptr, tab, lane, wt, T, nullptr);
+    const int64_t nv = ab_pass<kPassHist>(v, w, cols + lane, nullptr, tab, &mine->qu, lane, wt, T,
+                                          nullptr);
     __syncwarp();
     int64_t P0 = 0, P1 = 0;
     if (lane < B) {
@@ -493,36 +653,71 @@ __device__ __forceinline__ void ab_publish(AbWarpMem *lead, const AbWinS &w, int
     if (lane == 0) lead->win = w;
 }
 
-// One item (seed si, radius index ri) by a team of T warps; wt = this
-// warp's index in the team, team = the team's first warp memory.
+// One item (seed si, radius index ri; or candidate si) by a team of T
+// warps; wt = this warp's index in the team, team = the team's first warp
+// memory.
 template <int T>
 __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWarpMem *team,
                                      uint32_t *cols, int wt, int lane) {
     AbWarpMem *lead = team, *mine = team + wt;
     const bool leader = wt == 0;
     const int B = J.vol.B;
-    const int r = J.r_min + ri;
+    const int r = J.cx ? 0 : J.r_min + ri;
     const int dim[3] = {J.vol.nx, J.vol.ny, J.vol.nz};
     AbState *st = &lead->st;
     if (leader) {
-        const double r2 = (double)(r * r);
-        if (lane < 3) {
-            const double c = (double)J.seeds[3 * si + lane];
-            st->x[lane] = c;
-            st->xo[lane] = c;
+        if (J.cx) {
+            if (lane < 3) {
+                const double c = J.cx[3 * si + lane];
+                st->x[lane] = c;
+                st->xo[lane] = c;
+            }
+            if (lane < 6) {
+                const double h = J.cH[6 * si + lane];
+                st->H[lane] = h;
+                st->Ho[lane] = h;
+            }
+        } else {
+            const double r2 = (double)(r * r);
+            if (lane < 3) {
+                const double c = (double)J.seeds[3 * si + lane];
+                st->x[lane] = c;
+                st->xo[lane] = c;
+            }
+            if (lane < 6) {
+                const double h = (lane == 0 || lane == 3 || lane == 5) ? r2 : 0.0;
+                st->H[lane] = h;
+                st->Ho[lane] = h;
+            }
         }
-        if (lane < 6) {
-            const double h = (lane == 0 || lane == 3 || lane == 5) ? r2 : 0.0;
-            st->H[lane] = h;
-            st->Ho[lane] = h;
+        __syncwarp();
+        if (lane == 0) {
+            st->best = 0.0;
+            // a given candidate must lie in the volume with 1 <= H_aa <= 32^2
+            // (the window then stays inside the halo); otherwise it is
+            // flagged and left at iteration 0
+            bool ok = true;
+            if (J.cx) {
+                for (int a = 0; a < 3; ++a)
+                    ok = ok && st->x[a] >= 0.0 && st->x[a] <= (double)(dim[a] - 1);
+                for (int k = 0; k < 6; ++k) {
+                    const double h = st->H[k];
+                    const bool diag = k == 0 || k == 3 || k == 5;
+                    ok = ok && (diag ? (h >= 1.0 && h <= kHmax) : fabs(h) <= kHmax);
+                }
+                if (!ok) atomicOr(J.status, kStatusBadInput);
+            }
+            lead->flag = ok ? 0 : 1;
         }
-        if (lane == 0) st->best = 0.0;
     }
     if (lane == 0) mine->nv = 0;
+    team_sync<T>();
+    const bool skip = lead->flag != 0;
+    team_sync<T>();   // the flag is rewritten inside the loop
     int it = 0, stopped = 0;
     // the per-item values live in shared memory across the window passes
     // (the passes are calls; registers held across them would be spilled)
-    while (it < J.max_iter) {
+    while (!skip && it < J.max_iter) {
         // window at (x, H)
         if (leader) {
             __syncwarp();
@@ -545,13 +740,14 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
         team_sync<T>();
         if (leader) {
             double rho;
-            const int64_t K = ab_bins(team, T, lane, B, false, kQX, rho);
+            const int64_t K = ab_bins(team, T, lane, B, false, lead->win.qx, rho);
             if (lane == 0) lead->flag = K == 0 ? 1 : 0;
         }
         team_sync<T>();
         if (lead->flag) break;
         {
-            ab_pass<kPassPos>(J.vol, w, nullptr, lead->wf, mine->tab, lane, wt, T, mine->red);
+            ab_pass<kPassPos>(J.vol, w, nullptr, lead->wf, mine->tab, &mine->qu, lane, wt, T,
+                              mine->red);
         }
         team_sync<T>();
         if (leader) {
@@ -574,6 +770,12 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
             for (int k = 0; k < 6; ++k) sh.h[k] = lead->win.h[k];
 #pragma unroll
             for (int a = 0; a < 3; ++a) sh.E[a] = lead->win.E[a];
+            sh.qx = lead->win.qx;
+            sh.qm = lead->win.qm;
+            sh.band = lead->win.band;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sh.adj[k] = lead->win.adj[k];
+            sh.det = lead->win.det;
             __syncwarp();
             AbWinS w2;
             ab_place(st->xn, sh, dim, w2);
@@ -588,7 +790,7 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
         ++it;
         if (leader) {
             double rho;
-            const int64_t K2 = ab_bins(team, T, lane, B, true, kQH, rho);
+            const int64_t K2 = ab_bins(team, T, lane, B, true, lead->win.qm, rho);
             if (lane == 0) {
                 lead->flag = K2 == 0 ? 1 : 0;
                 st->rho = rho;
@@ -597,7 +799,8 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
         team_sync<T>();
         if (lead->flag) break;
         {
-            ab_pass<kPassMom>(J.vol, w, nullptr, lead->wf, mine->tab, lane, wt, T, mine->red);
+            ab_pass<kPassMom>(J.vol, w, nullptr, lead->wf, mine->tab, &mine->qu, lane, wt, T,
+                              mine->red);
         }
         team_sync<T>();
         if (leader) {
@@ -607,8 +810,10 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
                     mk += team[t].red[lane];
                     ws += team[t].red[6];
                 }
+                // 5 (M 2^-pm) / (W 2^-16) = (5 2^(16 - pm)) M / W
+                const double hsc = __dmul_rn(5.0, (double)__fdiv_rn(kQW, lead->win.qm));
                 st->Hn[lane] =
-                    ws > 0 ? __ddiv_rn(__dmul_rn(80.0, (double)mk), (double)ws) : st->H[lane];
+                    ws > 0 ? __ddiv_rn(__dmul_rn(hsc, (double)mk), (double)ws) : st->H[lane];
             }
             __syncwarp();
             if (lane == 0) {
@@ -682,6 +887,7 @@ __global__ void __launch_bounds__(kAbWarps * 32, 4) k_abmsod(const __grid_consta
     uint32_t *cols = reinterpret_cast<uint32_t *>(ab_smem + kAbWarps * sizeof(AbWarpMem)) +
                      (size_t)wid * B * 32;
     for (int i = lane; i < B * 32; i += 32) cols[i] = 0u;
+    if (lane == 0) mems[wid].qu.n = 0;
     __syncwarp();
     const int64_t ns = J.n_seeds;
     // block items: radii index S - S_team .. S - 1, largest first
@@ -714,8 +920,13 @@ size_t abmsod_smem_bytes(int B) {
 }
 
 cudaError_t launch_abmsod(const LaunchCtx &lc, const VolDesc &v, const int32_t *seeds,
-                          int64_t n_seeds, int r_min, int r_max, int max_iter, int r_team,
-                          int r_auto, ks_abmsod_result *out, unsigned long long *tickets) {
+                          const double *cx, const double *cH, int64_t n_seeds, int r_min,
+                          int r_max, int max_iter, int r_team, int r_auto, ks_abmsod_result *out,
+                          unsigned long long *tickets) {
+    if (cx) {            // candidates: one item each
+        r_min = 0;
+        r_max = 0;
+    }
     const int S = r_max - r_min + 1;
     const int64_t n_items = n_seeds * S;
     if (n_items == 0) return cudaSuccess;
@@ -729,11 +940,14 @@ cudaError_t launch_abmsod(const LaunchCtx &lc, const VolDesc &v, const int32_t *
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_abmsod, kAbWarps * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    if (r_team <= 0) {
-        const int64_t warps = (int64_t)lc.num_sms * per_sm * kAbWarps;
-        r_team = n_items < 4 * warps ? r_auto : kRmax + 1;
+    const int64_t warps = (int64_t)lc.num_sms * per_sm * kAbWarps;
+    int S_team;
+    if (cx) {            // all candidates on blocks or all on warps
+        S_team = r_team > kRmax ? 0 : (r_team > 0 || n_items < 4 * warps ? 1 : 0);
+    } else {
+        if (r_team <= 0) r_team = n_items < 4 * warps ? r_auto : kRmax + 1;
+        S_team = std::min(S, std::max(0, r_max - r_team + 1));
     }
-    const int S_team = std::min(S, std::max(0, r_max - r_team + 1));
     const int64_t want = n_seeds * S_team + (n_seeds * (S - S_team) + kAbWarps - 1) / kAbWarps;
     const int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)lc.num_sms * per_sm);
     e = cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned long long), lc.stream);
@@ -741,6 +955,8 @@ cudaError_t launch_abmsod(const LaunchCtx &lc, const VolDesc &v, const int32_t *
     AbJob J;
     J.vol = v;
     J.seeds = seeds;
+    J.cx = cx;
+    J.cH = cH;
     J.n_seeds = n_seeds;
     J.r_min = r_min;
     J.S = S;

@@ -66,7 +66,7 @@ struct Scratch {
 };
 enum ScratchSlot {
     kScRaw, kScSeeds, kScOct, kScMs, kScTraj, kScY, kScS, kScH, kScW, kScTune, kScPts,
-    kScSelIn, kScSelOut, kScAb, kScTicket, kScCount
+    kScSelIn, kScSelOut, kScAb, kScTicket, kScCand, kScCount
 };
 static std::mutex g_scratch_mu;
 static std::unordered_map<Ctx *, std::vector<Scratch>> g_scratch;
@@ -1349,14 +1349,72 @@ int ks_abmsod(ks_ctx *ctx, ks_vol vol, const ks_params *params, const int32_t *s
     if (e != cudaSuccess) return cuda_err(c, e, "abmsod outputs");
     ProfRec rec;
     prof_begin(c, "ks_abmsod", c->stream, &rec);
-    e = launch_abmsod(c->lc(), v->desc, ds, ns, params->r_min, params->r_max, params->max_iter,
-                      g_abmsod_team_radius, kAbmsodTeamRadius, dout, ticket);
+    e = launch_abmsod(c->lc(), v->desc, ds, nullptr, nullptr, ns, params->r_min, params->r_max,
+                      params->max_iter, g_abmsod_team_radius, kAbmsodTeamRadius, dout, ticket);
     prof_end(c, &rec, c->stream);
     KS_TRY_CUDA(c, e);
     if (!out_on_device)
         KS_TRY_CUDA(c, cudaMemcpyAsync(out, dout, n_items * sizeof(ks_abmsod_result),
                                        cudaMemcpyDeviceToHost, c->stream));
     return check_status(c);
+}
+
+int ks_abmsod_candidates(ks_ctx *ctx, ks_vol vol, const double *x, const double *H, int64_t n,
+                         int max_iter, ks_abmsod_result *out, int on_device) {
+    if (!ctx) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    if (n < 0 || (n > 0 && (!x || !H || !out)))
+        return set_err(c, KS_EINVAL, "n < 0 or a NULL buffer");
+    if (max_iter < 0 || max_iter > 1000) return set_err(c, KS_EINVAL, "max_iter outside [0, 1000]");
+    Volume *v = find_volume(c, vol);
+    if (!v) return set_err(c, KS_ENOTFOUND, "unknown volume");
+    if (n == 0) return KS_OK;
+    const double dim[3] = {(double)v->nx, (double)v->ny, (double)v->nz};
+    if (!on_device) {
+        for (int64_t i = 0; i < n; ++i) {
+            for (int a = 0; a < 3; ++a)
+                if (!(x[3 * i + a] >= 0.0 && x[3 * i + a] <= dim[a] - 1.0))
+                    return set_err(c, KS_EINVAL, "candidate centre outside the volume");
+            for (int k = 0; k < 6; ++k) {
+                const double h = H[6 * i + k];
+                const bool diag = k == 0 || k == 3 || k == 5;
+                if (!(diag ? (h >= 1.0 && h <= 1024.0) : std::fabs(h) <= 1024.0))
+                    return set_err(c, KS_EINVAL, "bandwidth entry outside its range");
+            }
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    const double *dx = x, *dH = H;
+    ks_abmsod_result *dout = out;
+    if (!on_device) {
+        double *buf = (double *)scratch(c, kScCand, (size_t)n * 9 * sizeof(double), &e);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(buf, x, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice,
+                                c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(buf + 3 * n, H, (size_t)n * 6 * sizeof(double),
+                                cudaMemcpyHostToDevice, c->stream);
+        dx = buf;
+        dH = buf + 3 * n;
+        if (e == cudaSuccess)
+            dout = (ks_abmsod_result *)scratch(c, kScAb, (size_t)n * sizeof(ks_abmsod_result), &e);
+    }
+    unsigned long long *ticket =
+        e == cudaSuccess ? (unsigned long long *)scratch(c, kScTicket, 16, &e) : nullptr;
+    if (e != cudaSuccess) return cuda_err(c, e, "abmsod candidates");
+    ProfRec rec;
+    prof_begin(c, "ks_abmsod", c->stream, &rec);
+    e = launch_abmsod(c->lc(), v->desc, nullptr, dx, dH, n, 0, 0, max_iter, g_abmsod_team_radius,
+                      kAbmsodTeamRadius, dout, ticket);
+    prof_end(c, &rec, c->stream);
+    KS_TRY_CUDA(c, e);
+    if (!on_device)
+        KS_TRY_CUDA(c, cudaMemcpyAsync(out, dout, (size_t)n * sizeof(ks_abmsod_result),
+                                       cudaMemcpyDeviceToHost, c->stream));
+    const int st = check_status(c);
+    if (st == KS_EINVAL)
+        return set_err(c, KS_EINVAL, "a candidate centre or bandwidth entry outside its range");
+    return st;
 }
 
 }  // extern "C"

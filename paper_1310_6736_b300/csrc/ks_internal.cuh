@@ -194,11 +194,18 @@ cudaError_t launch_bin_f32(const LaunchCtx &lc, const float *raw, int nx, int ny
 // block, the others on one warp each; persistent over two ticket counters
 // (tickets[0..1]) that the launch zeroes.  r_team = 0: r_auto when the
 // launch has fewer than 4 items per resident warp, else every item on one
-// warp (the small items then fill in behind the large ones).
+// warp (the small items then fill in behind the large ones).  With cx/cH
+// (device arrays, n_seeds x 3 and x 6) the items are those candidates
+// instead (record i, r = 0; r_min/r_max ignored): all on blocks when
+// r_team is 1..32 or, for r_team <= 0, when the launch has fewer than 4
+// items per resident warp, else all on warps.  A candidate outside the
+// volume or with a diagonal entry outside [1, 32^2] sets kStatusBadInput
+// and is left at iteration 0.
 size_t abmsod_smem_bytes(int B);
 cudaError_t launch_abmsod(const LaunchCtx &lc, const VolDesc &v, const int32_t *seeds,
-                          int64_t n_seeds, int r_min, int r_max, int max_iter, int r_team,
-                          int r_auto, ks_abmsod_result *out, unsigned long long *tickets);
+                          const double *cx, const double *cH, int64_t n_seeds, int r_min,
+                          int r_max, int max_iter, int r_team, int r_auto, ks_abmsod_result *out,
+                          unsigned long long *tickets);
 
 // ks_dense.cu
 struct DenseConfig {

@@ -91,6 +91,7 @@ SIGNATURES = {
                           C.POINTER(C.c_int64), _I]),
     "ks_abmsod": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _I64,
                        C.POINTER(C.c_int64), _I]),
+    "ks_abmsod_candidates": (_I, [_P, _I64, _P, _P, _I64, _I, _P, _I]),
     "ks_saliency": (_I, [_P, _I64, C.POINTER(ks_params), _P, _P, _P, _I64, C.POINTER(C.c_int64),
                          _P, _I64, C.POINTER(C.c_int64), _I]),
     "ks_dense_points": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _P, _P, _P, _I]),
@@ -334,6 +335,34 @@ class Context:
                                     C.c_void_p(out.ctypes.data), out.shape[0], C.byref(got), 0),
                     "ks_abmsod")
         return out[:got.value]
+
+    def abmsod_candidates(self, v, x, H, max_iter=20):
+        """Adaptive-bandwidth mean shift from given candidate ellipsoids:
+        x (n, 3) centres and H (n, 6) bandwidths (00 01 02 11 12 22), as
+        numpy arrays (host AB_RESULT records returned) or CUDA float64
+        tensors (returns a CUDA uint8 tensor of n records)."""
+        if _is_torch_cuda(x):
+            import torch
+            n = x.shape[0]
+            assert x.dtype == torch.float64 and H.dtype == torch.float64
+            assert x.is_contiguous() and H.is_contiguous() and H.shape[0] == n
+            out = torch.empty(max(n, 1) * AB_RESULT.itemsize, dtype=torch.uint8, device=x.device)
+            self._check(lib().ks_abmsod_candidates(self.h, int(v), C.c_void_p(x.data_ptr()),
+                                                   C.c_void_p(H.data_ptr()), n, int(max_iter),
+                                                   C.c_void_p(out.data_ptr()), 1),
+                        "ks_abmsod_candidates")
+            return out[:n * AB_RESULT.itemsize]
+        x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+        H = np.ascontiguousarray(H, np.float64).reshape(-1, 6)
+        if H.shape[0] != x.shape[0]:
+            raise ValueError("x and H must list the same number of candidates")
+        n = x.shape[0]
+        out = np.zeros(max(n, 1), AB_RESULT)
+        self._check(lib().ks_abmsod_candidates(self.h, int(v), C.c_void_p(x.ctypes.data),
+                                               C.c_void_p(H.ctypes.data), n, int(max_iter),
+                                               C.c_void_p(out.ctypes.data), 0),
+                    "ks_abmsod_candidates")
+        return out[:n]
 
     def _seeds_to_device(self, fn, name, v, params, sp, ns, out, need, rec, extra=()):
         if not out.is_cuda or out.numel() * out.element_size() < need:

@@ -11,6 +11,7 @@ the tests also report how many values are bit-identical.
 import numpy as np
 import pytest
 
+import abmsod_chain
 import oracle_checks
 from paper_1310_6736_b300 import synth
 
@@ -668,10 +669,12 @@ def test_quadrant_climb_equals_oracle(ctx, ko, ks_mod, name):
 
 # ----------------------------------------------------------------- ABMSOD
 def _ab_vs_oracle(ctx, ko, ks, w, seeds=None, max_iter=None):
-    """Adaptive-bandwidth mean shift (Alg. 2, Eq. 7): every item's best
-    centre, bandwidth, rho, iteration count and stop flag bit-exact against
-    the oracle (binary32 voxel terms and exact fixed-point sums on both
-    sides)."""
+    """Adaptive-bandwidth mean shift (Alg. 2, Eq. 7) against the kernel's
+    stated arithmetic (oracle.abmsod_fixed: binary32 voxel terms, exact
+    membership, exact fixed-point sums): every item's best centre,
+    bandwidth, rho, iteration count, stop flag and window voxels bit for
+    bit.  The distance of that arithmetic from the plain binary64 oracle is
+    bounded by the per-iteration tests below."""
     v = ctx.create_volume(w.volume, w.binning)
     it = w.max_iter if max_iter is None else max_iter
     p = ks.make_params(w.r_min, w.r_max, w.stride, it)
@@ -679,7 +682,7 @@ def _ab_vs_oracle(ctx, ko, ks, w, seeds=None, max_iter=None):
     ctx.release_volume(v)
     b = ko.bin_volume(w.volume, w.binning)
     sd = ko.seed_grid(w.dims, w.stride) if seeds is None else np.asarray(seeds, np.int32)
-    ref = ko.abmsod(b, w.binning["bins"], w.r_min, w.r_max, sd, it)
+    ref = ko.abmsod_fixed(b, w.binning["bins"], w.r_min, w.r_max, sd, it)
     S = w.r_max - w.r_min + 1
     assert np.array_equal(got["seed"], np.repeat(np.arange(len(sd)), S))
     assert np.array_equal(got["r"], np.tile(np.arange(w.r_min, w.r_max + 1), len(sd)))
@@ -786,3 +789,123 @@ def test_abmsod_team_split_does_not_change_results(ctx, ko, ks_mod):
     finally:
         ks.set_abmsod_team_radius(0)
     assert np.array_equal(outs[0], outs[1])
+
+
+# ------------------------------- ABMSOD against the plain binary64 oracle
+def _ab_per_iteration(ctx, ko, w, seeds):
+    """Every iteration of the oracle's searches from `seeds` at every radius,
+    replayed one at a time: the GPU runs one iteration (through
+    ks_abmsod_candidates) from each state the oracle visits, and the
+    results are compared at the bounds of tests/abmsod_chain.py."""
+    b = ko.bin_volume(w.volume, w.binning)
+    B = w.binning["bins"]
+    x0, H0 = abmsod_chain.seed_items(seeds, w.r_min, w.r_max)
+    st = abmsod_chain.oracle_states(ko, b, B, x0, H0, w.max_iter)
+    v = ctx.create_volume(w.volume, w.binning)
+    got = ctx.abmsod_candidates(v, st["x"], st["H"], max_iter=1)
+    ctx.release_volume(v)
+    assert np.array_equal(got["seed"], np.arange(len(st["x"])))
+    assert (got["r"] == 0).all()
+    far, near = abmsod_chain.compare(st, got)
+    return far, near
+
+
+def test_abmsod_per_iteration_vs_plain_oracle_spheres48(ctx, ko):
+    """All 4608 items of the spheres workload, every iteration."""
+    w = synth.workload("spheres48")
+    far, near = _ab_per_iteration(ctx, ko, w, ko.seed_grid(w.dims, w.stride))
+    assert far >= 0.8 * (far + near)
+
+
+def test_abmsod_per_iteration_vs_plain_oracle_pet128(ctx, ko):
+    """pet128 at full size (128 x 128 x 64 float32, 32 bins, r = 4..20):
+    every 16th grid seed at all 17 radii, every iteration."""
+    w = synth.workload("pet128")
+    far, near = _ab_per_iteration(ctx, ko, w, ko.seed_grid(w.dims, w.stride)[::16])
+    assert far >= 0.6 * (far + near)
+
+
+def test_abmsod_per_iteration_vs_plain_oracle_mr256_large_windows(ctx, ko):
+    """mr256 (64 bins, windows to r = 32 at the halo, corner seeds)."""
+    w = synth.workload("mr256")
+    grid = ko.seed_grid(w.dims, w.stride)
+    rng = np.random.default_rng(5)
+    seeds = np.concatenate([grid[rng.choice(len(grid), 5, replace=False)],
+                            np.array([[0, 0, 0], [255, 255, 159], [128, 0, 80]])]).astype(np.int32)
+    w.r_min, w.r_max, w.max_iter = 24, 32, 6
+    far, near = _ab_per_iteration(ctx, ko, w, seeds)
+    assert far + near > 100
+
+
+def test_abmsod_whole_searches_vs_plain_oracle(ctx, ko, ks_mod):
+    """Whole GPU searches against whole oracle searches: most items take the
+    same path; the others part where the stopping test meets a tie of rho
+    (flat to ~1e-7 near convergence) or a boundary voxel, and still end at
+    nearby optima.  Every record is valid: rho in [0, 1], the diagonal of
+    H in [1, 32^2], the centre in the volume, iterations within the limit,
+    a stop flag only before the limit."""
+    ks = ks_mod
+    for name, step in (("spheres48", 1), ("pet128", 8)):
+        w = synth.workload(name)
+        sd = ko.seed_grid(w.dims, w.stride)[::step].copy()
+        v = ctx.create_volume(w.volume, w.binning)
+        got = ctx.abmsod(v, _params(ks, w), seeds=sd)
+        ctx.release_volume(v)
+        ref = ko.abmsod(ko.bin_volume(w.volume, w.binning), w.binning["bins"], w.r_min,
+                        w.r_max, sd, w.max_iter)
+        same = (got["iters"] == ref["iters"]) & (got["stopped"] == ref["stopped"])
+        assert same.mean() >= 0.9, (name, same.mean())
+        dr = np.abs(got["rho"] - ref["rho"])
+        assert np.median(dr) <= 1e-6 and np.mean(dr <= 1e-4) >= 0.9, name
+        assert np.median(np.abs(got["x"] - ref["x"]).max(1)) <= 1e-3, name
+        assert abs(got["rho"].mean() - ref["rho"].mean()) <= 1e-3, name
+        assert ((got["rho"] >= 0) & (got["rho"] <= 1)).all()
+        for k in (0, 3, 5):
+            assert ((got["H"][:, k] >= 1) & (got["H"][:, k] <= 1024)).all()
+        assert ((got["x"] >= 0) & (got["x"] <= np.array(w.dims, float) - 1)).all()
+        assert ((got["iters"] >= 0) & (got["iters"] <= w.max_iter)).all()
+        assert not ((got["stopped"] == 1) & (got["iters"] == 0)).any()
+
+
+def test_abmsod_candidates_entry_point(ctx, ko, ks_mod):
+    """ks_abmsod_candidates from (seed, r^2 I) gives ks_abmsod's records;
+    device inputs give the host inputs' records; given oblique candidates
+    equal the fixed-point model; bad candidates are refused."""
+    import torch
+    ks = ks_mod
+    w = synth.workload("spheres48")
+    sd = ko.seed_grid(w.dims, w.stride)[::7].copy()
+    v = ctx.create_volume(w.volume, w.binning)
+    a = ctx.abmsod(v, _params(ks, w), seeds=sd)
+    x0, H0 = abmsod_chain.seed_items(sd, w.r_min, w.r_max)
+    c = ctx.abmsod_candidates(v, x0, H0, max_iter=w.max_iter)
+    for k in ("x", "H", "rho", "iters", "stopped", "voxels"):
+        assert np.array_equal(c[k], a[k]), k
+    rng = np.random.default_rng(4)
+    n = 300
+    xs = rng.uniform(0, 47, size=(n, 3))
+    Hs = np.zeros((n, 6))
+    for i in range(n):
+        Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        M = Q @ np.diag(np.exp(rng.uniform(np.log(2.0), np.log(90.0), 3))) @ Q.T
+        Hs[i] = [M[0, 0], M[0, 1], M[0, 2], M[1, 1], M[1, 2], M[2, 2]]
+    c = ctx.abmsod_candidates(v, xs, Hs, max_iter=6)
+    ref = ko.abmsod_fixed(ko.bin_volume(w.volume, w.binning), w.binning["bins"], 0, 0, None, 6,
+                          cand=(xs, Hs))
+    for k in ("x", "H", "rho", "iters", "stopped", "voxels"):
+        assert np.array_equal(c[k], ref[k]), k
+    d = ctx.abmsod_candidates(v, torch.from_numpy(xs).cuda(), torch.from_numpy(Hs).cuda(),
+                              max_iter=6)
+    assert np.array_equal(d.cpu().numpy().view(ks.AB_RESULT), c)
+    for bx, bH in (([[48.0, 1.0, 1.0]], [[4, 0, 0, 4, 0, 4]]),
+                   ([[5.0, 5.0, 5.0]], [[1100, 0, 0, 4, 0, 4]]),
+                   ([[5.0, 5.0, 5.0]], [[0.5, 0, 0, 4, 0, 4]])):
+        with pytest.raises(ks.KsError) as e:
+            ctx.abmsod_candidates(v, np.array(bx), np.array(bH, float))
+        assert e.value.status == ks.KS_EINVAL
+        with pytest.raises(ks.KsError) as e:
+            ctx.abmsod_candidates(v, torch.tensor(bx, dtype=torch.float64, device="cuda"),
+                                  torch.tensor(bH, dtype=torch.float64, device="cuda"))
+        assert e.value.status == ks.KS_EINVAL
+    assert len(ctx.abmsod_candidates(v, x0, H0, max_iter=1)) == len(x0)   # context still usable
+    ctx.release_volume(v)
