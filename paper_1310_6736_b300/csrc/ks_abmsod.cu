@@ -235,7 +235,7 @@ struct AbQueue {
 // The exact membership test of the definition: (s - x)^T adj(H) (s - x) <=
 // det H in FP64, one IEEE operation at a time in a fixed order (for integer
 // x and H, as in the first window of a seed, every operation is exact).
-__device__ __noinline__ bool ab_exact_inside(const AbWinS &w, int j, int dy, int dz) {
+__device__ __forceinline__ bool ab_exact_inside(const AbWinS &w, int j, int dy, int dz) {
     const double o0 = __dsub_rn((double)(w.n[0] + j), w.xc[0]);
     const double o1 = __dsub_rn((double)(w.n[1] + dy), w.xc[1]);
     const double o2 = __dsub_rn((double)(w.n[2] + dz), w.xc[2]);
@@ -262,6 +262,59 @@ __device__ __forceinline__ bool ab_near_boundary(const AbWinS &w, float d, float
     return fabsf(__fsub_rn(d, 1.0f)) <= __fmul_rn(m, 1.52587890625e-05f);
 }
 
+// The queued voxels of one warp's pass (binary32 d within the window's band
+// around 1): the exact test where binary32 cannot decide, binary32
+// elsewhere; then the pass's terms on the int64 path (the same rounding as
+// the int32 path, so the sums do not depend on which path a term took).
+// Clears the queue.
+template <int PASS>
+__device__ __noinline__ AbSums ab_flush(const AbWinS &w, AbQueue *qu, uint32_t col_s,
+                                        const float *wf, int lane) {
+    AbSums acc;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) acc.s[k] = 0;
+    const int nq = min(qu->n, kAbQueue);
+    const float h0 = w.h[0], h1 = w.h[1], h2 = w.h[2], h3 = w.h[3], h4 = w.h[4], h5 = w.h[5];
+    for (int i = lane; i < nq; i += 32) {
+        const uint32_t e = qu->e[i];
+        const int j = (int)(e & 127u) - 64, dy = (int)((e >> 7) & 127u) - 64;
+        const int dz = (int)((e >> 14) & 127u) - 64, b = (int)(e >> 21);
+        const float o0 = __fsub_rn(ab_i2f(j), w.f[0]);
+        const float r1 = __fsub_rn(ab_i2f(dy), w.f[1]), r2 = __fsub_rn(ab_i2f(dz), w.f[2]);
+        const float beta = __fadd_rn(__fmul_rn(h1, r1), __fmul_rn(h2, r2));
+        const float gamma = __fadd_rn(
+            __fmul_rn(__fadd_rn(__fmul_rn(h3, r1), __fmul_rn(__fmul_rn(2.0f, h4), r2)), r1),
+            __fmul_rn(__fmul_rn(h5, r2), r2));
+        const float d = __fmaf_rn(__fmaf_rn(h0, o0, __fadd_rn(beta, beta)), o0, gamma);
+        if (ab_near_boundary(w, d, o0, r1, r2) ? !ab_exact_inside(w, j, dy, dz) : d > 1.0f)
+            continue;
+        if (PASS == kPassHist) {
+            red_add_shared(col_s + (uint32_t)(b - 1) * 128u,
+                           (uint32_t)ab_rint_small(__fmul_rn(ab_kernel(d), kQK)));
+            acc.s[0] += 1;
+        } else if (PASS == kPassPos) {
+            const float tk = __fmul_rn(ab_kernel(d), wf[b - 1]);
+            acc.s[0] += ab_q(__fmul_rn(tk, o0));
+            acc.s[1] += ab_q(__fmul_rn(tk, r1));
+            acc.s[2] += ab_q(__fmul_rn(tk, r2));
+            acc.s[3] += ab_q(tk);
+        } else {
+            const float tw = wf[b - 1];
+            acc.s[0] += ab_q(__fmul_rn(tw, __fmul_rn(o0, o0)));
+            acc.s[1] += ab_q(__fmul_rn(tw, __fmul_rn(o0, r1)));
+            acc.s[2] += ab_q(__fmul_rn(tw, __fmul_rn(o0, r2)));
+            acc.s[3] += ab_q(__fmul_rn(tw, __fmul_rn(r1, r1)));
+            acc.s[4] += ab_q(__fmul_rn(tw, __fmul_rn(r1, r2)));
+            acc.s[5] += ab_q(__fmul_rn(tw, __fmul_rn(r2, r2)));
+            acc.s[6] += ab_q(__fmul_rn(tw, __fdiv_rn(kQW, w.qm)));
+        }
+    }
+    __syncwarp();
+    if (lane == 0) qu->n = 0;
+    __syncwarp();
+    return acc;
+}
+
 // One row of a batch, in the warp's table: where its voxels start in the
 // packed order, and, relative to that start, its first voxel's byte offset
 // from the pass base and the bit pattern of the binary32 1.5 * 2^23 + j of
@@ -277,7 +330,10 @@ struct AbRow {
 };
 
 // One pass of the warp over the window's voxels.
-template <int PASS>
+// EXACT = false: voxels in the band go to the warp's queue; if it
+// overflows (only windows so oblique that the band holds many voxels), the
+// pass is done again with EXACT = true, which tests them in place.
+template <int PASS, bool EXACT>
 __device__ __noinline__ int64_t ab_pass(const VolDesc &v, const AbWinS &w, uint32_t *col,
                                         const float *wf, AbRow *tab, AbQueue *qu, int lane,
                                         int wt, int T, int64_t *red) {
@@ -383,15 +439,16 @@ __device__ __noinline__ int64_t ab_pass(const VolDesc &v, const AbWinS &w, uint3
             if (!(d >= -0.0625f && d <= dhi)) return;
             const float r1 = rw.o1, r2 = rw.o2;
             if (d > dlo) {
-                if (ab_near_boundary(w, d, o0, r1, r2)) {
-                    const int j = rw.jp + p - 0x4B400000;
-                    const int slot = atomicAdd(&qu->n, 1);
-                    if (slot < kAbQueue) {
-                        qu->e[slot] = (uint32_t)(j + 64) | (uint32_t)rw.dyz << 7 | (uint32_t)b << 21;
+                const int j = rw.jp + p - 0x4B400000;
+                if (EXACT) {
+                    if (ab_near_boundary(w, d, o0, r1, r2)
+                            ? !ab_exact_inside(w, j, (rw.dyz & 127) - 64, (rw.dyz >> 7) - 64)
+                            : d > 1.0f)
                         return;
-                    }
-                    if (!ab_exact_inside(w, j, (rw.dyz & 127) - 64, (rw.dyz >> 7) - 64)) return;
-                } else if (d > 1.0f) {
+                } else {
+                    const int slot = atomicAdd(&qu->n, 1);
+                    if (slot < kAbQueue)
+                        qu->e[slot] = (uint32_t)(j + 64) | (uint32_t)rw.dyz << 7 | (uint32_t)b << 21;
                     return;
                 }
             }
@@ -487,45 +544,22 @@ __device__ __noinline__ int64_t ab_pass(const VolDesc &v, const AbWinS &w, uint3
         }
         __syncwarp();   // the table is rewritten by the next batch
     }
-    // the queued voxels: exact test, then the same terms on the int64 path
-    // (the same rounding as the int32 path, so the sums do not change)
-    const int nq = min(qu->n, kAbQueue);
-    for (int i = lane; i < nq; i += 32) {
-        const uint32_t e = qu->e[i];
-        const int j = (int)(e & 127u) - 64, dy = (int)((e >> 7) & 127u) - 64;
-        const int dz = (int)((e >> 14) & 127u) - 64, b = (int)(e >> 21);
-        if (!ab_exact_inside(w, j, dy, dz)) continue;
-        const float o0 = __fsub_rn(ab_i2f(j), f0);
-        const float r1 = __fsub_rn(ab_i2f(dy), f1), r2 = __fsub_rn(ab_i2f(dz), f2);
-        const float beta = __fadd_rn(__fmul_rn(h1, r1), __fmul_rn(h2, r2));
-        const float gamma = __fadd_rn(
-            __fmul_rn(__fadd_rn(__fmul_rn(h3, r1), __fmul_rn(__fmul_rn(2.0f, h4), r2)), r1),
-            __fmul_rn(__fmul_rn(h5, r2), r2));
-        const float d = __fmaf_rn(__fmaf_rn(h0, o0, __fadd_rn(beta, beta)), o0, gamma);
-        if (PASS == kPassHist) {
-            red_add_shared(col_s + (uint32_t)(b - 1) * 128u,
-                           (uint32_t)ab_rint_small(__fmul_rn(ab_kernel(d), kQK)));
-            acc.s[0] += 1;
-        } else if (PASS == kPassPos) {
-            const float tk = __fmul_rn(ab_kernel(d), wf[b - 1]);
-            acc.s[0] += ab_q(__fmul_rn(tk, o0));
-            acc.s[1] += ab_q(__fmul_rn(tk, r1));
-            acc.s[2] += ab_q(__fmul_rn(tk, r2));
-            acc.s[3] += ab_q(tk);
-        } else {
-            const float tw = wf[b - 1];
-            acc.s[0] += ab_q(__fmul_rn(tw, __fmul_rn(o0, o0)));
-            acc.s[1] += ab_q(__fmul_rn(tw, __fmul_rn(o0, r1)));
-            acc.s[2] += ab_q(__fmul_rn(tw, __fmul_rn(o0, r2)));
-            acc.s[3] += ab_q(__fmul_rn(tw, __fmul_rn(r1, r1)));
-            acc.s[4] += ab_q(__fmul_rn(tw, __fmul_rn(r1, r2)));
-            acc.s[5] += ab_q(__fmul_rn(tw, __fmul_rn(r2, r2)));
-            acc.s[6] += ab_q(__fmul_rn(tw, q6));
-        }
+    // the queued voxels (exact membership test)
+    __syncwarp();
+    if (!EXACT && qu->n > kAbQueue) {
+        // overflow: start the pass again, testing band voxels in place
+        __syncwarp();
+        if (lane == 0) qu->n = 0;
+        if (PASS == kPassHist)
+            for (int b = 0; b < v.B; ++b) st_shared_u32(col_s + (uint32_t)b * 128u, 0u);
+        __syncwarp();
+        return ab_pass<PASS, true>(v, w, col, wf, tab, qu, lane, wt, T, red);
     }
-    __syncwarp();
-    if (lane == 0) qu->n = 0;
-    __syncwarp();
+    if (!EXACT && qu->n) {
+        const AbSums fl = ab_flush<PASS>(w, qu, col_s, wf, lane);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) acc.s[k] += fl.s[k];
+    }
     if (PASS != kPassHist) {
         int64_t mine = 0;
 #pragma unroll
@@ -587,8 +621,8 @@ __device__ __forceinline__ void team_sync() {
 __device__ __forceinline__ int64_t ab_hist_part(const VolDesc &v, const AbWinS &w, uint32_t *cols,
                                                 AbRow *tab, int lane, int wt, int T, int B,
                                                 AbWarpMem *mine) {
-    const int64_t nv = ab_pass<kPassHist>(v, w, cols + lane, nullptr, tab, &mine->qu, lane, wt, T,
-                                          nullptr);
+    const int64_t nv = ab_pass<kPassHist, false>(v, w, cols + lane, nullptr, tab, &mine->qu,
+                                                 lane, wt, T, nullptr);
     __syncwarp();
     int64_t P0 = 0, P1 = 0;
     if (lane < B) {
@@ -746,8 +780,8 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
         team_sync<T>();
         if (lead->flag) break;
         {
-            ab_pass<kPassPos>(J.vol, w, nullptr, lead->wf, mine->tab, &mine->qu, lane, wt, T,
-                              mine->red);
+            ab_pass<kPassPos, false>(J.vol, w, nullptr, lead->wf, mine->tab, &mine->qu, lane, wt,
+                                     T, mine->red);
         }
         team_sync<T>();
         if (leader) {
@@ -799,8 +833,8 @@ __device__ __forceinline__ void ab_item(const AbJob &J, int64_t si, int ri, AbWa
         team_sync<T>();
         if (lead->flag) break;
         {
-            ab_pass<kPassMom>(J.vol, w, nullptr, lead->wf, mine->tab, &mine->qu, lane, wt, T,
-                              mine->red);
+            ab_pass<kPassMom, false>(J.vol, w, nullptr, lead->wf, mine->tab, &mine->qu, lane, wt,
+                                     T, mine->red);
         }
         team_sync<T>();
         if (leader) {
