@@ -34,10 +34,13 @@ METRIC = "window-entropies/s"
 WORKLOAD = "pet128"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_dense launch on the
-# pet128 workload (launch path 4, profiles/k_dense_pet128.md): the padded bin
-# volume is read once; the Y and s outputs stay in L2.
-DENSE_DRAM_BYTES = 3_769_344
+# dram__bytes_read.sum and dram__bytes_write.sum of one k_dense launch on the
+# pet128 workload, captured with ncu (launch path 4, profiles/k_dense_pet128.md):
+# the padded bin volume is read once; the Y and s_best outputs (9 bytes per
+# voxel) stay in L2 at the end of the launch, so the capture shows almost no
+# writes.  They leave L2 later, so the line's traffic counts them as written.
+DENSE_DRAM_READ = 3_769_344
+DENSE_DRAM_WRITE = 512
 
 
 def _dist():
@@ -354,8 +357,15 @@ def run_ks(args):
                                                 or (None,) * 4))},
             "roofline": {"bound": "smem", "achieved": achieved / 1e9,
                          "peak": smem_peak / 1e9, "unit": "Gupdates/s",
-                         "frac": achieved / smem_peak, "traffic": DENSE_DRAM_BYTES,
-                         "traffic_unit": "bytes per launch (dram read + write, ncu)",
+                         "frac": achieved / smem_peak,
+                         "traffic": DENSE_DRAM_READ + max(DENSE_DRAM_WRITE, n_vox * 9),
+                         "traffic_unit": "bytes per launch: dram__bytes_read.sum of one ncu "
+                                         "capture plus the outputs' 9 bytes per voxel, which "
+                                         "the capture shows still in L2 and which are written "
+                                         "back to DRAM after the launch",
+                         "traffic_measured": {"dram_read": DENSE_DRAM_READ,
+                                              "dram_write": DENSE_DRAM_WRITE,
+                                              "deferred_output_bytes": n_vox * 9},
                          "kernel": "k_dense", "peak_source":
                              "shared-memory histogram-increment micro-kernel, measured live",
                          "kernel_ms": dense_ms / max(1, dense_n),
@@ -385,13 +395,23 @@ def run_ks(args):
             "peaks_source": peak_kind,
         }
     if rank == 0 and not args.no_extras:
-        # short forms of the batched and serving workloads (full sizes:
-        # --mode batch / --mode serve)
+        # per-part rates and rooflines of the two seed kernels (each alone)
+        line["seed_rooflines"] = seed_rooflines(ctx, ks, w, params, smem_peak, flush)
+        line["config"]["parts_per_s"] = {
+            "dense": parts["dense"] / (alone_ms / max(1, alone_n) * 1e-3),
+            "octant": line["seed_rooflines"]["octant"]["window_entropies_per_s"],
+            "meanshift": line["seed_rooflines"]["meanshift"]["window_entropies_per_s"],
+            "note": "window-entropies/s of each part run alone on the same volume"}
         line["config"]["selection"] = run_selection(ctx, ks, w, params)
         line["config"]["abmsod"] = abmsod_summary(ctx, ks, w, params)
-        line["config"]["batched"] = run_batched(ctx, ks, synth, count=64, max_dim=128, reps=2)
-        line["config"]["serving"] = run_serving(ks.Context, ks, synth, rate=50.0, count=120,
-                                                pool=12, max_dim=96)
+        # the metric's other configurations at their stated sizes
+        line["config"]["mr256_seeds"] = run_mr256_seeds(ctx, ks, synth)
+        rows, what, hbm, kind = binning_rows(ctx, ks)
+        line["config"]["binning"] = {"workload": what, "peak_hbm_gbs": hbm, "rows": rows,
+                                     "min_frac_of_hbm": min(r["frac_of_hbm"] for r in rows)}
+        line["config"]["batched"] = run_batched(ctx, ks, synth, count=64, max_dim=None, reps=2)
+        line["config"]["serving"] = run_serving(ks.Context, ks, synth, rate=50.0, count=2000,
+                                                pool=32)
     if rank == 0 and not args.no_cpu_baseline:
         v_cpu, threads, desc, dt = oracle_sample(w, budget_s=args.ref_budget)
         line["cpu_baseline"] = {"value": v_cpu, "unit": "window-entropies/s", "cores": threads,
@@ -551,6 +571,142 @@ def run_window(ctx, ks, synth, name, top_k=20):
             "meanshift_converged": int(m["converged"].sum())}
 
 
+def _closed_octant_updates(r):
+    """Shared-memory updates of one octant pass over Ball(r): each offset
+    counts once per closed octant it belongs to, 2^(zero components)."""
+    g = np.arange(-r, r + 1)
+    o = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    o = o[(o ** 2).sum(1) <= r * r]
+    return int((2 ** (o == 0).sum(1)).sum())
+
+
+def _passes(res):
+    """Window passes of seed searches: one per iteration, plus the final
+    pass at the centre where the last iteration moved (no convergence)."""
+    return res["iters"].astype(np.int64) + (res["converged"] == 0)
+
+
+def seed_rooflines(ctx, ks, w, params, smem_peak, flush, reps=5):
+    """The two seed kernels alone on workload w (device outputs, L2 flushed
+    between launches), against the measured shared-memory update rate:
+    octant climb = closed-octant updates of Ball(r_max) per pass; mean
+    shift = |Ball(r)| window voxels per pass of each (seed, r) item."""
+    import torch
+    v = ctx.create_volume(w.volume, w.binning)
+    o = ctx.seed_climb(v, params)
+    m = ctx.meanshift(v, params)
+    od = torch.empty(len(o) * ks.SEED_RESULT.itemsize, dtype=torch.uint8, device="cuda")
+    md = torch.empty(len(m) * ks.MS_RESULT.itemsize, dtype=torch.uint8, device="cuda")
+    out = {}
+    oct_upd = int(_passes(o).sum()) * _closed_octant_updates(w.r_max)
+    ms_upd = int((_passes(m) * np.array([ks_ball_size(int(r)) for r in m["r"]])).sum())
+    S = w.r_max - w.r_min + 1
+    oct_we = int(o["iters"].sum()) * 8 * S + len(o) * S
+    ms_we = int(m["iters"].sum()) + int((m["converged"] == 0).sum())
+    for name, fn, upd, we, prefix in (
+            ("octant", lambda: ctx.seed_climb(v, params, out=od), oct_upd, oct_we, "ks_seeds"),
+            ("meanshift", lambda: ctx.meanshift(v, params, out=md), ms_upd, ms_we,
+             "ks_seeds_persistent")):
+        fn()
+        ctx.set_profiling(True)
+        for _ in range(reps):
+            flush.zero_()
+            fn()
+        ms, n = ctx.kernel_time(prefix)
+        ctx.set_profiling(False)
+        t = ms / max(1, n) * 1e-3
+        out[name] = {"kernel": "k_seeds<" + name + ">", "kernel_ms": t * 1e3,
+                     "updates_per_launch": upd, "achieved_gupdates_s": upd / t / 1e9,
+                     "frac_of_smem_peak": upd / t / smem_peak,
+                     "window_entropies_per_launch": we,
+                     "window_entropies_per_s": we / t, "launches": n}
+    ctx.release_volume(v)
+    out["unit"] = ("shared-memory histogram updates (octant: one per voxel and closed octant of "
+                   "each pass; mean shift: one per window voxel of each pass)")
+    return out
+
+
+def run_mr256_seeds(ctx, ks, synth, reps=3):
+    """The MR-shaped workload's seed searches at full size (256x256x160
+    int16, 64 bins, r = 4..32, stride 12: 5733 seeds, 166 257 mean-shift
+    items): octant climb and mean shift, results on the device, CUDA events
+    around the two calls."""
+    import torch
+    w = synth.workload("mr256")
+    params = ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter)
+    v = ctx.create_volume(w.volume, w.binning)
+    o = ctx.seed_climb(v, params)
+    m = ctx.meanshift(v, params)
+    od = torch.empty(len(o) * ks.SEED_RESULT.itemsize, dtype=torch.uint8, device="cuda")
+    md = torch.empty(len(m) * ks.MS_RESULT.itemsize, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+    times = {"octant": [], "meanshift": []}
+    for _ in range(reps):
+        for name, fn in (("octant", lambda: ctx.seed_climb(v, params, out=od)),
+                         ("meanshift", lambda: ctx.meanshift(v, params, out=md))):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            torch.cuda.synchronize()
+            times[name].append(a.elapsed_time(b))
+    same = (np.array_equal(od.cpu().numpy().view(ks.SEED_RESULT), o) and
+            np.array_equal(md.cpu().numpy().view(ks.MS_RESULT), m))
+    ctx.release_volume(v)
+    S = w.r_max - w.r_min + 1
+    oct_we = int(o["iters"].sum()) * 8 * S + len(o) * S
+    ms_we = int(m["iters"].sum()) + int((m["converged"] == 0).sum())
+    t_o, t_m = min(times["octant"]), min(times["meanshift"])
+    return {"workload": "mr256: 256x256x160 int16 MR-shaped, 64 bins, r = 4..32, stride 12",
+            "seeds": len(o), "meanshift_items": len(m),
+            "octant_ms": t_o, "meanshift_ms": t_m,
+            "window_entropies": oct_we + ms_we,
+            "window_entropies_per_s": (oct_we + ms_we) / ((t_o + t_m) * 1e-3),
+            "volumes_per_s": 1e3 / (t_o + t_m), "device_records_equal_host": bool(same)}
+
+
+def binning_rows(ctx, ks, steps=10, warmup=3):
+    """Binning alone, an HBM-bound kernel: three raw types on a 512x512x256
+    volume (far above the 126 MB L2).  Per type, the ks_bin kernels'
+    CUDA-event time over `steps` calls of ks_create_volume from device
+    memory; the algorithmic bytes are the raw read (float32 also its min/max
+    pass) plus one byte written per voxel."""
+    import torch
+    nz, ny, nx = 256, 512, 512
+    n = nx * ny * nz
+    peaks, kind = _peaks()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    cases = [
+        ("uint8, v >> 3 (32 bins)", lambda: torch.randint(0, 256, (nz, ny, nx), generator=g,
+                                                          device="cuda", dtype=torch.uint8),
+         {"kind": 0, "bins": 32, "shift": 3, "lo": 0, "hi": 255}, 2),
+        ("int16, clamp to [0, 2047] >> 5 (64 bins)",
+         lambda: torch.randint(-100, 2200, (nz, ny, nx), generator=g, device="cuda",
+                               dtype=torch.int16),
+         {"kind": 0, "bins": 64, "shift": 5, "lo": 0, "hi": 2047}, 3),
+        ("float32, affine over [vmin, vmax] (32 bins; min/max pass)",
+         lambda: torch.rand((nz, ny, nx), generator=g, device="cuda", dtype=torch.float32) * 100.0,
+         {"kind": 1, "bins": 32, "shift": 0, "lo": 0, "hi": 0}, 9),
+    ]
+    rows = []
+    for name, make, binning, bpv in cases:
+        raw = make()
+        for _ in range(warmup):
+            ctx.release_volume(ctx.create_volume(raw, binning))
+        ctx.set_profiling(True)
+        for _ in range(steps):
+            ctx.release_volume(ctx.create_volume(raw, binning))
+        ms, launches = ctx.kernel_time("ks_bin")
+        ctx.set_profiling(False)
+        del raw
+        t = ms / max(1, launches) * 1e-3
+        gbs = n * bpv / t / 1e9
+        rows.append({"raw": name, "voxels": n, "bytes_per_voxel": bpv, "ms": t * 1e3,
+                     "achieved_gbs": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"]})
+    return rows, f"{nx}x{ny}x{nz} random volumes", peaks["hbm_gbs"], kind
+
+
 def run_batched(ctx, ks, synth, count=64, max_dim=None, reps=3):
     """Batched form: `count` uneven volumes (uint8 spheres / int16 MR-like),
     octant climb + mean shift for every grid seed of every volume, as one
@@ -592,40 +748,49 @@ def run_batched(ctx, ks, synth, count=64, max_dim=None, reps=3):
             "identical_results": bool(same)}
 
 
-def run_serving(ctx_factory, ks, synth, rate=50.0, count=200, pool=24, max_dim=None,
-                dense_frac=0.3, seed=4):
+def run_serving(ctx_factory, ks, synth, rate=50.0, count=2000, pool=32, max_dim=None,
+                dense_frac=0.3, seed=4, wave_iters=None):
     """Serving form: a Poisson stream of `count` requests at `rate`/s, each a
-    volume from a pool drawn like the batched form, asking for both seed
-    schemes (70%) or the dense sweep (30%), replayed in real time against
-    the continuous-batching loop (ks_submit / ks_poll).  The plain
-    sequential path (one request at a time through the synchronous calls,
-    queueing in arrival order) is timed on the same requests.  Returns p50/p99
-    latency and volumes/s for both."""
+    volume from a pool drawn like the batched form (dims log-uniform in
+    [48, 256], z <= 160; uint8 spheres / int16 MR-like), asking for both
+    seed schemes (70%) or the dense sweep (30%).  Two arms replay the same
+    stream in real time:
+      - serving: the continuous-batching loop (ks_submit from a client
+        thread at the arrival times, ks_poll for every result);
+      - sequential: the plain path, one request at a time in arrival order
+        (a request that arrives while another runs waits): create_volume
+        from pinned host memory, the synchronous calls, results to host.
+    Latency is completion minus arrival; volumes/s is requests over the
+    span from the first arrival to the last completion."""
     import threading
+    import torch
     reqs = synth.request_stream(seed=seed, count=count, rate=rate, dense_frac=dense_frac)
     ws = synth.batch_volumes(seed=seed + 100, count=pool, max_dim=max_dim)
     kinds = [ks.KS_REQ_DENSE if r["kind"] == "dense" else ks.KS_REQ_SEEDS for r in reqs]
     picks = [r["vol_seed"] % pool for r in reqs]
+    params = [ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter) for w in ws]
+    # warm-up: the dense autotuner's classes and every kernel variant
     ctx = ctx_factory()
-    # warm-up (autotuner, graph of nothing): one of each kind per pool entry type
-    for i in range(min(pool, 4)):
-        w = ws[i]
+    if wave_iters is not None:
+        ctx.set_serve_wave_iters(wave_iters)
+    for i in range(pool):
         for k in (ks.KS_REQ_SEEDS, ks.KS_REQ_DENSE):
-            rid = ctx.submit(w.volume, w.binning,
-                             ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter), kind=k)
+            if k == ks.KS_REQ_DENSE and i >= 4:
+                continue
+            rid = ctx.submit(ws[i].volume, ws[i].binning, params[i], kind=k)
             ctx.poll(rid, -1)
             ctx.release_result(rid)
+    ctx.set_profiling(True)
     ids = [None] * count
     t0 = time.perf_counter()
+    t0_us = None
 
     def submitter():
         for i, r in enumerate(reqs):
             now = time.perf_counter() - t0
             if r["t"] > now:
                 time.sleep(r["t"] - now)
-            w = ws[picks[i]]
-            ids[i] = ctx.submit(w.volume, w.binning,
-                                ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter),
+            ids[i] = ctx.submit(ws[picks[i]].volume, ws[picks[i]].binning, params[picks[i]],
                                 kind=kinds[i])
 
     th = threading.Thread(target=submitter)
@@ -641,42 +806,55 @@ def run_serving(ctx_factory, ks, synth, rate=50.0, count=200, pool=24, max_dim=N
         t_last = max(t_last, res["t_done_us"])
         ctx.release_result(ids[i])
     span = (t_last - t_first) * 1e-6
+    seeds_ms, seeds_n = ctx.kernel_time("ks_seeds")
+    dense_ms, dense_n = ctx.kernel_time("ks_dense")
     ctx.close()
-    # plain sequential path: service time of each request alone, then an
-    # arrival-order queue
+
+    # sequential arm, measured: one worker, arrival order, real time
     ctx = ctx_factory()
-    service = {}
-    for i in range(count):
-        key = (picks[i], kinds[i])
-        if key in service:
-            continue
-        w = ws[picks[i]]
-        p = ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter)
-        for rep in range(2):
-            import torch
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            v = ctx.create_volume(w.volume, w.binning)
-            if kinds[i] == ks.KS_REQ_DENSE:
-                ctx.dense_saliency(v, p, w.volume.shape)
-            else:
-                ctx.seed_climb(v, p)
-                ctx.meanshift(v, p)
-            ctx.release_volume(v)
-            service[key] = time.perf_counter() - t
-    ctx.close()
-    finish, seq_lat = 0.0, []
+    pinned = []
+    for w in ws:
+        h = torch.empty(w.volume.nbytes, dtype=torch.uint8, pin_memory=True).numpy()
+        h = h.view(w.volume.dtype).reshape(w.volume.shape)
+        h[...] = w.volume
+        pinned.append(h)
+
+    def plain(i):
+        k = picks[i]
+        v = ctx.create_volume(pinned[k], ws[k].binning)
+        if kinds[i] == ks.KS_REQ_DENSE:
+            ctx.dense_saliency(v, params[k], ws[k].volume.shape)
+        else:
+            ctx.seed_climb(v, params[k])
+            ctx.meanshift(v, params[k])
+        ctx.release_volume(v)
+
+    for i in range(min(pool, 8)):                 # warm-up
+        plain(picks.index(i) if i in picks else 0)
+    torch.cuda.synchronize()
+    seq_lat = []
+    t0 = time.perf_counter()
     for i, r in enumerate(reqs):
-        finish = max(finish, r["t"]) + service[(picks[i], kinds[i])]
-        seq_lat.append((finish - r["t"]) * 1e3)
-    seq_span = finish - reqs[0]["t"]
+        now = time.perf_counter() - t0
+        if r["t"] > now:
+            time.sleep(r["t"] - now)
+        plain(i)
+        seq_lat.append((time.perf_counter() - t0 - r["t"]) * 1e3)
+    seq_span = time.perf_counter() - t0 - reqs[0]["t"]
+    ctx.close()
     return {"rate_per_s": rate, "requests": count, "pool_volumes": pool,
             "max_dim": max_dim or 256, "dense_fraction": dense_frac,
+            "wave_iters": 0 if wave_iters is None else wave_iters,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "volumes_per_s": count / span,
+            "volumes_per_s": count / span, "span_s": span,
+            "device_busy": {"seed_waves_ms": seeds_ms, "seed_launches": seeds_n,
+                            "dense_ms": dense_ms, "dense_launches": dense_n,
+                            "note": "CUDA-event time of the serving streams' launches; waves "
+                                    "and dense sweeps overlap, so the sum can exceed the span"},
             "sequential_p50_ms": float(np.percentile(seq_lat, 50)),
             "sequential_p99_ms": float(np.percentile(seq_lat, 99)),
-            "sequential_volumes_per_s": count / seq_span}
+            "sequential_volumes_per_s": count / seq_span, "sequential_span_s": seq_span,
+            "sequential": "measured: the plain calls, one request at a time in arrival order"}
 
 
 # FP32 and INT32 lane operations the ABMSOD definition takes per window
@@ -857,49 +1035,16 @@ def run_abmsod(args):
 
 
 def run_bin(args):
-    """Binning alone, an HBM-bound kernel: three raw types on a 512x512x256
-    volume (far above the 126 MB L2).  Per type, the ks_bin kernels' CUDA-event
-    time over --steps calls of ks_create_volume from device memory; the
-    algorithmic bytes are the raw read (float32 also its min/max pass) plus one
-    byte written per voxel."""
-    import torch
+    """Binning alone (binning_rows) as its own line."""
     from paper_1310_6736_b300 import ks
-    nz, ny, nx = 256, 512, 512
-    n = nx * ny * nz
-    peaks, kind = _peaks()
     ctx = ks.Context()
-    g = torch.Generator(device="cuda")
-    g.manual_seed(3)
-    cases = [
-        ("uint8, v >> 3 (32 bins)", torch.randint(0, 256, (nz, ny, nx), generator=g,
-                                                  device="cuda", dtype=torch.uint8),
-         {"kind": 0, "bins": 32, "shift": 3, "lo": 0, "hi": 255}, 2),
-        ("int16, clamp to [0, 2047] >> 5 (64 bins)",
-         torch.randint(-100, 2200, (nz, ny, nx), generator=g, device="cuda", dtype=torch.int16),
-         {"kind": 0, "bins": 64, "shift": 5, "lo": 0, "hi": 2047}, 3),
-        ("float32, affine over [vmin, vmax] (32 bins; min/max pass)",
-         torch.rand((nz, ny, nx), generator=g, device="cuda", dtype=torch.float32) * 100.0,
-         {"kind": 1, "bins": 32, "shift": 0, "lo": 0, "hi": 0}, 9),
-    ]
-    rows = []
-    for name, raw, binning, bpv in cases:
-        for _ in range(max(args.warmup, 3)):
-            ctx.release_volume(ctx.create_volume(raw, binning))
-        ctx.set_profiling(True)
-        for _ in range(args.steps):
-            ctx.release_volume(ctx.create_volume(raw, binning))
-        ms, launches = ctx.kernel_time("ks_bin")
-        ctx.set_profiling(False)
-        t = ms / max(1, launches) * 1e-3
-        gbs = n * bpv / t / 1e9
-        rows.append({"raw": name, "voxels": n, "bytes_per_voxel": bpv, "ms": t * 1e3,
-                     "achieved_gbs": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"]})
+    rows, what, hbm, kind = binning_rows(ctx, ks, steps=args.steps, warmup=max(args.warmup, 3))
     ctx.close()
     line = {"metric": "binning bandwidth (algorithmic bytes / kernel time)",
             "value": min(r["frac_of_hbm"] for r in rows), "unit": "fraction of measured HBM copy",
             "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": f"{nx}x{ny}x{nz} random volumes", "peak_hbm_gbs": peaks["hbm_gbs"],
-                       "peaks_source": kind, "rows": rows}}
+            "config": {"workload": what, "peak_hbm_gbs": hbm, "peaks_source": kind,
+                       "rows": rows}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -931,7 +1076,9 @@ def run_mode(args):
                 "config": {"workload": "batch of uneven uint8/int16 volumes", **r}}
     else:
         rows = [run_serving(ks.Context, ks, synth, rate=rate, count=args.count,
-                            max_dim=args.max_dim or None) for rate in args.rates]
+                            max_dim=args.max_dim or None, pool=args.pool,
+                            wave_iters=None if args.wave_iters < 0 else args.wave_iters)
+                for rate in args.rates]
         line = {"metric": "p50/p99 latency and volumes/s (continuous batching vs sequential)",
                 "value": rows[0]["p50_ms"], "unit": "ms (p50)", "higher_is_better": False,
                 "n_gpus": 1, "data": "synthetic", "config": {"serving": rows}}
@@ -972,6 +1119,9 @@ def main():
                          "choice; 33: every item on one warp)")
     ap.add_argument("--max-dim", type=int, default=0, help="cap on each volume dimension")
     ap.add_argument("--rates", type=float, nargs="+", default=[20.0, 50.0, 100.0])
+    ap.add_argument("--pool", type=int, default=32, help="serving: distinct volumes in the pool")
+    ap.add_argument("--wave-iters", type=int, default=-1,
+                    help="serving: iterations per seed item and wave (-1: the library default)")
     ap.add_argument("--no-extras", action="store_true",
                     help="step mode: skip the short batched and serving measurements")
     args = ap.parse_args()

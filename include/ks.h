@@ -374,6 +374,13 @@ int ks_cancel(ks_ctx *ctx, ks_req req);
 /* Free a finished request's result arrays. */
 int ks_release_result(ks_ctx *ctx, ks_req req);
 
+/* Iterations each seed item may advance per wave of the serving loop
+ * (default 0 = a whole search per wave).  Waves are one persistent
+ * launch per class over the items of every admitted seed request; a
+ * request that arrives joins the next wave.  Results do not depend on it.
+ * Errors: KS_EINVAL (iters outside [0, 1000]). */
+int ks_set_serve_wave_iters(ks_ctx *ctx, int iters);
+
 /* ---------------------------------------------------------- diagnostics */
 
 /* Copy the device tables T[0..nmax] and L[0..nmax] (nmax <= |Ball(32)|) to

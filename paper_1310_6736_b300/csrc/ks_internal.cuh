@@ -257,7 +257,19 @@ struct SeedJob {
     int32_t *traj;               // device, n_seeds * (max_iter+1) * 3, or null
     int planar;                  // octant kind: 1 = the quadrant climb (disks in the
                                  // seed's z-slice, four quadrants), 0 = octants
+    // Resumable searches (the serving loop), or null / 0 for whole searches:
+    // state holds one int4 per item (octant item s at [s], mean-shift item i
+    // at [n_seeds + i]): the centre and it | kItemStarted | kItemDone; a
+    // launch advances every unfinished item by at most iter_budget
+    // iterations, keeps its state, and on finishing writes the record and
+    // adds 1 to *finished.  Zeroed state = not started.  The sequence of
+    // operations per item is the whole search's, so records are identical.
+    int4 *state;
+    unsigned int *finished;
+    int iter_budget;
 };
+constexpr int kItemStarted = 1 << 8;
+constexpr int kItemDone = 1 << 9;
 // A work queue in tickets: segment k covers tickets [seg_start[k],
 // seg_start[k+1]) of kind seg_kind[k] on job seg_job[k]; seed_tickets()
 // tells how many tickets of a kind a job needs.  kMsWarp segments must come

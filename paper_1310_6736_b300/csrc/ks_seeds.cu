@@ -352,10 +352,22 @@ __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &
     uint32_t *extra = cnt + 8 * S * Bs;
     int P[3] = {J.seeds[3 * sidx], J.seeds[3 * sidx + 1], J.seeds[3 * sidx + 2]};
     const int T1 = J.max_iter + 1;
-    if (threadIdx.x == 0 && J.traj)
-        for (int a = 0; a < 3; ++a) J.traj[(sidx * T1) * 3 + a] = P[a];
     int it = 0, conv = 0, fresh = 0;
-    while (it < J.max_iter) {
+    int4 *stp = J.state ? J.state + sidx : nullptr;
+    if (stp) {
+        const int4 st = *stp;
+        if (st.w & kItemDone) return;
+        if (st.w & kItemStarted) {
+            P[0] = st.x;
+            P[1] = st.y;
+            P[2] = st.z;
+            it = st.w & 255;
+        }
+    }
+    if (threadIdx.x == 0 && J.traj && it == 0)
+        for (int a = 0; a < 3; ++a) J.traj[(sidx * T1) * 3 + a] = P[a];
+    const int it_end = J.iter_budget > 0 ? min(J.max_iter, it + J.iter_budget) : J.max_iter;
+    while (it < it_end) {
         octant_pass(J, ot, cnt, P);
         fresh = 1;
         for (int w = threadIdx.x; w < 8 * S; w += blockDim.x)
@@ -376,6 +388,11 @@ __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &
         if (threadIdx.x == 0 && J.traj)
             for (int a = 0; a < 3; ++a) J.traj[(sidx * T1 + it) * 3 + a] = P[a];
     }
+    if (stp && !conv && it < J.max_iter) {   // the budget ran out: keep the state
+        __syncthreads();
+        if (threadIdx.x == 0) *stp = make_int4(P[0], P[1], P[2], it | kItemStarted);
+        return;
+    }
     if (threadIdx.x == 0 && J.traj)
         for (int t = it + (conv ? 0 : 1); t <= J.max_iter; ++t)
             for (int a = 0; a < 3; ++a) J.traj[(sidx * T1 + t) * 3 + a] = P[a];
@@ -392,6 +409,10 @@ __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &
         o->iters = it;
         o->converged = conv;
         o->reserved = 0;
+        if (stp) {
+            *stp = make_int4(P[0], P[1], P[2], it | kItemStarted | kItemDone);
+            atomicAdd(J.finished, 1u);
+        }
     }
 }
 
@@ -715,7 +736,19 @@ __device__ void ms_item(const SeedJob &J, int64_t item, const OffsetTables &ot, 
     const int r = J.r_min + (int)(item % J.S);
     int P[3] = {J.seeds[3 * sidx], J.seeds[3 * sidx + 1], J.seeds[3 * sidx + 2]};
     int it = 0, conv = 0, fresh = 0;
-    while (it < J.max_iter) {
+    int4 *stp = J.state ? J.state + J.n_seeds + item : nullptr;
+    if (stp) {
+        const int4 st = *stp;
+        if (st.w & kItemDone) return;
+        if (st.w & kItemStarted) {
+            P[0] = st.x;
+            P[1] = st.y;
+            P[2] = st.z;
+            it = st.w & 255;
+        }
+    }
+    const int it_end = J.iter_budget > 0 ? min(J.max_iter, it + J.iter_budget) : J.max_iter;
+    while (it < it_end) {
         ms_pass(J, ot, cols, part, acc, P, r);
         if (threadIdx.x < 32) {
             int d[3];
@@ -736,8 +769,17 @@ __device__ void ms_item(const SeedJob &J, int64_t item, const OffsetTables &ot, 
         for (int a = 0; a < 3; ++a) P[a] = Pn[a];
         fresh = 0;
     }
+    if (stp && !conv && it < J.max_iter) {   // the budget ran out: keep the state
+        __syncthreads();
+        if (threadIdx.x == 0) *stp = make_int4(P[0], P[1], P[2], it | kItemStarted);
+        return;
+    }
     if (!fresh) ms_pass(J, ot, cols, part, acc, P, r);
     if (threadIdx.x < 32) ms_result_warp(J, item, acc, prod, T, L, P, r, it, conv);
+    if (stp && threadIdx.x == 0) {
+        *stp = make_int4(P[0], P[1], P[2], it | kItemStarted | kItemDone);
+        atomicAdd(J.finished, 1u);
+    }
     __syncthreads();
 }
 
@@ -753,7 +795,19 @@ __device__ void ms_item_warp(const SeedJob &J, int64_t item, const OffsetTables 
     const int r = J.r_min + (int)(item % J.S);
     int P[3] = {J.seeds[3 * sidx], J.seeds[3 * sidx + 1], J.seeds[3 * sidx + 2]};
     int it = 0, conv = 0, fresh = 0;
-    while (it < J.max_iter) {
+    int4 *stp = J.state ? J.state + J.n_seeds + item : nullptr;
+    if (stp) {
+        const int4 st = *stp;
+        if (st.w & kItemDone) return;
+        if (st.w & kItemStarted) {
+            P[0] = st.x;
+            P[1] = st.y;
+            P[2] = st.z;
+            it = st.w & 255;
+        }
+    }
+    const int it_end = J.iter_budget > 0 ? min(J.max_iter, it + J.iter_budget) : J.max_iter;
+    while (it < it_end) {
         ms_pass_warp(J, ot, region, acc, P, r);
         int d[3];
         ms_delta_warp(B, acc, prod, d);
@@ -768,8 +822,18 @@ __device__ void ms_item_warp(const SeedJob &J, int64_t item, const OffsetTables 
         for (int a = 0; a < 3; ++a) P[a] = Pn[a];
         fresh = 0;
     }
+    if (stp && !conv && it < J.max_iter) {   // the budget ran out: keep the state
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) *stp = make_int4(P[0], P[1], P[2], it | kItemStarted);
+        return;
+    }
     if (!fresh) ms_pass_warp(J, ot, region, acc, P, r);
     ms_result_warp(J, item, acc, prod, T, L, P, r, it, conv);
+    if (stp && (threadIdx.x & 31) == 0) {
+        *stp = make_int4(P[0], P[1], P[2], it | kItemStarted | kItemDone);
+        atomicAdd(J.finished, 1u);
+    }
+    __syncwarp();
 }
 
 // Shared-memory layout of one block (the octant and mean-shift views

@@ -103,6 +103,7 @@ SIGNATURES = {
     "ks_poll": (_I, [_P, _I64, _I64, C.POINTER(ks_result)]),
     "ks_cancel": (_I, [_P, _I64]),
     "ks_release_result": (_I, [_P, _I64]),
+    "ks_set_serve_wave_iters": (_I, [_P, _I]),
     "ks_tables": (_I, [_P, _I64, _P, _P]),
     "ks_launch_count": (_I64, [_P]),
     "ks_set_profiling": (_I, [_P, _I]),
@@ -504,6 +505,10 @@ class Context:
 
     def cancel(self, req):
         return lib().ks_cancel(self.h, int(req))
+
+    def set_serve_wave_iters(self, iters):
+        """Iterations per seed item and serving wave (0 = whole searches)."""
+        self._check(lib().ks_set_serve_wave_iters(self.h, int(iters)), "ks_set_serve_wave_iters")
 
     def release_result(self, req):
         return lib().ks_release_result(self.h, int(req))

@@ -487,6 +487,20 @@ def test_serving_results_alone_equal_mixed(ko, ks_mod):
             assert (k in a) == (k in res)
             if k in a:
                 assert np.array_equal(a[k], res[k]), k
+    # seed items advance 1 iteration per wave, or whole searches per wave:
+    # the same records
+    for iters in (1, 0):
+        c1.set_serve_wave_iters(iters)
+        ids = [c1.submit(w.volume, w.binning, _params(ks, w),
+                         kind=ks.KS_REQ_DENSE if i % 3 == 2 else ks.KS_REQ_SEEDS)
+               for i, w in enumerate(ws)]
+        for rid, a in zip(ids, alone):
+            st, res = c1.poll(rid, -1)
+            assert st == ks.KS_OK
+            for k in ("oct", "ms", "Y", "s"):
+                if k in a:
+                    assert np.array_equal(a[k], res[k]), (iters, k)
+    c1.set_serve_wave_iters(4)
     # the plain path gives the same numbers, and so does the oracle
     v = c1.create_volume(ws[0].volume, ws[0].binning)
     assert np.array_equal(alone[0]["oct"], c1.seed_climb(v, _params(ks, ws[0])))
