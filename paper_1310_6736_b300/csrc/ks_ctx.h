@@ -122,8 +122,9 @@ std::vector<ClassLaunch> plan_class_queues(Ctx *c, const std::vector<SeedJob> &j
                                            std::vector<uint8_t> &image, size_t plan_at,
                                            uint8_t *dev_base);
 // The classes run one after another on s, each a persistent launch over its
-// queue (running the octant and mean-shift classes side by side on two
-// streams made the batch slower: they compete for the same SMs).
+// queue.  Run side by side (octant and mean-shift classes on two streams of
+// equal priority, or every class on its own stream of descending priority)
+// they were slower: each class fills the GPU, and they compete for it.
 cudaError_t launch_class_queues(Ctx *c, cudaStream_t s, int *d_status,
                                 const std::vector<ClassLaunch> &cls);
 
