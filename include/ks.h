@@ -71,10 +71,15 @@ typedef enum ks_dtype { KS_U8 = 0, KS_I16 = 1, KS_F32 = 2 } ks_dtype;
  *                       vmin/vmax = exact volume minimum/maximum
  *   KS_BIN_WINDOW       integer input: v outside [lo, hi] is not counted,
  *                       otherwise b = (v - lo) >> shift
- * Requirements: 2 <= bins <= 64; for the integer kinds lo <= hi and
+ *   KS_BIN_STORED       uint8 input that is already a bin volume in the
+ *                       stored form (ks_volume_bins): v in [1, bins] is bin
+ *                       v - 1, any other value is not counted (lets ranks
+ *                       that share one volume exchange its bins instead of
+ *                       its raw values; shift, lo, hi unused)
+ * Requirements: 2 <= bins <= 64; for CLAMP_SHIFT and WINDOW lo <= hi and
  * ((hi - lo) >> shift) <= bins - 1. */
 typedef enum ks_bin_kind {
-    KS_BIN_CLAMP_SHIFT = 0, KS_BIN_AFFINE_F32 = 1, KS_BIN_WINDOW = 2
+    KS_BIN_CLAMP_SHIFT = 0, KS_BIN_AFFINE_F32 = 1, KS_BIN_WINDOW = 2, KS_BIN_STORED = 3
 } ks_bin_kind;
 
 typedef struct ks_binning {
@@ -185,6 +190,15 @@ int ks_volume_bins(ks_ctx *ctx, ks_vol vol, uint8_t *out, int out_on_device);
  * KS_ETIMEDOUT. */
 int ks_dense_saliency(ks_ctx *ctx, ks_vol vol, const ks_params *params,
                       double *Y_best, uint8_t *s_best, int out_on_device);
+
+/* ks_dense_saliency for the centres of the z-planes [z0, z1) only (0 <= z0
+ * < z1 <= nz): their windows still see the whole volume.  Y_best and s_best
+ * hold (z1 - z0)*ny*nx values, plane z0 first; each equals the whole
+ * sweep's value at the same voxel.  The split of one volume into z-slabs
+ * across ranks (Sec. 2.4 runs a search path per thread block; here a slab
+ * per GPU, each rank holding its slab plus r_max halo planes). */
+int ks_dense_saliency_range(ks_ctx *ctx, ks_vol vol, const ks_params *params, int z0, int z1,
+                            double *Y_best, uint8_t *s_best, int out_on_device);
 
 /* As ks_dense_saliency, optionally also writing H(r) and W(r) for every
  * voxel and scale: H, W are nx*ny*nz*S doubles (S = r_max - r_min + 1),

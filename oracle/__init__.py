@@ -28,7 +28,7 @@ _LIB = os.path.join(_HERE, "libks_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BIN_CLAMP_SHIFT, BIN_AFFINE_F32, BIN_WINDOW = 0, 1, 2
+BIN_CLAMP_SHIFT, BIN_AFFINE_F32, BIN_WINDOW, BIN_STORED = 0, 1, 2, 3
 
 
 def build(force=False):

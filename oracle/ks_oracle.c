@@ -65,7 +65,9 @@ void ko_tables(int64_t nmax, double *T, double *L)
 /* ------------------------------------------------------------------------ */
 /* Binning: the bin index beta(s) of Eq. 4-5, stored as b+1.                 */
 /* ------------------------------------------------------------------------ */
-enum { KO_BIN_CLAMP_SHIFT = 0, KO_BIN_AFFINE_F32 = 1, KO_BIN_WINDOW = 2 };
+/* KO_BIN_STORED: the input is already a bin volume in the stored form (b+1,
+ * 0 = not counted); values outside [1, bins] are not counted. */
+enum { KO_BIN_CLAMP_SHIFT = 0, KO_BIN_AFFINE_F32 = 1, KO_BIN_WINDOW = 2, KO_BIN_STORED = 3 };
 
 /* Integer inputs (uint8 / int16 widened to int32).
  *   CLAMP_SHIFT: b = (clamp(v, lo, hi) - lo) >> shift
@@ -76,6 +78,10 @@ void ko_bin_int(const int32_t *v, int64_t n, int kind, int bins, int shift,
 {
     for (int64_t i = 0; i < n; ++i) {
         int32_t x = v[i];
+        if (kind == KO_BIN_STORED) {           /* already stored bin values */
+            out[i] = (uint8_t)(x >= 1 && x <= bins ? x : 0);
+            continue;
+        }
         if (kind == KO_BIN_WINDOW && (x < lo || x > hi)) {
             out[i] = 0;
             continue;

@@ -167,6 +167,10 @@ int validate_binning(int dtype, const ks_binning *b, std::string *why) {
         if (dtype != KS_F32) return *why = "AFFINE_F32 binning needs float32 data", KS_EINVAL;
         return KS_OK;
     }
+    if (b->kind == KS_BIN_STORED) {
+        if (dtype != KS_U8) return *why = "STORED binning needs uint8 data", KS_EINVAL;
+        return KS_OK;
+    }
     if (b->kind != KS_BIN_CLAMP_SHIFT && b->kind != KS_BIN_WINDOW)
         return *why = "unknown binning kind", KS_EINVAL;
     if (dtype == KS_F32) return *why = "integer binning needs uint8 or int16 data", KS_EINVAL;
@@ -900,6 +904,39 @@ int ks_dense_saliency_ex(ks_ctx *ctx, ks_vol vol, const ks_params *params, doubl
         KS_TRY_CUDA(c, cudaMemcpyAsync(s_best, o.s, n, cudaMemcpyDeviceToHost, c->stream));
         if (H) KS_TRY_CUDA(c, cudaMemcpyAsync(H, o.H, n * S * 8, cudaMemcpyDeviceToHost, c->stream));
         if (W) KS_TRY_CUDA(c, cudaMemcpyAsync(W, o.W, n * S * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    return check_status(c);
+}
+
+int ks_dense_saliency_range(ks_ctx *ctx, ks_vol vol, const ks_params *params, int z0, int z1,
+                            double *Y, uint8_t *s_best, int out_on_device) {
+    if (!ctx) return KS_EINVAL;
+    Ctx *c = &ctx->impl;
+    std::string why;
+    int st = validate_params(params, &why);
+    if (st) return set_err(c, st, why);
+    if (!Y || !s_best) return set_err(c, KS_EINVAL, "Y_best / s_best is NULL");
+    Volume *v = find_volume(c, vol);
+    if (!v) return set_err(c, KS_ENOTFOUND, "unknown volume");
+    if (z0 < 0 || z1 > v->nz || z0 >= z1) return set_err(c, KS_EINVAL, "need 0 <= z0 < z1 <= nz");
+    const int64_t plane = (int64_t)v->nx * v->ny;
+    const size_t n = (size_t)(plane * (z1 - z0));
+    cudaError_t e = cudaSuccess;
+    double *dY = Y;
+    uint8_t *ds = s_best;
+    if (!out_on_device) {
+        dY = (double *)scratch(c, kScY, n * 8, &e);
+        if (dY) ds = (uint8_t *)scratch(c, kScS, n, &e);
+        if (e != cudaSuccess) return cuda_err(c, e, "dense outputs");
+    }
+    // the kernels index outputs by the voxel's index in the whole volume and
+    // write only planes [z0, z1): shift the bases back by z0 planes
+    const DenseOut o{dY - plane * z0, ds - plane * z0, nullptr, nullptr};
+    st = run_dense(c, c->stream, v, params, o, z0, z1);
+    if (st) return st;
+    if (!out_on_device) {
+        KS_TRY_CUDA(c, cudaMemcpyAsync(Y, dY, n * 8, cudaMemcpyDeviceToHost, c->stream));
+        KS_TRY_CUDA(c, cudaMemcpyAsync(s_best, ds, n, cudaMemcpyDeviceToHost, c->stream));
     }
     return check_status(c);
 }

@@ -17,6 +17,7 @@ struct IntBin {
     // and the cap never apply, so every voxel is (v >> shift) + 1
     bool bytewise;
     __device__ __forceinline__ uint8_t operator()(int v) const {
+        if (kind == KS_BIN_STORED) return (uint8_t)(v >= 1 && v <= bins ? v : 0);
         if (kind == KS_BIN_WINDOW && (v < lo || v > hi)) return 0;
         v = v < lo ? lo : (v > hi ? hi : v);
         int b = (v - lo) >> shift;

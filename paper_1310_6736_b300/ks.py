@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libks.so")
 KS_OK, KS_PENDING, KS_EINVAL, KS_ENOMEM, KS_ECUDA, KS_ETIMEDOUT, KS_ECANCELED, \
     KS_ENOTFOUND, KS_ENODEV = 0, 1, -1, -2, -3, -4, -5, -6, -7
 KS_U8, KS_I16, KS_F32 = 0, 1, 2
-KS_BIN_CLAMP_SHIFT, KS_BIN_AFFINE_F32, KS_BIN_WINDOW = 0, 1, 2
+KS_BIN_CLAMP_SHIFT, KS_BIN_AFFINE_F32, KS_BIN_WINDOW, KS_BIN_STORED = 0, 1, 2, 3
 KS_WNORM_KB, KS_WNORM_ONE = 0, 1
 KS_REQ_SEEDS, KS_REQ_DENSE = 0, 1
 
@@ -82,6 +82,7 @@ SIGNATURES = {
     "ks_volume_bins": (_I, [_P, _I64, _P, _I]),
     "ks_dense_saliency": (_I, [_P, _I64, C.POINTER(ks_params), _P, _P, _I]),
     "ks_dense_saliency_ex": (_I, [_P, _I64, C.POINTER(ks_params), _P, _P, _P, _P, _I]),
+    "ks_dense_saliency_range": (_I, [_P, _I64, C.POINTER(ks_params), _I, _I, _P, _P, _I]),
     "ks_seed_count": (_I, [_P, _I64, C.POINTER(ks_params), C.POINTER(C.c_int64)]),
     "ks_seed_climb": (_I, [_P, _I64, C.POINTER(ks_params), _P, _I64, _P, _I64,
                            C.POINTER(C.c_int64), _P, _I]),
@@ -255,6 +256,18 @@ class Context:
             C.c_void_p(H.ctypes.data) if want_hw else None,
             C.c_void_p(W.ctypes.data) if want_hw else None, 0), "ks_dense_saliency")
         return (Y, s, H, W) if want_hw else (Y, s)
+
+    def dense_saliency_range(self, v, params, shape, z0, z1):
+        """Dense sweep for the centres of planes [z0, z1): host (Y, s) of
+        shape (z1 - z0, ny, nx), equal to the whole sweep's planes."""
+        nz, ny, nx = shape
+        Y = np.empty((z1 - z0, ny, nx), np.float64)
+        s = np.empty((z1 - z0, ny, nx), np.uint8)
+        self._check(lib().ks_dense_saliency_range(self.h, int(v), C.byref(params), int(z0),
+                                                  int(z1), C.c_void_p(Y.ctypes.data),
+                                                  C.c_void_p(s.ctypes.data), 0),
+                    "ks_dense_saliency_range")
+        return Y, s
 
     def seed_count(self, v, params):
         n = C.c_int64()

@@ -923,3 +923,39 @@ def test_abmsod_candidates_entry_point(ctx, ko, ks_mod):
         assert e.value.status == ks.KS_EINVAL
     assert len(ctx.abmsod_candidates(v, x0, H0, max_iter=1)) == len(x0)   # context still usable
     ctx.release_volume(v)
+
+
+# ------------------------------------------- dense sweep in z-slabs (GPU)
+def test_stored_bins_and_dense_range_equal_the_whole_sweep(ctx, ko, ks_mod):
+    """A volume made from stored bins (KS_BIN_STORED) reproduces them
+    (values above `bins` are not counted); the sweep of planes [z0, z1)
+    equals the whole sweep's planes; three z-slabs with their r_max halos,
+    each swept on the GPU, merge into the whole sweep (the per-rank work of
+    the sharded dense sweep, run here in one process)."""
+    from paper_1310_6736_b300 import shard
+    ks = ks_mod
+    w = synth.workload("pet128")
+    p = _params(ks, w)
+    v = ctx.create_volume(w.volume, w.binning)
+    Y, s = ctx.dense_saliency(v, p, w.volume.shape)
+    bins = ctx.volume_bins(v, w.volume.shape)
+    Yr, sr = ctx.dense_saliency_range(v, p, w.volume.shape, 20, 44)
+    ctx.release_volume(v)
+    assert np.array_equal(sr, s[20:44]) and np.array_equal(Yr, Y[20:44])
+    noisy = bins.copy()
+    noisy[::7, 3, 5] = 250                                   # above bins: not counted
+    vs = ctx.create_volume(noisy, {"kind": ks.KS_BIN_STORED, "bins": 32, "shift": 0, "lo": 0,
+                                   "hi": 0})
+    want = np.where(noisy <= 32, noisy, 0)
+    assert np.array_equal(ctx.volume_bins(vs, w.volume.shape), want)
+    ctx.release_volume(vs)
+    ex = shard.gpu_slab_executor(ctx, 32, p)
+    parts = [shard.dense_slab(bins, w.r_max, z0, z1, ex) for z0, z1 in shard.z_slabs(64, 3)]
+    Ym, sm = shard.merge_slabs(parts, 64)
+    assert np.array_equal(sm, s) and np.array_equal(Ym, Y)
+    Yo, so = ko.dense(bins, 32, w.r_min, w.r_max,
+                      centres=np.array([[5, 7, 21], [64, 64, 22], [127, 0, 43]], np.int32))
+    assert np.array_equal(sm[[21, 22, 43], [7, 64, 0], [5, 64, 127]], so)
+    with pytest.raises(ks.KsError):
+        ctx.create_volume(w.volume, {"kind": ks.KS_BIN_STORED, "bins": 32, "shift": 0, "lo": 0,
+                                     "hi": 0})                # float32 data: refused

@@ -68,3 +68,74 @@ def test_two_gloo_ranks_equal_one_process(tmp_path, ko):
         assert np.array_equal(got[f"oc_{k}"], v), k
     for k, v in ms.items():
         assert np.array_equal(got[f"ms_{k}"], v), k
+
+
+# ------------------------------------------------- dense sweep in z-slabs
+def _oracle_slab_executor(ko, B, r_min, r_max):
+    """A rank's executor with the oracle standing in for its GPU: the dense
+    sweep of the halo'd slab, cut to the rank's own planes."""
+    def run(slab, lo, hi):
+        Y, s = ko.dense(slab, B, r_min, r_max, nthreads=1)
+        return Y[lo:hi], s[lo:hi]
+    return run
+
+
+def _slab_rank_main(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1310_6736_b300 import shard, synth
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    w = synth.workload("spheres48")
+    # rank 0 bins the volume and broadcasts the bins (the exchange step)
+    t = torch.from_numpy(oracle.bin_volume(w.volume, w.binning)) if rank == 0 else \
+        torch.empty(w.volume.shape, dtype=torch.uint8)
+    dist.broadcast(t, src=0)
+    bins = t.numpy()
+    z0, z1 = shard.z_slabs(bins.shape[0], world)[rank]
+    local = shard.dense_slab(bins, w.r_max, z0, z1,
+                             _oracle_slab_executor(oracle, 16, w.r_min, w.r_max))
+    Y, s = shard.gather_slabs(local, bins.shape[0])
+    if rank == 0:
+        np.savez(os.path.join(out_dir, "slabs.npz"), Y=Y, s=s)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_dense_z_slabs_two_gloo_ranks_equal_one_process(tmp_path, ko):
+    """Two gloo ranks sweep the two z-slabs of the spheres volume (48
+    planes, r_max = 10 halo planes each side) and gather: the result equals
+    the whole sweep exactly."""
+    from paper_1310_6736_b300 import synth
+    port = _free_port()
+    mp.start_processes(_slab_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    got = np.load(tmp_path / "slabs.npz")
+    w = synth.workload("spheres48")
+    Y, s = ko.dense(ko.bin_volume(w.volume, w.binning), 16, w.r_min, w.r_max)
+    assert np.array_equal(got["s"], s)
+    assert np.array_equal(got["Y"].view(np.uint64), Y.view(np.uint64))
+
+
+@pytest.mark.parametrize("world", [3, 5, 30])
+def test_dense_z_slabs_uneven_splits(ko, world):
+    """Uneven splits, halos wider than a slab, and more ranks than planes
+    (empty slabs): the merged slabs equal the whole sweep."""
+    from paper_1310_6736_b300 import shard
+    rng = np.random.default_rng(world)
+    bins = rng.integers(0, 6, size=(23, 14, 17)).astype(np.uint8)     # 0 = not counted
+    B, r_min, r_max = 5, 1, 6
+    ex = _oracle_slab_executor(ko, B, r_min, r_max)
+    parts = [shard.dense_slab(bins, r_max, z0, z1, ex)
+             for z0, z1 in shard.z_slabs(bins.shape[0], world)]
+    Y, s = shard.merge_slabs(parts, bins.shape[0])
+    Yo, so = ko.dense(bins, B, r_min, r_max)
+    assert np.array_equal(s, so)
+    assert np.array_equal(Y.view(np.uint64), Yo.view(np.uint64))
+    assert shard.z_slabs(23, world)[-1][1] == 23
+    assert all(h0 <= z0 and h1 >= z1 and h1 - h0 <= z1 - z0 + 2 * r_max
+               for z0, z1 in shard.z_slabs(23, world)
+               for h0, h1 in [shard.halo_planes(z0, z1, 23, r_max)])
