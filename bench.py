@@ -323,6 +323,7 @@ def run_ks(args):
 
     # ---- roofline of the dominant kernel (dense sweep: shared-memory bound)
     smem_peak = ctx.measure_smem_peak()
+    red_peak = ctx.measure_smem_red_rate()             # reductions alone: the strict ceiling
     fp64_rate = ctx.measure_fp64_rate()                # the FP64 sums' pipe, for context
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     upd_per_launch = n_vox * ks_ball_size(w.r_max)     # window-voxel updates per launch
@@ -372,13 +373,16 @@ def run_ks(args):
                          "kernel_share_of_step": dense_ms / max(1e-9, tot_ms),
                          "in_step": "the seed searches run beside the dense sweep's last wave, "
                                     "so its event time in the step includes sharing the SMs",
+                         "frac_of_reduction_only_rate": achieved / red_peak,
                          "alone": {"kernel_ms": alone_ms / max(1, alone_n),
                                    "achieved": upd_per_launch / (alone_ms / max(1, alone_n) * 1e-3)
                                    / 1e9,
                                    "frac": upd_per_launch / (alone_ms / max(1, alone_n) * 1e-3)
                                    / smem_peak,
                                    "launches": alone_n}},
-            "micro_peaks": {"smem_increments_per_s": smem_peak, "fp64_dadd_per_s": fp64_rate,
+            "micro_peaks": {"smem_increments_per_s": smem_peak,
+                            "smem_reductions_only_per_s": red_peak,
+                            "fp64_dadd_per_s": fp64_rate,
                             "fp64_dadd_per_sm_clock": fp64_rate / (n_sms * 1e6 *
                                                                    (clocks.get("sm_mhz") or 2032.0)),
                             "how": "ks_measure_smem_peak / ks_measure_fp64_rate micro-kernels"},

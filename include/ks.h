@@ -415,6 +415,11 @@ int ks_kernel_time(ks_ctx *ctx, const char *prefix, double *ms_total, int64_t *l
  * micro-kernel: the denominator of the histogram kernels' roofline. */
 int ks_measure_smem_peak(ks_ctx *ctx, double *increments_per_s);
 
+/* The same counters updated by shared-memory reductions alone (no byte
+ * loads, no address arithmetic): the rate no histogram kernel with one
+ * reduction per update can exceed. */
+int ks_measure_smem_red_rate(ks_ctx *ctx, double *increments_per_s);
+
 /* FP64 addition rate of this device (__dadd_rn lane operations per second):
  * a micro-kernel of independent addition chains on every SM.  The entropy
  * sums and the seed steps are FP64 additions in a fixed order. */
@@ -425,14 +430,17 @@ int ks_measure_fp64_rate(ks_ctx *ctx, double *dadd_per_s);
  * 2 = direct L2 reads with two centres (x and x + 32) per thread, 3 = four
  * adjacent centres per thread (r_max <= 25 only), 4 = path 3 with the
  * previous-scale counts in tensor memory (r_max <= 25, bins <= 32, and not
- * 8 or fewer); warps per block; tile rows in y and z. */
+ * 8 or fewer), 5 = sliding windows (one histogram per scale, each updated
+ * by the voxels entering and leaving its ball as the centre moves along z;
+ * r_max <= 25, 16 or 32 bins; one warp per block, tile_z = run length);
+ * warps per block; tile rows in y and z. */
 int ks_dense_config(ks_ctx *ctx, int bins, int r_max, int *path, int *warps,
                     int *tile_y, int *tile_z);
 
 /* Force the dense launch configuration for every context of the process
  * (tests use it to cover both paths); path < 0 returns to the autotuner.
- * KS_EINVAL: path > 4, warps outside [1, 16] ([1, 8] for paths 2 to 4) or
- * tile_y * tile_z != warps.
+ * KS_EINVAL: path > 5, warps outside [1, 16] ([1, 8] for paths 2 to 4) or
+ * tile_y * tile_z != warps (path 5: warps = tile_y = 1, tile_z in [1, 1024]).
  * A forced shape that does not fit a given (bins, r_max) is ignored for
  * that call. */
 int ks_force_dense_config(int path, int warps, int tile_y, int tile_z);

@@ -509,6 +509,10 @@ static std::vector<DenseConfig> dense_candidates(int B, int r_max) {
             DenseConfig c{path, s[0], s[1], s[2]};
             if (dense_config_fits(c, B, r_max)) out.push_back(c);
         }
+    // sliding windows: one warp per block, runs of 16 planes (the fastest
+    // run length on the PET-shaped workload; 32 and 64 were slower)
+    const DenseConfig slide{5, 1, 1, 16};
+    if (dense_config_fits(slide, B, r_max)) out.push_back(slide);
     return out;
 }
 
@@ -1630,7 +1634,7 @@ int ks_kernel_time(ks_ctx *ctx, const char *prefix, double *ms_total, int64_t *l
     return KS_OK;
 }
 
-int ks_measure_smem_peak(ks_ctx *ctx, double *per_s) {
+static int measure_smem(ks_ctx *ctx, double *per_s, bool red_only) {
     if (!ctx || !per_s) return KS_EINVAL;
     Ctx *c = &ctx->impl;
     cudaError_t e;
@@ -1644,7 +1648,7 @@ int ks_measure_smem_peak(ks_ctx *ctx, double *per_s) {
     for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(a, c->stream);
         c->launches++;
-        e = launch_smem_peak(c->lc(), sink, blocks, iters);
+        e = launch_smem_peak(c->lc(), sink, blocks, iters, red_only);
         cudaEventRecord(b, c->stream);
         if (e != cudaSuccess) break;
         cudaEventSynchronize(b);
@@ -1658,6 +1662,10 @@ int ks_measure_smem_peak(ks_ctx *ctx, double *per_s) {
     *per_s = (double)blocks * 256.0 * iters * 16.0 / (best * 1e-3);
     return KS_OK;
 }
+
+int ks_measure_smem_peak(ks_ctx *ctx, double *per_s) { return measure_smem(ctx, per_s, false); }
+
+int ks_measure_smem_red_rate(ks_ctx *ctx, double *per_s) { return measure_smem(ctx, per_s, true); }
 
 int ks_measure_fp64_rate(ks_ctx *ctx, double *per_s) {
     if (!ctx || !per_s) return KS_EINVAL;
@@ -1724,8 +1732,11 @@ int ks_force_dense_config(int path, int warps, int ty, int tz) {
         g_forced_path = -1;
         return KS_OK;
     }
-    if (path > 4 || warps < 1 || warps > (path >= 2 ? 8 : 16) || ty * tz != warps)
+    if (path == 5) {
+        if (warps != 1 || ty != 1 || tz < 1 || tz > 1024) return KS_EINVAL;
+    } else if (path > 5 || warps < 1 || warps > (path >= 2 ? 8 : 16) || ty * tz != warps) {
         return KS_EINVAL;
+    }
     g_forced_path = path;
     g_forced_warps = warps;
     g_forced_ty = ty;

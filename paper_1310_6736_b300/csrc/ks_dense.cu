@@ -622,6 +622,140 @@ __global__ void __launch_bounds__(256, TM ? 2 : 1) k_dense4(const DenseArgs a) {
     }
 }
 
+// Launch path 5 (sliding windows, r_max <= 25, 16 or 32 bins): a warp
+// takes 32 consecutive x-centres of one y and slides them along z over a
+// run of tz planes, keeping one histogram per scale (not a running one, as
+// the other paths do).  Moving a centre from z to z + 1 changes Ball(r) by
+// one voxel at each end of every z-row (dx, dy) of the ball: the voxel at
+// z + 1 + w(dx, dy) enters, the one at z - w leaves.  That is 2 rows(r)
+// updates per scale, sum over r of 2 rows(r) ~ 2 pi sum r^2 per centre
+// (17 945 for r = 4..20 against 33 401 for the shell-incremental paths).
+// The histograms of scales 2p and 2p + 1 share a word (16-bit halves:
+// |Ball(25)| < 2^16); a removal adds -inc, which borrows nothing because
+// the count it lowers is at least 1.  The first centre of a run builds its
+// histograms shell by shell in a scratch column and copies each scale's
+// counts out.  Each centre's scales are evaluated with the same FP64 steps,
+// in the same order, as scale_step, so Y and s_best are identical.
+template <int B>
+__global__ void __launch_bounds__(32) k_dense_slide(const DenseArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    constexpr int NW = B + 1;
+    const int lane = threadIdx.x & 31;
+    const int S = a.S, npair = (S + 1) / 2;
+    const uint32_t col = smem_u32(smem) + lane * 4;               // word w at col + 128 w
+    const uint32_t scr = col + ((uint32_t)(npair * NW) << 7);     // scratch column
+    const int xg = blockIdx.x * 32 + lane;
+    const bool live = xg < a.vol.nx;
+    const int x = live ? xg : a.vol.nx - 1;     // idle lanes repeat the last column
+    const int y = blockIdx.y;
+    const int zs = a.z0 + blockIdx.z * a.tz;
+    const int ze = min(zs + a.tz, a.z1);
+    if (zs >= ze) return;
+    const int pz = (int)a.vol.plane, py = (int)a.vol.pitch;
+    const uint8_t *c0 = a.vol.base + (int64_t)zs * a.vol.plane + (int64_t)y * a.vol.pitch + x;
+    const Tab<true> tab{a.ot};
+    for (int w = 0; w < (npair + 1) * NW; ++w) st_shared_u32(col + ((uint32_t)w << 7), 0u);
+    // the first centre: shells into the scratch column, each scale copied out
+    for (int rho = 0; rho <= a.r_max; ++rho) {
+        for (int k = tab.c8_start(rho); k < tab.c8_start(rho + 1); ++k) {
+            const uint32_t e = tab.c8(k);
+            const int X = (int)(e & 0xffu);
+            const int Y = (int)((e >> 8) & 0xffu) * py;
+            const int Z = (int)((e >> 16) & 0xffu) * pz;
+            const int o[8] = {Z + Y + X, Z + Y - X, Z - Y + X, Z - Y - X,
+                              Y - Z + X, Y - Z - X, -Z - Y + X, -Z - Y - X};
+            uint32_t v[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[m] = __ldg(c0 + o[m]);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) red_add_shared(scr + (v[m] << 7), 1u);
+        }
+        for (int k = tab.rest_start(rho); k < tab.rest_start(rho + 1); ++k) {
+            const uint32_t f = tab.rest(k);
+            const int off = ((int)((f >> 16) & 0xffu) - 64) * pz + ((int)((f >> 8) & 0xffu) - 64) * py +
+                            ((int)(f & 0xffu) - 64);
+            red_add_shared(scr + ((uint32_t)__ldg(c0 + off) << 7), 1u);
+        }
+        const int i = rho - a.r_min;
+        if (i >= 0) {
+            const uint32_t pw = col + ((uint32_t)((i >> 1) * NW) << 7);
+            for (int v = 0; v < NW; ++v) {
+                const uint32_t cv = ld_shared_u32(scr + ((uint32_t)v << 7));
+                const uint32_t adr = pw + ((uint32_t)v << 7);
+                st_shared_u32(adr, (i & 1) ? (ld_shared_u32(adr) | (cv << 16)) : cv);
+            }
+        }
+    }
+    for (int z = zs;;) {
+        // the centre (x, y, z): every scale from its own histogram
+        ScaleState st{0.0, 0.0, 0.0, 0u, 0u, 0ull, 0};
+        const int64_t oidx = ((int64_t)z * a.vol.ny + y) * a.vol.nx + x;
+        for (int i = 0; i < S; ++i) {
+            const int r = a.r_min + i;
+            const uint32_t pw = col + ((uint32_t)((i >> 1) * NW) << 7);
+            const uint32_t qw = col + ((uint32_t)(((i - 1) >> 1) * NW) << 7);   // scale i - 1
+            const int sh = 16 * (i & 1), qs = 16 * ((i - 1) & 1);
+            auto count = [&](int v) { return (ld_shared_u32(pw + ((uint32_t)v << 7)) >> sh) & 0xffffu; };
+            const uint32_t N = (uint32_t)__ldg(a.ot.ball_size + r) - count(0);
+            double ssum = 0.0;
+            int occ = 0;
+            uint64_t D = 0;
+#pragma unroll 4
+            for (int v = 1; v <= B; ++v) {
+                const uint32_t c = count(v);
+                const uint32_t p =
+                    i == 0 ? 0u : (ld_shared_u32(qw + ((uint32_t)v << 7)) >> qs) & 0xffffu;
+                occ += c > 0u;
+                if (c > 1u) ssum = __dadd_rn(ssum, __ldg(a.T + c));
+                const int64_t d = (int64_t)c * st.nm1 - (int64_t)p * N;
+                D += (uint64_t)(d < 0 ? -d : d);
+            }
+            const double H = entropy_from_sum(ssum, N, occ, a.L);
+            if (i >= 2 && st.hm2 < st.hm1 && st.hm1 >= H) {   // peak at scale i-1
+                const double W = kb_weight(st.dm1, st.nm1, st.nm2, r - 1, a.w_norm);
+                const double yv = __dmul_rn(st.hm1, W);
+                if (st.sb == 0 || yv > st.yb) {
+                    st.yb = yv;
+                    st.sb = r - 1;
+                }
+            }
+            if (live && (a.out.H || a.out.W)) {
+                if (a.out.H) a.out.H[oidx * a.S + i] = H;
+                if (a.out.W)
+                    a.out.W[oidx * a.S + i] = i == 0 ? 0.0 : kb_weight(D, N, st.nm1, r, a.w_norm);
+            }
+            st.hm2 = st.hm1;
+            st.hm1 = H;
+            st.nm2 = st.nm1;
+            st.nm1 = N;
+            st.dm1 = D;
+        }
+        if (live) {
+            a.out.Y[oidx] = st.yb;
+            a.out.s[oidx] = (uint8_t)st.sb;
+        }
+        if (++z >= ze) break;
+        // slide every scale's ball from z - 1 to z
+        for (int i = 0; i < S; ++i) {
+            const int r = a.r_min + i;
+            const uint32_t pw = col + ((uint32_t)((i >> 1) * NW) << 7);
+            const uint32_t inc = 1u << (16 * (i & 1)), dec = 0u - inc;
+            const int k1 = __ldg(a.ot.rows_start + r + 1);
+#pragma unroll 4
+            for (int k = __ldg(a.ot.rows_start + r); k < k1; ++k) {
+                const uint32_t e = __ldg(a.ot.rows + k);
+                const int base = ((int)(e & 0xffu) - 64) + ((int)((e >> 8) & 0xffu) - 64) * py;
+                const int w = (int)(e >> 16);
+                const uint32_t ve = __ldg(c0 + base + (w + 1) * pz);
+                const uint32_t vl = __ldg(c0 + base - w * pz);
+                red_add_shared(pw + (ve << 7), inc);
+                red_add_shared(pw + (vl << 7), dec);
+            }
+        }
+        c0 += pz;
+    }
+}
+
 // Kadir-Brady at listed centres: one warp per centre.  The lanes split the
 // offset entries of each shell and count into lane-private columns (word v
 // of lane l at +128 v + 4 l); after the shells of a scale, lane b gathers
@@ -752,6 +886,12 @@ int template_bins(int B) {
 
 bool is_wide(int r_max) { return r_max > kConstRmax; }
 
+// shared memory of a launch path 5 block: one word per bin and pair of
+// scales, plus the scratch column, for each of the 32 lanes
+size_t slide_smem_bytes(int B, int S) {
+    return (size_t)((S + 1) / 2 + 1) * (template_bins(B) + 1) * 128;
+}
+
 struct Geometry {
     int padx, bx, by, bz;
     size_t brick, cnt_off, cnt_bytes, mbar_off, total;
@@ -825,6 +965,19 @@ template <int B>
 cudaError_t launch_b(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap *tmap,
                      const DenseConfig &cfg, size_t smem) {
     const bool wide = is_wide(a.r_max);
+    if (cfg.path == 5) {
+        if constexpr (B == 16 || B == 32) {
+            if (wide) return cudaErrorInvalidValue;
+            const size_t sm = slide_smem_bytes(B, a.S);
+            cudaError_t e = cudaFuncSetAttribute(k_dense_slide<B>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            dim3 grid((a.vol.nx + 31) / 32, a.vol.ny, (a.z1 - a.z0 + a.tz - 1) / a.tz);
+            k_dense_slide<B><<<grid, 32, sm, lc.stream>>>(a);
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidValue;
+    }
     if (cfg.path == 3) return wide ? cudaErrorInvalidValue : launch_adj4<B, false>(lc, a, cfg, smem);
     if (cfg.path == 4) {
         if constexpr (B == 16 || B == 32)
@@ -968,6 +1121,10 @@ size_t dense_smem_bytes(const DenseConfig &c, int B, int r_max) {
 }
 
 bool dense_config_fits(const DenseConfig &c, int B, int r_max) {
+    if (c.path == 5)
+        return !is_wide(r_max) && (template_bins(B) == 16 || template_bins(B) == 32) &&
+               c.warps == 1 && c.ty == 1 && c.tz >= 1 && c.tz <= 1024 &&
+               slide_smem_bytes(B, r_max + 1) + 1024 <= 227 * 1024;
     if (c.path < 0 || c.path > 4) return false;
     if (c.path >= 3 && is_wide(r_max)) return false;      // counts need 16-bit packing
     if (c.path == 4 && template_bins(B) != 16 && template_bins(B) != 32) return false;

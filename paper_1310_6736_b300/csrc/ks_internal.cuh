@@ -313,7 +313,8 @@ cudaError_t launch_select(const LaunchCtx &lc, const ks_candidate *in, int64_t n
                           unsigned long long *d_count, int64_t *n_out);
 
 // Micro-kernel: shared-memory increment rate (see ks_measure_smem_peak).
-cudaError_t launch_smem_peak(const LaunchCtx &lc, uint32_t *sink, int blocks, int iters);
+cudaError_t launch_smem_peak(const LaunchCtx &lc, uint32_t *sink, int blocks, int iters,
+                             bool red_only);
 cudaError_t launch_fp64_peak(const LaunchCtx &lc, double *sink, int blocks, int iters);
 
 }  // namespace ks

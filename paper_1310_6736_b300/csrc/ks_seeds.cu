@@ -1016,8 +1016,33 @@ __global__ void __launch_bounds__(256) k_smem_peak(uint32_t *sink, int iters) {
     if (acc == 0xdeadbeefu) sink[blockIdx.x] = acc;   // keeps the work observable
 }
 
-cudaError_t launch_smem_peak(const LaunchCtx &lc, uint32_t *sink, int blocks, int iters) {
-    k_smem_peak<<<blocks, 256, 0, lc.stream>>>(sink, iters);
+// Shared-memory reduction rate alone: the same lane-private columns, but
+// every update is a red.shared.add at an address known at compile time
+// (the lane's column plus a constant word), so the kernel issues nothing
+// else -- no byte loads, no address arithmetic.  The ceiling of any
+// histogram kernel that makes one reduction per update.
+__global__ void __launch_bounds__(256) k_smem_red_peak(uint32_t *sink, int iters) {
+    __shared__ uint32_t cnt[8][33 * 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = lane; i < 33 * 32; i += 32) cnt[warp][i] = 0;
+    __syncwarp();
+    const uint32_t col = smem_u32(&cnt[warp][lane]);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) red_add_shared(col + (uint32_t)(((u * 5 + 3) % 33) << 7), 1u);
+    }
+    __syncwarp();
+    uint32_t acc = 0;
+    for (int w = 0; w < 33; ++w) acc += ld_shared_u32(col + (w << 7));
+    if (acc == 0xdeadbeefu) sink[blockIdx.x] = acc;   // keeps the work observable
+}
+
+cudaError_t launch_smem_peak(const LaunchCtx &lc, uint32_t *sink, int blocks, int iters,
+                             bool red_only) {
+    if (red_only)
+        k_smem_red_peak<<<blocks, 256, 0, lc.stream>>>(sink, iters);
+    else
+        k_smem_peak<<<blocks, 256, 0, lc.stream>>>(sink, iters);
     return cudaGetLastError();
 }
 

@@ -110,6 +110,7 @@ SIGNATURES = {
     "ks_set_profiling": (_I, [_P, _I]),
     "ks_kernel_time": (_I, [_P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "ks_measure_smem_peak": (_I, [_P, C.POINTER(C.c_double)]),
+    "ks_measure_smem_red_rate": (_I, [_P, C.POINTER(C.c_double)]),
     "ks_measure_fp64_rate": (_I, [_P, C.POINTER(C.c_double)]),
     "ks_dense_config": (_I, [_P, _I, _I, C.POINTER(C.c_int), C.POINTER(C.c_int),
                              C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -549,6 +550,12 @@ class Context:
     def measure_smem_peak(self):
         r = C.c_double()
         self._check(lib().ks_measure_smem_peak(self.h, C.byref(r)), "ks_measure_smem_peak")
+        return r.value
+
+    def measure_smem_red_rate(self):
+        """Shared-memory reductions per second with nothing else issued."""
+        r = C.c_double()
+        self._check(lib().ks_measure_smem_red_rate(self.h, C.byref(r)), "ks_measure_smem_red_rate")
         return r.value
 
     def measure_fp64_rate(self):

@@ -124,7 +124,8 @@ def _dense_vs_oracle(ctx, ko, ks, bins_vol_raw, binning, r_min, r_max, w_norm=0,
 @pytest.mark.parametrize("cfg", [None, (0, 16, 4, 4), (0, 8, 2, 4), (0, 4, 4, 1), (1, 16, 4, 4),
                                  (1, 8, 8, 1), (2, 8, 4, 2), (2, 4, 1, 4), (3, 4, 2, 2),
                                  (3, 1, 1, 1), (3, 8, 2, 4), (4, 4, 2, 2), (4, 1, 1, 1),
-                                 (4, 8, 2, 4), (4, 2, 1, 2)])
+                                 (4, 8, 2, 4), (4, 2, 1, 2), (5, 1, 1, 16), (5, 1, 1, 48),
+                                 (5, 1, 1, 7)])
 def test_dense_spheres48_full_volume(ctx, ko, ks_mod, cfg):
     ks = ks_mod
     try:
@@ -144,7 +145,7 @@ def test_dense_spheres48_full_volume(ctx, ko, ks_mod, cfg):
     ((70, 3, 2), 16, 2, 12, 0),      # thin slab, radius larger than the volume
     ((75, 6, 4), 8, 24, 28, 0),      # r_max > 25: global offset table, 32-bit previous counts
 ])
-@pytest.mark.parametrize("path", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("path", [0, 1, 2, 3, 4, 5])
 def test_dense_random_volumes(ctx, ko, ks_mod, case, path):
     ks = ks_mod
     dims, B, r_min, r_max, wn = case
@@ -157,7 +158,7 @@ def test_dense_random_volumes(ctx, ko, ks_mod, case, path):
     shift = max(0, int(np.ceil(np.log2(2048 / B))))
     binning = {"kind": 2, "bins": B, "shift": shift, "lo": 30, "hi": min(2047, (B << shift) - 1)}
     try:
-        ks.force_dense_config(path, 8, 4, 2)
+        ks.force_dense_config(*((5, 1, 1, 8) if path == 5 else (path, 8, 4, 2)))
         _dense_vs_oracle(ctx, ko, ks, vol, binning, r_min, r_max, wn)
     finally:
         ks.force_dense_config(-1)
@@ -258,14 +259,21 @@ def test_saliency_reports_a_small_capacity(ctx, ks_mod):
         ctx.release_volume(v)
 
 
-def test_dense_pet128_full_size_sampled(ctx, ko, ks_mod):
+@pytest.mark.parametrize("cfg", [None, (5, 1, 1, 64)])
+def test_dense_pet128_full_size_sampled(ctx, ko, ks_mod, cfg):
     """The bench workload (128x128x64 float32, 32 bins, r=4..20) at full size,
-    in the autotuned launch configuration; checked on sampled centres."""
+    in the autotuned launch configuration and in the sliding-window path;
+    checked on sampled centres."""
     ks = ks_mod
     w = synth.workload("pet128")
     v = ctx.create_volume(w.volume, w.binning)
     p = _params(ks, w)
-    Y, s = ctx.dense_saliency(v, p, w.volume.shape)
+    try:
+        if cfg is not None:
+            ks.force_dense_config(*cfg)
+        Y, s = ctx.dense_saliency(v, p, w.volume.shape)
+    finally:
+        ks.force_dense_config(-1)
     ctx.release_volume(v)
     b = ko.bin_volume(w.volume, w.binning)
     rng = np.random.default_rng(0)
