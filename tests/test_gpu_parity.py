@@ -259,11 +259,13 @@ def test_saliency_reports_a_small_capacity(ctx, ks_mod):
         ctx.release_volume(v)
 
 
-@pytest.mark.parametrize("cfg", [None, (5, 1, 1, 64)])
+@pytest.mark.parametrize("cfg", [None, (5, 1, 1, 64), (1, 8, 8, 1), (3, 4, 2, 2)])
 def test_dense_pet128_full_size_sampled(ctx, ko, ks_mod, cfg):
     """The bench workload (128x128x64 float32, 32 bins, r=4..20) at full size,
-    in the autotuned launch configuration and in the sliding-window path;
-    checked on sampled centres."""
+    in the autotuned launch configuration, the sliding-window path, the
+    one-centre-per-lane path and the shared-memory four-centre path;
+    checked on three whole z-planes (first, middle, last: 49 152 centres)
+    and 3000 random centres."""
     ks = ks_mod
     w = synth.workload("pet128")
     v = ctx.create_volume(w.volume, w.binning)
@@ -280,9 +282,9 @@ def test_dense_pet128_full_size_sampled(ctx, ko, ks_mod, cfg):
     nz, ny, nx = w.volume.shape
     cen = np.stack([rng.integers(0, nx, 3000), rng.integers(0, ny, 3000),
                     rng.integers(0, nz, 3000)], axis=1)
-    edges = np.array([[0, 0, 0], [nx - 1, ny - 1, nz - 1], [nx - 1, 0, nz // 2],
-                      [0, ny - 1, 0], [nx // 2, ny // 2, nz - 1]])
-    cen = np.concatenate([cen, edges]).astype(np.int32)
+    yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    planes = [np.stack([xx.ravel(), yy.ravel(), np.full(xx.size, z)], 1) for z in (0, nz // 2, nz - 1)]
+    cen = np.concatenate([cen] + planes).astype(np.int32)
     Yo, so = ko.dense(b, 32, w.r_min, w.r_max, centres=cen)
     got_Y = Y[cen[:, 2], cen[:, 1], cen[:, 0]]
     got_s = s[cen[:, 2], cen[:, 1], cen[:, 0]]
@@ -354,15 +356,20 @@ def test_meanshift_pet128_all_items(ctx, ko, ks_mod):
     _ms_vs_oracle(ctx, ko, ks_mod, synth.workload("pet128"))
 
 
-def test_seeds_mr256_sampled(ctx, ko, ks_mod):
+def test_seeds_mr256_full_grid_and_edges(ctx, ko, ks_mod):
+    """The MR-shaped workload at full size (256x256x160 int16, 64 bins,
+    r = 4..32): the octant climb on all 5733 grid seeds (trajectories
+    included) plus volume corners and faces; mean shift on 1024 grid seeds
+    at all 29 radii (29 696 items, every one of them on the block path:
+    more than 32 bins) plus the corners."""
     w = synth.workload("mr256")
     grid = ko.seed_grid(w.dims, w.stride)
-    rng = np.random.default_rng(3)
-    pick = grid[rng.choice(len(grid), 48, replace=False)]
-    edge = np.array([[0, 0, 0], [255, 255, 159], [128, 0, 80]], np.int32)
-    seeds = np.concatenate([pick, edge]).astype(np.int32)
+    edge = np.array([[0, 0, 0], [255, 255, 159], [128, 0, 80], [255, 130, 0]], np.int32)
+    seeds = np.concatenate([grid, edge]).astype(np.int32)
     _oct_vs_oracle(ctx, ko, ks_mod, w, seeds=seeds, traj=True)
-    _ms_vs_oracle(ctx, ko, ks_mod, w, seeds=seeds[:20])
+    rng = np.random.default_rng(3)
+    pick = grid[np.sort(rng.choice(len(grid), 1024, replace=False))]
+    _ms_vs_oracle(ctx, ko, ks_mod, w, seeds=np.concatenate([pick, edge]).astype(np.int32))
 
 
 def test_meanshift_radii_across_warp_and_block_paths(ctx, ko, ks_mod):
