@@ -37,11 +37,14 @@
 namespace ks {
 namespace {
 
+constexpr int kCycleMax = 8;     // longest cycle of centres the octant climb detects
+
 struct SeedShared {
     int step[3];
     int64_t ticket;
     uint32_t N[kMaxScales];
     unsigned long long D[kMaxScales];
+    int hist[kCycleMax][3];         // octant climb: centre t at t % kCycleMax
 };
 
 __device__ __forceinline__ const uint8_t *voxel_ptr(const VolDesc &v, const int P[3]) {
@@ -344,6 +347,16 @@ __device__ void kb_from_pass(const SeedJob &J, const double *T, const double *L,
     __syncthreads();
 }
 
+// One seed's climb.  The next centre is a function of the centre alone
+// (the pass, the entropies and the step read nothing else), so when the
+// centre after iteration t equals the centre after t - p (p >= 2; p = 1 is
+// convergence) the search repeats those p centres for good: it never
+// converges, and the centre after iteration t' >= t - p is the one after
+// t - p + (t' - t + p) mod p.  The search then jumps to iteration max_iter
+// and only the final pass at that centre remains: the records (centre,
+// iterations, convergence flag, trajectory and the Kadir-Brady values) are
+// those of running every iteration.  The last kCycleMax centres are kept
+// in shared memory, so cycles up to that length are found.
 __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &ot,
                             const double *T, const double *L, uint32_t *cnt, double *hb,
                             SeedShared &sh) {
@@ -366,6 +379,10 @@ __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &
     }
     if (threadIdx.x == 0 && J.traj && it == 0)
         for (int a = 0; a < 3; ++a) J.traj[(sidx * T1) * 3 + a] = P[a];
+    // centres before a resumed search's first iteration are not known
+    const int hist_lo = it;
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 3; ++a) sh.hist[it % kCycleMax][a] = P[a];
     const int it_end = J.iter_budget > 0 ? min(J.max_iter, it + J.iter_budget) : J.max_iter;
     while (it < it_end) {
         octant_pass(J, ot, cnt, P);
@@ -378,15 +395,40 @@ __device__ void octant_item(const SeedJob &J, int64_t sidx, const OffsetTables &
         ++it;
         int Pn[3];
         for (int a = 0; a < 3; ++a) Pn[a] = clampi(P[a] + sh.step[a], 0, dims[a] - 1);
-        __syncthreads();
-        if (Pn[0] == P[0] && Pn[1] == P[1] && Pn[2] == P[2]) {
+        const bool same = Pn[0] == P[0] && Pn[1] == P[1] && Pn[2] == P[2];
+        int per = 0;                          // the centre after it - per equals Pn
+        for (int p = 2; !same && p <= kCycleMax && it - p >= hist_lo; ++p) {
+            const int *h = sh.hist[(it - p) % kCycleMax];
+            if (h[0] == Pn[0] && h[1] == Pn[1] && h[2] == Pn[2]) {
+                per = p;
+                break;
+            }
+        }
+        __syncthreads();                      // sh.step and sh.hist read by every thread
+        if (same) {
             conv = 1;
+            break;
+        }
+        if (per) {
+            // centre after iteration t >= it: the one after it - per + (t - it) % per
+            if (threadIdx.x == 0 && J.traj)
+                for (int t = it; t <= J.max_iter; ++t)
+                    for (int a = 0; a < 3; ++a)
+                        J.traj[(sidx * T1 + t) * 3 + a] =
+                            sh.hist[(it - per + (t - it) % per) % kCycleMax][a];
+            const int *hf = sh.hist[(it - per + (J.max_iter - it) % per) % kCycleMax];
+            fresh = hf[0] == P[0] && hf[1] == P[1] && hf[2] == P[2];   // the last pass ran at P
+            for (int a = 0; a < 3; ++a) P[a] = hf[a];
+            it = J.max_iter;
             break;
         }
         for (int a = 0; a < 3; ++a) P[a] = Pn[a];
         fresh = 0;
-        if (threadIdx.x == 0 && J.traj)
-            for (int a = 0; a < 3; ++a) J.traj[(sidx * T1 + it) * 3 + a] = P[a];
+        if (threadIdx.x == 0) {
+            for (int a = 0; a < 3; ++a) sh.hist[it % kCycleMax][a] = P[a];
+            if (J.traj)
+                for (int a = 0; a < 3; ++a) J.traj[(sidx * T1 + it) * 3 + a] = P[a];
+        }
     }
     if (stp && !conv && it < J.max_iter) {   // the budget ran out: keep the state
         __syncthreads();

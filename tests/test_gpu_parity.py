@@ -352,6 +352,44 @@ def test_octant_pet128_all_seeds(ctx, ko, ks_mod):
     _oct_vs_oracle(ctx, ko, ks_mod, synth.workload("pet128"), traj=True)
 
 
+@pytest.mark.parametrize("max_iter", [5, 9, 14])
+def test_octant_cycles_jump_to_max_iter(ctx, ko, ks_mod, max_iter):
+    """Searches whose centres repeat with a period of 2..8 are finished by
+    a jump to max_iter.  Several max_iter values put the final centre at
+    different phases of each cycle, so both the reuse of the last pass and a
+    final pass at another centre of the cycle are taken; records and
+    trajectories equal the oracle's, which runs every iteration."""
+    w = synth.workload("pet128")
+    b = ko.bin_volume(w.volume, w.binning)
+    sd = ko.seed_grid(w.dims, w.stride)
+    ref = ko.octant_climb(b, w.binning["bins"], w.r_min, w.r_max, sd, max_iter, want_traj=True)
+    # per cycling search: does the final centre equal the last pass's centre?
+    reuse = extra = 0
+    for i in np.nonzero(ref["converged"] == 0)[0]:
+        tr = ref["traj"][i]
+        hit = [(t, p) for t in range(2, max_iter + 1) for p in range(2, min(t, 8) + 1)
+               if (tr[t] == tr[t - p]).all()]
+        if hit:
+            t, p = hit[0]
+            if (tr[t - p + (max_iter - t) % p] == tr[t - 1]).all():
+                reuse += 1
+            else:
+                extra += 1
+    assert reuse >= 10 and extra >= 10
+    v = ctx.create_volume(w.volume, w.binning)
+    p = ks_mod.make_params(w.r_min, w.r_max, w.stride, max_iter)
+    got, traj = ctx.seed_climb(v, p, want_traj=True)
+    assert np.array_equal(np.stack([got["x"], got["y"], got["z"]], 1), ref["xyz"])
+    assert np.array_equal(got["iters"], ref["iters"])
+    assert np.array_equal(got["converged"], ref["converged"])
+    assert np.array_equal(traj, ref["traj"])
+    assert np.array_equal(got["s_best"], ref["s"])
+    close(got["Y_best"], ref["Y"])
+    close(got["H_best"], ref["H"])
+    close(got["W_best"], ref["W"])
+    ctx.release_volume(v)
+
+
 def test_meanshift_pet128_all_items(ctx, ko, ks_mod):
     _ms_vs_oracle(ctx, ko, ks_mod, synth.workload("pet128"))
 
