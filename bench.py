@@ -7,7 +7,8 @@ dense sweep at every voxel, octant hill-climbing from every grid seed and
 mean shift for every (seed, radius) item.  The metric is window-entropies
 per second: one window-entropy is one (centre, window) histogram whose
 entropy is evaluated (dense: voxels x scales; octant: 8 x scales per
-iteration plus the final scales; mean shift: one per iteration).
+iteration run plus the final scales, where a search whose centres repeat
+stops running iterations; mean shift: one per iteration).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ks|reference]
 
@@ -101,10 +102,36 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def window_entropies(n_vox, S, oct_res, ms_res):
+def octant_run(res, traj):
+    """Iterations and window passes the octant kernel runs per seed.  A
+    converged search runs its iterations (the last pass serves the final
+    evaluation).  A search whose centre after iteration t repeats the one
+    after t - p (2 <= p <= 8) stops after t iterations and needs a final
+    pass unless its centre at max_iter is the last pass's centre.  Any
+    other search runs max_iter iterations and a final pass."""
+    it = res["iters"].astype(np.int64)
+    conv = res["converged"] != 0
+    M = traj.shape[1] - 1
+    stop = np.full(len(it), M, np.int64)
+    final_at = np.zeros(len(it), bool)        # the final centre is the last pass's
+    open_ = ~conv
+    for t in range(2, M + 1):
+        hit = np.zeros(len(it), bool)
+        for p in range(2, min(t, 8) + 1):
+            hit |= (traj[:, t] == traj[:, t - p]).all(1)
+        new = open_ & hit
+        stop[new] = t
+        final_at[new] = (traj[new, M] == traj[new, t - 1]).all(1)
+        open_ &= ~hit
+    run_it = np.where(conv, it, stop)
+    passes = np.where(conv, it, stop + (~final_at).astype(np.int64))
+    return run_it, passes
+
+
+def window_entropies(n_vox, S, oct_res, ms_res, oct_run_iters):
     """Histograms whose entropy the step evaluated (see module docstring)."""
     dense = n_vox * S
-    octant = int(oct_res["iters"].sum()) * 8 * S + len(oct_res) * S
+    octant = int(oct_run_iters.sum()) * 8 * S + len(oct_res) * S
     ms = int(ms_res["iters"].sum()) + int((ms_res["converged"] == 0).sum())
     return dense + octant + ms, {"dense": dense, "octant": octant, "meanshift": ms}
 
@@ -239,13 +266,18 @@ def run_ks(args):
 
     flush.zero_()
     o, m = step(host=True)                 # host records: the window-entropy count
+    v = ctx.create_volume(raw_dev, w.binning)
+    o_t, traj = ctx.seed_climb(v, params, want_traj=True)
+    ctx.release_volume(v)
+    assert np.array_equal(o_t, o)
+    oct_iters_run, _ = octant_run(o, traj)
     dev_out["oct"] = torch.empty(len(o) * ks.SEED_RESULT.itemsize, dtype=torch.uint8, device="cuda")
     dev_out["ms"] = torch.empty(len(m) * ks.MS_RESULT.itemsize, dtype=torch.uint8, device="cuda")
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
         step()
     torch.cuda.synchronize()
-    n_we, parts = window_entropies(n_vox, S, o, m)
+    n_we, parts = window_entropies(n_vox, S, o, m, oct_iters_run)
 
     # ---- timed region: device time per step with CUDA events on the stream
     ctx.set_profiling(True)
@@ -597,15 +629,16 @@ def seed_rooflines(ctx, ks, w, params, smem_peak, flush, reps=5):
     shift = |Ball(r)| window voxels per pass of each (seed, r) item."""
     import torch
     v = ctx.create_volume(w.volume, w.binning)
-    o = ctx.seed_climb(v, params)
+    o, traj = ctx.seed_climb(v, params, want_traj=True)
     m = ctx.meanshift(v, params)
     od = torch.empty(len(o) * ks.SEED_RESULT.itemsize, dtype=torch.uint8, device="cuda")
     md = torch.empty(len(m) * ks.MS_RESULT.itemsize, dtype=torch.uint8, device="cuda")
     out = {}
-    oct_upd = int(_passes(o).sum()) * _closed_octant_updates(w.r_max)
+    o_it, o_passes = octant_run(o, traj)
+    oct_upd = int(o_passes.sum()) * _closed_octant_updates(w.r_max)
     ms_upd = int((_passes(m) * np.array([ks_ball_size(int(r)) for r in m["r"]])).sum())
     S = w.r_max - w.r_min + 1
-    oct_we = int(o["iters"].sum()) * 8 * S + len(o) * S
+    oct_we = int(o_it.sum()) * 8 * S + len(o) * S
     ms_we = int(m["iters"].sum()) + int((m["converged"] == 0).sum())
     for name, fn, upd, we, prefix in (
             ("octant", lambda: ctx.seed_climb(v, params, out=od), oct_upd, oct_we, "ks_seeds"),
@@ -626,7 +659,9 @@ def seed_rooflines(ctx, ks, w, params, smem_peak, flush, reps=5):
                      "window_entropies_per_s": we / t, "launches": n}
     ctx.release_volume(v)
     out["unit"] = ("shared-memory histogram updates (octant: one per voxel and closed octant of "
-                   "each pass; mean shift: one per window voxel of each pass)")
+                   "each pass the kernel runs; mean shift: one per window voxel of each pass)")
+    out["octant"]["passes_run"] = int(o_passes.sum())
+    out["octant"]["passes_of_every_iteration"] = int(_passes(o).sum())
     return out
 
 
@@ -639,7 +674,7 @@ def run_mr256_seeds(ctx, ks, synth, reps=3):
     w = synth.workload("mr256")
     params = ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter)
     v = ctx.create_volume(w.volume, w.binning)
-    o = ctx.seed_climb(v, params)
+    o, traj = ctx.seed_climb(v, params, want_traj=True)
     m = ctx.meanshift(v, params)
     od = torch.empty(len(o) * ks.SEED_RESULT.itemsize, dtype=torch.uint8, device="cuda")
     md = torch.empty(len(m) * ks.MS_RESULT.itemsize, dtype=torch.uint8, device="cuda")
@@ -658,7 +693,7 @@ def run_mr256_seeds(ctx, ks, synth, reps=3):
             np.array_equal(md.cpu().numpy().view(ks.MS_RESULT), m))
     ctx.release_volume(v)
     S = w.r_max - w.r_min + 1
-    oct_we = int(o["iters"].sum()) * 8 * S + len(o) * S
+    oct_we = int(octant_run(o, traj)[0].sum()) * 8 * S + len(o) * S
     ms_we = int(m["iters"].sum()) + int((m["converged"] == 0).sum())
     t_o, t_m = min(times["octant"]), min(times["meanshift"])
     return {"workload": "mr256: 256x256x160 int16 MR-shaped, 64 bins, r = 4..32, stride 12",
