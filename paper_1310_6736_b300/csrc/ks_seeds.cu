@@ -507,66 +507,139 @@ __device__ __forceinline__ unsigned long long ms_row_word(uint32_t e, int *dy, i
 }
 
 // Block path: counts c_b and integer offset sums m_b of Ball(r) at P into
-// acc[b][4].
+// acc[b][4].  Column words are indexed by the stored value v (0..B): value
+// 0 (not counted) has its own columns, never read, so a byte costs no
+// branch, and bytes of a row's first and last words outside the row are
+// masked to 0.  Each thread takes whole rows (the rows table lists rows of
+// like length together, so the lanes of a warp walk similar lengths) and
+// streams a row as aligned 8-byte words, the next row's words loaded while
+// the current row is counted.
+constexpr int kBlkRowWords = 9;   // a row of Ball(r <= 32): <= 65 bins + 7 bytes of alignment
+
+// The row walk of the block path (W32: two 32-bit words per voxel, else one
+// 64-bit word); see ms_pass.
+template <bool W32>
+__device__ __forceinline__ void ms_walk_rows(const OffsetTables &ot, int r, const uint8_t *c0,
+                                             int plane, int pitch, uint32_t a_addr,
+                                             uint32_t b_addr, uint32_t a64, uint32_t stride) {
+    const uint32_t *rows = ot.rows + __ldg(ot.rows_start + r);
+    const int nrows = __ldg(ot.rows_start + r + 1) - __ldg(ot.rows_start + r);
+    // row ri of this thread: its aligned words, the row's offset in the
+    // first one, its length and its packed (dy, dz, w)
+    auto fetch = [&](int ri, uint32_t &e, int &off, int &n,
+                     unsigned long long (&wd)[kBlkRowWords]) {
+        e = 0u;
+        off = 0;
+        n = 0;
+        if (ri < nrows) {
+            e = __ldg(rows + ri);
+            const int dy = (int)(e & 0xffu) - 64, dz = (int)((e >> 8) & 0xffu) - 64;
+            const int w = (int)(e >> 16);
+            const uintptr_t a = reinterpret_cast<uintptr_t>(c0 + dz * plane + dy * pitch - w);
+            off = (int)(a & 7u);
+            n = 2 * w + 1;
+            const unsigned long long *q =
+                reinterpret_cast<const unsigned long long *>(a & ~uintptr_t(7));
+            const int nw = (off + n + 7) >> 3;
+#pragma unroll
+            for (int k = 0; k < kBlkRowWords; ++k) wd[k] = k < nw ? __ldg(q + k) : 0ull;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kBlkRowWords; ++k) wd[k] = 0ull;
+        }
+    };
+    uint32_t e;
+    int off, n;
+    unsigned long long wd[kBlkRowWords];
+    fetch(threadIdx.x, e, off, n, wd);
+    for (int r0 = 0; r0 < nrows; r0 += blockDim.x) {
+        uint32_t en;
+        int offn, nn;
+        unsigned long long wn[kBlkRowWords];
+        fetch(r0 + (int)blockDim.x + (int)threadIdx.x, en, offn, nn, wn);
+        const int dy = (int)(e & 0xffu) - 64, dz = (int)((e >> 8) & 0xffu) - 64;
+        const int w = (int)(e >> 16);
+        // the warp's longest row bounds the words it walks; a shorter row's
+        // extra words are zero, so they only add to the value-0 columns
+        const int nw_max = __reduce_max_sync(0xffffffffu, (off + n + 7) >> 3);
+        // 32-bit words: voxel t (dx = t - w) adds 1 + (t - w + r) << 11 to A
+        // and (dy + r) | (dz + r) << 16 to B.  64-bit word: 1 | (t - w + 32)
+        // << 11 | (dy + 32) << 28 | (dz + 32) << 45, built from its 32-bit
+        // halves (t only changes bits 11..27)
+        const uint32_t row_a = W32 ? 1u + ((uint32_t)(r - w) << 11)
+                                   : 1u | ((uint32_t)(32 - w) << 11) | ((uint32_t)(dy + 32) << 28);
+        const uint32_t row_b = W32 ? (uint32_t)(dy + r) | ((uint32_t)(dz + r) << 16)
+                                   : ((uint32_t)(dy + 32) >> 4) | ((uint32_t)(dz + 32) << 13);
+#pragma unroll
+        for (int k = 0; k < kBlkRowWords; ++k) {
+            if (k >= nw_max) break;
+            const int lo = off - 8 * k, hi = off + n - 8 * k;
+            unsigned long long x = wd[k];
+            if (lo > 0) x &= ~0ull << (8 * lo);           // word 0 only: lo = off <= 7
+            if (hi < 8) x = hi > 0 ? x & ((1ull << (8 * hi)) - 1ull) : 0ull;
+            // byte b is voxel t = 8k + b - off (mod 2^32 arithmetic)
+            const uint32_t a_k = row_a + ((uint32_t)(8 * k - off) << 11);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const uint32_t v = byte_of(x, b);
+                if constexpr (W32) {
+                    red_add_shared(a_addr + v * stride, a_k + ((uint32_t)b << 11));
+                    red_add_shared(b_addr + v * stride, row_b);
+                } else {
+                    const unsigned long long inc =
+                        ((unsigned long long)row_b << 32) | (a_k + ((uint32_t)b << 11));
+                    red_add_shared_u64(a64 + v * 2u * stride, inc);
+                }
+            }
+        }
+        e = en;
+        off = offn;
+        n = nn;
+#pragma unroll
+        for (int k = 0; k < kBlkRowWords; ++k) wd[k] = wn[k];
+    }
+}
+
 __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long long *cols,
-                        int *part, int *acc, const int P[3], int r) {
+                        int *acc, const int P[3], int r) {
     const int B = J.vol.B;
     const int NC = ms_columns(__ldg(ot.ball_size + r));
     // two 32-bit words per column where the row sums fit (ot.ms32), else
-    // one 64-bit word; the column area is B * NC * 8 bytes either way
+    // one 64-bit word; the column area is (B + 1) * NC * 8 bytes either way
     const bool w32 = __ldg(ot.ms32 + r) != 0;
-    for (int k = threadIdx.x; k < B * NC; k += blockDim.x) cols[k] = 0ull;
+    for (int k = threadIdx.x; k < (B + 1) * NC; k += blockDim.x) cols[k] = 0ull;
     __syncthreads();
     const uint8_t *c0 = voxel_ptr(J.vol, P);
     const int plane = (int)J.vol.plane, pitch = (int)J.vol.pitch;
     const int col = threadIdx.x & (NC - 1);
-    const uint32_t col_addr = smem_u32(cols + col);
-    // 32-bit words: A of value v at a_addr + 4 NC v, B at b_addr + 4 NC v
+    // 32-bit words: A of value v at a_addr + 4 NC v, B at b_addr + 4 NC v;
+    // 64-bit words: value v at a64 + 8 NC v
     uint32_t *colA = reinterpret_cast<uint32_t *>(cols);
-    const uint32_t a_addr = smem_u32(colA + col) - 4u * (uint32_t)NC;
-    const uint32_t b_addr = a_addr + 4u * (uint32_t)(B * NC);
-    const uint32_t *rows = ot.rows + __ldg(ot.rows_start + r);
-    const int nrows = __ldg(ot.rows_start + r + 1) - __ldg(ot.rows_start + r);
-    for (int ri = threadIdx.x; ri < nrows; ri += blockDim.x) {
-        int dy, dz, w;
-        const unsigned long long row_inc = ms_row_word(__ldg(rows + ri), &dy, &dz, &w);
-        if (w32) {
-            // voxel t (dx = t - w) adds 1 + (t - w + r) << 11 to A and
-            // (dy + r) | (dz + r) << 16 to B
-            const uint32_t row_a = 1u + ((uint32_t)(r - w) << 11);
-            const uint32_t row_b = (uint32_t)(dy + r) | ((uint32_t)(dz + r) << 16);
-            walk_row_masked(c0 + dz * plane + dy * pitch - w, w, [&](int t, uint32_t v) {
-                if (v != 0u) {
-                    red_add_shared(a_addr + v * 4u * (uint32_t)NC, row_a + ((uint32_t)t << 11));
-                    red_add_shared(b_addr + v * 4u * (uint32_t)NC, row_b);
-                }
-            });
-        } else {
-            walk_row_masked(c0 + dz * plane + dy * pitch - w, w, [&](int t, uint32_t v) {
-                if (v != 0u)
-                    red_add_shared_u64(col_addr + (v - 1) * NC * 8,
-                                       row_inc + ((unsigned long long)t << 11));
-            });
-        }
-    }
+    const uint32_t stride = 4u * (uint32_t)NC;
+    const uint32_t a_addr = smem_u32(colA + col);
+    const uint32_t b_addr = a_addr + stride * (uint32_t)(B + 1);
+    const uint32_t a64 = smem_u32(cols + col);
+    if (w32)
+        ms_walk_rows<true>(ot, r, c0, plane, pitch, a_addr, b_addr, a64, stride);
+    else
+        ms_walk_rows<false>(ot, r, c0, plane, pitch, a_addr, b_addr, a64, stride);
     __syncthreads();
     // column sums: warp w takes bins w, w + 8, ...; lane l reads columns l,
     // l + 32, ... of the bin (consecutive lanes, consecutive words: no bank
     // conflicts) and the warp adds the unpacked fields with shuffles
-    (void)part;
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int off = w32 ? r : 32;   // the offset added to dx, dy, dz
+    const int shift = w32 ? r : 32;   // the offset added to dx, dy, dz
     for (int b = threadIdx.x >> 5; b < B; b += nw) {
         int c = 0, sx = 0, sy = 0, sz = 0;
         for (int k = lane; k < NC; k += 32) {
             if (w32) {
-                const uint32_t xa = colA[b * NC + k], xb = colA[(B + b) * NC + k];
+                const uint32_t xa = colA[(b + 1) * NC + k], xb = colA[(B + 2 + b) * NC + k];
                 c += (int)(xa & 0x7ffu);
                 sx += (int)(xa >> 11);
                 sy += (int)(xb & 0xffffu);
                 sz += (int)(xb >> 16);
             } else {
-                const unsigned long long x = cols[b * NC + k];
+                const unsigned long long x = cols[(b + 1) * NC + k];
                 c += (int)(x & 0x7ffull);
                 sx += (int)((x >> 11) & 0x1ffffull);
                 sy += (int)((x >> 28) & 0x1ffffull);
@@ -582,9 +655,9 @@ __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long 
         }
         if (lane == 0) {
             acc[4 * b] = c;
-            acc[4 * b + 1] = sx - off * c;
-            acc[4 * b + 2] = sy - off * c;
-            acc[4 * b + 3] = sz - off * c;
+            acc[4 * b + 1] = sx - shift * c;
+            acc[4 * b + 2] = sy - shift * c;
+            acc[4 * b + 3] = sz - shift * c;
         }
     }
     __syncthreads();
@@ -771,8 +844,8 @@ __device__ void ms_result_warp(const SeedJob &J, int64_t item, const int *acc, d
 }
 
 __device__ void ms_item(const SeedJob &J, int64_t item, const OffsetTables &ot, const double *T,
-                        const double *L, unsigned long long *cols, int *part, int *acc,
-                        double *prod, SeedShared &sh) {
+                        const double *L, unsigned long long *cols, int *acc, double *prod,
+                        SeedShared &sh) {
     const int dims[3] = {J.vol.nx, J.vol.ny, J.vol.nz};
     const int64_t sidx = item / J.S;
     const int r = J.r_min + (int)(item % J.S);
@@ -791,7 +864,7 @@ __device__ void ms_item(const SeedJob &J, int64_t item, const OffsetTables &ot, 
     }
     const int it_end = J.iter_budget > 0 ? min(J.max_iter, it + J.iter_budget) : J.max_iter;
     while (it < it_end) {
-        ms_pass(J, ot, cols, part, acc, P, r);
+        ms_pass(J, ot, cols, acc, P, r);
         if (threadIdx.x < 32) {
             int d[3];
             ms_delta_warp(J.vol.B, acc, prod, d);
@@ -816,7 +889,7 @@ __device__ void ms_item(const SeedJob &J, int64_t item, const OffsetTables &ot, 
         if (threadIdx.x == 0) *stp = make_int4(P[0], P[1], P[2], it | kItemStarted);
         return;
     }
-    if (!fresh) ms_pass(J, ot, cols, part, acc, P, r);
+    if (!fresh) ms_pass(J, ot, cols, acc, P, r);
     if (threadIdx.x < 32) ms_result_warp(J, item, acc, prod, T, L, P, r, it, conv);
     if (stp && threadIdx.x == 0) {
         *stp = make_int4(P[0], P[1], P[2], it | kItemStarted | kItemDone);
@@ -883,16 +956,15 @@ __device__ void ms_item_warp(const SeedJob &J, int64_t item, const OffsetTables 
 // launch carries tickets of kind k.
 struct Layout {
     size_t cnt, hb, oct_total;                  // octant: cnt[9][S][B+1] u32, hb[8S] f64
-    size_t cols, part, acc, prod, msb_total;    // mean shift, block path
+    size_t cols, acc, prod, msb_total;          // mean shift, block path
     size_t msw, msw_stride, msw_total;          // mean shift, warp path: 8 regions
     int kinds;
     __host__ __device__ Layout(int B, int S, int kinds_) : kinds(kinds_) {
         cnt = 0;
         hb = ((size_t)9 * S * (B + 1) * 4 + 15) / 16 * 16;
         oct_total = hb + (size_t)8 * S * 8;
-        cols = 0;
-        part = (size_t)B * 128 * 8;
-        acc = part + (size_t)B * 8 * 4 * 4;
+        cols = 0;                                   // (B + 1) * NC words of 8 bytes, NC <= 128
+        acc = (size_t)(B + 1) * 128 * 8;
         prod = acc + (size_t)B * 4 * 4;
         msb_total = prod + (size_t)4 * ((B + 7) & ~7) * 8;   // 4 chains of Bp doubles
         // a warp region holds B * 32 column words, later acc (16 B bytes)
@@ -953,7 +1025,7 @@ __global__ void __launch_bounds__(KINDS == 1 ? kOctThreads : kSeedThreads,
             const int64_t r_idx = J.S - 1 - local / J.n_seeds;   // a block-path radius
             const int64_t item = (local % J.n_seeds) * J.S + r_idx;
             ms_item(J, item, ot, T, L, reinterpret_cast<unsigned long long *>(smem + lay.cols),
-                    reinterpret_cast<int *>(smem + lay.part), reinterpret_cast<int *>(smem + lay.acc),
+                    reinterpret_cast<int *>(smem + lay.acc),
                     reinterpret_cast<double *>(smem + lay.prod), sh);
             continue;
         }
