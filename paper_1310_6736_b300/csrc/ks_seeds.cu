@@ -663,80 +663,90 @@ __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long 
     __syncthreads();
 }
 
-// Warp path: the same sums with one column per lane.  cols holds B * 32
-// words; acc (B * 4 ints) is written over its start once the columns have
-// been read.
+// Warp path: the same sums with one column per lane.  cols holds (B + 1)
+// * 64 words: words A of value v at colA[v * 32 + lane], words B at
+// colA[(B + 1 + v) * 32 + lane], value 0 (not counted, and the masked bytes
+// of a row's first and last words) never read, so a byte costs no branch;
+// acc (B * 4 ints) is written over the start once the columns have been
+// read.
 __device__ void ms_pass_warp(const SeedJob &J, const OffsetTables &ot, unsigned long long *cols,
                              int *acc, const int P[3], int r) {
     const int B = J.vol.B, lane = threadIdx.x & 31;
-    // words A of bin b at colA[b * 32 + lane], words B at colA[(B + b) * 32 + lane]
     uint32_t *colA = reinterpret_cast<uint32_t *>(cols);
-    for (int k = lane; k < 2 * B * 32; k += 32) colA[k] = 0u;
+    for (int k = lane; k < 2 * (B + 1) * 32; k += 32) colA[k] = 0u;
     __syncwarp();
     const uint8_t *c0 = voxel_ptr(J.vol, P);
     const int plane = (int)J.vol.plane, pitch = (int)J.vol.pitch;
-    const uint32_t a_addr = smem_u32(colA + lane) - 32 * 4;      // value v: a_addr + 128 v
-    const uint32_t b_addr = a_addr + (uint32_t)B * 32 * 4;
+    const uint32_t a_addr = smem_u32(colA + lane);               // value v: a_addr + 128 v
+    const uint32_t b_addr = a_addr + (uint32_t)(B + 1) * 32 * 4;
     const uint32_t *rows = ot.rows + __ldg(ot.rows_start + r);
     const int nrows = __ldg(ot.rows_start + r + 1) - __ldg(ot.rows_start + r);
     // A lane's rows are lane, lane + 32, ...: the words of the next row are
     // loaded before the current row is counted, so one row's loads are
     // always in flight.  A row of Ball(r <= 20) has at most 41 voxels, which
     // with up to 7 bytes of alignment fit in kRowWords aligned words; the
-    // bytes read past the row stay inside the halo-padded allocation.
-    auto fetch = [&](int ri, uint32_t &e, int &off, unsigned long long (&wd)[kRowWords]) {
-        e = __ldg(rows + ri);
-        const int dy = (int)(e & 0xffu) - 64, dz = (int)((e >> 8) & 0xffu) - 64;
-        const int w = (int)(e >> 16);
-        const uintptr_t a = reinterpret_cast<uintptr_t>(c0 + dz * plane + dy * pitch - w);
-        off = (int)(a & 7u);
-        const unsigned long long *q =
-            reinterpret_cast<const unsigned long long *>(a & ~uintptr_t(7));
+    // words past a row's last one are not loaded.
+    auto fetch = [&](int ri, uint32_t &e, int &off, int &n, unsigned long long (&wd)[kRowWords]) {
+        e = 0u;
+        off = 0;
+        n = 0;
+        if (ri < nrows) {
+            e = __ldg(rows + ri);
+            const int dy = (int)(e & 0xffu) - 64, dz = (int)((e >> 8) & 0xffu) - 64;
+            const int w = (int)(e >> 16);
+            const uintptr_t a = reinterpret_cast<uintptr_t>(c0 + dz * plane + dy * pitch - w);
+            off = (int)(a & 7u);
+            n = 2 * w + 1;
+            const unsigned long long *q =
+                reinterpret_cast<const unsigned long long *>(a & ~uintptr_t(7));
+            const int nw = (off + n + 7) >> 3;
 #pragma unroll
-        for (int k = 0; k < kRowWords; ++k) wd[k] = __ldg(q + k);
+            for (int k = 0; k < kRowWords; ++k) wd[k] = k < nw ? __ldg(q + k) : 0ull;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kRowWords; ++k) wd[k] = 0ull;
+        }
     };
-    int ri = lane, off = 0;
-    uint32_t e = 0;
+    uint32_t e;
+    int off, n;
     unsigned long long wd[kRowWords];
-    if (ri < nrows) fetch(ri, e, off, wd);
-    while (ri < nrows) {
-        const int rn = ri + 32;
-        int offn = 0;
-        uint32_t en = 0;
+    fetch(lane, e, off, n, wd);
+    for (int r0 = 0; r0 < nrows; r0 += 32) {
+        uint32_t en;
+        int offn, nn;
         unsigned long long wn[kRowWords];
-        if (rn < nrows) fetch(rn, en, offn, wn);
+        fetch(r0 + 32 + lane, en, offn, nn, wn);
         const int dy = (int)(e & 0xffu) - 64, dz = (int)((e >> 8) & 0xffu) - 64;
         const int w = (int)(e >> 16);
-        const int n = 2 * w + 1;
+        // the warp's longest row bounds the words it walks
+        const int nw_max = __reduce_max_sync(0xffffffffu, (off + n + 7) >> 3);
         // voxel t of the row (dx = t - w) adds 1 + (t - w + 20) << 11 to A
         // and the row constant (dy + 20) | (dz + 20) << 16 to B
         const uint32_t row_a = 1u + ((uint32_t)(20 - w) << 11);
         const uint32_t row_b = (uint32_t)(dy + 20) | ((uint32_t)(dz + 20) << 16);
 #pragma unroll
         for (int k = 0; k < kRowWords; ++k) {
+            if (k >= nw_max) break;
             // bytes [lo, hi) of word k belong to the row; the others are
-            // zeroed and so read as "not counted"
+            // zeroed and so count as value 0
             const int lo = off - 8 * k, hi = off + n - 8 * k;
-            if (hi <= 0) break;
             unsigned long long x = wd[k];
             if (lo > 0) x &= ~0ull << (8 * lo);           // word 0 only: lo = off <= 7
-            if (hi < 8) x &= (1ull << (8 * hi)) - 1ull;
+            if (hi < 8) x = hi > 0 ? x & ((1ull << (8 * hi)) - 1ull) : 0ull;
             // byte b is voxel t = 8k + b - off (mod 2^32 arithmetic)
             const uint32_t a_k = row_a + ((uint32_t)(8 * k - off) << 11);
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
                 const uint32_t v = byte_of(x, b);
-                if (v != 0u) {
-                    red_add_shared(a_addr + (v << 7), a_k + ((uint32_t)b << 11));
-                    red_add_shared(b_addr + (v << 7), row_b);
-                }
+                red_add_shared(a_addr + (v << 7), a_k + ((uint32_t)b << 11));
+                red_add_shared(b_addr + (v << 7), row_b);
             }
         }
         e = en;
         off = offn;
+        n = nn;
 #pragma unroll
         for (int k = 0; k < kRowWords; ++k) wd[k] = wn[k];
-        ri = rn;
     }
     __syncwarp();
     // lane b sums bins b and b + 32 over the 32 columns, starting at its
@@ -747,8 +757,8 @@ __device__ void ms_pass_warp(const SeedJob &J, const OffsetTables &ot, unsigned 
         const int b = lane + 32 * h;
         if (b < B) {
             for (int k = 0; k < 32; ++k) {
-                const uint32_t xa = colA[b * 32 + ((k + lane) & 31)];
-                const uint32_t xb = colA[(B + b) * 32 + ((k + lane) & 31)];
+                const uint32_t xa = colA[(b + 1) * 32 + ((k + lane) & 31)];
+                const uint32_t xb = colA[(B + 2 + b) * 32 + ((k + lane) & 31)];
                 s[h][0] += (int)(xa & 0x7ffu);
                 s[h][1] += (int)(xa >> 11);
                 s[h][2] += (int)(xb & 0xffffu);
@@ -898,7 +908,7 @@ __device__ void ms_item(const SeedJob &J, int64_t item, const OffsetTables &ot, 
     __syncthreads();
 }
 
-// One item on one warp; region is the warp's own B * 256 bytes.
+// One item on one warp; region is the warp's own (B + 1) * 256 bytes.
 __device__ void ms_item_warp(const SeedJob &J, int64_t item, const OffsetTables &ot,
                              const double *T, const double *L, unsigned long long *region) {
     const int dims[3] = {J.vol.nx, J.vol.ny, J.vol.nz};
@@ -967,10 +977,10 @@ struct Layout {
         acc = (size_t)(B + 1) * 128 * 8;
         prod = acc + (size_t)B * 4 * 4;
         msb_total = prod + (size_t)4 * ((B + 7) & ~7) * 8;   // 4 chains of Bp doubles
-        // a warp region holds B * 32 column words, later acc (16 B bytes)
-        // and 4 chains of Bp doubles: 16 B + 32 (B + 7) <= 256 B for B >= 2
+        // a warp region holds (B + 1) * 64 column words, later acc (16 B
+        // bytes) and 4 chains of Bp doubles: 16 B + 32 (B + 7) <= 256 (B + 1)
         msw = 0;
-        msw_stride = (size_t)B * 256;
+        msw_stride = (size_t)(B + 1) * 256;
         msw_total = B <= kWarpMsBmax ? msw + (kSeedThreads / 32) * msw_stride : 0;
     }
     __host__ __device__ size_t total() const {
