@@ -996,9 +996,17 @@ struct Layout {
 
 // KINDS: bit k set when the launch carries tickets of kind k; one
 // instantiation per combination, so each gets its own register allocation.
+// KINDS bit: a mean-shift launch whose items all take the block path (more
+// than kWarpMsBmax bins), compiled without the warp path so that its
+// registers allow three blocks per SM.
+constexpr int kMsBlockOnly = 1 << 3;
+
 template <int KINDS>
 __global__ void __launch_bounds__(KINDS == 1 ? kOctThreads : kSeedThreads,
-                                  KINDS == 1 ? 6 : (KINDS == 2 ? 2 : 1))
+                                  KINDS == 1 ? 6
+                                  : KINDS == 2 ? 2
+                                  : KINDS == ((1 << kMeanShift) | kMsBlockOnly) ? 3
+                                                                                : 1)
     k_seeds(const SeedQueue q, const OffsetTables ot,
                                                         const double *__restrict__ T,
                                                         const double *__restrict__ L,
@@ -1039,6 +1047,9 @@ __global__ void __launch_bounds__(KINDS == 1 ? kOctThreads : kSeedThreads,
                     reinterpret_cast<double *>(smem + lay.prod), sh);
             continue;
         }
+        if constexpr ((KINDS & kMsBlockOnly) != 0) {
+            continue;                         // no warp-path items in such a launch
+        } else {
         // kMsWarp: items of radii <= kWarpMsRmax, one per warp.  Their
         // segments follow every other segment of the queue, so from the
         // first such ticket on each warp draws its own tickets and the block
@@ -1069,6 +1080,7 @@ __global__ void __launch_bounds__(KINDS == 1 ? kOctThreads : kSeedThreads,
         }
         return;
         }
+        }
     }
 }
 
@@ -1086,7 +1098,12 @@ using SeedKernel = void (*)(const SeedQueue, const OffsetTables, const double *,
                             int, int, int);
 static int seed_threads(int kinds) { return kinds == (1 << kOctant) ? kOctThreads : kSeedThreads; }
 
-static SeedKernel seed_kernel(int kinds) {
+// The instantiation for a launch of these kinds whose volumes have at most
+// max_B bins: mean shift alone with more than kWarpMsBmax bins has only
+// block-path items.
+static SeedKernel seed_kernel(int kinds, int max_B) {
+    if (kinds == (1 << kMeanShift) && max_B > kWarpMsBmax)
+        return k_seeds<(1 << kMeanShift) | kMsBlockOnly>;
     return kinds == (1 << kOctant) ? k_seeds<1 << kOctant>
            : kinds == (1 << kMeanShift) ? k_seeds<1 << kMeanShift>
                                         : k_seeds<(1 << kOctant) | (1 << kMeanShift)>;
@@ -1096,7 +1113,7 @@ int seed_blocks_per_sm(int max_B, int max_S, int kinds) {
     // the occupancy query honours the kernel's dynamic shared-memory limit,
     // so raise it to this layout's size first
     const size_t smem = seed_smem_bytes(max_B, max_S, kinds);
-    const SeedKernel k = seed_kernel(kinds);
+    const SeedKernel k = seed_kernel(kinds, max_B);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, seed_threads(kinds), smem);
@@ -1107,7 +1124,7 @@ cudaError_t launch_seeds(const LaunchCtx &lc, const SeedQueue &q, const OffsetTa
                          const double *T, const double *L, int max_B, int max_S, int kinds,
                          bool persistent, int grid) {
     const size_t smem = seed_smem_bytes(max_B, max_S, kinds);
-    const SeedKernel k = seed_kernel(kinds);
+    const SeedKernel k = seed_kernel(kinds, max_B);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, seed_threads(kinds), smem, lc.stream>>>(q, ot, T, L, max_B, max_S, persistent ? 1 : 0);
