@@ -624,36 +624,43 @@ __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long 
     else
         ms_walk_rows<false>(ot, r, c0, plane, pitch, a_addr, b_addr, a64, stride);
     __syncthreads();
-    // column sums: warp w takes bins w, w + 8, ...; lane l reads columns l,
-    // l + 32, ... of the bin (consecutive lanes, consecutive words: no bank
-    // conflicts) and the warp adds the unpacked fields with shuffles
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // column sums: G threads per bin (the largest power of two up to 32 with
+    // G B <= blockDim.x).  Thread q of a bin's group reads its NC / G
+    // columns q + G ((k + b) mod (NC / G)): rotated by the bin, so the 32
+    // lanes of a warp (32 / G bins) read 32 different banks.  The group adds
+    // the unpacked fields with xor shuffles.
+    int G = 32;
+    while (G > 1 && G * B > (int)blockDim.x) G >>= 1;
+    const int per = NC / G, q = threadIdx.x & (G - 1);
     const int shift = w32 ? r : 32;   // the offset added to dx, dy, dz
-    for (int b = threadIdx.x >> 5; b < B; b += nw) {
+    for (int b0 = 0; b0 < B; b0 += (int)blockDim.x / G) {
+        const int b = b0 + (int)threadIdx.x / G;
         int c = 0, sx = 0, sy = 0, sz = 0;
-        for (int k = lane; k < NC; k += 32) {
-            if (w32) {
-                const uint32_t xa = colA[(b + 1) * NC + k], xb = colA[(B + 2 + b) * NC + k];
-                c += (int)(xa & 0x7ffu);
-                sx += (int)(xa >> 11);
-                sy += (int)(xb & 0xffffu);
-                sz += (int)(xb >> 16);
-            } else {
-                const unsigned long long x = cols[(b + 1) * NC + k];
-                c += (int)(x & 0x7ffull);
-                sx += (int)((x >> 11) & 0x1ffffull);
-                sy += (int)((x >> 28) & 0x1ffffull);
-                sz += (int)((x >> 45) & 0x1ffffull);
+        if (b < B) {
+            for (int k = 0; k < per; ++k) {
+                const int cc = q + G * ((k + b) & (per - 1));
+                if (w32) {
+                    const uint32_t xa = colA[(b + 1) * NC + cc], xb = colA[(B + 2 + b) * NC + cc];
+                    c += (int)(xa & 0x7ffu);
+                    sx += (int)(xa >> 11);
+                    sy += (int)(xb & 0xffffu);
+                    sz += (int)(xb >> 16);
+                } else {
+                    const unsigned long long x = cols[(b + 1) * NC + cc];
+                    c += (int)(x & 0x7ffull);
+                    sx += (int)((x >> 11) & 0x1ffffull);
+                    sy += (int)((x >> 28) & 0x1ffffull);
+                    sz += (int)((x >> 45) & 0x1ffffull);
+                }
             }
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
+        for (int o = G >> 1; o; o >>= 1) {
             c += __shfl_xor_sync(0xffffffffu, c, o);
             sx += __shfl_xor_sync(0xffffffffu, sx, o);
             sy += __shfl_xor_sync(0xffffffffu, sy, o);
             sz += __shfl_xor_sync(0xffffffffu, sz, o);
         }
-        if (lane == 0) {
+        if (b < B && q == 0) {
             acc[4 * b] = c;
             acc[4 * b + 1] = sx - shift * c;
             acc[4 * b + 2] = sy - shift * c;
