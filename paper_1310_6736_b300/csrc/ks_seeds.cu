@@ -38,6 +38,10 @@ namespace ks {
 namespace {
 
 constexpr int kCycleMax = 8;     // longest cycle of centres the octant climb detects
+// KINDS bit: a mean-shift launch whose items all take the block path (more
+// than 32 bins), compiled without the warp path so that its registers allow
+// three blocks per SM.
+constexpr int kMsBlockOnly = 1 << 3;
 
 struct SeedShared {
     int step[3];
@@ -515,10 +519,19 @@ __device__ __forceinline__ unsigned long long ms_row_word(uint32_t e, int *dy, i
 // streams a row as aligned 8-byte words, the next row's words loaded while
 // the current row is counted.
 constexpr int kBlkRowWords = 9;   // a row of Ball(r <= 32): <= 65 bins + 7 bytes of alignment
+// Block-only launches (more than 32 bins) keep the B words at this fixed
+// byte offset from the A words when (B + 1) * 128 words fit below it, so
+// the second reduction of a voxel takes the A address plus an immediate.
+constexpr uint32_t kMsBOff = 34816;
+
+template <uint32_t OFF>
+__device__ __forceinline__ void red_add_shared_at(uint32_t addr, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0+%2], %1;" ::"r"(addr), "r"(v), "n"(OFF));
+}
 
 // The row walk of the block path (W32: two 32-bit words per voxel, else one
 // 64-bit word); see ms_pass.
-template <bool W32>
+template <bool W32, uint32_t BOFF>
 __device__ __forceinline__ void ms_walk_rows(const OffsetTables &ot, int r, const uint8_t *c0,
                                              int plane, int pitch, uint32_t a_addr,
                                              uint32_t b_addr, uint32_t a64, uint32_t stride) {
@@ -581,10 +594,15 @@ __device__ __forceinline__ void ms_walk_rows(const OffsetTables &ot, int r, cons
             const uint32_t a_k = row_a + ((uint32_t)(8 * k - off) << 11);
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
-                const uint32_t v = byte_of(x, b);
+                const uint32_t v =
+                    __byte_perm(b < 4 ? (uint32_t)x : (uint32_t)(x >> 32), 0u, 0x4440u + (b & 3));
                 if constexpr (W32) {
-                    red_add_shared(a_addr + v * stride, a_k + ((uint32_t)b << 11));
-                    red_add_shared(b_addr + v * stride, row_b);
+                    const uint32_t av = a_addr + v * stride;
+                    red_add_shared(av, a_k + ((uint32_t)b << 11));
+                    if constexpr (BOFF != 0u)
+                        red_add_shared_at<BOFF>(av, row_b);
+                    else
+                        red_add_shared(b_addr + v * stride, row_b);
                 } else {
                     const unsigned long long inc =
                         ((unsigned long long)row_b << 32) | (a_k + ((uint32_t)b << 11));
@@ -600,6 +618,9 @@ __device__ __forceinline__ void ms_walk_rows(const OffsetTables &ot, int r, cons
     }
 }
 
+// FIXB: the launch's layout reserves 2 kMsBOff bytes of columns, and the B
+// words go at kMsBOff when they fit (two 32-bit words per voxel only).
+template <bool FIXB>
 __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long long *cols,
                         int *acc, const int P[3], int r) {
     const int B = J.vol.B;
@@ -607,22 +628,30 @@ __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long 
     // two 32-bit words per column where the row sums fit (ot.ms32), else
     // one 64-bit word; the column area is (B + 1) * NC * 8 bytes either way
     const bool w32 = __ldg(ot.ms32 + r) != 0;
-    for (int k = threadIdx.x; k < (B + 1) * NC; k += blockDim.x) cols[k] = 0ull;
+    const bool fixed = FIXB && w32 && (uint32_t)((B + 1) * NC * 4) <= kMsBOff;
+    // 32-bit word index of the B words (64-bit words: the upper half)
+    const int boffw = fixed ? (int)(kMsBOff / 4) : (B + 1) * NC;
+    uint32_t *colA = reinterpret_cast<uint32_t *>(cols);
+    for (int k = threadIdx.x; k < (B + 1) * NC; k += blockDim.x) {
+        colA[k] = 0u;
+        colA[boffw + k] = 0u;
+    }
     __syncthreads();
     const uint8_t *c0 = voxel_ptr(J.vol, P);
     const int plane = (int)J.vol.plane, pitch = (int)J.vol.pitch;
     const int col = threadIdx.x & (NC - 1);
     // 32-bit words: A of value v at a_addr + 4 NC v, B at b_addr + 4 NC v;
     // 64-bit words: value v at a64 + 8 NC v
-    uint32_t *colA = reinterpret_cast<uint32_t *>(cols);
     const uint32_t stride = 4u * (uint32_t)NC;
     const uint32_t a_addr = smem_u32(colA + col);
-    const uint32_t b_addr = a_addr + stride * (uint32_t)(B + 1);
+    const uint32_t b_addr = a_addr + 4u * (uint32_t)boffw;
     const uint32_t a64 = smem_u32(cols + col);
-    if (w32)
-        ms_walk_rows<true>(ot, r, c0, plane, pitch, a_addr, b_addr, a64, stride);
+    if (fixed)
+        ms_walk_rows<true, kMsBOff>(ot, r, c0, plane, pitch, a_addr, b_addr, a64, stride);
+    else if (w32)
+        ms_walk_rows<true, 0u>(ot, r, c0, plane, pitch, a_addr, b_addr, a64, stride);
     else
-        ms_walk_rows<false>(ot, r, c0, plane, pitch, a_addr, b_addr, a64, stride);
+        ms_walk_rows<false, 0u>(ot, r, c0, plane, pitch, a_addr, b_addr, a64, stride);
     __syncthreads();
     // column sums: G threads per bin (the largest power of two up to 32 with
     // G B <= blockDim.x).  Thread q of a bin's group reads its NC / G
@@ -640,7 +669,7 @@ __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long 
             for (int k = 0; k < per; ++k) {
                 const int cc = q + G * ((k + b) & (per - 1));
                 if (w32) {
-                    const uint32_t xa = colA[(b + 1) * NC + cc], xb = colA[(B + 2 + b) * NC + cc];
+                    const uint32_t xa = colA[(b + 1) * NC + cc], xb = colA[boffw + (b + 1) * NC + cc];
                     c += (int)(xa & 0x7ffu);
                     sx += (int)(xa >> 11);
                     sy += (int)(xb & 0xffffu);
@@ -860,6 +889,7 @@ __device__ void ms_result_warp(const SeedJob &J, int64_t item, const int *acc, d
     __syncwarp();
 }
 
+template <bool FIXB>
 __device__ void ms_item(const SeedJob &J, int64_t item, const OffsetTables &ot, const double *T,
                         const double *L, unsigned long long *cols, int *acc, double *prod,
                         SeedShared &sh) {
@@ -881,7 +911,7 @@ __device__ void ms_item(const SeedJob &J, int64_t item, const OffsetTables &ot, 
     }
     const int it_end = J.iter_budget > 0 ? min(J.max_iter, it + J.iter_budget) : J.max_iter;
     while (it < it_end) {
-        ms_pass(J, ot, cols, acc, P, r);
+        ms_pass<FIXB>(J, ot, cols, acc, P, r);
         if (threadIdx.x < 32) {
             int d[3];
             ms_delta_warp(J.vol.B, acc, prod, d);
@@ -906,7 +936,7 @@ __device__ void ms_item(const SeedJob &J, int64_t item, const OffsetTables &ot, 
         if (threadIdx.x == 0) *stp = make_int4(P[0], P[1], P[2], it | kItemStarted);
         return;
     }
-    if (!fresh) ms_pass(J, ot, cols, acc, P, r);
+    if (!fresh) ms_pass<FIXB>(J, ot, cols, acc, P, r);
     if (threadIdx.x < 32) ms_result_warp(J, item, acc, prod, T, L, P, r, it, conv);
     if (stp && threadIdx.x == 0) {
         *stp = make_int4(P[0], P[1], P[2], it | kItemStarted | kItemDone);
@@ -982,6 +1012,7 @@ struct Layout {
         oct_total = hb + (size_t)8 * S * 8;
         cols = 0;                                   // (B + 1) * NC words of 8 bytes, NC <= 128
         acc = (size_t)(B + 1) * 128 * 8;
+        if ((kinds & kMsBlockOnly) && acc < 2 * (size_t)kMsBOff) acc = 2 * (size_t)kMsBOff;
         prod = acc + (size_t)B * 4 * 4;
         msb_total = prod + (size_t)4 * ((B + 7) & ~7) * 8;   // 4 chains of Bp doubles
         // a warp region holds (B + 1) * 64 column words, later acc (16 B
@@ -1003,11 +1034,6 @@ struct Layout {
 
 // KINDS: bit k set when the launch carries tickets of kind k; one
 // instantiation per combination, so each gets its own register allocation.
-// KINDS bit: a mean-shift launch whose items all take the block path (more
-// than kWarpMsBmax bins), compiled without the warp path so that its
-// registers allow three blocks per SM.
-constexpr int kMsBlockOnly = 1 << 3;
-
 template <int KINDS>
 __global__ void __launch_bounds__(KINDS == 1 ? kOctThreads : kSeedThreads,
                                   KINDS == 1 ? 6
@@ -1049,7 +1075,8 @@ __global__ void __launch_bounds__(KINDS == 1 ? kOctThreads : kSeedThreads,
             // largest radius first
             const int64_t r_idx = J.S - 1 - local / J.n_seeds;   // a block-path radius
             const int64_t item = (local % J.n_seeds) * J.S + r_idx;
-            ms_item(J, item, ot, T, L, reinterpret_cast<unsigned long long *>(smem + lay.cols),
+            ms_item<(KINDS & kMsBlockOnly) != 0>(
+                J, item, ot, T, L, reinterpret_cast<unsigned long long *>(smem + lay.cols),
                     reinterpret_cast<int *>(smem + lay.acc),
                     reinterpret_cast<double *>(smem + lay.prod), sh);
             continue;
@@ -1099,18 +1126,23 @@ int64_t seed_tickets(int kind, int64_t n_seeds, int r_min, int S, int B) {
     return n_seeds * (kind == kMeanShift ? S_big : S - S_big);
 }
 
-size_t seed_smem_bytes(int B, int S, int kinds) { return Layout(B, S, kinds).total(); }
+// The kinds of the instantiation a launch of these kinds uses with at most
+// max_B bins: mean shift alone with more than kWarpMsBmax bins has only
+// block-path items.
+static int launch_kinds(int kinds, int max_B) {
+    return kinds == (1 << kMeanShift) && max_B > kWarpMsBmax ? kinds | kMsBlockOnly : kinds;
+}
+
+size_t seed_smem_bytes(int B, int S, int kinds) {
+    return Layout(B, S, launch_kinds(kinds, B)).total();
+}
 
 using SeedKernel = void (*)(const SeedQueue, const OffsetTables, const double *, const double *,
                             int, int, int);
 static int seed_threads(int kinds) { return kinds == (1 << kOctant) ? kOctThreads : kSeedThreads; }
 
-// The instantiation for a launch of these kinds whose volumes have at most
-// max_B bins: mean shift alone with more than kWarpMsBmax bins has only
-// block-path items.
 static SeedKernel seed_kernel(int kinds, int max_B) {
-    if (kinds == (1 << kMeanShift) && max_B > kWarpMsBmax)
-        return k_seeds<(1 << kMeanShift) | kMsBlockOnly>;
+    if (launch_kinds(kinds, max_B) & kMsBlockOnly) return k_seeds<(1 << kMeanShift) | kMsBlockOnly>;
     return kinds == (1 << kOctant) ? k_seeds<1 << kOctant>
            : kinds == (1 << kMeanShift) ? k_seeds<1 << kMeanShift>
                                         : k_seeds<(1 << kOctant) | (1 << kMeanShift)>;
