@@ -474,13 +474,14 @@ def _grid_subset(w, step):
 
 def run_case(args):
     """Run one part of the step (for profilers): --case dense|octant|meanshift|bin.
-    --seed-step n: every n-th grid seed only (seed cases)."""
+    --seed-step n: every n-th grid seed only (seed cases); --workload: the
+    synthetic workload (default pet128)."""
     import torch
     from paper_1310_6736_b300 import build, ks, synth
     build.build()
     if args.dense_config:
         ks.force_dense_config(*[int(x) for x in args.dense_config.split(",")])
-    w = synth.workload(WORKLOAD)
+    w = synth.workload(args.workload)
     nz, ny, nx = w.volume.shape
     params = ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter)
     ctx = ks.Context()
@@ -507,7 +508,7 @@ def run_case(args):
         torch.cuda.synchronize()
         if i >= args.warmup:
             t.append(time.perf_counter() - t0)
-    print(json.dumps({"case": args.case, "workload": WORKLOAD, "ms": [1e3 * x for x in t],
+    print(json.dumps({"case": args.case, "workload": args.workload, "ms": [1e3 * x for x in t],
                       "dense_config": ctx.dense_config(w.binning["bins"], w.r_max)}), flush=True)
     ctx.close()
     return 0
@@ -1140,6 +1141,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=15.0,
                     help="seconds of oracle work per reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["pet128", "mr256", "spheres48"],
+                    help="--case: the synthetic workload")
     ap.add_argument("--case", choices=["dense", "octant", "quadrant", "meanshift", "bin"],
                     help="run one part of the step only (profiling)")
     ap.add_argument("--dense-config", default="",
