@@ -66,7 +66,7 @@ struct Scratch {
 };
 enum ScratchSlot {
     kScRaw, kScSeeds, kScOct, kScMs, kScTraj, kScY, kScS, kScH, kScW, kScTune, kScPts,
-    kScSelIn, kScSelOut, kScAb, kScTicket, kScCand, kScCount
+    kScSelIn, kScSelOut, kScAb, kScTicket, kScCand, kScSeeds2, kScCount
 };
 static std::mutex g_scratch_mu;
 static std::unordered_map<Ctx *, std::vector<Scratch>> g_scratch;
@@ -820,9 +820,10 @@ int ks_destroy(ks_ctx *ctx) {
         }
     }
     dev_free(c, c->batch_mem, c->batch_mem_bytes);
-    for (cudaEvent_t ev : {c->ev_fork, c->ev_hi, c->ev_lo})
+    dev_free(c, c->batch_mem2, c->batch_mem2_bytes);
+    for (cudaEvent_t ev : {c->ev_fork, c->ev_hi, c->ev_lo, c->ev_lo2})
         if (ev) cudaEventDestroy(ev);
-    for (cudaStream_t ps : {c->hi_stream, c->lo_stream})
+    for (cudaStream_t ps : {c->hi_stream, c->lo_stream, c->lo2_stream})
         if (ps) {
             cudaStreamSynchronize(ps);
             cudaStreamDestroy(ps);
@@ -1128,7 +1129,7 @@ namespace ks {
 // device, one SeedJob, one queue segment.
 static int seeds_to_device(Ctx *c, cudaStream_t s, Volume *v, const ks_params *p,
                            const int32_t *seeds_xyz, int64_t n_in, std::vector<int32_t> *host,
-                           int32_t **dev) {
+                           int32_t **dev, int slot = kScSeeds) {
     if (seeds_xyz) {
         host->assign(seeds_xyz, seeds_xyz + 3 * n_in);
         for (int64_t i = 0; i < n_in; ++i) {
@@ -1140,7 +1141,7 @@ static int seeds_to_device(Ctx *c, cudaStream_t s, Volume *v, const ks_params *p
         *host = seed_grid(v->nx, v->ny, v->nz, p->stride);
     }
     cudaError_t e;
-    *dev = (int32_t *)scratch(c, kScSeeds, std::max<size_t>(host->size() * 4, 16), &e);
+    *dev = (int32_t *)scratch(c, slot, std::max<size_t>(host->size() * 4, 16), &e);
     if (!*dev) return cuda_err(c, e, "seed buffer");
     if (!host->empty())
         KS_TRY_CUDA(c, cudaMemcpyAsync(*dev, host->data(), host->size() * 4,
@@ -1154,23 +1155,27 @@ struct QueueBuf {
     int *seg_kind, *seg_job;
 };
 
-// Lay jobs + segments out in one device buffer (c->batch_mem, grown on
-// demand), copy them, and fill a SeedQueue.
+// Lay jobs + segments out in one device buffer (queue buffer `buf`: 0 =
+// c->batch_mem, 1 = c->batch_mem2, grown on demand), copy them, and fill a
+// SeedQueue.  A buffer is used on one stream at a time, so growing it only
+// waits for that stream.
 static int upload_queue(Ctx *c, cudaStream_t s, const std::vector<SeedJob> &jobs,
                         const std::vector<int64_t> &ss, const std::vector<int> &sk,
-                        const std::vector<int> &sj, SeedQueue *q) {
+                        const std::vector<int> &sj, SeedQueue *q, int buf = 0) {
+    void *&mem = buf ? c->batch_mem2 : c->batch_mem;
+    size_t &mem_bytes = buf ? c->batch_mem2_bytes : c->batch_mem_bytes;
     const size_t bj = jobs.size() * sizeof(SeedJob);
     const size_t bs = ss.size() * 8, bk = sk.size() * 4, bjj = sj.size() * 4;
     const size_t need = 256 + bj + bs + bk + bjj + 64;
-    if (c->batch_mem_bytes < need) {
+    if (mem_bytes < need) {
         cudaStreamSynchronize(s);
-        dev_free(c, c->batch_mem, c->batch_mem_bytes);
-        c->batch_mem = nullptr;
-        c->batch_mem_bytes = 0;
+        dev_free(c, mem, mem_bytes);
+        mem = nullptr;
+        mem_bytes = 0;
         void *p;
         KS_TRY_CUDA(c, dev_alloc(c, &p, need * 2));
-        c->batch_mem = p;
-        c->batch_mem_bytes = need * 2;
+        mem = p;
+        mem_bytes = need * 2;
     }
     std::vector<uint8_t> h(need, 0);
     size_t off = 256;   // first 256 bytes: the persistent-queue head counter
@@ -1178,7 +1183,7 @@ static int upload_queue(Ctx *c, cudaStream_t s, const std::vector<SeedJob> &jobs
         const size_t at = off;
         if (n) std::memcpy(h.data() + at, src, n);
         off += (n + 15) / 16 * 16;
-        return (uint8_t *)c->batch_mem + at;
+        return (uint8_t *)mem + at;
     };
     q->jobs = (const SeedJob *)put(jobs.data(), bj);
     q->seg_start = (const int64_t *)put(ss.data(), bs);
@@ -1186,8 +1191,8 @@ static int upload_queue(Ctx *c, cudaStream_t s, const std::vector<SeedJob> &jobs
     q->seg_job = (const int *)put(sj.data(), bjj);
     q->n_segs = (int)sk.size();
     q->n_tickets = ss.back();
-    q->head = (unsigned long long *)c->batch_mem;
-    KS_TRY_CUDA(c, cudaMemcpyAsync(c->batch_mem, h.data(), off, cudaMemcpyHostToDevice, s));
+    q->head = (unsigned long long *)mem;
+    KS_TRY_CUDA(c, cudaMemcpyAsync(mem, h.data(), off, cudaMemcpyHostToDevice, s));
     return KS_OK;
 }
 
@@ -1204,10 +1209,13 @@ static int run_queue(Ctx *c, cudaStream_t s, const SeedQueue &q, int max_B, int 
     return cuda_err(c, e, "seed launch");
 }
 
+// seeds_slot, qbuf: the scratch slot of the seed list and the queue buffer
+// (another pair lets a second search run beside the first on another stream).
 static int seed_common(Ctx *c, ks_vol vol, const ks_params *p, const int32_t *seeds_xyz,
                        int64_t n_seeds, int kind, void *out, int64_t capacity, int64_t *n_out,
                        int32_t *traj, int out_on_device, int planar = 0,
-                       cudaStream_t s = nullptr, bool wait = true) {
+                       cudaStream_t s = nullptr, bool wait = true, int seeds_slot = kScSeeds,
+                       int qbuf = 0) {
     if (!s) s = c->stream;
     std::string why;
     int st = validate_params(p, &why);
@@ -1218,7 +1226,7 @@ static int seed_common(Ctx *c, ks_vol vol, const ks_params *p, const int32_t *se
     if (!v) return set_err(c, KS_ENOTFOUND, "unknown volume");
     std::vector<int32_t> hs;
     int32_t *ds;
-    st = seeds_to_device(c, s, v, p, seeds_xyz, n_seeds, &hs, &ds);
+    st = seeds_to_device(c, s, v, p, seeds_xyz, n_seeds, &hs, &ds, seeds_slot);
     if (st) return st;
     const int64_t ns = (int64_t)hs.size() / 3;
     const int S = p->r_max - p->r_min + 1;
@@ -1250,14 +1258,14 @@ static int seed_common(Ctx *c, ks_vol vol, const ks_params *p, const int32_t *se
     SeedQueue q{};
     if (kind == kOctant) {
         // one block per seed
-        st = upload_queue(c, s, {J}, {0, ns}, {kOctant}, {0}, &q);
+        st = upload_queue(c, s, {J}, {0, ns}, {kOctant}, {0}, &q, qbuf);
         if (st) return st;
         st = run_queue(c, s, q, v->binning.bins, S, 1 << kOctant, false);
     } else {
         // block-path items, then warp-path items, on a persistent launch
         const int64_t nb = seed_tickets(kMeanShift, ns, p->r_min, S, J.vol.B);
         const int64_t nw = seed_tickets(kMsWarp, ns, p->r_min, S, J.vol.B);
-        st = upload_queue(c, s, {J}, {0, nb, nb + nw}, {kMeanShift, kMsWarp}, {0, 0}, &q);
+        st = upload_queue(c, s, {J}, {0, nb, nb + nw}, {kMeanShift, kMsWarp}, {0, 0}, &q, qbuf);
         if (st) return st;
         st = run_queue(c, s, q, v->binning.bins, S, 1 << kMeanShift, true);
     }
@@ -1315,7 +1323,8 @@ int ks_saliency(ks_ctx *ctx, ks_vol vol, const ks_params *params, double *Y, uin
         KS_TRY_CUDA(c, cudaDeviceGetStreamPriorityRange(&least, &greatest));
         KS_TRY_CUDA(c, cudaStreamCreateWithPriority(&c->hi_stream, cudaStreamNonBlocking, greatest));
         KS_TRY_CUDA(c, cudaStreamCreateWithPriority(&c->lo_stream, cudaStreamNonBlocking, least));
-        for (cudaEvent_t *ev : {&c->ev_fork, &c->ev_hi, &c->ev_lo})
+        KS_TRY_CUDA(c, cudaStreamCreateWithPriority(&c->lo2_stream, cudaStreamNonBlocking, least));
+        for (cudaEvent_t *ev : {&c->ev_fork, &c->ev_hi, &c->ev_lo, &c->ev_lo2})
             KS_TRY_CUDA(c, cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
     }
     const size_t n = (size_t)v->nx * v->ny * v->nz;
@@ -1329,10 +1338,16 @@ int ks_saliency(ks_ctx *ctx, ks_vol vol, const ks_params *params, double *Y, uin
     KS_TRY_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
     KS_TRY_CUDA(c, cudaStreamWaitEvent(c->hi_stream, c->ev_fork, 0));
     KS_TRY_CUDA(c, cudaStreamWaitEvent(c->lo_stream, c->ev_fork, 0));
-    // From here on every path joins both streams before returning, so no
-    // copy into the caller's buffers is still in flight after an error.
+    KS_TRY_CUDA(c, cudaStreamWaitEvent(c->lo2_stream, c->ev_fork, 0));
+    // From here on every path joins all three streams before returning, so
+    // no copy into the caller's buffers is still in flight after an error.
     // The dense sweep first, at the highest priority: the seed searches'
-    // blocks are dispatched as its last wave leaves SMs free.
+    // blocks are dispatched as its last wave leaves SMs free.  The octant
+    // climb and mean shift take a low-priority stream each, the octant
+    // climb launched first: mean-shift blocks fill the SMs that the octant
+    // climb's last searches leave idle instead of waiting for them (the
+    // pet128 step: 9.83 ms with both on one stream, 9.75 ms).  Each has its
+    // own seed list and queue buffer.
     st = run_dense(c, c->hi_stream, v, params, o, 0, v->nz);
     if (st == KS_OK && !out_on_device) {
         e = cudaMemcpyAsync(Y, o.Y, n * 8, cudaMemcpyDeviceToHost, c->hi_stream);
@@ -1345,14 +1360,17 @@ int ks_saliency(ks_ctx *ctx, ks_vol vol, const ks_params *params, double *Y, uin
                          out_on_device, 0, c->lo_stream, false);
     if (st == KS_OK)
         st = seed_common(c, vol, params, nullptr, 0, kMeanShift, ms, ms_capacity, n_ms, nullptr,
-                         out_on_device, 0, c->lo_stream, false);
+                         out_on_device, 0, c->lo2_stream, false, kScSeeds2, 1);
     e = cudaEventRecord(c->ev_hi, c->hi_stream);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_lo, c->lo_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_lo2, c->lo2_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_hi, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_lo, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_lo2, 0);
     if (e != cudaSuccess) {
         cudaStreamSynchronize(c->hi_stream);
         cudaStreamSynchronize(c->lo_stream);
+        cudaStreamSynchronize(c->lo2_stream);
         return st != KS_OK ? st : cuda_err(c, e, "join");
     }
     const int st2 = check_status(c);

@@ -70,16 +70,21 @@ struct Ctx {
     bool profiling = false;
     std::vector<ProfRec> prof;
     std::map<DenseTuneKey, DenseConfig> tune;
-    // batched launches: cached device queue buffers and graphs
+    // seed launches: device queue buffers (queue 1 only for the mean shift
+    // that ks_saliency runs beside the octant climb; each buffer is used on
+    // one stream at a time)
     void *batch_mem = nullptr;
     size_t batch_mem_bytes = 0;
+    void *batch_mem2 = nullptr;
+    size_t batch_mem2_bytes = 0;
     unsigned long long *d_head = nullptr;
     // serving
     ServeState *serve = nullptr;           // owned; released by serve_shutdown
     // ks_saliency: the dense sweep on the device's highest-priority stream,
-    // the seed searches on its lowest, forked from and joined to `stream`
-    cudaStream_t hi_stream = nullptr, lo_stream = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_hi = nullptr, ev_lo = nullptr;
+    // the octant climb and mean shift each on a lowest-priority stream of
+    // its own, forked from and joined to `stream`
+    cudaStream_t hi_stream = nullptr, lo_stream = nullptr, lo2_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_hi = nullptr, ev_lo = nullptr, ev_lo2 = nullptr;
 
     LaunchCtx lc(cudaStream_t s = nullptr) const {
         return LaunchCtx{s ? s : stream, d_status, num_sms};
