@@ -421,6 +421,21 @@ def test_meanshift_radii_across_warp_and_block_paths(ctx, ko, ks_mod):
     _ms_vs_oracle(ctx, ko, ks_mod, w)
 
 
+@pytest.mark.parametrize("B", [33, 47])
+def test_meanshift_block_only_bin_counts(ctx, ko, ks_mod, B):
+    """More than 32 bins: every mean-shift item runs on the block path, in
+    the launch compiled without the warp path (the B words at a fixed
+    offset; column sums by groups of 4 threads per bin).  Radii 18..23,
+    bins that are neither a power of two nor a multiple of 8."""
+    rng = np.random.default_rng(B)
+    vol = rng.integers(0, 8 * B, size=(28, 33, 37)).astype(np.int16)
+    vol[:, :12, :] = 8 * (B // 2)            # a flat slab beside the noise
+    w = synth.Workload("block-only", vol, {"kind": 0, "bins": B, "shift": 3, "lo": 0,
+                                           "hi": 8 * B - 1}, 18, 23, 9, 12)
+    _ms_vs_oracle(ctx, ko, ks_mod, w)
+    _oct_vs_oracle(ctx, ko, ks_mod, w)
+
+
 def test_seed_edge_cases(ctx, ko, ks_mod):
     ks = ks_mod
     # constant volume: every seed converges at once; excluded voxels only: N = 0
