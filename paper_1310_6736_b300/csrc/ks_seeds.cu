@@ -555,7 +555,16 @@ __device__ __forceinline__ void ms_walk_rows(const OffsetTables &ot, int r, cons
                 reinterpret_cast<const unsigned long long *>(a & ~uintptr_t(7));
             const int nw = (off + n + 7) >> 3;
 #pragma unroll
-            for (int k = 0; k < kBlkRowWords; ++k) wd[k] = k < nw ? __ldg(q + k) : 0ull;
+            // bytes of the first and last words outside the row count as
+            // value 0: masked here once, not per word in the walk
+            const int hl = off + n - 8 * (nw - 1);        // row bytes in the last word, 1..8
+            const unsigned long long last = hl == 8 ? ~0ull : (1ull << (8 * hl)) - 1ull;
+#pragma unroll
+            for (int k = 0; k < kBlkRowWords; ++k) {
+                unsigned long long x = k < nw ? __ldg(q + k) : 0ull;
+                if (k == 0) x &= ~0ull << (8 * off);
+                wd[k] = x & (k == nw - 1 ? last : ~0ull);
+            }
         } else {
 #pragma unroll
             for (int k = 0; k < kBlkRowWords; ++k) wd[k] = 0ull;
@@ -586,10 +595,7 @@ __device__ __forceinline__ void ms_walk_rows(const OffsetTables &ot, int r, cons
 #pragma unroll
         for (int k = 0; k < kBlkRowWords; ++k) {
             if (k >= nw_max) break;
-            const int lo = off - 8 * k, hi = off + n - 8 * k;
-            unsigned long long x = wd[k];
-            if (lo > 0) x &= ~0ull << (8 * lo);           // word 0 only: lo = off <= 7
-            if (hi < 8) x = hi > 0 ? x & ((1ull << (8 * hi)) - 1ull) : 0ull;
+            const unsigned long long x = wd[k];           // masked at fetch
             // byte b is voxel t = 8k + b - off (mod 2^32 arithmetic)
             const uint32_t a_k = row_a + ((uint32_t)(8 * k - off) << 11);
 #pragma unroll
@@ -737,7 +743,16 @@ __device__ void ms_pass_warp(const SeedJob &J, const OffsetTables &ot, unsigned 
                 reinterpret_cast<const unsigned long long *>(a & ~uintptr_t(7));
             const int nw = (off + n + 7) >> 3;
 #pragma unroll
-            for (int k = 0; k < kRowWords; ++k) wd[k] = k < nw ? __ldg(q + k) : 0ull;
+            // bytes of the first and last words outside the row count as
+            // value 0: masked here once, not per word in the walk
+            const int hl = off + n - 8 * (nw - 1);        // row bytes in the last word, 1..8
+            const unsigned long long last = hl == 8 ? ~0ull : (1ull << (8 * hl)) - 1ull;
+#pragma unroll
+            for (int k = 0; k < kRowWords; ++k) {
+                unsigned long long x = k < nw ? __ldg(q + k) : 0ull;
+                if (k == 0) x &= ~0ull << (8 * off);
+                wd[k] = x & (k == nw - 1 ? last : ~0ull);
+            }
         } else {
 #pragma unroll
             for (int k = 0; k < kRowWords; ++k) wd[k] = 0ull;
@@ -763,12 +778,7 @@ __device__ void ms_pass_warp(const SeedJob &J, const OffsetTables &ot, unsigned 
 #pragma unroll
         for (int k = 0; k < kRowWords; ++k) {
             if (k >= nw_max) break;
-            // bytes [lo, hi) of word k belong to the row; the others are
-            // zeroed and so count as value 0
-            const int lo = off - 8 * k, hi = off + n - 8 * k;
-            unsigned long long x = wd[k];
-            if (lo > 0) x &= ~0ull << (8 * lo);           // word 0 only: lo = off <= 7
-            if (hi < 8) x = hi > 0 ? x & ((1ull << (8 * hi)) - 1ull) : 0ull;
+            const unsigned long long x = wd[k];           // masked at fetch
             // byte b is voxel t = 8k + b - off (mod 2^32 arithmetic)
             const uint32_t a_k = row_a + ((uint32_t)(8 * k - off) << 11);
 #pragma unroll
