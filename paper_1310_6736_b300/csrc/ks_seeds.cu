@@ -705,22 +705,26 @@ __device__ void ms_pass(const SeedJob &J, const OffsetTables &ot, unsigned long 
     __syncthreads();
 }
 
-// Warp path: the same sums with one column per lane.  cols holds (B + 1)
-// * 64 words: words A of value v at colA[v * 32 + lane], words B at
-// colA[(B + 1 + v) * 32 + lane], value 0 (not counted, and the masked bytes
-// of a row's first and last words) never read, so a byte costs no branch;
-// acc (B * 4 ints) is written over the start once the columns have been
-// read.
+// Warp path: the same sums with one column per lane.  cols holds words A
+// of value v at colA[v * 32 + lane] and words B at colA[kMswB + v * 32 +
+// lane], v = 0..B <= 32: B words at a fixed distance from the A words for
+// every bin count, so a voxel's second reduction takes the A address plus
+// an immediate.  Value 0 (not counted, and the masked bytes of a row's
+// first and last words) is never read, so a byte costs no branch; acc (B *
+// 4 ints) is written over the start once the columns have been read.
+constexpr int kMswB = 33 * 32;    // word offset of the B words in a warp region
 __device__ void ms_pass_warp(const SeedJob &J, const OffsetTables &ot, unsigned long long *cols,
                              int *acc, const int P[3], int r) {
     const int B = J.vol.B, lane = threadIdx.x & 31;
     uint32_t *colA = reinterpret_cast<uint32_t *>(cols);
-    for (int k = lane; k < 2 * (B + 1) * 32; k += 32) colA[k] = 0u;
+    for (int k = lane; k < (B + 1) * 32; k += 32) {
+        colA[k] = 0u;
+        colA[kMswB + k] = 0u;
+    }
     __syncwarp();
     const uint8_t *c0 = voxel_ptr(J.vol, P);
     const int plane = (int)J.vol.plane, pitch = (int)J.vol.pitch;
     const uint32_t a_addr = smem_u32(colA + lane);               // value v: a_addr + 128 v
-    const uint32_t b_addr = a_addr + (uint32_t)(B + 1) * 32 * 4;
     const uint32_t *rows = ot.rows + __ldg(ot.rows_start + r);
     const int nrows = __ldg(ot.rows_start + r + 1) - __ldg(ot.rows_start + r);
     // A lane's rows are lane, lane + 32, ...: the words of the next row are
@@ -783,9 +787,11 @@ __device__ void ms_pass_warp(const SeedJob &J, const OffsetTables &ot, unsigned 
             const uint32_t a_k = row_a + ((uint32_t)(8 * k - off) << 11);
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
-                const uint32_t v = byte_of(x, b);
-                red_add_shared(a_addr + (v << 7), a_k + ((uint32_t)b << 11));
-                red_add_shared(b_addr + (v << 7), row_b);
+                const uint32_t v =
+                    __byte_perm(b < 4 ? (uint32_t)x : (uint32_t)(x >> 32), 0u, 0x4440u + (b & 3));
+                const uint32_t av = a_addr + (v << 7);
+                red_add_shared(av, a_k + ((uint32_t)b << 11));
+                red_add_shared_at<4u * kMswB>(av, row_b);
             }
         }
         e = en;
@@ -804,7 +810,7 @@ __device__ void ms_pass_warp(const SeedJob &J, const OffsetTables &ot, unsigned 
         if (b < B) {
             for (int k = 0; k < 32; ++k) {
                 const uint32_t xa = colA[(b + 1) * 32 + ((k + lane) & 31)];
-                const uint32_t xb = colA[(B + 2 + b) * 32 + ((k + lane) & 31)];
+                const uint32_t xb = colA[kMswB + (b + 1) * 32 + ((k + lane) & 31)];
                 s[h][0] += (int)(xa & 0x7ffu);
                 s[h][1] += (int)(xa >> 11);
                 s[h][2] += (int)(xb & 0xffffu);
@@ -955,7 +961,7 @@ __device__ void ms_item(const SeedJob &J, int64_t item, const OffsetTables &ot, 
     __syncthreads();
 }
 
-// One item on one warp; region is the warp's own (B + 1) * 256 bytes.
+// One item on one warp; region is the warp's own 8448 bytes.
 __device__ void ms_item_warp(const SeedJob &J, int64_t item, const OffsetTables &ot,
                              const double *T, const double *L, unsigned long long *region) {
     const int dims[3] = {J.vol.nx, J.vol.ny, J.vol.nz};
@@ -1025,10 +1031,10 @@ struct Layout {
         if ((kinds & kMsBlockOnly) && acc < 2 * (size_t)kMsBOff) acc = 2 * (size_t)kMsBOff;
         prod = acc + (size_t)B * 4 * 4;
         msb_total = prod + (size_t)4 * ((B + 7) & ~7) * 8;   // 4 chains of Bp doubles
-        // a warp region holds (B + 1) * 64 column words, later acc (16 B
-        // bytes) and 4 chains of Bp doubles: 16 B + 32 (B + 7) <= 256 (B + 1)
+        // a warp region holds 2 * 33 * 32 column words, later acc (16 B
+        // bytes) and 4 chains of Bp doubles: 16 B + 32 (B + 7) <= 8448
         msw = 0;
-        msw_stride = (size_t)(B + 1) * 256;
+        msw_stride = (size_t)kMswB * 8;             // A and B words of 33 values
         msw_total = B <= kWarpMsBmax ? msw + (kSeedThreads / 32) * msw_stride : 0;
     }
     __host__ __device__ size_t total() const {
