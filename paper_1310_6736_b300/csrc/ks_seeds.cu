@@ -839,23 +839,30 @@ __device__ void ms_delta_warp(int B, const int *acc, double *prod, int step[3]) 
     for (int b = lane; b < B; b += 32) n += (uint32_t)acc[4 * b];
     for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
     const uint32_t N = n;
-    // Empty bins (and the padding up to Bp) get products of +0.0: adding
-    // them leaves every partial sum unchanged (no sum is -0.0), so the
-    // chains below need no branch and still equal the sums over the
-    // occupied bins in bin order.
-    for (int b = lane; b < Bp; b += 32) {
+    // The products of the occupied bins, packed in bin order: an empty bin
+    // would add +0.0, which leaves every partial sum unchanged (no product
+    // and so no partial sum is -0.0), so the chains below run over the
+    // occupied bins only and still give the sums over all bins in bin
+    // order.  The packed list is padded with +0.0 to a multiple of 8.
+    int K = 0;
+    for (int b0 = 0; b0 < B; b0 += 32) {
+        const int b = b0 + lane;
         const int c = b < B ? acc[4 * b] : 0;
+        const unsigned occ = __ballot_sync(0xffffffffu, c > 0);
         if (c > 0) {
+            const int k = K + __popc(occ & ((1u << lane) - 1u));
             const double w = __dsqrt_rn(__ddiv_rn((double)N, (double)((int64_t)B * c)));
-            for (int a = 0; a < 3; ++a) prod[a * Bp + b] = __dmul_rn(w, (double)acc[4 * b + 1 + a]);
-            prod[3 * Bp + b] = __dmul_rn(w, (double)c);
-        } else {
-            for (int a = 0; a < 4; ++a) prod[a * Bp + b] = 0.0;
+            for (int a = 0; a < 3; ++a) prod[a * Bp + k] = __dmul_rn(w, (double)acc[4 * b + 1 + a]);
+            prod[3 * Bp + k] = __dmul_rn(w, (double)c);
         }
+        K += __popc(occ);
     }
+    const int Kp = (K + 7) & ~7;
+    for (int k = K + lane; k < Kp; k += 32)
+        for (int a = 0; a < 4; ++a) prod[a * Bp + k] = 0.0;
     __syncwarp();
     // lane a < 4 sums chain a (three numerators, the denominator)
-    const double s = lane < 4 ? chain_sum(prod + lane * Bp, Bp) : 0.0;
+    const double s = lane < 4 ? chain_sum(prod + lane * Bp, Kp) : 0.0;
     const double den = __shfl_sync(0xffffffffu, s, 3);
     const int d = lane < 3 && N != 0 ? (int)round(__ddiv_rn(s, den)) : 0;
     for (int a = 0; a < 3; ++a) step[a] = __shfl_sync(0xffffffffu, d, a);
