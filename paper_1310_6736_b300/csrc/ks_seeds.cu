@@ -159,10 +159,17 @@ __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *
         const uint32_t *c8 = ot.c8_rows + __ldg(ot.c8_rows_start + J.r_max);
         const int n8 = __ldg(ot.c8_rows_start + J.r_max + 1) - __ldg(ot.c8_rows_start + J.r_max);
         // two entries per round: their 16 loads are in flight together
+        // each round's two entries are loaded one round ahead, so their
+        // latency overlaps the previous round's voxel loads
+        uint32_t pe0 = threadIdx.x < n8 ? __ldg(c8 + threadIdx.x) : 0u;
+        uint32_t pe1 = threadIdx.x + blockDim.x < n8 ? __ldg(c8 + threadIdx.x + blockDim.x) : 0u;
         for (int k = threadIdx.x; k < n8; k += 2 * blockDim.x) {
             const int k2 = k + blockDim.x;
-            const uint32_t e0 = __ldg(c8 + k);
-            const uint32_t e1 = k2 < n8 ? __ldg(c8 + k2) : 0u;   // 0: the centre, v unused
+            const uint32_t e0 = pe0;
+            const uint32_t e1 = k2 < n8 ? pe1 : 0u;   // 0: the centre, v unused
+            const int kn = k + 2 * blockDim.x, kn2 = kn + blockDim.x;
+            pe0 = kn < n8 ? __ldg(c8 + kn) : 0u;
+            pe1 = kn2 < n8 ? __ldg(c8 + kn2) : 0u;
             uint32_t v[2][8], base[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -193,8 +200,10 @@ __device__ void octant_pass(const SeedJob &J, const OffsetTables &ot, uint32_t *
     // 2^z - 1.  Quadrant climb: the entries on the disk dz = 0 only.
     const uint32_t *restm = ot.restm_rows + __ldg(ot.restm_rows_start + J.r_max);
     const int nr = __ldg(ot.restm_rows_start + J.r_max + 1) - __ldg(ot.restm_rows_start + J.r_max);
+    uint32_t pf = threadIdx.x < nr ? __ldg(restm + threadIdx.x) : 0u;   // one round ahead
     for (int k = threadIdx.x; k < nr; k += blockDim.x) {
-        const uint32_t f = __ldg(restm + k);
+        const uint32_t f = pf;
+        pf = k + blockDim.x < nr ? __ldg(restm + k + blockDim.x) : 0u;
         const int X = (int)(f & 0xffu), Yb = (int)((f >> 8) & 0xffu), Zb = (int)((f >> 16) & 0xffu);
         if (J.planar && Zb != 0) continue;
         const uint32_t zm = (X == 0 ? 1u : 0u) | (Yb == 0 ? 2u : 0u) | (Zb == 0 ? 4u : 0u);
