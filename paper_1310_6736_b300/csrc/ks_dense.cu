@@ -411,6 +411,10 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
                 // the constant and in the global table, so the prefetch of
                 // entry k + 1 needs no guard)
                 uint32_t e = tab.c8(k0);
+                // four entries unrolled, their loads in flight together (the
+                // 32-bit-counter sweep of r <= 32: 84.6 -> 82.6 ms on a 64 x 128 x
+                // 128 MR crop)
+#pragma unroll 4
                 for (int k = k0; k < k1; ++k) {
                     const uint32_t en = tab.c8(k + 1);
                     // (the top byte of e is the radius class, unused here)
@@ -542,6 +546,9 @@ __global__ void __launch_bounds__(256, TM ? 2 : 1) k_dense4(const DenseArgs a) {
             for (int rho = (i == 0 ? 0 : r); rho <= r; ++rho) {
                 const int k0 = tab.c8_start(rho), k1 = tab.c8_start(rho + 1);
                 uint32_t e = tab.c8(k0);
+                // four entries unrolled: 64 loads of the next entries are issued
+                // while earlier ones are counted (7.86 -> 7.55 ms on pet128)
+#pragma unroll 4
                 for (int k = k0; k < k1; ++k) {
                     const uint32_t en = tab.c8(k + 1);
                     const int X = (int)(e & 0xffu);
