@@ -710,7 +710,10 @@ def binning_rows(ctx, ks, steps=10, warmup=3):
     volume (far above the 126 MB L2).  Per type, the ks_bin kernels'
     CUDA-event time over `steps` calls of ks_create_volume from device
     memory; the algorithmic bytes are the raw read (float32 also its min/max
-    pass) plus one byte written per voxel."""
+    pass) plus one byte written per voxel.  A fourth row times the float32
+    binning through ks_bin_f32_noalloc on the same volume: CUDA events on
+    the stream around `steps` back-to-back calls (its two kernels per call,
+    launch gaps included)."""
     import torch
     nz, ny, nx = 256, 512, 512
     n = nx * ny * nz
@@ -743,7 +746,34 @@ def binning_rows(ctx, ks, steps=10, warmup=3):
         t = ms / max(1, launches) * 1e-3
         gbs = n * bpv / t / 1e9
         rows.append({"raw": name, "voxels": n, "bytes_per_voxel": bpv, "ms": t * 1e3,
-                     "achieved_gbs": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"]})
+                     "achieved_gbs": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"],
+                     "entry": "ks_create_volume"})
+        if binning["kind"] == 1:
+            import ctypes as C
+            raw = make()
+            out = torch.empty(n, dtype=torch.uint8, device="cuda")
+            s = torch.cuda.current_stream()
+            lib = ks.lib()
+
+            def call():
+                return lib.ks_bin_f32_noalloc(C.c_void_p(raw.data_ptr()), nx, ny, nz, 32,
+                                              C.c_void_p(out.data_ptr()),
+                                              C.c_void_p(s.cuda_stream))
+            for _ in range(warmup):
+                assert call() == 0
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            for _ in range(steps):
+                assert call() == 0
+            b.record(s)
+            b.synchronize()
+            t = a.elapsed_time(b) / steps * 1e-3
+            gbs = n * bpv / t / 1e9
+            rows.append({"raw": name, "voxels": n, "bytes_per_voxel": bpv, "ms": t * 1e3,
+                         "achieved_gbs": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"],
+                         "entry": "ks_bin_f32_noalloc (no device allocation; event time "
+                                  "of back-to-back calls)"})
+            del raw, out
     return rows, f"{nx}x{ny}x{nz} random volumes", peaks["hbm_gbs"], kind
 
 
