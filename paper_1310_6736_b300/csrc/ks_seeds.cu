@@ -1,32 +1,33 @@
 // Seed-grid searches: octant hill-climbing (Sec. 2.2, Alg. 1 in 3D) and
 // mean shift towards the uniform pmf (Sec. 2.3, Eq. 4-6).
 //
-// Scheduling.  Work is handed out in tickets, one block of 256 threads per
-// ticket: an octant ticket is one seed (all its iterations plus the final
-// Kadir-Brady evaluation); a mean-shift ticket is one (seed, r) item, items
-// taken largest radius first.  The same kernel serves a plain launch (block
-// i takes ticket i) and the persistent batched launch (blocks pull tickets
-// from a device counter until the queue is empty), so an item's arithmetic
-// never depends on how it was scheduled.
+// Scheduling.  Work is handed out in tickets: an octant ticket is one seed
+// on a block of 256 threads (all its iterations plus the final Kadir-Brady
+// evaluation); a mean-shift ticket is one (seed, r) item, on a whole block
+// for radii above 20 or more than 32 bins, else on one warp, items taken
+// largest radius first.  The same kernel serves a plain launch and the
+// persistent batched launch (blocks pull tickets from a device counter until
+// the queue is empty), so an item's arithmetic never depends on how it was
+// scheduled.
 //
-// Window walk.  A pass walks Ball(r) at P row by row: each thread takes one
-// x-row (dy, dz, half-length w) at a time and streams its 2w+1 bins, which
-// are consecutive bytes, so a thread's loads mostly hit L1 and the voxel
-// offset is just the loop counter.
+// Octant pass.  The block walks the offset tables of Ball(r_max) in row
+// order, each entry standing for a set of sign mirrors.  A voxel off the
+// coordinate planes lies in exactly one open octant and costs one
+// shared-memory atomic.  A plane/axis voxel belongs to every closed octant
+// it touches and is added to each; its multiplicity minus one is recorded
+// per (shell, bin), so that the full-ball histogram is the sum of the 8
+// closed-octant histograms minus that excess.  The Kadir-Brady quantities at
+// the final centre therefore come from the last octant pass whenever the
+// climb converged (the pass ran at that centre).  A climb whose centre
+// repeats stops early (octant_item).
 //
-// Octant pass.  A voxel off the coordinate planes lies in exactly one open
-// octant and costs one shared-memory atomic.  A plane/axis voxel belongs to
-// every closed octant it touches and is added to each; its multiplicity
-// minus one is recorded per (shell, bin), so that the full-ball histogram
-// is the sum of the 8 closed-octant histograms minus that excess.  The
-// Kadir-Brady quantities at the final centre therefore come from the last
-// octant pass whenever the climb converged (the pass ran at that centre).
-//
-// Mean-shift pass.  Each thread adds one packed 64-bit word per voxel
-// (count and the three offset sums, each offset shifted by +32, in
-// disjoint bit fields whose bounds are checked below) to a column of
-// accumulators private to a few threads, with one red.shared.add.u64; the
-// columns are then summed per bin.
+// Mean-shift pass.  A thread (block path) or lane (warp path) takes whole
+// x-rows of Ball(r) and streams each as aligned 8-byte words.  Per voxel it
+// adds the count and the three offset sums, each offset shifted to be
+// non-negative, in disjoint bit fields whose bounds are checked below: two
+// 32-bit reductions (count and dx sum, then dy and dz sums), or one 64-bit
+// reduction where a column's sums need more bits, into columns private to
+// a lane or a few threads; the columns are then summed per bin.
 //
 // Every accumulated quantity is an integer, so neither the order nor the
 // grouping of accumulation can change a result; the FP64 steps run
@@ -53,33 +54,6 @@ struct SeedShared {
 
 __device__ __forceinline__ const uint8_t *voxel_ptr(const VolDesc &v, const int P[3]) {
     return v.base + (int64_t)P[2] * v.plane + (int64_t)P[1] * v.pitch + P[0];
-}
-
-// Byte b of an 8-byte word.
-__device__ __forceinline__ uint32_t byte_of(unsigned long long word, int b) {
-    const uint32_t h = b < 4 ? (uint32_t)word : (uint32_t)(word >> 32);
-    return (h >> (8 * (b & 3))) & 0xffu;
-}
-
-// Streams the 2w+1 bins starting at p with aligned 8-byte loads and calls
-// f(t, v) for the bin v at p + t (every byte masked).  The loads cover at
-// most 7 bytes before p and 7 bytes after p + 2w: with |offset| <= 32 that
-// stays inside the halo-padded allocation, which ends in 256 bytes of slack.
-template <typename F>
-__device__ __forceinline__ void walk_row_masked(const uint8_t *p, int w, F &&f) {
-    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-    const unsigned long long *q = reinterpret_cast<const unsigned long long *>(a & ~uintptr_t(7));
-    const int off = (int)(a & 7u);
-    const int n = 2 * w + 1;
-    const int nw = (off + n + 7) >> 3;
-    for (int k = 0; k < nw; ++k) {
-        const unsigned long long word = __ldg(q + k);
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const int t = k * 8 + b - off;
-            if (t >= 0 && t < n) f(t, byte_of(word, b));
-        }
-    }
 }
 
 // Entropy of counts c[0..B) (bin order), the library's fixed formula.  The
@@ -509,16 +483,6 @@ __device__ __forceinline__ void red_add_shared_u64(uint32_t addr, unsigned long 
     asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(addr), "l"(v));
 }
 
-// The packed word of voxel t of row e (dy, dz, half-length w) is the row's
-// word plus t << 11.
-__device__ __forceinline__ unsigned long long ms_row_word(uint32_t e, int *dy, int *dz, int *w) {
-    *dy = (int)(e & 0xffu) - 64;
-    *dz = (int)((e >> 8) & 0xffu) - 64;
-    *w = (int)(e >> 16);
-    return 1ull | ((unsigned long long)(32 - *w) << 11) | ((unsigned long long)(*dy + 32) << 28) |
-           ((unsigned long long)(*dz + 32) << 45);
-}
-
 // Block path: counts c_b and integer offset sums m_b of Ball(r) at P into
 // acc[b][4].  Column words are indexed by the stored value v (0..B): value
 // 0 (not counted) has its own columns, never read, so a byte costs no
@@ -563,7 +527,6 @@ __device__ __forceinline__ void ms_walk_rows(const OffsetTables &ot, int r, cons
             const unsigned long long *q =
                 reinterpret_cast<const unsigned long long *>(a & ~uintptr_t(7));
             const int nw = (off + n + 7) >> 3;
-#pragma unroll
             // bytes of the first and last words outside the row count as
             // value 0: masked here once, not per word in the walk
             const int hl = off + n - 8 * (nw - 1);        // row bytes in the last word, 1..8
@@ -755,7 +718,6 @@ __device__ void ms_pass_warp(const SeedJob &J, const OffsetTables &ot, unsigned 
             const unsigned long long *q =
                 reinterpret_cast<const unsigned long long *>(a & ~uintptr_t(7));
             const int nw = (off + n + 7) >> 3;
-#pragma unroll
             // bytes of the first and last words outside the row count as
             // value 0: masked here once, not per word in the walk
             const int hl = off + n - 8 * (nw - 1);        // row bytes in the last word, 1..8
