@@ -247,9 +247,11 @@ int ks_meanshift(ks_ctx *ctx, ks_vol vol, const ks_params *params,
  * octant climb (as ks_seed_climb, Alg. 1) and the uniform-target mean shift
  * (as ks_meanshift, Eq. 4-6) from the default seed grid.  The results are
  * those of the three separate calls, bit for bit.  The dense sweep runs on
- * the device's highest-priority stream and the seed searches on its lowest,
- * both forked from the context's stream and joined to it before return, so
- * the seed blocks fill the SMs that the dense sweep's last wave leaves free.
+ * the device's highest-priority stream, and the octant climb and mean shift
+ * each on a lowest-priority stream of its own.  All three are forked from
+ * the context's stream and joined to it before return, so the seed blocks
+ * fill the SMs that the dense sweep's last wave leaves free, and mean-shift
+ * blocks those that the octant climb's last searches leave.
  * Outputs as in the three calls (Y and s_best: nx*ny*nz each; oct: one
  * record per seed; ms: one per (seed, r)); all on the device or all on the
  * host (out_on_device).  KS_EINVAL when a capacity is too small (the
