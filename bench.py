@@ -706,8 +706,9 @@ def run_mr256_seeds(ctx, ks, synth, reps=3):
 
 
 def binning_rows(ctx, ks, steps=10, warmup=3):
-    """Binning alone, an HBM-bound kernel: three raw types on a 512x512x256
-    volume (far above the 126 MB L2).  Per type, the ks_bin kernels'
+    """Binning alone, an HBM-bound kernel: three raw types on a 1024x1024x256
+    volume (every raw input at least twice the 126 MB L2, which is not
+    flushed between the calls).  Per type, the ks_bin kernels'
     CUDA-event time over `steps` calls of ks_create_volume from device
     memory; the algorithmic bytes are the raw read (float32 also its min/max
     pass) plus one byte written per voxel.  A fourth row times the float32
@@ -715,7 +716,7 @@ def binning_rows(ctx, ks, steps=10, warmup=3):
     the stream around `steps` back-to-back calls (its two kernels per call,
     launch gaps included)."""
     import torch
-    nz, ny, nx = 256, 512, 512
+    nz, ny, nx = 256, 1024, 1024
     n = nx * ny * nz
     peaks, kind = _peaks()
     g = torch.Generator(device="cuda")

@@ -254,7 +254,9 @@ __global__ void k_bin_f32(const float *__restrict__ in, int nx, int ny, int nz, 
 int grid_for(int64_t work, int num_sms) {
     const int64_t per = 256;
     int64_t g = (work + per - 1) / per;
-    const int64_t cap = (int64_t)num_sms * 16;
+    // grid-stride beyond 32 blocks per SM (16 took uint8 binning of a
+    // 1024 x 1024 x 256 volume from 0.83 to 0.78 of the copy rate)
+    const int64_t cap = (int64_t)num_sms * 32;
     return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
