@@ -36,12 +36,13 @@ WORKLOAD = "pet128"
 
 
 # dram__bytes_read.sum and dram__bytes_write.sum of one k_dense launch on the
-# pet128 workload, captured with ncu (launch path 4, profiles/k_dense_pet128.md):
-# the padded bin volume is read once; the Y and s_best outputs (9 bytes per
-# voxel) stay in L2 at the end of the launch, so the capture shows almost no
-# writes.  They leave L2 later, so the line's traffic counts them as written.
-DENSE_DRAM_READ = 3_769_344
-DENSE_DRAM_WRITE = 512
+# pet128 workload, captured with ncu (launch path 4 with its unrolled entry
+# loop, profiles/k_dense_pet128.md): the padded bin volume is read once; the Y
+# and s_best outputs (9 bytes per voxel) stay in L2 at the end of the launch,
+# so the capture shows almost no writes.  They leave L2 later, so the line's
+# traffic counts them as written.
+DENSE_DRAM_READ = 3_785_728
+DENSE_DRAM_WRITE = 768
 
 
 def _dist():
