@@ -37,12 +37,13 @@ WORKLOAD = "pet128"
 
 # dram__bytes_read.sum and dram__bytes_write.sum of one k_dense launch on the
 # pet128 workload, captured with ncu (launch path 4 with its unrolled entry
-# loop, profiles/k_dense_pet128.md): the padded bin volume is read once; the Y
+# loop, 4 warps in 4x1 rows, the autotuner's shape; profiles/k_dense_pet128.md):
+# the padded bin volume is read once; the Y
 # and s_best outputs (9 bytes per voxel) stay in L2 at the end of the launch,
 # so the capture shows almost no writes.  They leave L2 later, so the line's
 # traffic counts them as written.
-DENSE_DRAM_READ = 3_785_728
-DENSE_DRAM_WRITE = 768
+DENSE_DRAM_READ = 3_784_448
+DENSE_DRAM_WRITE = 512
 
 
 def _dist():
