@@ -202,6 +202,102 @@ __device__ __forceinline__ void tm_store_prev(uint32_t ta, const uint32_t (&v)[N
 }
 __host__ __device__ constexpr int tm_columns(int warps) { return 128 * ((warps + 3) / 4); }
 
+// Launch path 6 (r_max > 25): the previous-scale counts of a lane's centre,
+// bins 1..NW (NW = 16, 32 or 64 words, 32-bit), in NW consecutive columns
+// from ta.  As above, a load waits for its data in the same asm statement.
+template <int NW>
+__device__ __forceinline__ void tm_load_words(uint32_t ta, uint32_t (&v)[NW]);
+template <int NW>
+__device__ __forceinline__ void tm_store_words(uint32_t ta, const uint32_t (&v)[NW]);
+#define KS_R16(o) "=r"(v[o + 0]), "=r"(v[o + 1]), "=r"(v[o + 2]), "=r"(v[o + 3]), "=r"(v[o + 4]), \
+    "=r"(v[o + 5]), "=r"(v[o + 6]), "=r"(v[o + 7]), "=r"(v[o + 8]), "=r"(v[o + 9]),           \
+    "=r"(v[o + 10]), "=r"(v[o + 11]), "=r"(v[o + 12]), "=r"(v[o + 13]), "=r"(v[o + 14]),      \
+    "=r"(v[o + 15])
+#define KS_W16(o) "r"(v[o + 0]), "r"(v[o + 1]), "r"(v[o + 2]), "r"(v[o + 3]), "r"(v[o + 4]),   \
+    "r"(v[o + 5]), "r"(v[o + 6]), "r"(v[o + 7]), "r"(v[o + 8]), "r"(v[o + 9]), "r"(v[o + 10]),  \
+    "r"(v[o + 11]), "r"(v[o + 12]), "r"(v[o + 13]), "r"(v[o + 14]), "r"(v[o + 15])
+template <>
+__device__ __forceinline__ void tm_load_words<16>(uint32_t ta, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : KS_R16(0)
+        : "r"(ta)
+        : "memory");
+}
+template <>
+__device__ __forceinline__ void tm_load_words<32>(uint32_t ta, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, "
+        "%25, %26, %27, %28, %29, %30, %31}, [%33];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : KS_R16(0), KS_R16(16)
+        : "r"(ta), "r"(ta + 16u)
+        : "memory");
+}
+template <>
+__device__ __forceinline__ void tm_load_words<64>(uint32_t ta, uint32_t (&v)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%64];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, "
+        "%25, %26, %27, %28, %29, %30, %31}, [%65];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, "
+        "%41, %42, %43, %44, %45, %46, %47}, [%66];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48, %49, %50, %51, %52, %53, %54, %55, %56, "
+        "%57, %58, %59, %60, %61, %62, %63}, [%67];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : KS_R16(0), KS_R16(16), KS_R16(32), KS_R16(48)
+        : "r"(ta), "r"(ta + 16u), "r"(ta + 32u), "r"(ta + 48u)
+        : "memory");
+}
+template <>
+__device__ __forceinline__ void tm_store_words<16>(uint32_t ta, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16};"
+        ::"r"(ta), KS_W16(0)
+        : "memory");
+}
+template <>
+__device__ __forceinline__ void tm_store_words<32>(uint32_t ta, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%1], {%18, %19, %20, %21, %22, %23, %24, %25, "
+        "%26, %27, %28, %29, %30, %31, %32, %33};"
+        ::"r"(ta), "r"(ta + 16u), KS_W16(0), KS_W16(16)
+        : "memory");
+}
+template <>
+__device__ __forceinline__ void tm_store_words<64>(uint32_t ta, const uint32_t (&v)[64]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%4, %5, %6, %7, %8, %9, %10, %11, %12, "
+        "%13, %14, %15, %16, %17, %18, %19};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%1], {%20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31, %32, %33, %34, %35};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%2], {%36, %37, %38, %39, %40, %41, %42, %43, "
+        "%44, %45, %46, %47, %48, %49, %50, %51};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%3], {%52, %53, %54, %55, %56, %57, %58, %59, "
+        "%60, %61, %62, %63, %64, %65, %66, %67};"
+        ::"r"(ta), "r"(ta + 16u), "r"(ta + 32u), "r"(ta + 48u), KS_W16(0), KS_W16(16), KS_W16(32),
+          KS_W16(48)
+        : "memory");
+}
+#undef KS_R16
+#undef KS_W16
+// TMEM columns a launch path 6 block allocates: NW per group of four warps,
+// rounded up to a power of two of at least 32 (tcgen05.alloc's rule).
+__host__ __device__ constexpr int tm_columns_wide(int warps, int NW) {
+    int c = NW * ((warps + 3) / 4);
+    int p = 32;
+    while (p < c) p <<= 1;
+    return p;
+}
+
 // Shared-memory words of one lane.  Counters: one word per stored value
 // v = 0..B.  When every count fits in 16 bits (|Ball(r_max)| <= 65535, i.e.
 // r_max <= 25) two centres of a lane share each word (centre j in bits
@@ -263,7 +359,20 @@ __device__ __forceinline__ void scale_step(const DenseArgs &a, uint32_t cnt_lane
         const int64_t d = (int64_t)c * st.nm1 - (int64_t)p * N;
         D += (uint64_t)(d < 0 ? -d : d);
     };
-    if constexpr (WIDE) {
+    if constexpr (WIDE && TM) {
+        // launch path 6: the previous counts of bins 1..B in TMEM
+        uint32_t pv[B];
+        __syncwarp();                      // tcgen05 loads and stores are warp-wide
+        tm_load_words<B>(tprev, pv);
+#pragma unroll
+        for (int vv = 1; vv <= B; ++vv) {
+            const uint32_t c = count(vv);
+            term(c, pv[vv - 1]);
+            pv[vv - 1] = c;
+        }
+        __syncwarp();
+        tm_store_words<B>(tprev, pv);
+    } else if constexpr (WIDE) {
 #pragma unroll
         for (int vv = 1; vv <= B; ++vv) {
             const uint32_t c = count(vv);
@@ -321,18 +430,34 @@ __device__ __forceinline__ void scale_step(const DenseArgs &a, uint32_t cnt_lane
     st.dm1 = D;
 }
 
-template <int B, bool WIDE, int PATH, int CPL>
+// TM (launch path 6: PATH 1, one centre per lane, r_max > 25, 16, 32 or 64
+// bins): each centre's previous-scale counts in B TMEM columns instead of
+// shared memory, so a warp needs half the shared memory.  A block of 4, 8
+// or 16 warps allocates tm_columns_wide(warps, B) columns; warp w owns the
+// lane quarter w & 3 of columns B (w >> 2) .. + B - 1.
+template <int B, bool WIDE, int PATH, int CPL, bool TM = false>
 __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
     k_dense(const DenseArgs a, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ int s_ok;
-    using Wd = Words<B, WIDE, CPL>;
+    __shared__ uint32_t s_tmem;
+    static_assert(!TM || (WIDE && PATH == 1 && CPL == 1 && (B == 16 || B == 32 || B == 64)),
+                  "launch path 6: path 1, one centre per lane, 16, 32 or 64 bins, r_max > 25");
+    using Wd = Words<B, WIDE, CPL, TM>;
     constexpr bool CTAB = !WIDE;                 // r_max <= 25: table in constant memory
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int tx0 = blockIdx.x * 32 * CPL, ty0 = blockIdx.y * a.ty, tz0 = a.z0 + blockIdx.z * a.tz;
     const int R = a.r_max;
+    uint32_t tm_base = 0u;
+    if constexpr (TM) {
+        if (warp == 0) tm_alloc(smem_u32(&s_tmem), (uint32_t)tm_columns_wide(nwarps, B));
+        tm_fence_before();
+        __syncthreads();
+        tm_fence_after();
+        tm_base = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(B * (warp >> 2));
+    }
 
     Src<PATH> src;
     int pz, py;
@@ -395,6 +520,14 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
 
 #pragma unroll 4
         for (int w = 0; w < Wd::kPerLane; ++w) st_shared_u32(word(w), 0u);
+        if constexpr (TM) {
+            uint32_t z[B];
+#pragma unroll
+            for (int w = 0; w < B; ++w) z[w] = 0u;
+            __syncwarp();
+            tm_wait_st();                  // the previous row's last stores
+            tm_store_words<B>(tm_base, z);
+        }
 
         ScaleState st[CPL];
 #pragma unroll
@@ -449,10 +582,14 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
                 }
             }
             // ---- exact per-scale quantities from each centre's counters
+            if constexpr (TM) {
+                __syncwarp();
+                tm_wait_st();              // the previous scale's stores
+            }
 #pragma unroll
             for (int j = 0; j < CPL; ++j)
-                scale_step<B, WIDE, CPL>(a, cnt_lane, j, i, r, st[j], orow + cx + 32 * j,
-                                         cx + 32 * j < a.vol.nx);
+                scale_step<B, WIDE, CPL, TM>(a, cnt_lane, j, i, r, st[j], orow + cx + 32 * j,
+                                             cx + 32 * j < a.vol.nx, tm_base);
         }
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
@@ -462,6 +599,13 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
                 a.out.s[orow + cxj] = (uint8_t)st[j].sb;
             }
         }
+    }
+    if constexpr (TM) {
+        tm_wait_st();
+        tm_fence_before();
+        __syncthreads();
+        tm_fence_after();
+        if (warp == 0) tm_dealloc(s_tmem, (uint32_t)tm_columns_wide(nwarps, B));
     }
 }
 
@@ -904,7 +1048,9 @@ struct Geometry {
     size_t brick, cnt_off, cnt_bytes, mbar_off, total;
 };
 
-int centres_per_lane(const DenseConfig &c) { return c.path >= 3 ? 4 : (c.path == 2 ? 2 : 1); }
+int centres_per_lane(const DenseConfig &c) {
+    return c.path == 6 ? 1 : (c.path >= 3 ? 4 : (c.path == 2 ? 2 : 1));
+}
 
 Geometry geometry(const DenseConfig &c, int B_, int r_max) {
     Geometry g{};
@@ -913,7 +1059,7 @@ Geometry geometry(const DenseConfig &c, int B_, int r_max) {
     const int cpl = centres_per_lane(c);
     const bool wide = is_wide(r_max);
     const int words = (cpl >= 2 && !wide ? cpl / 2 : cpl) * (B + 1) +
-                      (c.path == 4 ? 0 : cpl * (wide ? B + 1 : (B + 2) / 2));
+                      (c.path == 4 || c.path == 6 ? 0 : cpl * (wide ? B + 1 : (B + 2) / 2));
     g.padx = (r_max + 15) / 16 * 16;
     g.bx = (g.padx + 32 + r_max + 15) / 16 * 16;
     g.by = c.ty + 2 * r_max;
@@ -937,6 +1083,33 @@ cudaError_t launch_t(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap 
               (a.z1 - a.z0 + a.tz - 1) / a.tz);
     CUtensorMap dummy{};
     kern<<<grid, cfg.warps * 32, smem, lc.stream>>>(a, tmap ? *tmap : dummy);
+    return cudaGetLastError();
+}
+
+// Launch path 6: path 1 with the previous counts in TMEM.  The dynamic
+// shared memory is padded until the blocks that fit on an SM hold at most
+// its 512 TMEM columns, so no tcgen05.alloc waits for another block's.
+template <int B>
+cudaError_t launch_t_tm(const LaunchCtx &lc, const DenseArgs &a, const DenseConfig &cfg,
+                        size_t smem) {
+    auto kern = k_dense<B, true, 1, 1, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int limit = 512 / tm_columns_wide(cfg.warps, B);
+    for (;;) {
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, cfg.warps * 32, smem);
+        if (e != cudaSuccess) return e;
+        if (nb <= limit) break;
+        smem += 1024;
+        if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((a.vol.nx + 31) / 32, (a.vol.ny + a.ty - 1) / a.ty, (a.z1 - a.z0 + a.tz - 1) / a.tz);
+    CUtensorMap dummy{};
+    kern<<<grid, cfg.warps * 32, smem, lc.stream>>>(a, dummy);
     return cudaGetLastError();
 }
 
@@ -983,6 +1156,11 @@ cudaError_t launch_b(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap 
             k_dense_slide<B><<<grid, 32, sm, lc.stream>>>(a);
             return cudaGetLastError();
         }
+        return cudaErrorInvalidValue;
+    }
+    if (cfg.path == 6) {
+        if constexpr (B == 16 || B == 32 || B == 64)
+            return wide ? launch_t_tm<B>(lc, a, cfg, smem) : cudaErrorInvalidValue;
         return cudaErrorInvalidValue;
     }
     if (cfg.path == 3) return wide ? cudaErrorInvalidValue : launch_adj4<B, false>(lc, a, cfg, smem);
@@ -1132,6 +1310,14 @@ bool dense_config_fits(const DenseConfig &c, int B, int r_max) {
         return !is_wide(r_max) && (template_bins(B) == 16 || template_bins(B) == 32) &&
                c.warps == 1 && c.ty == 1 && c.tz >= 1 && c.tz <= 1024 &&
                slide_smem_bytes(B, r_max + 1) + 1024 <= 227 * 1024;
+    if (c.path == 6) {
+        // whole warpgroups (each warp its TMEM lane quarter), 16, 32 or 64
+        // bins, only where the counts need 32 bits
+        const int tb = template_bins(B);
+        if (!is_wide(r_max) || (tb != 16 && tb != 32 && tb != 64)) return false;
+        if ((c.warps != 4 && c.warps != 8 && c.warps != 16) || c.ty * c.tz != c.warps) return false;
+        return geometry(c, B, r_max).total + 1024 <= 227 * 1024;
+    }
     if (c.path < 0 || c.path > 4) return false;
     if (c.path >= 3 && is_wide(r_max)) return false;      // counts need 16-bit packing
     if (c.path == 4 && template_bins(B) != 16 && template_bins(B) != 32) return false;

@@ -164,6 +164,33 @@ def test_dense_random_volumes(ctx, ko, ks_mod, case, path):
         ks.force_dense_config(-1)
 
 
+@pytest.mark.parametrize("case", [
+    ((41, 9, 6), 16, 20, 27, (6, 4, 4, 1)),     # 16 bins, ragged x tile
+    ((37, 8, 8), 40, 24, 30, (6, 8, 4, 2)),     # 40 bins (64-bin template), 8 warps
+    ((66, 5, 4), 64, 26, 32, (6, 4, 2, 2)),     # 64 bins, r_max = 32, two x tiles
+    ((35, 12, 5), 33, 22, 28, (6, 16, 4, 4)),   # 16 warps: 4 TMEM column groups
+])
+def test_dense_wide_tmem_path(ctx, ko, ks_mod, case):
+    """Launch path 6 (r_max > 25): the 32-bit previous-scale counts in TMEM.
+    Every H, W, Y and s_best of random volumes equals the oracle's.  Each
+    forced shape fits the path (r_max > 25, a 16-, 32- or 64-bin template,
+    4, 8 or 16 warps), so it is the one that runs."""
+    ks = ks_mod
+    dims, B, r_min, r_max, cfg = case
+    nx, ny, nz = dims
+    rng = np.random.default_rng(B * 5 + r_max)
+    vol = rng.choice([40, 41, 90], size=(nz, ny, nx), p=[0.6, 0.3, 0.1]).astype(np.int16)
+    blob = rng.random((nz, ny, nx)) < 0.3
+    vol[blob] = rng.integers(0, 2048, size=int(blob.sum()))
+    shift = max(0, int(np.ceil(np.log2(2048 / B))))
+    binning = {"kind": 2, "bins": B, "shift": shift, "lo": 30, "hi": min(2047, (B << shift) - 1)}
+    try:
+        ks.force_dense_config(*cfg)
+        _dense_vs_oracle(ctx, ko, ks, vol, binning, r_min, r_max)
+    finally:
+        ks.force_dense_config(-1)
+
+
 def test_host_out_into_pinned_arrays_equals_default_outputs(ctx, ks_mod):
     """The end-to-end path: the raw volume in pinned host memory and every
     result written into caller-owned pinned arrays gives the same records and
