@@ -477,17 +477,21 @@ def _grid_subset(w, step):
 def run_case(args):
     """Run one part of the step (for profilers): --case dense|octant|meanshift|bin.
     --seed-step n: every n-th grid seed only (seed cases); --workload: the
-    synthetic workload (default pet128)."""
+    synthetic workload (default pet128); --max-dim m: its corner crop of at
+    most m voxels per axis."""
     import torch
     from paper_1310_6736_b300 import build, ks, synth
     build.build()
     if args.dense_config:
         ks.force_dense_config(*[int(x) for x in args.dense_config.split(",")])
     w = synth.workload(args.workload)
-    nz, ny, nx = w.volume.shape
+    vol = w.volume
+    if args.max_dim:                      # a corner crop (smaller profiler captures)
+        vol = np.ascontiguousarray(vol[:args.max_dim, :args.max_dim, :args.max_dim])
+    nz, ny, nx = vol.shape
     params = ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter)
     ctx = ks.Context()
-    raw_dev = torch.from_numpy(w.volume).cuda()
+    raw_dev = torch.from_numpy(vol).cuda()
     Y = torch.empty((nz, ny, nx), dtype=torch.float64, device="cuda")
     sb = torch.empty((nz, ny, nx), dtype=torch.uint8, device="cuda")
     v = ctx.create_volume(raw_dev, w.binning)
@@ -510,7 +514,8 @@ def run_case(args):
         torch.cuda.synchronize()
         if i >= args.warmup:
             t.append(time.perf_counter() - t0)
-    print(json.dumps({"case": args.case, "workload": args.workload, "ms": [1e3 * x for x in t],
+    print(json.dumps({"case": args.case, "workload": args.workload, "shape": [nz, ny, nx],
+                      "ms": [1e3 * x for x in t],
                       "dense_config": ctx.dense_config(w.binning["bins"], w.r_max)}), flush=True)
     ctx.close()
     return 0

@@ -430,19 +430,22 @@ __device__ __forceinline__ void scale_step(const DenseArgs &a, uint32_t cnt_lane
     st.dm1 = D;
 }
 
-// TM (launch path 6: PATH 1, one centre per lane, r_max > 25, 16, 32 or 64
-// bins): each centre's previous-scale counts in B TMEM columns instead of
-// shared memory, so a warp needs half the shared memory.  A block of 4, 8
-// or 16 warps allocates tm_columns_wide(warps, B) columns; warp w owns the
-// lane quarter w & 3 of columns B (w >> 2) .. + B - 1.
+// TM (launch paths 6 and 7: PATH 1 with one or two centres per lane, r_max >
+// 25, 16, 32 or 64 bins): each centre's previous-scale counts in B TMEM
+// columns instead of shared memory, so a warp needs half the shared memory.
+// A block of 4, 8 or 16 warps allocates tm_columns_wide(warps, CPL B)
+// columns; warp w owns the lane quarter w & 3 of columns CPL B (w >> 2) ..
+// + CPL B - 1, centre j the B of them from CPL B (w >> 2) + j B.
 template <int B, bool WIDE, int PATH, int CPL, bool TM = false>
 __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
     k_dense(const DenseArgs a, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ int s_ok;
     __shared__ uint32_t s_tmem;
-    static_assert(!TM || (WIDE && PATH == 1 && CPL == 1 && (B == 16 || B == 32 || B == 64)),
-                  "launch path 6: path 1, one centre per lane, 16, 32 or 64 bins, r_max > 25");
+    static_assert(!TM || (WIDE && PATH == 1 && (CPL == 1 || CPL == 2) &&
+                          (B == 16 || B == 32 || B == 64)),
+                  "launch paths 6 and 7: path 1, one or two centres per lane, 16, 32 or 64 "
+                  "bins, r_max > 25");
     using Wd = Words<B, WIDE, CPL, TM>;
     constexpr bool CTAB = !WIDE;                 // r_max <= 25: table in constant memory
     const int lane = threadIdx.x & 31;
@@ -452,11 +455,11 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
     const int R = a.r_max;
     uint32_t tm_base = 0u;
     if constexpr (TM) {
-        if (warp == 0) tm_alloc(smem_u32(&s_tmem), (uint32_t)tm_columns_wide(nwarps, B));
+        if (warp == 0) tm_alloc(smem_u32(&s_tmem), (uint32_t)tm_columns_wide(nwarps, CPL * B));
         tm_fence_before();
         __syncthreads();
         tm_fence_after();
-        tm_base = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(B * (warp >> 2));
+        tm_base = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(CPL * B * (warp >> 2));
     }
 
     Src<PATH> src;
@@ -526,7 +529,8 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
             for (int w = 0; w < B; ++w) z[w] = 0u;
             __syncwarp();
             tm_wait_st();                  // the previous row's last stores
-            tm_store_words<B>(tm_base, z);
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) tm_store_words<B>(tm_base + (uint32_t)(j * B), z);
         }
 
         ScaleState st[CPL];
@@ -589,7 +593,7 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
 #pragma unroll
             for (int j = 0; j < CPL; ++j)
                 scale_step<B, WIDE, CPL, TM>(a, cnt_lane, j, i, r, st[j], orow + cx + 32 * j,
-                                             cx + 32 * j < a.vol.nx, tm_base);
+                                             cx + 32 * j < a.vol.nx, tm_base + (uint32_t)(j * B));
         }
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
@@ -605,7 +609,7 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
         tm_fence_before();
         __syncthreads();
         tm_fence_after();
-        if (warp == 0) tm_dealloc(s_tmem, (uint32_t)tm_columns_wide(nwarps, B));
+        if (warp == 0) tm_dealloc(s_tmem, (uint32_t)tm_columns_wide(nwarps, CPL * B));
     }
 }
 
@@ -1049,7 +1053,7 @@ struct Geometry {
 };
 
 int centres_per_lane(const DenseConfig &c) {
-    return c.path == 6 ? 1 : (c.path >= 3 ? 4 : (c.path == 2 ? 2 : 1));
+    return c.path == 6 ? 1 : c.path == 7 ? 2 : (c.path >= 3 ? 4 : (c.path == 2 ? 2 : 1));
 }
 
 Geometry geometry(const DenseConfig &c, int B_, int r_max) {
@@ -1059,7 +1063,7 @@ Geometry geometry(const DenseConfig &c, int B_, int r_max) {
     const int cpl = centres_per_lane(c);
     const bool wide = is_wide(r_max);
     const int words = (cpl >= 2 && !wide ? cpl / 2 : cpl) * (B + 1) +
-                      (c.path == 4 || c.path == 6 ? 0 : cpl * (wide ? B + 1 : (B + 2) / 2));
+                      (c.path == 4 || c.path >= 6 ? 0 : cpl * (wide ? B + 1 : (B + 2) / 2));
     g.padx = (r_max + 15) / 16 * 16;
     g.bx = (g.padx + 32 + r_max + 15) / 16 * 16;
     g.by = c.ty + 2 * r_max;
@@ -1086,17 +1090,18 @@ cudaError_t launch_t(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap 
     return cudaGetLastError();
 }
 
-// Launch path 6: path 1 with the previous counts in TMEM.  The dynamic
-// shared memory is padded until the blocks that fit on an SM hold at most
-// its 512 TMEM columns, so no tcgen05.alloc waits for another block's.
-template <int B>
+// Launch paths 6 and 7: path 1 with one (6) or two (7) centres per lane and
+// the previous counts in TMEM.  The dynamic shared memory is padded until
+// the blocks that fit on an SM hold at most its 512 TMEM columns, so no
+// tcgen05.alloc waits for another block's.
+template <int B, int CPL>
 cudaError_t launch_t_tm(const LaunchCtx &lc, const DenseArgs &a, const DenseConfig &cfg,
                         size_t smem) {
-    auto kern = k_dense<B, true, 1, 1, true>;
+    auto kern = k_dense<B, true, 1, CPL, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    const int limit = 512 / tm_columns_wide(cfg.warps, B);
+    const int limit = 512 / tm_columns_wide(cfg.warps, CPL * B);
     for (;;) {
         int nb = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, cfg.warps * 32, smem);
@@ -1107,7 +1112,8 @@ cudaError_t launch_t_tm(const LaunchCtx &lc, const DenseArgs &a, const DenseConf
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid((a.vol.nx + 31) / 32, (a.vol.ny + a.ty - 1) / a.ty, (a.z1 - a.z0 + a.tz - 1) / a.tz);
+    dim3 grid((a.vol.nx + 32 * CPL - 1) / (32 * CPL), (a.vol.ny + a.ty - 1) / a.ty,
+              (a.z1 - a.z0 + a.tz - 1) / a.tz);
     CUtensorMap dummy{};
     kern<<<grid, cfg.warps * 32, smem, lc.stream>>>(a, dummy);
     return cudaGetLastError();
@@ -1158,9 +1164,12 @@ cudaError_t launch_b(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap 
         }
         return cudaErrorInvalidValue;
     }
-    if (cfg.path == 6) {
-        if constexpr (B == 16 || B == 32 || B == 64)
-            return wide ? launch_t_tm<B>(lc, a, cfg, smem) : cudaErrorInvalidValue;
+    if (cfg.path == 6 || cfg.path == 7) {
+        if constexpr (B == 16 || B == 32 || B == 64) {
+            if (!wide) return cudaErrorInvalidValue;
+            return cfg.path == 6 ? launch_t_tm<B, 1>(lc, a, cfg, smem)
+                                 : launch_t_tm<B, 2>(lc, a, cfg, smem);
+        }
         return cudaErrorInvalidValue;
     }
     if (cfg.path == 3) return wide ? cudaErrorInvalidValue : launch_adj4<B, false>(lc, a, cfg, smem);
@@ -1310,12 +1319,15 @@ bool dense_config_fits(const DenseConfig &c, int B, int r_max) {
         return !is_wide(r_max) && (template_bins(B) == 16 || template_bins(B) == 32) &&
                c.warps == 1 && c.ty == 1 && c.tz >= 1 && c.tz <= 1024 &&
                slide_smem_bytes(B, r_max + 1) + 1024 <= 227 * 1024;
-    if (c.path == 6) {
+    if (c.path == 6 || c.path == 7) {
         // whole warpgroups (each warp its TMEM lane quarter), 16, 32 or 64
-        // bins, only where the counts need 32 bits
+        // bins, only where the counts need 32 bits; two centres per lane
+        // (path 7) allow at most 8 warps (the kernel's launch bounds)
         const int tb = template_bins(B);
         if (!is_wide(r_max) || (tb != 16 && tb != 32 && tb != 64)) return false;
-        if ((c.warps != 4 && c.warps != 8 && c.warps != 16) || c.ty * c.tz != c.warps) return false;
+        if ((c.warps != 4 && c.warps != 8 && (c.warps != 16 || c.path == 7)) ||
+            c.ty * c.tz != c.warps)
+            return false;
         return geometry(c, B, r_max).total + 1024 <= 227 * 1024;
     }
     if (c.path < 0 || c.path > 4) return false;

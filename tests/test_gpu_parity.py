@@ -169,12 +169,17 @@ def test_dense_random_volumes(ctx, ko, ks_mod, case, path):
     ((37, 8, 8), 40, 24, 30, (6, 8, 4, 2)),     # 40 bins (64-bin template), 8 warps
     ((66, 5, 4), 64, 26, 32, (6, 4, 2, 2)),     # 64 bins, r_max = 32, two x tiles
     ((35, 12, 5), 33, 22, 28, (6, 16, 4, 4)),   # 16 warps: 4 TMEM column groups
+    ((41, 9, 6), 16, 20, 27, (7, 4, 4, 1)),     # two centres per lane, one ragged x tile
+    ((70, 5, 4), 64, 26, 32, (7, 4, 2, 2)),     # 64 bins, r_max = 32, a 6-centre second tile
+    ((37, 8, 8), 40, 24, 30, (7, 8, 4, 2)),     # 8 warps: 2 TMEM column groups of 128
+    ((130, 3, 3), 32, 25, 26, (7, 8, 2, 4)),    # 32 bins, three x tiles
 ])
 def test_dense_wide_tmem_path(ctx, ko, ks_mod, case):
-    """Launch path 6 (r_max > 25): the 32-bit previous-scale counts in TMEM.
-    Every H, W, Y and s_best of random volumes equals the oracle's.  Each
-    forced shape fits the path (r_max > 25, a 16-, 32- or 64-bin template,
-    4, 8 or 16 warps), so it is the one that runs."""
+    """Launch paths 6 and 7 (r_max > 25): the 32-bit previous-scale counts
+    in TMEM, one or two centres per lane.  Every H, W, Y and s_best of random
+    volumes equals the oracle's.  Each forced shape fits its path (r_max >
+    25, a 16-, 32- or 64-bin template, 4, 8 or 16 warps, at most 8 for path
+    7), so it is the one that runs."""
     ks = ks_mod
     dims, B, r_min, r_max, cfg = case
     nx, ny, nz = dims
