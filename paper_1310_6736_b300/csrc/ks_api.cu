@@ -504,7 +504,7 @@ static std::vector<DenseConfig> dense_candidates(int B, int r_max) {
     std::vector<DenseConfig> out;
     const int shapes[][3] = {{1, 1, 1}, {2, 2, 1}, {2, 1, 2}, {4, 4, 1}, {4, 2, 2}, {8, 8, 1}, {8, 4, 2}, {8, 2, 4},
                              {16, 16, 1}, {16, 4, 4}, {16, 8, 2}, {16, 2, 8}};
-    for (int path : {0, 1, 2, 3, 4, 6, 7})
+    for (int path : {0, 1, 2, 3, 4, 6, 7, 8})
         for (auto &s : shapes) {
             DenseConfig c{path, s[0], s[1], s[2]};
             if (dense_config_fits(c, B, r_max)) out.push_back(c);
@@ -1752,10 +1752,10 @@ int ks_force_dense_config(int path, int warps, int ty, int tz) {
     }
     if (path == 5) {
         if (warps != 1 || ty != 1 || tz < 1 || tz > 1024) return KS_EINVAL;
-    } else if (path == 6 || path == 7) {
-        if ((warps != 4 && warps != 8 && (warps != 16 || path == 7)) || ty * tz != warps)
+    } else if (path >= 6 && path <= 8) {
+        if ((warps != 4 && warps != 8 && (warps != 16 || path != 6)) || ty * tz != warps)
             return KS_EINVAL;
-    } else if (path > 7 || warps < 1 || warps > (path >= 2 ? 8 : 16) || ty * tz != warps) {
+    } else if (path > 8 || warps < 1 || warps > (path >= 2 ? 8 : 16) || ty * tz != warps) {
         return KS_EINVAL;
     }
     g_forced_path = path;

@@ -305,9 +305,21 @@ __host__ __device__ constexpr int tm_columns_wide(int warps, int NW) {
 // 1 << 16 (j & 1)); otherwise each centre has its own 32-bit column.  After
 // the counters come the previous scale's counts of each centre: 16-bit
 // pairs (values 2w, 2w+1 in word w) when they fit, 32-bit words otherwise.
-template <int B, bool WIDE, int CPL, bool TM = false>
+//
+// WRAP (launch path 8, r_max > 25, previous counts in TMEM): the two centres
+// of a lane share a word although a count may pass 65 535.  The word is
+// x = L + 2^16 H modulo 2^32 (L, H the exact counts of centres 0 and 1 since
+// the row start; a low half that wraps carries into the high half), so
+// L mod 2^16 = x mod 2^16 and, once L is known, H mod 2^16 = (x - L) >> 16.
+// The scale step recovers each exact count from its 16-bit residue and the
+// exact previous count: c = p + ((c16 - p) mod 2^16), which holds while no
+// bin gains 65 536 or more between two recoveries.  A shell adds at most
+// 12 578 voxels (r = 32); the first scale is recovered once at rho =
+// kWrapFold (|Ball(25)| = 65 267) when r_min is larger, after which shells
+// 26..31 add at most 59 220.
+template <int B, bool WIDE, int CPL, bool TM = false, bool WRAP = false>
 struct Words {
-    static constexpr bool kPack = CPL >= 2 && !WIDE;
+    static constexpr bool kPack = CPL >= 2 && (!WIDE || WRAP);
     static constexpr int kNW = B + 1;                          // counter words per column
     static constexpr int kNP = WIDE ? B + 1 : (B + 2) / 2;     // previous words per centre
     static constexpr int kCols = kPack ? CPL / 2 : CPL;        // counter columns
@@ -326,30 +338,53 @@ struct Words {
 };
 
 // Running state of one centre over the scales: H at scale index i-1 and
-// i-2, N at i-1 and i-2, D at i-1, and the best Y and its scale so far.
+// i-2, N at i-1 and i-2, D at i-1, and the best Y and its scale so far;
+// with WRAP also the exact count of value 0 at the last recovery.
 struct ScaleState {
     double hm1, hm2, yb;
     uint32_t nm1, nm2;
     uint64_t dm1;
     int sb;
+    uint32_t c0;
 };
+
+constexpr int kWrapFold = 25;             // |Ball(25)| = 65267 < 2^16
+static_assert(kRmax <= 32, "WRAP recovery bounds assume r <= 32");
+
+// WRAP: the exact count of value v from its 16-bit half c16 and the exact
+// count p at the last recovery.
+__device__ __forceinline__ uint32_t wrap_count(uint32_t c16, uint32_t p) {
+    return p + ((c16 - p) & 0xffffu);
+}
 
 // After the shell of scale r (index i): the centre's exact N, the bin-order
 // entropy sum, D against the previous scale's counts (refreshed in the same
 // pass), H, the peak test at scale r - 1 and the optional H/W outputs.
 // With TM the previous counts are the NP words at TMEM address tprev.
-template <int B, bool WIDE, int CPL, bool TM = false>
+// WRAP: tlow and low_c0 are the low-half centre's exact counts (its TMEM
+// columns, already refreshed for this scale, and its value-0 count), used
+// by the high-half centre (j odd).
+template <int B, bool WIDE, int CPL, bool TM = false, bool WRAP = false>
 __device__ __forceinline__ void scale_step(const DenseArgs &a, uint32_t cnt_lane, int j, int i,
                                            int r, ScaleState &st, int64_t oidx, bool live,
-                                           uint32_t tprev = 0u) {
-    using Wd = Words<B, WIDE, CPL, TM>;
+                                           uint32_t tprev = 0u, uint32_t tlow = 0u,
+                                           uint32_t low_c0 = 0u) {
+    using Wd = Words<B, WIDE, CPL, TM, WRAP>;
     constexpr int NP = Wd::kNP;
     auto word = [&](int w) { return cnt_lane + ((uint32_t)w << 7); };
     auto count = [&](int v) -> uint32_t {
         const uint32_t x = ld_shared_u32(word(Wd::cnt(j, v)));
         return Wd::kPack ? (x >> (16 * (j & 1))) & 0xffffu : x;
     };
-    const uint32_t N = (uint32_t)__ldg(a.ot.ball_size + r) - count(0);
+    uint32_t c0;
+    if constexpr (WRAP) {
+        const uint32_t x = ld_shared_u32(word(Wd::cnt(j, 0)));
+        c0 = wrap_count((j & 1) ? (x - low_c0) >> 16 : x & 0xffffu, st.c0);
+        st.c0 = c0;
+    } else {
+        c0 = count(0);
+    }
+    const uint32_t N = (uint32_t)__ldg(a.ot.ball_size + r) - c0;
     double ssum = 0.0;
     int occ = 0;
     uint64_t D = 0;
@@ -359,8 +394,28 @@ __device__ __forceinline__ void scale_step(const DenseArgs &a, uint32_t cnt_lane
         const int64_t d = (int64_t)c * st.nm1 - (int64_t)p * N;
         D += (uint64_t)(d < 0 ? -d : d);
     };
-    if constexpr (WIDE && TM) {
-        // launch path 6: the previous counts of bins 1..B in TMEM
+    if constexpr (WIDE && TM && WRAP) {
+        // launch path 8: 16 bins at a time (the high half also needs the
+        // low-half centre's exact counts, whose stores must have landed)
+        if (j & 1) tm_wait_st();
+#pragma unroll
+        for (int k0 = 0; k0 < B; k0 += 16) {
+            uint32_t pv[16], lv[16];
+            __syncwarp();                  // tcgen05 loads and stores are warp-wide
+            tm_load_words<16>(tprev + (uint32_t)k0, pv);
+            if (j & 1) tm_load_words<16>(tlow + (uint32_t)k0, lv);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const uint32_t x = ld_shared_u32(word(Wd::cnt(j, k0 + t + 1)));
+                const uint32_t c = wrap_count((j & 1) ? (x - lv[t]) >> 16 : x & 0xffffu, pv[t]);
+                term(c, pv[t]);
+                pv[t] = c;
+            }
+            __syncwarp();
+            tm_store_words<16>(tprev + (uint32_t)k0, pv);
+        }
+    } else if constexpr (WIDE && TM) {
+        // launch paths 6 and 7: the previous counts of bins 1..B in TMEM
         uint32_t pv[B];
         __syncwarp();                      // tcgen05 loads and stores are warp-wide
         tm_load_words<B>(tprev, pv);
@@ -430,13 +485,44 @@ __device__ __forceinline__ void scale_step(const DenseArgs &a, uint32_t cnt_lane
     st.dm1 = D;
 }
 
+// WRAP: the recovery of scale_step without a scale (the first scale's
+// counts at rho = kWrapFold when r_min is larger): the exact counts become
+// the reference of the next recovery.  As in scale_step, the high-half
+// centre (j odd) uses the low-half centre's freshly recovered counts at
+// tlow and low_c0.
+template <int B, int CPL>
+__device__ __forceinline__ void wrap_fold(uint32_t cnt_lane, int j, ScaleState &st,
+                                          uint32_t tprev, uint32_t tlow, uint32_t low_c0) {
+    using Wd = Words<B, true, CPL, true, true>;
+    auto word = [&](int v) { return ld_shared_u32(cnt_lane + ((uint32_t)Wd::cnt(j, v) << 7)); };
+    const uint32_t x0 = word(0);
+    st.c0 = wrap_count((j & 1) ? (x0 - low_c0) >> 16 : x0 & 0xffffu, st.c0);
+    if (j & 1) tm_wait_st();
+#pragma unroll
+    for (int k0 = 0; k0 < B; k0 += 16) {
+        uint32_t pv[16], lv[16];
+        __syncwarp();
+        tm_load_words<16>(tprev + (uint32_t)k0, pv);
+        if (j & 1) tm_load_words<16>(tlow + (uint32_t)k0, lv);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const uint32_t x = word(k0 + t + 1);
+            pv[t] = wrap_count((j & 1) ? (x - lv[t]) >> 16 : x & 0xffffu, pv[t]);
+        }
+        __syncwarp();
+        tm_store_words<16>(tprev + (uint32_t)k0, pv);
+    }
+}
+
 // TM (launch paths 6 and 7: PATH 1 with one or two centres per lane, r_max >
 // 25, 16, 32 or 64 bins): each centre's previous-scale counts in B TMEM
 // columns instead of shared memory, so a warp needs half the shared memory.
 // A block of 4, 8 or 16 warps allocates tm_columns_wide(warps, CPL B)
 // columns; warp w owns the lane quarter w & 3 of columns CPL B (w >> 2) ..
-// + CPL B - 1, centre j the B of them from CPL B (w >> 2) + j B.
-template <int B, bool WIDE, int PATH, int CPL, bool TM = false>
+// + CPL B - 1, centre j the B of them from CPL B (w >> 2) + j B.  WRAP
+// (launch path 8): path 7 with the two centres' counters in 16-bit halves of
+// one column (Words), so a warp needs half the shared memory again.
+template <int B, bool WIDE, int PATH, int CPL, bool TM = false, bool WRAP = false>
 __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
     k_dense(const DenseArgs a, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -446,7 +532,8 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
                           (B == 16 || B == 32 || B == 64)),
                   "launch paths 6 and 7: path 1, one or two centres per lane, 16, 32 or 64 "
                   "bins, r_max > 25");
-    using Wd = Words<B, WIDE, CPL, TM>;
+    static_assert(!WRAP || (TM && CPL == 2), "launch path 8: path 7 with 16-bit counters");
+    using Wd = Words<B, WIDE, CPL, TM, WRAP>;
     constexpr bool CTAB = !WIDE;                 // r_max <= 25: table in constant memory
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -470,7 +557,7 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
         // aligned and the tensor map 64-byte aligned: checked once per block,
         // reported instead of issuing a copy that would fault
         if (((smem_u32(smem) & 127u) | (mbar & 7u) |
-             ((uint32_t)reinterpret_cast<uintptr_t>(&tmap) & 63u)) != 0u) {
+             (uint32_t)(reinterpret_cast<uintptr_t>(&tmap) & 63u)) != 0u) {
             if (threadIdx.x == 0) atomicOr(a.status, kStatusMisaligned);
             return;
         }
@@ -584,6 +671,16 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
 #pragma unroll
                     for (int j = 0; j < CPL; ++j) red_add_shared(word(Wd::cnt(j, v[j])), Wd::inc(j));
                 }
+                if constexpr (WRAP) {
+                    if (i == 0 && rho == kWrapFold && r > kWrapFold) {
+                        __syncwarp();
+                        tm_wait_st();      // the row start's stores
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j)
+                            wrap_fold<B, CPL>(cnt_lane, j, st[j], tm_base + (uint32_t)(j * B),
+                                              tm_base + (uint32_t)((j ^ 1) * B), st[j ^ 1].c0);
+                    }
+                }
             }
             // ---- exact per-scale quantities from each centre's counters
             if constexpr (TM) {
@@ -592,8 +689,9 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
             }
 #pragma unroll
             for (int j = 0; j < CPL; ++j)
-                scale_step<B, WIDE, CPL, TM>(a, cnt_lane, j, i, r, st[j], orow + cx + 32 * j,
-                                             cx + 32 * j < a.vol.nx, tm_base + (uint32_t)(j * B));
+                scale_step<B, WIDE, CPL, TM, WRAP>(a, cnt_lane, j, i, r, st[j], orow + cx + 32 * j,
+                                                   cx + 32 * j < a.vol.nx, tm_base + (uint32_t)(j * B),
+                                                   tm_base + (uint32_t)((j ^ 1) * B), st[j ^ 1].c0);
         }
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
@@ -1053,7 +1151,7 @@ struct Geometry {
 };
 
 int centres_per_lane(const DenseConfig &c) {
-    return c.path == 6 ? 1 : c.path == 7 ? 2 : (c.path >= 3 ? 4 : (c.path == 2 ? 2 : 1));
+    return c.path == 6 ? 1 : c.path >= 7 ? 2 : (c.path >= 3 ? 4 : (c.path == 2 ? 2 : 1));
 }
 
 Geometry geometry(const DenseConfig &c, int B_, int r_max) {
@@ -1062,7 +1160,7 @@ Geometry geometry(const DenseConfig &c, int B_, int r_max) {
     // counter columns + previous-scale counts per lane (layout of Words)
     const int cpl = centres_per_lane(c);
     const bool wide = is_wide(r_max);
-    const int words = (cpl >= 2 && !wide ? cpl / 2 : cpl) * (B + 1) +
+    const int words = (cpl >= 2 && (!wide || c.path == 8) ? cpl / 2 : cpl) * (B + 1) +
                       (c.path == 4 || c.path >= 6 ? 0 : cpl * (wide ? B + 1 : (B + 2) / 2));
     g.padx = (r_max + 15) / 16 * 16;
     g.bx = (g.padx + 32 + r_max + 15) / 16 * 16;
@@ -1090,14 +1188,14 @@ cudaError_t launch_t(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap 
     return cudaGetLastError();
 }
 
-// Launch paths 6 and 7: path 1 with one (6) or two (7) centres per lane and
-// the previous counts in TMEM.  The dynamic shared memory is padded until
+// Launch paths 6 to 8: path 1 with one (6) or two (7, 8: 16-bit wrapping
+// counters) centres per lane and the previous counts in TMEM.  The dynamic shared memory is padded until
 // the blocks that fit on an SM hold at most its 512 TMEM columns, so no
 // tcgen05.alloc waits for another block's.
-template <int B, int CPL>
+template <int B, int CPL, bool WRAP = false>
 cudaError_t launch_t_tm(const LaunchCtx &lc, const DenseArgs &a, const DenseConfig &cfg,
                         size_t smem) {
-    auto kern = k_dense<B, true, 1, CPL, true>;
+    auto kern = k_dense<B, true, 1, CPL, true, WRAP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -1164,11 +1262,12 @@ cudaError_t launch_b(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap 
         }
         return cudaErrorInvalidValue;
     }
-    if (cfg.path == 6 || cfg.path == 7) {
+    if (cfg.path >= 6 && cfg.path <= 8) {
         if constexpr (B == 16 || B == 32 || B == 64) {
             if (!wide) return cudaErrorInvalidValue;
-            return cfg.path == 6 ? launch_t_tm<B, 1>(lc, a, cfg, smem)
-                                 : launch_t_tm<B, 2>(lc, a, cfg, smem);
+            return cfg.path == 6   ? launch_t_tm<B, 1>(lc, a, cfg, smem)
+                   : cfg.path == 7 ? launch_t_tm<B, 2>(lc, a, cfg, smem)
+                                   : launch_t_tm<B, 2, true>(lc, a, cfg, smem);
         }
         return cudaErrorInvalidValue;
     }
@@ -1319,13 +1418,13 @@ bool dense_config_fits(const DenseConfig &c, int B, int r_max) {
         return !is_wide(r_max) && (template_bins(B) == 16 || template_bins(B) == 32) &&
                c.warps == 1 && c.ty == 1 && c.tz >= 1 && c.tz <= 1024 &&
                slide_smem_bytes(B, r_max + 1) + 1024 <= 227 * 1024;
-    if (c.path == 6 || c.path == 7) {
+    if (c.path >= 6 && c.path <= 8) {
         // whole warpgroups (each warp its TMEM lane quarter), 16, 32 or 64
         // bins, only where the counts need 32 bits; two centres per lane
-        // (path 7) allow at most 8 warps (the kernel's launch bounds)
+        // (paths 7 and 8) allow at most 8 warps (the kernel's launch bounds)
         const int tb = template_bins(B);
         if (!is_wide(r_max) || (tb != 16 && tb != 32 && tb != 64)) return false;
-        if ((c.warps != 4 && c.warps != 8 && (c.warps != 16 || c.path == 7)) ||
+        if ((c.warps != 4 && c.warps != 8 && (c.warps != 16 || c.path != 6)) ||
             c.ty * c.tz != c.warps)
             return false;
         return geometry(c, B, r_max).total + 1024 <= 227 * 1024;

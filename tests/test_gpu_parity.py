@@ -173,13 +173,18 @@ def test_dense_random_volumes(ctx, ko, ks_mod, case, path):
     ((70, 5, 4), 64, 26, 32, (7, 4, 2, 2)),     # 64 bins, r_max = 32, a 6-centre second tile
     ((37, 8, 8), 40, 24, 30, (7, 8, 4, 2)),     # 8 warps: 2 TMEM column groups of 128
     ((130, 3, 3), 32, 25, 26, (7, 8, 2, 4)),    # 32 bins, three x tiles
+    ((41, 9, 6), 16, 20, 27, (8, 4, 4, 1)),     # 16-bit wrapping counters, one ragged x tile
+    ((70, 5, 4), 64, 26, 32, (8, 4, 2, 2)),     # r_min > 25: the first scale recovered at 25
+    ((37, 8, 8), 40, 31, 32, (8, 8, 4, 2)),     # r_min = 31: 59 220 voxels after the recovery
+    ((130, 3, 3), 32, 4, 32, (8, 4, 4, 1)),     # every scale from 4 to 32
 ])
 def test_dense_wide_tmem_path(ctx, ko, ks_mod, case):
-    """Launch paths 6 and 7 (r_max > 25): the 32-bit previous-scale counts
-    in TMEM, one or two centres per lane.  Every H, W, Y and s_best of random
-    volumes equals the oracle's.  Each forced shape fits its path (r_max >
-    25, a 16-, 32- or 64-bin template, 4, 8 or 16 warps, at most 8 for path
-    7), so it is the one that runs."""
+    """Launch paths 6 to 8 (r_max > 25): the 32-bit previous-scale counts
+    in TMEM, one or two centres per lane (path 8: 16-bit counters modulo
+    2^16, recovered from the previous counts).  Every H, W, Y and s_best of
+    random volumes equals the oracle's.  Each forced shape fits its path
+    (r_max > 25, a 16-, 32- or 64-bin template, 4, 8 or 16 warps, at most 8
+    for paths 7 and 8), so it is the one that runs."""
     ks = ks_mod
     dims, B, r_min, r_max, cfg = case
     nx, ny, nz = dims
@@ -194,6 +199,46 @@ def test_dense_wide_tmem_path(ctx, ko, ks_mod, case):
         _dense_vs_oracle(ctx, ko, ks, vol, binning, r_min, r_max)
     finally:
         ks.force_dense_config(-1)
+
+
+def test_dense_wrap_counts_past_16_bits(ctx, ko, ks_mod):
+    """Launch path 8 counts modulo 2^16: on a 72^3 volume that is 95% one
+    value, a centre's Ball(32) holds about 130 000 voxels of one bin, so the
+    counts wrap twice.  H, W, Y and s_best equal path 7's (32-bit counters)
+    everywhere and the oracle's at sampled centres, the middle ones (whole
+    balls inside the volume) included."""
+    ks = ks_mod
+    rng = np.random.default_rng(72)
+    n = 72
+    vol = np.full((n, n, n), 700, np.int16)
+    noise = rng.random((n, n, n)) < 0.05
+    vol[noise] = rng.integers(0, 2048, size=int(noise.sum()))
+    binning = {"kind": 2, "bins": 64, "shift": 5, "lo": 0, "hi": 2047}
+    p = ks.make_params(4, 32, 8, 20)
+    out = {}
+    for path in (7, 8):
+        try:
+            ks.force_dense_config(path, 4, 4, 1)
+            v = ctx.create_volume(vol, binning)
+            out[path] = ctx.dense_saliency(v, p, vol.shape, want_hw=True)
+            ctx.release_volume(v)
+        finally:
+            ks.force_dense_config(-1)
+    for a7, a8 in zip(out[7], out[8]):
+        assert np.array_equal(a7, a8)
+    Y, s, H, W = out[8]
+    cen = np.concatenate([np.array([[36, 36, 36], [35, 37, 36], [32, 32, 39], [39, 39, 32]]),
+                          rng.integers(0, n, size=(60, 3))]).astype(np.int32)
+    b = ko.bin_volume(vol, binning)
+    Yo, so, Ho, Wo = ko.dense(b, 64, 4, 32, centres=cen, want_hw=True)
+    x, y, z = cen[:, 0], cen[:, 1], cen[:, 2]
+    flat = (z * n + y) * n + x
+    assert np.array_equal(s[z, y, x], so)
+    close(Y[z, y, x], Yo)
+    close(H[flat], Ho)
+    close(W[flat], Wo)
+    # the middle centres' dominant bin passed 2^17 at r = 32
+    assert int((b[4:69, 4:69, 4:69] == b[36, 36, 36]).sum()) > 2 * 65536
 
 
 def test_host_out_into_pinned_arrays_equals_default_outputs(ctx, ks_mod):
