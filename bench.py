@@ -444,6 +444,7 @@ def run_ks(args):
         line["config"]["abmsod"] = abmsod_summary(ctx, ks, w, params)
         # the metric's other configurations at their stated sizes
         line["config"]["mr256_seeds"] = run_mr256_seeds(ctx, ks, synth)
+        line["config"]["mr256_dense"] = run_mr256_dense(ctx, ks, synth, smem_peak)
         rows, what, hbm, kind = binning_rows(ctx, ks)
         line["config"]["binning"] = {"workload": what, "peak_hbm_gbs": hbm, "rows": rows,
                                      "min_frac_of_hbm": min(r["frac_of_hbm"] for r in rows)}
@@ -710,6 +711,38 @@ def run_mr256_seeds(ctx, ks, synth, reps=3):
             "window_entropies": oct_we + ms_we,
             "window_entropies_per_s": (oct_we + ms_we) / ((t_o + t_m) * 1e-3),
             "volumes_per_s": 1e3 / (t_o + t_m), "device_records_equal_host": bool(same)}
+
+
+def run_mr256_dense(ctx, ks, synth, smem_peak, reps=2):
+    """The dense sweep of the MR-shaped volume (256x256x160 int16, 64 bins,
+    r = 4..32), whose counts pass 16 bits: the wide launch paths.  The first
+    call autotunes; then `reps` calls with the L2 flushed before each, the
+    dense kernel's CUDA-event time.  Updates = centres x |Ball(r_max)|."""
+    import torch
+    w = synth.workload("mr256")
+    params = ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter)
+    nz, ny, nx = w.volume.shape
+    v = ctx.create_volume(w.volume, w.binning)
+    Y = torch.empty((nz, ny, nx), dtype=torch.float64, device="cuda")
+    sb = torch.empty((nz, ny, nx), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ctx.dense_saliency(v, params, (nz, ny, nx), out=(Y, sb))
+    ctx.set_profiling(True)
+    for _ in range(reps):
+        flush.zero_()
+        ctx.dense_saliency(v, params, (nz, ny, nx), out=(Y, sb))
+    k_ms, k_n = ctx.kernel_time("ks_dense")
+    ctx.set_profiling(False)
+    ctx.release_volume(v)
+    ms = k_ms / max(k_n, 1)
+    centres = nx * ny * nz
+    upd = centres * ks_ball_size(w.r_max)
+    S = w.r_max - w.r_min + 1
+    return {"workload": "mr256: 256x256x160 int16 MR-shaped, 64 bins, r = 4..32, every voxel",
+            "launch": ctx.dense_config(w.binning["bins"], w.r_max), "kernel_ms": ms,
+            "updates_per_launch": upd, "achieved_gupdates_s": upd / (ms * 1e-3) / 1e9,
+            "frac_of_smem_peak": upd / (ms * 1e-3) / smem_peak,
+            "window_entropies_per_s": centres * S / (ms * 1e-3)}
 
 
 def binning_rows(ctx, ks, steps=10, warmup=3):
