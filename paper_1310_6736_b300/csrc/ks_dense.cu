@@ -593,9 +593,12 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
     auto word = [&](int w) { return cnt_lane + ((uint32_t)w << 7); };
     const int nrows = a.ty * a.tz;
 
-    for (int row = warp; row < nrows; row += nwarps) {
+    // One row of the tile with CE centres per lane (CE = CPL, or 1 in a
+    // tile whose second centres x + 32 all lie past nx: then they are not
+    // computed at all).
+    auto sweep_row = [&](int row, auto ce) {
+        constexpr int CE = decltype(ce)::value;
         const int cy = ty0 + row % a.ty, cz = tz0 + row / a.ty;
-        if (cy >= a.vol.ny || cz >= a.z1) continue;              // warp-uniform
         // Lane centres cx + 32 j.  The source address of centre j is the
         // centre-0 address plus 32 j (an immediate); centres past nx are
         // computed but not written.
@@ -606,7 +609,7 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
             c0 = (cz - tz0 + R) * pz + (cy - ty0 + R) * py + (a.padx + lane);
         else
             c0 = a.vol.base + (int64_t)cz * a.vol.plane + (int64_t)cy * a.vol.pitch +
-                 (CPL == 1 && cx >= a.vol.nx ? a.vol.nx - 1 : cx);
+                 (CE == 1 && cx >= a.vol.nx ? a.vol.nx - 1 : cx);
 
 #pragma unroll 4
         for (int w = 0; w < Wd::kPerLane; ++w) st_shared_u32(word(w), 0u);
@@ -617,12 +620,12 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
             __syncwarp();
             tm_wait_st();                  // the previous row's last stores
 #pragma unroll
-            for (int j = 0; j < CPL; ++j) tm_store_words<B>(tm_base + (uint32_t)(j * B), z);
+            for (int j = 0; j < CE; ++j) tm_store_words<B>(tm_base + (uint32_t)(j * B), z);
         }
 
-        ScaleState st[CPL];
+        ScaleState st[CE];
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) st[j] = ScaleState{0.0, 0.0, 0.0, 0u, 0u, 0ull, 0};
+        for (int j = 0; j < CE; ++j) st[j] = ScaleState{0.0, 0.0, 0.0, 0u, 0u, 0ull, 0};
         const int64_t orow = ((int64_t)cz * a.vol.ny + cy) * a.vol.nx;
 
         for (int i = 0; i < a.S; ++i) {
@@ -647,15 +650,15 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
                     const int Z = (int)((e >> 16) & 0xffu) * pz;
                     const int o[8] = {Z + Y + X, Z + Y - X, Z - Y + X, Z - Y - X,
                                       Y - Z + X, Y - Z - X, -Z - Y + X, -Z - Y - X};
-                    uint32_t v[8][CPL];
+                    uint32_t v[8][CE];
 #pragma unroll
                     for (int m = 0; m < 8; ++m)
 #pragma unroll
-                        for (int j = 0; j < CPL; ++j) v[m][j] = src.at(c0, o[m] + 32 * j);
+                        for (int j = 0; j < CE; ++j) v[m][j] = src.at(c0, o[m] + 32 * j);
 #pragma unroll
                     for (int m = 0; m < 8; ++m)
 #pragma unroll
-                        for (int j = 0; j < CPL; ++j)
+                        for (int j = 0; j < CE; ++j)
                             red_add_shared(word(Wd::cnt(j, v[m][j])), Wd::inc(j));
                     e = en;
                 }
@@ -665,20 +668,21 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
                     const uint32_t f = tab.rest(k);
                     const int off = ((int)((f >> 16) & 0xffu) - 64) * pz +
                                     ((int)((f >> 8) & 0xffu) - 64) * py + ((int)(f & 0xffu) - 64);
-                    uint32_t v[CPL];
+                    uint32_t v[CE];
 #pragma unroll
-                    for (int j = 0; j < CPL; ++j) v[j] = src.at(c0, off + 32 * j);
+                    for (int j = 0; j < CE; ++j) v[j] = src.at(c0, off + 32 * j);
 #pragma unroll
-                    for (int j = 0; j < CPL; ++j) red_add_shared(word(Wd::cnt(j, v[j])), Wd::inc(j));
+                    for (int j = 0; j < CE; ++j) red_add_shared(word(Wd::cnt(j, v[j])), Wd::inc(j));
                 }
                 if constexpr (WRAP) {
                     if (i == 0 && rho == kWrapFold && r > kWrapFold) {
                         __syncwarp();
                         tm_wait_st();      // the row start's stores
 #pragma unroll
-                        for (int j = 0; j < CPL; ++j)
+                        for (int j = 0; j < CE; ++j)
                             wrap_fold<B, CPL>(cnt_lane, j, st[j], tm_base + (uint32_t)(j * B),
-                                              tm_base + (uint32_t)((j ^ 1) * B), st[j ^ 1].c0);
+                                              tm_base + (uint32_t)((j ^ 1) * B),
+                                              st[(j ^ 1) & (CE - 1)].c0);
                     }
                 }
             }
@@ -688,19 +692,29 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
                 tm_wait_st();              // the previous scale's stores
             }
 #pragma unroll
-            for (int j = 0; j < CPL; ++j)
+            for (int j = 0; j < CE; ++j)
                 scale_step<B, WIDE, CPL, TM, WRAP>(a, cnt_lane, j, i, r, st[j], orow + cx + 32 * j,
                                                    cx + 32 * j < a.vol.nx, tm_base + (uint32_t)(j * B),
-                                                   tm_base + (uint32_t)((j ^ 1) * B), st[j ^ 1].c0);
+                                                   tm_base + (uint32_t)((j ^ 1) * B),
+                                                   st[(j ^ 1) & (CE - 1)].c0);
         }
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) {
+        for (int j = 0; j < CE; ++j) {
             const int cxj = cx + 32 * j;
             if (cxj < a.vol.nx) {
                 a.out.Y[orow + cxj] = st[j].yb;
                 a.out.s[orow + cxj] = (uint8_t)st[j].sb;
             }
         }
+    };
+    // second centres past nx in the whole tile: one centre per lane
+    const bool single = CPL == 2 && tx0 + 32 >= a.vol.nx;
+    for (int row = warp; row < nrows; row += nwarps) {
+        if (ty0 + row % a.ty >= a.vol.ny || tz0 + row / a.ty >= a.z1) continue;   // warp-uniform
+        if (single)
+            sweep_row(row, std::integral_constant<int, 1>{});
+        else
+            sweep_row(row, std::integral_constant<int, CPL>{});
     }
     if constexpr (TM) {
         tm_wait_st();
