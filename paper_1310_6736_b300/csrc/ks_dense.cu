@@ -1202,6 +1202,31 @@ cudaError_t launch_t(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap 
     return cudaGetLastError();
 }
 
+// An upper bound of the blocks of `kern` that an SM can hold with `threads`
+// threads and `dyn` bytes of dynamic shared memory: the register file, the
+// whole shared memory (whatever carveout the driver picks), the thread and
+// block limits.  cudaOccupancyMaxActiveBlocksPerMultiprocessor is not used
+// here: for the TMEM kernels it reports 1 block per SM (it assumes a smaller
+// shared-memory carveout) while 4 are resident.
+cudaError_t max_resident_blocks(const void *kern, int threads, size_t dyn, int *out) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    int dev = 0, regs = 0, smem = 0, thr = 0, blk = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) ||
+        (e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) ||
+        (e = cudaDeviceGetAttribute(&thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev)) ||
+        (e = cudaDeviceGetAttribute(&blk, cudaDevAttrMaxBlocksPerMultiprocessor, dev)))
+        return e;
+    int n = std::min(blk, thr / threads);
+    if (fa.numRegs > 0) n = std::min(n, regs / (fa.numRegs * threads));
+    const size_t per_block = dyn + fa.sharedSizeBytes;
+    if (per_block > 0) n = std::min(n, (int)((size_t)smem / per_block));
+    *out = n;
+    return cudaSuccess;
+}
+
 // Launch paths 6 to 8: path 1 with one (6) or two (7, 8: 16-bit wrapping
 // counters) centres per lane and the previous counts in TMEM.  The dynamic shared memory is padded until
 // the blocks that fit on an SM hold at most its 512 TMEM columns, so no
@@ -1216,7 +1241,7 @@ cudaError_t launch_t_tm(const LaunchCtx &lc, const DenseArgs &a, const DenseConf
     const int limit = 512 / tm_columns_wide(cfg.warps, CPL * B);
     for (;;) {
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, cfg.warps * 32, smem);
+        e = max_resident_blocks(reinterpret_cast<const void *>(kern), cfg.warps * 32, smem, &nb);
         if (e != cudaSuccess) return e;
         if (nb <= limit) break;
         smem += 1024;
@@ -1245,7 +1270,8 @@ cudaError_t launch_adj4(const LaunchCtx &lc, const DenseArgs &a, const DenseConf
         const int limit = 512 / tm_columns(cfg.warps);
         for (;;) {
             int nb = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, cfg.warps * 32, smem);
+            e = max_resident_blocks(reinterpret_cast<const void *>(kern), cfg.warps * 32, smem,
+                                    &nb);
             if (e != cudaSuccess) return e;
             if (nb <= limit) break;
             smem += 1024;
