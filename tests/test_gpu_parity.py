@@ -145,8 +145,11 @@ def test_dense_spheres48_full_volume(ctx, ko, ks_mod, cfg):
     ((70, 3, 2), 16, 2, 12, 0),      # thin slab, radius larger than the volume
     ((75, 6, 4), 8, 24, 28, 0),      # r_max > 25: global offset table, 32-bit previous counts
 ])
-@pytest.mark.parametrize("path", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("path", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 def test_dense_random_volumes(ctx, ko, ks_mod, case, path):
+    """Every launch path forced on random volumes (a shape that does not fit
+    the path, e.g. paths 6 to 8 below r_max = 26, falls back to the
+    autotuner)."""
     ks = ks_mod
     dims, B, r_min, r_max, wn = case
     nx, ny, nz = dims
