@@ -204,6 +204,40 @@ def test_dense_wide_tmem_path(ctx, ko, ks_mod, case):
         ks.force_dense_config(-1)
 
 
+def test_dense_mr256_full_volume_sampled(ctx, ko, ks_mod):
+    """The MR-shaped volume at full size (256x256x160 int16, 64 bins, r =
+    4..32), as the serving loop sweeps it: the autotuned wide launch gives
+    the same Y and s_best as launch path 6 everywhere, and the oracle's at
+    sampled centres (corners, x-tile edges and random ones)."""
+    ks = ks_mod
+    w = synth.workload("mr256")
+    p = _params(ks, w)
+    nz, ny, nx = w.volume.shape
+    v = ctx.create_volume(w.volume, w.binning)
+    Y, s = ctx.dense_saliency(v, p, (nz, ny, nx))
+    try:
+        ks.force_dense_config(6, 4, 2, 2)
+        Y6, s6 = ctx.dense_saliency(v, p, (nz, ny, nx))
+    finally:
+        ks.force_dense_config(-1)
+    ctx.release_volume(v)
+    assert np.array_equal(s, s6) and np.array_equal(Y.view(np.uint64), Y6.view(np.uint64))
+    rng = np.random.default_rng(256)
+    n = 240
+    cen = np.stack([rng.integers(0, nx, n), rng.integers(0, ny, n), rng.integers(0, nz, n)],
+                   1).astype(np.int32)
+    edges = [[0, 0, 0], [nx - 1, ny - 1, nz - 1], [31, 7, 80], [32, 7, 80], [63, 100, 3],
+             [64, 100, 3], [95, 128, 159], [96, 128, 159], [127, 255, 0], [128, 0, 77],
+             [200, 130, 79], [255, 131, 80]]
+    cen = np.concatenate([np.array(edges, np.int32), cen])
+    Yo, so = ko.dense(ko.bin_volume(w.volume, w.binning), w.binning["bins"], w.r_min, w.r_max,
+                      centres=cen)
+    x, y, z = cen[:, 0], cen[:, 1], cen[:, 2]
+    assert np.array_equal(s[z, y, x], so)
+    close(Y[z, y, x], Yo)
+    assert int((so > 0).sum()) > n // 4       # peaks in scale were found
+
+
 def test_dense_wrap_counts_past_16_bits(ctx, ko, ks_mod):
     """Launch path 8 counts modulo 2^16: on a 72^3 volume that is 95% one
     value, a centre's Ball(32) holds about 130 000 voxels of one bin, so the
