@@ -14,12 +14,19 @@
 //            so one table decode and one address serve two loads that differ
 //            by an immediate.  Centres past nx are evaluated (their reads stay
 //            inside the zeroed halo and the allocation's slack) but not
-//            written.
+//            written; a tile whose second centres all lie past nx walks one
+//            centre per lane.
 //   PATH 3 = (launch path 3, r_max <= 25) four adjacent centres per lane,
 //            128 per warp, whose four bins per offset come from two aligned
 //            32-bit loads and a funnel shift (k_dense4).
 //   PATH 4 = (launch path 4, 16 or 32 bins, r_max <= 25) PATH 3 with the
 //            previous-scale counts in tensor memory (k_dense4<B, true>).
+//   launch path 5 = one histogram per scale slid along z (k_dense_slide).
+//   launch paths 6 to 8 (r_max > 25; 16, 32 or 64 template bins) = PATH 1
+//            with the previous-scale counts as 32-bit words in tensor memory:
+//            one centre per lane (6), two (7), or two sharing each counter
+//            word as 16-bit halves counted modulo 2^16 and recovered exactly
+//            from the previous counts (8, WRAP).
 //   scale  = built incrementally: shell r (offsets o with ceil|o| == r, and
 //            everything up to r_min for the first scale) is added to the
 //            counts of r-1.
