@@ -439,15 +439,18 @@ int ks_measure_fp64_rate(ks_ctx *ctx, double *dadd_per_s);
  * memory (r_max > 25, 16, 32 or 64 template bins, 4, 8 or 16 warps),
  * 7 = path 6 with two centres (x and x + 32) per thread (4 or 8 warps),
  * 8 = path 7 with the two centres' counts in 16-bit halves of one word,
- * counted modulo 2^16 and recovered exactly from the previous scale's;
+ * counted modulo 2^16 and recovered exactly from the previous scale's,
+ * 9 = path 4's four adjacent centres per thread for r_max > 25, with the
+ * counts of path 8 and the previous counts as 32-bit words in tensor memory
+ * (16, 32 or 64 template bins, 4 or 8 warps);
  * warps per block; tile rows in y and z. */
 int ks_dense_config(ks_ctx *ctx, int bins, int r_max, int *path, int *warps,
                     int *tile_y, int *tile_z);
 
 /* Force the dense launch configuration for every context of the process
  * (tests use it to cover both paths); path < 0 returns to the autotuner.
- * KS_EINVAL: path > 8, warps outside [1, 16] ([1, 8] for paths 2 to 4;
- * 4, 8 or 16 for path 6; 4 or 8 for paths 7 and 8) or tile_y * tile_z != warps
+ * KS_EINVAL: path > 9, warps outside [1, 16] ([1, 8] for paths 2 to 4;
+ * 4, 8 or 16 for path 6; 4 or 8 for paths 7 to 9) or tile_y * tile_z != warps
  * (path 5: warps = tile_y = 1, tile_z in [1, 1024]).
  * A forced shape that does not fit a given (bins, r_max) is ignored for
  * that call. */

@@ -504,7 +504,20 @@ static std::vector<DenseConfig> dense_candidates(int B, int r_max) {
     std::vector<DenseConfig> out;
     const int shapes[][3] = {{1, 1, 1}, {2, 2, 1}, {2, 1, 2}, {4, 4, 1}, {4, 2, 2}, {8, 8, 1}, {8, 4, 2}, {8, 2, 4},
                              {16, 16, 1}, {16, 4, 4}, {16, 8, 2}, {16, 2, 8}};
-    for (int path : {0, 1, 2, 3, 4, 6, 7, 8})
+    // r_max > 25: only the TMEM paths where they fit (a 16-, 32- or 64-bin
+    // template), in the three shapes that won on the MR-shaped volumes
+    // (paths 1 and 2 took about twice as long there, and every candidate
+    // costs a timed sweep)
+    if (r_max > 25) {
+        const int wide_shapes[][3] = {{4, 4, 1}, {4, 2, 2}, {8, 4, 2}};
+        for (int path : {6, 7, 8, 9})
+            for (auto &s : wide_shapes) {
+                DenseConfig c{path, s[0], s[1], s[2]};
+                if (dense_config_fits(c, B, r_max)) out.push_back(c);
+            }
+        if (!out.empty()) return out;
+    }
+    for (int path : {0, 1, 2, 3, 4, 6, 7, 8, 9})
         for (auto &s : shapes) {
             DenseConfig c{path, s[0], s[1], s[2]};
             if (dense_config_fits(c, B, r_max)) out.push_back(c);
@@ -539,6 +552,32 @@ static int launch_dense_cfg(Ctx *c, cudaStream_t s, Volume *v, int r_min, int r_
     return cuda_err(c, e, "dense launch");
 }
 
+// The dense autotuner's measurements, shared by every context of the
+// process (keyed by device as well): per candidate, its time per computed
+// centre on the tuning slab.  A volume then takes the candidate with the
+// least time for its own computed centres, so a width that leaves part of
+// a wide tile idle (128 centres per warp row in paths 3, 4 and 9) is
+// charged for it without timing the candidates again.
+struct TuneEntry {
+    DenseConfig cfg;
+    double ms_per_centre;
+};
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, DenseTuneKey>, std::vector<TuneEntry>> g_tune;
+
+static DenseConfig tune_pick(const std::vector<TuneEntry> &t, const Volume *v) {
+    DenseConfig best = t[0].cfg;
+    double best_ms = 1e300;
+    for (const TuneEntry &e : t) {
+        const double ms = e.ms_per_centre * (double)dense_computed_centres(e.cfg, v->nx, v->ny, v->nz);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = e.cfg;
+        }
+    }
+    return best;
+}
+
 DenseConfig pick_dense_config(Ctx *c, cudaStream_t s, Volume *v, int r_min, int r_max,
                               int w_norm) {
     if (g_forced_path >= 0) {
@@ -547,49 +586,58 @@ DenseConfig pick_dense_config(Ctx *c, cudaStream_t s, Volume *v, int r_min, int 
     }
     const int64_t nvox = (int64_t)v->nx * v->ny * v->nz;
     const DenseTuneKey key{v->binning.bins, r_max, nvox < (1 << 18) ? 0 : 1};
+    std::vector<TuneEntry> table;
     {
-        std::lock_guard<std::mutex> g(c->mu);
-        auto it = c->tune.find(key);
-        if (it != c->tune.end()) return it->second;
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune.find({c->device, key});
+        if (it != g_tune.end()) table = it->second;
     }
-    auto cands = dense_candidates(v->binning.bins, r_max);
-    DenseConfig best = cands.empty() ? DenseConfig{1, 8, 8, 1} : cands[0];
-    if (cands.size() > 1) {
-        // Time every candidate on the same slab of the volume (outputs to a
-        // temporary buffer) and keep the fastest.  The slab is deep enough
-        // (up to 64 planes) that every candidate's grid spans several waves
-        // of resident blocks; a thin slab favours shapes with a small tail.
-        const int z1 = std::min(v->nz, 64);
-        const size_t n = (size_t)v->nx * v->ny * z1;
-        void *buf = nullptr;
-        if (dev_alloc(c, &buf, n * 9 + 256) == cudaSuccess) {
-            DenseOut o{(double *)buf, (uint8_t *)buf + n * 8, nullptr, nullptr};
-            cudaEvent_t e0, e1;
-            cudaEventCreate(&e0);
-            cudaEventCreate(&e1);
-            float best_ms = 1e30f;
-            for (auto &cfg : cands) {
-                // one untimed launch first: the first launch of a kernel
-                // variant also loads its module
-                bool ok = launch_dense_cfg(c, s, v, r_min, r_max, w_norm, cfg, o, 0, z1) == KS_OK;
-                cudaEventRecord(e0, s);
-                for (int rep = 0; rep < 3 && ok; ++rep)
-                    ok = launch_dense_cfg(c, s, v, r_min, r_max, w_norm, cfg, o, 0, z1) == KS_OK;
-                cudaEventRecord(e1, s);
-                if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best = cfg;
+    if (table.empty()) {
+        auto cands = dense_candidates(v->binning.bins, r_max);
+        if (cands.size() == 1) table.push_back({cands[0], 1.0});
+        if (cands.size() > 1) {
+            // Time every candidate on the same slab of the volume (outputs to
+            // a temporary buffer).  The slab holds about 2^20 centres (at
+            // most 64 planes, at least 4): enough that every candidate's grid
+            // spans several waves of resident blocks (a thin slab favours
+            // shapes with a small tail), few enough that a wide sweep (r_max
+            // = 32: 137 065 updates per centre) times each candidate in tens
+            // of milliseconds.
+            const int64_t plane_c = std::max<int64_t>(1, (int64_t)v->nx * v->ny);
+            const int z_budget = (int)std::max<int64_t>(4, ((int64_t)1 << 20) / plane_c);
+            const int z1 = std::min({v->nz, 64, z_budget});
+            const size_t n = (size_t)v->nx * v->ny * z1;
+            void *buf = nullptr;
+            if (dev_alloc(c, &buf, n * 9 + 256) == cudaSuccess) {
+                DenseOut o{(double *)buf, (uint8_t *)buf + n * 8, nullptr, nullptr};
+                cudaEvent_t e0, e1;
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                for (auto &cfg : cands) {
+                    // one untimed launch first: the first launch of a kernel
+                    // variant also loads its module
+                    bool ok = launch_dense_cfg(c, s, v, r_min, r_max, w_norm, cfg, o, 0, z1) == KS_OK;
+                    cudaEventRecord(e0, s);
+                    for (int rep = 0; rep < 2 && ok; ++rep)
+                        ok = launch_dense_cfg(c, s, v, r_min, r_max, w_norm, cfg, o, 0, z1) == KS_OK;
+                    cudaEventRecord(e1, s);
+                    if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    table.push_back(
+                        {cfg, ms / 2.0 / (double)dense_computed_centres(cfg, v->nx, v->ny, z1)});
                 }
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                cudaStreamSynchronize(s);
+                dev_free(c, buf, n * 9 + 256);
             }
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            cudaStreamSynchronize(s);
-            dev_free(c, buf, n * 9 + 256);
         }
+        if (table.empty()) table.push_back({cands.empty() ? DenseConfig{1, 8, 8, 1} : cands[0], 1.0});
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune[{c->device, key}] = table;
     }
+    const DenseConfig best = tune_pick(table, v);
     std::lock_guard<std::mutex> g(c->mu);
     c->tune[key] = best;
     return best;
@@ -1752,10 +1800,10 @@ int ks_force_dense_config(int path, int warps, int ty, int tz) {
     }
     if (path == 5) {
         if (warps != 1 || ty != 1 || tz < 1 || tz > 1024) return KS_EINVAL;
-    } else if (path >= 6 && path <= 8) {
+    } else if (path >= 6 && path <= 9) {
         if ((warps != 4 && warps != 8 && (warps != 16 || path != 6)) || ty * tz != warps)
             return KS_EINVAL;
-    } else if (path > 8 || warps < 1 || warps > (path >= 2 ? 8 : 16) || ty * tz != warps) {
+    } else if (path > 9 || warps < 1 || warps > (path >= 2 ? 8 : 16) || ty * tz != warps) {
         return KS_EINVAL;
     }
     g_forced_path = path;

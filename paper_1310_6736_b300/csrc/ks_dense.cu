@@ -749,26 +749,39 @@ __global__ void __launch_bounds__(CPL == 1 ? 512 : 256)
 // memory per lane (66 instead of 134 words for 32 bins), so 16 warps fit on
 // an SM instead of 12; the host keeps the blocks per SM within the 512
 // TMEM columns, so the allocation never waits.
-template <int B, bool TM>
+//
+// W (launch path 9, r_max > 25, 16, 32 or 64 bins): the same walk with the
+// counters of centres (0, 1) and (2, 3) in 16-bit halves counted modulo 2^16
+// (WRAP, as launch path 8) and each centre's B previous counts as 32-bit
+// words in TMEM: warp w owns the lane quarter w & 3 of columns 4 B (w >> 2)
+// .. + 4 B - 1, centre j the B of them from 4 B (w >> 2) + j B.  The tables
+// come from global memory: the three-nonzero entries as above, the plane and
+// axis offsets one entry each.
+template <int B, bool TM, bool W = false>
 __global__ void __launch_bounds__(256, TM ? 2 : 1) k_dense4(const DenseArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint32_t s_tmem;
     constexpr int CPL = 4;
-    using Wd = Words<B, false, CPL, TM>;
+    static_assert(!W || (TM && (B == 16 || B == 32 || B == 64)),
+                  "launch path 9: TMEM previous counts, 16, 32 or 64 bins");
+    using Wd = Words<B, W, CPL, TM, W>;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     uint32_t tm_base = 0u;
+    constexpr int kCols4 = W ? 4 * B : 128;     // TMEM columns of a warp's lane quarter
+    const uint32_t tm_cols =
+        (uint32_t)(W ? tm_columns_wide(nwarps, 4 * B) : tm_columns(nwarps));
     if constexpr (TM) {
-        if (warp == 0) tm_alloc(smem_u32(&s_tmem), (uint32_t)tm_columns(nwarps));
+        if (warp == 0) tm_alloc(smem_u32(&s_tmem), tm_cols);
         tm_fence_before();
         __syncthreads();
         tm_fence_after();
-        tm_base = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(128 * (warp >> 2));
+        tm_base = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(kCols4 * (warp >> 2));
     }
     const int tx0 = blockIdx.x * 128, ty0 = blockIdx.y * a.ty, tz0 = a.z0 + blockIdx.z * a.tz;
     const int pz = (int)a.vol.plane, py = (int)a.vol.pitch;
-    const Tab<true> tab{a.ot};
+    const Tab<!W> tab{a.ot};
     const uint32_t cnt_lane = smem_u32(smem + a.cnt_off) + (warp * Wd::kPerLane * 32 + lane) * 4;
     auto word = [&](int w) { return cnt_lane + ((uint32_t)w << 7); };
     // the four bins of offset o, centre j in byte j
@@ -792,7 +805,15 @@ __global__ void __launch_bounds__(256, TM ? 2 : 1) k_dense4(const DenseArgs a) {
 
 #pragma unroll 4
         for (int w = 0; w < Wd::kPerLane; ++w) st_shared_u32(word(w), 0u);
-        if constexpr (TM) {
+        if constexpr (W) {
+            uint32_t z[B];
+#pragma unroll
+            for (int w = 0; w < B; ++w) z[w] = 0u;
+            __syncwarp();
+            tm_wait_st();                  // the previous row's last stores
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) tm_store_words<B>(tm_base + (uint32_t)(j * B), z);
+        } else if constexpr (TM) {
             constexpr int NP = Wd::kNP;
             uint32_t z[NP];
 #pragma unroll
@@ -837,6 +858,25 @@ __global__ void __launch_bounds__(256, TM ? 2 : 1) k_dense4(const DenseArgs a) {
                     for (int m = 0; m < 8; ++m) add4(b[m]);
                     e = en;
                 }
+                if constexpr (W) {
+                    // offsets on a coordinate plane or axis, one entry each
+                    for (int k = tab.rest_start(rho); k < tab.rest_start(rho + 1); ++k) {
+                        const uint32_t f = tab.rest(k);
+                        const int off = ((int)((f >> 16) & 0xffu) - 64) * pz +
+                                        ((int)((f >> 8) & 0xffu) - 64) * py +
+                                        ((int)(f & 0xffu) - 64);
+                        add4(bins4(c0, off));
+                    }
+                    if (i == 0 && rho == kWrapFold && r > kWrapFold) {
+                        __syncwarp();
+                        tm_wait_st();      // the row start's stores
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j)
+                            wrap_fold<B, CPL>(cnt_lane, j, st[j], tm_base + (uint32_t)(j * B),
+                                              tm_base + (uint32_t)((j ^ 1) * B), st[j ^ 1].c0);
+                    }
+                    continue;
+                }
                 // offsets on a coordinate plane: 4 sign mirrors per entry,
                 // +-A +-C with C the component along the row when it is
                 // nonzero (plane 0 or 1), else the y part (a multiple of 16)
@@ -875,9 +915,16 @@ __global__ void __launch_bounds__(256, TM ? 2 : 1) k_dense4(const DenseArgs a) {
                 tm_wait_st();              // the previous scale's stores
             }
 #pragma unroll
-            for (int j = 0; j < CPL; ++j)
-                scale_step<B, false, CPL, TM>(a, cnt_lane, j, i, r, st[j], orow + cx + j,
-                                              cx + j < a.vol.nx, tm_base + 32u * j);
+            for (int j = 0; j < CPL; ++j) {
+                if constexpr (W)
+                    scale_step<B, true, CPL, true, true>(
+                        a, cnt_lane, j, i, r, st[j], orow + cx + j, cx + j < a.vol.nx,
+                        tm_base + (uint32_t)(j * B), tm_base + (uint32_t)((j ^ 1) * B),
+                        st[j ^ 1].c0);
+                else
+                    scale_step<B, false, CPL, TM>(a, cnt_lane, j, i, r, st[j], orow + cx + j,
+                                                  cx + j < a.vol.nx, tm_base + 32u * j);
+            }
         }
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
@@ -892,7 +939,7 @@ __global__ void __launch_bounds__(256, TM ? 2 : 1) k_dense4(const DenseArgs a) {
         tm_fence_before();
         __syncthreads();
         tm_fence_after();
-        if (warp == 0) tm_dealloc(s_tmem, (uint32_t)tm_columns(nwarps));
+        if (warp == 0) tm_dealloc(s_tmem, tm_cols);
     }
 }
 
@@ -1172,7 +1219,7 @@ struct Geometry {
 };
 
 int centres_per_lane(const DenseConfig &c) {
-    return c.path == 6 ? 1 : c.path >= 7 ? 2 : (c.path >= 3 ? 4 : (c.path == 2 ? 2 : 1));
+    return c.path == 6 ? 1 : (c.path == 7 || c.path == 8) ? 2 : (c.path >= 3 ? 4 : (c.path == 2 ? 2 : 1));
 }
 
 Geometry geometry(const DenseConfig &c, int B_, int r_max) {
@@ -1181,7 +1228,7 @@ Geometry geometry(const DenseConfig &c, int B_, int r_max) {
     // counter columns + previous-scale counts per lane (layout of Words)
     const int cpl = centres_per_lane(c);
     const bool wide = is_wide(r_max);
-    const int words = (cpl >= 2 && (!wide || c.path == 8) ? cpl / 2 : cpl) * (B + 1) +
+    const int words = (cpl >= 2 && (!wide || c.path == 8 || c.path == 9) ? cpl / 2 : cpl) * (B + 1) +
                       (c.path == 4 || c.path >= 6 ? 0 : cpl * (wide ? B + 1 : (B + 2) / 2));
     g.padx = (r_max + 15) / 16 * 16;
     g.bx = (g.padx + 32 + r_max + 15) / 16 * 16;
@@ -1263,10 +1310,10 @@ cudaError_t launch_t_tm(const LaunchCtx &lc, const DenseArgs &a, const DenseConf
     return cudaGetLastError();
 }
 
-template <int B, bool TM>
+template <int B, bool TM, bool W = false>
 cudaError_t launch_adj4(const LaunchCtx &lc, const DenseArgs &a, const DenseConfig &cfg,
                         size_t smem) {
-    auto kern = k_dense4<B, TM>;
+    auto kern = k_dense4<B, TM, W>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -1274,7 +1321,7 @@ cudaError_t launch_adj4(const LaunchCtx &lc, const DenseArgs &a, const DenseConf
         // Pad the dynamic shared memory until the blocks that fit on an SM
         // hold at most its 512 TMEM columns, so no tcgen05.alloc waits for
         // another block's columns.
-        const int limit = 512 / tm_columns(cfg.warps);
+        const int limit = 512 / (W ? tm_columns_wide(cfg.warps, 4 * B) : tm_columns(cfg.warps));
         for (;;) {
             int nb = 0;
             e = max_resident_blocks(reinterpret_cast<const void *>(kern), cfg.warps * 32, smem,
@@ -1316,6 +1363,11 @@ cudaError_t launch_b(const LaunchCtx &lc, const DenseArgs &a, const CUtensorMap 
                    : cfg.path == 7 ? launch_t_tm<B, 2>(lc, a, cfg, smem)
                                    : launch_t_tm<B, 2, true>(lc, a, cfg, smem);
         }
+        return cudaErrorInvalidValue;
+    }
+    if (cfg.path == 9) {
+        if constexpr (B == 16 || B == 32 || B == 64)
+            return wide ? launch_adj4<B, true, true>(lc, a, cfg, smem) : cudaErrorInvalidValue;
         return cudaErrorInvalidValue;
     }
     if (cfg.path == 3) return wide ? cudaErrorInvalidValue : launch_adj4<B, false>(lc, a, cfg, smem);
@@ -1460,15 +1512,33 @@ size_t dense_smem_bytes(const DenseConfig &c, int B, int r_max) {
     return geometry(c, B, r_max).total;
 }
 
+int64_t dense_computed_centres(const DenseConfig &c, int nx, int ny, int nz) {
+    int64_t x;
+    if (c.path == 5) {
+        x = (int64_t)(nx + 31) / 32 * 32;
+    } else {
+        const int cpl = centres_per_lane(c), w = 32 * cpl;
+        x = (int64_t)(nx / w) * w;
+        const int rem = nx % w;
+        // two centres per lane: a last tile of at most 32 centres walks one
+        // per lane
+        if (rem) x += cpl == 2 && rem <= 32 ? 32 : w;
+    }
+    const int64_t y = (int64_t)(ny + c.ty - 1) / c.ty * c.ty;
+    const int64_t z = (int64_t)(nz + c.tz - 1) / c.tz * c.tz;
+    return x * y * z;
+}
+
 bool dense_config_fits(const DenseConfig &c, int B, int r_max) {
     if (c.path == 5)
         return !is_wide(r_max) && (template_bins(B) == 16 || template_bins(B) == 32) &&
                c.warps == 1 && c.ty == 1 && c.tz >= 1 && c.tz <= 1024 &&
                slide_smem_bytes(B, r_max + 1) + 1024 <= 227 * 1024;
-    if (c.path >= 6 && c.path <= 8) {
+    if (c.path >= 6 && c.path <= 9) {
         // whole warpgroups (each warp its TMEM lane quarter), 16, 32 or 64
-        // bins, only where the counts need 32 bits; two centres per lane
-        // (paths 7 and 8) allow at most 8 warps (the kernel's launch bounds)
+        // bins, only where the counts need 32 bits; two or four centres per
+        // lane (paths 7 to 9) allow at most 8 warps (the kernels' launch
+        // bounds)
         const int tb = template_bins(B);
         if (!is_wide(r_max) || (tb != 16 && tb != 32 && tb != 64)) return false;
         if ((c.warps != 4 && c.warps != 8 && (c.warps != 16 || c.path != 6)) ||

@@ -230,6 +230,10 @@ cudaError_t dense_upload_constant_table(const uint32_t *c8, const int *c8_start,
 int dense_const_rmax();
 bool dense_config_fits(const DenseConfig &c, int B, int r_max);
 size_t dense_smem_bytes(const DenseConfig &c, int B, int r_max);
+// Centres a launch of shape c computes for a volume (its tiles padded to
+// whole x-tiles and tile rows; centres past the volume are computed but
+// not written).
+int64_t dense_computed_centres(const DenseConfig &c, int nx, int ny, int nz);
 // Kadir-Brady at n listed centres (xyz int32 triples on the device); a
 // centre outside the volume is skipped and sets kStatusBadInput.
 cudaError_t launch_dense_points(const LaunchCtx &lc, const VolDesc &v, const OffsetTables &ot,

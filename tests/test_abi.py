@@ -88,7 +88,9 @@ def test_error_strings_and_no_device_path(libks):
     assert lib.ks_force_dense_config(7, 16, 4, 4) == ks.KS_EINVAL  # two centres per lane: <= 8 warps
     assert lib.ks_force_dense_config(8, 4, 2, 2) == ks.KS_OK
     assert lib.ks_force_dense_config(8, 16, 4, 4) == ks.KS_EINVAL
-    assert lib.ks_force_dense_config(9, 4, 2, 2) == ks.KS_EINVAL
+    assert lib.ks_force_dense_config(9, 4, 2, 2) == ks.KS_OK
+    assert lib.ks_force_dense_config(9, 16, 4, 4) == ks.KS_EINVAL
+    assert lib.ks_force_dense_config(10, 4, 2, 2) == ks.KS_EINVAL
     assert lib.ks_force_dense_config(-1, 0, 0, 0) == ks.KS_OK
     import torch
     if not torch.cuda.is_available():

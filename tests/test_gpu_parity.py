@@ -145,7 +145,7 @@ def test_dense_spheres48_full_volume(ctx, ko, ks_mod, cfg):
     ((70, 3, 2), 16, 2, 12, 0),      # thin slab, radius larger than the volume
     ((75, 6, 4), 8, 24, 28, 0),      # r_max > 25: global offset table, 32-bit previous counts
 ])
-@pytest.mark.parametrize("path", [0, 1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("path", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_dense_random_volumes(ctx, ko, ks_mod, case, path):
     """Every launch path forced on random volumes (a shape that does not fit
     the path, e.g. paths 6 to 8 below r_max = 26, falls back to the
@@ -180,14 +180,18 @@ def test_dense_random_volumes(ctx, ko, ks_mod, case, path):
     ((70, 5, 4), 64, 26, 32, (8, 4, 2, 2)),     # r_min > 25: the first scale recovered at 25
     ((37, 8, 8), 40, 31, 32, (8, 8, 4, 2)),     # r_min = 31: 59 220 voxels after the recovery
     ((130, 3, 3), 32, 4, 32, (8, 4, 4, 1)),     # every scale from 4 to 32
+    ((41, 9, 6), 16, 20, 27, (9, 4, 4, 1)),     # four centres per lane, one ragged x tile
+    ((140, 5, 4), 64, 26, 32, (9, 4, 2, 2)),    # r_min > 25, a 12-centre second tile
+    ((37, 8, 8), 40, 31, 32, (9, 8, 4, 2)),     # r_min = 31, 8 warps
+    ((130, 3, 3), 32, 4, 32, (9, 4, 4, 1)),     # every scale from 4 to 32
 ])
 def test_dense_wide_tmem_path(ctx, ko, ks_mod, case):
-    """Launch paths 6 to 8 (r_max > 25): the 32-bit previous-scale counts
-    in TMEM, one or two centres per lane (path 8: 16-bit counters modulo
-    2^16, recovered from the previous counts).  Every H, W, Y and s_best of
+    """Launch paths 6 to 9 (r_max > 25): the 32-bit previous-scale counts
+    in TMEM, one, two or four centres per lane (paths 8 and 9: 16-bit
+    counters modulo 2^16, recovered from the previous counts).  Every H, W, Y and s_best of
     random volumes equals the oracle's.  Each forced shape fits its path
     (r_max > 25, a 16-, 32- or 64-bin template, 4, 8 or 16 warps, at most 8
-    for paths 7 and 8), so it is the one that runs."""
+    for paths 7 to 9), so it is the one that runs."""
     ks = ks_mod
     dims, B, r_min, r_max, cfg = case
     nx, ny, nz = dims
@@ -239,7 +243,7 @@ def test_dense_mr256_full_volume_sampled(ctx, ko, ks_mod):
 
 
 def test_dense_wrap_counts_past_16_bits(ctx, ko, ks_mod):
-    """Launch path 8 counts modulo 2^16: on a 72^3 volume that is 95% one
+    """Launch paths 8 and 9 count modulo 2^16: on a 72^3 volume that is 95% one
     value, a centre's Ball(32) holds about 130 000 voxels of one bin, so the
     counts wrap twice.  H, W, Y and s_best equal path 7's (32-bit counters)
     everywhere and the oracle's at sampled centres, the middle ones (whole
@@ -253,7 +257,7 @@ def test_dense_wrap_counts_past_16_bits(ctx, ko, ks_mod):
     binning = {"kind": 2, "bins": 64, "shift": 5, "lo": 0, "hi": 2047}
     p = ks.make_params(4, 32, 8, 20)
     out = {}
-    for path in (7, 8):
+    for path in (7, 8, 9):
         try:
             ks.force_dense_config(path, 4, 4, 1)
             v = ctx.create_volume(vol, binning)
@@ -261,8 +265,9 @@ def test_dense_wrap_counts_past_16_bits(ctx, ko, ks_mod):
             ctx.release_volume(v)
         finally:
             ks.force_dense_config(-1)
-    for a7, a8 in zip(out[7], out[8]):
-        assert np.array_equal(a7, a8)
+    for path in (8, 9):
+        for a7, ap in zip(out[7], out[path]):
+            assert np.array_equal(a7, ap)
     Y, s, H, W = out[8]
     cen = np.concatenate([np.array([[36, 36, 36], [35, 37, 36], [32, 32, 39], [39, 39, 32]]),
                           rng.integers(0, n, size=(60, 3))]).astype(np.int32)
