@@ -880,14 +880,16 @@ def run_serving(ctx_factory, ks, synth, rate=50.0, count=2000, pool=32, max_dim=
     kinds = [ks.KS_REQ_DENSE if r["kind"] == "dense" else ks.KS_REQ_SEEDS for r in reqs]
     picks = [r["vol_seed"] % pool for r in reqs]
     params = [ks.make_params(w.r_min, w.r_max, w.stride, w.max_iter) for w in ws]
-    # warm-up: the dense autotuner's classes and every kernel variant
+    # warm-up: every pool volume once as a seed request and once as a dense
+    # sweep, so the dense autotuner has timed every class it will meet
+    # (its measurements are shared by every context of the process, so
+    # both arms below run with the same tuned shapes) and every kernel
+    # variant is loaded
     ctx = ctx_factory()
     if wave_iters is not None:
         ctx.set_serve_wave_iters(wave_iters)
     for i in range(pool):
         for k in (ks.KS_REQ_SEEDS, ks.KS_REQ_DENSE):
-            if k == ks.KS_REQ_DENSE and i >= 4:
-                continue
             rid = ctx.submit(ws[i].volume, ws[i].binning, params[i], kind=k)
             ctx.poll(rid, -1)
             ctx.release_result(rid)

@@ -21,15 +21,16 @@
 //               request's finished counter.  A request that becomes ready
 //               joins the next wave; up to two waves are queued on the
 //               stream, so the device never idles between them;
-//     dense     sweeps run whole on the lowest-priority stream, one at a
-//               time from a host queue in the order they became ready: their
-//               blocks are short, so the seed waves (high priority) take SMs
-//               as dense blocks retire, and dense blocks fill the SMs the
-//               waves leave idle.  (Handing every ready sweep to the stream
-//               at once raised the median latency of 2000 requests at 50 /s
-//               from 1.1 to 10.3 s and the 99th percentile from 40 to 58 s;
-//               moving a sweep that had waited long to a high-priority
-//               stream traded median latency for almost no tail);
+//     dense     sweeps run whole on their own stream, one at a time from a
+//               host queue in the order they became ready, at the seed
+//               waves' priority: blocks of both take SMs as others retire,
+//               and each fills the SMs the other leaves idle.  (Handing
+//               every ready sweep to the stream at once raised the median
+//               latency of 2000 requests at 50 /s from 1.1 to 10.3 s and the
+//               99th percentile from 40 to 58 s.  Sweeps at the lowest
+//               priority gave a median of 0.21 s against 1.08 s, but 37.7
+//               against 40.1 volumes/s and a 99th percentile of 19.7 against
+//               14.9 s);
 //     results   a finished request's records go to pinned host memory on
 //               the download stream; when that copy's event has completed
 //               the request is done and its device memory returns to the
@@ -704,7 +705,7 @@ static ServeState *ensure_serve(Ctx *c) {
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
     bool ok = cudaStreamCreateWithPriority(&S->s_up, cudaStreamNonBlocking, hi) == cudaSuccess &&
               cudaStreamCreateWithPriority(&S->s_seed, cudaStreamNonBlocking, hi) == cudaSuccess &&
-              cudaStreamCreateWithPriority(&S->s_dense, cudaStreamNonBlocking, lo) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&S->s_dense, cudaStreamNonBlocking, hi) == cudaSuccess &&
 
               cudaStreamCreateWithPriority(&S->s_down, cudaStreamNonBlocking, hi) == cudaSuccess;
     void *p = nullptr;
